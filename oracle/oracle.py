@@ -1,0 +1,362 @@
+"""Python face of the FP64 oracle (TEST INFRASTRUCTURE ONLY).
+
+Only the tests, `__graft_entry__.smoke()` and the CPU-baseline leg of
+`bench.py` may import this module.  It loads `liboracle.so` (plain C, FP64,
+built from `dogs_oracle.c` by `build()` below) and composes its per-view
+functions into multi-view renders, the analytic backward, the x-step (Adam on
+the loss plus the ADMM penalty, Eq. 8a / 12a) and the consensus step (Eq. 8b-c,
+12b-c), in the order the paper states them.  D-SSIM (the lambda term of Eq. 3)
+is written here in numpy, from its definition.
+
+Parity status: pinned by tests/test_oracle_*.py (closed forms, brute force,
+central finite differences, hand-worked ADMM examples, textbook ADMM
+convergence on quadratics).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import List, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dogs_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE FP64, no contraction, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", _LIB, _SRC, "-lm"])
+    return _LIB
+
+
+class OcCam(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32),
+                ("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("R", C.c_double * 9), ("t", C.c_double * 3), ("campos", C.c_double * 3),
+                ("near_z", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        dp, ip, fp, u32p, u64p, u8p, i64p = (C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                                              C.POINTER(C.c_float), C.POINTER(C.c_uint32),
+                                              C.POINTER(C.c_uint64), C.POINTER(C.c_uint8),
+                                              C.POINTER(C.c_int64))
+        _lib.oc_sh_basis.restype = C.c_double
+        _lib.oc_sh_basis.argtypes = [C.c_int, C.c_int, dp, dp]
+        _lib.oc_project.restype = C.c_int
+        _lib.oc_project.argtypes = [C.c_int, C.c_int, dp, C.POINTER(OcCam), C.c_int, C.c_int,
+                                    dp, ip, fp, dp]
+        _lib.oc_bin_sort.restype = C.c_int64
+        _lib.oc_bin_sort.argtypes = [C.c_int64, ip, ip, fp, ip, ip, ip, C.c_int64, C.c_int64,
+                                     u64p, u32p, u32p]
+        _lib.oc_rasterize_fwd.restype = None
+        _lib.oc_rasterize_fwd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, u32p, u32p,
+                                          dp, dp, dp, dp, u32p, dp]
+        _lib.oc_rasterize_bwd.restype = None
+        _lib.oc_rasterize_bwd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, u32p, u32p,
+                                          dp, dp, dp, dp]
+        _lib.oc_project_bwd.restype = None
+        _lib.oc_project_bwd.argtypes = [C.c_int, C.c_int, dp, C.POINTER(OcCam), C.c_int, C.c_int,
+                                        dp, dp]
+        _lib.oc_adam_admm_step.restype = None
+        _lib.oc_adam_admm_step.argtypes = [C.c_int64, C.c_int, dp, dp, dp, dp, dp, dp, ip, u8p, dp, dp,
+                                           C.c_double, C.c_double, C.c_double, C.c_int]
+        _lib.oc_consensus.restype = None
+        _lib.oc_consensus.argtypes = [C.c_int64, C.c_int, i64p, ip, dp, dp, dp, C.c_double, dp, dp]
+    return _lib
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+REC_N = 16
+(REC_MX, REC_MY, REC_A, REC_B, REC_C, REC_OP, REC_R, REC_G, REC_BL, REC_DEPTH,
+ REC_RAWR, REC_RAWG, REC_RAWB, REC_RADIUS, REC_TILES, REC_VIS) = range(16)
+
+
+# --------------------------------------------------------------------------
+# layout conversion (oracle's own layout: P = 11 + 3K doubles per Gaussian)
+# --------------------------------------------------------------------------
+def n_params(sh_degree: int) -> int:
+    return 11 + 3 * (sh_degree + 1) ** 2
+
+
+def params_from(g) -> np.ndarray:
+    n = g.n
+    K = g.sh.shape[1]
+    P = 11 + 3 * K
+    x = np.empty((n, P), np.float64)
+    x[:, 0:3] = g.means
+    x[:, 3:7] = g.quats
+    x[:, 7:10] = g.log_scales
+    x[:, 10:10 + 3 * K] = g.sh.reshape(n, 3 * K)
+    x[:, 10 + 3 * K] = g.opacity_logits
+    return x
+
+
+def split_params(x: np.ndarray, sh_degree: int) -> dict:
+    """Return parameter groups (the paper's p, q, s, f, o) as views."""
+    K = (sh_degree + 1) ** 2
+    return {"mean": x[:, 0:3], "quat": x[:, 3:7], "scale": x[:, 7:10],
+            "sh": x[:, 10:10 + 3 * K].reshape(-1, K, 3), "opacity": x[:, 10 + 3 * K]}
+
+
+def cam_struct(c) -> OcCam:
+    s = OcCam()
+    s.width, s.height = int(c.width), int(c.height)
+    s.fx, s.fy, s.cx, s.cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+    for i in range(9):
+        s.R[i] = float(np.asarray(c.R, np.float32).reshape(9)[i])
+    for i in range(3):
+        s.t[i] = float(np.asarray(c.t, np.float32)[i])
+        s.campos[i] = float(np.asarray(c.campos, np.float32)[i])
+    s.near_z = float(np.float32(c.near))
+    return s
+
+
+def sh_basis(l: int, m: int, d) -> tuple:
+    d = np.ascontiguousarray(d, np.float64)
+    g = np.zeros(3, np.float64)
+    v = lib().oc_sh_basis(l, m, _p(d, C.c_double), _p(g, C.c_double))
+    return v, g
+
+
+# --------------------------------------------------------------------------
+# per-view pieces
+# --------------------------------------------------------------------------
+def project(x: np.ndarray, sh_degree: int, cam, tile_w: int, tile_h: int) -> dict:
+    x = np.ascontiguousarray(x, np.float64)
+    n = x.shape[0]
+    rec = np.zeros((n, REC_N), np.float64)
+    rect = np.zeros((n, 4), np.int32)
+    dk = np.zeros(n, np.float32)
+    mg = np.zeros(n, np.float64)
+    cs = cam_struct(cam)
+    lib().oc_project(n, sh_degree, _p(x, C.c_double), C.byref(cs), tile_w, tile_h,
+                     _p(rec, C.c_double), _p(rect, C.c_int32), _p(dk, C.c_float), _p(mg, C.c_double))
+    return {"rec": rec, "rect": rect, "depth_key": dk, "margin": mg,
+            "visible": rec[:, REC_VIS].astype(np.int32),
+            "tiles": rec[:, REC_TILES].astype(np.int64)}
+
+
+def tiles_of(cam, tile_w: int, tile_h: int) -> tuple:
+    return (cam.width + tile_w - 1) // tile_w, (cam.height + tile_h - 1) // tile_h
+
+
+class ViewPlan:
+    """Numbering of records, tiles and pixels over a batch of views.
+
+    View v renders the Gaussians [rows[v][0], rows[v][1]) of the parameter
+    array; its records are numbered from rec_off[v] (record = rec_off[v] +
+    local index) and its tiles from tile_off[v]."""
+
+    def __init__(self, cams: Sequence, rows: Sequence[tuple], tile_w: int, tile_h: int):
+        self.cams, self.rows, self.tw, self.th = list(cams), list(rows), tile_w, tile_h
+        self.rec_off, self.tile_off, self.tiles_x = [], [], []
+        r = t = 0
+        for c, (b, e) in zip(self.cams, self.rows):
+            tx, ty = tiles_of(c, tile_w, tile_h)
+            self.rec_off.append(r)
+            self.tile_off.append(t)
+            self.tiles_x.append(tx)
+            r += e - b
+            t += tx * ty
+        self.n_rec, self.n_tiles = r, t
+
+
+def project_views(x: np.ndarray, sh_degree: int, plan: ViewPlan) -> dict:
+    recs, rects, dks, mgs, views = [], [], [], [], []
+    for v, (c, (b, e)) in enumerate(zip(plan.cams, plan.rows)):
+        p = project(x[b:e], sh_degree, c, plan.tw, plan.th)
+        recs.append(p["rec"]); rects.append(p["rect"]); dks.append(p["depth_key"])
+        mgs.append(p["margin"]); views.append(np.full(e - b, v, np.int32))
+    cat = lambda a, dt, sh: np.concatenate(a) if a else np.zeros(sh, dt)
+    return {"rec": cat(recs, np.float64, (0, REC_N)), "rect": cat(rects, np.int32, (0, 4)),
+            "depth_key": cat(dks, np.float32, (0,)), "margin": cat(mgs, np.float64, (0,)),
+            "view": cat(views, np.int32, (0,))}
+
+
+def bin_sort(proj: dict, plan: ViewPlan) -> dict:
+    n = proj["rec"].shape[0]
+    vis = np.ascontiguousarray(proj["rec"][:, REC_VIS].astype(np.int32))
+    view = np.ascontiguousarray(proj["view"], np.int32)
+    rect = np.ascontiguousarray(proj["rect"], np.int32)
+    dk = np.ascontiguousarray(proj["depth_key"], np.float32)
+    toff = np.asarray(plan.tile_off, np.int32)
+    tx = np.asarray(plan.tiles_x, np.int32)
+    ranges = np.zeros((plan.n_tiles, 2), np.uint32)
+    empty64 = np.zeros(1, np.uint64)
+    empty32 = np.zeros(1, np.uint32)
+    M = lib().oc_bin_sort(n, _p(view, C.c_int32), _p(rect, C.c_int32), _p(dk, C.c_float),
+                          _p(vis, C.c_int32), _p(toff, C.c_int32), _p(tx, C.c_int32),
+                          plan.n_tiles, 0, _p(empty64, C.c_uint64), _p(empty32, C.c_uint32),
+                          _p(ranges, C.c_uint32))
+    keys = np.zeros(max(M, 1), np.uint64)
+    vals = np.zeros(max(M, 1), np.uint32)
+    lib().oc_bin_sort(n, _p(view, C.c_int32), _p(rect, C.c_int32), _p(dk, C.c_float),
+                      _p(vis, C.c_int32), _p(toff, C.c_int32), _p(tx, C.c_int32),
+                      plan.n_tiles, M, _p(keys, C.c_uint64), _p(vals, C.c_uint32),
+                      _p(ranges, C.c_uint32))
+    return {"keys": keys[:M], "vals": vals[:M], "ranges": ranges, "M": int(M)}
+
+
+def rasterize_fwd(proj: dict, bins: dict, plan: ViewPlan, bg=(0.0, 0.0, 0.0)) -> List[dict]:
+    out = []
+    rec = np.ascontiguousarray(proj["rec"])
+    bgv = np.asarray(bg, np.float64)
+    vals = np.ascontiguousarray(bins["vals"]) if bins["M"] else np.zeros(1, np.uint32)
+    for v, c in enumerate(plan.cams):
+        W, H = c.width, c.height
+        img = np.zeros((3, H, W)); Tf = np.zeros((H, W)); last = np.zeros((H, W), np.uint32)
+        mg = np.zeros((H, W))
+        lib().oc_rasterize_fwd(W, H, plan.tw, plan.th, plan.tile_off[v], _p(vals, C.c_uint32),
+                               _p(bins["ranges"], C.c_uint32), _p(rec, C.c_double),
+                               _p(bgv, C.c_double), _p(img, C.c_double), _p(Tf, C.c_double),
+                               _p(last, C.c_uint32), _p(mg, C.c_double))
+        out.append({"image": img, "T_final": Tf, "last": last, "margin": mg})
+    return out
+
+
+def rasterize_bwd(proj: dict, bins: dict, plan: ViewPlan, dL_dimages: Sequence[np.ndarray],
+                  bg=(0.0, 0.0, 0.0)) -> np.ndarray:
+    rec = np.ascontiguousarray(proj["rec"])
+    drec = np.zeros((rec.shape[0], 9))
+    bgv = np.asarray(bg, np.float64)
+    vals = np.ascontiguousarray(bins["vals"]) if bins["M"] else np.zeros(1, np.uint32)
+    for v, c in enumerate(plan.cams):
+        g = np.ascontiguousarray(dL_dimages[v], np.float64)
+        lib().oc_rasterize_bwd(c.width, c.height, plan.tw, plan.th, plan.tile_off[v],
+                               _p(vals, C.c_uint32), _p(bins["ranges"], C.c_uint32),
+                               _p(rec, C.c_double), _p(bgv, C.c_double), _p(g, C.c_double),
+                               _p(drec, C.c_double))
+    return drec
+
+
+def project_bwd(x: np.ndarray, sh_degree: int, plan: ViewPlan, drec: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float64)
+    dx = np.zeros_like(x)
+    for v, (c, (b, e)) in enumerate(zip(plan.cams, plan.rows)):
+        cs = cam_struct(c)
+        r0 = plan.rec_off[v]
+        dr = np.ascontiguousarray(drec[r0:r0 + (e - b)])
+        part = np.zeros((e - b, x.shape[1]))
+        lib().oc_project_bwd(e - b, sh_degree, _p(np.ascontiguousarray(x[b:e]), C.c_double),
+                             C.byref(cs), plan.tw, plan.th, _p(dr, C.c_double), _p(part, C.c_double))
+        dx[b:e] += part
+    return dx
+
+
+# --------------------------------------------------------------------------
+# whole passes
+# --------------------------------------------------------------------------
+def render(x: np.ndarray, sh_degree: int, plan: ViewPlan, bg=(0.0, 0.0, 0.0)) -> dict:
+    proj = project_views(x, sh_degree, plan)
+    bins = bin_sort(proj, plan)
+    views = rasterize_fwd(proj, bins, plan, bg)
+    return {"proj": proj, "bins": bins, "views": views}
+
+
+def backward(x: np.ndarray, sh_degree: int, plan: ViewPlan, fwd: dict,
+             dL_dimages: Sequence[np.ndarray], bg=(0.0, 0.0, 0.0)) -> dict:
+    drec = rasterize_bwd(fwd["proj"], fwd["bins"], plan, dL_dimages, bg)
+    return {"drec": drec, "dparams": project_bwd(x, sh_degree, plan, drec)}
+
+
+# --------------------------------------------------------------------------
+# losses (Eq. 3): L1 and D-SSIM, means over all channels and pixels
+# --------------------------------------------------------------------------
+def l1(img: np.ndarray, tgt: np.ndarray) -> tuple:
+    d = np.asarray(img, np.float64) - np.asarray(tgt, np.float64)
+    return float(np.abs(d).mean()), np.sign(d) / d.size
+
+
+def gaussian_window(size: int = 11, sigma: float = 1.5) -> np.ndarray:
+    ax = np.arange(size) - (size - 1) / 2.0
+    w = np.exp(-(ax ** 2) / (2.0 * sigma ** 2))
+    return w / w.sum()
+
+
+def _filt(a: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """'same'-size 2D correlation of each channel with the separable window
+    w x w, zero padding (scipy's routine as the library primitive)."""
+    from scipy.ndimage import correlate1d
+    a = correlate1d(a, w, axis=-1, mode="constant", cval=0.0)
+    return correlate1d(a, w, axis=-2, mode="constant", cval=0.0)
+
+
+def ssim(img: np.ndarray, tgt: np.ndarray, C1: float = 0.01 ** 2, C2: float = 0.03 ** 2) -> tuple:
+    """Mean SSIM (Wang et al. 2004) with an 11x11 Gaussian window, sigma 1.5,
+    and its gradient w.r.t. img.  S = (2 m1 m2 + C1)(2 s12 + C2) /
+    ((m1^2 + m2^2 + C1)(s1 + s2 + C2)), moments taken with the window."""
+    x = np.asarray(img, np.float64)
+    y = np.asarray(tgt, np.float64)
+    w = gaussian_window()
+    m1, m2 = _filt(x, w), _filt(y, w)
+    e11, e22, e12 = _filt(x * x, w), _filt(y * y, w), _filt(x * y, w)
+    s1, s2, s12 = e11 - m1 * m1, e22 - m2 * m2, e12 - m1 * m2
+    A1, A2 = 2 * m1 * m2 + C1, 2 * s12 + C2
+    B1, B2 = m1 * m1 + m2 * m2 + C1, s1 + s2 + C2
+    S = (A1 * A2) / (B1 * B2)
+    N = S.size
+    # partials of S w.r.t. m1, e11, e12 (m2, e22 do not depend on x)
+    dS_dA1 = A2 / (B1 * B2)
+    dS_dA2 = A1 / (B1 * B2)
+    dS_dB1 = -S / B1
+    dS_dB2 = -S / B2
+    dS_dm1 = dS_dA1 * 2 * m2 + dS_dA2 * 2 * (-m2) + dS_dB1 * 2 * m1 + dS_dB2 * (-2 * m1)
+    dS_de11 = dS_dB2
+    dS_de12 = dS_dA2 * 2
+    # adjoint of the (symmetric-window) correlation is the same correlation
+    g = _filt(dS_dm1 / N, w) + 2 * x * _filt(dS_de11 / N, w) + y * _filt(dS_de12 / N, w)
+    return float(S.mean()), g
+
+
+def dssim_loss(img: np.ndarray, tgt: np.ndarray, lam: float = 0.2) -> tuple:
+    """(1 - lam) L1 + lam (1 - SSIM): Eq. 3 with lambda = 0.2."""
+    a, ga = l1(img, tgt)
+    s, gs = ssim(img, tgt)
+    return (1 - lam) * a + lam * (1 - s), (1 - lam) * ga - lam * gs
+
+
+# --------------------------------------------------------------------------
+# ADMM (Eq. 8a-c, 12a-c; Sec. 3.3)
+# --------------------------------------------------------------------------
+def adam_admm_step(x, grad, m, v, z, u, copy_gid, shared, rho, lr, sh_degree,
+                   b1=0.9, b2=0.999, eps=1e-15, step=1) -> None:
+    """In place on x, m, v (all n_copies x P, float64, C-contiguous)."""
+    for a in (x, grad, m, v, z, u):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    gid = np.ascontiguousarray(copy_gid, np.int32)
+    sh = np.ascontiguousarray(shared, np.uint8)
+    rho = np.ascontiguousarray(rho, np.float64)
+    lr = np.ascontiguousarray(lr, np.float64)
+    lib().oc_adam_admm_step(x.shape[0], sh_degree, _p(x, C.c_double), _p(grad, C.c_double),
+                            _p(m, C.c_double), _p(v, C.c_double), _p(z, C.c_double),
+                            _p(u, C.c_double), _p(gid, C.c_int32), _p(sh, C.c_uint8),
+                            _p(rho, C.c_double), _p(lr, C.c_double), b1, b2, eps, step)
+
+
+def consensus(x, u, z, g_off, g_copies, sh_degree, alpha=1.0, rho=(1, 1, 1, 1, 1)) -> np.ndarray:
+    """In place on u and z; returns the 10 residual sums (Eq. 9)."""
+    for a in (x, u, z):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    go = np.ascontiguousarray(g_off, np.int64)
+    gc = np.ascontiguousarray(g_copies, np.int32)
+    res = np.zeros(10)
+    rr = np.ascontiguousarray(rho, np.float64)
+    lib().oc_consensus(z.shape[0], sh_degree, _p(go, C.c_int64), _p(gc, C.c_int32),
+                       _p(x, C.c_double), _p(u, C.c_double), _p(z, C.c_double), float(alpha),
+                       _p(rr, C.c_double), _p(res, C.c_double))
+    return res

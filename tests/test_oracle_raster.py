@@ -1,0 +1,194 @@
+"""Pins of the oracle's binning and compositing (Sec. 3.1, Eq. 2)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2405_13943_b300 import synth as S
+
+
+def one(mean, log_scale, ologit, colour, quat=(1, 0, 0, 0)):
+    Y00 = 0.5 / math.sqrt(math.pi)
+    sh = ((np.asarray(colour, np.float64) - 0.5) / Y00).reshape(1, 1, 3)
+    return S.Gaussians(np.asarray([mean], np.float32), np.asarray([quat], np.float32),
+                       np.asarray([[log_scale] * 3], np.float32), np.asarray([ologit], np.float32),
+                       sh.astype(np.float32))
+
+
+def render1(O, g, cam, tw=16, th=16, bg=(0, 0, 0)):
+    plan = O.ViewPlan([cam], [(0, g.n)], tw, th)
+    f = O.render(O.params_from(g), g.sh_degree, plan, bg)
+    return f, plan
+
+
+def test_lone_isotropic_gaussian_closed_form(oracle):
+    """One isotropic Gaussian (scale sigma) on the optical axis at depth tz,
+    opacity o, colour c, black background: pixel = c o exp(-d^2 / (2 s^2)),
+    s^2 = (f sigma / tz)^2 + 0.3, wherever 1/255 <= alpha < 0.99 and the pixel's
+    tile lies in the Gaussian's tile rectangle; 0 elsewhere."""
+    O = oracle
+    cam = S.cube_camera(96, 80, f=110.0, distance=4.0)
+    sigma, o_logit, c = math.exp(-2.0), 0.4, np.array([0.9, 0.5, 0.2])
+    g = one([0.0, 0.0, 0.0], -2.0, o_logit, c)
+    f, plan = render1(O, g, cam)
+    img = f["views"][0]["image"]
+    rec = f["proj"]["rec"][0]
+    x0, y0, x1, y1 = f["proj"]["rect"][0]
+    o = 1 / (1 + math.exp(-np.float32(o_logit)))
+    sig = float(np.float32(sigma))
+    s2 = (110.0 * math.exp(float(np.float32(-2.0))) / 4.0) ** 2 + 0.3
+    colour = rec[O.REC_R:O.REC_R + 3]
+    np.testing.assert_allclose(colour, c, rtol=1e-6)
+    want = np.zeros_like(img)
+    for py in range(80):
+        for px in range(96):
+            if not (x0 <= px // 16 < x1 and y0 <= py // 16 < y1):
+                continue
+            d2 = (px + 0.5 - 48.0) ** 2 + (py + 0.5 - 40.0) ** 2
+            a = o * math.exp(-d2 / (2 * s2))
+            if a < 1 / 255:
+                continue
+            want[:, py, px] = colour * min(a, 0.99)
+    np.testing.assert_allclose(img, want, atol=1e-14)
+    assert sig > 0
+
+
+def test_occlusion_and_transmittance_stop(oracle):
+    """Three wide Gaussians on the axis, the optical axis through a pixel
+    centre: alpha_1 = 0.99 (clamped), alpha_2 = 0.98 composited with
+    T = 0.01, then T = 2e-4; alpha_3 = 0.6 would give T = 8e-5 < 1e-4, so the
+    third is not composited and the pixel ignores everything behind."""
+    O = oracle
+    cam = S.cube_camera(129, 129, f=100.0, distance=4.0)
+    cam.cx = cam.cy = 64.5
+    c1, c2, c3 = [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]
+    logit = lambda p: math.log(p / (1 - p))
+    parts = [one([0, 0, 0.0], -0.5, 10.0, c1), one([0, 0, 1.0], -0.5, logit(0.98), c2),
+             one([0, 0, 2.0], -0.5, logit(0.6), c3)]
+    g = S.Gaussians.concat(parts)
+    f, _ = render1(O, g, cam)
+    v = f["views"][0]
+    o2 = 1 / (1 + math.exp(-float(np.float32(logit(0.98)))))
+    want = 0.99 * np.array(c1) + o2 * 0.01 * np.array(c2)
+    np.testing.assert_allclose(v["image"][:, 64, 64], want, rtol=1e-6, atol=1e-12)
+    assert v["T_final"][64, 64] == pytest.approx(0.01 * (1 - o2), rel=1e-12)
+    assert v["last"][64, 64] == 2
+
+
+def test_transmittance_product_no_stop(oracle):
+    """Layers that never reach the stop: T_final = prod (1 - alpha_i) and
+    C = sum c_i alpha_i prod_{j<i}(1 - alpha_j) + T_final * bg."""
+    O = oracle
+    cam = S.cube_camera(33, 33, f=100.0, distance=4.0)
+    cam.cx = cam.cy = 16.5
+    logit = lambda p: math.log(p / (1 - p))
+    ps = [0.3, 0.5, 0.2, 0.7]
+    cols = [[0.1, 0.2, 0.3], [0.9, 0.1, 0.5], [0.4, 0.4, 0.4], [0.2, 0.8, 0.6]]
+    g = S.Gaussians.concat([one([0, 0, 0.5 * i], 0.0, logit(p), c) for i, (p, c) in enumerate(zip(ps, cols))])
+    bg = (0.25, 0.5, 0.75)
+    f, _ = render1(O, g, cam, bg=bg)
+    al = [1 / (1 + math.exp(-float(np.float32(logit(p))))) for p in ps]
+    Y00 = 0.5 / math.sqrt(math.pi)
+    cols = [np.asarray(np.float32((np.asarray(c) - 0.5) / Y00), np.float64) * Y00 + 0.5 for c in cols]
+    T, C = 1.0, np.zeros(3)
+    for a, c in zip(al, cols):
+        C += np.asarray(c) * a * T
+        T *= 1 - a
+    C += T * np.asarray(bg)
+    v = f["views"][0]
+    np.testing.assert_allclose(v["image"][:, 16, 16], C, rtol=1e-12)
+    assert v["T_final"][16, 16] == pytest.approx(T, rel=1e-12)
+    assert v["last"][16, 16] == 4
+
+
+def brute_force(O, x, deg, cams, rows, tw, th, bg):
+    """Per pixel: gather exactly the records whose tile rectangle contains
+    the pixel's tile, order them by (float depth, record index) and
+    composite front to back.  No keys, no sort of a global list, no ranges."""
+    out = []
+    for v, (cam, (b, e)) in enumerate(zip(cams, rows)):
+        p = O.project(x[b:e], deg, cam, tw, th)
+        rec, rect, dk, vis = p["rec"], p["rect"], p["depth_key"], p["visible"]
+        img = np.zeros((3, cam.height, cam.width))
+        for py in range(cam.height):
+            for px in range(cam.width):
+                tx, ty = px // tw, py // th
+                cand = [i for i in range(e - b) if vis[i] and rect[i, 0] <= tx < rect[i, 2]
+                        and rect[i, 1] <= ty < rect[i, 3]]
+                cand.sort(key=lambda i: (float(dk[i]), i))
+                T, C = 1.0, np.zeros(3)
+                for i in cand:
+                    r = rec[i]
+                    dx, dy = r[O.REC_MX] - (px + 0.5), r[O.REC_MY] - (py + 0.5)
+                    pw = -0.5 * (r[O.REC_A] * dx * dx + r[O.REC_C] * dy * dy) - r[O.REC_B] * dx * dy
+                    if pw > 0:
+                        continue
+                    a = min(0.99, r[O.REC_OP] * math.exp(pw))
+                    if a < 1 / 255:
+                        continue
+                    if T * (1 - a) < 1e-4:
+                        break
+                    C += r[O.REC_R:O.REC_R + 3] * a * T
+                    T *= 1 - a
+                img[:, py, px] = C + T * np.asarray(bg)
+        out.append(img)
+    return out
+
+
+def test_tiled_equals_per_pixel_brute_force(oracle):
+    """Two views with ragged edges (40x35 and 23x47 pixels, 16x16 and 8x16
+    tiles) over different Gaussian ranges."""
+    O = oracle
+    g = S.cube_scene(60, 77, log_scale_mu=-2.3)
+    x = O.params_from(g)
+    for tw, th in ((16, 16), (8, 16)):
+        cams = [S.cube_camera(40, 35, f=30.0), S.cube_camera(23, 47, f=25.0)]
+        rows = [(0, 40), (20, 60)]
+        plan = O.ViewPlan(cams, rows, tw, th)
+        bg = (0.1, 0.2, 0.3)
+        f = O.render(x, 0, plan, bg)
+        want = brute_force(O, x, 0, cams, rows, tw, th, bg)
+        for v in range(2):
+            np.testing.assert_allclose(f["views"][v]["image"], want[v], atol=1e-12)
+
+
+def test_keys_values_ranges_properties(oracle):
+    O = oracle
+    g = S.cube_scene(300, 9)
+    cams = [S.cube_camera(128, 128), S.cube_camera(64, 48, f=60.0)]
+    plan = O.ViewPlan(cams, [(0, 300), (100, 250)], 16, 16)
+    x = O.params_from(g)
+    proj = O.project_views(x, 0, plan)
+    b = O.bin_sort(proj, plan)
+    keys, vals, ranges = b["keys"], b["vals"], b["ranges"]
+    # ascending (key, value)
+    order = np.lexsort((vals, keys))
+    np.testing.assert_array_equal(order, np.arange(len(keys)))
+    # every record once per tile of its rectangle, with its depth bits
+    vis = proj["rec"][:, O.REC_VIS] == 1
+    assert b["M"] == int(proj["rec"][vis, O.REC_TILES].sum())
+    for r in np.nonzero(vis)[0][:50]:
+        v = proj["view"][r]
+        x0, y0, x1, y1 = proj["rect"][r]
+        tiles = sorted(plan.tile_off[v] + ty * plan.tiles_x[v] + tx for ty in range(y0, y1) for tx in range(x0, x1))
+        mine = sorted((keys[vals == r] >> np.uint64(32)).astype(np.int64).tolist())
+        assert mine == tiles
+        assert np.all((keys[vals == r] & np.uint64(0xFFFFFFFF)) == proj["depth_key"][r:r + 1].view(np.uint32)[0])
+    # ranges partition the sorted list by tile
+    assert ranges[0, 0] == 0 and ranges[-1, 1] == len(keys)
+    np.testing.assert_array_equal(ranges[1:, 0], ranges[:-1, 1])
+    for t in range(plan.n_tiles):
+        s, e = ranges[t]
+        assert np.all((keys[s:e] >> np.uint64(32)) == t)
+
+
+def test_empty_scene_gives_background(oracle):
+    O = oracle
+    g = S.cube_scene(0, 1)
+    cam = S.cube_camera(20, 20)
+    plan = O.ViewPlan([cam], [(0, 0)], 16, 16)
+    f = O.render(O.params_from(g), 0, plan, (0.3, 0.2, 0.1))
+    v = f["views"][0]
+    np.testing.assert_array_equal(v["image"][0], 0.3)
+    np.testing.assert_array_equal(v["T_final"], 1.0)
+    assert f["bins"]["M"] == 0
