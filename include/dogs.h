@@ -1,0 +1,239 @@
+/*
+ * dogs.h -- C ABI of libdogs, the B300 (sm_103a) hot path of DOGS
+ * (distributed 3D Gaussian Splatting by ADMM Gaussian consensus).
+ *
+ * The library computes, on one GPU:
+ *   - the differentiable tile rasteriser of 3D Gaussian Splatting (Sec. 3.1:
+ *     Gaussian primitive, Eq. 1; Sigma = R S S^T R^T; alpha blending, Eq. 2):
+ *     dg_project, dg_bin_sort, dg_rasterize_fwd, dg_rasterize_bwd, and the
+ *     loss of Eq. 3 (dg_loss_l1, dg_loss_dssim);
+ *   - the block ADMM of Sec. 3.2: the x-step (Eq. 8a / 12a) as one Adam step
+ *     on the loss plus the penalty rho/2 ||x - z + u||^2 (dg_adam_admm_step),
+ *     and the consensus z = mean(x + u), u += x - z (Eq. 8b-c / 12b-c, with
+ *     over-relaxation and the residuals of Sec. 3.3) (dg_admm_consensus);
+ *   - rendering of the global model for serving (dg_render).
+ * The K block-local models are batched instances in one launch per step.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an int status (DG_OK or a DG_ERR_* code below).
+ *     Host-side argument errors are detected before anything is launched.
+ *   - The caller owns all memory.  No call allocates, frees or synchronises;
+ *     device buffers are passed as plain device pointers, host tables as
+ *     host pointers, and work is enqueued on the cudaStream_t passed as
+ *     `stream` (NULL = legacy default stream).  Calls are re-entrant and can
+ *     be captured in a CUDA graph.
+ *   - Conditions found on the device (instance capacity exceeded) are OR-ed
+ *     into the caller's device word `dev_status` (DG_STATUS_* bits), to be
+ *     read after the stream is synchronised.
+ *   - n = 0 Gaussians is valid and renders the background.
+ */
+#ifndef DOGS_H
+#define DOGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define DG_OK 0
+#define DG_ERR_INVALID (-1)   /* null pointer with work to do, bad size, bad layout */
+#define DG_ERR_WORKSPACE (-2) /* workspace smaller than the matching *_workspace_size */
+#define DG_ERR_CAPACITY (-3)  /* reserved: host-visible capacity failure */
+#define DG_ERR_CUDA (-4)      /* a CUDA launch or memset failed */
+
+/* bits OR-ed into *dev_status by device code */
+#define DG_STATUS_CAPACITY 1u /* tile instances exceed `capacity`; ranges were emptied */
+
+#define DG_MAX_BLOCKS 64      /* K, the number of block-local models in one batch */
+#define DG_MAX_VIEWS 4096
+
+/* ---- Gaussian parameter set ---------------------------------------------- */
+/* One Gaussian x_i = {mean p, rotation q, scale s, SH features f, opacity o}
+ * (Sec. 3.1, under Eq. 3; the same property split as the per-property ADMM of
+ * Eq. 12).  Structure of arrays in one device buffer `data` of
+ * dg_gaussian_floats(ld, sh_degree) floats:
+ *   floats [0, 4 ld)        float4 per Gaussian: (p.x, p.y, p.z, opacity logit)
+ *   floats [4 ld, 8 ld)     float4 per Gaussian: quaternion (w, x, y, z), any norm
+ *   floats [8 ld, 12 ld)    float4 per Gaussian: (log s.x, log s.y, log s.z, 0)
+ *   floats [12 ld + j ld)   SH plane j = 3 k + channel, k = l*l + l + m the real
+ *                           SH index (Condon-Shortley phase), j < 3 (D+1)^2
+ * ld >= n, ld % 4 == 0, data 16-byte aligned.  Gradients, Adam moments, duals
+ * u and the penalty anchor use the same layout. */
+typedef struct dg_gaussians {
+    float* data;
+    int64_t n;
+    int64_t ld;
+    int32_t sh_degree; /* 0..3 */
+    int32_t reserved;
+} dg_gaussians;
+
+/* floats needed for a parameter set of leading dimension ld */
+int64_t dg_gaussian_floats(int64_t ld, int sh_degree);
+
+/* ---- cameras and the batch plan ------------------------------------------ */
+/* Pinhole camera, OpenCV axes (x right, y down, z forward): a world point p
+ * maps to R p + t; pixel (px, py) covers [px, px+1) x [py, py+1) and is
+ * sampled at its centre.  View v renders the copies of block `block`.
+ * The fields after `block` are filled by dg_plan_views. */
+typedef struct dg_camera {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float R[9];       /* world -> camera rotation, row-major */
+    float t[3];       /* world -> camera translation         */
+    float campos[3];  /* camera centre (for the SH view direction) */
+    float near_z;     /* copies with camera z <= near_z are culled */
+    int32_t block;
+    /* derived */
+    int32_t tiles_x, tiles_y;
+    int32_t tile_off;  /* first tile of this view in the batch numbering */
+    int32_t reserved;
+    int64_t rec_off;   /* first projected record of this view */
+    int64_t pix_off;   /* first pixel of this view in the batch image buffers */
+    int64_t gauss_begin, gauss_end; /* copy range of `block` */
+} dg_camera;
+
+/* Batch plan: K blocks of copies [blk_off[k], blk_off[k+1]) and the views of
+ * each block [blk_view_off[k], blk_view_off[k+1]) (views grouped by block in
+ * ascending order).  Record r of view v is copy gauss_begin + (r - rec_off). */
+typedef struct dg_plan {
+    int32_t n_views, n_blocks;
+    int32_t tile_w, tile_h;
+    int64_t n_rec;     /* sum over views of the copies of its block */
+    int64_t n_tiles;   /* sum over views of tiles_x * tiles_y      */
+    int64_t n_pixels;  /* sum over views of width * height         */
+    int64_t blk_off[DG_MAX_BLOCKS + 1];
+    int32_t blk_view_off[DG_MAX_BLOCKS + 1];
+    int32_t reserved;
+} dg_plan;
+
+/* Fill the derived camera fields (host array cams[n_views]) and the plan.
+ * blk_off: host, n_blocks + 1 entries.  Tile shapes: tile_w * tile_h == 256
+ * with tile_w in {8, 16, 32}.  Fails with DG_ERR_INVALID if views are not
+ * grouped by ascending block, a size is non-positive, or a count overflows
+ * 32-bit tile / record numbering. */
+int dg_plan_views(dg_camera* cams, int n_views, const int64_t* blk_off, int n_blocks,
+                  int tile_w, int tile_h, dg_plan* plan);
+
+/* ---- projection (K1) ------------------------------------------------------ */
+/* Projected record of (view, copy): three float4 per record at rec[3 r + i]:
+ *   rec[3r+0] = (mean2d.x, mean2d.y, conic.a, conic.b)
+ *   rec[3r+1] = (conic.c, opacity, colour.r, colour.g)
+ *   rec[3r+2] = (colour.b, depth, 0, 0)
+ * where conic = inverse of the 2D covariance J W Sigma W^T J^T + 0.3 I,
+ * colour = max(0, sum_k f_k Y_k(d) + 0.5), d the unit view direction,
+ * opacity = sigmoid(logit), depth = camera z.  rect[r] = (x0 | y0 << 16,
+ * x1 | y1 << 16): the covered tiles [x0, x1) x [y0, y1), from the radius
+ * ceil(3 sqrt(lambda_max)); x0 == x1 marks a culled record, whose `rec` is
+ * left unwritten.  Culled: camera z <= near_z, |x/z| > 1.3 W / (2 fx),
+ * |y/z| > 1.3 H / (2 fy), or no tile covered. */
+int dg_project(const dg_gaussians* x, const dg_camera* dev_cams, const dg_plan* plan,
+               float* rec, uint32_t* rect, void* stream);
+
+/* ---- tile binning and the key sort (K2-K4) ------------------------------- */
+/* One instance per (record, covered tile), key = (tile << 32) | bits(depth),
+ * value = record index, sorted ascending by (key, value).  Outputs: vals
+ * (capacity entries), keys (optional, NULL to skip), ranges[2 t] = first
+ * and end index of tile t (empty tiles: start == end), dev_count[0] = number
+ * of instances M.  If M > capacity the DG_STATUS_CAPACITY bit is set and
+ * every range is emptied (nothing is rendered); retry with capacity >= M.
+ * Workspace: dg_bin_sort_workspace_size bytes of device memory. */
+size_t dg_bin_sort_workspace_size(const dg_plan* plan, int64_t capacity);
+int dg_bin_sort(const float* rec, const uint32_t* rect, const dg_camera* dev_cams,
+                const dg_plan* plan, int64_t capacity, uint64_t* keys, uint32_t* vals,
+                uint32_t* ranges, uint32_t* dev_count, void* ws, size_t ws_bytes,
+                uint32_t* dev_status, void* stream);
+
+/* ---- compositing (K5) ------------------------------------------------------ */
+/* Eq. 2 front to back per pixel over its tile's instances: alpha =
+ * min(0.99, opacity * G), G = exp(-0.5 d^T conic d); pairs with alpha < 1/255
+ * are skipped; the pass stops before T (1 - alpha) < 1e-4; pixel = sum + T bg.
+ * image: [3][H][W] per view at 3 * pix_off; T_final, last: [H][W] at pix_off
+ * (last = list position + 1 of the last composited instance, 0 if none).
+ * bg: host float[3]. */
+int dg_rasterize_fwd(const float* rec, const uint32_t* vals, const uint32_t* ranges,
+                     const dg_camera* dev_cams, const dg_plan* plan, const float* bg,
+                     float* image, float* T_final, uint32_t* last, void* stream);
+
+/* ---- losses (K6, K11) ----------------------------------------------------- */
+/* Per view v: loss[v] = w_l1 * mean |I - I*| + w_ssim * (1 - mean SSIM(I, I*))
+ * (Eq. 3 with lambda = w_ssim and the L1 weight w_l1; SSIM with an 11x11
+ * Gaussian window, sigma 1.5, C1 = 0.01^2, C2 = 0.03^2, zero padding) and
+ * dL_dimage = d loss[v] / d image.  loss: device double[n_views], overwritten.
+ * dg_loss_l1 is the w_ssim = 0 case.  Workspace for SSIM:
+ * dg_loss_workspace_size bytes. */
+int dg_loss_l1(const float* image, const float* target, const dg_camera* dev_cams,
+               const dg_plan* plan, float w_l1, double* loss, float* dL_dimage, void* stream);
+size_t dg_loss_workspace_size(const dg_plan* plan);
+int dg_loss_dssim(const float* image, const float* target, const dg_camera* dev_cams,
+                  const dg_plan* plan, float w_l1, float w_ssim, double* loss,
+                  float* dL_dimage, void* ws, size_t ws_bytes, void* stream);
+
+/* ---- backward (K7 + K8) ---------------------------------------------------- */
+/* Analytic adjoint of dg_project + dg_rasterize_fwd: each tile is walked
+ * back to front from T_final and last.  drec: device scratch, 12 floats per
+ * record (zeroed here, then dL/d(mean2d, conic, opacity, colour) accumulated).
+ * grads: same layout as x, OVERWRITTEN with dL/dx for every copy (zero for
+ * copies no view sees).  bg: host float[3]. */
+int dg_rasterize_bwd(const float* rec, const uint32_t* rect, const uint32_t* vals,
+                     const uint32_t* ranges, const dg_camera* dev_cams, const dg_plan* plan,
+                     const float* bg, const float* T_final, const uint32_t* last,
+                     const float* dL_dimage, const dg_gaussians* x, float* drec,
+                     dg_gaussians* grads, void* stream);
+
+/* ---- ADMM (K9, K10) -------------------------------------------------------- */
+/* x-step (Eq. 8a / 12a): one Adam step on every local copy with gradient
+ * g + rho_grp (x - anchor) on shared copies (copy_shared[c] != 0), where the
+ * anchor of a shared copy is z_{g(c)} - u_c, kept by dg_admm_consensus and
+ * dg_admm_anchor.  Groups in the paper's order (Eq. 12): 0 p (mean),
+ * 1 q (rotation), 2 s (scale), 3 f (SH), 4 o (opacity): rho[5] (host).
+ * lr[6] (host): p, q, s, SH DC, SH rest, o.  Moments m, v updated in place;
+ * bias correction with `step` >= 1. */
+int dg_adam_admm_step(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m,
+                      dg_gaussians* v, const dg_gaussians* anchor, const uint8_t* copy_shared,
+                      const float* rho, const float* lr, float beta1, float beta2, float eps,
+                      int step, void* stream);
+
+/* Consensus (Eq. 8b-c / 12b-c) over the global model z (n_global Gaussians).
+ * Sharing map as CSR: the copies of global i are g_copies[g_off[i] ..
+ * g_off[i+1]) (device).  For a global held by n_i >= 2 blocks:
+ *   xh_k = alpha x_k + (1 - alpha) z     (over-relaxation, Sec. 3.3)
+ *   z    = (1/n_i) sum_k (xh_k + u_k)    (complete form of Eq. 8b)
+ *   u_k += xh_k - z                      (Eq. 8c)
+ *   anchor_k = z - u_k                   (for the next x-steps)
+ * A global held by one block gets z = x.  residuals (device double[10], may
+ * be NULL, overwritten): per group the squared primal residual
+ * sum ||x_k - z||^2 (0..4) and squared dual residual rho^2 n_i ||z - z_prev||^2
+ * (5..9), shared globals only (Eq. 9). */
+int dg_admm_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z,
+                      dg_gaussians* anchor, const int64_t* g_off, const int32_t* g_copies,
+                      const float* rho, float alpha, double* residuals, void* stream);
+
+/* anchor_c = z_{copy_gid[c]} - u_c for every shared copy (initialisation). */
+int dg_admm_anchor(const dg_gaussians* z, const dg_gaussians* u, const int32_t* copy_gid,
+                   const uint8_t* copy_shared, dg_gaussians* anchor, void* stream);
+
+/* ---- serving render (K12) ------------------------------------------------ */
+/* Render n_views requests (any mix of resolutions) of the global model z:
+ * dg_project + dg_bin_sort + dg_rasterize_fwd on one plan with a single
+ * block holding all of z.  dg_render_plan fills host_cams' derived fields
+ * and the plan (copy host_cams to dev_cams afterwards); buffers are sized
+ * from the plan.  Workspace: dg_render_workspace_size. */
+int dg_render_plan(dg_camera* host_cams, int n_views, int64_t n_gauss, int tile_w,
+                   int tile_h, dg_plan* plan);
+size_t dg_render_workspace_size(const dg_plan* plan, int64_t capacity);
+int dg_render(const dg_gaussians* z, const dg_camera* dev_cams, const dg_plan* plan,
+              const float* bg, int64_t capacity, float* image, void* ws, size_t ws_bytes,
+              uint32_t* dev_count, uint32_t* dev_status, void* stream);
+
+/* ---- misc ------------------------------------------------------------------ */
+const char* dg_version(void);
+/* number of kernel launches this library has enqueued since load (monotone) */
+uint64_t dg_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOGS_H */

@@ -1,0 +1,121 @@
+// Internal helpers shared by the libdogs kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dogs.h"
+
+namespace dg {
+
+// launch accounting (dg_launch_count)
+void note_launch(int n = 1);
+
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// ---- parameter-set views ----------------------------------------------------
+struct GView {
+    float4* mo;     // (p.xyz, opacity logit)
+    float4* quat;   // (w, x, y, z)
+    float4* scale;  // (log s.xyz, 0)
+    float* sh;      // planes, plane j at sh + j * ld
+    int64_t n, ld;
+    int deg;
+};
+
+inline GView gview(const dg_gaussians* g)
+{
+    GView v;
+    v.mo = reinterpret_cast<float4*>(g->data);
+    v.quat = reinterpret_cast<float4*>(g->data + 4 * g->ld);
+    v.scale = reinterpret_cast<float4*>(g->data + 8 * g->ld);
+    v.sh = g->data + 12 * g->ld;
+    v.n = g->n;
+    v.ld = g->ld;
+    v.deg = g->sh_degree;
+    return v;
+}
+
+__host__ __device__ inline int sh_coefs(int deg) { return (deg + 1) * (deg + 1); }
+
+// block of a copy index (blk_off has n_blocks + 1 ascending entries)
+__device__ __forceinline__ int find_block(const dg_plan& p, int64_t c)
+{
+    int lo = 0, hi = p.n_blocks - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (p.blk_off[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// view owning global tile index t (cams sorted by tile_off)
+__device__ __forceinline__ int find_view_of_tile(const dg_camera* cams, int n_views, int64_t t)
+{
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&cams[mid].tile_off) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_view_of_rec(const dg_camera* cams, int n_views, int64_t r)
+{
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&cams[mid].rec_off) <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---- compositing decision shared by the forward and the backward -------------
+// A staged instance: exponent coefficients in log2 units and log2(opacity):
+// power2 = A dx^2 + B dx dy + C dy^2, alpha = 2^(power2 + lo).
+struct Staged {
+    float mx, my, A, B, C, lo;
+};
+
+__device__ __forceinline__ Staged stage_geometry(float4 r0, float4 r1)
+{
+    Staged s;
+    s.mx = r0.x;
+    s.my = r0.y;
+    s.A = __fmul_rn(-0.5f * kLog2e, r0.z);
+    s.B = __fmul_rn(-kLog2e, r0.w);
+    s.C = __fmul_rn(-0.5f * kLog2e, r1.x);
+    s.lo = __log2f(r1.y);
+    return s;
+}
+
+// Returns alpha (> 0) for a composited pair or 0 for a skipped one.  Fixed
+// rounding (no contraction) so that the forward and the backward take
+// identical decisions.  `raw` = opacity * G before the 0.99 clamp.
+__device__ __forceinline__ float pair_alpha(float mx, float my, float A, float B, float C, float lo,
+                                            float px, float py, float& dx, float& dy, float& raw)
+{
+    dx = __fsub_rn(mx, px);
+    dy = __fsub_rn(my, py);
+    float t = __fmul_rn(A, dx);
+    t = __fmaf_rn(B, dy, t);
+    float p = __fmul_rn(dx, t);
+    p = __fmaf_rn(__fmul_rn(C, dy), dy, p);
+    if (p > 0.0f) return 0.0f;
+    float e = __fadd_rn(p, lo);
+    if (e < -8.0f) return 0.0f;   // alpha <= 1/256 < 1/255: skip without the exponential
+    raw = exp2f(e);
+    float a = fminf(raw, kAlphaMax);
+    if (a < kAlphaMin) return 0.0f;
+    return a;
+}
+
+}  // namespace dg
+
+#define DG_CHECK_LAUNCH()                                      \
+    do {                                                       \
+        cudaError_t _e = cudaGetLastError();                   \
+        if (_e != cudaSuccess) return DG_ERR_CUDA;             \
+    } while (0)

@@ -1,0 +1,439 @@
+// K1 project_fwd and K8 project_bwd.
+//
+// Projection of 3D Gaussians (Sec. 3.1: Eq. 1, Sigma = R S S^T R^T) to 2D
+// conics with the EWA local-affine approximation J W Sigma W^T J^T + 0.3 I,
+// real SH colour of degree <= 3, sigmoid opacity; and its analytic adjoint.
+//
+// One thread per local copy.  A copy is loaded once (coalesced float4 SoA for
+// mean/opacity, rotation, scale; planar SH) and projected into every view of
+// its block, so the parameters are read once per step however many views a
+// block has.  HBM-bound.
+#include "common.cuh"
+
+namespace dg {
+
+// Real SH basis with the Condon-Shortley phase, k = l*l + l + m, written as
+// polynomials in the unit direction (x, y, z).  Coefficients are the closed
+// forms 1/2 sqrt(1/pi), sqrt(3/(4pi)), 1/2 sqrt(15/pi), 1/4 sqrt(5/pi),
+// 1/4 sqrt(15/pi), 1/4 sqrt(35/(2pi)), 1/2 sqrt(105/pi), 1/4 sqrt(21/(2pi)),
+// 1/4 sqrt(7/pi), 1/4 sqrt(105/pi).
+#define SH_C0 0.28209479177387814f
+#define SH_C1 0.48860251190291992f
+#define SH_C2A 1.0925484305920792f
+#define SH_C2B 0.31539156525252005f
+#define SH_C2C 0.54627421529603959f
+#define SH_C3A 0.59004358992664352f
+#define SH_C3B 2.8906114426405538f
+#define SH_C3C 0.45704579946446572f
+#define SH_C3D 0.37317633259011540f
+#define SH_C3E 1.4453057213202769f
+
+template <int DEG>
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y)
+{
+    Y[0] = SH_C0;
+    if (DEG >= 1) {
+        Y[1] = -SH_C1 * y;
+        Y[2] = SH_C1 * z;
+        Y[3] = -SH_C1 * x;
+    }
+    if (DEG >= 2) {
+        Y[4] = SH_C2A * x * y;
+        Y[5] = -SH_C2A * y * z;
+        Y[6] = SH_C2B * (3.f * z * z - 1.f);
+        Y[7] = -SH_C2A * x * z;
+        Y[8] = SH_C2C * (x * x - y * y);
+    }
+    if (DEG >= 3) {
+        Y[9] = -SH_C3A * y * (3.f * x * x - y * y);
+        Y[10] = SH_C3B * x * y * z;
+        Y[11] = -SH_C3C * y * (5.f * z * z - 1.f);
+        Y[12] = SH_C3D * z * (5.f * z * z - 3.f);
+        Y[13] = -SH_C3C * x * (5.f * z * z - 1.f);
+        Y[14] = SH_C3E * z * (x * x - y * y);
+        Y[15] = -SH_C3A * x * (x * x - 3.f * y * y);
+    }
+}
+
+// sum_k w_k grad Y_k of the polynomials above
+template <int DEG>
+__device__ __forceinline__ float3 sh_grad_dot(float x, float y, float z, const float* w)
+{
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (DEG >= 1) {
+        gy -= SH_C1 * w[1];
+        gz += SH_C1 * w[2];
+        gx -= SH_C1 * w[3];
+    }
+    if (DEG >= 2) {
+        gx += SH_C2A * y * w[4];            gy += SH_C2A * x * w[4];
+        gy -= SH_C2A * z * w[5];            gz -= SH_C2A * y * w[5];
+        gz += 6.f * SH_C2B * z * w[6];
+        gx -= SH_C2A * z * w[7];            gz -= SH_C2A * x * w[7];
+        gx += 2.f * SH_C2C * x * w[8];      gy -= 2.f * SH_C2C * y * w[8];
+    }
+    if (DEG >= 3) {
+        gx -= 6.f * SH_C3A * x * y * w[9];  gy -= SH_C3A * (3.f * x * x - 3.f * y * y) * w[9];
+        gx += SH_C3B * y * z * w[10];       gy += SH_C3B * x * z * w[10];   gz += SH_C3B * x * y * w[10];
+        gy -= SH_C3C * (5.f * z * z - 1.f) * w[11];                          gz -= 10.f * SH_C3C * y * z * w[11];
+        gz += SH_C3D * (15.f * z * z - 3.f) * w[12];
+        gx -= SH_C3C * (5.f * z * z - 1.f) * w[13];                          gz -= 10.f * SH_C3C * x * z * w[13];
+        gx += 2.f * SH_C3E * x * z * w[14]; gy -= 2.f * SH_C3E * y * z * w[14]; gz += SH_C3E * (x * x - y * y) * w[14];
+        gx -= SH_C3A * (3.f * x * x - 3.f * y * y) * w[15];                  gy += 6.f * SH_C3A * x * y * w[15];
+    }
+    return make_float3(gx, gy, gz);
+}
+
+struct CamL {
+    float R[9], t[3], cp[3];
+    float fx, fy, cx, cy, nearz;
+    int W, H, TX, TY;
+    int64_t rec_off, gb;
+};
+
+__device__ __forceinline__ void load_cam(const dg_camera* cams, int v, CamL& c)
+{
+    const dg_camera* p = cams + v;
+#pragma unroll
+    for (int i = 0; i < 9; i++) c.R[i] = __ldg(&p->R[i]);
+#pragma unroll
+    for (int i = 0; i < 3; i++) { c.t[i] = __ldg(&p->t[i]); c.cp[i] = __ldg(&p->campos[i]); }
+    c.fx = __ldg(&p->fx); c.fy = __ldg(&p->fy); c.cx = __ldg(&p->cx); c.cy = __ldg(&p->cy);
+    c.nearz = __ldg(&p->near_z);
+    c.W = __ldg(&p->width); c.H = __ldg(&p->height);
+    c.TX = __ldg(&p->tiles_x); c.TY = __ldg(&p->tiles_y);
+    c.rec_off = __ldg(&p->rec_off); c.gb = __ldg(&p->gauss_begin);
+}
+
+// camera-frame depth, summed in double in a fixed order: the products of two
+// floats are exact in double, so the result rounds identically everywhere
+__device__ __forceinline__ double cam_depth(const CamL& c, float3 mu)
+{
+    double s = __dmul_rn((double)c.R[6], (double)mu.x);
+    s = __dadd_rn(s, __dmul_rn((double)c.R[7], (double)mu.y));
+    s = __dadd_rn(s, __dmul_rn((double)c.R[8], (double)mu.z));
+    return __dadd_rn(s, (double)c.t[2]);
+}
+
+// Screen-space geometry of one Gaussian in one view.
+struct Geom {
+    float tx, ty, tz, xn, yn;
+    float Rq[9];          // rotation from the normalised quaternion
+    float qn[4], qinv;    // normalised quaternion (w,x,y,z), 1/|q|
+    float s[3];           // scales
+    float Sig[6];         // Sigma: 00 01 02 11 12 22
+    float T0[3], T1[3];   // rows of J W
+    float A, B, C, det;   // Sigma' = [[A, B], [B, C]]
+    float a, b, c;        // conic
+    float mx, my;
+};
+
+// Computes every field; returns false if the Gaussian is culled in this
+// view.  The caller has already checked camera z > near_z (exact, in double),
+// so no division below is by a non-positive depth.  Fills rect if non-null.
+__device__ __forceinline__ bool geom(const CamL& cam, double tzd, float3 mu, float4 q, float4 sc, int tw,
+                                     int th, Geom& g, uint2* rect_out)
+{
+    g.tz = (float)tzd;
+    g.tx = fmaf(cam.R[0], mu.x, fmaf(cam.R[1], mu.y, fmaf(cam.R[2], mu.z, cam.t[0])));
+    g.ty = fmaf(cam.R[3], mu.x, fmaf(cam.R[4], mu.y, fmaf(cam.R[5], mu.z, cam.t[1])));
+    g.xn = g.tx / g.tz;
+    g.yn = g.ty / g.tz;
+    float limx = 0.65f * (float)cam.W / cam.fx, limy = 0.65f * (float)cam.H / cam.fy;
+    bool vis = !(fabsf(g.xn) > limx || fabsf(g.yn) > limy);
+    // rotation from the normalised quaternion (w, x, y, z) = (q.x, q.y, q.z, q.w)
+    float qq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+    g.qinv = rsqrtf(qq);
+    float w = q.x * g.qinv, x = q.y * g.qinv, y = q.z * g.qinv, z = q.w * g.qinv;
+    g.qn[0] = w; g.qn[1] = x; g.qn[2] = y; g.qn[3] = z;
+    g.Rq[0] = 1.f - 2.f * (y * y + z * z); g.Rq[1] = 2.f * (x * y - w * z); g.Rq[2] = 2.f * (x * z + w * y);
+    g.Rq[3] = 2.f * (x * y + w * z); g.Rq[4] = 1.f - 2.f * (x * x + z * z); g.Rq[5] = 2.f * (y * z - w * x);
+    g.Rq[6] = 2.f * (x * z - w * y); g.Rq[7] = 2.f * (y * z + w * x); g.Rq[8] = 1.f - 2.f * (x * x + y * y);
+    g.s[0] = __expf(sc.x); g.s[1] = __expf(sc.y); g.s[2] = __expf(sc.z);
+    float M[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) M[3 * i + j] = g.Rq[3 * i + j] * g.s[j];
+    g.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    g.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    g.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    g.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    g.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    g.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+    float fz = cam.fx / g.tz, gz = cam.fy / g.tz;
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        g.T0[j] = fz * (cam.R[j] - g.xn * cam.R[6 + j]);
+        g.T1[j] = gz * (cam.R[3 + j] - g.yn * cam.R[6 + j]);
+    }
+    float U0[3], U1[3];
+    U0[0] = g.Sig[0] * g.T0[0] + g.Sig[1] * g.T0[1] + g.Sig[2] * g.T0[2];
+    U0[1] = g.Sig[1] * g.T0[0] + g.Sig[3] * g.T0[1] + g.Sig[4] * g.T0[2];
+    U0[2] = g.Sig[2] * g.T0[0] + g.Sig[4] * g.T0[1] + g.Sig[5] * g.T0[2];
+    U1[0] = g.Sig[0] * g.T1[0] + g.Sig[1] * g.T1[1] + g.Sig[2] * g.T1[2];
+    U1[1] = g.Sig[1] * g.T1[0] + g.Sig[3] * g.T1[1] + g.Sig[4] * g.T1[2];
+    U1[2] = g.Sig[2] * g.T1[0] + g.Sig[4] * g.T1[1] + g.Sig[5] * g.T1[2];
+    g.A = g.T0[0] * U0[0] + g.T0[1] * U0[1] + g.T0[2] * U0[2] + 0.3f;
+    g.B = g.T0[0] * U1[0] + g.T0[1] * U1[1] + g.T0[2] * U1[2];
+    g.C = g.T1[0] * U1[0] + g.T1[1] * U1[1] + g.T1[2] * U1[2] + 0.3f;
+    g.det = g.A * g.C - g.B * g.B;
+    vis = vis && (g.det > 0.f);
+    float id = 1.f / g.det;
+    g.a = g.C * id; g.b = -g.B * id; g.c = g.A * id;
+    g.mx = cam.fx * g.xn + cam.cx;
+    g.my = cam.fy * g.yn + cam.cy;
+    if (!vis) return false;
+    float mid = 0.5f * (g.A + g.C);
+    float lmax = mid + sqrtf(fmaxf(mid * mid - g.det, 0.f));
+    float r = ceilf(3.f * sqrtf(lmax));
+    int x0 = (int)floorf((g.mx - r) / (float)tw), x1 = (int)floorf((g.mx + r) / (float)tw) + 1;
+    int y0 = (int)floorf((g.my - r) / (float)th), y1 = (int)floorf((g.my + r) / (float)th) + 1;
+    x0 = min(max(x0, 0), cam.TX); x1 = min(max(x1, 0), cam.TX);
+    y0 = min(max(y0, 0), cam.TY); y1 = min(max(y1, 0), cam.TY);
+    if (x1 <= x0 || y1 <= y0) return false;
+    if (rect_out) *rect_out = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+    return true;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) k_project(GView x, const dg_camera* __restrict__ cams, dg_plan plan,
+                                                 float4* __restrict__ rec, uint2* __restrict__ rect)
+{
+    constexpr int NK = (DEG + 1) * (DEG + 1);
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= plan.blk_off[plan.n_blocks]) return;
+    int k = find_block(plan, c);
+    int v0 = plan.blk_view_off[k], v1 = plan.blk_view_off[k + 1];
+    if (v0 == v1) return;
+    float4 mo = x.mo[c];
+    float3 mu = make_float3(mo.x, mo.y, mo.z);
+    bool loaded = false;
+    float4 q = make_float4(0, 0, 0, 0), sc = make_float4(0, 0, 0, 0);
+    float f[3 * NK];
+    float opac = 0.f;
+    for (int v = v0; v < v1; v++) {
+        CamL cam;
+        load_cam(cams, v, cam);
+        int64_t r = cam.rec_off + (c - cam.gb);
+        double tzd = cam_depth(cam, mu);
+        if (!(tzd > (double)cam.nearz)) { rect[r] = make_uint2(0, 0); continue; }
+        if (!loaded) {   // the rest of the parameters only for copies in front of some camera
+            q = x.quat[c];
+            sc = x.scale[c];
+#pragma unroll
+            for (int j = 0; j < 3 * NK; j++) f[j] = x.sh[(int64_t)j * x.ld + c];
+            opac = 1.f / (1.f + __expf(-mo.w));
+            loaded = true;
+        }
+        Geom g;
+        uint2 rr;
+        if (!geom(cam, tzd, mu, q, sc, plan.tile_w, plan.tile_h, g, &rr)) { rect[r] = make_uint2(0, 0); continue; }
+        float dx = mu.x - cam.cp[0], dy = mu.y - cam.cp[1], dz = mu.z - cam.cp[2];
+        float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float Y[NK];
+        sh_eval<DEG>(dx * il, dy * il, dz * il, Y);
+        float col[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            float s = 0.5f;
+#pragma unroll
+            for (int kk = 0; kk < NK; kk++) s = fmaf(f[3 * kk + ch], Y[kk], s);
+            col[ch] = fmaxf(s, 0.f);
+        }
+        rec[3 * r + 0] = make_float4(g.mx, g.my, g.a, g.b);
+        rec[3 * r + 1] = make_float4(g.c, opac, col[0], col[1]);
+        rec[3 * r + 2] = make_float4(col[2], g.tz, 0.f, 0.f);
+        rect[r] = rr;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K8: adjoint of the projection, accumulated over the views of the block.
+// ---------------------------------------------------------------------------
+template <int DEG>
+__global__ void __launch_bounds__(128) k_project_bwd(GView x, const dg_camera* __restrict__ cams, dg_plan plan,
+                                                     const uint2* __restrict__ rect,
+                                                     const float4* __restrict__ drec, GView gr)
+{
+    constexpr int NK = (DEG + 1) * (DEG + 1);
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= plan.blk_off[plan.n_blocks]) return;
+    int k = find_block(plan, c);
+    int v0 = plan.blk_view_off[k], v1 = plan.blk_view_off[k + 1];
+    float gmu[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gs[3] = {0, 0, 0}, go = 0.f;
+    float gf[3 * NK];
+#pragma unroll
+    for (int j = 0; j < 3 * NK; j++) gf[j] = 0.f;
+    float4 mo = x.mo[c];
+    float3 mu = make_float3(mo.x, mo.y, mo.z);
+    bool loaded = false;
+    float4 q = make_float4(0, 0, 0, 0), sc = make_float4(0, 0, 0, 0);
+    float f[3 * NK];
+    float opac = 0.f;
+    for (int v = v0; v < v1; v++) {
+        CamL cam;
+        load_cam(cams, v, cam);
+        int64_t r = cam.rec_off + (c - cam.gb);
+        uint2 rr = rect[r];
+        if ((rr.x & 0xFFFFu) == (rr.y & 0xFFFFu)) continue;     // culled in the forward
+        if (!loaded) {
+            q = x.quat[c];
+            sc = x.scale[c];
+#pragma unroll
+            for (int j = 0; j < 3 * NK; j++) f[j] = x.sh[(int64_t)j * x.ld + c];
+            opac = 1.f / (1.f + __expf(-mo.w));
+            loaded = true;
+        }
+        float4 d0 = drec[3 * r + 0], d1 = drec[3 * r + 1], d2 = drec[3 * r + 2];
+        Geom g;
+        geom(cam, cam_depth(cam, mu), mu, q, sc, plan.tile_w, plan.tile_h, g, nullptr);  // forward's rect decides
+        // opacity logit
+        go += d1.y * opac * (1.f - opac);
+        // colour -> SH coefficients and the view direction
+        float vx = mu.x - cam.cp[0], vy = mu.y - cam.cp[1], vz = mu.z - cam.cp[2];
+        float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+        float ux = vx * il, uy = vy * il, uz = vz * il;
+        float Y[NK];
+        sh_eval<DEG>(ux, uy, uz, Y);
+        float gc[3] = {d1.z, d1.w, d2.x};
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            float s = 0.5f;
+#pragma unroll
+            for (int kk = 0; kk < NK; kk++) s = fmaf(f[3 * kk + ch], Y[kk], s);
+            if (!(s > 0.f)) gc[ch] = 0.f;            // clamped channel
+        }
+        float wk[NK];
+#pragma unroll
+        for (int kk = 0; kk < NK; kk++) {
+            gf[3 * kk + 0] += gc[0] * Y[kk];
+            gf[3 * kk + 1] += gc[1] * Y[kk];
+            gf[3 * kk + 2] += gc[2] * Y[kk];
+            wk[kk] = gc[0] * f[3 * kk] + gc[1] * f[3 * kk + 1] + gc[2] * f[3 * kk + 2];
+        }
+        if (DEG > 0) {
+            float3 gd = sh_grad_dot<DEG>(ux, uy, uz, wk);
+            float dd = gd.x * ux + gd.y * uy + gd.z * uz;
+            gmu[0] += (gd.x - ux * dd) * il;
+            gmu[1] += (gd.y - uy * dd) * il;
+            gmu[2] += (gd.z - uz * dd) * il;
+        }
+        // conic (a, b, c) -> Sigma' entries (A, B, C)
+        float da = d0.z, db = d0.w, dc = d1.x;
+        float id2 = 1.f / (g.det * g.det);
+        float gA = (-g.C * g.C * da + g.B * g.C * db - g.B * g.B * dc) * id2;
+        float gB = (2.f * g.B * g.C * da - (g.A * g.C + g.B * g.B) * db + 2.f * g.A * g.B * dc) * id2;
+        float gC = (-g.B * g.B * da + g.A * g.B * db - g.A * g.A * dc) * id2;
+        // Sigma' = T Sigma T^T: dSigma = T^T G T, dT = 2 G T Sigma, G = [[gA, gB/2], [gB/2, gC]]
+        float U0[3], U1[3];
+        U0[0] = g.Sig[0] * g.T0[0] + g.Sig[1] * g.T0[1] + g.Sig[2] * g.T0[2];
+        U0[1] = g.Sig[1] * g.T0[0] + g.Sig[3] * g.T0[1] + g.Sig[4] * g.T0[2];
+        U0[2] = g.Sig[2] * g.T0[0] + g.Sig[4] * g.T0[1] + g.Sig[5] * g.T0[2];
+        U1[0] = g.Sig[0] * g.T1[0] + g.Sig[1] * g.T1[1] + g.Sig[2] * g.T1[2];
+        U1[1] = g.Sig[1] * g.T1[0] + g.Sig[3] * g.T1[1] + g.Sig[4] * g.T1[2];
+        U1[2] = g.Sig[2] * g.T1[0] + g.Sig[4] * g.T1[1] + g.Sig[5] * g.T1[2];
+        float dT0[3], dT1[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            dT0[j] = 2.f * gA * U0[j] + gB * U1[j];
+            dT1[j] = gB * U0[j] + 2.f * gC * U1[j];
+        }
+        float hB = 0.5f * gB;
+        float dS[6];   // dL/dSigma as a symmetric matrix: 00 01 02 11 12 22
+        dS[0] = gA * g.T0[0] * g.T0[0] + 2.f * hB * g.T0[0] * g.T1[0] + gC * g.T1[0] * g.T1[0];
+        dS[1] = gA * g.T0[0] * g.T0[1] + hB * (g.T0[0] * g.T1[1] + g.T1[0] * g.T0[1]) + gC * g.T1[0] * g.T1[1];
+        dS[2] = gA * g.T0[0] * g.T0[2] + hB * (g.T0[0] * g.T1[2] + g.T1[0] * g.T0[2]) + gC * g.T1[0] * g.T1[2];
+        dS[3] = gA * g.T0[1] * g.T0[1] + 2.f * hB * g.T0[1] * g.T1[1] + gC * g.T1[1] * g.T1[1];
+        dS[4] = gA * g.T0[1] * g.T0[2] + hB * (g.T0[1] * g.T1[2] + g.T1[1] * g.T0[2]) + gC * g.T1[1] * g.T1[2];
+        dS[5] = gA * g.T0[2] * g.T0[2] + 2.f * hB * g.T0[2] * g.T1[2] + gC * g.T1[2] * g.T1[2];
+        // rows of T depend on t through fx/tz and x/z; the mean through the pinhole
+        const float* W = cam.R;
+        float iz = 1.f / g.tz, iz2 = iz * iz, iz3 = iz2 * iz;
+        float dT0W0 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
+        float dT0W2 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
+        float dT1W1 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
+        float dT1W2 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
+        float dtx = -cam.fx * iz2 * dT0W2 + d0.x * cam.fx * iz;
+        float dty = -cam.fy * iz2 * dT1W2 + d0.y * cam.fy * iz;
+        float dtz = -cam.fx * iz2 * dT0W0 + 2.f * cam.fx * g.tx * iz3 * dT0W2
+                  - cam.fy * iz2 * dT1W1 + 2.f * cam.fy * g.ty * iz3 * dT1W2
+                  - d0.x * cam.fx * g.tx * iz2 - d0.y * cam.fy * g.ty * iz2;
+        gmu[0] += W[0] * dtx + W[3] * dty + W[6] * dtz;
+        gmu[1] += W[1] * dtx + W[4] * dty + W[7] * dtz;
+        gmu[2] += W[2] * dtx + W[5] * dty + W[8] * dtz;
+        // Sigma = M M^T, M = R diag(s): dM = 2 dSigma M
+        float Sf[9] = {dS[0], dS[1], dS[2], dS[1], dS[3], dS[4], dS[2], dS[4], dS[5]};
+        float M[9];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) M[3 * i + j] = g.Rq[3 * i + j] * g.s[j];
+        float dR[9];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            float ds = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                float dM = 2.f * (Sf[3 * i + 0] * M[0 + j] + Sf[3 * i + 1] * M[3 + j] + Sf[3 * i + 2] * M[6 + j]);
+                ds += dM * g.Rq[3 * i + j];
+                dR[3 * i + j] = dM * g.s[j];
+            }
+            gs[j] += ds * g.s[j];
+        }
+        // rotation partials w.r.t. the normalised quaternion, then the normalisation
+        float qw = g.qn[0], qx = g.qn[1], qy = g.qn[2], qz = g.qn[3];
+        float dqw = 2.f * (qz * (dR[3] - dR[1]) + qy * (dR[2] - dR[6]) + qx * (dR[7] - dR[5]));
+        float dqx = 2.f * (qy * (dR[1] + dR[3]) + qz * (dR[2] + dR[6]) + qw * (dR[7] - dR[5])) - 4.f * qx * (dR[4] + dR[8]);
+        float dqy = 2.f * (qx * (dR[1] + dR[3]) + qz * (dR[5] + dR[7]) + qw * (dR[2] - dR[6])) - 4.f * qy * (dR[0] + dR[8]);
+        float dqz = 2.f * (qx * (dR[2] + dR[6]) + qy * (dR[5] + dR[7]) + qw * (dR[3] - dR[1])) - 4.f * qz * (dR[0] + dR[4]);
+        float qd = dqw * qw + dqx * qx + dqy * qy + dqz * qz;
+        gq[0] += (dqw - qw * qd) * g.qinv;
+        gq[1] += (dqx - qx * qd) * g.qinv;
+        gq[2] += (dqy - qy * qd) * g.qinv;
+        gq[3] += (dqz - qz * qd) * g.qinv;
+    }
+    gr.mo[c] = make_float4(gmu[0], gmu[1], gmu[2], go);
+    gr.quat[c] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+    gr.scale[c] = make_float4(gs[0], gs[1], gs[2], 0.f);
+#pragma unroll
+    for (int j = 0; j < 3 * NK; j++) gr.sh[(int64_t)j * gr.ld + c] = gf[j];
+}
+
+int launch_project(const dg_gaussians* x, const dg_camera* cams, const dg_plan& plan, float4* rec, uint2* rect,
+                   cudaStream_t st)
+{
+    int64_t n = plan.blk_off[plan.n_blocks];
+    if (n == 0) return DG_OK;
+    GView xv = gview(x);
+    dim3 grid((unsigned)((n + 255) / 256));
+    switch (x->sh_degree) {
+    case 0: k_project<0><<<grid, 256, 0, st>>>(xv, cams, plan, rec, rect); break;
+    case 1: k_project<1><<<grid, 256, 0, st>>>(xv, cams, plan, rec, rect); break;
+    case 2: k_project<2><<<grid, 256, 0, st>>>(xv, cams, plan, rec, rect); break;
+    default: k_project<3><<<grid, 256, 0, st>>>(xv, cams, plan, rec, rect); break;
+    }
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
+int launch_project_bwd(const dg_gaussians* x, const dg_camera* cams, const dg_plan& plan, const uint2* rect,
+                       const float4* drec, dg_gaussians* grads, cudaStream_t st)
+{
+    int64_t n = plan.blk_off[plan.n_blocks];
+    if (n == 0) return DG_OK;
+    GView xv = gview(x), gv = gview(grads);
+    dim3 grid((unsigned)((n + 127) / 128));
+    switch (x->sh_degree) {
+    case 0: k_project_bwd<0><<<grid, 128, 0, st>>>(xv, cams, plan, rect, drec, gv); break;
+    case 1: k_project_bwd<1><<<grid, 128, 0, st>>>(xv, cams, plan, rect, drec, gv); break;
+    case 2: k_project_bwd<2><<<grid, 128, 0, st>>>(xv, cams, plan, rect, drec, gv); break;
+    default: k_project_bwd<3><<<grid, 128, 0, st>>>(xv, cams, plan, rect, drec, gv); break;
+    }
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
+}  // namespace dg
