@@ -106,7 +106,7 @@ typedef struct dg_plan {
     int64_t n_pixels;  /* sum over views of width * height         */
     int64_t blk_off[DG_MAX_BLOCKS + 1];
     int32_t blk_view_off[DG_MAX_BLOCKS + 1];
-    int32_t reserved;
+    int32_t max_width, max_height;  /* largest view in the batch */
 } dg_plan;
 
 /* Fill the derived camera fields (host array cams[n_views]) and the plan.

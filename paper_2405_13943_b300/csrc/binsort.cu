@@ -1,0 +1,335 @@
+// K2-K4: tile binning and the 64-bit (tile | depth) key sort.
+//
+// Each projected record covers a rectangle of tiles; every (record, tile)
+// pair is an instance with key (tile << 32) | bits(depth) and value = record
+// index.  The instances are sorted by (key, value): by tile first, then by
+// depth, ties broken by record index (Sec. 3.1, Eq. 2 composites in depth
+// order within each tile).
+//
+// Sort design (a most-significant-digit radix sort): the tile id is one
+// wide digit.  Pass 1 histograms instances per tile with atomics; an
+// exclusive scan of the histogram gives every tile's range (K4's output
+// directly); pass 2 scatters (depth bits, record) pairs into their tile's
+// range; then each tile's segment is sorted by (depth bits, record) in shared
+// memory with a bitonic network (segments above the shared-memory limit
+// fall back to the same network in global memory).  Instance data crosses
+// HBM about three times (scatter write, sort read, value write) instead of
+// twice per digit of an LSD sort.  No kernel waits on another CTA.
+#include "common.cuh"
+
+namespace dg {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanChunk = kScanThreads * kScanPer;   // tiles per scan CTA
+constexpr int kSmallCap = 2048;                       // segment sorted by a 256-thread CTA
+constexpr int kBigCap = 16384;                        // segment sorted by a 1024-thread CTA in smem
+
+struct BinWs {
+    uint32_t* counts;     // n_tiles + 2 (two list counters at the end), zeroed
+    uint32_t* cursor;     // n_tiles
+    uint32_t* partials;   // n_chunks + 1
+    uint32_t* big_list;   // n_tiles
+    uint32_t* huge_list;  // n_tiles
+    uint64_t* pairs;      // capacity
+};
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static size_t bin_ws_layout(int64_t n_tiles, int64_t capacity, BinWs* w, char* base)
+{
+    int64_t n_chunks = (n_tiles + kScanChunk - 1) / kScanChunk;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align256(bytes); return p; };
+    BinWs t;
+    t.counts = (uint32_t*)take(4 * (size_t)(n_tiles + 2));
+    t.cursor = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
+    t.partials = (uint32_t*)take(4 * (size_t)(n_chunks + 1));
+    t.big_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
+    t.huge_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
+    t.pairs = (uint64_t*)take(8 * (size_t)(capacity > 0 ? capacity : 1));
+    if (w) *w = t;
+    return off;
+}
+
+size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity) { return bin_ws_layout(n_tiles, capacity, nullptr, nullptr); }
+
+// ---- pass 1: instances per tile ------------------------------------------------
+__global__ void __launch_bounds__(256) k_count(const uint2* __restrict__ rect, const dg_camera* __restrict__ cams,
+                                               int n_views, int64_t n_rec, uint32_t* __restrict__ counts)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rec) return;
+    uint2 rr = rect[r];
+    uint32_t x0 = rr.x & 0xFFFFu, y0 = rr.x >> 16, x1 = rr.y & 0xFFFFu, y1 = rr.y >> 16;
+    if (x1 <= x0 || y1 <= y0) return;
+    int v = find_view_of_rec(cams, n_views, r);
+    uint32_t toff = (uint32_t)__ldg(&cams[v].tile_off), TX = (uint32_t)__ldg(&cams[v].tiles_x);
+    for (uint32_t ty = y0; ty < y1; ty++)
+        for (uint32_t tx = x0; tx < x1; tx++) atomicAdd(&counts[toff + ty * TX + tx], 1u);
+}
+
+// ---- CTA-wide exclusive scan of one value per thread (1024 threads) -----------
+__device__ __forceinline__ uint32_t cta_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t& total)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        uint32_t w = lane < nw ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) s_warp[lane] = w;   // inclusive warp prefix
+    }
+    __syncthreads();
+    total = s_warp[(blockDim.x >> 5) - 1];
+    uint32_t before = wid > 0 ? s_warp[wid - 1] : 0u;
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ counts, int64_t n_tiles,
+                                                              uint32_t* __restrict__ partials)
+{
+    __shared__ uint32_t s_warp[32];
+    int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; i++)
+        if (base + i < n_tiles) s += counts[base + i];
+    uint32_t tot;
+    cta_exclusive_scan(s, s_warp, tot);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t* __restrict__ partials, int64_t n_chunks,
+                                                           int64_t capacity, uint32_t* __restrict__ dev_count,
+                                                           uint32_t* __restrict__ dev_status)
+{
+    __shared__ uint32_t s_warp[32];
+    // 64-bit running total so an overflow of the 32-bit instance count is seen
+    uint64_t carry = 0;
+    for (int64_t base = 0; base < n_chunks; base += (int64_t)kScanThreads * kScanPer) {
+        int64_t i0 = base + (int64_t)threadIdx.x * kScanPer;
+        uint32_t v[kScanPer];
+        uint32_t s = 0;
+#pragma unroll
+        for (int i = 0; i < kScanPer; i++) { v[i] = (i0 + i < n_chunks) ? partials[i0 + i] : 0u; s += v[i]; }
+        uint32_t tot;
+        uint32_t ex = cta_exclusive_scan(s, s_warp, tot);
+        uint64_t run = carry + ex;
+#pragma unroll
+        for (int i = 0; i < kScanPer; i++) {
+            if (i0 + i < n_chunks) partials[i0 + i] = (uint32_t)run;
+            run += v[i];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        partials[n_chunks] = (uint32_t)carry;
+        *dev_count = carry > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)carry;
+        if ((int64_t)carry > capacity) atomicOr(dev_status, DG_STATUS_CAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ counts, int64_t n_tiles,
+                                                            const uint32_t* __restrict__ partials, int64_t n_chunks,
+                                                            const uint32_t* __restrict__ dev_count, int64_t capacity,
+                                                            uint32_t* __restrict__ ranges, uint32_t* __restrict__ cursor)
+{
+    __shared__ uint32_t s_warp[32];
+    bool overflow = (int64_t)(*dev_count) > capacity;
+    int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+    uint32_t v[kScanPer], s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; i++) { v[i] = base + i < n_tiles ? counts[base + i] : 0u; s += v[i]; }
+    uint32_t tot;
+    uint32_t run = partials[blockIdx.x] + cta_exclusive_scan(s, s_warp, tot);
+#pragma unroll
+    for (int i = 0; i < kScanPer; i++) {
+        int64_t t = base + i;
+        if (t < n_tiles) {
+            uint32_t b = overflow ? 0u : run, e = overflow ? 0u : run + v[i];
+            ranges[2 * t] = b;
+            ranges[2 * t + 1] = e;
+            cursor[t] = b;
+        }
+        run += v[i];
+    }
+}
+
+// ---- pass 2: scatter (depth bits, record) into tile segments ------------------------
+__global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ rect, const float4* __restrict__ rec,
+                                                 const dg_camera* __restrict__ cams, int n_views, int64_t n_rec,
+                                                 const uint32_t* __restrict__ dev_count, int64_t capacity,
+                                                 uint32_t* __restrict__ cursor, uint64_t* __restrict__ pairs)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rec) return;
+    if ((int64_t)(*dev_count) > capacity) return;
+    uint2 rr = rect[r];
+    uint32_t x0 = rr.x & 0xFFFFu, y0 = rr.x >> 16, x1 = rr.y & 0xFFFFu, y1 = rr.y >> 16;
+    if (x1 <= x0 || y1 <= y0) return;
+    int v = find_view_of_rec(cams, n_views, r);
+    uint32_t toff = (uint32_t)__ldg(&cams[v].tile_off), TX = (uint32_t)__ldg(&cams[v].tiles_x);
+    uint64_t pr = ((uint64_t)__float_as_uint(rec[3 * r + 2].y) << 32) | (uint64_t)(uint32_t)r;
+    for (uint32_t ty = y0; ty < y1; ty++)
+        for (uint32_t tx = x0; tx < x1; tx++) {
+            uint32_t pos = atomicAdd(&cursor[toff + ty * TX + tx], 1u);
+            pairs[pos] = pr;
+        }
+}
+
+// ---- per-segment sort ----------------------------------------------------------------
+// Bitonic network in its "all ascending" form: for each merge size k the
+// first step compares i with its mirror in the k-block, later steps compare
+// i with i + j.  The smaller element always goes to the lower index, so
+// positions >= n behave as +infinity and need no storage (virtual padding).
+template <int NT>
+__device__ __forceinline__ void bitonic_sort(uint64_t* s, uint32_t n)
+{
+    uint32_t N = 1;
+    while (N < n) N <<= 1;
+    for (uint32_t k = 2; k <= N; k <<= 1) {
+        uint32_t half = k >> 1;
+        for (uint32_t p = threadIdx.x; p < N / 2; p += NT) {
+            uint32_t blk = p / half, off = p % half;
+            uint32_t i = blk * k + off, l = blk * k + k - 1 - off;
+            if (l < n) {
+                uint64_t a = s[i], b = s[l];
+                if (a > b) { s[i] = b; s[l] = a; }
+            }
+        }
+        __syncthreads();
+        for (uint32_t j = half >> 1; j > 0; j >>= 1) {
+            for (uint32_t p = threadIdx.x; p < N / 2; p += NT) {
+                uint32_t i = (p / j) * 2 * j + (p % j), l = i + j;
+                if (l < n) {
+                    uint64_t a = s[i], b = s[l];
+                    if (a > b) { s[i] = b; s[l] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ void write_segment(const uint64_t* s, uint32_t n, uint32_t start, uint64_t tile,
+                                              uint32_t* vals, uint64_t* keys, int nt)
+{
+    for (uint32_t i = threadIdx.x; i < n; i += nt) {
+        uint64_t p = s[i];
+        vals[start + i] = (uint32_t)p;
+        if (keys) keys[start + i] = (tile << 32) | (p >> 32);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sort_small(const uint32_t* __restrict__ ranges, int64_t n_tiles,
+                                                    const uint64_t* __restrict__ pairs, uint32_t* __restrict__ vals,
+                                                    uint64_t* __restrict__ keys, uint32_t* __restrict__ counters,
+                                                    uint32_t* __restrict__ big_list, uint32_t* __restrict__ huge_list)
+{
+    __shared__ uint64_t s[kSmallCap];
+    int64_t t = blockIdx.x;
+    uint32_t start = ranges[2 * t], n = ranges[2 * t + 1] - start;
+    if (n == 0) return;
+    if (n > kSmallCap) {
+        if (threadIdx.x == 0) {
+            if (n <= kBigCap) big_list[atomicAdd(&counters[0], 1u)] = (uint32_t)t;
+            else huge_list[atomicAdd(&counters[1], 1u)] = (uint32_t)t;
+        }
+        return;
+    }
+    for (uint32_t i = threadIdx.x; i < n; i += 256) s[i] = pairs[start + i];
+    __syncthreads();
+    bitonic_sort<256>(s, n);
+    write_segment(s, n, start, (uint64_t)t, vals, keys, 256);
+}
+
+__global__ void __launch_bounds__(1024) k_sort_big(const uint32_t* __restrict__ ranges,
+                                                   const uint64_t* __restrict__ pairs, uint32_t* __restrict__ vals,
+                                                   uint64_t* __restrict__ keys, const uint32_t* __restrict__ counters,
+                                                   const uint32_t* __restrict__ big_list)
+{
+    extern __shared__ uint64_t s_big[];
+    uint32_t nb = counters[0];
+    for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+        uint32_t t = big_list[i];
+        uint32_t start = ranges[2 * (int64_t)t], n = ranges[2 * (int64_t)t + 1] - start;
+        for (uint32_t j = threadIdx.x; j < n; j += 1024) s_big[j] = pairs[start + j];
+        __syncthreads();
+        bitonic_sort<1024>(s_big, n);
+        write_segment(s_big, n, start, (uint64_t)t, vals, keys, 1024);
+        __syncthreads();
+    }
+}
+
+// Segments larger than shared memory: the same network in place in global
+// memory (one CTA per segment; rare for the workloads here).
+__global__ void __launch_bounds__(1024) k_sort_huge(const uint32_t* __restrict__ ranges, uint64_t* __restrict__ pairs,
+                                                    uint32_t* __restrict__ vals, uint64_t* __restrict__ keys,
+                                                    const uint32_t* __restrict__ counters,
+                                                    const uint32_t* __restrict__ huge_list)
+{
+    uint32_t nh = counters[1];
+    for (uint32_t i = blockIdx.x; i < nh; i += gridDim.x) {
+        uint32_t t = huge_list[i];
+        uint32_t start = ranges[2 * (int64_t)t], n = ranges[2 * (int64_t)t + 1] - start;
+        bitonic_sort<1024>(pairs + start, n);
+        __threadfence_block();
+        write_segment(pairs + start, n, start, (uint64_t)t, vals, keys, 1024);
+        __syncthreads();
+    }
+}
+
+int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams, const dg_plan& plan,
+                    int64_t capacity, uint64_t* keys, uint32_t* vals, uint32_t* ranges, uint32_t* dev_count,
+                    void* ws, uint32_t* dev_status, cudaStream_t st)
+{
+    BinWs w;
+    bin_ws_layout(plan.n_tiles, capacity, &w, (char*)ws);
+    int64_t n_chunks = (plan.n_tiles + kScanChunk - 1) / kScanChunk;
+    if (cudaMemsetAsync(w.counts, 0, 4 * (size_t)(plan.n_tiles + 2), st) != cudaSuccess) return DG_ERR_CUDA;
+    if (plan.n_rec > 0) {
+        k_count<<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(rect, cams, plan.n_views, plan.n_rec, w.counts);
+        note_launch();
+    }
+    k_scan_reduce<<<(unsigned)n_chunks, kScanThreads, 0, st>>>(w.counts, plan.n_tiles, w.partials);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(w.partials, n_chunks, capacity, dev_count, dev_status);
+    k_scan_down<<<(unsigned)n_chunks, kScanThreads, 0, st>>>(w.counts, plan.n_tiles, w.partials, n_chunks, dev_count,
+                                                             capacity, ranges, w.cursor);
+    note_launch(3);
+    if (plan.n_rec > 0) {
+        k_scatter<<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(rect, rec, cams, plan.n_views, plan.n_rec,
+                                                                        dev_count, capacity, w.cursor, w.pairs);
+        note_launch();
+    }
+    uint32_t* counters = w.counts + plan.n_tiles;
+    k_sort_small<<<(unsigned)plan.n_tiles, 256, 0, st>>>(ranges, plan.n_tiles, w.pairs, vals, keys, counters,
+                                                         w.big_list, w.huge_list);
+    k_sort_big<<<148, 1024, kBigCap * sizeof(uint64_t), st>>>(ranges, w.pairs, vals, keys, counters, w.big_list);
+    k_sort_huge<<<148, 1024, 0, st>>>(ranges, w.pairs, vals, keys, counters, w.huge_list);
+    note_launch(3);
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
+int bin_sort_init()
+{
+    if (cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kBigCap * sizeof(uint64_t))) != cudaSuccess)
+        return DG_ERR_CUDA;
+    return DG_OK;
+}
+
+}  // namespace dg
