@@ -1,0 +1,263 @@
+// K9 and K10: the block ADMM of Sec. 3.2 over the batched block-local copies.
+//
+// K9 (x-step, Eq. 8a / 12a): one Adam step on every copy with the gradient
+// of f_k plus rho_grp (x - z + u) on shared copies; z - u is kept per shared
+// copy as the "anchor" so the step reads one extra float per shared float.
+// Elementwise over the whole parameter buffer in float4 units; HBM-bound.
+//
+// K10 (consensus, Eq. 8b-c / 12b-c, over-relaxation of Sec. 3.3, residuals of
+// Eq. 9): one thread per global Gaussian gathers its n_i copies through the
+// CSR sharing map.  HBM-bound.
+#include "common.cuh"
+
+namespace dg {
+
+struct AdamArgs {
+    float rho[5];
+    float lr[6];
+    float b1, b2, eps;
+    int step;
+};
+
+__device__ __forceinline__ void adam1(float& x, float g, float& m, float& v, float lr, float b1, float b2,
+                                      float eps, float c1, float c2)
+{
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    x -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
+__global__ void __launch_bounds__(256) k_adam_admm(float4* __restrict__ x, const float4* __restrict__ g,
+                                                   float4* __restrict__ m, float4* __restrict__ v,
+                                                   const float4* __restrict__ anchor,
+                                                   const uint8_t* __restrict__ shared, int64_t n, int64_t ld,
+                                                   int64_t units, AdamArgs a)
+{
+    float c1 = 1.f - powf(a.b1, (float)a.step), c2 = 1.f - powf(a.b2, (float)a.step);
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t q4 = ld >> 2;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += stride) {
+        // which field, which copies, which group / learning rate per lane
+        int64_t c0;
+        int field;              // 0 mean+opacity, 1 rotation, 2 scale, 3 SH plane
+        int plane = 0;
+        if (u < 3 * ld) { field = (int)(u / ld); c0 = u - field * ld; }
+        else { int64_t s = u - 3 * ld; plane = (int)(s / q4); c0 = 4 * (s - plane * q4); field = 3; }
+        float rho[4], lr[4];
+        bool act[4], sh[4];
+        if (field == 0) {
+            rho[0] = rho[1] = rho[2] = a.rho[0]; rho[3] = a.rho[4];
+            lr[0] = lr[1] = lr[2] = a.lr[0]; lr[3] = a.lr[5];
+            bool ok = c0 < n, s = ok && shared[c0];
+            act[0] = act[1] = act[2] = act[3] = ok;
+            sh[0] = sh[1] = sh[2] = sh[3] = s;
+        } else if (field == 1) {
+            rho[0] = rho[1] = rho[2] = rho[3] = a.rho[1];
+            lr[0] = lr[1] = lr[2] = lr[3] = a.lr[1];
+            bool ok = c0 < n, s = ok && shared[c0];
+            act[0] = act[1] = act[2] = act[3] = ok;
+            sh[0] = sh[1] = sh[2] = sh[3] = s;
+        } else if (field == 2) {
+            rho[0] = rho[1] = rho[2] = rho[3] = a.rho[2];
+            lr[0] = lr[1] = lr[2] = lr[3] = a.lr[2];
+            bool ok = c0 < n, s = ok && shared[c0];
+            act[0] = act[1] = act[2] = ok; act[3] = false;     // padding lane
+            sh[0] = sh[1] = sh[2] = sh[3] = s;
+        } else {
+            float l = plane < 3 ? a.lr[3] : a.lr[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                rho[i] = a.rho[3]; lr[i] = l;
+                act[i] = c0 + i < n;
+                sh[i] = act[i] && shared[c0 + i];
+            }
+        }
+        if (!(act[0] || act[1] || act[2] || act[3])) continue;
+        float4 xv = x[u], gv = g[u], mv = m[u], vv = v[u];
+        float xs[4] = {xv.x, xv.y, xv.z, xv.w}, gs[4] = {gv.x, gv.y, gv.z, gv.w};
+        float ms[4] = {mv.x, mv.y, mv.z, mv.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
+        if (sh[0] || sh[1] || sh[2] || sh[3]) {
+            float4 av = anchor[u];
+            float as[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                if (sh[i]) gs[i] += rho[i] * (xs[i] - as[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            if (act[i]) adam1(xs[i], gs[i], ms[i], vs[i], lr[i], a.b1, a.b2, a.eps, c1, c2);
+        x[u] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+        m[u] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+        v[u] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+    }
+}
+
+// ---- consensus ---------------------------------------------------------------------
+struct ConsArgs {
+    float rho[5];
+    float alpha;
+    int n_planes;
+};
+
+// one scalar element of a global held by n >= 2 copies
+__device__ __forceinline__ float cons_elem(const float* xp, float* up, float* ap, const int32_t* cp, int n,
+                                           int64_t stride, float zprev, float alpha, float& r_primal)
+{
+    float acc = 0.f;
+    for (int k = 0; k < n; k++) {
+        int64_t c = (int64_t)cp[k] * stride;
+        float xh = alpha * xp[c] + (1.f - alpha) * zprev;
+        acc += xh + up[c];
+    }
+    float z = acc / (float)n;
+    for (int k = 0; k < n; k++) {
+        int64_t c = (int64_t)cp[k] * stride;
+        float xv = xp[c];
+        float xh = alpha * xv + (1.f - alpha) * zprev;
+        float un = up[c] + xh - z;
+        up[c] = un;
+        ap[c] = z - un;
+        r_primal += (xv - z) * (xv - z);
+    }
+    return z;
+}
+
+__global__ void __launch_bounds__(128) k_consensus(GView x, GView u, GView z, GView an,
+                                                   const int64_t* __restrict__ g_off,
+                                                   const int32_t* __restrict__ g_copies, int64_t n_glob,
+                                                   ConsArgs a, double* __restrict__ res)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float rp[5] = {0, 0, 0, 0, 0}, rd[5] = {0, 0, 0, 0, 0};
+    if (i < n_glob) {
+        int64_t b = g_off[i];
+        int n = (int)(g_off[i + 1] - b);
+        const int32_t* cp = g_copies + b;
+        if (n == 1) {
+            int64_t c = cp[0];
+            z.mo[i] = x.mo[c];
+            z.quat[i] = x.quat[c];
+            z.scale[i] = x.scale[c];
+            for (int j = 0; j < a.n_planes; j++) z.sh[(int64_t)j * z.ld + i] = x.sh[(int64_t)j * x.ld + c];
+        } else if (n > 1) {
+            // float4 fields: mean+opacity, rotation, scale, as scalar lanes
+            float4* xf[3] = {x.mo, x.quat, x.scale};
+            float4* uf[3] = {u.mo, u.quat, u.scale};
+            float4* zf[3] = {z.mo, z.quat, z.scale};
+            float4* af[3] = {an.mo, an.quat, an.scale};
+            for (int f = 0; f < 3; f++) {
+                float4 zo = zf[f][i];
+                float zp[4] = {zo.x, zo.y, zo.z, zo.w}, zn[4];
+#pragma unroll
+                for (int l = 0; l < 4; l++) {
+                    int grp = f == 0 ? (l < 3 ? 0 : 4) : (f == 1 ? 1 : 2);
+                    float r = 0.f;
+                    zn[l] = cons_elem((const float*)xf[f] + l, (float*)uf[f] + l, (float*)af[f] + l, cp, n, 4,
+                                      zp[l], a.alpha, r);
+                    if (!(f == 2 && l == 3)) {
+                        rp[grp] += r;
+                        float dz = zn[l] - zp[l];
+                        rd[grp] += a.rho[grp] * a.rho[grp] * (float)n * dz * dz;
+                    }
+                }
+                zf[f][i] = make_float4(zn[0], zn[1], zn[2], zn[3]);
+            }
+            for (int j = 0; j < a.n_planes; j++) {
+                float zo = z.sh[(int64_t)j * z.ld + i];
+                float r = 0.f;
+                float zn = cons_elem(x.sh + (int64_t)j * x.ld, u.sh + (int64_t)j * u.ld, an.sh + (int64_t)j * an.ld,
+                                     cp, n, 1, zo, a.alpha, r);
+                z.sh[(int64_t)j * z.ld + i] = zn;
+                rp[3] += r;
+                rd[3] += a.rho[3] * a.rho[3] * (float)n * (zn - zo) * (zn - zo);
+            }
+        }
+    }
+    if (res) {
+        __shared__ float s_r[4][10];
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+            float a0 = rp[k], a1 = rd[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            }
+            if (lane == 0) { s_r[w][k] = a0; s_r[w][5 + k] = a1; }
+        }
+        __syncthreads();
+        if (threadIdx.x < 10) {
+            double t = 0.0;
+            for (int ww = 0; ww < 4; ww++) t += s_r[ww][threadIdx.x];
+            if (t != 0.0) atomicAdd(&res[threadIdx.x], t);
+        }
+    }
+}
+
+// anchor = z[gid] - u for shared copies
+__global__ void __launch_bounds__(256) k_anchor(GView z, GView u, GView an, const int32_t* __restrict__ gid,
+                                                const uint8_t* __restrict__ shared, int64_t n, int n_planes)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n || !shared[c]) return;
+    int64_t gI = gid[c];
+    float4 a, b;
+    a = z.mo[gI]; b = u.mo[c]; an.mo[c] = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+    a = z.quat[gI]; b = u.quat[c]; an.quat[c] = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+    a = z.scale[gI]; b = u.scale[c]; an.scale[c] = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+    for (int j = 0; j < n_planes; j++)
+        an.sh[(int64_t)j * an.ld + c] = z.sh[(int64_t)j * z.ld + gI] - u.sh[(int64_t)j * u.ld + c];
+}
+
+int launch_adam_admm(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m, dg_gaussians* v,
+                     const dg_gaussians* anchor, const uint8_t* shared, const float* rho, const float* lr,
+                     float b1, float b2, float eps, int step, cudaStream_t st)
+{
+    if (x->n == 0) return DG_OK;
+    AdamArgs a;
+    for (int i = 0; i < 5; i++) a.rho[i] = rho[i];
+    for (int i = 0; i < 6; i++) a.lr[i] = lr[i];
+    a.b1 = b1; a.b2 = b2; a.eps = eps; a.step = step;
+    int64_t units = (12 + 3 * (int64_t)sh_coefs(x->sh_degree)) * x->ld / 4;
+    int64_t blocks = (units + 255) / 256;
+    if (blocks > 148 * 64) blocks = 148 * 64;
+    const float4* an = anchor ? reinterpret_cast<const float4*>(anchor->data) : nullptr;
+    k_adam_admm<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<float4*>(x->data),
+                                                 reinterpret_cast<const float4*>(g->data),
+                                                 reinterpret_cast<float4*>(m->data), reinterpret_cast<float4*>(v->data),
+                                                 an, shared, x->n, x->ld, units, a);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
+int launch_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z, dg_gaussians* an,
+                     const int64_t* g_off, const int32_t* g_copies, const float* rho, float alpha, double* res,
+                     cudaStream_t st)
+{
+    if (res && cudaMemsetAsync(res, 0, 10 * sizeof(double), st) != cudaSuccess) return DG_ERR_CUDA;
+    if (z->n == 0) return DG_OK;
+    ConsArgs a;
+    for (int i = 0; i < 5; i++) a.rho[i] = rho[i];
+    a.alpha = alpha;
+    a.n_planes = 3 * sh_coefs(x->sh_degree);
+    k_consensus<<<(unsigned)((z->n + 127) / 128), 128, 0, st>>>(gview(x), gview(u), gview(z), gview(an), g_off,
+                                                                 g_copies, z->n, a, res);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
+int launch_anchor(const dg_gaussians* z, const dg_gaussians* u, const int32_t* gid, const uint8_t* shared,
+                  dg_gaussians* an, cudaStream_t st)
+{
+    if (u->n == 0) return DG_OK;
+    k_anchor<<<(unsigned)((u->n + 255) / 256), 256, 0, st>>>(gview(z), gview(u), gview(an), gid, shared, u->n,
+                                                             3 * sh_coefs(z->sh_degree));
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
+}  // namespace dg

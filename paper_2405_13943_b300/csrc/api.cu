@@ -1,0 +1,327 @@
+// C ABI of libdogs: argument checks, batch planning, workspace carving and
+// the launch sequences.  No allocation, no synchronisation.
+#include <atomic>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace dg {
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+int launch_project(const dg_gaussians*, const dg_camera*, const dg_plan&, float4*, uint2*, cudaStream_t);
+int launch_project_bwd(const dg_gaussians*, const dg_camera*, const dg_plan&, const uint2*, const float4*,
+                       dg_gaussians*, cudaStream_t);
+size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity);
+int launch_bin_sort(const float4*, const uint2*, const dg_camera*, const dg_plan&, int64_t, uint64_t*, uint32_t*,
+                    uint32_t*, uint32_t*, void*, uint32_t*, cudaStream_t);
+int bin_sort_init();
+int launch_raster_fwd(const float4*, const uint32_t*, const uint32_t*, const dg_camera*, const dg_plan&,
+                      const float*, float*, float*, uint32_t*, cudaStream_t);
+int launch_raster_bwd(const float4*, const uint32_t*, const uint32_t*, const dg_camera*, const dg_plan&,
+                      const float*, const float*, const uint32_t*, const float*, float*, cudaStream_t);
+size_t loss_ws_bytes(const dg_plan&);
+int launch_loss(const float*, const float*, const dg_camera*, const dg_plan&, float, float, double*, float*, void*,
+                cudaStream_t);
+int launch_adam_admm(dg_gaussians*, const dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*,
+                     const uint8_t*, const float*, const float*, float, float, float, int, cudaStream_t);
+int launch_consensus(const dg_gaussians*, dg_gaussians*, dg_gaussians*, dg_gaussians*, const int64_t*,
+                     const int32_t*, const float*, float, double*, cudaStream_t);
+int launch_anchor(const dg_gaussians*, const dg_gaussians*, const int32_t*, const uint8_t*, dg_gaussians*,
+                  cudaStream_t);
+
+static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static bool valid_gauss(const dg_gaussians* g)
+{
+    if (!g) return false;
+    if (g->n < 0 || g->ld < g->n || (g->ld & 3) || g->sh_degree < 0 || g->sh_degree > 3) return false;
+    if (g->n > 0 && (!g->data || !aligned16(g->data))) return false;
+    return true;
+}
+
+static bool same_layout(const dg_gaussians* a, const dg_gaussians* b)
+{
+    return a->n == b->n && a->ld == b->ld && a->sh_degree == b->sh_degree;
+}
+
+static bool valid_plan(const dg_plan* p)
+{
+    if (!p || p->n_views < 0 || p->n_views > DG_MAX_VIEWS || p->n_blocks < 1 || p->n_blocks > DG_MAX_BLOCKS) return false;
+    if (!((p->tile_w == 16 && p->tile_h == 16) || (p->tile_w == 32 && p->tile_h == 8) || (p->tile_w == 8 && p->tile_h == 32)))
+        return false;
+    if (p->n_rec < 0 || p->n_rec >= (int64_t)0xFFFFFFFFll || p->n_tiles < 0 || p->n_tiles > (int64_t)1 << 24) return false;
+    return true;
+}
+
+// per-device one-time function attributes
+static int ensure_init()
+{
+    static std::atomic<uint64_t> done_mask{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DG_ERR_CUDA;
+    uint64_t bit = 1ull << (dev & 63);
+    if (done_mask.load() & bit) return DG_OK;
+    int rc = bin_sort_init();
+    if (rc == DG_OK) done_mask.fetch_or(bit);
+    return rc;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" {
+
+const char* dg_version(void) { return "libdogs 0.1 sm_103a"; }
+
+uint64_t dg_launch_count(void) { return g_launches.load(); }
+
+int64_t dg_gaussian_floats(int64_t ld, int sh_degree)
+{
+    if (ld < 0 || sh_degree < 0 || sh_degree > 3) return -1;
+    return (12 + 3 * (int64_t)sh_coefs(sh_degree)) * ld;
+}
+
+int dg_plan_views(dg_camera* cams, int n_views, const int64_t* blk_off, int n_blocks, int tile_w, int tile_h,
+                  dg_plan* plan)
+{
+    if (!cams || !blk_off || !plan || n_views < 1 || n_views > DG_MAX_VIEWS || n_blocks < 1 || n_blocks > DG_MAX_BLOCKS)
+        return DG_ERR_INVALID;
+    dg_plan p;
+    memset(&p, 0, sizeof p);
+    p.n_views = n_views;
+    p.n_blocks = n_blocks;
+    p.tile_w = tile_w;
+    p.tile_h = tile_h;
+    if (blk_off[0] != 0) return DG_ERR_INVALID;
+    for (int k = 0; k <= n_blocks; k++) {
+        if (k > 0 && blk_off[k] < blk_off[k - 1]) return DG_ERR_INVALID;
+        p.blk_off[k] = blk_off[k];
+    }
+    if (blk_off[n_blocks] >= (int64_t)0x7FFFFFFFll) return DG_ERR_INVALID;
+    int64_t rec = 0, tiles = 0, pix = 0;
+    int prev_block = 0;
+    for (int k = 0; k <= n_blocks; k++) p.blk_view_off[k] = 0;
+    for (int v = 0; v < n_views; v++) {
+        dg_camera& c = cams[v];
+        if (c.block < prev_block || c.block >= n_blocks) return DG_ERR_INVALID;
+        if (c.width <= 0 || c.height <= 0 || !(c.fx > 0.f) || !(c.fy > 0.f)) return DG_ERR_INVALID;
+        prev_block = c.block;
+        c.tiles_x = (c.width + tile_w - 1) / tile_w;
+        c.tiles_y = (c.height + tile_h - 1) / tile_h;
+        if (c.tiles_x > 65535 || c.tiles_y > 65535) return DG_ERR_INVALID;
+        c.tile_off = (int32_t)tiles;
+        c.reserved = 0;
+        c.rec_off = rec;
+        c.pix_off = pix;
+        c.gauss_begin = blk_off[c.block];
+        c.gauss_end = blk_off[c.block + 1];
+        rec += c.gauss_end - c.gauss_begin;
+        tiles += (int64_t)c.tiles_x * c.tiles_y;
+        pix += (int64_t)c.width * c.height;
+        if (c.width > p.max_width) p.max_width = c.width;
+        if (c.height > p.max_height) p.max_height = c.height;
+        if (tiles > ((int64_t)1 << 24) || rec >= (int64_t)0xFFFFFFFFll) return DG_ERR_INVALID;
+        p.blk_view_off[c.block + 1] = v + 1;
+    }
+    // blocks with no views: their view range is empty
+    for (int k = 1; k <= n_blocks; k++)
+        if (p.blk_view_off[k] < p.blk_view_off[k - 1]) p.blk_view_off[k] = p.blk_view_off[k - 1];
+    p.n_rec = rec;
+    p.n_tiles = tiles;
+    p.n_pixels = pix;
+    if (!valid_plan(&p)) return DG_ERR_INVALID;
+    *plan = p;
+    return DG_OK;
+}
+
+int dg_project(const dg_gaussians* x, const dg_camera* dev_cams, const dg_plan* plan, float* rec, uint32_t* rect,
+               void* stream)
+{
+    if (!valid_gauss(x) || !valid_plan(plan)) return DG_ERR_INVALID;
+    if (plan->blk_off[plan->n_blocks] > x->n) return DG_ERR_INVALID;
+    if (plan->n_rec > 0 && (!dev_cams || !rec || !rect || !aligned16(rec))) return DG_ERR_INVALID;
+    return launch_project(x, dev_cams, *plan, (float4*)rec, (uint2*)rect, (cudaStream_t)stream);
+}
+
+size_t dg_bin_sort_workspace_size(const dg_plan* plan, int64_t capacity)
+{
+    if (!valid_plan(plan) || capacity < 0) return 0;
+    return bin_sort_ws_bytes(plan->n_tiles, capacity);
+}
+
+int dg_bin_sort(const float* rec, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                int64_t capacity, uint64_t* keys, uint32_t* vals, uint32_t* ranges, uint32_t* dev_count, void* ws,
+                size_t ws_bytes, uint32_t* dev_status, void* stream)
+{
+    if (!valid_plan(plan) || capacity < 0 || capacity >= (int64_t)0xFFFFFFFFll) return DG_ERR_INVALID;
+    if (plan->n_tiles == 0) return DG_OK;
+    if (!dev_cams || !ranges || !dev_count || !dev_status || !ws || !vals) return DG_ERR_INVALID;
+    if (plan->n_rec > 0 && (!rec || !rect)) return DG_ERR_INVALID;
+    if (ws_bytes < bin_sort_ws_bytes(plan->n_tiles, capacity)) return DG_ERR_WORKSPACE;
+    int rc = ensure_init();
+    if (rc != DG_OK) return rc;
+    return launch_bin_sort((const float4*)rec, (const uint2*)rect, dev_cams, *plan, capacity, keys, vals, ranges,
+                           dev_count, ws, dev_status, (cudaStream_t)stream);
+}
+
+int dg_rasterize_fwd(const float* rec, const uint32_t* vals, const uint32_t* ranges, const dg_camera* dev_cams,
+                     const dg_plan* plan, const float* bg, float* image, float* T_final, uint32_t* last, void* stream)
+{
+    if (!valid_plan(plan) || !bg) return DG_ERR_INVALID;
+    if (plan->n_tiles == 0) return DG_OK;
+    if (!dev_cams || !ranges || !vals || !image || !T_final || !last) return DG_ERR_INVALID;
+    return launch_raster_fwd((const float4*)rec, vals, ranges, dev_cams, *plan, bg, image, T_final, last,
+                             (cudaStream_t)stream);
+}
+
+int dg_loss_l1(const float* image, const float* target, const dg_camera* dev_cams, const dg_plan* plan, float w_l1,
+               double* loss, float* dL_dimage, void* stream)
+{
+    if (!valid_plan(plan) || plan->n_views == 0) return DG_ERR_INVALID;
+    if (!image || !target || !dev_cams || !loss || !dL_dimage) return DG_ERR_INVALID;
+    return launch_loss(image, target, dev_cams, *plan, w_l1, 0.f, loss, dL_dimage, nullptr, (cudaStream_t)stream);
+}
+
+size_t dg_loss_workspace_size(const dg_plan* plan)
+{
+    if (!valid_plan(plan)) return 0;
+    return loss_ws_bytes(*plan);
+}
+
+int dg_loss_dssim(const float* image, const float* target, const dg_camera* dev_cams, const dg_plan* plan,
+                  float w_l1, float w_ssim, double* loss, float* dL_dimage, void* ws, size_t ws_bytes, void* stream)
+{
+    if (!valid_plan(plan) || plan->n_views == 0) return DG_ERR_INVALID;
+    if (!image || !target || !dev_cams || !loss || !dL_dimage) return DG_ERR_INVALID;
+    if (w_ssim != 0.f && (!ws || ws_bytes < loss_ws_bytes(*plan))) return DG_ERR_WORKSPACE;
+    return launch_loss(image, target, dev_cams, *plan, w_l1, w_ssim, loss, dL_dimage, ws, (cudaStream_t)stream);
+}
+
+int dg_rasterize_bwd(const float* rec, const uint32_t* rect, const uint32_t* vals, const uint32_t* ranges,
+                     const dg_camera* dev_cams, const dg_plan* plan, const float* bg, const float* T_final,
+                     const uint32_t* last, const float* dL_dimage, const dg_gaussians* x, float* drec,
+                     dg_gaussians* grads, void* stream)
+{
+    if (!valid_plan(plan) || !bg || !valid_gauss(x) || !valid_gauss(grads) || !same_layout(x, grads))
+        return DG_ERR_INVALID;
+    if (plan->blk_off[plan->n_blocks] > x->n) return DG_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (plan->n_rec > 0) {
+        if (!rec || !rect || !vals || !ranges || !dev_cams || !T_final || !last || !dL_dimage || !drec)
+            return DG_ERR_INVALID;
+        if (cudaMemsetAsync(drec, 0, (size_t)plan->n_rec * 12 * sizeof(float), st) != cudaSuccess) return DG_ERR_CUDA;
+        int rc = launch_raster_bwd((const float4*)rec, vals, ranges, dev_cams, *plan, bg, T_final, last, dL_dimage,
+                                   drec, st);
+        if (rc != DG_OK) return rc;
+    }
+    // K8 writes every copy in [0, blk_off[K]); zero the rest only when there is a rest
+    if (plan->blk_off[plan->n_blocks] < x->n && cudaMemsetAsync(grads->data, 0, (size_t)dg_gaussian_floats(grads->ld, grads->sh_degree) * 4, st)
+                        != cudaSuccess)
+        return DG_ERR_CUDA;
+    return launch_project_bwd(x, dev_cams, *plan, (const uint2*)rect, (const float4*)drec, grads, st);
+}
+
+int dg_adam_admm_step(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m, dg_gaussians* v,
+                      const dg_gaussians* anchor, const uint8_t* copy_shared, const float* rho, const float* lr,
+                      float beta1, float beta2, float eps, int step, void* stream)
+{
+    if (!valid_gauss(x) || !valid_gauss(g) || !valid_gauss(m) || !valid_gauss(v)) return DG_ERR_INVALID;
+    if (!same_layout(x, g) || !same_layout(x, m) || !same_layout(x, v)) return DG_ERR_INVALID;
+    if (anchor && (!valid_gauss(anchor) || !same_layout(x, anchor))) return DG_ERR_INVALID;
+    if (!rho || !lr || step < 1) return DG_ERR_INVALID;
+    if (x->n > 0 && anchor && !copy_shared) return DG_ERR_INVALID;
+    return launch_adam_admm(x, g, m, v, anchor, anchor ? copy_shared : nullptr, rho, lr, beta1, beta2, eps, step,
+                            (cudaStream_t)stream);
+}
+
+int dg_admm_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z, dg_gaussians* anchor,
+                      const int64_t* g_off, const int32_t* g_copies, const float* rho, float alpha,
+                      double* residuals, void* stream)
+{
+    if (!valid_gauss(x) || !valid_gauss(u) || !valid_gauss(z) || !valid_gauss(anchor)) return DG_ERR_INVALID;
+    if (!same_layout(x, u) || !same_layout(x, anchor) || z->sh_degree != x->sh_degree) return DG_ERR_INVALID;
+    if (!rho || !(alpha > 0.f && alpha < 2.f)) return DG_ERR_INVALID;
+    if (z->n > 0 && (!g_off || !g_copies)) return DG_ERR_INVALID;
+    return launch_consensus(x, u, z, anchor, g_off, g_copies, rho, alpha, residuals, (cudaStream_t)stream);
+}
+
+int dg_admm_anchor(const dg_gaussians* z, const dg_gaussians* u, const int32_t* copy_gid, const uint8_t* copy_shared,
+                   dg_gaussians* anchor, void* stream)
+{
+    if (!valid_gauss(z) || !valid_gauss(u) || !valid_gauss(anchor) || !same_layout(u, anchor)) return DG_ERR_INVALID;
+    if (z->sh_degree != u->sh_degree) return DG_ERR_INVALID;
+    if (u->n > 0 && (!copy_gid || !copy_shared)) return DG_ERR_INVALID;
+    return launch_anchor(z, u, copy_gid, copy_shared, anchor, (cudaStream_t)stream);
+}
+
+int dg_render_plan(dg_camera* host_cams, int n_views, int64_t n_gauss, int tile_w, int tile_h, dg_plan* plan)
+{
+    if (!host_cams || n_gauss < 0) return DG_ERR_INVALID;
+    int64_t off[2] = {0, n_gauss};
+    for (int v = 0; v < n_views; v++) host_cams[v].block = 0;
+    return dg_plan_views(host_cams, n_views, off, 1, tile_w, tile_h, plan);
+}
+
+struct RenderWs {
+    float4* rec;
+    uint2* rect;
+    uint32_t* vals;
+    uint32_t* ranges;
+    float* T_final;
+    uint32_t* last;
+    void* bin;
+    size_t bin_bytes;
+};
+
+static size_t render_ws_layout(const dg_plan& p, int64_t capacity, char* base, RenderWs* w)
+{
+    size_t off = 0;
+    auto take = [&](size_t b) { char* q = base ? base + off : nullptr; off += a256(b); return q; };
+    RenderWs r;
+    r.rec = (float4*)take((size_t)p.n_rec * 48 + 16);
+    r.rect = (uint2*)take((size_t)p.n_rec * 8 + 8);
+    r.vals = (uint32_t*)take((size_t)(capacity > 0 ? capacity : 1) * 4);
+    r.ranges = (uint32_t*)take((size_t)p.n_tiles * 8 + 8);
+    r.T_final = (float*)take((size_t)p.n_pixels * 4 + 4);
+    r.last = (uint32_t*)take((size_t)p.n_pixels * 4 + 4);
+    r.bin_bytes = bin_sort_ws_bytes(p.n_tiles, capacity);
+    r.bin = take(r.bin_bytes);
+    if (w) *w = r;
+    return off;
+}
+
+size_t dg_render_workspace_size(const dg_plan* plan, int64_t capacity)
+{
+    if (!valid_plan(plan) || capacity < 0) return 0;
+    return render_ws_layout(*plan, capacity, nullptr, nullptr);
+}
+
+int dg_render(const dg_gaussians* z, const dg_camera* dev_cams, const dg_plan* plan, const float* bg,
+              int64_t capacity, float* image, void* ws, size_t ws_bytes, uint32_t* dev_count, uint32_t* dev_status,
+              void* stream)
+{
+    if (!valid_gauss(z) || !valid_plan(plan) || !bg || plan->n_blocks != 1 || plan->blk_off[1] != z->n)
+        return DG_ERR_INVALID;
+    if (plan->n_tiles == 0) return DG_OK;
+    if (!dev_cams || !image || !ws || !dev_count || !dev_status) return DG_ERR_INVALID;
+    if (capacity < 0 || capacity >= (int64_t)0xFFFFFFFFll) return DG_ERR_INVALID;
+    if (ws_bytes < render_ws_layout(*plan, capacity, nullptr, nullptr)) return DG_ERR_WORKSPACE;
+    RenderWs w;
+    render_ws_layout(*plan, capacity, (char*)ws, &w);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = launch_project(z, dev_cams, *plan, w.rec, w.rect, st);
+    if (rc != DG_OK) return rc;
+    rc = ensure_init();
+    if (rc != DG_OK) return rc;
+    rc = launch_bin_sort(w.rec, w.rect, dev_cams, *plan, capacity, nullptr, w.vals, w.ranges, dev_count, w.bin,
+                         dev_status, st);
+    if (rc != DG_OK) return rc;
+    return launch_raster_fwd(w.rec, w.vals, w.ranges, dev_cams, *plan, bg, image, w.T_final, w.last, st);
+}
+
+}  // extern "C"
