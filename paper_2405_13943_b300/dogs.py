@@ -1,0 +1,302 @@
+"""Python face of libdogs: device buffers in the library's layout, batches of
+views, thin wrappers with the C ABI's names, and the autograd boundary.
+
+Layout conversion (numpy -> the structure-of-arrays parameter buffer) and
+buffer allocation happen here; every step of the method runs in libdogs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import synth as S
+
+
+def _round_up(x: int, m: int) -> int:
+    return (x + m - 1) // m * m
+
+
+def sh_coefs(deg: int) -> int:
+    return (deg + 1) ** 2
+
+
+# ---------------------------------------------------------------------------
+# parameter sets
+# ---------------------------------------------------------------------------
+class GaussianBuffer:
+    """n Gaussians of SH degree `deg` in one float32 device tensor laid out as
+    dg_gaussians: float4 (mean, opacity logit), float4 quaternion, float4
+    (log-scale, 0), then 3 (deg+1)^2 SH planes of ld floats."""
+
+    def __init__(self, n: int, deg: int, device="cuda", ld: Optional[int] = None,
+                 data: Optional[torch.Tensor] = None):
+        self.n, self.deg = int(n), int(deg)
+        self.ld = int(ld) if ld is not None else _round_up(max(self.n, 1), 32)
+        self.floats = (12 + 3 * sh_coefs(self.deg)) * self.ld
+        if data is None:
+            data = torch.zeros(self.floats, dtype=torch.float32, device=device)
+        assert data.numel() == self.floats and data.dtype == torch.float32
+        self.data = data
+        self.struct = L.DgGaussians(data.data_ptr(), self.n, self.ld, self.deg, 0)
+
+    @property
+    def ref(self):
+        return C.byref(self.struct)
+
+    def like(self) -> "GaussianBuffer":
+        return GaussianBuffer(self.n, self.deg, self.data.device, self.ld)
+
+    def clone(self) -> "GaussianBuffer":
+        return GaussianBuffer(self.n, self.deg, self.data.device, self.ld, self.data.clone())
+
+    def copy_(self, other: "GaussianBuffer") -> "GaussianBuffer":
+        self.data.copy_(other.data)
+        return self
+
+    # host-side packing -------------------------------------------------------
+    @staticmethod
+    def pack(g: S.Gaussians, ld: Optional[int] = None) -> np.ndarray:
+        n, K = g.n, g.sh.shape[1]
+        ld = ld if ld is not None else _round_up(max(n, 1), 32)
+        a = np.zeros((12 + 3 * K) * ld, np.float32)
+        mo = a[0:4 * ld].reshape(ld, 4)
+        mo[:n, :3] = g.means
+        mo[:n, 3] = g.opacity_logits
+        a[4 * ld:8 * ld].reshape(ld, 4)[:n] = g.quats
+        a[8 * ld:12 * ld].reshape(ld, 4)[:n, :3] = g.log_scales
+        a[12 * ld:].reshape(3 * K, ld)[:, :n] = g.sh.reshape(n, 3 * K).T
+        return a
+
+    @staticmethod
+    def unpack(a: np.ndarray, n: int, deg: int, ld: int) -> S.Gaussians:
+        K = sh_coefs(deg)
+        a = np.asarray(a, np.float32)
+        mo = a[0:4 * ld].reshape(ld, 4)[:n]
+        q = a[4 * ld:8 * ld].reshape(ld, 4)[:n]
+        s = a[8 * ld:12 * ld].reshape(ld, 4)[:n, :3]
+        sh = a[12 * ld:].reshape(3 * K, ld)[:, :n].T.reshape(n, K, 3)
+        return S.Gaussians(mo[:, :3].copy(), q.copy(), s.copy(), mo[:, 3].copy(), sh.copy())
+
+    @classmethod
+    def from_synth(cls, g: S.Gaussians, device="cuda", ld: Optional[int] = None) -> "GaussianBuffer":
+        a = cls.pack(g, ld)
+        b = cls(g.n, g.sh_degree, device, ld if ld is not None else _round_up(max(g.n, 1), 32),
+                torch.from_numpy(a).to(device))
+        return b
+
+    def to_synth(self) -> S.Gaussians:
+        return self.unpack(self.data.detach().cpu().numpy(), self.n, self.deg, self.ld)
+
+    def pad_lane(self) -> torch.Tensor:
+        return self.data[8 * self.ld:12 * self.ld].view(self.ld, 4)[:, 3]
+
+
+# ---------------------------------------------------------------------------
+# cameras, plans and per-batch buffers
+# ---------------------------------------------------------------------------
+def camera_array(cams: Sequence[S.Camera]):
+    arr = (L.DgCamera * len(cams))()
+    for i, c in enumerate(cams):
+        d = arr[i]
+        d.width, d.height = int(c.width), int(c.height)
+        d.fx, d.fy, d.cx, d.cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        R = np.asarray(c.R, np.float32).reshape(9)
+        t = np.asarray(c.t, np.float32).reshape(3)
+        p = np.asarray(c.campos, np.float32).reshape(3)
+        for k in range(9):
+            d.R[k] = float(R[k])
+        for k in range(3):
+            d.t[k] = float(t[k])
+            d.campos[k] = float(p[k])
+        d.near_z = float(c.near)
+        d.block = int(getattr(c, "block", 0))
+    return arr
+
+
+def plan_views(cams: Sequence[S.Camera], blk_off: Sequence[int], tile_w=16, tile_h=16):
+    arr = camera_array(cams)
+    off = (C.c_int64 * len(blk_off))(*[int(v) for v in blk_off])
+    plan = L.DgPlan()
+    L.check(L.lib().dg_plan_views(arr, len(cams), off, len(blk_off) - 1, tile_w, tile_h, C.byref(plan)),
+            "dg_plan_views")
+    return arr, plan
+
+
+def render_plan(cams: Sequence[S.Camera], n_gauss: int, tile_w=16, tile_h=16):
+    arr = camera_array(cams)
+    plan = L.DgPlan()
+    L.check(L.lib().dg_render_plan(arr, len(cams), int(n_gauss), tile_w, tile_h, C.byref(plan)), "dg_render_plan")
+    return arr, plan
+
+
+def cams_to_device(arr, device="cuda") -> torch.Tensor:
+    raw = np.frombuffer(bytes(arr), dtype=np.uint8).copy()
+    return torch.from_numpy(raw).to(device)
+
+
+class ViewBatch:
+    """A planned batch of views over block-local copies, with the device
+    buffers the rasteriser needs (records, tile rectangles, sorted instances,
+    ranges, images, saved forward state)."""
+
+    def __init__(self, cams: Sequence[S.Camera], blk_off: Sequence[int], tile_w=16, tile_h=16,
+                 device="cuda", capacity: Optional[int] = None, keep_keys=False, loss_ws=False):
+        self.cams = list(cams)
+        self.blk_off = [int(v) for v in blk_off]
+        self.device = device
+        self.host_cams, self.plan = plan_views(self.cams, self.blk_off, tile_w, tile_h)
+        self.dev_cams = cams_to_device(self.host_cams, device)
+        p = self.plan
+        self.n_rec, self.n_tiles, self.n_pixels = p.n_rec, p.n_tiles, p.n_pixels
+        i32 = dict(dtype=torch.int32, device=device)
+        self.rec = torch.zeros(max(p.n_rec, 1) * 12, dtype=torch.float32, device=device)
+        self.rect = torch.zeros(max(p.n_rec, 1) * 2, **i32)
+        self.ranges = torch.zeros(max(p.n_tiles, 1) * 2, **i32)
+        self.count = torch.zeros(1, **i32)
+        self.status = torch.zeros(1, **i32)
+        self.image = torch.zeros(max(p.n_pixels, 1) * 3, dtype=torch.float32, device=device)
+        self.T_final = torch.zeros(max(p.n_pixels, 1), dtype=torch.float32, device=device)
+        self.last = torch.zeros(max(p.n_pixels, 1), **i32)
+        self.drec = torch.zeros(max(p.n_rec, 1) * 12, dtype=torch.float32, device=device)
+        self.dL_dimage = torch.zeros_like(self.image)
+        self.loss = torch.zeros(max(p.n_views, 1), dtype=torch.float64, device=device)
+        self.keep_keys = keep_keys
+        self.loss_ws = None
+        if loss_ws:
+            self.loss_ws = torch.zeros(L.lib().dg_loss_workspace_size(C.byref(self.plan)), dtype=torch.uint8,
+                                       device=device)
+        self.set_capacity(capacity if capacity is not None else max(4 * p.n_rec, 1 << 16))
+
+    def set_capacity(self, cap: int) -> None:
+        self.capacity = int(cap)
+        dev = self.device
+        self.vals = torch.zeros(max(self.capacity, 1), dtype=torch.int32, device=dev)
+        self.keys = torch.zeros(max(self.capacity, 1), dtype=torch.int64, device=dev) if self.keep_keys else None
+        ws = L.lib().dg_bin_sort_workspace_size(C.byref(self.plan), self.capacity)
+        self.ws = torch.zeros(max(ws, 1), dtype=torch.uint8, device=dev)
+
+    # per-view image views (3, H, W)
+    def view_image(self, v: int, buf: Optional[torch.Tensor] = None) -> torch.Tensor:
+        c = self.host_cams[v]
+        b = self.image if buf is None else buf
+        o = 3 * c.pix_off
+        return b[o:o + 3 * c.width * c.height].view(3, c.height, c.width)
+
+    def view_pixels(self, v: int, buf: torch.Tensor) -> torch.Tensor:
+        c = self.host_cams[v]
+        return buf[c.pix_off:c.pix_off + c.width * c.height].view(c.height, c.width)
+
+
+# ---------------------------------------------------------------------------
+# wrappers with the C ABI's names
+# ---------------------------------------------------------------------------
+def dg_project(x: GaussianBuffer, vb: ViewBatch, stream=None) -> None:
+    L.check(L.lib().dg_project(x.ref, L.ptr(vb.dev_cams), C.byref(vb.plan), L.ptr(vb.rec), L.ptr(vb.rect),
+                               L.stream_handle(stream)), "dg_project")
+
+
+def dg_bin_sort(vb: ViewBatch, stream=None) -> None:
+    L.check(L.lib().dg_bin_sort(L.ptr(vb.rec), L.ptr(vb.rect), L.ptr(vb.dev_cams), C.byref(vb.plan), vb.capacity,
+                                L.ptr(vb.keys), L.ptr(vb.vals), L.ptr(vb.ranges), L.ptr(vb.count), L.ptr(vb.ws),
+                                vb.ws.numel(), L.ptr(vb.status), L.stream_handle(stream)), "dg_bin_sort")
+
+
+def dg_rasterize_fwd(vb: ViewBatch, bg=(0.0, 0.0, 0.0), stream=None) -> None:
+    L.check(L.lib().dg_rasterize_fwd(L.ptr(vb.rec), L.ptr(vb.vals), L.ptr(vb.ranges), L.ptr(vb.dev_cams),
+                                     C.byref(vb.plan), L.floats(bg), L.ptr(vb.image), L.ptr(vb.T_final),
+                                     L.ptr(vb.last), L.stream_handle(stream)), "dg_rasterize_fwd")
+
+
+def dg_loss_l1(vb: ViewBatch, target: torch.Tensor, w_l1=1.0, stream=None) -> None:
+    L.check(L.lib().dg_loss_l1(L.ptr(vb.image), L.ptr(target), L.ptr(vb.dev_cams), C.byref(vb.plan), w_l1,
+                               L.ptr(vb.loss), L.ptr(vb.dL_dimage), L.stream_handle(stream)), "dg_loss_l1")
+
+
+def dg_loss_dssim(vb: ViewBatch, target: torch.Tensor, w_l1=0.8, w_ssim=0.2, stream=None) -> None:
+    ws = vb.loss_ws
+    L.check(L.lib().dg_loss_dssim(L.ptr(vb.image), L.ptr(target), L.ptr(vb.dev_cams), C.byref(vb.plan), w_l1, w_ssim,
+                                  L.ptr(vb.loss), L.ptr(vb.dL_dimage), L.ptr(ws), 0 if ws is None else ws.numel(),
+                                  L.stream_handle(stream)), "dg_loss_dssim")
+
+
+def dg_rasterize_bwd(vb: ViewBatch, x: GaussianBuffer, grads: GaussianBuffer, dL_dimage=None, bg=(0.0, 0.0, 0.0),
+                     stream=None) -> None:
+    g = vb.dL_dimage if dL_dimage is None else dL_dimage
+    L.check(L.lib().dg_rasterize_bwd(L.ptr(vb.rec), L.ptr(vb.rect), L.ptr(vb.vals), L.ptr(vb.ranges),
+                                     L.ptr(vb.dev_cams), C.byref(vb.plan), L.floats(bg), L.ptr(vb.T_final),
+                                     L.ptr(vb.last), L.ptr(g), x.ref, L.ptr(vb.drec), grads.ref,
+                                     L.stream_handle(stream)), "dg_rasterize_bwd")
+
+
+def dg_adam_admm_step(x: GaussianBuffer, g: GaussianBuffer, m: GaussianBuffer, v: GaussianBuffer,
+                      anchor: Optional[GaussianBuffer], shared: Optional[torch.Tensor], rho, lr,
+                      beta1=0.9, beta2=0.999, eps=1e-15, step=1, stream=None) -> None:
+    L.check(L.lib().dg_adam_admm_step(x.ref, g.ref, m.ref, v.ref, None if anchor is None else anchor.ref,
+                                      L.ptr(shared), L.floats(rho), L.floats(lr), beta1, beta2, eps, int(step),
+                                      L.stream_handle(stream)), "dg_adam_admm_step")
+
+
+def dg_admm_consensus(x: GaussianBuffer, u: GaussianBuffer, z: GaussianBuffer, anchor: GaussianBuffer,
+                      g_off: torch.Tensor, g_copies: torch.Tensor, rho, alpha=1.0,
+                      residuals: Optional[torch.Tensor] = None, stream=None) -> None:
+    L.check(L.lib().dg_admm_consensus(x.ref, u.ref, z.ref, anchor.ref, L.ptr(g_off), L.ptr(g_copies),
+                                      L.floats(rho), float(alpha), L.ptr(residuals), L.stream_handle(stream)),
+            "dg_admm_consensus")
+
+
+def dg_admm_anchor(z: GaussianBuffer, u: GaussianBuffer, copy_gid: torch.Tensor, shared: torch.Tensor,
+                   anchor: GaussianBuffer, stream=None) -> None:
+    L.check(L.lib().dg_admm_anchor(z.ref, u.ref, L.ptr(copy_gid), L.ptr(shared), anchor.ref,
+                                   L.stream_handle(stream)), "dg_admm_anchor")
+
+
+# ---------------------------------------------------------------------------
+# composed passes
+# ---------------------------------------------------------------------------
+def forward(x: GaussianBuffer, vb: ViewBatch, bg=(0.0, 0.0, 0.0), stream=None, retry=True) -> None:
+    """dg_project + dg_bin_sort + dg_rasterize_fwd.  With retry=True the
+    instance count is checked on the host (one synchronisation) and the
+    binning is redone with a larger capacity if it overflowed."""
+    dg_project(x, vb, stream)
+    vb.status.zero_()
+    dg_bin_sort(vb, stream)
+    if retry:
+        m = int(vb.count.item()) & 0xFFFFFFFF
+        if m > vb.capacity or int(vb.status.item()) & L.DG_STATUS_CAPACITY:
+            vb.set_capacity(int(m * 1.25) + 1024)
+            vb.status.zero_()
+            dg_bin_sort(vb, stream)
+    dg_rasterize_fwd(vb, bg, stream)
+
+
+class RasterizeFn(torch.autograd.Function):
+    """Autograd boundary: forward = dg_project + dg_bin_sort +
+    dg_rasterize_fwd on a ViewBatch; backward = dg_rasterize_bwd (tile walk
+    back to front from T_final and last, then the projection adjoint).  The
+    differentiable input is the flat parameter tensor of a GaussianBuffer."""
+
+    @staticmethod
+    def forward(ctx, data: torch.Tensor, xbuf: GaussianBuffer, vb: ViewBatch, bg=(0.0, 0.0, 0.0)):
+        assert data.data_ptr() == xbuf.data.data_ptr()
+        forward(xbuf, vb, bg)
+        ctx.xbuf, ctx.vb, ctx.bg = xbuf, vb, bg
+        return vb.image[:3 * vb.n_pixels].clone()
+
+    @staticmethod
+    def backward(ctx, grad_image: torch.Tensor):
+        xbuf, vb = ctx.xbuf, ctx.vb
+        g = torch.zeros_like(vb.image)
+        g[:3 * vb.n_pixels] = grad_image
+        grads = xbuf.like()
+        dg_rasterize_bwd(vb, xbuf, grads, dL_dimage=g.contiguous(), bg=ctx.bg)
+        return grads.data, None, None, None
+
+
+def rasterize(xbuf: GaussianBuffer, vb: ViewBatch, bg=(0.0, 0.0, 0.0)) -> torch.Tensor:
+    """Differentiable render of all views in `vb`; returns the concatenated
+    planar images (sum over views of 3 H W floats)."""
+    return RasterizeFn.apply(xbuf.data, xbuf, vb, bg)

@@ -1,0 +1,105 @@
+"""CPU checks of the C ABI: the library loads without a GPU, exports every
+function include/dogs.h declares, the ctypes mirrors have the C layout, and
+the host-side batch planning validates its inputs."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2405_13943_b300 import _lib as L
+from paper_2405_13943_b300 import build as B
+from paper_2405_13943_b300 import synth as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dogs.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_function_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(L.exported_symbols())
+
+
+def test_struct_layouts_match_c(tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dogs.h"\nint main(void){'
+                   'printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(dg_gaussians), sizeof(dg_camera),'
+                   ' sizeof(dg_plan), offsetof(dg_camera, rec_off), offsetof(dg_camera, gauss_end),'
+                   ' offsetof(dg_plan, blk_off), offsetof(dg_plan, blk_view_off), offsetof(dg_plan, max_height));'
+                   'return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), "-o", str(exe), str(src)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = [C.sizeof(L.DgGaussians), C.sizeof(L.DgCamera), C.sizeof(L.DgPlan),
+            L.DgCamera.rec_off.offset, L.DgCamera.gauss_end.offset, L.DgPlan.blk_off.offset,
+            L.DgPlan.blk_view_off.offset, L.DgPlan.max_height.offset]
+    assert got == want
+
+
+def test_plan_numbering(lib):
+    from paper_2405_13943_b300 import dogs as D
+    cams = [S.cube_camera(40, 35), S.cube_camera(64, 48), S.cube_camera(17, 90)]
+    cams[0].block, cams[1].block, cams[2].block = 0, 0, 2
+    arr, plan = D.plan_views(cams, [0, 100, 150, 400], 16, 16)
+    assert plan.n_views == 3 and plan.n_blocks == 3
+    assert [arr[i].rec_off for i in range(3)] == [0, 100, 200]
+    assert plan.n_rec == 450
+    assert [arr[i].tiles_x for i in range(3)] == [3, 4, 2]
+    assert [arr[i].tile_off for i in range(3)] == [0, 9, 21]
+    assert plan.n_tiles == 9 + 12 + 12
+    assert [arr[i].pix_off for i in range(3)] == [0, 1400, 1400 + 3072]
+    assert list(plan.blk_view_off[:4]) == [0, 2, 2, 3]
+    assert (arr[2].gauss_begin, arr[2].gauss_end) == (150, 400)
+    assert (plan.max_width, plan.max_height) == (64, 90)
+
+
+def test_plan_rejects_bad_input(lib):
+    from paper_2405_13943_b300 import dogs as D
+    cams = [S.cube_camera(40, 35), S.cube_camera(64, 48)]
+    cams[0].block, cams[1].block = 1, 0           # not grouped by ascending block
+    with pytest.raises(L.DogsError):
+        D.plan_views(cams, [0, 10, 20], 16, 16)
+    cams[0].block, cams[1].block = 0, 0
+    with pytest.raises(L.DogsError):
+        D.plan_views(cams, [0, 10, 20], 16, 8)     # unsupported tile shape
+    with pytest.raises(L.DogsError):
+        D.plan_views(cams, [0, 30, 20], 16, 16)    # decreasing block offsets
+    bad = [S.cube_camera(0, 35)]
+    with pytest.raises(L.DogsError):
+        D.plan_views(bad, [0, 10], 16, 16)
+
+
+def test_pack_unpack_roundtrip():
+    from paper_2405_13943_b300 import dogs as D
+    g = S.cube_scene(37, 3, sh_degree=3)
+    a = D.GaussianBuffer.pack(g)
+    h = D.GaussianBuffer.unpack(a, 37, 3, 64)
+    for f in ("means", "quats", "log_scales", "opacity_logits", "sh"):
+        np.testing.assert_array_equal(getattr(g, f), getattr(h, f))
+    assert a.size == (12 + 48) * 64
+
+
+def test_calls_reject_null_arguments_without_touching_the_gpu(lib):
+    """Argument checks happen on the host, before any launch."""
+    plan = L.DgPlan()
+    g = L.DgGaussians(None, 10, 8, 0, 0)           # ld < n
+    assert lib.dg_project(C.byref(g), None, C.byref(plan), None, None, None) == L.DG_ERR_INVALID
+    assert lib.dg_gaussian_floats(64, 3) == 60 * 64
+    assert lib.dg_gaussian_floats(64, 4) == -1
