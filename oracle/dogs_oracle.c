@@ -341,11 +341,14 @@ int64_t oc_bin_sort(int64_t n_rec, const int32_t* view, const int32_t* rect, con
 typedef struct { uint32_t rec; double alpha, alpha_raw, G, T, dx, dy; } pair_t;
 
 /* composites one pixel; fills `pairs` (if non-NULL) with composited pairs    */
+/* margin: relative distance of the value decisions (1/255 skip, T stop) from */
+/* their thresholds; margin_grad (may be NULL): of the 0.99 clamp, which only   */
+/* decides gradients                                                           */
 static int composite_pixel(int px, int py, const uint32_t* vals, uint32_t beg, uint32_t end,
                            const double* rec, const double* bg, double* C, double* Tout,
-                           uint32_t* last, double* margin, pair_t* pairs)
+                           uint32_t* last, double* margin, double* margin_grad, pair_t* pairs)
 {
-    double T = 1.0, col[3] = {0, 0, 0}, mg = INFINITY;
+    double T = 1.0, col[3] = {0, 0, 0}, mg = INFINITY, mg2 = INFINITY;
     int np = 0;
     uint32_t lst = 0;
     for (uint32_t j = beg; j < end; j++) {
@@ -358,7 +361,7 @@ static int composite_pixel(int px, int py, const uint32_t* vals, uint32_t beg, u
         double alpha = ar < ALPHA_MAX ? ar : ALPHA_MAX;
         mg = fmin(mg, fabs(alpha - ALPHA_MIN) / ALPHA_MIN);
         if (alpha < ALPHA_MIN) continue;
-        mg = fmin(mg, fabs(ar - ALPHA_MAX) / ALPHA_MAX);   /* clamp decides the gradient */
+        mg2 = fmin(mg2, fabs(ar - ALPHA_MAX) / ALPHA_MAX);   /* clamp decides the gradient */
         double Tn = T * (1.0 - alpha);
         mg = fmin(mg, fabs(Tn - T_MIN) / T_MIN);
         if (Tn < T_MIN) break;
@@ -373,6 +376,7 @@ static int composite_pixel(int px, int py, const uint32_t* vals, uint32_t beg, u
     }
     for (int ch = 0; ch < 3; ch++) C[ch] = col[ch] + T * bg[ch];
     *Tout = T; *last = lst; *margin = mg;
+    if (margin_grad) *margin_grad = mg2;
     return np;
 }
 
@@ -381,7 +385,7 @@ static int composite_pixel(int px, int py, const uint32_t* vals, uint32_t beg, u
 void oc_rasterize_fwd(int width, int height, int tile_w, int tile_h, int64_t tile_off,
                       const uint32_t* vals, const uint32_t* ranges, const double* rec,
                       const double* bg, double* image, double* T_final, uint32_t* last,
-                      double* margin)
+                      double* margin, double* margin_grad)
 {
     int TX = (width + tile_w - 1) / tile_w;
     for (int py = 0; py < height; py++)
@@ -390,7 +394,7 @@ void oc_rasterize_fwd(int width, int height, int tile_w, int tile_h, int64_t til
             double C[3];
             int64_t p = (int64_t)py * width + px;
             composite_pixel(px, py, vals, ranges[2 * tile], ranges[2 * tile + 1], rec, bg, C,
-                            &T_final[p], &last[p], &margin[p], NULL);
+                            &T_final[p], &last[p], &margin[p], &margin_grad[p], NULL);
             for (int ch = 0; ch < 3; ch++) image[(int64_t)ch * width * height + p] = C[ch];
         }
 }
@@ -413,7 +417,7 @@ void oc_rasterize_bwd(int width, int height, int tile_w, int tile_h, int64_t til
             int64_t p = (int64_t)py * width + px;
             double C[3], Tf, mg; uint32_t lst;
             int np = composite_pixel(px, py, vals, ranges[2 * tile], ranges[2 * tile + 1], rec, bg, C,
-                                     &Tf, &lst, &mg, pairs);
+                                     &Tf, &lst, &mg, NULL, pairs);
             double gpix[3];
             for (int ch = 0; ch < 3; ch++) gpix[ch] = dL_dimage[(int64_t)ch * width * height + p];
             /* S_i = sum_{j > i} c_j alpha_j T_j + T_final * bg (suffix sums) */

@@ -62,7 +62,7 @@ def lib():
                                      u64p, u32p, u32p]
         _lib.oc_rasterize_fwd.restype = None
         _lib.oc_rasterize_fwd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, u32p, u32p,
-                                          dp, dp, dp, dp, u32p, dp]
+                                          dp, dp, dp, dp, u32p, dp, dp]
         _lib.oc_rasterize_bwd.restype = None
         _lib.oc_rasterize_bwd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, u32p, u32p,
                                           dp, dp, dp, dp]
@@ -221,11 +221,13 @@ def rasterize_fwd(proj: dict, bins: dict, plan: ViewPlan, bg=(0.0, 0.0, 0.0)) ->
         W, H = c.width, c.height
         img = np.zeros((3, H, W)); Tf = np.zeros((H, W)); last = np.zeros((H, W), np.uint32)
         mg = np.zeros((H, W))
+        mg2 = np.zeros((H, W))
         lib().oc_rasterize_fwd(W, H, plan.tw, plan.th, plan.tile_off[v], _p(vals, C.c_uint32),
                                _p(bins["ranges"], C.c_uint32), _p(rec, C.c_double),
                                _p(bgv, C.c_double), _p(img, C.c_double), _p(Tf, C.c_double),
-                               _p(last, C.c_uint32), _p(mg, C.c_double))
-        out.append({"image": img, "T_final": Tf, "last": last, "margin": mg})
+                               _p(last, C.c_uint32), _p(mg, C.c_double), _p(mg2, C.c_double))
+        # margin: value decisions (1/255 skip, T stop); margin_grad: the 0.99 clamp
+        out.append({"image": img, "T_final": Tf, "last": last, "margin": mg, "margin_grad": mg2})
     return out
 
 

@@ -23,8 +23,12 @@ def curate_gaussians(O, g: S.Gaussians, cams, tile_w, tile_h, thr=1e-4) -> S.Gau
     return g.subset(np.nonzero(keep)[0])
 
 
-def pixel_mask(views, thr=1e-4):
-    """Per view, True where every pixel decision has relative margin >= thr."""
+def pixel_mask(views, thr=1e-4, grad=False):
+    """Per view, True where every value decision of the pixel (and with
+    grad=True also the 0.99 clamp, which only decides gradients) has relative
+    margin >= thr."""
+    if grad:
+        return [(v["margin"] >= thr) & (v["margin_grad"] >= thr) for v in views]
     return [v["margin"] >= thr for v in views]
 
 

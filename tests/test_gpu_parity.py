@@ -54,8 +54,9 @@ def run_pair(D, O, g, cams, rows, blk_off, tw, th, bg, weights_seed=5, thr=1e-4)
     plan = O.ViewPlan(cams, rows, tw, th)
     f = O.render(x, g.sh_degree, plan, bg)
     masks = pixel_mask(f["views"], thr)
+    gmasks = pixel_mask(f["views"], thr, grad=True)
     rng = np.random.default_rng(weights_seed)
-    W = [rng.uniform(-1, 1, (3, c.height, c.width)) * m[None] for c, m in zip(cams, masks)]
+    W = [rng.uniform(-1, 1, (3, c.height, c.width)) * m[None] for c, m in zip(cams, gmasks)]
     dimg = torch.zeros_like(vb.image)
     for v, w in enumerate(W):
         vb.view_image(v, dimg).copy_(torch.from_numpy(w.astype(np.float32)))

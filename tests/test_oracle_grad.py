@@ -40,7 +40,7 @@ def test_backward_matches_central_differences(oracle, seed):
     x = O.params_from(g)
     deg = 3
     f0 = O.render(x, deg, plan, BG)
-    margins = min(float(v["margin"].min()) for v in f0["views"])
+    margins = min(min(float(v["margin"].min()), float(v["margin_grad"].min())) for v in f0["views"])
     if margins < 1e-4:
         pytest.skip("draw has a near-threshold pixel decision")
     W = smooth_weights(seed + 100, plan.cams)
