@@ -15,6 +15,8 @@ pytestmark = pytest.mark.gpu
 
 IMG_TOL = 1e-4
 REL_L2 = 1e-3
+FLIP_TOL = 2e-2          # one flipped decision moves a pixel by at most ~alpha T |c|
+EXCLUDE_FRAC = 5e-3
 GROUPS = ("means", "quats", "log_scales", "sh", "opacity_logits")
 
 
@@ -97,12 +99,16 @@ def check_forward(D, O, vb, f, masks, plan):
         excluded += int((~m).sum())
         err = np.abs(img - ov["image"]).max(0)
         assert err[m].max(initial=0.0) <= IMG_TOL, (v, err[m].max())
+        # excluded pixels: at most one flipped 1/255-skip or T-stop decision
+        assert err[~m].max(initial=0.0) <= FLIP_TOL, (v, err[~m].max())
         Tf = vb.view_pixels(v, vb.T_final).cpu().numpy()
         assert np.abs(Tf - ov["T_final"])[m].max(initial=0.0) <= IMG_TOL
         last = vb.view_pixels(v, vb.last).cpu().numpy().view(np.uint32)
         np.testing.assert_array_equal(last[m], ov["last"][m])
     total = sum(c.width * c.height for c in plan.cams)
-    assert excluded <= max(2, 1e-3 * total), excluded
+    # a Gaussian of screen std s puts about 2 pi s^2 eps pixels within relative
+    # eps of the 1/255 cut; with eps = 1e-4 that is ~0.1 % of pixels here
+    assert excluded <= max(2, EXCLUDE_FRAC * total), excluded
 
 
 def check_backward(D, O, g, grads, ob, deg):
