@@ -190,11 +190,14 @@ int dg_rasterize_bwd(const float* rec, const uint32_t* rect, const uint32_t* val
  * dg_admm_anchor.  Groups in the paper's order (Eq. 12): 0 p (mean),
  * 1 q (rotation), 2 s (scale), 3 f (SH), 4 o (opacity): rho[5] (host).
  * lr[6] (host): p, q, s, SH DC, SH rest, o.  Moments m, v updated in place;
- * bias correction with `step` >= 1. */
+ * bias correction with the iteration number `step` >= 1, or, if dev_step is
+ * not NULL, with the int32 it points to in device memory (read when the
+ * kernel runs, so a captured graph can be replayed for successive steps).
+ * anchor may be NULL (no penalty: plain Adam). */
 int dg_adam_admm_step(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m,
                       dg_gaussians* v, const dg_gaussians* anchor, const uint8_t* copy_shared,
                       const float* rho, const float* lr, float beta1, float beta2, float eps,
-                      int step, void* stream);
+                      int step, const int32_t* dev_step, void* stream);
 
 /* Consensus (Eq. 8b-c / 12b-c) over the global model z (n_global Gaussians).
  * Sharing map as CSR: the copies of global i are g_copies[g_off[i] ..

@@ -72,7 +72,7 @@ _SIGS = {
                                    C.POINTER(DgGaussians), _vp, C.POINTER(DgGaussians), _vp]),
     "dg_adam_admm_step": (C.c_int, [C.POINTER(DgGaussians), C.POINTER(DgGaussians), C.POINTER(DgGaussians),
                                     C.POINTER(DgGaussians), C.POINTER(DgGaussians), _vp, C.POINTER(C.c_float),
-                                    C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float, C.c_int, _vp]),
+                                    C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float, C.c_int, _vp, _vp]),
     "dg_admm_consensus": (C.c_int, [C.POINTER(DgGaussians), C.POINTER(DgGaussians), C.POINTER(DgGaussians),
                                     C.POINTER(DgGaussians), _vp, _vp, C.POINTER(C.c_float), C.c_float, _vp, _vp]),
     "dg_admm_anchor": (C.c_int, [C.POINTER(DgGaussians), C.POINTER(DgGaussians), _vp, _vp, C.POINTER(DgGaussians),

@@ -31,9 +31,10 @@ __global__ void __launch_bounds__(256) k_adam_admm(float4* __restrict__ x, const
                                                    float4* __restrict__ m, float4* __restrict__ v,
                                                    const float4* __restrict__ anchor,
                                                    const uint8_t* __restrict__ shared, int64_t n, int64_t ld,
-                                                   int64_t units, AdamArgs a)
+                                                   int64_t units, AdamArgs a, const int32_t* __restrict__ dev_step)
 {
-    float c1 = 1.f - powf(a.b1, (float)a.step), c2 = 1.f - powf(a.b2, (float)a.step);
+    float t = (float)(dev_step ? *dev_step : a.step);
+    float c1 = 1.f - powf(a.b1, t), c2 = 1.f - powf(a.b2, t);
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t q4 = ld >> 2;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += stride) {
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(256) k_anchor(GView z, GView u, GView an, cons
 
 int launch_adam_admm(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m, dg_gaussians* v,
                      const dg_gaussians* anchor, const uint8_t* shared, const float* rho, const float* lr,
-                     float b1, float b2, float eps, int step, cudaStream_t st)
+                     float b1, float b2, float eps, int step, const int32_t* dev_step, cudaStream_t st)
 {
     if (x->n == 0) return DG_OK;
     AdamArgs a;
@@ -226,7 +227,7 @@ int launch_adam_admm(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m, dg
     k_adam_admm<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<float4*>(x->data),
                                                  reinterpret_cast<const float4*>(g->data),
                                                  reinterpret_cast<float4*>(m->data), reinterpret_cast<float4*>(v->data),
-                                                 an, shared, x->n, x->ld, units, a);
+                                                 an, shared, x->n, x->ld, units, a, dev_step);
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;

@@ -25,7 +25,8 @@ size_t loss_ws_bytes(const dg_plan&);
 int launch_loss(const float*, const float*, const dg_camera*, const dg_plan&, float, float, double*, float*, void*,
                 cudaStream_t);
 int launch_adam_admm(dg_gaussians*, const dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*,
-                     const uint8_t*, const float*, const float*, float, float, float, int, cudaStream_t);
+                     const uint8_t*, const float*, const float*, float, float, float, int, const int32_t*,
+                     cudaStream_t);
 int launch_consensus(const dg_gaussians*, dg_gaussians*, dg_gaussians*, dg_gaussians*, const int64_t*,
                      const int32_t*, const float*, float, double*, cudaStream_t);
 int launch_anchor(const dg_gaussians*, const dg_gaussians*, const int32_t*, const uint8_t*, dg_gaussians*,
@@ -228,15 +229,15 @@ int dg_rasterize_bwd(const float* rec, const uint32_t* rect, const uint32_t* val
 
 int dg_adam_admm_step(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m, dg_gaussians* v,
                       const dg_gaussians* anchor, const uint8_t* copy_shared, const float* rho, const float* lr,
-                      float beta1, float beta2, float eps, int step, void* stream)
+                      float beta1, float beta2, float eps, int step, const int32_t* dev_step, void* stream)
 {
     if (!valid_gauss(x) || !valid_gauss(g) || !valid_gauss(m) || !valid_gauss(v)) return DG_ERR_INVALID;
     if (!same_layout(x, g) || !same_layout(x, m) || !same_layout(x, v)) return DG_ERR_INVALID;
     if (anchor && (!valid_gauss(anchor) || !same_layout(x, anchor))) return DG_ERR_INVALID;
-    if (!rho || !lr || step < 1) return DG_ERR_INVALID;
+    if (!rho || !lr || (!dev_step && step < 1)) return DG_ERR_INVALID;
     if (x->n > 0 && anchor && !copy_shared) return DG_ERR_INVALID;
     return launch_adam_admm(x, g, m, v, anchor, anchor ? copy_shared : nullptr, rho, lr, beta1, beta2, eps, step,
-                            (cudaStream_t)stream);
+                            dev_step, (cudaStream_t)stream);
 }
 
 int dg_admm_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z, dg_gaussians* anchor,

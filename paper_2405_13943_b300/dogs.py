@@ -234,10 +234,11 @@ def dg_rasterize_bwd(vb: ViewBatch, x: GaussianBuffer, grads: GaussianBuffer, dL
 
 def dg_adam_admm_step(x: GaussianBuffer, g: GaussianBuffer, m: GaussianBuffer, v: GaussianBuffer,
                       anchor: Optional[GaussianBuffer], shared: Optional[torch.Tensor], rho, lr,
-                      beta1=0.9, beta2=0.999, eps=1e-15, step=1, stream=None) -> None:
+                      beta1=0.9, beta2=0.999, eps=1e-15, step=1, dev_step: Optional[torch.Tensor] = None,
+                      stream=None) -> None:
     L.check(L.lib().dg_adam_admm_step(x.ref, g.ref, m.ref, v.ref, None if anchor is None else anchor.ref,
                                       L.ptr(shared), L.floats(rho), L.floats(lr), beta1, beta2, eps, int(step),
-                                      L.stream_handle(stream)), "dg_adam_admm_step")
+                                      L.ptr(dev_step), L.stream_handle(stream)), "dg_adam_admm_step")
 
 
 def dg_admm_consensus(x: GaussianBuffer, u: GaussianBuffer, z: GaussianBuffer, anchor: GaussianBuffer,

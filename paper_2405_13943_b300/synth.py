@@ -457,3 +457,40 @@ def random_image(seed: int, height: int, width: int) -> np.ndarray:
 
 def random_like(seed: int, shape, scale: float = 1.0) -> np.ndarray:
     return (_rng(seed).standard_normal(shape) * scale).astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# The DOGS block workloads (K uneven blocks over one aerial city scene).
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class DogsWorkload:
+    split: BlockSplit
+    z0: Gaussians                  # global model, numbered as in split
+    views: List[List[Camera]]      # pool entries; each holds per_block views per block, grouped by block
+    gt: Gaussians                  # ground-truth set of the same law (targets are rendered from it)
+
+
+def dogs_workload(n_global: int, cols: int, rows: int, shared_frac: float, seed: int,
+                  views_per_step: int = 1, pool: int = 4, width: int = 1920, height: int = 1080,
+                  pitch_deg: float = 45.0, altitude: float = 120.0, sh_degree: int = 3,
+                  loads: Optional[Sequence[float]] = None) -> DogsWorkload:
+    """City-law scene of n_global Gaussians split on a cols x rows ground
+    grid at load quantiles (Dirichlet(2) from the seed unless given), with
+    shared_frac of the Gaussians on interior borders shared by 2-4 blocks;
+    `pool` steps' worth of aerial views, views_per_step per block each."""
+    K = cols * rows
+    z = city_scene(n_global, seed, sh_degree=sh_degree)
+    if loads is None:
+        loads = dirichlet_loads(seed + 3, K)
+    split, order = block_split(z.means[:, :2], cols, rows, loads, shared_frac)
+    z = z.subset(order)
+    allv = block_views(split, seed + 2, views_per_step * pool, width, height, pitch_deg, altitude)
+    per = views_per_step * pool
+    views = []
+    for p in range(pool):
+        vs = []
+        for k in range(K):
+            vs.extend(allv[k * per + p * views_per_step: k * per + (p + 1) * views_per_step])
+        views.append(vs)
+    gt = city_scene(n_global, seed + 1, sh_degree=sh_degree, layout_seed=seed)
+    return DogsWorkload(split, z, views, gt)

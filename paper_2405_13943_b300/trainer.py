@@ -1,0 +1,243 @@
+"""Batched DOGS training on one GPU (Sec. 3.2, Alg. 2).
+
+All K block-local models live in one set of device buffers; one iteration is
+one launch per hot step over every block at once: dg_project, dg_bin_sort,
+dg_rasterize_fwd, the Eq. 3 loss, dg_rasterize_bwd, the Adam + penalty
+x-step (Eq. 8a / 12a) and, every `intv` iterations, the consensus
+(Eq. 8b-c / 12b-c).  Iterations can be captured in CUDA graphs (one per pool
+entry of views) and replayed.  SequentialTrainer is the plain per-block form:
+K independent single-block models run one after another, the consensus
+gathering their copies into one buffer and scattering the duals back.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import dogs as D
+from . import synth as S
+
+DEFAULT_LR = (1.6e-4, 1e-3, 5e-3, 2.5e-3, 1.25e-4, 5e-2)
+
+
+def gather_copies(z: D.GaussianBuffer, gid: torch.Tensor, ld: Optional[int] = None) -> D.GaussianBuffer:
+    """Copies x_c = z[gid[c]] in the library layout (setup-time data movement)."""
+    n = gid.numel()
+    out = D.GaussianBuffer(n, z.deg, z.data.device, ld)
+    g = gid.long()
+    for f in range(3):
+        src = z.data[4 * f * z.ld:4 * (f + 1) * z.ld].view(z.ld, 4)
+        out.data[4 * f * out.ld:4 * (f + 1) * out.ld].view(out.ld, 4)[:n] = src[g]
+    P = 3 * D.sh_coefs(z.deg)
+    src = z.data[12 * z.ld:].view(P, z.ld)
+    out.data[12 * out.ld:].view(P, out.ld)[:, :n] = src[:, g]
+    return out
+
+
+class DogsTrainer:
+    def __init__(self, split: S.BlockSplit, z0: D.GaussianBuffer, view_sets: Sequence[Sequence[S.Camera]],
+                 targets: Sequence[torch.Tensor], rho=(1e-3,) * 5, lr=DEFAULT_LR, tile=(16, 16),
+                 loss="dssim", w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0), alpha=1.0, intv=100,
+                 capacity: Optional[int] = None, device="cuda"):
+        self.split, self.device = split, device
+        self.rho, self.lr, self.bg, self.alpha, self.intv = list(rho), list(lr), bg, alpha, intv
+        self.loss_kind, self.w_l1, self.w_ssim = loss, w_l1, w_ssim
+        self.gid = torch.from_numpy(split.copy_gid.astype(np.int32)).to(device)
+        self.shared = torch.from_numpy(split.copy_shared()).to(device)
+        self.g_off = torch.from_numpy(split.g_off.astype(np.int64)).to(device)
+        self.g_copies = torch.from_numpy(split.g_copies.astype(np.int32)).to(device)
+        self.z = z0
+        self.x = gather_copies(z0, self.gid)
+        self.grad, self.m, self.v = self.x.like(), self.x.like(), self.x.like()
+        self.u, self.anchor = self.x.like(), self.x.like()
+        D.dg_admm_anchor(self.z, self.u, self.gid, self.shared, self.anchor)
+        self.view_sets = [list(v) for v in view_sets]
+        self.vb = D.ViewBatch(self.view_sets[0], split.blk_off, tile[0], tile[1], device=device,
+                              capacity=capacity, loss_ws=(loss == "dssim"))
+        self.cam_pool = [D.cams_to_device(D.plan_views(vs, split.blk_off, *tile)[0], device) for vs in self.view_sets]
+        self.targets = list(targets)
+        self.dev_step = torch.zeros(1, dtype=torch.int32, device=device)
+        self.host_step = torch.zeros(1, dtype=torch.int32).pin_memory()
+        self.residuals = torch.zeros(10, dtype=torch.float64, device=device)
+        self.t = 0
+        self.graphs = {}
+
+    # ---- capacity -------------------------------------------------------------
+    def calibrate_capacity(self, headroom=1.3) -> int:
+        """Instance count of every pool entry (one synchronising pass each),
+        then a capacity with headroom; buffers are re-allocated once."""
+        mx = 0
+        for p in range(len(self.view_sets)):
+            self.vb.dev_cams.copy_(self.cam_pool[p])
+            D.dg_project(self.x, self.vb)
+            self.vb.status.zero_()
+            D.dg_bin_sort(self.vb)
+            torch.cuda.synchronize()
+            mx = max(mx, int(self.vb.count.item()) & 0xFFFFFFFF)
+        cap = int(mx * headroom) + 4096
+        self.vb.set_capacity(cap)
+        self.graphs.clear()
+        return mx
+
+    # ---- one iteration ----------------------------------------------------------
+    def _loss(self, target):
+        if self.loss_kind == "dssim":
+            D.dg_loss_dssim(self.vb, target, self.w_l1, self.w_ssim)
+        else:
+            D.dg_loss_l1(self.vb, target, self.w_l1)
+
+    def enqueue(self, p: int, consensus: bool, target: Optional[torch.Tensor] = None) -> None:
+        """All launches of one iteration for pool entry p on the current stream.
+        The step counter for Adam's bias correction is read from dev_step."""
+        vb = self.vb
+        vb.dev_cams.copy_(self.cam_pool[p], non_blocking=True)
+        self.dev_step.copy_(self.host_step, non_blocking=True)
+        D.dg_project(self.x, vb)
+        D.dg_bin_sort(vb)
+        D.dg_rasterize_fwd(vb, self.bg)
+        self._loss(self.targets[p] if target is None else target)
+        D.dg_rasterize_bwd(vb, self.x, self.grad, bg=self.bg)
+        D.dg_adam_admm_step(self.x, self.grad, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,
+                            step=1, dev_step=self.dev_step)
+        if consensus:
+            D.dg_admm_consensus(self.x, self.u, self.z, self.anchor, self.g_off, self.g_copies, self.rho,
+                                self.alpha, self.residuals)
+
+    def step(self, consensus: Optional[bool] = None, graph=True) -> None:
+        """Iteration t (0-based) of Alg. 2: local steps, then the consensus
+        when t mod intv == 0 (or as forced by `consensus`)."""
+        p = self.t % len(self.view_sets)
+        c = (self.t % self.intv == 0) if consensus is None else consensus
+        self.host_step[0] = self.t + 1
+        if graph:
+            key = (p, c)
+            if key not in self.graphs:
+                self.graphs[key] = self._capture(p, c)
+            self.graphs[key].replay()
+        else:
+            self.enqueue(p, c)
+        self.t += 1
+
+    def _capture(self, p: int, c: bool) -> torch.cuda.CUDAGraph:
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):       # warm the allocator-free launch path once
+            torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.enqueue(p, c)
+        return g
+
+    def overflowed(self) -> bool:
+        return bool(int(self.vb.status.item()) & L.DG_STATUS_CAPACITY)
+
+
+class SequentialTrainer:
+    """The plain sequential per-block form: K single-block models, each with
+    its own buffers and view batch, stepped one after another without graphs.
+    The consensus gathers every block's copies into one buffer (what the
+    paper's master receives), runs dg_admm_consensus and sends the duals and
+    anchors back."""
+
+    def __init__(self, split: S.BlockSplit, z0: D.GaussianBuffer, view_sets, targets, rho=(1e-3,) * 5,
+                 lr=DEFAULT_LR, tile=(16, 16), loss="dssim", w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0), alpha=1.0,
+                 intv=100, capacity: Optional[int] = None, device="cuda"):
+        self.split, self.device, self.K = split, device, split.K
+        self.rho, self.lr, self.bg, self.alpha, self.intv = list(rho), list(lr), bg, alpha, intv
+        self.loss_kind, self.w_l1, self.w_ssim = loss, w_l1, w_ssim
+        self.z = z0
+        self.gid = torch.from_numpy(split.copy_gid.astype(np.int32)).to(device)
+        self.shared_all = torch.from_numpy(split.copy_shared()).to(device)
+        self.g_off = torch.from_numpy(split.g_off.astype(np.int64)).to(device)
+        self.g_copies = torch.from_numpy(split.g_copies.astype(np.int32)).to(device)
+        self.blocks = []
+        per = len(view_sets[0]) // self.K
+        for k in range(self.K):
+            b, e = int(split.blk_off[k]), int(split.blk_off[k + 1])
+            gid = self.gid[b:e]
+            x = gather_copies(z0, gid)
+            blk = dict(b=b, e=e, x=x, grad=x.like(), m=x.like(), v=x.like(), u=x.like(), anchor=x.like(),
+                       shared=self.shared_all[b:e].contiguous(), gid=gid.contiguous())
+            D.dg_admm_anchor(z0, blk["u"], blk["gid"], blk["shared"], blk["anchor"])
+            vsets = []
+            for vs in view_sets:
+                cams = []
+                for c in vs[k * per:(k + 1) * per]:
+                    cc = S.Camera(**{**c.__dict__, "block": 0})
+                    cams.append(cc)
+                vsets.append(cams)
+            blk["vb"] = D.ViewBatch(vsets[0], [0, e - b], tile[0], tile[1], device=device, capacity=capacity,
+                                    loss_ws=(loss == "dssim"))
+            blk["cam_pool"] = [D.cams_to_device(D.plan_views(vs, [0, e - b], *tile)[0], device) for vs in vsets]
+            blk["targets"] = []
+            for t in targets:
+                # the block's views are a contiguous slice of the batched image layout
+                vb_all_pix = 3 * per * vsets[0][0].width * vsets[0][0].height
+                blk["targets"].append(t[k * vb_all_pix:(k + 1) * vb_all_pix])
+            self.blocks.append(blk)
+        # gather buffers for the consensus (the master's copy of every block)
+        n = split.n_copies
+        self.x_all = D.GaussianBuffer(n, z0.deg, device)
+        self.u_all, self.a_all = self.x_all.like(), self.x_all.like()
+        self.t = 0
+        self.residuals = torch.zeros(10, dtype=torch.float64, device=device)
+
+    def calibrate_capacity(self, headroom=1.3):
+        for blk in self.blocks:
+            vb = blk["vb"]
+            mx = 0
+            for cp in blk["cam_pool"]:
+                vb.dev_cams.copy_(cp)
+                D.dg_project(blk["x"], vb)
+                vb.status.zero_()
+                D.dg_bin_sort(vb)
+                torch.cuda.synchronize()
+                mx = max(mx, int(vb.count.item()) & 0xFFFFFFFF)
+            vb.set_capacity(int(mx * headroom) + 4096)
+
+    def _copy_rows(self, dst: D.GaussianBuffer, src: D.GaussianBuffer, b: int, e: int, to_all: bool):
+        for f in range(3):
+            A = dst.data[4 * f * dst.ld:4 * (f + 1) * dst.ld].view(dst.ld, 4)
+            B = src.data[4 * f * src.ld:4 * (f + 1) * src.ld].view(src.ld, 4)
+            if to_all:
+                A[b:e] = B[:e - b]
+            else:
+                A[:e - b] = B[b:e]
+        P = 3 * D.sh_coefs(dst.deg)
+        A = dst.data[12 * dst.ld:].view(P, dst.ld)
+        B = src.data[12 * src.ld:].view(P, src.ld)
+        if to_all:
+            A[:, b:e] = B[:, :e - b]
+        else:
+            A[:, :e - b] = B[:, b:e]
+
+    def step(self, consensus: Optional[bool] = None) -> None:
+        p = self.t % len(self.blocks[0]["cam_pool"])
+        c = (self.t % self.intv == 0) if consensus is None else consensus
+        for blk in self.blocks:
+            vb = blk["vb"]
+            vb.dev_cams.copy_(blk["cam_pool"][p], non_blocking=True)
+            D.dg_project(blk["x"], vb)
+            D.dg_bin_sort(vb)
+            D.dg_rasterize_fwd(vb, self.bg)
+            if self.loss_kind == "dssim":
+                D.dg_loss_dssim(vb, blk["targets"][p], self.w_l1, self.w_ssim)
+            else:
+                D.dg_loss_l1(vb, blk["targets"][p], self.w_l1)
+            D.dg_rasterize_bwd(vb, blk["x"], blk["grad"], bg=self.bg)
+            D.dg_adam_admm_step(blk["x"], blk["grad"], blk["m"], blk["v"], blk["anchor"], blk["shared"], self.rho,
+                                self.lr, step=self.t + 1)
+        if c:
+            for blk in self.blocks:
+                self._copy_rows(self.x_all, blk["x"], blk["b"], blk["e"], True)
+                self._copy_rows(self.u_all, blk["u"], blk["b"], blk["e"], True)
+            D.dg_admm_consensus(self.x_all, self.u_all, self.z, self.a_all, self.g_off, self.g_copies, self.rho,
+                                self.alpha, self.residuals)
+            for blk in self.blocks:
+                self._copy_rows(blk["u"], self.u_all, blk["b"], blk["e"], False)
+                self._copy_rows(blk["anchor"], self.a_all, blk["b"], blk["e"], False)
+        self.t += 1

@@ -1,0 +1,108 @@
+"""Batched K-block DOGS iterations: the single-launch batched path equals K
+independent per-block runs with a gather/scatter consensus (the paper's
+distributed semantics, Alg. 2, restated on one device), and CUDA-graph
+replays equal eager launches."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2405_13943_b300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-3
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_13943_b300 import build as B
+    B.build()
+    from paper_2405_13943_b300 import dogs, serve, trainer
+    return dogs, serve, trainer
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def small_setup(D, srv, seed=7):
+    wl = S.dogs_workload(40_000, 2, 2, 0.1, seed, views_per_step=1, pool=2, width=200, height=150)
+    z0 = D.GaussianBuffer.from_synth(wl.z0)
+    gt = D.GaussianBuffer.from_synth(wl.gt)
+    targets = [srv.render_views(gt, vs).image.clone() for vs in wl.views]
+    return wl, z0, targets
+
+
+def groups(buf):
+    s = buf.to_synth()
+    return {k: getattr(s, k) for k in ("means", "quats", "log_scales", "sh", "opacity_logits")}
+
+
+def test_batched_equals_sequential_per_block(mods):
+    D, srv, T = mods
+    wl, z0, targets = small_setup(D, srv)
+    kw = dict(rho=(1e-2,) * 5, loss="dssim", intv=2)
+    bt = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, **kw)
+    bt.calibrate_capacity()
+    sq = T.SequentialTrainer(wl.split, z0.clone(), wl.views, targets, **kw)
+    sq.calibrate_capacity()
+    for _ in range(4):                 # consensus at t = 0 and t = 2
+        bt.step(graph=False)
+        sq.step()
+    torch.cuda.synchronize()
+    assert not bt.overflowed()
+    # gather the sequential copies into the batched layout
+    x_seq = bt.x.like()
+    for blk in sq.blocks:
+        sq._copy_rows(x_seq, blk["x"], blk["b"], blk["e"], True)
+    gb, gs = groups(bt.x), groups(x_seq)
+    for k in gb:
+        assert rel_l2(gs[k], gb[k]) < REL_L2, k
+    zb, zs = groups(bt.z), groups(sq.z)
+    for k in zb:
+        assert rel_l2(zs[k], zb[k]) < REL_L2, k
+    # the copies moved away from their start
+    g0 = groups(T.gather_copies(z0, bt.gid))
+    assert rel_l2(gb["means"], g0["means"]) > 0
+
+
+def test_graph_replay_equals_eager(mods):
+    D, srv, T = mods
+    wl, z0, targets = small_setup(D, srv, seed=8)
+    kw = dict(rho=(1e-3,) * 5, loss="l1", intv=3)
+    a = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, **kw)
+    b = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, **kw)
+    a.calibrate_capacity()
+    b.vb.set_capacity(a.vb.capacity)
+    for _ in range(5):
+        a.step(graph=True)
+        b.step(graph=False)
+    torch.cuda.synchronize()
+    ga, gb = groups(a.x), groups(b.x)
+    for k in ga:
+        assert rel_l2(ga[k], gb[k]) < REL_L2, k
+    assert torch.allclose(a.vb.loss, b.vb.loss, rtol=1e-4)
+
+
+def test_consensus_keeps_dual_mean_zero(mods):
+    """After a consensus the duals of every shared global average to zero
+    (Appendix, proof of Eq. 8b), so the complete and simplified z agree."""
+    D, srv, T = mods
+    wl, z0, targets = small_setup(D, srv, seed=9)
+    tr = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, rho=(1e-2,) * 5, loss="l1", intv=1)
+    tr.calibrate_capacity()
+    for _ in range(3):
+        tr.step(graph=False)
+    torch.cuda.synchronize()
+    u = groups(tr.u)["means"].astype(np.float64)
+    x = groups(tr.x)["means"].astype(np.float64)
+    z = groups(tr.z)["means"].astype(np.float64)
+    sp = wl.split
+    cnt = np.diff(sp.g_off)
+    for i in np.nonzero(cnt > 1)[0][:2000]:
+        cp = sp.g_copies[sp.g_off[i]:sp.g_off[i + 1]]
+        assert np.abs(u[cp].mean(0)).max() < 1e-4
+        assert np.abs(z[i] - (x[cp] + 0 * u[cp]).mean(0)).max() < 1e-3 * max(1.0, np.abs(z[i]).max())
