@@ -70,6 +70,10 @@ def test_batched_equals_sequential_per_block(mods):
 
 
 def test_graph_replay_equals_eager(mods):
+    """Graph replays launch exactly the eager sequence: identical images,
+    gradients equal up to the order of the float atomics, and the same
+    losses over several steps.  (Parameters are not compared after many
+    steps: Adam maps noise-level gradient differences to +-lr updates.)"""
     D, srv, T = mods
     wl, z0, targets = small_setup(D, srv, seed=8)
     kw = dict(rho=(1e-3,) * 5, loss="l1", intv=3)
@@ -77,14 +81,20 @@ def test_graph_replay_equals_eager(mods):
     b = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, **kw)
     a.calibrate_capacity()
     b.vb.set_capacity(a.vb.capacity)
-    for _ in range(5):
+    a.step(graph=True)
+    b.step(graph=False)
+    torch.cuda.synchronize()
+    assert torch.equal(a.vb.image, b.vb.image)
+    assert rel_l2(a.grad.data.cpu().numpy(), b.grad.data.cpu().numpy()) < 1e-5
+    la, lb = [], []
+    for _ in range(4):
         a.step(graph=True)
         b.step(graph=False)
+        la.append(a.vb.loss.clone())
+        lb.append(b.vb.loss.clone())
     torch.cuda.synchronize()
-    ga, gb = groups(a.x), groups(b.x)
-    for k in ga:
-        assert rel_l2(ga[k], gb[k]) < REL_L2, k
-    assert torch.allclose(a.vb.loss, b.vb.loss, rtol=1e-4)
+    for x, y in zip(la, lb):
+        assert torch.allclose(x, y, rtol=1e-4)
 
 
 def test_consensus_keeps_dual_mean_zero(mods):
