@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "small"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "small"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-seq", action="store_true")
@@ -56,6 +56,8 @@ def parse():
 WORKLOADS = {
     "large": dict(n_global=6_000_000, cols=2, rows=4, shared=0.10, seed=1004, width=1920, height=1080, pool=4),
     "small": dict(n_global=200_000, cols=2, rows=2, shared=0.05, seed=1003, width=640, height=480, pool=2),
+    # same law and views as "large" at 1/6 of the Gaussians: a profiling case of a few GB, above L2
+    "medium": dict(n_global=1_000_000, cols=2, rows=4, shared=0.10, seed=1004, width=1920, height=1080, pool=2),
 }
 
 
@@ -223,9 +225,12 @@ def run_ours(args, dist, rank, world):
     if tr.overflowed():
         raise RuntimeError("instance capacity overflow during warmup")
     if args.profile:
+        # two eager iterations inside an NVTX range "dogs_step" (ncu --nvtx-include dogs_step/)
+        torch.cuda.nvtx.range_push("dogs_step")
         for _ in range(2):
             tr.step(consensus=True, graph=False)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         if rank == 0:
             print(json.dumps({"profile_run": True, "instances": m_max}))
         return
