@@ -27,69 +27,83 @@ __device__ __forceinline__ void adam1(float& x, float g, float& m, float& v, flo
     x -= lr * (m / c1) / (sqrtf(v / c2) + eps);
 }
 
+// One thread per group of four consecutive copies: the three float4 fields of
+// each of the four copies, then one float4 (the four copies) of every SH
+// plane.  Each warp reads 2 KB contiguous per field and 512 B per plane; no
+// index arithmetic beyond additions.
+__device__ __forceinline__ void adam_unit(float4* __restrict__ x, const float4* __restrict__ g,
+                                          float4* __restrict__ m, float4* __restrict__ v,
+                                          const float4* __restrict__ anchor, int64_t u, const float* rho,
+                                          const float* lr, const bool* act, const bool* sh, const AdamArgs& a,
+                                          float c1, float c2)
+{
+    float4 xv = x[u], gv = g[u], mv = m[u], vv = v[u];
+    float xs[4] = {xv.x, xv.y, xv.z, xv.w}, gs[4] = {gv.x, gv.y, gv.z, gv.w};
+    float ms[4] = {mv.x, mv.y, mv.z, mv.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
+    if (sh[0] || sh[1] || sh[2] || sh[3]) {
+        float4 av = anchor[u];
+        float as[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            if (sh[i]) gs[i] += rho[i] * (xs[i] - as[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        if (act[i]) adam1(xs[i], gs[i], ms[i], vs[i], lr[i], a.b1, a.b2, a.eps, c1, c2);
+    x[u] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+    m[u] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+    v[u] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+}
+
 __global__ void __launch_bounds__(256) k_adam_admm(float4* __restrict__ x, const float4* __restrict__ g,
                                                    float4* __restrict__ m, float4* __restrict__ v,
                                                    const float4* __restrict__ anchor,
                                                    const uint8_t* __restrict__ shared, int64_t n, int64_t ld,
-                                                   int64_t units, AdamArgs a, const int32_t* __restrict__ dev_step)
+                                                   int n_planes, AdamArgs a, const int32_t* __restrict__ dev_step)
 {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // copies 4q .. 4q+3
+    int64_t c0 = 4 * q;
+    if (c0 >= n) return;
     float t = (float)(dev_step ? *dev_step : a.step);
     float c1 = 1.f - powf(a.b1, t), c2 = 1.f - powf(a.b2, t);
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool ok[4], shr[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        ok[i] = c0 + i < n;
+        shr[i] = ok[i] && shared && shared[c0 + i];
+    }
+    // float4 fields: one unit per copy
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if (!ok[i]) continue;
+        int64_t c = c0 + i;
+        bool sh4[4] = {shr[i], shr[i], shr[i], shr[i]};
+        {   // mean (p) and opacity (o)
+            float rho[4] = {a.rho[0], a.rho[0], a.rho[0], a.rho[4]};
+            float lr[4] = {a.lr[0], a.lr[0], a.lr[0], a.lr[5]};
+            bool act[4] = {true, true, true, true};
+            adam_unit(x, g, m, v, anchor, c, rho, lr, act, sh4, a, c1, c2);
+        }
+        {   // rotation (q)
+            float rho[4] = {a.rho[1], a.rho[1], a.rho[1], a.rho[1]};
+            float lr[4] = {a.lr[1], a.lr[1], a.lr[1], a.lr[1]};
+            bool act[4] = {true, true, true, true};
+            adam_unit(x, g, m, v, anchor, ld + c, rho, lr, act, sh4, a, c1, c2);
+        }
+        {   // scale (s); the fourth lane is padding
+            float rho[4] = {a.rho[2], a.rho[2], a.rho[2], a.rho[2]};
+            float lr[4] = {a.lr[2], a.lr[2], a.lr[2], a.lr[2]};
+            bool act[4] = {true, true, true, false};
+            adam_unit(x, g, m, v, anchor, 2 * ld + c, rho, lr, act, sh4, a, c1, c2);
+        }
+    }
+    // SH planes (f): one unit holds the four copies
     int64_t q4 = ld >> 2;
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += stride) {
-        // which field, which copies, which group / learning rate per lane
-        int64_t c0;
-        int field;              // 0 mean+opacity, 1 rotation, 2 scale, 3 SH plane
-        int plane = 0;
-        if (u < 3 * ld) { field = (int)(u / ld); c0 = u - field * ld; }
-        else { int64_t s = u - 3 * ld; plane = (int)(s / q4); c0 = 4 * (s - plane * q4); field = 3; }
-        float rho[4], lr[4];
-        bool act[4], sh[4];
-        if (field == 0) {
-            rho[0] = rho[1] = rho[2] = a.rho[0]; rho[3] = a.rho[4];
-            lr[0] = lr[1] = lr[2] = a.lr[0]; lr[3] = a.lr[5];
-            bool ok = c0 < n, s = ok && shared[c0];
-            act[0] = act[1] = act[2] = act[3] = ok;
-            sh[0] = sh[1] = sh[2] = sh[3] = s;
-        } else if (field == 1) {
-            rho[0] = rho[1] = rho[2] = rho[3] = a.rho[1];
-            lr[0] = lr[1] = lr[2] = lr[3] = a.lr[1];
-            bool ok = c0 < n, s = ok && shared[c0];
-            act[0] = act[1] = act[2] = act[3] = ok;
-            sh[0] = sh[1] = sh[2] = sh[3] = s;
-        } else if (field == 2) {
-            rho[0] = rho[1] = rho[2] = rho[3] = a.rho[2];
-            lr[0] = lr[1] = lr[2] = lr[3] = a.lr[2];
-            bool ok = c0 < n, s = ok && shared[c0];
-            act[0] = act[1] = act[2] = ok; act[3] = false;     // padding lane
-            sh[0] = sh[1] = sh[2] = sh[3] = s;
-        } else {
-            float l = plane < 3 ? a.lr[3] : a.lr[4];
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                rho[i] = a.rho[3]; lr[i] = l;
-                act[i] = c0 + i < n;
-                sh[i] = act[i] && shared[c0 + i];
-            }
-        }
-        if (!(act[0] || act[1] || act[2] || act[3])) continue;
-        float4 xv = x[u], gv = g[u], mv = m[u], vv = v[u];
-        float xs[4] = {xv.x, xv.y, xv.z, xv.w}, gs[4] = {gv.x, gv.y, gv.z, gv.w};
-        float ms[4] = {mv.x, mv.y, mv.z, mv.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
-        if (sh[0] || sh[1] || sh[2] || sh[3]) {
-            float4 av = anchor[u];
-            float as[4] = {av.x, av.y, av.z, av.w};
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-                if (sh[i]) gs[i] += rho[i] * (xs[i] - as[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-            if (act[i]) adam1(xs[i], gs[i], ms[i], vs[i], lr[i], a.b1, a.b2, a.eps, c1, c2);
-        x[u] = make_float4(xs[0], xs[1], xs[2], xs[3]);
-        m[u] = make_float4(ms[0], ms[1], ms[2], ms[3]);
-        v[u] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+    float rho[4] = {a.rho[3], a.rho[3], a.rho[3], a.rho[3]};
+    for (int p = 0; p < n_planes; p++) {
+        float l = p < 3 ? a.lr[3] : a.lr[4];
+        float lr[4] = {l, l, l, l};
+        adam_unit(x, g, m, v, anchor, 3 * ld + (int64_t)p * q4 + q, rho, lr, ok, shr, a, c1, c2);
     }
 }
 
@@ -220,14 +234,12 @@ int launch_adam_admm(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m, dg
     for (int i = 0; i < 5; i++) a.rho[i] = rho[i];
     for (int i = 0; i < 6; i++) a.lr[i] = lr[i];
     a.b1 = b1; a.b2 = b2; a.eps = eps; a.step = step;
-    int64_t units = (12 + 3 * (int64_t)sh_coefs(x->sh_degree)) * x->ld / 4;
-    int64_t blocks = (units + 255) / 256;
-    if (blocks > 148 * 64) blocks = 148 * 64;
+    int64_t groups = (x->n + 3) / 4;
     const float4* an = anchor ? reinterpret_cast<const float4*>(anchor->data) : nullptr;
-    k_adam_admm<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<float4*>(x->data),
-                                                 reinterpret_cast<const float4*>(g->data),
-                                                 reinterpret_cast<float4*>(m->data), reinterpret_cast<float4*>(v->data),
-                                                 an, shared, x->n, x->ld, units, a, dev_step);
+    k_adam_admm<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(
+        reinterpret_cast<float4*>(x->data), reinterpret_cast<const float4*>(g->data),
+        reinterpret_cast<float4*>(m->data), reinterpret_cast<float4*>(v->data), an, shared, x->n, x->ld,
+        3 * sh_coefs(x->sh_degree), a, dev_step);
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;
