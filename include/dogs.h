@@ -43,6 +43,7 @@ extern "C" {
 #define DG_ERR_WORKSPACE (-2) /* workspace smaller than the matching *_workspace_size */
 #define DG_ERR_CAPACITY (-3)  /* reserved: host-visible capacity failure */
 #define DG_ERR_CUDA (-4)      /* a CUDA launch or memset failed */
+#define DG_ERR_TOO_LARGE (-6) /* sizes beyond the fixed limits of dg_bin_sort_noalloc */
 
 /* bits OR-ed into *dev_status by device code */
 #define DG_STATUS_CAPACITY 1u /* tile instances exceed `capacity`; ranges were emptied */
@@ -145,6 +146,26 @@ int dg_bin_sort(const float* rec, const uint32_t* rect, const dg_camera* dev_cam
                 const dg_plan* plan, int64_t capacity, uint64_t* keys, uint32_t* vals,
                 uint32_t* ranges, uint32_t* dev_count, void* ws, size_t ws_bytes,
                 uint32_t* dev_status, void* stream);
+
+/* ---- binning without caller-provided scratch ------------------------------ */
+/* The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory when they bin, e.g. a plugin inside an
+ * application whose allocator owns the device's memory, or a latency-bound
+ * loop that must not pay cudaMalloc's implicit synchronisation.  Same inputs,
+ * outputs and results as dg_bin_sort, but the scratch comes from a static
+ * device array of 40 MiB that the library reserves on every GPU that loads it,
+ * for the life of the process.  Limits: plan->n_tiles <= DG_NOALLOC_MAX_TILES
+ * and capacity <= DG_NOALLOC_MAX_INSTANCES, else DG_ERR_TOO_LARGE before any
+ * launch.  The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  Every call shares the array: calls whose work overlaps
+ * on the GPU (unordered streams, concurrent host threads) race and give wrong
+ * results; serialise them.  Allocates and frees nothing. */
+#define DG_NOALLOC_MAX_TILES 262144
+#define DG_NOALLOC_MAX_INSTANCES 4194304
+int dg_bin_sort_noalloc(const float* rec, const uint32_t* rect, const dg_camera* dev_cams,
+                        const dg_plan* plan, int64_t capacity, uint64_t* keys, uint32_t* vals,
+                        uint32_t* ranges, uint32_t* dev_count, uint32_t* dev_status, void* stream);
 
 /* ---- compositing (K5) ------------------------------------------------------ */
 /* Eq. 2 front to back per pixel over its tile's instances: alpha =

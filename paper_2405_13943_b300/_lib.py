@@ -16,12 +16,15 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdogs.so")
 
 DG_OK, DG_ERR_INVALID, DG_ERR_WORKSPACE, DG_ERR_CAPACITY, DG_ERR_CUDA = 0, -1, -2, -3, -4
+DG_ERR_TOO_LARGE = -6
+DG_NOALLOC_MAX_TILES, DG_NOALLOC_MAX_INSTANCES = 262144, 4194304
 DG_STATUS_CAPACITY = 1
 DG_MAX_BLOCKS = 64
 DG_MAX_VIEWS = 4096
 
 _ERR = {DG_ERR_INVALID: "invalid argument", DG_ERR_WORKSPACE: "workspace too small",
-        DG_ERR_CAPACITY: "capacity", DG_ERR_CUDA: "CUDA launch failed"}
+        DG_ERR_CAPACITY: "capacity", DG_ERR_CUDA: "CUDA launch failed",
+        DG_ERR_TOO_LARGE: "beyond the fixed limits of the allocation-free entry point"}
 
 
 class DogsError(RuntimeError):
@@ -63,6 +66,7 @@ _SIGS = {
     "dg_bin_sort_workspace_size": (C.c_size_t, [C.POINTER(DgPlan), C.c_int64]),
     "dg_bin_sort": (C.c_int, [_vp, _vp, _vp, C.POINTER(DgPlan), C.c_int64, _vp, _vp, _vp, _vp, _vp, C.c_size_t,
                               _vp, _vp]),
+    "dg_bin_sort_noalloc": (C.c_int, [_vp, _vp, _vp, C.POINTER(DgPlan), C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "dg_rasterize_fwd": (C.c_int, [_vp, _vp, _vp, _vp, C.POINTER(DgPlan), C.POINTER(C.c_float), _vp, _vp, _vp, _vp]),
     "dg_loss_l1": (C.c_int, [_vp, _vp, _vp, C.POINTER(DgPlan), C.c_float, _vp, _vp, _vp]),
     "dg_loss_workspace_size": (C.c_size_t, [C.POINTER(DgPlan)]),
