@@ -19,23 +19,15 @@ struct AdamArgs {
     int step;
 };
 
-__device__ __forceinline__ void adam1(float& x, float g, float& m, float& v, float lr, float b1, float b2,
-                                      float eps, float c1, float c2)
-{
-    m = b1 * m + (1.f - b1) * g;
-    v = b2 * v + (1.f - b2) * g * g;
-    x -= lr * (m / c1) / (sqrtf(v / c2) + eps);
-}
-
-// One thread per group of four consecutive copies: the three float4 fields of
-// each of the four copies, then one float4 (the four copies) of every SH
-// plane.  Each warp reads 2 KB contiguous per field and 512 B per plane; no
-// index arithmetic beyond additions.
+// The x-step runs as two launches with contiguous warp accesses and no
+// per-element index division: the float4 fields (four copies per thread,
+// copies strided by the CTA width) and the SH planes (a 2D grid of quads of
+// copies x planes, four quads per thread).
 __device__ __forceinline__ void adam_unit(float4* __restrict__ x, const float4* __restrict__ g,
                                           float4* __restrict__ m, float4* __restrict__ v,
                                           const float4* __restrict__ anchor, int64_t u, const float* rho,
-                                          const float* lr, const bool* act, const bool* sh, const AdamArgs& a,
-                                          float c1, float c2)
+                                          const float* lr, const bool* act, const bool* sh, float b1, float b2,
+                                          float eps, float ic1, float ic2)
 {
     float4 xv = x[u], gv = g[u], mv = m[u], vv = v[u];
     float xs[4] = {xv.x, xv.y, xv.z, xv.w}, gs[4] = {gv.x, gv.y, gv.z, gv.w};
@@ -48,62 +40,81 @@ __device__ __forceinline__ void adam_unit(float4* __restrict__ x, const float4* 
             if (sh[i]) gs[i] += rho[i] * (xs[i] - as[i]);
     }
 #pragma unroll
-    for (int i = 0; i < 4; i++)
-        if (act[i]) adam1(xs[i], gs[i], ms[i], vs[i], lr[i], a.b1, a.b2, a.eps, c1, c2);
+    for (int i = 0; i < 4; i++) {
+        if (!act[i]) continue;
+        ms[i] = b1 * ms[i] + (1.f - b1) * gs[i];
+        vs[i] = b2 * vs[i] + (1.f - b2) * gs[i] * gs[i];
+        xs[i] -= lr[i] * __fdividef(ms[i] * ic1, sqrtf(vs[i] * ic2) + eps);
+    }
     x[u] = make_float4(xs[0], xs[1], xs[2], xs[3]);
     m[u] = make_float4(ms[0], ms[1], ms[2], ms[3]);
     v[u] = make_float4(vs[0], vs[1], vs[2], vs[3]);
 }
 
-__global__ void __launch_bounds__(256) k_adam_admm(float4* __restrict__ x, const float4* __restrict__ g,
-                                                   float4* __restrict__ m, float4* __restrict__ v,
-                                                   const float4* __restrict__ anchor,
-                                                   const uint8_t* __restrict__ shared, int64_t n, int64_t ld,
-                                                   int n_planes, AdamArgs a, const int32_t* __restrict__ dev_step)
+__device__ __forceinline__ void bias_corr(const AdamArgs& a, const int32_t* dev_step, float& ic1, float& ic2)
 {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // copies 4q .. 4q+3
-    int64_t c0 = 4 * q;
-    if (c0 >= n) return;
     float t = (float)(dev_step ? *dev_step : a.step);
-    float c1 = 1.f - powf(a.b1, t), c2 = 1.f - powf(a.b2, t);
-    bool ok[4], shr[4];
+    ic1 = 1.f / (1.f - powf(a.b1, t));
+    ic2 = 1.f / (1.f - powf(a.b2, t));
+}
+
+constexpr int kAdamThreads = 256, kAdamPer = 4;
+
+__global__ void __launch_bounds__(kAdamThreads) k_adam_fields(float4* __restrict__ x, const float4* __restrict__ g,
+                                                              float4* __restrict__ m, float4* __restrict__ v,
+                                                              const float4* __restrict__ anchor,
+                                                              const uint8_t* __restrict__ shared, int64_t n,
+                                                              int64_t ld, AdamArgs a, const int32_t* __restrict__ dev_step)
+{
+    float ic1, ic2;
+    bias_corr(a, dev_step, ic1, ic2);
+    const float rho0[4] = {a.rho[0], a.rho[0], a.rho[0], a.rho[4]}, lr0[4] = {a.lr[0], a.lr[0], a.lr[0], a.lr[5]};
+    const float rho1[4] = {a.rho[1], a.rho[1], a.rho[1], a.rho[1]}, lr1[4] = {a.lr[1], a.lr[1], a.lr[1], a.lr[1]};
+    const float rho2[4] = {a.rho[2], a.rho[2], a.rho[2], a.rho[2]}, lr2[4] = {a.lr[2], a.lr[2], a.lr[2], a.lr[2]};
+    const bool all4[4] = {true, true, true, true}, three[4] = {true, true, true, false};
+    int64_t base = (int64_t)blockIdx.x * (kAdamThreads * kAdamPer) + threadIdx.x;
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        ok[i] = c0 + i < n;
-        shr[i] = ok[i] && shared && shared[c0 + i];
+    for (int i = 0; i < kAdamPer; i++) {
+        int64_t c = base + i * kAdamThreads;
+        if (c >= n) break;
+        bool s = shared && shared[c];
+        bool s4[4] = {s, s, s, s};
+        adam_unit(x, g, m, v, anchor, c, rho0, lr0, all4, s4, a.b1, a.b2, a.eps, ic1, ic2);          // p, o
+        adam_unit(x, g, m, v, anchor, ld + c, rho1, lr1, all4, s4, a.b1, a.b2, a.eps, ic1, ic2);     // q
+        adam_unit(x, g, m, v, anchor, 2 * ld + c, rho2, lr2, three, s4, a.b1, a.b2, a.eps, ic1, ic2); // s (+pad)
     }
-    // float4 fields: one unit per copy
+}
+
+__global__ void __launch_bounds__(kAdamThreads) k_adam_planes(float4* __restrict__ x, const float4* __restrict__ g,
+                                                              float4* __restrict__ m, float4* __restrict__ v,
+                                                              const float4* __restrict__ anchor,
+                                                              const uint8_t* __restrict__ shared, int64_t n,
+                                                              int64_t ld, AdamArgs a, const int32_t* __restrict__ dev_step)
+{
+    float ic1, ic2;
+    bias_corr(a, dev_step, ic1, ic2);
+    const int p = blockIdx.y;
+    const float l = p < 3 ? a.lr[3] : a.lr[4];
+    const float rho[4] = {a.rho[3], a.rho[3], a.rho[3], a.rho[3]}, lr[4] = {l, l, l, l};
+    const int64_t q4 = ld >> 2;
+    const int64_t row = 3 * ld + (int64_t)p * q4;
+    int64_t base = (int64_t)blockIdx.x * (kAdamThreads * kAdamPer) + threadIdx.x;
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        if (!ok[i]) continue;
-        int64_t c = c0 + i;
-        bool sh4[4] = {shr[i], shr[i], shr[i], shr[i]};
-        {   // mean (p) and opacity (o)
-            float rho[4] = {a.rho[0], a.rho[0], a.rho[0], a.rho[4]};
-            float lr[4] = {a.lr[0], a.lr[0], a.lr[0], a.lr[5]};
-            bool act[4] = {true, true, true, true};
-            adam_unit(x, g, m, v, anchor, c, rho, lr, act, sh4, a, c1, c2);
+    for (int i = 0; i < kAdamPer; i++) {
+        int64_t q = base + i * kAdamThreads;
+        int64_t c0 = 4 * q;
+        if (c0 >= n) break;
+        bool act[4], sh[4];
+        uchar4 f = shared && c0 + 3 < n ? *reinterpret_cast<const uchar4*>(shared + c0) : make_uchar4(0, 0, 0, 0);
+#pragma unroll
+        for (int k = 0; k < 4; k++) act[k] = c0 + k < n;
+        if (shared && c0 + 3 >= n) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) sh[k] = act[k] && shared[c0 + k];
+        } else {
+            sh[0] = f.x; sh[1] = f.y; sh[2] = f.z; sh[3] = f.w;
         }
-        {   // rotation (q)
-            float rho[4] = {a.rho[1], a.rho[1], a.rho[1], a.rho[1]};
-            float lr[4] = {a.lr[1], a.lr[1], a.lr[1], a.lr[1]};
-            bool act[4] = {true, true, true, true};
-            adam_unit(x, g, m, v, anchor, ld + c, rho, lr, act, sh4, a, c1, c2);
-        }
-        {   // scale (s); the fourth lane is padding
-            float rho[4] = {a.rho[2], a.rho[2], a.rho[2], a.rho[2]};
-            float lr[4] = {a.lr[2], a.lr[2], a.lr[2], a.lr[2]};
-            bool act[4] = {true, true, true, false};
-            adam_unit(x, g, m, v, anchor, 2 * ld + c, rho, lr, act, sh4, a, c1, c2);
-        }
-    }
-    // SH planes (f): one unit holds the four copies
-    int64_t q4 = ld >> 2;
-    float rho[4] = {a.rho[3], a.rho[3], a.rho[3], a.rho[3]};
-    for (int p = 0; p < n_planes; p++) {
-        float l = p < 3 ? a.lr[3] : a.lr[4];
-        float lr[4] = {l, l, l, l};
-        adam_unit(x, g, m, v, anchor, 3 * ld + (int64_t)p * q4 + q, rho, lr, ok, shr, a, c1, c2);
+        adam_unit(x, g, m, v, anchor, row + q, rho, lr, act, sh, a.b1, a.b2, a.eps, ic1, ic2);
     }
 }
 
@@ -234,13 +245,17 @@ int launch_adam_admm(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m, dg
     for (int i = 0; i < 5; i++) a.rho[i] = rho[i];
     for (int i = 0; i < 6; i++) a.lr[i] = lr[i];
     a.b1 = b1; a.b2 = b2; a.eps = eps; a.step = step;
-    int64_t groups = (x->n + 3) / 4;
     const float4* an = anchor ? reinterpret_cast<const float4*>(anchor->data) : nullptr;
-    k_adam_admm<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(
-        reinterpret_cast<float4*>(x->data), reinterpret_cast<const float4*>(g->data),
-        reinterpret_cast<float4*>(m->data), reinterpret_cast<float4*>(v->data), an, shared, x->n, x->ld,
-        3 * sh_coefs(x->sh_degree), a, dev_step);
-    note_launch();
+    float4* X = reinterpret_cast<float4*>(x->data);
+    const float4* G = reinterpret_cast<const float4*>(g->data);
+    float4* M = reinterpret_cast<float4*>(m->data);
+    float4* V = reinterpret_cast<float4*>(v->data);
+    const int64_t per = kAdamThreads * kAdamPer;
+    k_adam_fields<<<(unsigned)((x->n + per - 1) / per), kAdamThreads, 0, st>>>(X, G, M, V, an, shared, x->n, x->ld,
+                                                                               a, dev_step);
+    dim3 grid((unsigned)(((x->n + 3) / 4 + per - 1) / per), (unsigned)(3 * sh_coefs(x->sh_degree)));
+    k_adam_planes<<<grid, kAdamThreads, 0, st>>>(X, G, M, V, an, shared, x->n, x->ld, a, dev_step);
+    note_launch(2);
     DG_CHECK_LAUNCH();
     return DG_OK;
 }
