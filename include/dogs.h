@@ -26,6 +26,11 @@
  *     into the caller's device word `dev_status` (DG_STATUS_* bits), to be
  *     read after the stream is synchronised.
  *   - n = 0 Gaussians is valid and renders the background.
+ *   - Alignment (checked on the host, DG_ERR_INVALID otherwise): parameter
+ *     buffers and projected records 16 bytes; tile rectangles, keys, camera
+ *     tables, int64 and double arrays 8 bytes; int32 arrays 4 bytes; the
+ *     bin-sort and render workspaces 256 bytes.  Byte arrays (copy_shared)
+ *     need none.
  */
 #ifndef DOGS_H
 #define DOGS_H

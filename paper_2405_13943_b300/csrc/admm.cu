@@ -105,14 +105,11 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam_planes(float4* __restrict
         int64_t c0 = 4 * q;
         if (c0 >= n) break;
         bool act[4], sh[4];
-        uchar4 f = shared && c0 + 3 < n ? *reinterpret_cast<const uchar4*>(shared + c0) : make_uchar4(0, 0, 0, 0);
+        // byte loads: copy_shared carries no alignment guarantee
 #pragma unroll
-        for (int k = 0; k < 4; k++) act[k] = c0 + k < n;
-        if (shared && c0 + 3 >= n) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) sh[k] = act[k] && shared[c0 + k];
-        } else {
-            sh[0] = f.x; sh[1] = f.y; sh[2] = f.z; sh[3] = f.w;
+        for (int k = 0; k < 4; k++) {
+            act[k] = c0 + k < n;
+            sh[k] = act[k] && shared && shared[c0 + k];
         }
         adam_unit(x, g, m, v, anchor, row + q, rho, lr, act, sh, a.b1, a.b2, a.eps, ic1, ic2);
     }

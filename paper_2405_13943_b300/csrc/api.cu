@@ -35,6 +35,7 @@ int launch_anchor(const dg_gaussians*, const dg_gaussians*, const int32_t*, cons
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+static bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
 static bool valid_gauss(const dg_gaussians* g)
 {
@@ -145,7 +146,8 @@ int dg_project(const dg_gaussians* x, const dg_camera* dev_cams, const dg_plan* 
 {
     if (!valid_gauss(x) || !valid_plan(plan)) return DG_ERR_INVALID;
     if (plan->blk_off[plan->n_blocks] > x->n) return DG_ERR_INVALID;
-    if (plan->n_rec > 0 && (!dev_cams || !rec || !rect || !aligned16(rec))) return DG_ERR_INVALID;
+    if (plan->n_rec > 0 && (!dev_cams || !rec || !rect || !aligned16(rec) || !aligned8(rect) || !aligned8(dev_cams)))
+        return DG_ERR_INVALID;
     return launch_project(x, dev_cams, *plan, (float4*)rec, (uint2*)rect, (cudaStream_t)stream);
 }
 
@@ -163,6 +165,8 @@ int dg_bin_sort(const float* rec, const uint32_t* rect, const dg_camera* dev_cam
     if (plan->n_tiles == 0) return DG_OK;
     if (!dev_cams || !ranges || !dev_count || !dev_status || !ws || !vals) return DG_ERR_INVALID;
     if (plan->n_rec > 0 && (!rec || !rect)) return DG_ERR_INVALID;
+    if (!aligned16(rec) || !aligned8(rect) || !aligned8(dev_cams) || !aligned8(keys) || ((uintptr_t)ws & 255u))
+        return DG_ERR_INVALID;
     if (ws_bytes < bin_sort_ws_bytes(plan->n_tiles, capacity)) return DG_ERR_WORKSPACE;
     int rc = ensure_init();
     if (rc != DG_OK) return rc;
@@ -176,6 +180,7 @@ int dg_rasterize_fwd(const float* rec, const uint32_t* vals, const uint32_t* ran
     if (!valid_plan(plan) || !bg) return DG_ERR_INVALID;
     if (plan->n_tiles == 0) return DG_OK;
     if (!dev_cams || !ranges || !vals || !image || !T_final || !last) return DG_ERR_INVALID;
+    if (!aligned16(rec) || !aligned8(dev_cams)) return DG_ERR_INVALID;
     return launch_raster_fwd((const float4*)rec, vals, ranges, dev_cams, *plan, bg, image, T_final, last,
                              (cudaStream_t)stream);
 }
@@ -185,6 +190,7 @@ int dg_loss_l1(const float* image, const float* target, const dg_camera* dev_cam
 {
     if (!valid_plan(plan) || plan->n_views == 0) return DG_ERR_INVALID;
     if (!image || !target || !dev_cams || !loss || !dL_dimage) return DG_ERR_INVALID;
+    if (!aligned8(dev_cams) || !aligned8(loss)) return DG_ERR_INVALID;
     return launch_loss(image, target, dev_cams, *plan, w_l1, 0.f, loss, dL_dimage, nullptr, (cudaStream_t)stream);
 }
 
@@ -199,6 +205,7 @@ int dg_loss_dssim(const float* image, const float* target, const dg_camera* dev_
 {
     if (!valid_plan(plan) || plan->n_views == 0) return DG_ERR_INVALID;
     if (!image || !target || !dev_cams || !loss || !dL_dimage) return DG_ERR_INVALID;
+    if (!aligned8(dev_cams) || !aligned8(loss) || ((uintptr_t)ws & 7u)) return DG_ERR_INVALID;
     if (w_ssim != 0.f && (!ws || ws_bytes < loss_ws_bytes(*plan))) return DG_ERR_WORKSPACE;
     return launch_loss(image, target, dev_cams, *plan, w_l1, w_ssim, loss, dL_dimage, ws, (cudaStream_t)stream);
 }
@@ -215,6 +222,7 @@ int dg_rasterize_bwd(const float* rec, const uint32_t* rect, const uint32_t* val
     if (plan->n_rec > 0) {
         if (!rec || !rect || !vals || !ranges || !dev_cams || !T_final || !last || !dL_dimage || !drec)
             return DG_ERR_INVALID;
+        if (!aligned16(rec) || !aligned8(rect) || !aligned8(dev_cams) || !aligned16(drec)) return DG_ERR_INVALID;
         if (cudaMemsetAsync(drec, 0, (size_t)plan->n_rec * 12 * sizeof(float), st) != cudaSuccess) return DG_ERR_CUDA;
         int rc = launch_raster_bwd((const float4*)rec, vals, ranges, dev_cams, *plan, bg, T_final, last, dL_dimage,
                                    drec, st);
@@ -235,6 +243,7 @@ int dg_adam_admm_step(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m, d
     if (!same_layout(x, g) || !same_layout(x, m) || !same_layout(x, v)) return DG_ERR_INVALID;
     if (anchor && (!valid_gauss(anchor) || !same_layout(x, anchor))) return DG_ERR_INVALID;
     if (!rho || !lr || (!dev_step && step < 1)) return DG_ERR_INVALID;
+    if ((uintptr_t)dev_step & 3u) return DG_ERR_INVALID;
     if (x->n > 0 && anchor && !copy_shared) return DG_ERR_INVALID;
     return launch_adam_admm(x, g, m, v, anchor, anchor ? copy_shared : nullptr, rho, lr, beta1, beta2, eps, step,
                             dev_step, (cudaStream_t)stream);
@@ -248,6 +257,7 @@ int dg_admm_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z, d
     if (!same_layout(x, u) || !same_layout(x, anchor) || z->sh_degree != x->sh_degree) return DG_ERR_INVALID;
     if (!rho || !(alpha > 0.f && alpha < 2.f)) return DG_ERR_INVALID;
     if (z->n > 0 && (!g_off || !g_copies)) return DG_ERR_INVALID;
+    if (!aligned8(g_off) || ((uintptr_t)g_copies & 3u) || !aligned8(residuals)) return DG_ERR_INVALID;
     return launch_consensus(x, u, z, anchor, g_off, g_copies, rho, alpha, residuals, (cudaStream_t)stream);
 }
 
@@ -257,6 +267,7 @@ int dg_admm_anchor(const dg_gaussians* z, const dg_gaussians* u, const int32_t* 
     if (!valid_gauss(z) || !valid_gauss(u) || !valid_gauss(anchor) || !same_layout(u, anchor)) return DG_ERR_INVALID;
     if (z->sh_degree != u->sh_degree) return DG_ERR_INVALID;
     if (u->n > 0 && (!copy_gid || !copy_shared)) return DG_ERR_INVALID;
+    if ((uintptr_t)copy_gid & 3u) return DG_ERR_INVALID;
     return launch_anchor(z, u, copy_gid, copy_shared, anchor, (cudaStream_t)stream);
 }
 
@@ -310,6 +321,7 @@ int dg_render(const dg_gaussians* z, const dg_camera* dev_cams, const dg_plan* p
         return DG_ERR_INVALID;
     if (plan->n_tiles == 0) return DG_OK;
     if (!dev_cams || !image || !ws || !dev_count || !dev_status) return DG_ERR_INVALID;
+    if (!aligned8(dev_cams) || ((uintptr_t)ws & 255u)) return DG_ERR_INVALID;
     if (capacity < 0 || capacity >= (int64_t)0xFFFFFFFFll) return DG_ERR_INVALID;
     if (ws_bytes < render_ws_layout(*plan, capacity, nullptr, nullptr)) return DG_ERR_WORKSPACE;
     RenderWs w;

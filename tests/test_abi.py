@@ -103,3 +103,18 @@ def test_calls_reject_null_arguments_without_touching_the_gpu(lib):
     assert lib.dg_project(C.byref(g), None, C.byref(plan), None, None, None) == L.DG_ERR_INVALID
     assert lib.dg_gaussian_floats(64, 3) == 60 * 64
     assert lib.dg_gaussian_floats(64, 4) == -1
+
+
+def test_misaligned_pointers_are_rejected_before_launch(lib):
+    """Vector-accessed buffers must carry their alignment; a violation is an
+    argument error found on the host, never a device fault."""
+    from paper_2405_13943_b300 import dogs as D
+    arr, plan = D.plan_views([S.cube_camera(32, 32)], [0, 64], 16, 16)
+    g = L.DgGaussians(0x10000, 64, 64, 0, 0)
+    assert lib.dg_project(C.byref(g), 0x20000, C.byref(plan), 0x30008, 0x40000, None) == L.DG_ERR_INVALID
+    assert lib.dg_project(C.byref(g), 0x20000, C.byref(plan), 0x30000, 0x40004, None) == L.DG_ERR_INVALID
+    x = L.DgGaussians(0x10000, 64, 64, 0, 0)
+    rho = L.floats([1] * 5)
+    lr = L.floats([1] * 6)
+    assert lib.dg_adam_admm_step(C.byref(x), C.byref(x), C.byref(x), C.byref(x), None, None, rho, lr,
+                                 0.9, 0.999, 1e-15, 1, 0x50002, None) == L.DG_ERR_INVALID
