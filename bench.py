@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--no-autotune", action="store_true", help="keep --tile and the default compositing variant")
     ap.add_argument("--loss", default="dssim", choices=["dssim", "l1"])
     ap.add_argument("--profile", action="store_true", help="setup + warmup + a few eager steps only (for ncu)")
     return ap.parse_args()
@@ -216,6 +217,12 @@ def run_ours(args, dist, rank, world):
     del gt
     tr = T.DogsTrainer(wl.split, z0, wl.views, targets, rho=(1e-3,) * 5, tile=tile, loss=args.loss)
     m_max = tr.calibrate_capacity()
+    tuned = None
+    if not args.no_autotune and not args.profile:
+        from paper_2405_13943_b300 import autotune
+        tuned = autotune.tune(tr, use_cache=False)
+        tile = tr.tile
+        m_max = tr.calibrate_capacity()
     torch.cuda.synchronize()
     setup_s = time.time() - t_setup
 
@@ -352,7 +359,12 @@ def run_ours(args, dist, rank, world):
                                    f"{wl.split.n_copies} copies, 10% shared, V=8 x "
                                    f"{WORKLOADS[args.workload]['width']}x{WORKLOADS[args.workload]['height']}",
                        "blocks": wl.split.K, "copies": wl.split.n_copies, "views_per_step": len(wl.views[0]),
-                       "tile": args.tile, "loss": "0.8 L1 + 0.2 D-SSIM" if args.loss == "dssim" else "L1",
+                       "tile": f"{tr.tile[0]}x{tr.tile[1]}",
+                       "raster_variant": {"warps_per_tile": tr.vb.plan.raster_warps,
+                                          "staged_per_thread": tr.vb.plan.raster_stage},
+                       "autotune": (None if tuned is None else
+                                    {"best_ms": tuned["ms"], "candidates": len(tuned["candidates"])}),
+                       "loss": "0.8 L1 + 0.2 D-SSIM" if args.loss == "dssim" else "L1",
                        "consensus_every_timed_step": True, "cuda_graph": True,
                        "l2": "working set > L2 (no flush needed)", "instances_per_step": instances,
                        "parallelism": "replicas" if world > 1 else "single GPU",

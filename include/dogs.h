@@ -113,6 +113,10 @@ typedef struct dg_plan {
     int64_t blk_off[DG_MAX_BLOCKS + 1];
     int32_t blk_view_off[DG_MAX_BLOCKS + 1];
     int32_t max_width, max_height;  /* largest view in the batch */
+    /* compositing variant (set to 4, 2 by dg_plan_views; a tuner may change
+     * them): warps per tile in {1, 2, 4, 8} (8 / warps pixels per thread) and
+     * instances staged per thread per round in {1, 2} */
+    int32_t raster_warps, raster_stage;
 } dg_plan;
 
 /* Fill the derived camera fields (host array cams[n_views]) and the plan.

@@ -52,7 +52,8 @@ class DgPlan(C.Structure):
                 ("n_rec", C.c_int64), ("n_tiles", C.c_int64), ("n_pixels", C.c_int64),
                 ("blk_off", C.c_int64 * (DG_MAX_BLOCKS + 1)),
                 ("blk_view_off", C.c_int32 * (DG_MAX_BLOCKS + 1)),
-                ("max_width", C.c_int32), ("max_height", C.c_int32)]
+                ("max_width", C.c_int32), ("max_height", C.c_int32),
+                ("raster_warps", C.c_int32), ("raster_stage", C.c_int32)]
 
 
 _vp = C.c_void_p

@@ -1,27 +1,27 @@
 // K5 blend_fwd and K7 blend_bwd: per-tile front-to-back alpha compositing
 // (Sec. 3.1, Eq. 2) and its adjoint.
 //
-// One warp per (view, tile) of 256 pixels, eight pixels per lane (pixel
-// q = lane + 32 k of the tile, k = 0..7); four independent warps per CTA.
-// Each warp stages 32 of its tile's instances at a time in its own slice of
-// shared memory (one per lane, warp-synchronous: no CTA barrier) and walks
-// them for all eight of its pixels, so one set of shared-memory loads and
-// one per-instance decision serve 256 pixels.  The forward stops a warp as
-// soon as all of its pixels have hit the transmittance cut.  The backward
-// walks the tile back to front from the stored T_final and last index,
-// recovering T_i = T_{i+1} / (1 - alpha_i) and the colour behind each
-// instance by the recurrence B_{i-1} = c_i alpha_i + (1 - alpha_i) B_i
-// (B = background behind the last composited instance); each lane sums its
-// eight pixels' gradients, and the nine per-instance gradients are reduced
-// across the warp by a shuffle reduce-scatter, then added to global memory
-// by nine lanes -- one set of atomics per (instance, tile).
+// One CTA per (view, tile) of 256 pixels with NW warps; each thread owns
+// PPL = 8 / NW pixels of the tile (pixel q = tid + 32 NW k), so a thread's
+// pixels share a column and need no coordinate registers.  Rounds of
+// 32 NW S instances (S per thread) are staged in shared memory -- fetched
+// into registers one round ahead so the gather overlaps compositing -- and
+// every thread walks the round for all of its pixels: one set of
+// shared-memory loads and one decision path serve PPL pixels.  The forward
+// stops a tile as soon as every pixel has hit the transmittance cut.  The
+// backward walks the tile back to front from the stored T_final and last
+// index, recovering T_i = T_{i+1} / (1 - alpha_i) and the colour behind each
+// instance by the recurrence B_{i-1} = c_i alpha_i + (1 - alpha_i) B_i (B =
+// background behind the last composited instance); each lane sums its
+// pixels' gradients, the nine per-instance gradients are reduced across the
+// warp by a shuffle reduce-scatter, and nine lanes add them to global
+// memory (NW sets of atomics per instance and tile).
+//
+// The variant (NW in {1, 2, 4, 8}, S in {1, 2}) and the tile shape are
+// chosen per workload by the autotuner (plan.raster_warps / raster_stage).
 #include "common.cuh"
 
 namespace dg {
-
-constexpr int kWarps = 4;          // tiles per CTA
-constexpr int kPPL = 8;            // pixels per lane
-constexpr int kStage = 32;         // instances staged per warp per round
 
 struct TileInfo {
     int v, W, H, px0, py0;
@@ -45,63 +45,106 @@ __device__ __forceinline__ void tile_info(const dg_camera* cams, int n_views, in
     ti.end = ranges[2 * t + 1];
 }
 
-__global__ void __launch_bounds__(32 * kWarps) k_raster_fwd(const float4* __restrict__ rec,
-                                                            const uint32_t* __restrict__ vals,
-                                                            const uint32_t* __restrict__ ranges,
-                                                            const dg_camera* __restrict__ cams, int n_views,
-                                                            int64_t n_tiles, int tw, int th, float bg0, float bg1,
-                                                            float bg2, float* __restrict__ image,
-                                                            float* __restrict__ T_final,
-                                                            uint32_t* __restrict__ last_out)
+// Thread pixels: column tid % tw, rows tid / tw + k * (32 NW / tw).
+struct LaneGeom {
+    float fx, fy0, dy;
+    int px, py0, dpy;
+};
+
+__device__ __forceinline__ LaneGeom lane_geom(const TileInfo& ti, int tw, int tid, int nthreads)
 {
-    __shared__ float4 s_g[kWarps][kStage];   // mx, my, A, B
-    __shared__ float2 s_h[kWarps][kStage];   // C, log2 opacity
-    __shared__ float4 s_c[kWarps][kStage];   // colour
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t t = (int64_t)blockIdx.x * kWarps + w;
-    if (t >= n_tiles) return;
+    LaneGeom L;
+    L.px = ti.px0 + tid % tw;
+    L.py0 = ti.py0 + tid / tw;
+    L.dpy = nthreads / tw;
+    L.fx = (float)L.px + 0.5f;
+    L.fy0 = (float)L.py0 + 0.5f;
+    L.dy = (float)L.dpy;
+    return L;
+}
+
+struct Fetch {
+    float4 r0, r1, r2;
+    uint32_t r;
+};
+
+__device__ __forceinline__ void fetch(const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
+                                      uint32_t start, uint32_t idx, uint32_t lim, Fetch& f)
+{
+    if (idx < lim) {
+        f.r = vals[start + idx];
+        f.r0 = rec[3 * (int64_t)f.r];
+        f.r1 = rec[3 * (int64_t)f.r + 1];
+        f.r2 = rec[3 * (int64_t)f.r + 2];
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void cta_sync()
+{
+    if (NW == 1) __syncwarp(); else __syncthreads();
+}
+
+template <int NW, int S>
+__global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict__ rec,
+                                                        const uint32_t* __restrict__ vals,
+                                                        const uint32_t* __restrict__ ranges,
+                                                        const dg_camera* __restrict__ cams, int n_views, int tw,
+                                                        int th, float bg0, float bg1, float bg2,
+                                                        float* __restrict__ image, float* __restrict__ T_final,
+                                                        uint32_t* __restrict__ last_out)
+{
+    constexpr int NT = 32 * NW, PPL = 8 / NW, R = NT * S;
+    __shared__ float4 s_g[R];   // mx, my, A, B
+    __shared__ float2 s_h[R];   // C, log2 opacity
+    __shared__ float4 s_c[R];   // colour
+    const int tid = threadIdx.x;
     TileInfo ti;
-    tile_info(cams, n_views, t, tw, th, ranges, ti);
-    float fx[kPPL], fy[kPPL], T[kPPL], C0[kPPL], C1[kPPL], C2[kPPL];
-    uint32_t last[kPPL];
+    tile_info(cams, n_views, blockIdx.x, tw, th, ranges, ti);
+    const LaneGeom G = lane_geom(ti, tw, tid, NT);
+    float T[PPL], C0[PPL], C1[PPL], C2[PPL];
+    uint32_t last[PPL];
     uint32_t live = 0;   // bit k: pixel k inside the image and not yet stopped
 #pragma unroll
-    for (int k = 0; k < kPPL; k++) {
-        int q = lane + 32 * k;
-        int px = ti.px0 + q % tw, py = ti.py0 + q / tw;
-        fx[k] = (float)px + 0.5f;
-        fy[k] = (float)py + 0.5f;
+    for (int k = 0; k < PPL; k++) {
         T[k] = 1.f; C0[k] = C1[k] = C2[k] = 0.f; last[k] = 0;
-        if (px < ti.W && py < ti.H) live |= 1u << k;
+        if (G.px < ti.W && G.py0 + k * G.dpy < ti.H) live |= 1u << k;
     }
     const uint32_t n = ti.end - ti.start;
-    for (uint32_t base = 0; base < n; base += kStage) {
-        if (!__any_sync(0xffffffffu, live != 0)) break;
-        uint32_t idx = base + lane;
-        if (idx < n) {
-            uint32_t r = vals[ti.start + idx];
-            float4 r0 = rec[3 * (int64_t)r], r1 = rec[3 * (int64_t)r + 1], r2 = rec[3 * (int64_t)r + 2];
-            Staged s = stage_geometry(r0, r1);
-            s_g[w][lane] = make_float4(s.mx, s.my, s.A, s.B);
-            s_h[w][lane] = make_float2(s.C, s.lo);
-            s_c[w][lane] = make_float4(r1.z, r1.w, r2.x, 0.f);
+    Fetch nx[S];
+#pragma unroll
+    for (int s = 0; s < S; s++) fetch(rec, vals, ti.start, tid + s * NT, n, nx[s]);
+    for (uint32_t base = 0; base < n; base += R) {
+        bool all_done = NW == 1 ? !__any_sync(0xffffffffu, live != 0) : __syncthreads_count(live != 0) == 0;
+        if (all_done) break;
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            const int j = tid + s * NT;
+            if (base + j < n) {
+                Staged st = stage_geometry(nx[s].r0, nx[s].r1);
+                s_g[j] = make_float4(st.mx, st.my, st.A, st.B);
+                s_h[j] = make_float2(st.C, st.lo);
+                s_c[j] = make_float4(nx[s].r1.z, nx[s].r1.w, nx[s].r2.x, 0.f);
+            }
         }
-        __syncwarp();
-        const uint32_t cnt = min((uint32_t)kStage, n - base);
+        cta_sync<NW>();
+#pragma unroll
+        for (int s = 0; s < S; s++) fetch(rec, vals, ti.start, base + R + tid + s * NT, n, nx[s]);
+        const uint32_t cnt = min((uint32_t)R, n - base);
         for (uint32_t j = 0; j < cnt && live; j++) {
-            const float4 g = s_g[w][j];
-            const float2 h = s_h[w][j];
+            const float4 g = s_g[j];
+            const float2 h = s_h[j];
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
             bool have_c = false;
 #pragma unroll
-            for (int k = 0; k < kPPL; k++) {
+            for (int k = 0; k < PPL; k++) {
                 if (!(live >> k & 1u)) continue;
                 float dx, dy, raw;
-                const float a = pair_alpha(g.x, g.y, g.z, g.w, h.x, h.y, fx[k], fy[k], dx, dy, raw);
+                const float a = pair_alpha(g.x, g.y, g.z, g.w, h.x, h.y, G.fx, G.fy0 + k * G.dy, dx, dy, raw);
                 if (a == 0.f) continue;
                 const float Tn = T[k] * (1.f - a);
                 if (Tn < kTMin) { live &= ~(1u << k); continue; }
-                if (!have_c) { c = s_c[w][j]; have_c = true; }
+                if (!have_c) { c = s_c[j]; have_c = true; }
                 const float wt = a * T[k];
                 C0[k] = fmaf(c.x, wt, C0[k]);
                 C1[k] = fmaf(c.y, wt, C1[k]);
@@ -110,16 +153,15 @@ __global__ void __launch_bounds__(32 * kWarps) k_raster_fwd(const float4* __rest
                 last[k] = base + j + 1;
             }
         }
-        __syncwarp();
+        cta_sync<NW>();
     }
     const int64_t HW = (int64_t)ti.W * ti.H;
     float* im = image + 3 * ti.pix_off;
 #pragma unroll
-    for (int k = 0; k < kPPL; k++) {
-        int q = lane + 32 * k;
-        int px = ti.px0 + q % tw, py = ti.py0 + q / tw;
-        if (px >= ti.W || py >= ti.H) continue;
-        int64_t p = (int64_t)py * ti.W + px;
+    for (int k = 0; k < PPL; k++) {
+        int py = G.py0 + k * G.dpy;
+        if (G.px >= ti.W || py >= ti.H) continue;
+        int64_t p = (int64_t)py * ti.W + G.px;
         im[p] = fmaf(T[k], bg0, C0[k]);
         im[HW + p] = fmaf(T[k], bg1, C1[k]);
         im[2 * HW + p] = fmaf(T[k], bg2, C2[k]);
@@ -157,79 +199,93 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float* v, float& v8,
     return s;
 }
 
-__global__ void __launch_bounds__(32 * kWarps) k_raster_bwd(const float4* __restrict__ rec,
-                                                            const uint32_t* __restrict__ vals,
-                                                            const uint32_t* __restrict__ ranges,
-                                                            const dg_camera* __restrict__ cams, int n_views,
-                                                            int64_t n_tiles, int tw, int th, float bg0, float bg1,
-                                                            float bg2, const float* __restrict__ T_final,
-                                                            const uint32_t* __restrict__ last_in,
-                                                            const float* __restrict__ dL_dimage,
-                                                            float* __restrict__ drec)
+template <int NW, int S>
+__global__ void __launch_bounds__(32 * NW) k_raster_bwd(const float4* __restrict__ rec,
+                                                        const uint32_t* __restrict__ vals,
+                                                        const uint32_t* __restrict__ ranges,
+                                                        const dg_camera* __restrict__ cams, int n_views, int tw,
+                                                        int th, float bg0, float bg1, float bg2,
+                                                        const float* __restrict__ T_final,
+                                                        const uint32_t* __restrict__ last_in,
+                                                        const float* __restrict__ dL_dimage,
+                                                        float* __restrict__ drec)
 {
-    __shared__ float4 s_g[kWarps][kStage];   // mx, my, A, B   (log2-scaled exponent)
-    __shared__ float4 s_h[kWarps][kStage];   // C, log2 o, 1 / o, record index (bits)
-    __shared__ float4 s_k[kWarps][kStage];   // conic a, b, c, -
-    __shared__ float4 s_c[kWarps][kStage];   // colour
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t t = (int64_t)blockIdx.x * kWarps + w;
-    if (t >= n_tiles) return;
+    constexpr int NT = 32 * NW, PPL = 8 / NW, R = NT * S;
+    __shared__ float4 s_g[R];   // mx, my, A, B   (log2-scaled exponent)
+    __shared__ float4 s_h[R];   // C, log2 o, 1 / o, record index (bits)
+    __shared__ float4 s_k[R];   // conic a, b, c, -
+    __shared__ float4 s_c[R];   // colour
+    __shared__ uint32_t s_max;
+    const int tid = threadIdx.x, lane = tid & 31;
     TileInfo ti;
-    tile_info(cams, n_views, t, tw, th, ranges, ti);
+    tile_info(cams, n_views, blockIdx.x, tw, th, ranges, ti);
+    const LaneGeom Lg = lane_geom(ti, tw, tid, NT);
     const int64_t HW = (int64_t)ti.W * ti.H;
     const float* gi = dL_dimage + 3 * ti.pix_off;
-    float fx[kPPL], fy[kPPL], T[kPPL], B0[kPPL], B1[kPPL], B2[kPPL], G0[kPPL], G1[kPPL], G2[kPPL];
-    uint32_t last[kPPL];
+    float T[PPL], B0[PPL], B1[PPL], B2[PPL], G0[PPL], G1[PPL], G2[PPL];
+    uint32_t last[PPL];
     uint32_t ml = 0;
 #pragma unroll
-    for (int k = 0; k < kPPL; k++) {
-        int q = lane + 32 * k;
-        int px = ti.px0 + q % tw, py = ti.py0 + q / tw;
-        fx[k] = (float)px + 0.5f;
-        fy[k] = (float)py + 0.5f;
+    for (int k = 0; k < PPL; k++) {
+        int py = Lg.py0 + k * Lg.dpy;
         T[k] = 1.f; G0[k] = G1[k] = G2[k] = 0.f; last[k] = 0;
         B0[k] = bg0; B1[k] = bg1; B2[k] = bg2;
-        if (px < ti.W && py < ti.H) {
-            int64_t p = (int64_t)py * ti.W + px;
+        if (Lg.px < ti.W && py < ti.H) {
+            int64_t p = (int64_t)py * ti.W + Lg.px;
             G0[k] = gi[p]; G1[k] = gi[HW + p]; G2[k] = gi[2 * HW + p];
             T[k] = T_final[ti.pix_off + p];
             last[k] = last_in[ti.pix_off + p];
             ml = max(ml, last[k]);
         }
     }
-    const uint32_t maxlast = __reduce_max_sync(0xffffffffu, ml);
+    uint32_t maxlast = __reduce_max_sync(0xffffffffu, ml);
+    if (NW > 1) {
+        if (tid == 0) s_max = 0;
+        __syncthreads();
+        if (lane == 0 && maxlast) atomicMax(&s_max, maxlast);
+        __syncthreads();
+        maxlast = s_max;
+    }
     if (maxlast == 0) return;
-    const int rounds = (int)((maxlast + kStage - 1) / kStage);
+    const int rounds = (int)((maxlast + R - 1) / R);
+    Fetch nx[S];
+#pragma unroll
+    for (int s = 0; s < S; s++) fetch(rec, vals, ti.start, (uint32_t)(rounds - 1) * R + tid + s * NT, maxlast, nx[s]);
     for (int rd = rounds - 1; rd >= 0; rd--) {
-        const uint32_t base = (uint32_t)rd * kStage;
-        const uint32_t idx = base + lane;
-        __syncwarp();
-        if (idx < maxlast) {
-            uint32_t r = vals[ti.start + idx];
-            float4 r0 = rec[3 * (int64_t)r], r1 = rec[3 * (int64_t)r + 1], r2 = rec[3 * (int64_t)r + 2];
-            Staged s = stage_geometry(r0, r1);
-            s_g[w][lane] = make_float4(s.mx, s.my, s.A, s.B);
-            s_h[w][lane] = make_float4(s.C, s.lo, __frcp_rn(r1.y), __uint_as_float(r));
-            s_k[w][lane] = make_float4(r0.z, r0.w, r1.x, 0.f);
-            s_c[w][lane] = make_float4(r1.z, r1.w, r2.x, 0.f);
+        const uint32_t base = (uint32_t)rd * R;
+        cta_sync<NW>();
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            const int j = tid + s * NT;
+            if (base + j < maxlast) {
+                Staged st = stage_geometry(nx[s].r0, nx[s].r1);
+                s_g[j] = make_float4(st.mx, st.my, st.A, st.B);
+                s_h[j] = make_float4(st.C, st.lo, __frcp_rn(nx[s].r1.y), __uint_as_float(nx[s].r));
+                s_k[j] = make_float4(nx[s].r0.z, nx[s].r0.w, nx[s].r1.x, 0.f);
+                s_c[j] = make_float4(nx[s].r1.z, nx[s].r1.w, nx[s].r2.x, 0.f);
+            }
         }
-        __syncwarp();
-        const int cnt = (int)min((uint32_t)kStage, maxlast - base);
+        cta_sync<NW>();
+        if (rd > 0) {
+#pragma unroll
+            for (int s = 0; s < S; s++) fetch(rec, vals, ti.start, base - R + tid + s * NT, maxlast, nx[s]);
+        }
+        const int cnt = (int)min((uint32_t)R, maxlast - base);
         for (int j = cnt - 1; j >= 0; j--) {
             const uint32_t pos = base + (uint32_t)j;
-            const float4 g = s_g[w][j];
-            const float4 h = s_h[w][j];
+            const float4 g = s_g[j];
+            const float4 h = s_h[j];
             float gr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             float g8 = 0.f;
             bool any = false;
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f), kc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < kPPL; k++) {
+            for (int k = 0; k < PPL; k++) {
                 if (pos >= last[k]) continue;
                 float dx, dy, raw = 0.f;
-                const float a = pair_alpha(g.x, g.y, g.z, g.w, h.x, h.y, fx[k], fy[k], dx, dy, raw);
+                const float a = pair_alpha(g.x, g.y, g.z, g.w, h.x, h.y, Lg.fx, Lg.fy0 + k * Lg.dy, dx, dy, raw);
                 if (!(a > 0.f)) continue;
-                if (!any) { c = s_c[w][j]; kc = s_k[w][j]; any = true; }
+                if (!any) { c = s_c[j]; kc = s_k[j]; any = true; }
                 const float Tj = T[k] * __fdividef(1.f, 1.f - a);
                 const float wT = a * Tj;
                 gr[6] = fmaf(G0[k], wT, gr[6]);
@@ -252,25 +308,55 @@ __global__ void __launch_bounds__(32 * kWarps) k_raster_bwd(const float4* __rest
                 }
             }
             if (!__any_sync(0xffffffffu, any)) continue;
-            const float s = warp_reduce_scatter8(gr, g8, lane);
+            const float sred = warp_reduce_scatter8(gr, g8, lane);
             float* d = drec + 12 * (int64_t)__float_as_uint(h.w);
             if ((lane & 3) == 0) {
                 const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                if (s != 0.f) atomicAdd(d + vi, s);
+                if (sred != 0.f) atomicAdd(d + vi, sred);
             }
             if (lane == 0 && g8 != 0.f) atomicAdd(d + 8, g8);
         }
     }
 }
 
+template <int NW, int S>
+static void fwd_launch(const float4* rec, const uint32_t* vals, const uint32_t* ranges, const dg_camera* cams,
+                       const dg_plan& p, const float* bg, float* image, float* T_final, uint32_t* last,
+                       cudaStream_t st)
+{
+    k_raster_fwd<NW, S><<<(unsigned)p.n_tiles, 32 * NW, 0, st>>>(rec, vals, ranges, cams, p.n_views, p.tile_w,
+                                                                 p.tile_h, bg[0], bg[1], bg[2], image, T_final, last);
+}
+
+template <int NW, int S>
+static void bwd_launch(const float4* rec, const uint32_t* vals, const uint32_t* ranges, const dg_camera* cams,
+                       const dg_plan& p, const float* bg, const float* T_final, const uint32_t* last,
+                       const float* dL_dimage, float* drec, cudaStream_t st)
+{
+    k_raster_bwd<NW, S><<<(unsigned)p.n_tiles, 32 * NW, 0, st>>>(rec, vals, ranges, cams, p.n_views, p.tile_w,
+                                                                 p.tile_h, bg[0], bg[1], bg[2], T_final, last,
+                                                                 dL_dimage, drec);
+}
+
+#define DG_RASTER_DISPATCH(FN, ...)                                          \
+    switch (plan.raster_warps * 10 + plan.raster_stage) {                    \
+    case 11: FN<1, 1>(__VA_ARGS__); break;                                   \
+    case 12: FN<1, 2>(__VA_ARGS__); break;                                   \
+    case 21: FN<2, 1>(__VA_ARGS__); break;                                   \
+    case 22: FN<2, 2>(__VA_ARGS__); break;                                   \
+    case 41: FN<4, 1>(__VA_ARGS__); break;                                   \
+    case 42: FN<4, 2>(__VA_ARGS__); break;                                   \
+    case 81: FN<8, 1>(__VA_ARGS__); break;                                   \
+    case 82: FN<8, 2>(__VA_ARGS__); break;                                   \
+    default: return DG_ERR_INVALID;                                          \
+    }
+
 int launch_raster_fwd(const float4* rec, const uint32_t* vals, const uint32_t* ranges, const dg_camera* cams,
                       const dg_plan& plan, const float* bg, float* image, float* T_final, uint32_t* last,
                       cudaStream_t st)
 {
     if (plan.n_tiles == 0) return DG_OK;
-    unsigned grid = (unsigned)((plan.n_tiles + kWarps - 1) / kWarps);
-    k_raster_fwd<<<grid, 32 * kWarps, 0, st>>>(rec, vals, ranges, cams, plan.n_views, plan.n_tiles, plan.tile_w,
-                                                plan.tile_h, bg[0], bg[1], bg[2], image, T_final, last);
+    DG_RASTER_DISPATCH(fwd_launch, rec, vals, ranges, cams, plan, bg, image, T_final, last, st)
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;
@@ -281,9 +367,7 @@ int launch_raster_bwd(const float4* rec, const uint32_t* vals, const uint32_t* r
                       const float* dL_dimage, float* drec, cudaStream_t st)
 {
     if (plan.n_tiles == 0) return DG_OK;
-    unsigned grid = (unsigned)((plan.n_tiles + kWarps - 1) / kWarps);
-    k_raster_bwd<<<grid, 32 * kWarps, 0, st>>>(rec, vals, ranges, cams, plan.n_views, plan.n_tiles, plan.tile_w,
-                                                plan.tile_h, bg[0], bg[1], bg[2], T_final, last, dL_dimage, drec);
+    DG_RASTER_DISPATCH(bwd_launch, rec, vals, ranges, cams, plan, bg, T_final, last, dL_dimage, drec, st)
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;

@@ -117,12 +117,22 @@ def camera_array(cams: Sequence[S.Camera]):
     return arr
 
 
+# compositing variant (warps per tile, instances staged per thread) applied to
+# new plans; the autotuner sets it from measurements
+RASTER_VARIANT = [4, 2]
+
+
+def set_raster_variant(warps: int, stage: int) -> None:
+    RASTER_VARIANT[0], RASTER_VARIANT[1] = int(warps), int(stage)
+
+
 def plan_views(cams: Sequence[S.Camera], blk_off: Sequence[int], tile_w=16, tile_h=16):
     arr = camera_array(cams)
     off = (C.c_int64 * len(blk_off))(*[int(v) for v in blk_off])
     plan = L.DgPlan()
     L.check(L.lib().dg_plan_views(arr, len(cams), off, len(blk_off) - 1, tile_w, tile_h, C.byref(plan)),
             "dg_plan_views")
+    plan.raster_warps, plan.raster_stage = RASTER_VARIANT
     return arr, plan
 
 
@@ -130,6 +140,7 @@ def render_plan(cams: Sequence[S.Camera], n_gauss: int, tile_w=16, tile_h=16):
     arr = camera_array(cams)
     plan = L.DgPlan()
     L.check(L.lib().dg_render_plan(arr, len(cams), int(n_gauss), tile_w, tile_h, C.byref(plan)), "dg_render_plan")
+    plan.raster_warps, plan.raster_stage = RASTER_VARIANT
     return arr, plan
 
 

@@ -56,6 +56,7 @@ class DogsTrainer:
         self.u, self.anchor = self.x.like(), self.x.like()
         D.dg_admm_anchor(self.z, self.u, self.gid, self.shared, self.anchor)
         self.view_sets = [list(v) for v in view_sets]
+        self.tile = tuple(tile)
         self.vb = D.ViewBatch(self.view_sets[0], split.blk_off, tile[0], tile[1], device=device,
                               capacity=capacity, loss_ws=(loss == "dssim"))
         self.cam_pool = [D.cams_to_device(D.plan_views(vs, split.blk_off, *tile)[0], device) for vs in self.view_sets]
@@ -65,6 +66,27 @@ class DogsTrainer:
         self.residuals = torch.zeros(10, dtype=torch.float64, device=device)
         self.t = 0
         self.graphs = {}
+
+    # ---- rasteriser configuration (autotuner) ------------------------------------
+    def set_tile(self, tile) -> None:
+        """Re-plan the batch for another tile shape (new buffers, capacity
+        recalibrated); captured graphs are dropped."""
+        tile = tuple(tile)
+        if tile == self.tile:
+            return
+        self.vb = None
+        torch.cuda.empty_cache()
+        self.tile = tile
+        self.vb = D.ViewBatch(self.view_sets[0], self.split.blk_off, tile[0], tile[1], device=self.device,
+                              loss_ws=(self.loss_kind == "dssim"))
+        self.cam_pool = [D.cams_to_device(D.plan_views(vs, self.split.blk_off, *tile)[0], self.device)
+                         for vs in self.view_sets]
+        self.graphs.clear()
+        self.calibrate_capacity()
+
+    def set_variant(self, warps: int, stage: int) -> None:
+        self.vb.plan.raster_warps, self.vb.plan.raster_stage = int(warps), int(stage)
+        self.graphs.clear()
 
     # ---- capacity -------------------------------------------------------------
     def calibrate_capacity(self, headroom=1.3) -> int:
