@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-autotune", action="store_true", help="keep --tile and the default compositing variant")
+    ap.add_argument("--variant", default=None, help="compositing variant W,S (warps per tile, staged per thread)")
     ap.add_argument("--loss", default="dssim", choices=["dssim", "l1"])
     ap.add_argument("--profile", action="store_true", help="setup + warmup + a few eager steps only (for ncu)")
     return ap.parse_args()
@@ -215,10 +216,12 @@ def run_ours(args, dist, rank, world):
     gt = D.GaussianBuffer.from_synth(wl.gt)
     targets = render_targets(gt, wl.views, tile)
     del gt
+    if args.variant:
+        D.set_raster_variant(*[int(v) for v in args.variant.split(",")])
     tr = T.DogsTrainer(wl.split, z0, wl.views, targets, rho=(1e-3,) * 5, tile=tile, loss=args.loss)
     m_max = tr.calibrate_capacity()
     tuned = None
-    if not args.no_autotune and not args.profile:
+    if not args.no_autotune and not args.profile and not args.variant:
         from paper_2405_13943_b300 import autotune
         tuned = autotune.tune(tr, use_cache=False)
         tile = tr.tile
