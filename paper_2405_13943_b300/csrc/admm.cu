@@ -122,27 +122,117 @@ struct ConsArgs {
     int n_planes;
 };
 
-// one scalar element of a global held by n >= 2 copies
+// Up to kFast copies per global are handled with all their loads issued
+// together; globals held by more blocks take the loop below.
+constexpr int kFast = 4;
+
+struct ResAcc {
+    float rp[5], rd[5];
+};
+
+// One float4 field (lanes l: group grp[l]; lane 3 of the scale field is padding).
+__device__ __forceinline__ void cons_field4(const float4* __restrict__ X, float4* __restrict__ U,
+                                            float4* __restrict__ A, float4* __restrict__ Z, int64_t i,
+                                            const int32_t* cp, int n, const int* grp, float alpha, const float* rho,
+                                            ResAcc& r)
+{
+    float4 xs[kFast], us[kFast];
+#pragma unroll
+    for (int k = 0; k < kFast; k++)
+        if (k < n) { xs[k] = X[cp[k]]; us[k] = U[cp[k]]; }
+    const float4 zo = Z[i];
+    const float zp[4] = {zo.x, zo.y, zo.z, zo.w};
+    float zn[4];
+    const float inv = 1.f / (float)n;
+#pragma unroll
+    for (int l = 0; l < 4; l++) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < kFast; k++)
+            if (k < n) {
+                const float xv = (&xs[k].x)[l];
+                acc += alpha * xv + (1.f - alpha) * zp[l] + (&us[k].x)[l];
+            }
+        zn[l] = acc * inv;
+    }
+#pragma unroll
+    for (int k = 0; k < kFast; k++) {
+        if (k >= n) continue;
+        float un[4], an[4];
+#pragma unroll
+        for (int l = 0; l < 4; l++) {
+            const float xv = (&xs[k].x)[l];
+            const float xh = alpha * xv + (1.f - alpha) * zp[l];
+            un[l] = (&us[k].x)[l] + xh - zn[l];
+            an[l] = zn[l] - un[l];
+            if (grp[l] >= 0) r.rp[grp[l]] += (xv - zn[l]) * (xv - zn[l]);
+        }
+        U[cp[k]] = make_float4(un[0], un[1], un[2], un[3]);
+        A[cp[k]] = make_float4(an[0], an[1], an[2], an[3]);
+    }
+#pragma unroll
+    for (int l = 0; l < 4; l++)
+        if (grp[l] >= 0) {
+            const float dz = zn[l] - zp[l];
+            r.rd[grp[l]] += rho[grp[l]] * rho[grp[l]] * (float)n * dz * dz;
+        }
+    Z[i] = make_float4(zn[0], zn[1], zn[2], zn[3]);
+}
+
+// generic path: one scalar element, any number of copies
 __device__ __forceinline__ float cons_elem(const float* xp, float* up, float* ap, const int32_t* cp, int n,
                                            int64_t stride, float zprev, float alpha, float& r_primal)
 {
     float acc = 0.f;
     for (int k = 0; k < n; k++) {
         int64_t c = (int64_t)cp[k] * stride;
-        float xh = alpha * xp[c] + (1.f - alpha) * zprev;
-        acc += xh + up[c];
+        acc += alpha * xp[c] + (1.f - alpha) * zprev + up[c];
     }
     float z = acc / (float)n;
     for (int k = 0; k < n; k++) {
         int64_t c = (int64_t)cp[k] * stride;
         float xv = xp[c];
-        float xh = alpha * xv + (1.f - alpha) * zprev;
-        float un = up[c] + xh - z;
+        float un = up[c] + alpha * xv + (1.f - alpha) * zprev - z;
         up[c] = un;
         ap[c] = z - un;
         r_primal += (xv - z) * (xv - z);
     }
     return z;
+}
+
+// globals held by more than kFast blocks (rare): element by element
+__device__ __noinline__ void cons_generic(GView x, GView u, GView z, GView an, int64_t i, const int32_t* cpg, int n,
+                                          const ConsArgs& a, ResAcc& r)
+{
+    float4* xf[3] = {x.mo, x.quat, x.scale};
+    float4* uf[3] = {u.mo, u.quat, u.scale};
+    float4* zf[3] = {z.mo, z.quat, z.scale};
+    float4* af[3] = {an.mo, an.quat, an.scale};
+    for (int f = 0; f < 3; f++) {
+        float4 zo = zf[f][i];
+        float zp[4] = {zo.x, zo.y, zo.z, zo.w}, zn[4];
+        for (int l = 0; l < 4; l++) {
+            int grp = f == 0 ? (l < 3 ? 0 : 4) : (f == 1 ? 1 : 2);
+            float rr = 0.f;
+            zn[l] = cons_elem((const float*)xf[f] + l, (float*)uf[f] + l, (float*)af[f] + l, cpg, n, 4, zp[l],
+                              a.alpha, rr);
+            if (!(f == 2 && l == 3)) {
+                r.rp[grp] += rr;
+                float dz = zn[l] - zp[l];
+                r.rd[grp] += a.rho[grp] * a.rho[grp] * (float)n * dz * dz;
+            }
+        }
+        zf[f][i] = make_float4(zn[0], zn[1], zn[2], zn[3]);
+    }
+    for (int j = 0; j < a.n_planes; j++) {
+        float zo = z.sh[(int64_t)j * z.ld + i];
+        float rr = 0.f;
+        float zn = cons_elem(x.sh + (int64_t)j * x.ld, u.sh + (int64_t)j * u.ld, an.sh + (int64_t)j * an.ld, cpg, n,
+                             1, zo, a.alpha, rr);
+        z.sh[(int64_t)j * z.ld + i] = zn;
+        r.rp[3] += rr;
+        r.rd[3] += a.rho[3] * a.rho[3] * (float)n * (zn - zo) * (zn - zo);
+    }
 }
 
 __global__ void __launch_bounds__(128) k_consensus(GView x, GView u, GView z, GView an,
@@ -151,49 +241,55 @@ __global__ void __launch_bounds__(128) k_consensus(GView x, GView u, GView z, GV
                                                    ConsArgs a, double* __restrict__ res)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float rp[5] = {0, 0, 0, 0, 0}, rd[5] = {0, 0, 0, 0, 0};
+    ResAcc r;
+#pragma unroll
+    for (int k = 0; k < 5; k++) { r.rp[k] = 0.f; r.rd[k] = 0.f; }
     if (i < n_glob) {
-        int64_t b = g_off[i];
-        int n = (int)(g_off[i + 1] - b);
-        const int32_t* cp = g_copies + b;
+        const int64_t b = g_off[i];
+        const int n = (int)(g_off[i + 1] - b);
+        const int32_t* cpg = g_copies + b;
         if (n == 1) {
-            int64_t c = cp[0];
+            const int64_t c = cpg[0];
             z.mo[i] = x.mo[c];
             z.quat[i] = x.quat[c];
             z.scale[i] = x.scale[c];
             for (int j = 0; j < a.n_planes; j++) z.sh[(int64_t)j * z.ld + i] = x.sh[(int64_t)j * x.ld + c];
-        } else if (n > 1) {
-            // float4 fields: mean+opacity, rotation, scale, as scalar lanes
-            float4* xf[3] = {x.mo, x.quat, x.scale};
-            float4* uf[3] = {u.mo, u.quat, u.scale};
-            float4* zf[3] = {z.mo, z.quat, z.scale};
-            float4* af[3] = {an.mo, an.quat, an.scale};
-            for (int f = 0; f < 3; f++) {
-                float4 zo = zf[f][i];
-                float zp[4] = {zo.x, zo.y, zo.z, zo.w}, zn[4];
+        } else if (n > 1 && n <= kFast) {
+            int32_t cp[kFast];
 #pragma unroll
-                for (int l = 0; l < 4; l++) {
-                    int grp = f == 0 ? (l < 3 ? 0 : 4) : (f == 1 ? 1 : 2);
-                    float r = 0.f;
-                    zn[l] = cons_elem((const float*)xf[f] + l, (float*)uf[f] + l, (float*)af[f] + l, cp, n, 4,
-                                      zp[l], a.alpha, r);
-                    if (!(f == 2 && l == 3)) {
-                        rp[grp] += r;
-                        float dz = zn[l] - zp[l];
-                        rd[grp] += a.rho[grp] * a.rho[grp] * (float)n * dz * dz;
-                    }
-                }
-                zf[f][i] = make_float4(zn[0], zn[1], zn[2], zn[3]);
-            }
+            for (int k = 0; k < kFast; k++) cp[k] = k < n ? cpg[k] : 0;
+            const int g_mo[4] = {0, 0, 0, 4}, g_q[4] = {1, 1, 1, 1}, g_s[4] = {2, 2, 2, -1};
+            cons_field4(x.mo, u.mo, an.mo, z.mo, i, cp, n, g_mo, a.alpha, a.rho, r);
+            cons_field4(x.quat, u.quat, an.quat, z.quat, i, cp, n, g_q, a.alpha, a.rho, r);
+            cons_field4(x.scale, u.scale, an.scale, z.scale, i, cp, n, g_s, a.alpha, a.rho, r);
+            const float inv = 1.f / (float)n;
             for (int j = 0; j < a.n_planes; j++) {
-                float zo = z.sh[(int64_t)j * z.ld + i];
-                float r = 0.f;
-                float zn = cons_elem(x.sh + (int64_t)j * x.ld, u.sh + (int64_t)j * u.ld, an.sh + (int64_t)j * an.ld,
-                                     cp, n, 1, zo, a.alpha, r);
+                const float* X = x.sh + (int64_t)j * x.ld;
+                float* U = u.sh + (int64_t)j * u.ld;
+                float* A = an.sh + (int64_t)j * an.ld;
+                float xs[kFast], us[kFast];
+#pragma unroll
+                for (int k = 0; k < kFast; k++)
+                    if (k < n) { xs[k] = X[cp[k]]; us[k] = U[cp[k]]; }
+                const float zo = z.sh[(int64_t)j * z.ld + i];
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < kFast; k++)
+                    if (k < n) acc += a.alpha * xs[k] + (1.f - a.alpha) * zo + us[k];
+                const float zn = acc * inv;
+#pragma unroll
+                for (int k = 0; k < kFast; k++)
+                    if (k < n) {
+                        const float un = us[k] + a.alpha * xs[k] + (1.f - a.alpha) * zo - zn;
+                        U[cp[k]] = un;
+                        A[cp[k]] = zn - un;
+                        r.rp[3] += (xs[k] - zn) * (xs[k] - zn);
+                    }
                 z.sh[(int64_t)j * z.ld + i] = zn;
-                rp[3] += r;
-                rd[3] += a.rho[3] * a.rho[3] * (float)n * (zn - zo) * (zn - zo);
+                r.rd[3] += a.rho[3] * a.rho[3] * (float)n * (zn - zo) * (zn - zo);
             }
+        } else if (n > kFast) {
+            cons_generic(x, u, z, an, i, cpg, n, a, r);
         }
     }
     if (res) {
@@ -201,7 +297,7 @@ __global__ void __launch_bounds__(128) k_consensus(GView x, GView u, GView z, GV
         int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
         for (int k = 0; k < 5; k++) {
-            float a0 = rp[k], a1 = rd[k];
+            float a0 = r.rp[k], a1 = r.rd[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 a0 += __shfl_xor_sync(0xffffffffu, a0, o);

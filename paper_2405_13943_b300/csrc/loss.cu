@@ -3,7 +3,7 @@
 //
 // SSIM: 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2, zero
 // padding, "same" size.  The forward computes the five local moments with a
-// separable filter in shared memory (tile 32x16 plus a 5-pixel halo), the SSIM
+// separable filter in shared memory (tile 32x32 plus a 5-pixel halo), the SSIM
 // map, and the three per-pixel partials dS/d(mean_x), dS/d(E[x^2]),
 // dS/d(E[xy]); the backward applies the same (symmetric) filter to those
 // partials: dL/dx = F(a) + 2 x F(b) + y F(c).
@@ -11,8 +11,7 @@
 
 namespace dg {
 
-constexpr int kSW = 32, kSH = 16, kR = 5, kWin = 11;
-constexpr int kInW = kSW + 2 * kR, kInH = kSH + 2 * kR;
+constexpr int kR = 5, kWin = 11;
 
 struct Win { float w[kWin]; };
 
@@ -63,134 +62,163 @@ __global__ void k_loss_final(const dg_camera* __restrict__ cams, int n_views, fl
 }
 
 // ---- SSIM ------------------------------------------------------------------------
-// Separable filtering of NM maps held in shared memory (kInH x kInW) into
-// kSH x kSW outputs; tmp is kInH x kSW per map.
-template <int NM>
-__device__ __forceinline__ void filter_tile(float (*in)[kInH][kInW], float (*tmp)[kInH][kSW], const Win& g,
-                                            float out[][2])
+// Output tile 32 x 32 per CTA (256 threads) with a 5-pixel halo.  Both passes
+// of the separable 11-tap filter are register-blocked: a thread produces 8
+// consecutive outputs from a window of 18 inputs held in registers, so each
+// input is read from shared memory once per pass instead of 11 times.
+constexpr int kTS = 32;                 // output tile side
+constexpr int kTI = kTS + 2 * kR;       // input tile side (42)
+constexpr int kBlk = 8;                 // outputs per thread per pass
+constexpr int kWin8 = kBlk + 2 * kR;    // 18 inputs per 8 outputs
+
+// horizontal pass over NM maps: for input rows [0, kTI) and output columns
+// [0, kTS): tmp[m][r][c] = sum_k w_k in_m[r][c + k]
+template <int NM, typename Load>
+__device__ __forceinline__ void hpass(const Win& g, float (*tmp)[kTI][kTS], Load load)
 {
-    for (int i = threadIdx.x; i < kInH * kSW; i += blockDim.x) {
-        int r = i / kSW, c = i % kSW;
+    for (int task = threadIdx.x; task < kTI * (kTS / kBlk); task += blockDim.x) {
+        const int r = task / (kTS / kBlk), c0 = (task % (kTS / kBlk)) * kBlk;
+        float in[NM][kWin8];
 #pragma unroll
-        for (int m = 0; m < NM; m++) {
-            float s = 0.f;
+        for (int i = 0; i < kWin8; i++) load(r, c0 + i, in, i);
 #pragma unroll
-            for (int k = 0; k < kWin; k++) s = fmaf(g.w[k], in[m][r][c + k], s);
-            tmp[m][r][c] = s;
-        }
+        for (int m = 0; m < NM; m++)
+#pragma unroll
+            for (int j = 0; j < kBlk; j++) {
+                float s = 0.f;
+#pragma unroll
+                for (int k = 0; k < kWin; k++) s = fmaf(g.w[k], in[m][j + k], s);
+                tmp[m][r][c0 + j] = s;
+            }
     }
-    __syncthreads();
-    // each thread: column threadIdx.x % 32, rows (threadIdx.x / 32) + 8 * e
+}
+
+// vertical pass: out[m][j] = sum_k w_k tmp[m][r0 + j + k][c] for the thread's
+// column c and rows r0 .. r0 + 7
+template <int NM>
+__device__ __forceinline__ void vpass(const Win& g, float (*tmp)[kTI][kTS], int c, int r0, float out[][kBlk])
+{
 #pragma unroll
-    for (int e = 0; e < 2; e++) {
-        int c = threadIdx.x % kSW, r = threadIdx.x / kSW + 8 * e;
+    for (int m = 0; m < NM; m++) {
+        float col[kWin8];
 #pragma unroll
-        for (int m = 0; m < NM; m++) {
+        for (int i = 0; i < kWin8; i++) col[i] = tmp[m][r0 + i][c];
+#pragma unroll
+        for (int j = 0; j < kBlk; j++) {
             float s = 0.f;
 #pragma unroll
-            for (int k = 0; k < kWin; k++) s = fmaf(g.w[k], tmp[m][r + k][c], s);
-            out[m][e] = s;
+            for (int k = 0; k < kWin; k++) s = fmaf(g.w[k], col[j + k], s);
+            out[m][j] = s;
         }
     }
 }
 
-__global__ void __launch_bounds__(256) k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt,
+__global__ void __launch_bounds__(128) k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt,
                                                   const dg_camera* __restrict__ cams, Win g, float w_ssim,
                                                   double* __restrict__ sums, float* __restrict__ partial)
 {
-    __shared__ float s_in[5][kInH][kInW];
-    __shared__ float s_tmp[5][kInH][kSW];
-    int v = blockIdx.z / 3, ch = blockIdx.z % 3;
-    int W = __ldg(&cams[v].width), H = __ldg(&cams[v].height);
-    int x0 = blockIdx.x * kSW, y0 = blockIdx.y * kSH;
+    __shared__ float s_x[kTI][kTI + 1];
+    __shared__ float s_y[kTI][kTI + 1];
+    __shared__ float s_tmp[5][kTI][kTS];
+    const int v = blockIdx.z / 3, ch = blockIdx.z % 3;
+    const int W = __ldg(&cams[v].width), H = __ldg(&cams[v].height);
+    const int x0 = blockIdx.x * kTS, y0 = blockIdx.y * kTS;
     if (x0 >= W || y0 >= H) return;
-    int64_t HW = (int64_t)W * H;
-    int64_t pix = __ldg(&cams[v].pix_off);
+    const int64_t HW = (int64_t)W * H;
+    const int64_t pix = __ldg(&cams[v].pix_off);
     const float* X = img + 3 * pix + ch * HW;
     const float* Y = tgt + 3 * pix + ch * HW;
-    for (int i = threadIdx.x; i < kInH * kInW; i += blockDim.x) {
-        int r = i / kInW, c = i % kInW;
-        int gx = x0 + c - kR, gy = y0 + r - kR;
-        float a = 0.f, b = 0.f;
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H) { a = X[(int64_t)gy * W + gx]; b = Y[(int64_t)gy * W + gx]; }
-        s_in[0][r][c] = a; s_in[1][r][c] = b;
-        s_in[2][r][c] = a * a; s_in[3][r][c] = b * b; s_in[4][r][c] = a * b;
+    for (int i = threadIdx.x; i < kTI * kTI; i += blockDim.x) {
+        const int r = i / kTI, c = i % kTI;
+        const int gx = x0 + c - kR, gy = y0 + r - kR;
+        const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        s_x[r][c] = ok ? X[(int64_t)gy * W + gx] : 0.f;
+        s_y[r][c] = ok ? Y[(int64_t)gy * W + gx] : 0.f;
     }
     __syncthreads();
-    float mo[5][2];
-    filter_tile<5>(s_in, s_tmp, g, mo);
+    hpass<5>(g, s_tmp, [&](int r, int c, float (*in)[kWin8], int i) {
+        const float a = s_x[r][c], b = s_y[r][c];
+        in[0][i] = a; in[1][i] = b; in[2][i] = a * a; in[3][i] = b * b; in[4][i] = a * b;
+    });
+    __syncthreads();
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-    float invN = 1.f / (float)(3 * HW);
+    const float sc = -w_ssim / (float)(3 * HW);
     float acc = 0.f;
+    float* P = partial + 9 * pix + 3 * ch * HW;
+    for (int task = threadIdx.x; task < kTS * (kTS / kBlk); task += blockDim.x) {
+        const int c = task % kTS, r0 = (task / kTS) * kBlk;
+        float mo[5][kBlk];
+        vpass<5>(g, s_tmp, c, r0, mo);
+        const int gx = x0 + c;
 #pragma unroll
-    for (int e = 0; e < 2; e++) {
-        int c = threadIdx.x % kSW, r = threadIdx.x / kSW + 8 * e;
-        int gx = x0 + c, gy = y0 + r;
-        if (gx >= W || gy >= H) continue;
-        float m1 = mo[0][e], m2 = mo[1][e];
-        float s1 = mo[2][e] - m1 * m1, s2 = mo[3][e] - m2 * m2, s12 = mo[4][e] - m1 * m2;
-        float A1 = 2.f * m1 * m2 + C1, A2 = 2.f * s12 + C2;
-        float B1 = m1 * m1 + m2 * m2 + C1, B2 = s1 + s2 + C2;
-        float iB = 1.f / (B1 * B2);
-        float S = A1 * A2 * iB;
-        acc += S;
-        float dA1 = A2 * iB, dA2 = A1 * iB, dB1 = -S / B1, dB2 = -S / B2;
-        float dm1 = 2.f * m2 * dA1 - 2.f * m2 * dA2 + 2.f * m1 * dB1 - 2.f * m1 * dB2;
-        // loss term w_ssim * (1 - mean S): scale partials by -w_ssim / N
-        float sc = -w_ssim * invN;
-        int64_t p = (int64_t)gy * W + gx;
-        float* P = partial + 9 * pix + 3 * ch * HW;
-        P[p] = sc * dm1;
-        P[HW + p] = sc * dB2;
-        P[2 * HW + p] = sc * 2.f * dA2;
+        for (int j = 0; j < kBlk; j++) {
+            const int gy = y0 + r0 + j;
+            if (gx >= W || gy >= H) continue;
+            const float m1 = mo[0][j], m2 = mo[1][j];
+            const float s1 = mo[2][j] - m1 * m1, s2 = mo[3][j] - m2 * m2, s12 = mo[4][j] - m1 * m2;
+            const float A1 = 2.f * m1 * m2 + C1, A2 = 2.f * s12 + C2;
+            const float B1 = m1 * m1 + m2 * m2 + C1, B2 = s1 + s2 + C2;
+            const float iB = 1.f / (B1 * B2);
+            const float S = A1 * A2 * iB;
+            acc += S;
+            const float dA1 = A2 * iB, dA2 = A1 * iB, dB1 = -S / B1, dB2 = -S / B2;
+            const float dm1 = 2.f * m2 * dA1 - 2.f * m2 * dA2 + 2.f * m1 * dB1 - 2.f * m1 * dB2;
+            const int64_t p = (int64_t)gy * W + gx;
+            P[p] = sc * dm1;
+            P[HW + p] = sc * dB2;
+            P[2 * HW + p] = sc * 2.f * dA2;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    __shared__ float s_w[8];
+    __shared__ float s_w[4];
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < 8; i++) t += s_w[i];
-        atomicAdd(&sums[v], t);
-    }
+    if (threadIdx.x == 0) atomicAdd(&sums[v], (double)s_w[0] + s_w[1] + s_w[2] + s_w[3]);
 }
 
 // dL/dx += F(a) + 2 x F(b) + y F(c), added onto the L1 gradient already in grad
-__global__ void __launch_bounds__(256) k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt,
+__global__ void __launch_bounds__(128) k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt,
                                                   const dg_camera* __restrict__ cams, Win g,
                                                   const float* __restrict__ partial, float* __restrict__ grad)
 {
-    __shared__ float s_in[3][kInH][kInW];
-    __shared__ float s_tmp[3][kInH][kSW];
-    int v = blockIdx.z / 3, ch = blockIdx.z % 3;
-    int W = __ldg(&cams[v].width), H = __ldg(&cams[v].height);
-    int x0 = blockIdx.x * kSW, y0 = blockIdx.y * kSH;
+    __shared__ float s_p[3][kTI][kTI + 1];
+    __shared__ float s_tmp[3][kTI][kTS];
+    const int v = blockIdx.z / 3, ch = blockIdx.z % 3;
+    const int W = __ldg(&cams[v].width), H = __ldg(&cams[v].height);
+    const int x0 = blockIdx.x * kTS, y0 = blockIdx.y * kTS;
     if (x0 >= W || y0 >= H) return;
-    int64_t HW = (int64_t)W * H;
-    int64_t pix = __ldg(&cams[v].pix_off);
+    const int64_t HW = (int64_t)W * H;
+    const int64_t pix = __ldg(&cams[v].pix_off);
     const float* P = partial + 9 * pix + 3 * ch * HW;
-    for (int i = threadIdx.x; i < kInH * kInW; i += blockDim.x) {
-        int r = i / kInW, c = i % kInW;
-        int gx = x0 + c - kR, gy = y0 + r - kR;
-        bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        int64_t p = (int64_t)gy * W + gx;
+    for (int i = threadIdx.x; i < kTI * kTI; i += blockDim.x) {
+        const int r = i / kTI, c = i % kTI;
+        const int gx = x0 + c - kR, gy = y0 + r - kR;
+        const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const int64_t p = (int64_t)gy * W + gx;
 #pragma unroll
-        for (int m = 0; m < 3; m++) s_in[m][r][c] = ok ? P[m * HW + p] : 0.f;
+        for (int m = 0; m < 3; m++) s_p[m][r][c] = ok ? P[m * HW + p] : 0.f;
     }
     __syncthreads();
-    float fo[3][2];
-    filter_tile<3>(s_in, s_tmp, g, fo);
+    hpass<3>(g, s_tmp, [&](int r, int c, float (*in)[kWin8], int i) {
+        in[0][i] = s_p[0][r][c]; in[1][i] = s_p[1][r][c]; in[2][i] = s_p[2][r][c];
+    });
+    __syncthreads();
     const float* X = img + 3 * pix + ch * HW;
     const float* Y = tgt + 3 * pix + ch * HW;
     float* G = grad + 3 * pix + ch * HW;
+    for (int task = threadIdx.x; task < kTS * (kTS / kBlk); task += blockDim.x) {
+        const int c = task % kTS, r0 = (task / kTS) * kBlk;
+        float fo[3][kBlk];
+        vpass<3>(g, s_tmp, c, r0, fo);
+        const int gx = x0 + c;
 #pragma unroll
-    for (int e = 0; e < 2; e++) {
-        int c = threadIdx.x % kSW, r = threadIdx.x / kSW + 8 * e;
-        int gx = x0 + c, gy = y0 + r;
-        if (gx >= W || gy >= H) continue;
-        int64_t p = (int64_t)gy * W + gx;
-        G[p] += fo[0][e] + 2.f * X[p] * fo[1][e] + Y[p] * fo[2][e];
+        for (int j = 0; j < kBlk; j++) {
+            const int gy = y0 + r0 + j;
+            if (gx >= W || gy >= H) continue;
+            const int64_t p = (int64_t)gy * W + gx;
+            G[p] += fo[0][j] + 2.f * X[p] * fo[1][j] + Y[p] * fo[2][j];
+        }
     }
 }
 
@@ -213,10 +241,10 @@ int launch_loss(const float* img, const float* tgt, const dg_camera* cams, const
         float* partial = (float*)((char*)ws + sums_bytes(plan));
         if (cudaMemsetAsync(ssum, 0, (size_t)plan.n_views * sizeof(double), st) != cudaSuccess) return DG_ERR_CUDA;
         Win g = gaussian_window();
-        dim3 grid((unsigned)((plan.max_width + kSW - 1) / kSW), (unsigned)((plan.max_height + kSH - 1) / kSH),
+        dim3 grid((unsigned)((plan.max_width + kTS - 1) / kTS), (unsigned)((plan.max_height + kTS - 1) / kTS),
                   (unsigned)(3 * plan.n_views));
-        k_ssim_fwd<<<grid, 256, 0, st>>>(img, tgt, cams, g, w_ssim, ssum, partial);
-        k_ssim_bwd<<<grid, 256, 0, st>>>(img, tgt, cams, g, partial, grad);
+        k_ssim_fwd<<<grid, 128, 0, st>>>(img, tgt, cams, g, w_ssim, ssum, partial);
+        k_ssim_bwd<<<grid, 128, 0, st>>>(img, tgt, cams, g, partial, grad);
         note_launch(2);
     }
     k_loss_final<<<(plan.n_views + 127) / 128, 128, 0, st>>>(cams, plan.n_views, w_l1, w_ssim, ssum, loss);

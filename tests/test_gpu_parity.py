@@ -343,3 +343,36 @@ def test_every_compositing_variant_matches_oracle(D, oracle, warps, stage):
         check_backward(D, O, g, grads, ob, 2)
     finally:
         D.set_raster_variant(4, 2)
+
+
+def test_consensus_with_many_copies_per_global(D, oracle):
+    """Globals held by 1 to 7 blocks: the batched fast path (up to four
+    copies) and the generic path (more) against the oracle."""
+    O = oracle
+    rng = np.random.default_rng(21)
+    n_glob, K = 600, 8
+    members = [np.sort(rng.choice(K, rng.integers(1, 8), replace=False)) for _ in range(n_glob)]
+    gid = np.array([i for k in range(K) for i in range(n_glob) if k in members[i]], np.int32)
+    g_cp = np.argsort(gid, kind="stable").astype(np.int32)
+    g_off = np.concatenate([[0], np.cumsum(np.bincount(gid, minlength=n_glob))]).astype(np.int64)
+    base = S.cube_scene(n_glob, 5, sh_degree=1)
+    x = base.subset(gid)
+    jit = lambda a, s: (a + S.random_like(s, a.shape, 0.1)).astype(np.float32)
+    x = S.Gaussians(jit(x.means, 1), jit(x.quats, 2), jit(x.log_scales, 3), jit(x.opacity_logits, 4), jit(x.sh, 5))
+    u = S.Gaussians(*(S.random_like(10 + i, a.shape, 0.05) for i, a in
+                      enumerate((x.means, x.quats, x.log_scales, x.opacity_logits, x.sh))))
+    xb, ub, zb = D.GaussianBuffer.from_synth(x), D.GaussianBuffer.from_synth(u), D.GaussianBuffer.from_synth(base)
+    an = xb.like()
+    res = torch.zeros(10, dtype=torch.float64, device="cuda")
+    rho = [1.0, 2.0, 3.0, 4.0, 5.0]
+    D.dg_admm_consensus(xb, ub, zb, an, torch.from_numpy(g_off).cuda(), torch.from_numpy(g_cp).cuda(), rho, 1.4, res)
+    torch.cuda.synchronize()
+    ox, ou, oz = O.params_from(x), O.params_from(u), O.params_from(base)
+    ores = O.consensus(ox, ou, oz, g_off, g_cp, 1, alpha=1.4, rho=rho)
+    zg, ug = zb.to_synth(), ub.to_synth()
+    oz_g, ou_g = oracle_params_groups(O, oz, 1), oracle_params_groups(O, ou, 1)
+    for name in GROUPS:
+        assert rel_l2(getattr(zg, name), oz_g[name]) < REL_L2, ("z", name)
+        assert rel_l2(getattr(ug, name), ou_g[name]) < REL_L2, ("u", name)
+    np.testing.assert_allclose(res.cpu().numpy(), ores, rtol=1e-3)
+    assert np.diff(g_off).max() > 4
