@@ -235,6 +235,7 @@ __device__ __noinline__ void cons_generic(GView x, GView u, GView z, GView an, i
     }
 }
 
+template <int NP>
 __global__ void __launch_bounds__(128) k_consensus(GView x, GView u, GView z, GView an,
                                                    const int64_t* __restrict__ g_off,
                                                    const int32_t* __restrict__ g_copies, int64_t n_glob,
@@ -249,11 +250,17 @@ __global__ void __launch_bounds__(128) k_consensus(GView x, GView u, GView z, GV
         const int n = (int)(g_off[i + 1] - b);
         const int32_t* cpg = g_copies + b;
         if (n == 1) {
+            // unshared: z = x; every load is issued before the first store
             const int64_t c = cpg[0];
-            z.mo[i] = x.mo[c];
-            z.quat[i] = x.quat[c];
-            z.scale[i] = x.scale[c];
-            for (int j = 0; j < a.n_planes; j++) z.sh[(int64_t)j * z.ld + i] = x.sh[(int64_t)j * x.ld + c];
+            const float4 m0 = x.mo[c], q0 = x.quat[c], s0 = x.scale[c];
+            float f[NP];
+#pragma unroll
+            for (int j = 0; j < NP; j++) f[j] = x.sh[(int64_t)j * x.ld + c];
+            z.mo[i] = m0;
+            z.quat[i] = q0;
+            z.scale[i] = s0;
+#pragma unroll
+            for (int j = 0; j < NP; j++) z.sh[(int64_t)j * z.ld + i] = f[j];
         } else if (n > 1 && n <= kFast) {
             int32_t cp[kFast];
 #pragma unroll
@@ -263,30 +270,42 @@ __global__ void __launch_bounds__(128) k_consensus(GView x, GView u, GView z, GV
             cons_field4(x.quat, u.quat, an.quat, z.quat, i, cp, n, g_q, a.alpha, a.rho, r);
             cons_field4(x.scale, u.scale, an.scale, z.scale, i, cp, n, g_s, a.alpha, a.rho, r);
             const float inv = 1.f / (float)n;
-            for (int j = 0; j < a.n_planes; j++) {
-                const float* X = x.sh + (int64_t)j * x.ld;
-                float* U = u.sh + (int64_t)j * u.ld;
-                float* A = an.sh + (int64_t)j * an.ld;
-                float xs[kFast], us[kFast];
+            constexpr int CH = 4;   // planes per batch of loads
 #pragma unroll
-                for (int k = 0; k < kFast; k++)
-                    if (k < n) { xs[k] = X[cp[k]]; us[k] = U[cp[k]]; }
-                const float zo = z.sh[(int64_t)j * z.ld + i];
-                float acc = 0.f;
+            for (int j0 = 0; j0 < NP; j0 += CH) {
+                float xs[CH][kFast], us[CH][kFast], zo[CH];
 #pragma unroll
-                for (int k = 0; k < kFast; k++)
-                    if (k < n) acc += a.alpha * xs[k] + (1.f - a.alpha) * zo + us[k];
-                const float zn = acc * inv;
+                for (int jj = 0; jj < CH; jj++) {
+                    const int j = j0 + jj;
+                    if (j >= NP) continue;
+                    zo[jj] = z.sh[(int64_t)j * z.ld + i];
 #pragma unroll
-                for (int k = 0; k < kFast; k++)
-                    if (k < n) {
-                        const float un = us[k] + a.alpha * xs[k] + (1.f - a.alpha) * zo - zn;
-                        U[cp[k]] = un;
-                        A[cp[k]] = zn - un;
-                        r.rp[3] += (xs[k] - zn) * (xs[k] - zn);
-                    }
-                z.sh[(int64_t)j * z.ld + i] = zn;
-                r.rd[3] += a.rho[3] * a.rho[3] * (float)n * (zn - zo) * (zn - zo);
+                    for (int k = 0; k < kFast; k++)
+                        if (k < n) {
+                            xs[jj][k] = x.sh[(int64_t)j * x.ld + cp[k]];
+                            us[jj][k] = u.sh[(int64_t)j * u.ld + cp[k]];
+                        }
+                }
+#pragma unroll
+                for (int jj = 0; jj < CH; jj++) {
+                    const int j = j0 + jj;
+                    if (j >= NP) continue;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < kFast; k++)
+                        if (k < n) acc += a.alpha * xs[jj][k] + (1.f - a.alpha) * zo[jj] + us[jj][k];
+                    const float zn = acc * inv;
+#pragma unroll
+                    for (int k = 0; k < kFast; k++)
+                        if (k < n) {
+                            const float un = us[jj][k] + a.alpha * xs[jj][k] + (1.f - a.alpha) * zo[jj] - zn;
+                            u.sh[(int64_t)j * u.ld + cp[k]] = un;
+                            an.sh[(int64_t)j * an.ld + cp[k]] = zn - un;
+                            r.rp[3] += (xs[jj][k] - zn) * (xs[jj][k] - zn);
+                        }
+                    z.sh[(int64_t)j * z.ld + i] = zn;
+                    r.rd[3] += a.rho[3] * a.rho[3] * (float)n * (zn - zo[jj]) * (zn - zo[jj]);
+                }
             }
         } else if (n > kFast) {
             cons_generic(x, u, z, an, i, cpg, n, a, r);
@@ -363,8 +382,13 @@ int launch_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z, dg
     for (int i = 0; i < 5; i++) a.rho[i] = rho[i];
     a.alpha = alpha;
     a.n_planes = 3 * sh_coefs(x->sh_degree);
-    k_consensus<<<(unsigned)((z->n + 127) / 128), 128, 0, st>>>(gview(x), gview(u), gview(z), gview(an), g_off,
-                                                                 g_copies, z->n, a, res);
+    const unsigned grid = (unsigned)((z->n + 127) / 128);
+    switch (x->sh_degree) {
+    case 0: k_consensus<3><<<grid, 128, 0, st>>>(gview(x), gview(u), gview(z), gview(an), g_off, g_copies, z->n, a, res); break;
+    case 1: k_consensus<12><<<grid, 128, 0, st>>>(gview(x), gview(u), gview(z), gview(an), g_off, g_copies, z->n, a, res); break;
+    case 2: k_consensus<27><<<grid, 128, 0, st>>>(gview(x), gview(u), gview(z), gview(an), g_off, g_copies, z->n, a, res); break;
+    default: k_consensus<48><<<grid, 128, 0, st>>>(gview(x), gview(u), gview(z), gview(an), g_off, g_copies, z->n, a, res); break;
+    }
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;
