@@ -177,10 +177,13 @@ __global__ void __launch_bounds__(128) k_ssim_fwd(const float* __restrict__ img,
     if (threadIdx.x == 0) atomicAdd(&sums[v], (double)s_w[0] + s_w[1] + s_w[2] + s_w[3]);
 }
 
-// dL/dx += F(a) + 2 x F(b) + y F(c), added onto the L1 gradient already in grad
+// dL/dx = w_l1 sign(x - y) / N + F(a) + 2 x F(b) + y F(c); the L1 sum of the
+// tile is added to l1_sum[v].  The output pixels' x and y are loaded before the
+// filter passes so that their latency overlaps the shared-memory work.
 __global__ void __launch_bounds__(128) k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt,
-                                                  const dg_camera* __restrict__ cams, Win g,
-                                                  const float* __restrict__ partial, float* __restrict__ grad)
+                                                  const dg_camera* __restrict__ cams, Win g, float w_l1,
+                                                  const float* __restrict__ partial, float* __restrict__ grad,
+                                                  double* __restrict__ l1_sum)
 {
     __shared__ float s_p[3][kTI][kTI + 1];
     __shared__ float s_tmp[3][kTI][kTS];
@@ -191,35 +194,55 @@ __global__ void __launch_bounds__(128) k_ssim_bwd(const float* __restrict__ img,
     const int64_t HW = (int64_t)W * H;
     const int64_t pix = __ldg(&cams[v].pix_off);
     const float* P = partial + 9 * pix + 3 * ch * HW;
-    for (int i = threadIdx.x; i < kTI * kTI; i += blockDim.x) {
-        const int r = i / kTI, c = i % kTI;
-        const int gx = x0 + c - kR, gy = y0 + r - kR;
-        const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const int64_t p = (int64_t)gy * W + gx;
-#pragma unroll
-        for (int m = 0; m < 3; m++) s_p[m][r][c] = ok ? P[m * HW + p] : 0.f;
-    }
-    __syncthreads();
-    hpass<3>(g, s_tmp, [&](int r, int c, float (*in)[kWin8], int i) {
-        in[0][i] = s_p[0][r][c]; in[1][i] = s_p[1][r][c]; in[2][i] = s_p[2][r][c];
-    });
-    __syncthreads();
     const float* X = img + 3 * pix + ch * HW;
     const float* Y = tgt + 3 * pix + ch * HW;
     float* G = grad + 3 * pix + ch * HW;
-    for (int task = threadIdx.x; task < kTS * (kTS / kBlk); task += blockDim.x) {
-        const int c = task % kTS, r0 = (task / kTS) * kBlk;
-        float fo[3][kBlk];
-        vpass<3>(g, s_tmp, c, r0, fo);
-        const int gx = x0 + c;
+    // this thread's outputs: column c, rows r0 .. r0 + 7 (one task per thread)
+    const int c = threadIdx.x % kTS, r0 = (threadIdx.x / kTS) * kBlk;
+    const int gx = x0 + c;
+    float xv[kBlk], yv[kBlk];
 #pragma unroll
-        for (int j = 0; j < kBlk; j++) {
-            const int gy = y0 + r0 + j;
-            if (gx >= W || gy >= H) continue;
-            const int64_t p = (int64_t)gy * W + gx;
-            G[p] += fo[0][j] + 2.f * X[p] * fo[1][j] + Y[p] * fo[2][j];
-        }
+    for (int j = 0; j < kBlk; j++) {
+        const int gy = y0 + r0 + j;
+        const bool ok = gx < W && gy < H;
+        const int64_t p = (int64_t)gy * W + gx;
+        xv[j] = ok ? X[p] : 0.f;
+        yv[j] = ok ? Y[p] : 0.f;
     }
+#pragma unroll 4
+    for (int i = threadIdx.x; i < kTI * kTI; i += blockDim.x) {
+        const int r = i / kTI, cc = i % kTI;
+        const int hx = x0 + cc - kR, hy = y0 + r - kR;
+        const bool ok = hx >= 0 && hx < W && hy >= 0 && hy < H;
+        const int64_t p = (int64_t)hy * W + hx;
+#pragma unroll
+        for (int m = 0; m < 3; m++) s_p[m][r][cc] = ok ? P[m * HW + p] : 0.f;
+    }
+    __syncthreads();
+    hpass<3>(g, s_tmp, [&](int r, int cc, float (*in)[kWin8], int i) {
+        in[0][i] = s_p[0][r][cc]; in[1][i] = s_p[1][r][cc]; in[2][i] = s_p[2][r][cc];
+    });
+    __syncthreads();
+    float fo[3][kBlk];
+    vpass<3>(g, s_tmp, c, r0, fo);
+    const float wl = w_l1 / (float)(3 * HW);
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < kBlk; j++) {
+        const int gy = y0 + r0 + j;
+        if (gx >= W || gy >= H) continue;
+        const int64_t p = (int64_t)gy * W + gx;
+        const float d = xv[j] - yv[j];
+        acc += fabsf(d);
+        const float l1g = d > 0.f ? wl : (d < 0.f ? -wl : 0.f);
+        G[p] = l1g + fo[0][j] + 2.f * xv[j] * fo[1][j] + yv[j] * fo[2][j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ float s_w[4];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&l1_sum[v], (double)s_w[0] + s_w[1] + s_w[2] + s_w[3]);
 }
 
 static size_t sums_bytes(const dg_plan& plan) { return ((size_t)plan.n_views * sizeof(double) + 255) / 256 * 256; }
@@ -231,12 +254,15 @@ int launch_loss(const float* img, const float* tgt, const dg_camera* cams, const
                 float w_ssim, double* loss, float* grad, void* ws, cudaStream_t st)
 {
     if (cudaMemsetAsync(loss, 0, (size_t)plan.n_views * sizeof(double), st) != cudaSuccess) return DG_ERR_CUDA;
-    int64_t nblk = (3 * (int64_t)plan.max_width * plan.max_height + 255) / 256;
-    unsigned gx = (unsigned)(nblk < 2048 ? nblk : 2048);
-    k_l1<<<dim3(gx, plan.n_views), 256, 0, st>>>(img, tgt, cams, w_l1, loss, grad);
-    note_launch();
     double* ssum = nullptr;
-    if (w_ssim != 0.f) {
+    if (w_ssim == 0.f) {
+        int64_t nblk = (3 * (int64_t)plan.max_width * plan.max_height + 255) / 256;
+        unsigned gx = (unsigned)(nblk < 2048 ? nblk : 2048);
+        k_l1<<<dim3(gx, plan.n_views), 256, 0, st>>>(img, tgt, cams, w_l1, loss, grad);
+        note_launch();
+    } else {
+        // SSIM forward (moments, map, partials), then one backward pass that
+        // writes the whole gradient (L1 + SSIM terms) and the L1 sums
         ssum = (double*)ws;
         float* partial = (float*)((char*)ws + sums_bytes(plan));
         if (cudaMemsetAsync(ssum, 0, (size_t)plan.n_views * sizeof(double), st) != cudaSuccess) return DG_ERR_CUDA;
@@ -244,7 +270,7 @@ int launch_loss(const float* img, const float* tgt, const dg_camera* cams, const
         dim3 grid((unsigned)((plan.max_width + kTS - 1) / kTS), (unsigned)((plan.max_height + kTS - 1) / kTS),
                   (unsigned)(3 * plan.n_views));
         k_ssim_fwd<<<grid, 128, 0, st>>>(img, tgt, cams, g, w_ssim, ssum, partial);
-        k_ssim_bwd<<<grid, 128, 0, st>>>(img, tgt, cams, g, partial, grad);
+        k_ssim_bwd<<<grid, 128, 0, st>>>(img, tgt, cams, g, w_l1, partial, grad, loss);
         note_launch(2);
     }
     k_loss_final<<<(plan.n_views + 127) / 128, 128, 0, st>>>(cams, plan.n_views, w_l1, w_ssim, ssum, loss);

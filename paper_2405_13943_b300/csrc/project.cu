@@ -197,8 +197,8 @@ __device__ __forceinline__ bool geom(const CamL& cam, double tzd, float3 mu, flo
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(256) k_project(GView x, const dg_camera* __restrict__ cams, dg_plan plan,
-                                                 float4* __restrict__ rec, uint2* __restrict__ rect)
+__global__ void __launch_bounds__(256, 4) k_project(GView x, const dg_camera* __restrict__ cams, dg_plan plan,
+                                                    float4* __restrict__ rec, uint2* __restrict__ rect)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -206,12 +206,12 @@ __global__ void __launch_bounds__(256) k_project(GView x, const dg_camera* __res
     int k = find_block(plan, c);
     int v0 = plan.blk_view_off[k], v1 = plan.blk_view_off[k + 1];
     if (v0 == v1) return;
-    float4 mo = x.mo[c];
-    float3 mu = make_float3(mo.x, mo.y, mo.z);
+    const float4 mo = x.mo[c];
+    const float3 mu = make_float3(mo.x, mo.y, mo.z);
     bool loaded = false;
     float4 q = make_float4(0, 0, 0, 0), sc = make_float4(0, 0, 0, 0);
-    float f[3 * NK];
     float opac = 0.f;
+    const float* __restrict__ shp = x.sh + c;
     for (int v = v0; v < v1; v++) {
         CamL cam;
         load_cam(cams, v, cam);
@@ -221,8 +221,6 @@ __global__ void __launch_bounds__(256) k_project(GView x, const dg_camera* __res
         if (!loaded) {   // the rest of the parameters only for copies in front of some camera
             q = x.quat[c];
             sc = x.scale[c];
-#pragma unroll
-            for (int j = 0; j < 3 * NK; j++) f[j] = x.sh[(int64_t)j * x.ld + c];
             opac = 1.f / (1.f + __expf(-mo.w));
             loaded = true;
         }
@@ -233,17 +231,15 @@ __global__ void __launch_bounds__(256) k_project(GView x, const dg_camera* __res
         float il = rsqrtf(dx * dx + dy * dy + dz * dz);
         float Y[NK];
         sh_eval<DEG>(dx * il, dy * il, dz * il, Y);
-        float col[3];
+        // colour: SH coefficients streamed from their planes (coalesced across the warp)
+        float col[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-        for (int ch = 0; ch < 3; ch++) {
-            float s = 0.5f;
+        for (int kk = 0; kk < NK; kk++)
 #pragma unroll
-            for (int kk = 0; kk < NK; kk++) s = fmaf(f[3 * kk + ch], Y[kk], s);
-            col[ch] = fmaxf(s, 0.f);
-        }
+            for (int ch = 0; ch < 3; ch++) col[ch] = fmaf(__ldg(shp + (int64_t)(3 * kk + ch) * x.ld), Y[kk], col[ch]);
         rec[3 * r + 0] = make_float4(g.mx, g.my, g.a, g.b);
-        rec[3 * r + 1] = make_float4(g.c, opac, col[0], col[1]);
-        rec[3 * r + 2] = make_float4(col[2], g.tz, 0.f, 0.f);
+        rec[3 * r + 1] = make_float4(g.c, opac, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
+        rec[3 * r + 2] = make_float4(fmaxf(col[2], 0.f), g.tz, 0.f, 0.f);
         rect[r] = rr;
     }
 }
@@ -252,9 +248,9 @@ __global__ void __launch_bounds__(256) k_project(GView x, const dg_camera* __res
 // K8: adjoint of the projection, accumulated over the views of the block.
 // ---------------------------------------------------------------------------
 template <int DEG>
-__global__ void __launch_bounds__(128) k_project_bwd(GView x, const dg_camera* __restrict__ cams, dg_plan plan,
-                                                     const uint2* __restrict__ rect,
-                                                     const float4* __restrict__ drec, GView gr)
+__global__ void __launch_bounds__(128, 4) k_project_bwd(GView x, const dg_camera* __restrict__ cams, dg_plan plan,
+                                                        const uint2* __restrict__ rect,
+                                                        const float4* __restrict__ drec, GView gr)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -262,15 +258,13 @@ __global__ void __launch_bounds__(128) k_project_bwd(GView x, const dg_camera* _
     int k = find_block(plan, c);
     int v0 = plan.blk_view_off[k], v1 = plan.blk_view_off[k + 1];
     float gmu[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gs[3] = {0, 0, 0}, go = 0.f;
-    float gf[3 * NK];
-#pragma unroll
-    for (int j = 0; j < 3 * NK; j++) gf[j] = 0.f;
-    float4 mo = x.mo[c];
-    float3 mu = make_float3(mo.x, mo.y, mo.z);
-    bool loaded = false;
+    const float4 mo = x.mo[c];
+    const float3 mu = make_float3(mo.x, mo.y, mo.z);
+    bool loaded = false, sh_written = false;
     float4 q = make_float4(0, 0, 0, 0), sc = make_float4(0, 0, 0, 0);
-    float f[3 * NK];
     float opac = 0.f;
+    const float* __restrict__ shp = x.sh + c;
+    float* __restrict__ gsh = gr.sh + c;
     for (int v = v0; v < v1; v++) {
         CamL cam;
         load_cam(cams, v, cam);
@@ -280,22 +274,23 @@ __global__ void __launch_bounds__(128) k_project_bwd(GView x, const dg_camera* _
         if (!loaded) {
             q = x.quat[c];
             sc = x.scale[c];
-#pragma unroll
-            for (int j = 0; j < 3 * NK; j++) f[j] = x.sh[(int64_t)j * x.ld + c];
             opac = 1.f / (1.f + __expf(-mo.w));
             loaded = true;
         }
-        float4 d0 = drec[3 * r + 0], d1 = drec[3 * r + 1], d2 = drec[3 * r + 2];
+        const float4 d0 = drec[3 * r + 0], d1 = drec[3 * r + 1], d2 = drec[3 * r + 2];
         Geom g;
         geom(cam, cam_depth(cam, mu), mu, q, sc, plan.tile_w, plan.tile_h, g, nullptr);  // forward's rect decides
         // opacity logit
         go += d1.y * opac * (1.f - opac);
-        // colour -> SH coefficients and the view direction
+        // colour -> SH coefficients and the view direction (coefficients streamed)
         float vx = mu.x - cam.cp[0], vy = mu.y - cam.cp[1], vz = mu.z - cam.cp[2];
         float il = rsqrtf(vx * vx + vy * vy + vz * vz);
         float ux = vx * il, uy = vy * il, uz = vz * il;
         float Y[NK];
         sh_eval<DEG>(ux, uy, uz, Y);
+        float f[3 * NK];
+#pragma unroll
+        for (int j = 0; j < 3 * NK; j++) f[j] = __ldg(shp + (int64_t)j * x.ld);
         float gc[3] = {d1.z, d1.w, d2.x};
 #pragma unroll
         for (int ch = 0; ch < 3; ch++) {
@@ -307,11 +302,15 @@ __global__ void __launch_bounds__(128) k_project_bwd(GView x, const dg_camera* _
         float wk[NK];
 #pragma unroll
         for (int kk = 0; kk < NK; kk++) {
-            gf[3 * kk + 0] += gc[0] * Y[kk];
-            gf[3 * kk + 1] += gc[1] * Y[kk];
-            gf[3 * kk + 2] += gc[2] * Y[kk];
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) {
+                const int64_t o = (int64_t)(3 * kk + ch) * gr.ld;
+                const float val = gc[ch] * Y[kk];
+                gsh[o] = sh_written ? gsh[o] + val : val;
+            }
             wk[kk] = gc[0] * f[3 * kk] + gc[1] * f[3 * kk + 1] + gc[2] * f[3 * kk + 2];
         }
+        sh_written = true;
         if (DEG > 0) {
             float3 gd = sh_grad_dot<DEG>(ux, uy, uz, wk);
             float dd = gd.x * ux + gd.y * uy + gd.z * uz;
@@ -396,8 +395,10 @@ __global__ void __launch_bounds__(128) k_project_bwd(GView x, const dg_camera* _
     gr.mo[c] = make_float4(gmu[0], gmu[1], gmu[2], go);
     gr.quat[c] = make_float4(gq[0], gq[1], gq[2], gq[3]);
     gr.scale[c] = make_float4(gs[0], gs[1], gs[2], 0.f);
+    if (!sh_written) {
 #pragma unroll
-    for (int j = 0; j < 3 * NK; j++) gr.sh[(int64_t)j * gr.ld + c] = gf[j];
+        for (int j = 0; j < 3 * NK; j++) gsh[(int64_t)j * gr.ld] = 0.f;
+    }
 }
 
 int launch_project(const dg_gaussians* x, const dg_camera* cams, const dg_plan& plan, float4* rec, uint2* rect,

@@ -275,23 +275,21 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd(const float4* __restrict
             const uint32_t pos = base + (uint32_t)j;
             const float4 g = s_g[j];
             const float4 h = s_h[j];
-            // per-lane moments over the thread's pixels: S0 = sum dL/dpower,
-            // Sx, Sy, Sxx, Sxy, Syy its dx / dy moments, then the colour terms
-            float mo[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            float gr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             float g8 = 0.f;
             bool any = false;
-            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 c = make_float4(0.f, 0.f, 0.f, 0.f), kc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
                 if (pos >= last[k]) continue;
                 float dx, dy, raw = 0.f;
                 const float a = pair_alpha(g.x, g.y, g.z, g.w, h.x, h.y, Lg.fx, Lg.fy0 + k * Lg.dy, dx, dy, raw);
                 if (!(a > 0.f)) continue;
-                if (!any) { c = s_c[j]; any = true; }
+                if (!any) { c = s_c[j]; kc = s_k[j]; any = true; }
                 const float Tj = T[k] * __fdividef(1.f, 1.f - a);
                 const float wT = a * Tj;
-                mo[6] = fmaf(G0[k], wT, mo[6]);
-                mo[7] = fmaf(G1[k], wT, mo[7]);
+                gr[6] = fmaf(G0[k], wT, gr[6]);
+                gr[7] = fmaf(G1[k], wT, gr[7]);
                 g8 = fmaf(G2[k], wT, g8);
                 const float d0 = c.x - B0[k], d1 = c.y - B1[k], d2 = c.z - B2[k];
                 const float dLda = Tj * fmaf(G0[k], d0, fmaf(G1[k], d1, G2[k] * d2));
@@ -300,37 +298,23 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd(const float4* __restrict
                 B2[k] = fmaf(a, d2, B2[k]);
                 T[k] = Tj;
                 if (raw < kAlphaMax) {
-                    const float dLdp = dLda * a;     // d alpha / d power = alpha
-                    const float px = dLdp * dx, py = dLdp * dy;
-                    mo[0] += dLdp;
-                    mo[1] += px;
-                    mo[2] += py;
-                    mo[3] = fmaf(px, dx, mo[3]);
-                    mo[4] = fmaf(px, dy, mo[4]);
-                    mo[5] = fmaf(py, dy, mo[5]);
+                    const float dLdp = dLda * a;             // d alpha / d power = alpha
+                    gr[5] = fmaf(dLdp, h.z, gr[5]);         // d alpha / d opacity = alpha / opacity
+                    gr[0] = fmaf(-dLdp, kc.x * dx + kc.y * dy, gr[0]);
+                    gr[1] = fmaf(-dLdp, kc.y * dx + kc.z * dy, gr[1]);
+                    gr[2] = fmaf(-0.5f * dLdp, dx * dx, gr[2]);
+                    gr[3] = fmaf(-dLdp, dx * dy, gr[3]);
+                    gr[4] = fmaf(-0.5f * dLdp, dy * dy, gr[4]);
                 }
             }
             if (!__any_sync(0xffffffffu, any)) continue;
-            const float sred = warp_reduce_scatter8(mo, g8, lane);
-            // lane with value index vi holds moment vi; the mean gradient needs
-            // both Sx (vi 1, lane 4) and Sy (vi 2, lane 8)
-            const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-            const float other = __shfl_sync(0xffffffffu, sred, lane == 4 ? 8 : (lane == 8 ? 4 : lane));
+            const float sred = warp_reduce_scatter8(gr, g8, lane);
+            float* d = drec + 12 * (int64_t)__float_as_uint(h.w);
             if ((lane & 3) == 0) {
-                const float4 kc = s_k[j];
-                float val;
-                if (vi == 0) val = sred * h.z;                          // d opacity = S0 / o
-                else if (vi == 1) val = -(kc.x * sred + kc.y * other);  // d mean.x = -(a Sx + b Sy)
-                else if (vi == 2) val = -(kc.y * other + kc.z * sred);  // d mean.y = -(b Sx + c Sy)
-                else if (vi == 3) val = -0.5f * sred;                   // d conic.a
-                else if (vi == 4) val = -sred;                          // d conic.b
-                else if (vi == 5) val = -0.5f * sred;                   // d conic.c
-                else val = sred;                                        // colour r, g
-                const int slot = vi == 0 ? 5 : (vi <= 2 ? vi - 1 : (vi <= 5 ? vi - 1 : vi));
-                float* d = drec + 12 * (int64_t)__float_as_uint(h.w);
-                if (val != 0.f) atomicAdd(d + slot, val);
+                const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                if (sred != 0.f) atomicAdd(d + vi, sred);
             }
-            if (lane == 0 && g8 != 0.f) atomicAdd(drec + 12 * (int64_t)__float_as_uint(h.w) + 8, g8);
+            if (lane == 0 && g8 != 0.f) atomicAdd(d + 8, g8);
         }
     }
 }
