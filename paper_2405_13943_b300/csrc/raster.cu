@@ -63,6 +63,53 @@ __device__ __forceinline__ LaneGeom lane_geom(const TileInfo& ti, int tw, int ti
     return L;
 }
 
+// The exponent (log2 units) of one instance along a thread's strip of PPL
+// pixels (fixed column, rows fy0 + k dy): p(k) = p0 + beta k + gamma k^2 with
+// dx = mx - fx, dy_k = my - fy0 - k dy.  It is evaluated by the exact
+// second-order recurrence p += d1, d1 += 2 gamma (same instructions in the
+// forward and the backward, so both take the same decisions), and the strip's
+// largest value bounds every pixel of it: when even that gives alpha < 2^-8
+// the whole strip skips the instance.
+struct Strip {
+    float p, d1, d2, pmax;
+};
+
+template <int PPL>
+__device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float B, float C, float fx, float fy0,
+                                             float ddy)
+{
+    Strip st;
+    const float dx = __fsub_rn(mx, fx), dy0 = __fsub_rn(my, fy0);
+    const float t = __fmaf_rn(B, dy0, __fmul_rn(A, dx));
+    st.p = __fmaf_rn(__fmul_rn(C, dy0), dy0, __fmul_rn(dx, t));
+    const float beta = __fmul_rn(-ddy, __fmaf_rn(2.f * C, dy0, __fmul_rn(B, dx)));
+    const float gamma = __fmul_rn(C, __fmul_rn(ddy, ddy));
+    st.d1 = __fadd_rn(beta, gamma);
+    st.d2 = __fmul_rn(2.f, gamma);
+    if (PPL == 1) {
+        st.pmax = st.p;
+    } else {
+        // concave in k (gamma < 0): largest at the vertex, clamped to [0, PPL-1]
+        float ks = gamma < 0.f ? fminf(fmaxf(-beta / (2.f * gamma), 0.f), (float)(PPL - 1)) : 0.f;
+        float pv = st.p + ks * (beta + gamma * ks);
+        float pe = st.p + (float)(PPL - 1) * (beta + gamma * (float)(PPL - 1));
+        st.pmax = fmaxf(fmaxf(pv, pe), st.p) + 1e-3f;   // margin over rounding
+    }
+    return st;
+}
+
+// alpha of the strip's current pixel from its exponent p (0 = skipped)
+__device__ __forceinline__ float strip_alpha(float p, float lo, float& raw)
+{
+    if (p > 0.0f) return 0.0f;
+    const float e = __fadd_rn(p, lo);
+    if (e < -8.0f) return 0.0f;          // alpha <= 1/256 < 1/255
+    raw = exp2f(e);
+    const float a = fminf(raw, kAlphaMax);
+    if (a < kAlphaMin) return 0.0f;
+    return a;
+}
+
 struct Fetch {
     float4 r0, r1, r2;
     uint32_t r;
@@ -134,13 +181,17 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
         for (uint32_t j = 0; j < cnt && live; j++) {
             const float4 g = s_g[j];
             const float2 h = s_h[j];
+            Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, G.fx, G.fy0, G.dy);
+            if (__fadd_rn(sp.pmax, h.y) < -8.0f) continue;   // no pixel of the strip reaches 2^-8
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
             bool have_c = false;
+            float p = sp.p, inc = sp.d1;
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
+                if (k > 0) { p = __fadd_rn(p, inc); inc = __fadd_rn(inc, sp.d2); }
                 if (!(live >> k & 1u)) continue;
-                float dx, dy, raw;
-                const float a = pair_alpha(g.x, g.y, g.z, g.w, h.x, h.y, G.fx, G.fy0 + k * G.dy, dx, dy, raw);
+                float raw;
+                const float a = strip_alpha(p, h.y, raw);
                 if (a == 0.f) continue;
                 const float Tn = T[k] * (1.f - a);
                 if (Tn < kTMin) { live &= ~(1u << k); continue; }
@@ -279,12 +330,18 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd(const float4* __restrict
             float g8 = 0.f;
             bool any = false;
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f), kc = make_float4(0.f, 0.f, 0.f, 0.f);
+            Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, Lg.fx, Lg.fy0, Lg.dy);
+            const bool reach = __fadd_rn(sp.pmax, h.y) >= -8.0f;
+            float p = sp.p, inc = sp.d1;
+            const float dx = g.x - Lg.fx;
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
-                if (pos >= last[k]) continue;
-                float dx, dy, raw = 0.f;
-                const float a = pair_alpha(g.x, g.y, g.z, g.w, h.x, h.y, Lg.fx, Lg.fy0 + k * Lg.dy, dx, dy, raw);
+                if (k > 0) { p = __fadd_rn(p, inc); inc = __fadd_rn(inc, sp.d2); }
+                if (!reach || pos >= last[k]) continue;
+                float raw = 0.f;
+                const float a = strip_alpha(p, h.y, raw);
                 if (!(a > 0.f)) continue;
+                const float dy = g.y - (Lg.fy0 + k * Lg.dy);
                 if (!any) { c = s_c[j]; kc = s_k[j]; any = true; }
                 const float Tj = T[k] * __fdividef(1.f, 1.f - a);
                 const float wT = a * Tj;
