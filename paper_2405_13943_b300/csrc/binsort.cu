@@ -26,11 +26,12 @@ constexpr int kSmallCap = 2048;                       // segment sorted by a 256
 constexpr int kBigCap = 16384;                        // segment sorted by a 1024-thread CTA in smem
 
 struct BinWs {
-    uint32_t* counts;     // n_tiles + 2 (two list counters at the end), zeroed
+    uint32_t* counts;     // n_tiles + 3 (three list counters at the end), zeroed
     uint32_t* cursor;     // n_tiles
     uint32_t* partials;   // n_chunks + 1
     uint32_t* big_list;   // n_tiles
     uint32_t* huge_list;  // n_tiles
+    uint32_t* mid_list;   // n_tiles
     uint64_t* pairs;      // capacity
 };
 
@@ -42,11 +43,12 @@ static size_t bin_ws_layout(int64_t n_tiles, int64_t capacity, BinWs* w, char* b
     size_t off = 0;
     auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align256(bytes); return p; };
     BinWs t;
-    t.counts = (uint32_t*)take(4 * (size_t)(n_tiles + 2));
+    t.counts = (uint32_t*)take(4 * (size_t)(n_tiles + 3));
     t.cursor = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.partials = (uint32_t*)take(4 * (size_t)(n_chunks + 1));
     t.big_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.huge_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
+    t.mid_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.pairs = (uint64_t*)take(8 * (size_t)(capacity > 0 ? capacity : 1));
     if (w) *w = t;
     return off;
@@ -234,26 +236,112 @@ __device__ __forceinline__ void write_segment(const uint64_t* s, uint32_t n, uin
     }
 }
 
-__global__ void __launch_bounds__(256) k_sort_small(const uint32_t* __restrict__ ranges, int64_t n_tiles,
-                                                    const uint64_t* __restrict__ pairs, uint32_t* __restrict__ vals,
-                                                    uint64_t* __restrict__ keys, uint32_t* __restrict__ counters,
-                                                    uint32_t* __restrict__ big_list, uint32_t* __restrict__ huge_list)
+// Segments of up to 256 instances: one warp per tile, a bitonic network on
+// 64-bit (depth bits, record) keys held in registers -- element e = i * 32 +
+// lane in register i of the lane -- with lane shuffles for distances below 32
+// and register exchanges above; positions >= n hold +infinity.  No barriers.
+template <int NR>
+__device__ __forceinline__ void warp_bitonic(uint64_t* v, int lane)
 {
-    __shared__ uint64_t s[kSmallCap];
-    int64_t t = blockIdx.x;
-    uint32_t start = ranges[2 * t], n = ranges[2 * t + 1] - start;
+    constexpr int N = 32 * NR;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int ri = j >> 5;
+#pragma unroll
+                for (int i = 0; i < NR; i++) {
+                    if (i & ri) continue;
+                    const int e = i * 32 + lane;
+                    const bool asc = (e & k) == 0;
+                    const uint64_t a = v[i], b = v[i | ri];
+                    const bool sw = asc ? (a > b) : (a < b);
+                    v[i] = sw ? b : a;
+                    v[i | ri] = sw ? a : b;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < NR; i++) {
+                    const int e = i * 32 + lane;
+                    const bool asc = (e & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    const uint64_t w = __shfl_xor_sync(0xffffffffu, v[i], j);
+                    const uint64_t mn = v[i] < w ? v[i] : w, mx = v[i] < w ? w : v[i];
+                    v[i] = (lower == asc) ? mn : mx;
+                }
+            }
+        }
+    }
+}
+
+template <int NR>
+__device__ __forceinline__ void warp_sort_segment(const uint64_t* __restrict__ pairs, uint32_t start, uint32_t n,
+                                                  uint64_t tile, uint32_t* __restrict__ vals,
+                                                  uint64_t* __restrict__ keys, int lane)
+{
+    uint64_t v[NR];
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        const uint32_t e = (uint32_t)(i * 32 + lane);
+        v[i] = e < n ? pairs[start + e] : ~0ull;
+    }
+    warp_bitonic<NR>(v, lane);
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        const uint32_t e = (uint32_t)(i * 32 + lane);
+        if (e < n) {
+            vals[start + e] = (uint32_t)v[i];
+            if (keys) keys[start + e] = (tile << 32) | (v[i] >> 32);
+        }
+    }
+}
+
+constexpr int kWarpSortMax = 256;
+
+__global__ void __launch_bounds__(128) k_sort_warp(const uint32_t* __restrict__ ranges, int64_t n_tiles,
+                                                   const uint64_t* __restrict__ pairs, uint32_t* __restrict__ vals,
+                                                   uint64_t* __restrict__ keys, uint32_t* __restrict__ counters,
+                                                   uint32_t* __restrict__ mid_list, uint32_t* __restrict__ big_list,
+                                                   uint32_t* __restrict__ huge_list)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (t >= n_tiles) return;
+    const uint32_t start = ranges[2 * t], n = ranges[2 * t + 1] - start;
     if (n == 0) return;
-    if (n > kSmallCap) {
-        if (threadIdx.x == 0) {
-            if (n <= kBigCap) big_list[atomicAdd(&counters[0], 1u)] = (uint32_t)t;
+    if (n > kWarpSortMax) {
+        if (lane == 0) {
+            if (n <= kSmallCap) mid_list[atomicAdd(&counters[2], 1u)] = (uint32_t)t;
+            else if (n <= kBigCap) big_list[atomicAdd(&counters[0], 1u)] = (uint32_t)t;
             else huge_list[atomicAdd(&counters[1], 1u)] = (uint32_t)t;
         }
         return;
     }
-    for (uint32_t i = threadIdx.x; i < n; i += 256) s[i] = pairs[start + i];
-    __syncthreads();
-    bitonic_sort<256>(s, n);
-    write_segment(s, n, start, (uint64_t)t, vals, keys, 256);
+    if (n <= 32) warp_sort_segment<1>(pairs, start, n, (uint64_t)t, vals, keys, lane);
+    else if (n <= 64) warp_sort_segment<2>(pairs, start, n, (uint64_t)t, vals, keys, lane);
+    else if (n <= 128) warp_sort_segment<4>(pairs, start, n, (uint64_t)t, vals, keys, lane);
+    else warp_sort_segment<8>(pairs, start, n, (uint64_t)t, vals, keys, lane);
+}
+
+// Segments of 257 .. kSmallCap instances: one 256-thread CTA each, bitonic in
+// shared memory (persistent over the list filled by k_sort_warp).
+__global__ void __launch_bounds__(256) k_sort_small(const uint32_t* __restrict__ ranges,
+                                                    const uint64_t* __restrict__ pairs, uint32_t* __restrict__ vals,
+                                                    uint64_t* __restrict__ keys, const uint32_t* __restrict__ counters,
+                                                    const uint32_t* __restrict__ mid_list)
+{
+    __shared__ uint64_t s[kSmallCap];
+    const uint32_t nm = counters[2];
+    for (uint32_t i = blockIdx.x; i < nm; i += gridDim.x) {
+        const uint32_t t = mid_list[i];
+        const uint32_t start = ranges[2 * (int64_t)t], n = ranges[2 * (int64_t)t + 1] - start;
+        for (uint32_t j = threadIdx.x; j < n; j += 256) s[j] = pairs[start + j];
+        __syncthreads();
+        bitonic_sort<256>(s, n);
+        write_segment(s, n, start, (uint64_t)t, vals, keys, 256);
+        __syncthreads();
+    }
 }
 
 __global__ void __launch_bounds__(1024) k_sort_big(const uint32_t* __restrict__ ranges,
@@ -299,7 +387,7 @@ int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams,
     BinWs w;
     bin_ws_layout(plan.n_tiles, capacity, &w, (char*)ws);
     int64_t n_chunks = (plan.n_tiles + kScanChunk - 1) / kScanChunk;
-    if (cudaMemsetAsync(w.counts, 0, 4 * (size_t)(plan.n_tiles + 2), st) != cudaSuccess) return DG_ERR_CUDA;
+    if (cudaMemsetAsync(w.counts, 0, 4 * (size_t)(plan.n_tiles + 3), st) != cudaSuccess) return DG_ERR_CUDA;
     if (plan.n_rec > 0) {
         k_count<<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(rect, cams, plan.n_views, plan.n_rec, w.counts);
         note_launch();
@@ -315,11 +403,12 @@ int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams,
         note_launch();
     }
     uint32_t* counters = w.counts + plan.n_tiles;
-    k_sort_small<<<(unsigned)plan.n_tiles, 256, 0, st>>>(ranges, plan.n_tiles, w.pairs, vals, keys, counters,
-                                                         w.big_list, w.huge_list);
+    k_sort_warp<<<(unsigned)((plan.n_tiles + 3) / 4), 128, 0, st>>>(ranges, plan.n_tiles, w.pairs, vals, keys,
+                                                                    counters, w.mid_list, w.big_list, w.huge_list);
+    k_sort_small<<<148 * 4, 256, 0, st>>>(ranges, w.pairs, vals, keys, counters, w.mid_list);
     k_sort_big<<<148, 1024, kBigCap * sizeof(uint64_t), st>>>(ranges, w.pairs, vals, keys, counters, w.big_list);
     k_sort_huge<<<148, 1024, 0, st>>>(ranges, w.pairs, vals, keys, counters, w.huge_list);
-    note_launch(3);
+    note_launch(4);
     DG_CHECK_LAUNCH();
     return DG_OK;
 }
