@@ -244,6 +244,12 @@ int dg_admm_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z,
                       dg_gaussians* anchor, const int64_t* g_off, const int32_t* g_copies,
                       const float* rho, float alpha, double* residuals, void* stream);
 
+/* Adaptive penalty (Sec. 3.3, Eq. 10): when rho_grp changes to rho'_grp the
+ * scaled duals u = y / rho follow as u_grp *= rho_grp / rho'_grp.  This call
+ * multiplies each group of u on shared copies by factor[5] (host); rerun
+ * dg_admm_anchor afterwards. */
+int dg_admm_scale_duals(dg_gaussians* u, const uint8_t* copy_shared, const float* factor, void* stream);
+
 /* anchor_c = z_{copy_gid[c]} - u_c for every shared copy (initialisation). */
 int dg_admm_anchor(const dg_gaussians* z, const dg_gaussians* u, const int32_t* copy_gid,
                    const uint8_t* copy_shared, dg_gaussians* anchor, void* stream);

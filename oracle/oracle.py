@@ -362,3 +362,35 @@ def consensus(x, u, z, g_off, g_copies, sh_degree, alpha=1.0, rho=(1, 1, 1, 1, 1
                        _p(x, C.c_double), _p(u, C.c_double), _p(z, C.c_double), float(alpha),
                        _p(rr, C.c_double), _p(res, C.c_double))
     return res
+
+
+# --------------------------------------------------------------------------
+# adaptive penalty (Sec. 3.3, Eq. 10) and the rescale of the scaled duals
+# --------------------------------------------------------------------------
+def adaptive_rho(rho, residuals, t, mu=10.0, tau_inc=2.0, tau_dec=2.0, freeze_after=2000):
+    """Eq. 10 per property group: rho * tau_inc if ||r|| > mu ||s||,
+    rho / tau_dec if ||s|| > mu ||r||, rho otherwise; no change from
+    iteration `freeze_after` on.  residuals = (||r_g||^2 for g in p,q,s,f,o)
+    followed by (||s_g||^2 ...)."""
+    out = []
+    for g in range(5):
+        r = float(np.sqrt(residuals[g]))
+        s = float(np.sqrt(residuals[5 + g]))
+        if t >= freeze_after:
+            out.append(float(rho[g]))
+        elif r > mu * s:
+            out.append(float(rho[g]) * tau_inc)
+        elif s > mu * r:
+            out.append(float(rho[g]) / tau_dec)
+        else:
+            out.append(float(rho[g]))
+    return out
+
+
+def scale_duals(u, shared, factor, sh_degree):
+    """u <- u * factor[group] on shared copies (u = y / rho keeps y fixed
+    when rho changes)."""
+    K = (sh_degree + 1) ** 2
+    groups = [0] * 3 + [1] * 4 + [2] * 3 + [3] * (3 * K) + [4]
+    f = np.array([factor[g] for g in groups])
+    u[np.asarray(shared, bool)] *= f

@@ -348,6 +348,32 @@ __global__ void __launch_bounds__(256) k_anchor(GView z, GView u, GView an, cons
         an.sh[(int64_t)j * an.ld + c] = z.sh[(int64_t)j * z.ld + gI] - u.sh[(int64_t)j * u.ld + c];
 }
 
+// u_grp *= factor[grp] on shared copies (the scaled duals follow a change of
+// rho: u = y / rho, so rho -> rho' rescales u by rho / rho')
+__global__ void __launch_bounds__(256) k_scale_duals(GView u, const uint8_t* __restrict__ shared, int64_t n,
+                                                     int n_planes, float f0, float f1, float f2, float f3, float f4)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n || !shared[c]) return;
+    float4 m = u.mo[c];
+    u.mo[c] = make_float4(m.x * f0, m.y * f0, m.z * f0, m.w * f4);
+    float4 q = u.quat[c];
+    u.quat[c] = make_float4(q.x * f1, q.y * f1, q.z * f1, q.w * f1);
+    float4 s = u.scale[c];
+    u.scale[c] = make_float4(s.x * f2, s.y * f2, s.z * f2, s.w * f2);
+    for (int j = 0; j < n_planes; j++) u.sh[(int64_t)j * u.ld + c] *= f3;
+}
+
+int launch_scale_duals(dg_gaussians* u, const uint8_t* shared, const float* f, cudaStream_t st)
+{
+    if (u->n == 0) return DG_OK;
+    k_scale_duals<<<(unsigned)((u->n + 255) / 256), 256, 0, st>>>(gview(u), shared, u->n, 3 * sh_coefs(u->sh_degree),
+                                                                  f[0], f[1], f[2], f[3], f[4]);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
 int launch_adam_admm(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m, dg_gaussians* v,
                      const dg_gaussians* anchor, const uint8_t* shared, const float* rho, const float* lr,
                      float b1, float b2, float eps, int step, const int32_t* dev_step, cudaStream_t st)

@@ -31,6 +31,7 @@ int launch_consensus(const dg_gaussians*, dg_gaussians*, dg_gaussians*, dg_gauss
                      const int32_t*, const float*, float, double*, cudaStream_t);
 int launch_anchor(const dg_gaussians*, const dg_gaussians*, const int32_t*, const uint8_t*, dg_gaussians*,
                   cudaStream_t);
+int launch_scale_duals(dg_gaussians*, const uint8_t*, const float*, cudaStream_t);
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -273,6 +274,13 @@ int dg_admm_anchor(const dg_gaussians* z, const dg_gaussians* u, const int32_t* 
     if (u->n > 0 && (!copy_gid || !copy_shared)) return DG_ERR_INVALID;
     if ((uintptr_t)copy_gid & 3u) return DG_ERR_INVALID;
     return launch_anchor(z, u, copy_gid, copy_shared, anchor, (cudaStream_t)stream);
+}
+
+int dg_admm_scale_duals(dg_gaussians* u, const uint8_t* copy_shared, const float* factor, void* stream)
+{
+    if (!valid_gauss(u) || !factor) return DG_ERR_INVALID;
+    if (u->n > 0 && !copy_shared) return DG_ERR_INVALID;
+    return launch_scale_duals(u, copy_shared, factor, (cudaStream_t)stream);
 }
 
 int dg_render_plan(dg_camera* host_cams, int n_views, int64_t n_gauss, int tile_w, int tile_h, dg_plan* plan)

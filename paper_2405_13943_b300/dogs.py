@@ -260,6 +260,11 @@ def dg_admm_consensus(x: GaussianBuffer, u: GaussianBuffer, z: GaussianBuffer, a
             "dg_admm_consensus")
 
 
+def dg_admm_scale_duals(u: GaussianBuffer, shared: torch.Tensor, factor, stream=None) -> None:
+    L.check(L.lib().dg_admm_scale_duals(u.ref, L.ptr(shared), L.floats(factor), L.stream_handle(stream)),
+            "dg_admm_scale_duals")
+
+
 def dg_admm_anchor(z: GaussianBuffer, u: GaussianBuffer, copy_gid: torch.Tensor, shared: torch.Tensor,
                    anchor: GaussianBuffer, stream=None) -> None:
     L.check(L.lib().dg_admm_anchor(z.ref, u.ref, L.ptr(copy_gid), L.ptr(shared), anchor.ref,

@@ -20,6 +20,7 @@ import torch
 from . import _lib as L
 from . import dogs as D
 from . import synth as S
+from .admm import AdaptivePenalty
 
 DEFAULT_LR = (1.6e-4, 1e-3, 5e-3, 2.5e-3, 1.25e-4, 5e-2)
 
@@ -42,8 +43,11 @@ class DogsTrainer:
     def __init__(self, split: S.BlockSplit, z0: D.GaussianBuffer, view_sets: Sequence[Sequence[S.Camera]],
                  targets: Sequence[torch.Tensor], rho=(1e-3,) * 5, lr=DEFAULT_LR, tile=(16, 16),
                  loss="dssim", w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0), alpha=1.0, intv=100,
-                 capacity: Optional[int] = None, device="cuda"):
+                 capacity: Optional[int] = None, device="cuda", adaptive: Optional[AdaptivePenalty] = None):
         self.split, self.device = split, device
+        self.adaptive = adaptive
+        if adaptive is not None:
+            adaptive.rho = [float(r) for r in rho]
         self.rho, self.lr, self.bg, self.alpha, self.intv = list(rho), list(lr), bg, alpha, intv
         self.loss_kind, self.w_l1, self.w_ssim = loss, w_l1, w_ssim
         self.gid = torch.from_numpy(split.copy_gid.astype(np.int32)).to(device)
@@ -142,7 +146,23 @@ class DogsTrainer:
             self.graphs[key].replay()
         else:
             self.enqueue(p, c)
+        if c and self.adaptive is not None and self.t < self.adaptive.freeze_after:
+            self._adapt_penalty()
         self.t += 1
+
+    def _adapt_penalty(self) -> None:
+        """Eq. 10 after a consensus: read the residuals (one synchronisation),
+        update rho, rescale the scaled duals of the shared copies and rebuild
+        the anchors z - u.  rho is a launch argument, so captured graphs are
+        dropped when it changes (at most freeze_after / intv times)."""
+        res = self.residuals.cpu().tolist()
+        rho, factor = self.adaptive.update(res, self.t)
+        if all(f == 1.0 for f in factor):
+            return
+        D.dg_admm_scale_duals(self.u, self.shared, factor)
+        D.dg_admm_anchor(self.z, self.u, self.gid, self.shared, self.anchor)
+        self.rho = rho
+        self.graphs.clear()
 
     def _capture(self, p: int, c: bool) -> torch.cuda.CUDAGraph:
         s = torch.cuda.Stream()

@@ -376,3 +376,26 @@ def test_consensus_with_many_copies_per_global(D, oracle):
         assert rel_l2(getattr(ug, name), ou_g[name]) < REL_L2, ("u", name)
     np.testing.assert_allclose(res.cpu().numpy(), ores, rtol=1e-3)
     assert np.diff(g_off).max() > 4
+
+
+def test_scale_duals_matches_oracle(D, oracle):
+    """Eq. 10's rescale of the scaled duals: shared copies scale by the
+    per-group factor, the rest stay untouched, padding lanes stay zero."""
+    O = oracle
+    split, z0, x, _ = random_admm_problem(12)
+    deg = 3
+    # nonzero values on every copy, to see that the non-shared ones stay put
+    u = S.Gaussians(*(S.random_like(70 + i, a.shape, 0.5) for i, a in
+                      enumerate((x.means, x.quats, x.log_scales, x.opacity_logits, x.sh))))
+    ub = D.GaussianBuffer.from_synth(u)
+    shared = torch.from_numpy(split.copy_shared()).to("cuda")
+    factor = [2.0, 0.5, 0.3, 1.0, 4.0 / 3.0]
+    D.dg_admm_scale_duals(ub, shared, factor)
+    torch.cuda.synchronize()
+    ou = O.params_from(u)
+    O.scale_duals(ou, split.copy_shared(), factor, deg)
+    got = ub.to_synth()
+    want = oracle_params_groups(O, ou, deg)
+    for name in GROUPS:
+        np.testing.assert_allclose(getattr(got, name), want[name], rtol=1e-6, atol=0, err_msg=name)
+    assert torch.all(ub.pad_lane() == 0)

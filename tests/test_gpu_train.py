@@ -113,3 +113,53 @@ def test_consensus_keeps_dual_mean_zero(mods):
         cp = sp.g_copies[sp.g_off[i]:sp.g_off[i + 1]]
         assert np.abs(u[cp].mean(0)).max() < 1e-4
         assert np.abs(z[i] - (x[cp] + 0 * u[cp]).mean(0)).max() < 1e-3 * max(1.0, np.abs(z[i]).max())
+
+
+def test_adaptive_penalty_follows_eq10(mods):
+    """Adaptive penalty in the batched trainer: at each consensus before the
+    freeze the rho update is the oracle's Eq. 10 on the residuals the
+    consensus produced, the unscaled duals rho * u of the shared copies are
+    unchanged by the rescale, and the anchors are z - u afterwards."""
+    D, srv, T = mods
+    from oracle import oracle as O
+    from paper_2405_13943_b300.admm import AdaptivePenalty
+    wl, z0, targets = small_setup(D, srv, seed=11)
+    rho0 = (1e-4, 1.0, 1e-4, 10.0, 1e-3)
+    ap = AdaptivePenalty(rho0, freeze_after=6)
+    bt = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, rho=rho0, loss="l1", intv=2, adaptive=ap)
+    bt.calibrate_capacity()
+    sh = wl.split.copy_shared().astype(bool)
+    deg = z0.deg
+    changed = 0
+    for t in range(10):
+        before_rho = list(bt.rho)
+        c = t % 2 == 0
+        if c:
+            # run the iteration without adaptation to read u and the residuals
+            bt.adaptive, saved = None, bt.adaptive
+            bt.step(graph=True)
+            bt.adaptive = saved
+            torch.cuda.synchronize()
+            res = bt.residuals.cpu().numpy()
+            u_before = O.params_from(bt.u.to_synth())
+            bt.t -= 1
+            if bt.t < ap.freeze_after:
+                bt._adapt_penalty()
+            bt.t += 1
+            want_rho = O.adaptive_rho(before_rho, res, t, freeze_after=6)
+            assert bt.rho == pytest.approx(want_rho, rel=1e-12), t
+            changed += bt.rho != before_rho
+            torch.cuda.synchronize()
+            u_after = O.params_from(bt.u.to_synth())
+            grp = np.array([0] * 3 + [1] * 4 + [2] * 3 + [3] * (3 * (deg + 1) ** 2) + [4])
+            y0 = u_before[sh] * np.array(before_rho)[grp]
+            y1 = u_after[sh] * np.array(bt.rho)[grp]
+            np.testing.assert_allclose(y1, y0, rtol=1e-6, atol=1e-30)
+            an = O.params_from(bt.anchor.to_synth())
+            zz = O.params_from(bt.z.to_synth())
+            np.testing.assert_allclose(an[sh], zz[wl.split.copy_gid[sh]] - u_after[sh], rtol=1e-5, atol=1e-6)
+        else:
+            bt.step(graph=True)
+    assert changed >= 1              # the deliberately unbalanced start moves rho
+    assert bt.rho == list(ap.rho)
+    assert not bt.overflowed()

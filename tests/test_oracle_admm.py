@@ -153,3 +153,55 @@ def test_consensus_admm_on_quadratics_converges(oracle):
             x[:] = (a * b + rho * (z - u)) / (a + rho)
             O.consensus(x, u, z, off, cp, 0, alpha=alpha)
         np.testing.assert_allclose(z[0], (a * b).sum(0) / a.sum(), atol=1e-10)
+
+
+def test_adaptive_penalty_rule(oracle):
+    """Eq. 10 on hand cases: r >> s doubles rho, s >> r halves it, balanced
+    keeps it, nothing changes from iteration 2000 on."""
+    rho = [1.0, 2.0, 3.0, 4.0, 5.0]
+    res = [100.0, 1.0, 4.0, 0.0, 1e-6] + [0.01, 1.0, 1e-2 * 4.0 * 99, 4.0, 1.0]
+    # group 0: r=10, s=0.1 -> inc; group 1: r=1, s=1 -> keep; group 2: r=2, s~1.99 -> keep;
+    # group 3: r=0, s=2 -> dec; group 4: r=1e-3, s=1 -> dec
+    assert oracle.adaptive_rho(rho, res, 10) == [2.0, 2.0, 3.0, 2.0, 2.5]
+    assert oracle.adaptive_rho(rho, res, 2000) == rho
+
+
+def test_dual_rescale_keeps_unscaled_dual(oracle):
+    """u = y / rho: after rho changes and u is rescaled by rho_old / rho_new,
+    the unscaled dual y = rho u is unchanged (Sec. 3.2, scaled form)."""
+    rng = np.random.default_rng(5)
+    P = 14
+    u = rng.standard_normal((6, P))
+    shared = np.array([1, 0, 1, 1, 0, 1], np.uint8)
+    old = [1.0, 2.0, 3.0, 4.0, 5.0]
+    new = [2.0, 2.0, 1.5, 8.0, 5.0]
+    grp = [0] * 3 + [1] * 4 + [2] * 3 + [3] * 3 + [4]
+    y_before = u * np.array([old[g] for g in grp])
+    u2 = u.copy()
+    oracle.scale_duals(u2, shared, [o / n for o, n in zip(old, new)], 0)
+    y_after = u2 * np.array([new[g] for g in grp])
+    np.testing.assert_allclose(y_after[shared == 1], y_before[shared == 1], rtol=1e-14)
+    np.testing.assert_array_equal(u2[shared == 0], u[shared == 0])
+
+
+def test_adaptive_consensus_admm_on_quadratics_converges(oracle):
+    """Consensus ADMM on f_k = a_k/2 ||x - b_k||^2 with Eq. 10 applied after
+    each consensus (u rescaled) and frozen later still reaches sum a b / sum a
+    (Boyd et al., varying penalty)."""
+    O = oracle
+    rng = np.random.default_rng(6)
+    K, P = 3, 14
+    a = rng.uniform(0.5, 3.0, (K, 1))
+    b = rng.standard_normal((K, P))
+    x = np.zeros((K, P)); u = np.zeros((K, P)); z = np.zeros((1, P))
+    off = np.array([0, K], np.int64); cp = np.arange(K, dtype=np.int32)
+    rho = [50.0] * 5                 # deliberately poor start
+    grp = [0] * 3 + [1] * 4 + [2] * 3 + [3] * 3 + [4]
+    for t in range(400):
+        rv = np.array([rho[g] for g in grp])
+        x[:] = (a * b + rv * (z - u)) / (a + rv)
+        res = O.consensus(x, u, z, off, cp, 0, alpha=1.0, rho=rho)
+        new = O.adaptive_rho(rho, res, t, freeze_after=100)
+        O.scale_duals(u, np.ones(K, np.uint8), [o / n for o, n in zip(rho, new)], 0)
+        rho = new
+    np.testing.assert_allclose(z[0], (a * b).sum(0) / a.sum(), atol=1e-9)
