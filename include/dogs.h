@@ -267,6 +267,37 @@ int dg_render(const dg_gaussians* z, const dg_camera* dev_cams, const dg_plan* p
               const float* bg, int64_t capacity, float* image, void* ws, size_t ws_bytes,
               uint32_t* dev_count, uint32_t* dev_status, void* stream);
 
+/* ---- scene splitting (host pre-processing; Sec. 3.2, Alg. 1) --------------- */
+/* Recursive bipartite split of n ground-plane positions xy (host, double[2n],
+ * x and y of point i at 2i, 2i+1; finite) into K cells, 1 <= K <= 64.
+ * Starting from one cell holding every point with a budget of K leaves,
+ * cells are processed level by level in first-in first-out order (Alg. 1);
+ * a cell with budget k >= 2 is cut across the longer side of the tight box
+ * of its points (ties: x), the lower child taking the first floor(n_c
+ * floor(k/2) / k) of its n_c points in (coordinate, index) order and budget
+ * floor(k/2), the upper child the rest and budget k - floor(k/2); cells with
+ * budget 1 are kept.  For K a power of two this is the median bipartition of
+ * Alg. 1, and every cell ends with floor(n/K) or ceil(n/K) points.
+ * Outputs (host, caller-owned): cell[i] (int32[n]) the cell of point i in the
+ * final order of the cell list; boxes (double[4K]) xmin, xmax, ymin, ymax of
+ * each cell's tight box (an empty cell gets +inf, -inf, +inf, -inf).
+ * DG_ERR_INVALID on a bad K, a null pointer with n > 0 or a non-finite
+ * coordinate; nothing is written then.  No GPU work. */
+int dg_scene_split(const double* xy, int64_t n, int K, int32_t* cell, double* boxes);
+
+/* Overlap by a scale factor (Sec. 3.2): each box is expanded about its centre
+ * by s >= 1 on both sides (centre c = (lo + hi) / 2, half side s (hi - lo) / 2,
+ * evaluated in double in that order), and position i belongs to every block
+ * whose expanded box contains it (closed intervals).  own (int32[n] or NULL)
+ * adds each point's own cell; nearest != 0 gives a position covered by no
+ * expanded box the block of the nearest one (ties: lowest index), as for
+ * camera centres outside the point cloud's boxes.  member (host, uint64[n],
+ * caller-owned) receives bit k set for block k.  Empty boxes contain nothing.
+ * DG_ERR_INVALID on a bad K or s, an own[i] outside [0, K), a null pointer
+ * with n > 0 or a non-finite coordinate.  No GPU work. */
+int dg_scene_assign(const double* xy, int64_t n, const double* boxes, int K, double s,
+                    const int32_t* own, int nearest, uint64_t* member);
+
 /* ---- misc ------------------------------------------------------------------ */
 const char* dg_version(void);
 /* number of kernel launches this library has enqueued since load (monotone) */

@@ -394,3 +394,105 @@ def scale_duals(u, shared, factor, sh_degree):
     groups = [0] * 3 + [1] * 4 + [2] * 3 + [3] * (3 * K) + [4]
     f = np.array([factor[g] for g in groups])
     u[np.asarray(shared, bool)] *= f
+
+
+# --------------------------------------------------------------------------
+# recursive bipartite scene splitting (Sec. 3.2 "Scene Splitting", Alg. 1)
+# and the overlap by a box scale factor s (Sec. 3.2)
+# --------------------------------------------------------------------------
+def _aabb(xy, idx):
+    """Tight ground box (xmin, xmax, ymin, ymax) of the points idx; an empty
+    set gives (+inf, -inf, +inf, -inf)."""
+    if len(idx) == 0:
+        return (np.inf, -np.inf, np.inf, -np.inf)
+    p = xy[idx]
+    return (p[:, 0].min(), p[:, 0].max(), p[:, 1].min(), p[:, 1].max())
+
+
+def scene_split(xy, K):
+    """Alg. 1 on ground positions xy (n, 2) float64.  Reading: every cell
+    carries a budget of leaves (K at the root); a cell with budget k >= 2 is
+    cut on the longer side of its tight box (ties: x), the lower child
+    getting the first floor(n_c floor(k/2) / k) points in (coordinate, index)
+    order and budget floor(k/2); budget-1 cells are popped and pushed back
+    unchanged.  Returns (cell (n,) int32, boxes (K, 4))."""
+    xy = np.asarray(xy, np.float64)
+    n = xy.shape[0]
+    # line 1-2: one cell with a tight box over all points
+    C = [(np.arange(n), K)]
+    # line 3-13: split every current cell until there are K of them
+    while len(C) < K:
+        C_cur = list(C)
+        while len(C_cur) > 0:
+            cell = C_cur.pop(0)                 # pop a cell of this level
+            C.pop(_index_of(C, cell))           # and remove it from the cells
+            idx, k = cell
+            if k < 2:
+                C.append(cell)
+                continue
+            box = _aabb(xy, idx)
+            axis = 0 if (len(idx) == 0 or box[1] - box[0] >= box[3] - box[2]) else 1
+            order = idx[np.lexsort((idx, xy[idx, axis]))]   # group by the cut
+            k1 = k // 2
+            m = (len(idx) * k1) // k
+            C.append((order[:m], k1))
+            C.append((order[m:], k - k1))
+    # line 14-17: group the points of each cell into its block
+    cell_of = np.empty(n, np.int32)
+    boxes = np.empty((K, 4))
+    for k, (idx, _) in enumerate(C):
+        cell_of[idx] = k
+        boxes[k] = _aabb(xy, idx)
+    return cell_of, boxes
+
+
+def _index_of(C, cell):
+    for i, c in enumerate(C):
+        if c is cell:
+            return i
+    raise ValueError("cell not in the list")
+
+
+def scene_assign(xy, boxes, s, own=None, nearest=False):
+    """Membership (n, K) bool in the boxes expanded about their centres by
+    s: centre (lo + hi) / 2, half side s (hi - lo) / 2, closed intervals.
+    own adds each point's own cell; nearest gives a point outside every
+    expanded box the block of the nearest one (lowest index on ties)."""
+    xy = np.asarray(xy, np.float64)
+    boxes = np.asarray(boxes, np.float64)
+    n, K = xy.shape[0], boxes.shape[0]
+    member = np.zeros((n, K), bool)
+    ex = np.empty((K, 4))
+    empty = np.zeros(K, bool)
+    for k in range(K):
+        b = boxes[k]
+        empty[k] = not (b[0] <= b[1] and b[2] <= b[3])
+        if empty[k]:
+            continue
+        for a in range(2):
+            lo, hi = b[2 * a], b[2 * a + 1]
+            c = 0.5 * (lo + hi)
+            h = 0.5 * s * (hi - lo)
+            ex[k, 2 * a], ex[k, 2 * a + 1] = c - h, c + h
+    for k in range(K):
+        if empty[k]:
+            continue
+        member[:, k] = ((xy[:, 0] >= ex[k, 0]) & (xy[:, 0] <= ex[k, 1]) &
+                        (xy[:, 1] >= ex[k, 2]) & (xy[:, 1] <= ex[k, 3]))
+    if own is not None:
+        member[np.arange(n), np.asarray(own)] = True
+    if nearest:
+        for i in np.nonzero(~member.any(1))[0]:
+            best, bd = -1, 0.0
+            for k in range(K):
+                if empty[k]:
+                    continue
+                x, y = xy[i]
+                dx = ex[k, 0] - x if x < ex[k, 0] else (x - ex[k, 1] if x > ex[k, 1] else 0.0)
+                dy = ex[k, 2] - y if y < ex[k, 2] else (y - ex[k, 3] if y > ex[k, 3] else 0.0)
+                d = dx * dx + dy * dy
+                if best < 0 or d < bd:
+                    best, bd = k, d
+            if best >= 0:
+                member[i, best] = True
+    return member

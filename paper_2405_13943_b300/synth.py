@@ -361,8 +361,18 @@ def block_split(xy: np.ndarray, cols: int, rows: int, loads: Sequence[float],
     globals are numbered first (by position along the first block that holds
     them), then unshared globals block by block."""
     cells, member, band = grid_split(xy, cols, rows, loads, shared_frac)
-    K = cols * rows
+    return split_layout(xy, member, cells, band)
+
+
+def split_layout(xy: np.ndarray, member: np.ndarray, cells: np.ndarray, band: float) -> tuple:
+    """Copy layout of a membership (n, K) bool (every point in at least one
+    block).  Returns (BlockSplit, order), `order` mapping new global ids to
+    the caller's point indices: shared globals first (by first block, then
+    x, y), then unshared globals block by block."""
+    K = member.shape[1]
     n = xy.shape[0]
+    if not member.any(1).all():
+        raise ValueError("every point needs a block")
     cnt = member.sum(1)
     shared = cnt >= 2
     first_blk = np.argmax(member, axis=1)

@@ -163,3 +163,42 @@ def test_adaptive_penalty_follows_eq10(mods):
     assert changed >= 1              # the deliberately unbalanced start moves rho
     assert bt.rho == list(ap.rho)
     assert not bt.overflowed()
+
+
+def test_training_on_a_recursive_split(mods):
+    """Blocks from Alg. 1 (K = 3, not a power of two, s = 1.4) train through
+    the batched path exactly as through the per-block path, and the
+    iterations lower the loss."""
+    D, srv, T = mods
+    from paper_2405_13943_b300 import scene_split as SS
+    z = S.city_scene(30_000, 21, sh_degree=1)
+    gt = D.GaussianBuffer.from_synth(S.city_scene(30_000, 22, sh_degree=1, layout_seed=21))
+    cams = S.grid_cameras(23, n_side=4, size=1000.0, width=160, height=120)
+    split, z, view_sets = SS.make_blocks(z, cams, 3, 1.4, views_per_step=2, pool=2)
+    assert split.K == 3 and split.n_shared_globals > 0
+    targets = [srv.render_views(gt, vs).image.clone() for vs in view_sets]
+    z0 = D.GaussianBuffer.from_synth(z)
+    kw = dict(rho=(1e-2,) * 5, loss="l1", intv=2)
+    bt = T.DogsTrainer(split, z0.clone(), view_sets, targets, **kw)
+    bt.calibrate_capacity()
+    sq = T.SequentialTrainer(split, z0.clone(), view_sets, targets, **kw)
+    sq.calibrate_capacity()
+    for _ in range(4):
+        bt.step(graph=False)
+        sq.step()
+    torch.cuda.synchronize()
+    x_seq = bt.x.like()
+    for blk in sq.blocks:
+        sq._copy_rows(x_seq, blk["x"], blk["b"], blk["e"], True)
+    gb, gs = groups(bt.x), groups(x_seq)
+    for k in gb:
+        assert rel_l2(gs[k], gb[k]) < REL_L2, k
+    first = None
+    for t in range(40):
+        bt.step(graph=True)
+        if t % 2 == 1:
+            torch.cuda.synchronize()
+            cur = float(bt.vb.loss.sum())
+            first = cur if first is None else first
+    assert not bt.overflowed()
+    assert cur < first
