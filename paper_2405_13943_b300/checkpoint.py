@@ -1,0 +1,166 @@
+"""Checkpoint and resume of a batched DOGS run.
+
+A checkpoint holds everything the next iteration reads: the global model z,
+the block-local copies x_k, the scaled duals u_k, Adam's moments m and v,
+the iteration counter t and the penalties rho (with the adaptive-penalty
+state of Eq. 10 when it is on).  The anchors z - u are not stored: after a
+load they are rebuilt by dg_admm_anchor, the same single subtraction the
+consensus writes, so they come back bit for bit.  Gradients are scratch and
+are not stored either.
+
+File layout (little endian):
+    8 bytes   magic "DOGSCKPT"
+    8 bytes   uint64 length H of the header
+    8 bytes   uint64 start of the data area (a multiple of 4096)
+    H bytes   UTF-8 JSON header: format version, t, rho, the run's
+              configuration, a fingerprint of the block split, and for each
+              buffer its name, byte offset in the data area, byte length
+              and CRC-32
+    ...       raw buffers, each starting on a 4096-byte boundary, in the
+              library's device layout (padding lanes included)
+The file is written to `path + ".tmp"` and renamed into place, so a crash
+mid-write leaves the previous checkpoint intact.  Loading checks the
+magic, the version, the split fingerprint, the configuration, every
+buffer's size and CRC before anything on the device is overwritten.
+"""
+from __future__ import annotations
+
+import json
+import os
+import struct
+import zlib
+from typing import Dict, List
+
+import numpy as np
+import torch
+
+MAGIC = b"DOGSCKPT"
+VERSION = 1
+ALIGN = 4096
+CHUNK = 64 << 20          # bytes staged through host memory at a time
+BUFFERS = ("z", "x", "u", "m", "v")
+CONFIG = ("lr", "alpha", "intv", "loss_kind", "w_l1", "w_ssim", "bg")
+
+
+class CheckpointError(RuntimeError):
+    pass
+
+
+def split_fingerprint(split) -> str:
+    crc = 0
+    for a in (split.copy_gid, split.blk_off, split.blk_nshared, split.g_off, split.g_copies):
+        crc = zlib.crc32(np.ascontiguousarray(a).tobytes(), crc)
+    return f"{crc:08x}:{split.K}:{split.n_copies}:{int(split.n_shared_globals)}"
+
+
+def _config(tr) -> Dict:
+    return {k: (list(getattr(tr, k)) if isinstance(getattr(tr, k), (list, tuple)) else getattr(tr, k))
+            for k in CONFIG}
+
+
+def _chunks(t: torch.Tensor):
+    flat = t.reshape(-1).view(torch.uint8)
+    for b in range(0, flat.numel(), CHUNK):
+        yield flat[b:b + CHUNK]
+
+
+def save(tr, path: str) -> None:
+    """Write the state of DogsTrainer `tr` after its last completed iteration
+    (one pass over the device data: the CRCs are fixed-width hex, so the
+    header is written with placeholders and rewritten in place at the end)."""
+    bufs = {name: getattr(tr, name) for name in BUFFERS}
+    on_gpu = bufs["z"].data.is_cuda
+    if on_gpu:
+        torch.cuda.synchronize()
+    entries: List[Dict] = []
+    off = 0
+    for name, b in bufs.items():
+        nbytes = b.data.numel() * 4
+        entries.append(dict(name=name, n=b.n, ld=b.ld, deg=b.deg, nbytes=nbytes, offset=off, crc32="0" * 8))
+        off += -(-nbytes // ALIGN) * ALIGN          # offsets relative to the data start
+    ad = tr.adaptive
+    header = dict(format="dogs-checkpoint", version=VERSION, t=int(tr.t), rho=[float(r) for r in tr.rho],
+                  adaptive=None if ad is None else dict(rho=list(ad.rho), mu=ad.mu, tau_inc=ad.tau_inc,
+                                                        tau_dec=ad.tau_dec, freeze_after=ad.freeze_after),
+                  config=_config(tr), split=split_fingerprint(tr.split), buffers=entries)
+    hdr = json.dumps(header, sort_keys=True).encode()
+    data_start = -(-(24 + len(hdr)) // ALIGN) * ALIGN
+    staging = torch.empty(CHUNK, dtype=torch.uint8, pin_memory=on_gpu)
+    tmp = path + ".tmp"
+    with open(tmp, "wb") as f:
+        f.write(MAGIC + struct.pack("<QQ", len(hdr), data_start) + hdr)
+        for e in entries:
+            f.seek(data_start + e["offset"])
+            crc = 0
+            for c in _chunks(bufs[e["name"]].data):
+                h = staging[:c.numel()]
+                h.copy_(c)
+                crc = zlib.crc32(h.numpy(), crc)
+                f.write(h.numpy().tobytes())
+            e["crc32"] = f"{crc:08x}"
+        f.truncate(data_start + entries[-1]["offset"] + entries[-1]["nbytes"])
+        final = json.dumps(header, sort_keys=True).encode()
+        assert len(final) == len(hdr)
+        f.seek(24)
+        f.write(final)
+        f.flush()
+        os.fsync(f.fileno())
+    os.replace(tmp, path)
+
+
+def read_header(path: str) -> Dict:
+    with open(path, "rb") as f:
+        head = f.read(24)
+        if len(head) < 24 or head[:8] != MAGIC:
+            raise CheckpointError(f"{path}: not a DOGS checkpoint")
+        hlen, data_start = struct.unpack("<QQ", head[8:])
+        raw = f.read(hlen)
+    if len(raw) != hlen:
+        raise CheckpointError(f"{path}: truncated header")
+    header = json.loads(raw.decode())
+    header["data_start"] = data_start
+    if header.get("format") != "dogs-checkpoint" or header.get("version") != VERSION:
+        raise CheckpointError(f"{path}: unsupported format {header.get('format')} v{header.get('version')}")
+    return header
+
+
+def load(tr, path: str) -> Dict:
+    """Restore DogsTrainer `tr` (built on the same split, views and targets)
+    from `path`.  Everything is verified on the host before the device
+    buffers are written.  Returns the header."""
+    header = read_header(path)
+    if header["split"] != split_fingerprint(tr.split):
+        raise CheckpointError("checkpoint was written for another block split")
+    cfg, want = header["config"], _config(tr)
+    diff = [k for k in CONFIG if json.loads(json.dumps(want[k])) != cfg[k]]
+    if diff:
+        raise CheckpointError(f"configuration differs from the checkpoint's: {diff}")
+    if (header["adaptive"] is None) != (tr.adaptive is None):
+        raise CheckpointError("adaptive penalty on in one of checkpoint and trainer only")
+    size = os.path.getsize(path)
+    host: Dict[str, np.ndarray] = {}
+    with open(path, "rb") as f:
+        for e in header["buffers"]:
+            b = getattr(tr, e["name"])
+            if (e["n"], e["ld"], e["deg"], e["nbytes"]) != (b.n, b.ld, b.deg, b.data.numel() * 4):
+                raise CheckpointError(f"buffer {e['name']}: shape differs from the trainer's")
+            at = header["data_start"] + e["offset"]
+            if at + e["nbytes"] > size:
+                raise CheckpointError(f"buffer {e['name']}: file truncated")
+            f.seek(at)
+            raw = f.read(e["nbytes"])
+            if f"{zlib.crc32(raw):08x}" != e["crc32"]:
+                raise CheckpointError(f"buffer {e['name']}: CRC mismatch")
+            host[e["name"]] = np.frombuffer(raw, np.float32)
+    for name, a in host.items():
+        getattr(tr, name).data.copy_(torch.from_numpy(a.copy()))
+    tr.t = int(header["t"])
+    tr.rho = [float(r) for r in header["rho"]]
+    if tr.adaptive is not None:
+        ad = header["adaptive"]
+        tr.adaptive.rho = list(ad["rho"])
+        tr.adaptive.mu, tr.adaptive.tau_inc, tr.adaptive.tau_dec = ad["mu"], ad["tau_inc"], ad["tau_dec"]
+        tr.adaptive.freeze_after = ad["freeze_after"]
+    tr.refresh_anchor()
+    tr.graphs.clear()
+    return header

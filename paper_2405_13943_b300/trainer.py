@@ -177,6 +177,20 @@ class DogsTrainer:
     def overflowed(self) -> bool:
         return bool(int(self.vb.status.item()) & L.DG_STATUS_CAPACITY)
 
+    # ---- checkpoint / resume ------------------------------------------------------
+    def refresh_anchor(self) -> None:
+        """Anchors z - u of the shared copies from the current z and u."""
+        D.dg_admm_anchor(self.z, self.u, self.gid, self.shared, self.anchor)
+        torch.cuda.synchronize()
+
+    def save_checkpoint(self, path: str) -> None:
+        from . import checkpoint
+        checkpoint.save(self, path)
+
+    def load_checkpoint(self, path: str) -> dict:
+        from . import checkpoint
+        return checkpoint.load(self, path)
+
 
 class SequentialTrainer:
     """The plain sequential per-block form: K single-block models, each with

@@ -202,3 +202,37 @@ def test_training_on_a_recursive_split(mods):
             first = cur if first is None else first
     assert not bt.overflowed()
     assert cur < first
+
+
+def test_checkpoint_resume(mods, tmp_path):
+    """A run saved after 3 iterations and loaded into a fresh trainer holds
+    the saved state bit for bit (anchors included), and 3 more iterations of
+    the resumed and of the uninterrupted run agree up to the order of the
+    float atomics."""
+    D, srv, T = mods
+    from paper_2405_13943_b300.admm import AdaptivePenalty
+    wl, z0, targets = small_setup(D, srv, seed=13)
+    kw = dict(rho=(1e-2, 1e-2, 1e-2, 1e-3, 1e-2), loss="dssim", intv=2)
+    a = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, adaptive=AdaptivePenalty(kw["rho"]), **kw)
+    a.calibrate_capacity()
+    for _ in range(3):
+        a.step()
+    p = str(tmp_path / "a.ckpt")
+    a.save_checkpoint(p)
+    saved = {n: getattr(a, n).data.clone() for n in ("z", "x", "u", "m", "v", "anchor")}
+    b = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, adaptive=AdaptivePenalty(kw["rho"]), **kw)
+    b.calibrate_capacity()
+    b.step()                                     # state to be overwritten
+    b.load_checkpoint(p)
+    for n, t in saved.items():
+        assert torch.equal(getattr(b, n).data.view(torch.int32), t.view(torch.int32)), n
+    assert (b.t, b.rho, b.adaptive.rho) == (a.t, a.rho, a.adaptive.rho)
+    for _ in range(3):
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    assert b.t == a.t == 6 and b.rho == a.rho
+    for buf in ("x", "z", "u"):
+        ga, gb = groups(getattr(a, buf)), groups(getattr(b, buf))
+        for k in ga:
+            assert rel_l2(gb[k], ga[k]) < REL_L2, (buf, k)
