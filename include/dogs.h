@@ -187,6 +187,16 @@ int dg_rasterize_fwd(const float* rec, const uint32_t* vals, const uint32_t* ran
                      const dg_camera* dev_cams, const dg_plan* plan, const float* bg,
                      float* image, float* T_final, uint32_t* last, void* stream);
 
+/* dg_rasterize_fwd with the same outputs, plus work counters for measuring:
+ * counts (device uint64[2], 8-byte aligned, zeroed by the call, then
+ * accumulated on the stream) receives [0] the (pixel, instance) pairs
+ * examined while the pixel was still compositing and [1] the pairs that
+ * contributed (alpha >= 1/255, before the stop).  The pairs the backward
+ * visits are the sum of `last`; the ones it differentiates are counts[1]. */
+int dg_rasterize_count(const float* rec, const uint32_t* vals, const uint32_t* ranges,
+                       const dg_camera* dev_cams, const dg_plan* plan, const float* bg,
+                       float* image, float* T_final, uint32_t* last, uint64_t* counts, void* stream);
+
 /* ---- losses (K6, K11) ----------------------------------------------------- */
 /* Per view v: loss[v] = w_l1 * mean |I - I*| + w_ssim * (1 - mean SSIM(I, I*))
  * (Eq. 3 with lambda = w_ssim and the L1 weight w_l1; SSIM with an 11x11

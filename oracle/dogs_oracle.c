@@ -344,13 +344,15 @@ typedef struct { uint32_t rec; double alpha, alpha_raw, G, T, dx, dy; } pair_t;
 /* margin: relative distance of the value decisions (1/255 skip, T stop) from */
 /* their thresholds; margin_grad (may be NULL): of the 0.99 clamp, which only   */
 /* decides gradients                                                           */
-static int composite_pixel(int px, int py, const uint32_t* vals, uint32_t beg, uint32_t end,
-                           const double* rec, const double* bg, double* C, double* Tout,
-                           uint32_t* last, double* margin, double* margin_grad, pair_t* pairs)
+static int composite_pixel_seen(int px, int py, const uint32_t* vals, uint32_t beg, uint32_t end,
+                                const double* rec, const double* bg, double* C, double* Tout,
+                                uint32_t* last, double* margin, double* margin_grad, pair_t* pairs,
+                                uint32_t* seen)
 {
     double T = 1.0, col[3] = {0, 0, 0}, mg = INFINITY, mg2 = INFINITY;
     int np = 0;
     uint32_t lst = 0;
+    if (seen) *seen = end - beg;                 /* no stop: every position examined */
     for (uint32_t j = beg; j < end; j++) {
         const double* g = rec + (int64_t)vals[j] * REC_N;
         double dx = g[REC_MX] - (px + 0.5), dy = g[REC_MY] - (py + 0.5);
@@ -364,7 +366,10 @@ static int composite_pixel(int px, int py, const uint32_t* vals, uint32_t beg, u
         mg2 = fmin(mg2, fabs(ar - ALPHA_MAX) / ALPHA_MAX);   /* clamp decides the gradient */
         double Tn = T * (1.0 - alpha);
         mg = fmin(mg, fabs(Tn - T_MIN) / T_MIN);
-        if (Tn < T_MIN) break;
+        if (Tn < T_MIN) {
+            if (seen) *seen = j - beg + 1;
+            break;
+        }
         for (int ch = 0; ch < 3; ch++) col[ch] += g[REC_R + ch] * alpha * T;
         if (pairs) {
             pairs[np].rec = vals[j]; pairs[np].alpha = alpha; pairs[np].alpha_raw = ar;
@@ -378,6 +383,34 @@ static int composite_pixel(int px, int py, const uint32_t* vals, uint32_t beg, u
     *Tout = T; *last = lst; *margin = mg;
     if (margin_grad) *margin_grad = mg2;
     return np;
+}
+
+static int composite_pixel(int px, int py, const uint32_t* vals, uint32_t beg, uint32_t end,
+                           const double* rec, const double* bg, double* C, double* Tout,
+                           uint32_t* last, double* margin, double* margin_grad, pair_t* pairs)
+{
+    return composite_pixel_seen(px, py, vals, beg, end, rec, bg, C, Tout, last, margin, margin_grad, pairs,
+                                NULL);
+}
+
+/* Work counts of the compositing per pixel: seen = list positions examined  */
+/* (up to and including the one that stops the pixel), used = Eq. 2 terms     */
+/* composited (alpha >= 1/255, before the stop).                              */
+void oc_rasterize_counts(int width, int height, int tile_w, int tile_h, int64_t tile_off,
+                         const uint32_t* vals, const uint32_t* ranges, const double* rec,
+                         uint32_t* seen, uint32_t* used)
+{
+    const double bg[3] = {0, 0, 0};
+    int TX = (width + tile_w - 1) / tile_w;
+    for (int py = 0; py < height; py++)
+        for (int px = 0; px < width; px++) {
+            int64_t tile = tile_off + (int64_t)(py / tile_h) * TX + px / tile_w;
+            int64_t p = (int64_t)py * width + px;
+            double C[3], Tf, mg;
+            uint32_t lst;
+            used[p] = (uint32_t)composite_pixel_seen(px, py, vals, ranges[2 * tile], ranges[2 * tile + 1], rec,
+                                                     bg, C, &Tf, &lst, &mg, NULL, NULL, &seen[p]);
+        }
 }
 
 /* Render one view of size W x H whose tiles are numbered from tile_off.      */

@@ -63,6 +63,9 @@ def lib():
         _lib.oc_rasterize_fwd.restype = None
         _lib.oc_rasterize_fwd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, u32p, u32p,
                                           dp, dp, dp, dp, u32p, dp, dp]
+        _lib.oc_rasterize_counts.restype = None
+        _lib.oc_rasterize_counts.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, u32p, u32p,
+                                             dp, u32p, u32p]
         _lib.oc_rasterize_bwd.restype = None
         _lib.oc_rasterize_bwd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, u32p, u32p,
                                           dp, dp, dp, dp]
@@ -228,6 +231,22 @@ def rasterize_fwd(proj: dict, bins: dict, plan: ViewPlan, bg=(0.0, 0.0, 0.0)) ->
                                _p(last, C.c_uint32), _p(mg, C.c_double), _p(mg2, C.c_double))
         # margin: value decisions (1/255 skip, T stop); margin_grad: the 0.99 clamp
         out.append({"image": img, "T_final": Tf, "last": last, "margin": mg, "margin_grad": mg2})
+    return out
+
+
+def rasterize_counts(proj: dict, bins: dict, plan: ViewPlan) -> List[dict]:
+    """Per view and pixel: list positions examined by the compositing (up to
+    the stop) and Eq. 2 terms composited."""
+    out = []
+    rec = np.ascontiguousarray(proj["rec"])
+    vals = np.ascontiguousarray(bins["vals"]) if bins["M"] else np.zeros(1, np.uint32)
+    for v, c in enumerate(plan.cams):
+        W, H = c.width, c.height
+        seen = np.zeros((H, W), np.uint32); used = np.zeros((H, W), np.uint32)
+        lib().oc_rasterize_counts(W, H, plan.tw, plan.th, plan.tile_off[v], _p(vals, C.c_uint32),
+                                  _p(bins["ranges"], C.c_uint32), _p(rec, C.c_double),
+                                  _p(seen, C.c_uint32), _p(used, C.c_uint32))
+        out.append({"seen": seen, "used": used})
     return out
 
 

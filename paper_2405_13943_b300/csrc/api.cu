@@ -19,6 +19,8 @@ int launch_bin_sort(const float4*, const uint2*, const dg_camera*, const dg_plan
 int bin_sort_init();
 int launch_raster_fwd(const float4*, const uint32_t*, const uint32_t*, const dg_camera*, const dg_plan&,
                       const float*, float*, float*, uint32_t*, cudaStream_t);
+int launch_raster_count(const float4*, const uint32_t*, const uint32_t*, const dg_camera*, const dg_plan&,
+                        const float*, float*, float*, uint32_t*, unsigned long long*, cudaStream_t);
 int launch_raster_bwd(const float4*, const uint32_t*, const uint32_t*, const dg_camera*, const dg_plan&,
                       const float*, const float*, const uint32_t*, const float*, float*, cudaStream_t);
 size_t loss_ws_bytes(const dg_plan&);
@@ -188,6 +190,17 @@ int dg_rasterize_fwd(const float* rec, const uint32_t* vals, const uint32_t* ran
     if (!aligned16(rec) || !aligned8(dev_cams)) return DG_ERR_INVALID;
     return launch_raster_fwd((const float4*)rec, vals, ranges, dev_cams, *plan, bg, image, T_final, last,
                              (cudaStream_t)stream);
+}
+
+int dg_rasterize_count(const float* rec, const uint32_t* vals, const uint32_t* ranges, const dg_camera* dev_cams,
+                       const dg_plan* plan, const float* bg, float* image, float* T_final, uint32_t* last,
+                       uint64_t* counts, void* stream)
+{
+    if (!valid_plan(plan) || !bg || !counts || !aligned8(counts)) return DG_ERR_INVALID;
+    if (plan->n_tiles > 0 && (!dev_cams || !ranges || !vals || !image || !T_final || !last)) return DG_ERR_INVALID;
+    if (!aligned16(rec) || !aligned8(dev_cams)) return DG_ERR_INVALID;
+    return launch_raster_count((const float4*)rec, vals, ranges, dev_cams, *plan, bg, image, T_final, last,
+                               (unsigned long long*)counts, (cudaStream_t)stream);
 }
 
 int dg_loss_l1(const float* image, const float* target, const dg_camera* dev_cams, const dg_plan* plan, float w_l1,

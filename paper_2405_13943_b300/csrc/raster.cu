@@ -132,15 +132,20 @@ __device__ __forceinline__ void cta_sync()
     if (NW == 1) __syncwarp(); else __syncthreads();
 }
 
-template <int NW, int S>
+// CNT = true is the counting instantiation behind dg_rasterize_count: the same
+// compositing, plus the number of (pixel, instance) pairs examined while the
+// pixel was live and the number that contributed, added into counts[0..1].
+template <int NW, int S, bool CNT = false>
 __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict__ rec,
                                                         const uint32_t* __restrict__ vals,
                                                         const uint32_t* __restrict__ ranges,
                                                         const dg_camera* __restrict__ cams, int n_views, int tw,
                                                         int th, float bg0, float bg1, float bg2,
                                                         float* __restrict__ image, float* __restrict__ T_final,
-                                                        uint32_t* __restrict__ last_out)
+                                                        uint32_t* __restrict__ last_out,
+                                                        unsigned long long* __restrict__ counts)
 {
+    uint32_t n_seen = 0, n_used = 0;
     constexpr int NT = 32 * NW, PPL = 8 / NW, R = NT * S;
     __shared__ float4 s_g[R];   // mx, my, A, B
     __shared__ float2 s_h[R];   // C, log2 opacity
@@ -181,6 +186,7 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
         for (uint32_t j = 0; j < cnt && live; j++) {
             const float4 g = s_g[j];
             const float2 h = s_h[j];
+            if (CNT) n_seen += __popc(live);
             Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, G.fx, G.fy0, G.dy);
             if (__fadd_rn(sp.pmax, h.y) < -8.0f) continue;   // no pixel of the strip reaches 2^-8
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -202,9 +208,18 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
                 C2[k] = fmaf(c.z, wt, C2[k]);
                 T[k] = Tn;
                 last[k] = base + j + 1;
+                if (CNT) n_used++;
             }
         }
         cta_sync<NW>();
+    }
+    if (CNT) {
+        n_seen = __reduce_add_sync(0xffffffffu, n_seen);
+        n_used = __reduce_add_sync(0xffffffffu, n_used);
+        if ((tid & 31) == 0) {
+            atomicAdd(counts, (unsigned long long)n_seen);
+            atomicAdd(counts + 1, (unsigned long long)n_used);
+        }
     }
     const int64_t HW = (int64_t)ti.W * ti.H;
     float* im = image + 3 * ti.pix_off;
@@ -382,7 +397,18 @@ static void fwd_launch(const float4* rec, const uint32_t* vals, const uint32_t* 
                        cudaStream_t st)
 {
     k_raster_fwd<NW, S><<<(unsigned)p.n_tiles, 32 * NW, 0, st>>>(rec, vals, ranges, cams, p.n_views, p.tile_w,
-                                                                 p.tile_h, bg[0], bg[1], bg[2], image, T_final, last);
+                                                                 p.tile_h, bg[0], bg[1], bg[2], image, T_final, last,
+                                                                 nullptr);
+}
+
+template <int NW, int S>
+static void count_launch(const float4* rec, const uint32_t* vals, const uint32_t* ranges, const dg_camera* cams,
+                         const dg_plan& p, const float* bg, float* image, float* T_final, uint32_t* last,
+                         unsigned long long* counts, cudaStream_t st)
+{
+    k_raster_fwd<NW, S, true><<<(unsigned)p.n_tiles, 32 * NW, 0, st>>>(rec, vals, ranges, cams, p.n_views,
+                                                                       p.tile_w, p.tile_h, bg[0], bg[1], bg[2],
+                                                                       image, T_final, last, counts);
 }
 
 template <int NW, int S>
@@ -414,6 +440,18 @@ int launch_raster_fwd(const float4* rec, const uint32_t* vals, const uint32_t* r
 {
     if (plan.n_tiles == 0) return DG_OK;
     DG_RASTER_DISPATCH(fwd_launch, rec, vals, ranges, cams, plan, bg, image, T_final, last, st)
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
+int launch_raster_count(const float4* rec, const uint32_t* vals, const uint32_t* ranges, const dg_camera* cams,
+                        const dg_plan& plan, const float* bg, float* image, float* T_final, uint32_t* last,
+                        unsigned long long* counts, cudaStream_t st)
+{
+    if (cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return DG_ERR_CUDA;
+    if (plan.n_tiles == 0) return DG_OK;
+    DG_RASTER_DISPATCH(count_launch, rec, vals, ranges, cams, plan, bg, image, T_final, last, counts, st)
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;

@@ -222,6 +222,17 @@ def dg_rasterize_fwd(vb: ViewBatch, bg=(0.0, 0.0, 0.0), stream=None) -> None:
                                      L.ptr(vb.last), L.stream_handle(stream)), "dg_rasterize_fwd")
 
 
+def dg_rasterize_count(vb: ViewBatch, bg=(0.0, 0.0, 0.0), stream=None) -> torch.Tensor:
+    """dg_rasterize_fwd plus its pair counters: returns a device int64[2]
+    (pairs examined while compositing, pairs that contributed)."""
+    counts = torch.zeros(2, dtype=torch.int64, device=vb.image.device)
+    L.check(L.lib().dg_rasterize_count(L.ptr(vb.rec), L.ptr(vb.vals), L.ptr(vb.ranges), L.ptr(vb.dev_cams),
+                                       C.byref(vb.plan), L.floats(bg), L.ptr(vb.image), L.ptr(vb.T_final),
+                                       L.ptr(vb.last), L.ptr(counts), L.stream_handle(stream)),
+            "dg_rasterize_count")
+    return counts
+
+
 def dg_loss_l1(vb: ViewBatch, target: torch.Tensor, w_l1=1.0, stream=None) -> None:
     L.check(L.lib().dg_loss_l1(L.ptr(vb.image), L.ptr(target), L.ptr(vb.dev_cams), C.byref(vb.plan), w_l1,
                                L.ptr(vb.loss), L.ptr(vb.dL_dimage), L.stream_handle(stream)), "dg_loss_l1")

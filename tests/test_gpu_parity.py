@@ -130,6 +130,7 @@ def test_small_single_view_forward_backward(D, oracle):
     xbuf, vb, grads, f, ob, masks, plan = run_pair(D, O, g, [cam], [(0, g.n)], [0, g.n], 16, 16, (0, 0, 0))
     check_forward(D, O, vb, f, masks, plan)
     check_backward(D, O, g, grads, ob, 0)
+    check_counts(D, O, vb, f, masks, plan, (0, 0, 0))
 
 
 @pytest.mark.parametrize("tw,th", [(16, 16), (32, 8), (8, 32)])
@@ -158,6 +159,26 @@ def test_multi_block_multi_view_sh3(D, oracle, tw, th):
     # copies of the block with no view get exactly zero gradient
     gs = grads.to_synth()
     assert np.all(gs.means[off[1]:off[2]] == 0) and np.all(gs.sh[off[1]:off[2]] == 0)
+    check_counts(D, O, vb, f, masks, plan, bg)
+
+
+def check_counts(D, O, vb, f, masks, plan, bg):
+    """dg_rasterize_count: the forward's outputs bit for bit, and the pair
+    counters equal the oracle's per-pixel work summed (exactly when no pixel
+    sits at a decision margin)."""
+    before = [t.clone() for t in (vb.image, vb.T_final, vb.last)]
+    counts = D.dg_rasterize_count(vb, bg).cpu().numpy()
+    for a, b in zip(before, (vb.image, vb.T_final, vb.last)):
+        assert torch.equal(a, b)
+    oc = O.rasterize_counts(f["proj"], f["bins"], plan)
+    seen = sum(int(c["seen"].sum()) for c in oc)
+    used = sum(int(c["used"].sum()) for c in oc)
+    excluded = sum(int((~m).sum()) for m in masks)
+    assert counts[1] <= int(vb.last[:vb.n_pixels].sum()) <= counts[0]
+    if excluded == 0:
+        assert (counts[0], counts[1]) == (seen, used)
+    else:
+        assert abs(counts[0] - seen) <= 1e-3 * seen and abs(counts[1] - used) <= 1e-3 * used
 
 
 def test_losses_match_oracle(D, oracle):
@@ -341,6 +362,7 @@ def test_every_compositing_variant_matches_oracle(D, oracle, warps, stage):
         assert (vb.plan.raster_warps, vb.plan.raster_stage) == (warps, stage)
         check_forward(D, O, vb, f, masks, plan)
         check_backward(D, O, g, grads, ob, 2)
+        check_counts(D, O, vb, f, masks, plan, (0.05, 0.1, 0.15))
     finally:
         D.set_raster_variant(4, 2)
 

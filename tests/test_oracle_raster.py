@@ -192,3 +192,30 @@ def test_empty_scene_gives_background(oracle):
     np.testing.assert_array_equal(v["image"][0], 0.3)
     np.testing.assert_array_equal(v["T_final"], 1.0)
     assert f["bins"]["M"] == 0
+
+
+def test_work_counts(oracle):
+    """Work counters of the compositing: with the occluding stack above the
+    centre pixel examines 3 positions (the third stops it) and composites 2;
+    for a lone Gaussian every pixel of its tiles examines 1 position and
+    the composited ones are exactly the pixels it colours."""
+    O = oracle
+    cam = S.cube_camera(129, 129, f=100.0, distance=4.0)
+    cam.cx = cam.cy = 64.5
+    logit = lambda p: math.log(p / (1 - p))
+    g = S.Gaussians.concat([one([0, 0, 0.0], -0.5, 10.0, [1, 0, 0]), one([0, 0, 1.0], -0.5, logit(0.98), [0, 1, 0]),
+                            one([0, 0, 2.0], -0.5, logit(0.6), [0, 0, 1])])
+    f, plan = render1(O, g, cam)
+    cnt = O.rasterize_counts(f["proj"], f["bins"], plan)[0]
+    assert (cnt["seen"][64, 64], cnt["used"][64, 64]) == (3, 2)
+    assert (cnt["used"] <= cnt["seen"]).all()
+    assert (cnt["used"] >= (f["views"][0]["last"] > 0)).all()
+    cam1 = S.cube_camera(96, 80, f=110.0, distance=4.0)
+    g1 = one([0.0, 0.0, 0.0], -2.0, 0.4, [0.9, 0.5, 0.2])
+    f1, plan1 = render1(O, g1, cam1)
+    c1 = O.rasterize_counts(f1["proj"], f1["bins"], plan1)[0]
+    x0, y0, x1, y1 = f1["proj"]["rect"][0]
+    in_rect = np.zeros((80, 96), bool)
+    in_rect[y0 * 16:y1 * 16, x0 * 16:x1 * 16] = True
+    np.testing.assert_array_equal(c1["seen"], in_rect.astype(np.uint32))
+    np.testing.assert_array_equal(c1["used"], (f1["views"][0]["image"].max(0) > 0).astype(np.uint32))
