@@ -144,7 +144,12 @@ int dg_project(const dg_gaussians* x, const dg_camera* dev_cams, const dg_plan* 
 
 /* ---- tile binning and the key sort (K2-K4) ------------------------------- */
 /* One instance per (record, covered tile), key = (tile << 32) | bits(depth),
- * value = record index, sorted ascending by (key, value).  Outputs: vals
+ * value = record index, sorted ascending by (key, value).  A tile of the
+ * record's rectangle is covered when some pixel centre of it can reach
+ * alpha >= 1/255: min over the tile's pixel-centre box of q(d) = a dx^2 +
+ * 2 b dx dy + c dy^2 is at most 2 ln(255 o) (1 + 2^-10) + 2^-6 (a widened
+ * form of Eq. 2's 1/255 skip; the compositing would skip every pair of the
+ * other tiles, so no image or gradient depends on it).  Outputs: vals
  * (capacity entries), keys (optional, NULL to skip), ranges[2 t] = first
  * and end index of tile t (empty tiles: start == end), dev_count[0] = number
  * of instances M.  If M > capacity the DG_STATUS_CAPACITY bit is set and

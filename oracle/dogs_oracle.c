@@ -186,6 +186,50 @@ static void to_camera(const oc_cam* cam, const double* mu, double* t)
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* tile culling at binning: a reading of Eq. 2's 1/255 rule                   */
+/* ------------------------------------------------------------------------ */
+/* A pixel at offset d from the mean can only be composited if               */
+/* o exp(-q(d) / 2) >= 1/255, q(d) = a dx^2 + 2 b dx dy + c dy^2, i.e.        */
+/* q(d) <= 2 ln(255 o).  A tile of the record's rectangle is binned only if   */
+/* the minimum of q over the box of its pixel centres is within that bound,  */
+/* widened to tau = 2 ln(255 o) (1 + 2^-10) + 2^-6 so that no FP32 decision   */
+/* of the compositing can fall outside it.  Dropped pairs would all be       */
+/* skipped by the compositing, so images and gradients are unchanged.        */
+static double cull_tau(double o) { return 2.0 * log(255.0 * o) * (1.0 + 1.0 / 1024.0) + 1.0 / 64.0; }
+
+static double dclamp(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* minimum of the convex q over [X0, X1] x [Y0, Y1] (offsets from the mean):  */
+/* 0 if the box holds the mean, else the least of the four edge minima, each */
+/* edge minimiser being the unconstrained one clamped to the edge.           */
+static double box_qmin(double a, double b, double c, double X0, double X1, double Y0, double Y1)
+{
+    if (X0 <= 0.0 && 0.0 <= X1 && Y0 <= 0.0 && 0.0 <= Y1) return 0.0;
+    double best = INFINITY, xs[2] = {X0, X1}, ys[2] = {Y0, Y1};
+    for (int i = 0; i < 2; i++) {
+        double X = xs[i], y = dclamp(-b * X / c, Y0, Y1);
+        best = fmin(best, a * X * X + 2.0 * b * X * y + c * y * y);
+        double Y = ys[i], x = dclamp(-b * Y / a, X0, X1);
+        best = fmin(best, a * x * x + 2.0 * b * x * Y + c * Y * Y);
+    }
+    return best;
+}
+
+/* exported for the tests: box_qmin */
+double oc_box_qmin(double a, double b, double c, double X0, double X1, double Y0, double Y1)
+{
+    return box_qmin(a, b, c, X0, X1, Y0, Y1);
+}
+
+/* q-minimum of tile (tx, ty) for a record; the box spans the pixel centres */
+static double tile_qmin(const double* rec, int tx, int ty, int tile_w, int tile_h)
+{
+    double X0 = tx * tile_w + 0.5 - rec[REC_MX], X1 = tx * tile_w + tile_w - 0.5 - rec[REC_MX];
+    double Y0 = ty * tile_h + 0.5 - rec[REC_MY], Y1 = ty * tile_h + tile_h - 0.5 - rec[REC_MY];
+    return box_qmin(rec[REC_A], rec[REC_B], rec[REC_C], X0, X1, Y0, Y1);
+}
+
 static int project_one(const double* x, int K, const oc_cam* cam, int tile_w, int tile_h,
                        double* rec, int32_t* rect, float* depth_key, double* margin, proj_tmp* tp)
 {
@@ -264,6 +308,12 @@ static int project_one(const double* x, int K, const oc_cam* cam, int tile_w, in
     rec[REC_RADIUS] = radius; rec[REC_TILES] = tiles; rec[REC_VIS] = 1.0;
     rect[0] = x0; rect[1] = y0; rect[2] = x1; rect[3] = y1;
     *depth_key = (float)tz;
+    /* margin of every tile-culling decision */
+    double tau = cull_tau(T->o);
+    for (int ty = y0; ty < y1; ty++)
+        for (int tx = x0; tx < x1; tx++)
+            mg = fmin(mg, fabs(tile_qmin(rec, tx, ty, tile_w, tile_h) - tau) / (1.0 + fabs(tau)));
+    *margin = mg;
     return 1;
 }
 
@@ -292,17 +342,27 @@ static int kv_cmp(const void* A, const void* B)
     return 0;
 }
 
-/* Records r of all views: view[r], rect[4r..], depth_key[r], visible[r].     */
-/* Per view: tile_off[v], tiles_x[v].  Writes keys/vals (count returned; at   */
-/* most `capacity` written) and ranges[2*tile] for n_tiles tiles.             */
+/* Records r of all views: view[r], rect[4r..], depth_key[r], visible[r],    */
+/* rec[REC_N r..].  Per view: tile_off[v], tiles_x[v].  Writes keys/vals      */
+/* (count returned; at most `capacity` written) and ranges[2*tile] for        */
+/* n_tiles tiles.  cull != 0 drops the tiles the record cannot reach (above). */
+static int keep_tile(int cull, const double* rec, int tx, int ty, int tile_w, int tile_h)
+{
+    return !cull || tile_qmin(rec, tx, ty, tile_w, tile_h) <= cull_tau(rec[REC_OP]);
+}
+
 int64_t oc_bin_sort(int64_t n_rec, const int32_t* view, const int32_t* rect, const float* depth_key,
                     const int32_t* visible, const int32_t* tile_off, const int32_t* tiles_x,
                     int64_t n_tiles, int64_t capacity, uint64_t* keys, uint32_t* vals,
-                    uint32_t* ranges)
+                    uint32_t* ranges, const double* rec, int tile_w, int tile_h, int cull)
 {
     int64_t M = 0;
-    for (int64_t r = 0; r < n_rec; r++)
-        if (visible[r]) M += (int64_t)(rect[4 * r + 2] - rect[4 * r]) * (rect[4 * r + 3] - rect[4 * r + 1]);
+    for (int64_t r = 0; r < n_rec; r++) {
+        if (!visible[r]) continue;
+        for (int ty = rect[4 * r + 1]; ty < rect[4 * r + 3]; ty++)
+            for (int tx = rect[4 * r]; tx < rect[4 * r + 2]; tx++)
+                M += keep_tile(cull, rec + r * REC_N, tx, ty, tile_w, tile_h);
+    }
     if (M > capacity) return M;
     kv* list = (kv*)malloc(sizeof(kv) * (M > 0 ? M : 1));
     int64_t p = 0;
@@ -311,6 +371,7 @@ int64_t oc_bin_sort(int64_t n_rec, const int32_t* view, const int32_t* rect, con
         uint32_t dbits; memcpy(&dbits, &depth_key[r], 4);
         for (int ty = rect[4 * r + 1]; ty < rect[4 * r + 3]; ty++)
             for (int tx = rect[4 * r]; tx < rect[4 * r + 2]; tx++) {
+                if (!keep_tile(cull, rec + r * REC_N, tx, ty, tile_w, tile_h)) continue;
                 uint64_t tile = (uint64_t)tile_off[view[r]] + (uint64_t)ty * tiles_x[view[r]] + tx;
                 list[p].key = (tile << 32) | dbits;
                 list[p].val = (uint32_t)r;

@@ -59,10 +59,12 @@ def lib():
                                     dp, ip, fp, dp]
         _lib.oc_bin_sort.restype = C.c_int64
         _lib.oc_bin_sort.argtypes = [C.c_int64, ip, ip, fp, ip, ip, ip, C.c_int64, C.c_int64,
-                                     u64p, u32p, u32p]
+                                     u64p, u32p, u32p, dp, C.c_int, C.c_int, C.c_int]
         _lib.oc_rasterize_fwd.restype = None
         _lib.oc_rasterize_fwd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, u32p, u32p,
                                           dp, dp, dp, dp, u32p, dp, dp]
+        _lib.oc_box_qmin.restype = C.c_double
+        _lib.oc_box_qmin.argtypes = [C.c_double] * 7
         _lib.oc_rasterize_counts.restype = None
         _lib.oc_rasterize_counts.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, u32p, u32p,
                                              dp, u32p, u32p]
@@ -191,8 +193,12 @@ def project_views(x: np.ndarray, sh_degree: int, plan: ViewPlan) -> dict:
             "view": cat(views, np.int32, (0,))}
 
 
-def bin_sort(proj: dict, plan: ViewPlan) -> dict:
+def bin_sort(proj: dict, plan: ViewPlan, cull: bool = True) -> dict:
+    """Instances of the records' tile rectangles, sorted by (tile, depth,
+    record); with cull, tiles no pixel centre of which can reach alpha >=
+    1/255 are left out (the images do not depend on it)."""
     n = proj["rec"].shape[0]
+    rec = np.ascontiguousarray(proj["rec"], np.float64) if n else np.zeros((1, REC_N))
     vis = np.ascontiguousarray(proj["rec"][:, REC_VIS].astype(np.int32))
     view = np.ascontiguousarray(proj["view"], np.int32)
     rect = np.ascontiguousarray(proj["rect"], np.int32)
@@ -205,13 +211,13 @@ def bin_sort(proj: dict, plan: ViewPlan) -> dict:
     M = lib().oc_bin_sort(n, _p(view, C.c_int32), _p(rect, C.c_int32), _p(dk, C.c_float),
                           _p(vis, C.c_int32), _p(toff, C.c_int32), _p(tx, C.c_int32),
                           plan.n_tiles, 0, _p(empty64, C.c_uint64), _p(empty32, C.c_uint32),
-                          _p(ranges, C.c_uint32))
+                          _p(ranges, C.c_uint32), _p(rec, C.c_double), plan.tw, plan.th, int(cull))
     keys = np.zeros(max(M, 1), np.uint64)
     vals = np.zeros(max(M, 1), np.uint32)
     lib().oc_bin_sort(n, _p(view, C.c_int32), _p(rect, C.c_int32), _p(dk, C.c_float),
                       _p(vis, C.c_int32), _p(toff, C.c_int32), _p(tx, C.c_int32),
                       plan.n_tiles, M, _p(keys, C.c_uint64), _p(vals, C.c_uint32),
-                      _p(ranges, C.c_uint32))
+                      _p(ranges, C.c_uint32), _p(rec, C.c_double), plan.tw, plan.th, int(cull))
     return {"keys": keys[:M], "vals": vals[:M], "ranges": ranges, "M": int(M)}
 
 
@@ -282,9 +288,19 @@ def project_bwd(x: np.ndarray, sh_degree: int, plan: ViewPlan, drec: np.ndarray)
 # --------------------------------------------------------------------------
 # whole passes
 # --------------------------------------------------------------------------
-def render(x: np.ndarray, sh_degree: int, plan: ViewPlan, bg=(0.0, 0.0, 0.0)) -> dict:
+def box_qmin(a, b, c, X0, X1, Y0, Y1) -> float:
+    """Minimum of a x^2 + 2 b x y + c y^2 over [X0, X1] x [Y0, Y1]."""
+    return lib().oc_box_qmin(a, b, c, X0, X1, Y0, Y1)
+
+
+def cull_tau(o: float) -> float:
+    """Widened bound on q(d) for alpha >= 1/255 (see bin_sort)."""
+    return 2.0 * np.log(255.0 * o) * (1.0 + 1.0 / 1024.0) + 1.0 / 64.0
+
+
+def render(x: np.ndarray, sh_degree: int, plan: ViewPlan, bg=(0.0, 0.0, 0.0), cull: bool = True) -> dict:
     proj = project_views(x, sh_degree, plan)
-    bins = bin_sort(proj, plan)
+    bins = bin_sort(proj, plan, cull)
     views = rasterize_fwd(proj, bins, plan, bg)
     return {"proj": proj, "bins": bins, "views": views}
 

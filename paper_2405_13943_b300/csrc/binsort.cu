@@ -1,8 +1,9 @@
 // K2-K4: tile binning and the 64-bit (tile | depth) key sort.
 //
 // Each projected record covers a rectangle of tiles; every (record, tile)
-// pair is an instance with key (tile << 32) | bits(depth) and value = record
-// index.  The instances are sorted by (key, value): by tile first, then by
+// pair whose tile the record can reach at alpha >= 1/255 (tile culling,
+// below) is an instance with key (tile << 32) | bits(depth) and value =
+// record index.  The instances are sorted by (key, value): by tile first, then by
 // depth, ties broken by record index (Sec. 3.1, Eq. 2 composites in depth
 // order within each tile).
 //
@@ -56,9 +57,52 @@ static size_t bin_ws_layout(int64_t n_tiles, int64_t capacity, BinWs* w, char* b
 
 size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity) { return bin_ws_layout(n_tiles, capacity, nullptr, nullptr); }
 
+// ---- tile culling --------------------------------------------------------------
+// A pixel at offset d from the mean is composited only if o exp(-q(d)/2) >=
+// 1/255 with q(d) = a dx^2 + 2 b dx dy + c dy^2 (Eq. 2's skip rule).  A tile
+// of a record's rectangle is binned only if the minimum of q over the box of
+// its pixel centres is at most tau = 2 ln(255 o) (1 + 2^-10) + 2^-6; the
+// widening keeps every pair the compositing could take, so culling changes
+// no image, transmittance or gradient.  q is convex, so its minimum over the
+// box is 0 when the box holds the mean and otherwise lies on an edge, at the
+// edge's unconstrained minimiser clamped to the edge.  Rounding is pinned
+// (no contraction) so that the count and the scatter decide alike.
+struct CullRec {
+    float mx, my, a, b, c, tau;
+};
+
+__device__ __forceinline__ CullRec cull_rec(const float4* __restrict__ rec, int64_t r)
+{
+    const float4 g0 = rec[3 * r], g1 = rec[3 * r + 1];
+    CullRec k;
+    k.mx = g0.x; k.my = g0.y; k.a = g0.z; k.b = g0.w; k.c = g1.x;
+    k.tau = __fmaf_rn(__fmul_rn(2.f, __logf(__fmul_rn(255.f, g1.y))), 1.f + 1.f / 1024.f, 1.f / 64.f);
+    return k;
+}
+
+// minimum over t in [lo, hi] of a X^2 + 2 b X t + c t^2
+__device__ __forceinline__ float edge_qmin(float a, float b, float c, float X, float lo, float hi)
+{
+    const float t = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, X), c), lo), hi);
+    return __fmaf_rn(__fmul_rn(c, t), t, __fmul_rn(X, __fmaf_rn(__fmul_rn(2.f, b), t, __fmul_rn(a, X))));
+}
+
+__device__ __forceinline__ bool tile_reached(const CullRec& k, uint32_t tx, uint32_t ty, int tw, int th)
+{
+    const float X0 = __fsub_rn(__fadd_rn((float)(tx * tw), 0.5f), k.mx);
+    const float X1 = __fsub_rn(__fsub_rn((float)(tx * tw + tw), 0.5f), k.mx);
+    const float Y0 = __fsub_rn(__fadd_rn((float)(ty * th), 0.5f), k.my);
+    const float Y1 = __fsub_rn(__fsub_rn((float)(ty * th + th), 0.5f), k.my);
+    if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return 0.f <= k.tau;
+    const float m = fminf(fminf(edge_qmin(k.a, k.b, k.c, X0, Y0, Y1), edge_qmin(k.a, k.b, k.c, X1, Y0, Y1)),
+                          fminf(edge_qmin(k.c, k.b, k.a, Y0, X0, X1), edge_qmin(k.c, k.b, k.a, Y1, X0, X1)));
+    return m <= k.tau;
+}
+
 // ---- pass 1: instances per tile ------------------------------------------------
-__global__ void __launch_bounds__(256) k_count(const uint2* __restrict__ rect, const dg_camera* __restrict__ cams,
-                                               int n_views, int64_t n_rec, uint32_t* __restrict__ counts)
+__global__ void __launch_bounds__(256) k_count(const uint2* __restrict__ rect, const float4* __restrict__ rec,
+                                               const dg_camera* __restrict__ cams, int n_views, int64_t n_rec,
+                                               int tw, int th, uint32_t* __restrict__ counts)
 {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rec) return;
@@ -67,8 +111,10 @@ __global__ void __launch_bounds__(256) k_count(const uint2* __restrict__ rect, c
     if (x1 <= x0 || y1 <= y0) return;
     int v = find_view_of_rec(cams, n_views, r);
     uint32_t toff = (uint32_t)__ldg(&cams[v].tile_off), TX = (uint32_t)__ldg(&cams[v].tiles_x);
+    const CullRec k = cull_rec(rec, r);
     for (uint32_t ty = y0; ty < y1; ty++)
-        for (uint32_t tx = x0; tx < x1; tx++) atomicAdd(&counts[toff + ty * TX + tx], 1u);
+        for (uint32_t tx = x0; tx < x1; tx++)
+            if (tile_reached(k, tx, ty, tw, th)) atomicAdd(&counts[toff + ty * TX + tx], 1u);
 }
 
 // ---- CTA-wide exclusive scan of one value per thread (1024 threads) -----------
@@ -173,7 +219,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
 // ---- pass 2: scatter (depth bits, record) into tile segments ------------------------
 __global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ rect, const float4* __restrict__ rec,
                                                  const dg_camera* __restrict__ cams, int n_views, int64_t n_rec,
-                                                 const uint32_t* __restrict__ dev_count, int64_t capacity,
+                                                 int tw, int th, const uint32_t* __restrict__ dev_count,
+                                                 int64_t capacity, const uint32_t* __restrict__ ranges,
                                                  uint32_t* __restrict__ cursor, uint64_t* __restrict__ pairs)
 {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -185,10 +232,13 @@ __global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ rect,
     int v = find_view_of_rec(cams, n_views, r);
     uint32_t toff = (uint32_t)__ldg(&cams[v].tile_off), TX = (uint32_t)__ldg(&cams[v].tiles_x);
     uint64_t pr = ((uint64_t)__float_as_uint(rec[3 * r + 2].y) << 32) | (uint64_t)(uint32_t)r;
+    const CullRec k = cull_rec(rec, r);
     for (uint32_t ty = y0; ty < y1; ty++)
         for (uint32_t tx = x0; tx < x1; tx++) {
-            uint32_t pos = atomicAdd(&cursor[toff + ty * TX + tx], 1u);
-            pairs[pos] = pr;
+            if (!tile_reached(k, tx, ty, tw, th)) continue;
+            const uint32_t t = toff + ty * TX + tx;
+            uint32_t pos = atomicAdd(&cursor[t], 1u);
+            if (pos < ranges[2 * t + 1]) pairs[pos] = pr;   // never false: the count decided alike
         }
 }
 
@@ -389,7 +439,8 @@ int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams,
     int64_t n_chunks = (plan.n_tiles + kScanChunk - 1) / kScanChunk;
     if (cudaMemsetAsync(w.counts, 0, 4 * (size_t)(plan.n_tiles + 3), st) != cudaSuccess) return DG_ERR_CUDA;
     if (plan.n_rec > 0) {
-        k_count<<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(rect, cams, plan.n_views, plan.n_rec, w.counts);
+        k_count<<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(rect, rec, cams, plan.n_views, plan.n_rec,
+                                                                      plan.tile_w, plan.tile_h, w.counts);
         note_launch();
     }
     k_scan_reduce<<<(unsigned)n_chunks, kScanThreads, 0, st>>>(w.counts, plan.n_tiles, w.partials);
@@ -399,7 +450,8 @@ int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams,
     note_launch(3);
     if (plan.n_rec > 0) {
         k_scatter<<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(rect, rec, cams, plan.n_views, plan.n_rec,
-                                                                        dev_count, capacity, w.cursor, w.pairs);
+                                                                        plan.tile_w, plan.tile_h, dev_count,
+                                                                        capacity, ranges, w.cursor, w.pairs);
         note_launch();
     }
     uint32_t* counters = w.counts + plan.n_tiles;

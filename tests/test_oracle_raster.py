@@ -159,7 +159,7 @@ def test_keys_values_ranges_properties(oracle):
     plan = O.ViewPlan(cams, [(0, 300), (100, 250)], 16, 16)
     x = O.params_from(g)
     proj = O.project_views(x, 0, plan)
-    b = O.bin_sort(proj, plan)
+    b = O.bin_sort(proj, plan, cull=False)
     keys, vals, ranges = b["keys"], b["vals"], b["ranges"]
     # ascending (key, value)
     order = np.lexsort((vals, keys))
@@ -167,6 +167,11 @@ def test_keys_values_ranges_properties(oracle):
     # every record once per tile of its rectangle, with its depth bits
     vis = proj["rec"][:, O.REC_VIS] == 1
     assert b["M"] == int(proj["rec"][vis, O.REC_TILES].sum())
+    # culling keeps a subset: the same list with the unreachable tiles removed
+    bc = O.bin_sort(proj, plan)
+    assert 0 < bc["M"] < b["M"]
+    full = set(zip(keys.tolist(), vals.tolist()))
+    assert set(zip(bc["keys"].tolist(), bc["vals"].tolist())) <= full
     for r in np.nonzero(vis)[0][:50]:
         v = proj["view"][r]
         x0, y0, x1, y1 = proj["rect"][r]
@@ -219,3 +224,81 @@ def test_work_counts(oracle):
     in_rect[y0 * 16:y1 * 16, x0 * 16:x1 * 16] = True
     np.testing.assert_array_equal(c1["seen"], in_rect.astype(np.uint32))
     np.testing.assert_array_equal(c1["used"], (f1["views"][0]["image"].max(0) > 0).astype(np.uint32))
+
+
+def test_box_qmin_against_dense_sampling(oracle):
+    """Minimum of a positive definite quadratic form over a box: never above
+    any sampled point of the box, and reached to within the sampling error."""
+    O = oracle
+    rng = np.random.default_rng(17)
+    for _ in range(300):
+        L = rng.standard_normal((2, 2)) * rng.uniform(0.01, 2.0)
+        Q = L @ L.T + np.eye(2) * 1e-3
+        a, b, c = Q[0, 0], Q[0, 1], Q[1, 1]
+        X0, Y0 = rng.uniform(-20, 20, 2)
+        X1, Y1 = X0 + rng.uniform(0.1, 16), Y0 + rng.uniform(0.1, 16)
+        m = O.box_qmin(a, b, c, X0, X1, Y0, Y1)
+        xs, ys = np.linspace(X0, X1, 301), np.linspace(Y0, Y1, 301)
+        X, Y = np.meshgrid(xs, ys)
+        q = a * X * X + 2 * b * X * Y + c * Y * Y
+        assert m <= q.min() + 1e-9 * (1 + q.min())
+        h = max(X1 - X0, Y1 - Y0) / 300
+        assert q.min() - m <= 2 * (abs(a) + abs(b) + abs(c)) * h * (h + 2 * max(abs(X0), abs(X1), abs(Y0), abs(Y1)))
+        if X0 <= 0 <= X1 and Y0 <= 0 <= Y1:
+            assert m == 0.0
+
+
+def test_culled_tiles_cannot_reach_the_alpha_cut(oracle):
+    """Brute force: for every (record, tile) of its rectangle that binning
+    leaves out, every pixel centre of the tile has o exp(-q/2) < 1/255."""
+    O = oracle
+    g = S.cube_scene(400, 23, log_scale_mu=-2.2)
+    cams = [S.cube_camera(96, 80, f=90.0)]
+    plan = O.ViewPlan(cams, [(0, g.n)], 16, 16)
+    proj = O.project_views(O.params_from(g), 0, plan)
+    bc = O.bin_sort(proj, plan)
+    kept = set(zip((bc["keys"] >> np.uint64(32)).astype(np.int64).tolist(), bc["vals"].tolist()))
+    dropped = 0
+    for r in np.nonzero(proj["rec"][:, O.REC_VIS] == 1)[0]:
+        rec = proj["rec"][r]
+        x0, y0, x1, y1 = proj["rect"][r]
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                if (ty * plan.tiles_x[0] + tx, r) in kept:
+                    continue
+                dropped += 1
+                X, Y = np.meshgrid(np.arange(tx * 16, tx * 16 + 16) + 0.5 - rec[O.REC_MX],
+                                   np.arange(ty * 16, ty * 16 + 16) + 0.5 - rec[O.REC_MY])
+                q = rec[O.REC_A] * X * X + 2 * rec[O.REC_B] * X * Y + rec[O.REC_C] * Y * Y
+                assert (rec[O.REC_OP] * np.exp(-0.5 * q)).max() < 1 / 255
+    assert dropped > 0
+
+
+def test_culling_changes_no_image_or_gradient(oracle):
+    """Rendering and the adjoint with and without tile culling agree bit for
+    bit: the dropped pairs are all below the 1/255 cut."""
+    O = oracle
+    g = S.cube_scene(600, 29, sh_degree=1, log_scale_mu=-2.4)
+    cams = [S.cube_camera(80, 64, f=70.0), S.cube_camera(48, 72, f=50.0)]
+    plan = O.ViewPlan(cams, [(0, g.n), (0, g.n)], 16, 16)
+    x = O.params_from(g)
+    bg = (0.1, 0.2, 0.3)
+    fc, fu = O.render(x, 1, plan, bg), O.render(x, 1, plan, bg, cull=False)
+    assert fc["bins"]["M"] < fu["bins"]["M"]
+    for v, (vc, vu) in enumerate(zip(fc["views"], fu["views"])):
+        for k in ("image", "T_final"):
+            np.testing.assert_array_equal(vc[k], vu[k])
+        # `last` indexes each tile's list, which culling shortens: the record
+        # it points at is the same
+        for f, vw in ((fc, vc), (fu, vu)):
+            H, W_ = vw["last"].shape
+            ty, tx = np.meshgrid(np.arange(H) // 16, np.arange(W_) // 16, indexing="ij")
+            t = plan.tile_off[v] + ty * plan.tiles_x[v] + tx
+            start = f["bins"]["ranges"][t, 0].astype(np.int64)
+            pos = np.maximum(start + vw["last"].astype(np.int64) - 1, 0)
+            vw["last_rec"] = np.where(vw["last"] > 0, f["bins"]["vals"][pos].astype(np.int64), -1)
+        np.testing.assert_array_equal(vc["last_rec"], vu["last_rec"])
+        assert (vc["last"] <= vu["last"]).all()
+    W = [np.random.default_rng(3 + v).uniform(-1, 1, (3, c.height, c.width)) for v, c in enumerate(cams)]
+    bc, bu = O.backward(x, 1, plan, fc, W, bg), O.backward(x, 1, plan, fu, W, bg)
+    np.testing.assert_allclose(bc["dparams"], bu["dparams"], rtol=1e-12, atol=1e-15)
