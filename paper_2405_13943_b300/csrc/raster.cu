@@ -65,14 +65,20 @@ __device__ __forceinline__ LaneGeom lane_geom(const TileInfo& ti, int tw, int ti
 
 // The exponent (log2 units) of one instance along a thread's strip of PPL
 // pixels (fixed column, rows fy0 + k dy): p(k) = p0 + beta k + gamma k^2 with
-// dx = mx - fx, dy_k = my - fy0 - k dy.  It is evaluated by the exact
-// second-order recurrence p += d1, d1 += 2 gamma (same instructions in the
-// forward and the backward, so both take the same decisions), and the strip's
-// largest value bounds every pixel of it: when even that gives alpha < 2^-8
-// the whole strip skips the instance.
+// dx = mx - fx, dy_k = my - fy0 - k dy.  Each p(k) is evaluated on its own
+// as p0 + k (beta + gamma k) (two fused multiply-adds, no chain across the
+// strip; the forward and the backward use the same instructions, so both
+// take the same decisions), and the strip's largest value bounds every
+// pixel of it: when even that gives alpha < 2^-8 the whole strip skips the
+// instance.
 struct Strip {
-    float p, d1, d2, pmax;
+    float p0, beta, gamma, pmax;
 };
+
+__device__ __forceinline__ float strip_p(const Strip& s, int k)
+{
+    return __fmaf_rn(__fmaf_rn(s.gamma, (float)k, s.beta), (float)k, s.p0);
+}
 
 template <int PPL>
 __device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float B, float C, float fx, float fy0,
@@ -81,33 +87,44 @@ __device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float 
     Strip st;
     const float dx = __fsub_rn(mx, fx), dy0 = __fsub_rn(my, fy0);
     const float t = __fmaf_rn(B, dy0, __fmul_rn(A, dx));
-    st.p = __fmaf_rn(__fmul_rn(C, dy0), dy0, __fmul_rn(dx, t));
-    const float beta = __fmul_rn(-ddy, __fmaf_rn(2.f * C, dy0, __fmul_rn(B, dx)));
-    const float gamma = __fmul_rn(C, __fmul_rn(ddy, ddy));
-    st.d1 = __fadd_rn(beta, gamma);
-    st.d2 = __fmul_rn(2.f, gamma);
+    st.p0 = __fmaf_rn(__fmul_rn(C, dy0), dy0, __fmul_rn(dx, t));
+    st.beta = __fmul_rn(-ddy, __fmaf_rn(2.f * C, dy0, __fmul_rn(B, dx)));
+    st.gamma = __fmul_rn(C, __fmul_rn(ddy, ddy));
     if (PPL == 1) {
-        st.pmax = st.p;
+        st.pmax = st.p0;
     } else {
         // concave in k (gamma < 0): largest at the vertex, clamped to [0, PPL-1]
+        const float beta = st.beta, gamma = st.gamma;
         float ks = gamma < 0.f ? fminf(fmaxf(-beta / (2.f * gamma), 0.f), (float)(PPL - 1)) : 0.f;
-        float pv = st.p + ks * (beta + gamma * ks);
-        float pe = st.p + (float)(PPL - 1) * (beta + gamma * (float)(PPL - 1));
-        st.pmax = fmaxf(fmaxf(pv, pe), st.p) + 1e-3f;   // margin over rounding
+        float pv = st.p0 + ks * (beta + gamma * ks);
+        float pe = st.p0 + (float)(PPL - 1) * (beta + gamma * (float)(PPL - 1));
+        st.pmax = fmaxf(fmaxf(pv, pe), st.p0) + 1e-3f;   // margin over rounding
     }
     return st;
 }
 
-// alpha of the strip's current pixel from its exponent p (0 = skipped)
+// Pixels of the strip that pass the first two tests of a pair: exponent
+// p <= 0 and alpha bound 2^(p + log2 o) >= 2^-8 (below that alpha < 1/255).
+// Evaluated for the whole strip without branches; only the pixels left in
+// the mask take the exponential and the exact 1/255 test (strip_alpha).
+template <int PPL>
+__device__ __forceinline__ uint32_t strip_reach(const Strip& sp, float lo)
+{
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < PPL; k++) {
+        const float p = strip_p(sp, k);
+        m |= (uint32_t)((p <= 0.0f) & (__fadd_rn(p, lo) >= -8.0f)) << k;
+    }
+    return m;
+}
+
+// alpha of a pixel in the strip's reach mask (0 = skipped by the 1/255 rule)
 __device__ __forceinline__ float strip_alpha(float p, float lo, float& raw)
 {
-    if (p > 0.0f) return 0.0f;
-    const float e = __fadd_rn(p, lo);
-    if (e < -8.0f) return 0.0f;          // alpha <= 1/256 < 1/255
-    raw = exp2f(e);
+    raw = exp2f(__fadd_rn(p, lo));
     const float a = fminf(raw, kAlphaMax);
-    if (a < kAlphaMin) return 0.0f;
-    return a;
+    return a < kAlphaMin ? 0.0f : a;
 }
 
 struct Fetch {
@@ -189,15 +206,14 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
             if (CNT) n_seen += __popc(live);
             Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, G.fx, G.fy0, G.dy);
             if (__fadd_rn(sp.pmax, h.y) < -8.0f) continue;   // no pixel of the strip reaches 2^-8
+            const uint32_t todo = live & strip_reach<PPL>(sp, h.y);
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
             bool have_c = false;
-            float p = sp.p, inc = sp.d1;
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
-                if (k > 0) { p = __fadd_rn(p, inc); inc = __fadd_rn(inc, sp.d2); }
-                if (!(live >> k & 1u)) continue;
+                if (!(todo >> k & 1u)) continue;
                 float raw;
-                const float a = strip_alpha(p, h.y, raw);
+                const float a = strip_alpha(strip_p(sp, k), h.y, raw);
                 if (a == 0.f) continue;
                 const float Tn = T[k] * (1.f - a);
                 if (Tn < kTMin) { live &= ~(1u << k); continue; }
@@ -265,8 +281,22 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float* v, float& v8,
     return s;
 }
 
+// Per-pixel inputs of the backward that are read only when a pair
+// contributes (dL/dpixel) or when a pixel joins the walk (last) live in
+// shared memory, indexed by the pixel's slot q = tid + 32 NW k (conflict
+// free: slot q is in bank tid % 32); T and the colour behind B, updated at
+// every composited pair, stay in registers.  A pixel joins the back-to-front
+// walk at position last - 1; each thread keeps a mask of its joined pixels
+// and the next position at which another one joins, so the per-pair test is
+// one bit.
+// register budget: 20 resident single-warp CTAs per SM for NW = 1; for the
+// wider variants 32 warps per SM with one staged instance per thread and 24
+// with two (the budgets that compile without spilling)
 template <int NW, int S>
-__global__ void __launch_bounds__(32 * NW) k_raster_bwd(const float4* __restrict__ rec,
+constexpr int bwd_min_blocks() { return NW == 1 ? 20 : (S == 1 ? 32 : 24) / NW; }
+
+template <int NW, int S>
+__global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd(const float4* __restrict__ rec,
                                                         const uint32_t* __restrict__ vals,
                                                         const uint32_t* __restrict__ ranges,
                                                         const dg_camera* __restrict__ cams, int n_views, int tw,
@@ -281,6 +311,8 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd(const float4* __restrict
     __shared__ float4 s_h[R];   // C, log2 o, 1 / o, record index (bits)
     __shared__ float4 s_k[R];   // conic a, b, c, -
     __shared__ float4 s_c[R];   // colour
+    __shared__ float s_G[3][256];       // dL/dpixel per slot
+    __shared__ uint32_t s_last[256];    // last per slot
     __shared__ uint32_t s_max;
     const int tid = threadIdx.x, lane = tid & 31;
     TileInfo ti;
@@ -288,21 +320,25 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd(const float4* __restrict
     const LaneGeom Lg = lane_geom(ti, tw, tid, NT);
     const int64_t HW = (int64_t)ti.W * ti.H;
     const float* gi = dL_dimage + 3 * ti.pix_off;
-    float T[PPL], B0[PPL], B1[PPL], B2[PPL], G0[PPL], G1[PPL], G2[PPL];
-    uint32_t last[PPL];
+    float T[PPL], B0[PPL], B1[PPL], B2[PPL];
     uint32_t ml = 0;
 #pragma unroll
     for (int k = 0; k < PPL; k++) {
+        const int q = tid + NT * k;
         int py = Lg.py0 + k * Lg.dpy;
-        T[k] = 1.f; G0[k] = G1[k] = G2[k] = 0.f; last[k] = 0;
+        T[k] = 1.f;
         B0[k] = bg0; B1[k] = bg1; B2[k] = bg2;
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        uint32_t lk = 0;
         if (Lg.px < ti.W && py < ti.H) {
             int64_t p = (int64_t)py * ti.W + Lg.px;
-            G0[k] = gi[p]; G1[k] = gi[HW + p]; G2[k] = gi[2 * HW + p];
+            g0 = gi[p]; g1 = gi[HW + p]; g2 = gi[2 * HW + p];
             T[k] = T_final[ti.pix_off + p];
-            last[k] = last_in[ti.pix_off + p];
-            ml = max(ml, last[k]);
+            lk = last_in[ti.pix_off + p];
         }
+        s_G[0][q] = g0; s_G[1][q] = g1; s_G[2][q] = g2;
+        s_last[q] = lk;
+        ml = max(ml, lk);
     }
     uint32_t maxlast = __reduce_max_sync(0xffffffffu, ml);
     if (NW > 1) {
@@ -313,6 +349,8 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd(const float4* __restrict
         maxlast = s_max;
     }
     if (maxlast == 0) return;
+    // joined pixels: bit k set once the walk is below last[k]
+    uint32_t joined = 0, next_join = ml;
     const int rounds = (int)((maxlast + R - 1) / R);
     Fetch nx[S];
 #pragma unroll
@@ -339,6 +377,15 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd(const float4* __restrict
         const int cnt = (int)min((uint32_t)R, maxlast - base);
         for (int j = cnt - 1; j >= 0; j--) {
             const uint32_t pos = base + (uint32_t)j;
+            if (pos < next_join) {              // pixels whose last composited pair is at or after pos
+                next_join = 0;
+#pragma unroll
+                for (int k = 0; k < PPL; k++) {
+                    const uint32_t lk = s_last[tid + NT * k];
+                    if (pos < lk) joined |= 1u << k;
+                    else next_join = max(next_join, lk);
+                }
+            }
             const float4 g = s_g[j];
             const float4 h = s_h[j];
             float gr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -346,25 +393,25 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd(const float4* __restrict
             bool any = false;
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f), kc = make_float4(0.f, 0.f, 0.f, 0.f);
             Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, Lg.fx, Lg.fy0, Lg.dy);
-            const bool reach = __fadd_rn(sp.pmax, h.y) >= -8.0f;
-            float p = sp.p, inc = sp.d1;
+            const uint32_t todo = __fadd_rn(sp.pmax, h.y) >= -8.0f ? joined & strip_reach<PPL>(sp, h.y) : 0u;
             const float dx = g.x - Lg.fx;
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
-                if (k > 0) { p = __fadd_rn(p, inc); inc = __fadd_rn(inc, sp.d2); }
-                if (!reach || pos >= last[k]) continue;
+                if (!(todo >> k & 1u)) continue;
                 float raw = 0.f;
-                const float a = strip_alpha(p, h.y, raw);
+                const float a = strip_alpha(strip_p(sp, k), h.y, raw);
                 if (!(a > 0.f)) continue;
+                const int q = tid + NT * k;
+                const float G0 = s_G[0][q], G1 = s_G[1][q], G2 = s_G[2][q];
                 const float dy = g.y - (Lg.fy0 + k * Lg.dy);
                 if (!any) { c = s_c[j]; kc = s_k[j]; any = true; }
                 const float Tj = T[k] * __fdividef(1.f, 1.f - a);
                 const float wT = a * Tj;
-                gr[6] = fmaf(G0[k], wT, gr[6]);
-                gr[7] = fmaf(G1[k], wT, gr[7]);
-                g8 = fmaf(G2[k], wT, g8);
+                gr[6] = fmaf(G0, wT, gr[6]);
+                gr[7] = fmaf(G1, wT, gr[7]);
+                g8 = fmaf(G2, wT, g8);
                 const float d0 = c.x - B0[k], d1 = c.y - B1[k], d2 = c.z - B2[k];
-                const float dLda = Tj * fmaf(G0[k], d0, fmaf(G1[k], d1, G2[k] * d2));
+                const float dLda = Tj * fmaf(G0, d0, fmaf(G1, d1, G2 * d2));
                 B0[k] = fmaf(a, d0, B0[k]);      // B <- c a + (1 - a) B
                 B1[k] = fmaf(a, d1, B1[k]);
                 B2[k] = fmaf(a, d2, B2[k]);
