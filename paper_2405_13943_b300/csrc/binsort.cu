@@ -99,22 +99,87 @@ __device__ __forceinline__ bool tile_reached(const CullRec& k, uint32_t tx, uint
     return m <= k.tau;
 }
 
-// ---- pass 1: instances per tile ------------------------------------------------
-__global__ void __launch_bounds__(256) k_count(const uint2* __restrict__ rect, const float4* __restrict__ rec,
-                                               const dg_camera* __restrict__ cams, int n_views, int64_t n_rec,
-                                               int tw, int th, uint32_t* __restrict__ counts)
+// ---- passes 1 and 2: expansion of (record, tile) candidates ---------------------
+// Each lane owns one record; the candidate pairs of the warp's 32 records
+// (every tile of each rectangle) are numbered by a warp scan and dealt out 32
+// at a time, so the lanes stay busy however the rectangle sizes vary (most
+// records of a view are empty).  A lane finds the owner of its candidate by
+// a five-step search over the scan and takes the owner's data by shuffles.
+// Pass 1 (SCATTER = false) counts the kept pairs per tile; pass 2 writes them
+// into the tiles' ranges.  Both take the same decisions: the same inputs go
+// through the same instructions.
+template <bool SCATTER>
+__global__ void __launch_bounds__(256) k_expand(const uint2* __restrict__ rect, const float4* __restrict__ rec,
+                                                const dg_camera* __restrict__ cams, int n_views, int64_t n_rec,
+                                                int tw, int th, uint32_t* __restrict__ counts,
+                                                const uint32_t* __restrict__ dev_count, int64_t capacity,
+                                                const uint32_t* __restrict__ ranges, uint32_t* __restrict__ cursor,
+                                                uint64_t* __restrict__ pairs)
 {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rec) return;
-    uint2 rr = rect[r];
-    uint32_t x0 = rr.x & 0xFFFFu, y0 = rr.x >> 16, x1 = rr.y & 0xFFFFu, y1 = rr.y >> 16;
-    if (x1 <= x0 || y1 <= y0) return;
-    int v = find_view_of_rec(cams, n_views, r);
-    uint32_t toff = (uint32_t)__ldg(&cams[v].tile_off), TX = (uint32_t)__ldg(&cams[v].tiles_x);
-    const CullRec k = cull_rec(rec, r);
-    for (uint32_t ty = y0; ty < y1; ty++)
-        for (uint32_t tx = x0; tx < x1; tx++)
-            if (tile_reached(k, tx, ty, tw, th)) atomicAdd(&counts[toff + ty * TX + tx], 1u);
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    if (SCATTER && (int64_t)(*dev_count) > capacity) return;   // uniform over the grid
+    uint32_t x0 = 0, y0 = 0, w = 0, n = 0, toff = 0, TX = 0, dbits = 0;
+    CullRec k = {0.f, 0.f, 0.f, 0.f, 0.f, -1.f};
+    if (r < n_rec) {
+        const uint2 rr = rect[r];
+        x0 = rr.x & 0xFFFFu; y0 = rr.x >> 16;
+        const uint32_t x1 = rr.y & 0xFFFFu, y1 = rr.y >> 16;
+        if (x1 > x0 && y1 > y0) {
+            w = x1 - x0;
+            n = w * (y1 - y0);
+            const int v = find_view_of_rec(cams, n_views, r);
+            toff = (uint32_t)__ldg(&cams[v].tile_off);
+            TX = (uint32_t)__ldg(&cams[v].tiles_x);
+            k = cull_rec(rec, r);
+            if (SCATTER) dbits = __float_as_uint(rec[3 * r + 2].y);
+        }
+    }
+    uint32_t incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t excl = incl - n;
+    const uint32_t rlo = (uint32_t)r;   // record index of this lane (low 32 bits suffice: n_rec < 2^32)
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t item = base + (uint32_t)lane;
+        int o = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1)
+            if (__shfl_sync(0xffffffffu, incl, o + st - 1) <= item) o += st;
+        const int src = o < 31 ? o : 31;
+        const uint32_t oex = __shfl_sync(0xffffffffu, excl, src);
+        const uint32_t ox0 = __shfl_sync(0xffffffffu, x0, src), oy0 = __shfl_sync(0xffffffffu, y0, src);
+        const uint32_t ow = __shfl_sync(0xffffffffu, w, src);
+        const uint32_t otoff = __shfl_sync(0xffffffffu, toff, src), oTX = __shfl_sync(0xffffffffu, TX, src);
+        CullRec ok;
+        ok.mx = __shfl_sync(0xffffffffu, k.mx, src);
+        ok.my = __shfl_sync(0xffffffffu, k.my, src);
+        ok.a = __shfl_sync(0xffffffffu, k.a, src);
+        ok.b = __shfl_sync(0xffffffffu, k.b, src);
+        ok.c = __shfl_sync(0xffffffffu, k.c, src);
+        ok.tau = __shfl_sync(0xffffffffu, k.tau, src);
+        uint32_t od = 0, orec = 0;
+        if (SCATTER) {
+            od = __shfl_sync(0xffffffffu, dbits, src);
+            orec = __shfl_sync(0xffffffffu, rlo, src);
+        }
+        if (item >= total) continue;
+        const uint32_t li = item - oex;
+        const uint32_t dy = li / ow, dx = li - dy * ow;
+        const uint32_t tx = ox0 + dx, ty = oy0 + dy;
+        if (!tile_reached(ok, tx, ty, tw, th)) continue;
+        const uint32_t t = otoff + ty * oTX + tx;
+        if (!SCATTER) {
+            atomicAdd(&counts[t], 1u);
+        } else {
+            const uint32_t pos = atomicAdd(&cursor[t], 1u);
+            if (pos < ranges[2 * t + 1]) pairs[pos] = ((uint64_t)od << 32) | (uint64_t)orec;   // never false
+        }
+    }
 }
 
 // ---- CTA-wide exclusive scan of one value per thread (1024 threads) -----------
@@ -217,31 +282,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
 }
 
 // ---- pass 2: scatter (depth bits, record) into tile segments ------------------------
-__global__ void __launch_bounds__(256) k_scatter(const uint2* __restrict__ rect, const float4* __restrict__ rec,
-                                                 const dg_camera* __restrict__ cams, int n_views, int64_t n_rec,
-                                                 int tw, int th, const uint32_t* __restrict__ dev_count,
-                                                 int64_t capacity, const uint32_t* __restrict__ ranges,
-                                                 uint32_t* __restrict__ cursor, uint64_t* __restrict__ pairs)
-{
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rec) return;
-    if ((int64_t)(*dev_count) > capacity) return;
-    uint2 rr = rect[r];
-    uint32_t x0 = rr.x & 0xFFFFu, y0 = rr.x >> 16, x1 = rr.y & 0xFFFFu, y1 = rr.y >> 16;
-    if (x1 <= x0 || y1 <= y0) return;
-    int v = find_view_of_rec(cams, n_views, r);
-    uint32_t toff = (uint32_t)__ldg(&cams[v].tile_off), TX = (uint32_t)__ldg(&cams[v].tiles_x);
-    uint64_t pr = ((uint64_t)__float_as_uint(rec[3 * r + 2].y) << 32) | (uint64_t)(uint32_t)r;
-    const CullRec k = cull_rec(rec, r);
-    for (uint32_t ty = y0; ty < y1; ty++)
-        for (uint32_t tx = x0; tx < x1; tx++) {
-            if (!tile_reached(k, tx, ty, tw, th)) continue;
-            const uint32_t t = toff + ty * TX + tx;
-            uint32_t pos = atomicAdd(&cursor[t], 1u);
-            if (pos < ranges[2 * t + 1]) pairs[pos] = pr;   // never false: the count decided alike
-        }
-}
-
 // ---- per-segment sort ----------------------------------------------------------------
 // Bitonic network in its "all ascending" form: for each merge size k the
 // first step compares i with its mirror in the k-block, later steps compare
@@ -439,8 +479,9 @@ int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams,
     int64_t n_chunks = (plan.n_tiles + kScanChunk - 1) / kScanChunk;
     if (cudaMemsetAsync(w.counts, 0, 4 * (size_t)(plan.n_tiles + 3), st) != cudaSuccess) return DG_ERR_CUDA;
     if (plan.n_rec > 0) {
-        k_count<<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(rect, rec, cams, plan.n_views, plan.n_rec,
-                                                                      plan.tile_w, plan.tile_h, w.counts);
+        k_expand<false><<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(
+            rect, rec, cams, plan.n_views, plan.n_rec, plan.tile_w, plan.tile_h, w.counts, nullptr, 0, nullptr,
+            nullptr, nullptr);
         note_launch();
     }
     k_scan_reduce<<<(unsigned)n_chunks, kScanThreads, 0, st>>>(w.counts, plan.n_tiles, w.partials);
@@ -449,9 +490,9 @@ int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams,
                                                              capacity, ranges, w.cursor);
     note_launch(3);
     if (plan.n_rec > 0) {
-        k_scatter<<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(rect, rec, cams, plan.n_views, plan.n_rec,
-                                                                        plan.tile_w, plan.tile_h, dev_count,
-                                                                        capacity, ranges, w.cursor, w.pairs);
+        k_expand<true><<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(
+            rect, rec, cams, plan.n_views, plan.n_rec, plan.tile_w, plan.tile_h, nullptr, dev_count, capacity,
+            ranges, w.cursor, w.pairs);
         note_launch();
     }
     uint32_t* counters = w.counts + plan.n_tiles;
