@@ -206,14 +206,17 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
             if (CNT) n_seen += __popc(live);
             Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, G.fx, G.fy0, G.dy);
             if (__fadd_rn(sp.pmax, h.y) < -8.0f) continue;   // no pixel of the strip reaches 2^-8
-            const uint32_t todo = live & strip_reach<PPL>(sp, h.y);
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
             bool have_c = false;
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
-                if (!(todo >> k & 1u)) continue;
+                if (!(live >> k & 1u)) continue;
+                // the reach tests of strip_reach, taken pixel by pixel (the
+                // forward often stops early, so a mask up front would not pay)
+                const float p = strip_p(sp, k);
+                if (!(p <= 0.0f) || !(__fadd_rn(p, h.y) >= -8.0f)) continue;
                 float raw;
-                const float a = strip_alpha(strip_p(sp, k), h.y, raw);
+                const float a = strip_alpha(p, h.y, raw);
                 if (a == 0.f) continue;
                 const float Tn = T[k] * (1.f - a);
                 if (Tn < kTMin) { live &= ~(1u << k); continue; }
