@@ -391,43 +391,54 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             }
             const float4 g = s_g[j];
             const float4 h = s_h[j];
-            float gr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            float g8 = 0.f;
-            bool any = false;
-            float4 c = make_float4(0.f, 0.f, 0.f, 0.f), kc = make_float4(0.f, 0.f, 0.f, 0.f);
             Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, Lg.fx, Lg.fy0, Lg.dy);
             const uint32_t todo = __fadd_rn(sp.pmax, h.y) >= -8.0f ? joined & strip_reach<PPL>(sp, h.y) : 0u;
-            const float dx = g.x - Lg.fx;
+            if (!__any_sync(0xffffffffu, todo != 0u)) continue;
+            const float4 c = s_c[j];
+            // colour sums and the moments of dL/dpower along the strip:
+            // S0 = sum dLdp, S1 = sum k dLdp, S2 = sum k^2 dLdp (dy_k = dy0 - k dy)
+            float c0 = 0.f, c1 = 0.f, c2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
+            bool any = false;
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
                 if (!(todo >> k & 1u)) continue;
                 float raw = 0.f;
                 const float a = strip_alpha(strip_p(sp, k), h.y, raw);
                 if (!(a > 0.f)) continue;
+                any = true;
                 const int q = tid + NT * k;
                 const float G0 = s_G[0][q], G1 = s_G[1][q], G2 = s_G[2][q];
-                const float dy = g.y - (Lg.fy0 + k * Lg.dy);
-                if (!any) { c = s_c[j]; kc = s_k[j]; any = true; }
                 const float Tj = T[k] * __fdividef(1.f, 1.f - a);
                 const float wT = a * Tj;
-                gr[6] = fmaf(G0, wT, gr[6]);
-                gr[7] = fmaf(G1, wT, gr[7]);
-                g8 = fmaf(G2, wT, g8);
+                c0 = fmaf(G0, wT, c0);
+                c1 = fmaf(G1, wT, c1);
+                c2 = fmaf(G2, wT, c2);
                 const float d0 = c.x - B0[k], d1 = c.y - B1[k], d2 = c.z - B2[k];
                 const float dLda = Tj * fmaf(G0, d0, fmaf(G1, d1, G2 * d2));
                 B0[k] = fmaf(a, d0, B0[k]);      // B <- c a + (1 - a) B
                 B1[k] = fmaf(a, d1, B1[k]);
                 B2[k] = fmaf(a, d2, B2[k]);
                 T[k] = Tj;
-                if (raw < kAlphaMax) {
-                    const float dLdp = dLda * a;             // d alpha / d power = alpha
-                    gr[5] = fmaf(dLdp, h.z, gr[5]);         // d alpha / d opacity = alpha / opacity
-                    gr[0] = fmaf(-dLdp, kc.x * dx + kc.y * dy, gr[0]);
-                    gr[1] = fmaf(-dLdp, kc.y * dx + kc.z * dy, gr[1]);
-                    gr[2] = fmaf(-0.5f * dLdp, dx * dx, gr[2]);
-                    gr[3] = fmaf(-dLdp, dx * dy, gr[3]);
-                    gr[4] = fmaf(-0.5f * dLdp, dy * dy, gr[4]);
-                }
+                const float dLdp = raw < kAlphaMax ? dLda * a : 0.f;   // d alpha / d power = alpha below the clamp
+                S0 += dLdp;
+                S1 = fmaf(dLdp, (float)k, S1);
+                S2 = fmaf(dLdp, (float)(k * k), S2);
+            }
+            float gr[8] = {0, 0, 0, 0, 0, 0, c0, c1};
+            float g8 = c2;
+            if (any) {
+                // power = -(a dx^2 + 2 b dx dy + c dy^2) / 2 with dx = mx - px,
+                // dy = my - py; its gradients summed over the strip's pixels
+                const float4 kc = s_k[j];
+                const float dx = g.x - Lg.fx, dy0 = g.y - Lg.fy0;
+                const float Sy = fmaf(-Lg.dy, S1, dy0 * S0);                                  // sum dLdp dy
+                const float Syy = fmaf(Lg.dy * Lg.dy, S2, fmaf(-2.f * dy0 * Lg.dy, S1, dy0 * dy0 * S0));  // sum dLdp dy^2
+                gr[0] = -fmaf(kc.x * dx, S0, kc.y * Sy);
+                gr[1] = -fmaf(kc.y * dx, S0, kc.z * Sy);
+                gr[2] = -0.5f * dx * dx * S0;
+                gr[3] = -dx * Sy;
+                gr[4] = -0.5f * Syy;
+                gr[5] = S0 * h.z;                       // d alpha / d opacity = alpha / opacity
             }
             if (!__any_sync(0xffffffffu, any)) continue;
             const float sred = warp_reduce_scatter8(gr, g8, lane);
