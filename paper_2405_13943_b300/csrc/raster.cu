@@ -95,7 +95,7 @@ __device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float 
     } else {
         // concave in k (gamma < 0): largest at the vertex, clamped to [0, PPL-1]
         const float beta = st.beta, gamma = st.gamma;
-        float ks = gamma < 0.f ? fminf(fmaxf(-beta / (2.f * gamma), 0.f), (float)(PPL - 1)) : 0.f;
+        float ks = gamma < 0.f ? fminf(fmaxf(__fdividef(-beta, 2.f * gamma), 0.f), (float)(PPL - 1)) : 0.f;
         float pv = st.p0 + ks * (beta + gamma * ks);
         float pe = st.p0 + (float)(PPL - 1) * (beta + gamma * (float)(PPL - 1));
         st.pmax = fmaxf(fmaxf(pv, pe), st.p0) + 1e-3f;   // margin over rounding
@@ -119,10 +119,18 @@ __device__ __forceinline__ uint32_t strip_reach(const Strip& sp, float lo)
     return m;
 }
 
+// 2^x by the SFU (PTX ex2.approx.ftz; x >= -8 here, so no denormal result)
+__device__ __forceinline__ float ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // alpha of a pixel in the strip's reach mask (0 = skipped by the 1/255 rule)
 __device__ __forceinline__ float strip_alpha(float p, float lo, float& raw)
 {
-    raw = exp2f(__fadd_rn(p, lo));
+    raw = ex2(__fadd_rn(p, lo));
     const float a = fminf(raw, kAlphaMax);
     return a < kAlphaMin ? 0.0f : a;
 }
@@ -206,8 +214,7 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
             if (CNT) n_seen += __popc(live);
             Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, G.fx, G.fy0, G.dy);
             if (__fadd_rn(sp.pmax, h.y) < -8.0f) continue;   // no pixel of the strip reaches 2^-8
-            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-            bool have_c = false;
+            const float4 c = s_c[j];
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
                 if (!(live >> k & 1u)) continue;
@@ -220,7 +227,6 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
                 if (a == 0.f) continue;
                 const float Tn = T[k] * (1.f - a);
                 if (Tn < kTMin) { live &= ~(1u << k); continue; }
-                if (!have_c) { c = s_c[j]; have_c = true; }
                 const float wt = a * T[k];
                 C0[k] = fmaf(c.x, wt, C0[k]);
                 C1[k] = fmaf(c.y, wt, C1[k]);
