@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-autotune", action="store_true", help="keep --tile and the default compositing variant")
-    ap.add_argument("--variant", default=None, help="compositing variant W,S (warps per tile, staged per thread)")
+    ap.add_argument("--variant", default=None,
+                    help="compositing variant W,S[,Wb,Sb] (warps per tile, staged per thread; backward)")
     ap.add_argument("--loss", default="dssim", choices=["dssim", "l1"])
     ap.add_argument("--profile", action="store_true", help="setup + warmup + a few eager steps only (for ncu)")
     return ap.parse_args()
@@ -411,10 +412,13 @@ def run_ours(args, dist, rank, world):
                                    f"{WORKLOADS[args.workload]['width']}x{WORKLOADS[args.workload]['height']}",
                        "blocks": wl.split.K, "copies": wl.split.n_copies, "views_per_step": len(wl.views[0]),
                        "tile": f"{tr.tile[0]}x{tr.tile[1]}",
-                       "raster_variant": {"warps_per_tile": tr.vb.plan.raster_warps,
-                                          "staged_per_thread": tr.vb.plan.raster_stage},
+                       "raster_variant": {"fwd": {"warps_per_tile": tr.vb.plan.raster_warps,
+                                                  "staged_per_thread": tr.vb.plan.raster_stage},
+                                          "bwd": {"warps_per_tile": tr.vb.plan.raster_warps_bwd or tr.vb.plan.raster_warps,
+                                                  "staged_per_thread": tr.vb.plan.raster_stage_bwd or tr.vb.plan.raster_stage}},
                        "autotune": (None if tuned is None else
-                                    {"best_ms": tuned["ms"], "candidates": len(tuned["candidates"])}),
+                                    {"best_ms": tuned["ms"], "tiles": len(tuned["candidates"]),
+                                     "variants_per_tile": len(tuned["candidates"][0]["variants"])}),
                        "loss": "0.8 L1 + 0.2 D-SSIM" if args.loss == "dssim" else "L1",
                        "consensus_every_timed_step": True, "cuda_graph": True,
                        "l2": "working set > L2 (no flush needed)", "instances_per_step": instances,

@@ -117,6 +117,9 @@ typedef struct dg_plan {
      * them): warps per tile in {1, 2, 4, 8} (8 / warps pixels per thread) and
      * instances staged per thread per round in {1, 2} */
     int32_t raster_warps, raster_stage;
+    /* the backward's variant, same ranges; 0, 0 (the dg_plan_views default)
+     * = the forward's */
+    int32_t raster_warps_bwd, raster_stage_bwd;
 } dg_plan;
 
 /* Fill the derived camera fields (host array cams[n_views]) and the plan.

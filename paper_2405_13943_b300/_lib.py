@@ -53,7 +53,8 @@ class DgPlan(C.Structure):
                 ("blk_off", C.c_int64 * (DG_MAX_BLOCKS + 1)),
                 ("blk_view_off", C.c_int32 * (DG_MAX_BLOCKS + 1)),
                 ("max_width", C.c_int32), ("max_height", C.c_int32),
-                ("raster_warps", C.c_int32), ("raster_stage", C.c_int32)]
+                ("raster_warps", C.c_int32), ("raster_stage", C.c_int32),
+                ("raster_warps_bwd", C.c_int32), ("raster_stage_bwd", C.c_int32)]
 
 
 _vp = C.c_void_p

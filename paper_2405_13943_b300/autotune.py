@@ -1,14 +1,19 @@
 """Autotuner of the rasteriser configuration: tile shape (16x16, 32x8, 8x32)
-x compositing variant (warps per tile 1/2/4/8, i.e. 8/4/2/1 pixels per
-thread, and 1 or 2 instances staged per thread per round = Gaussians per
-batch).  Each candidate is timed on the workload itself: full eager
+x compositing variant of the forward and of the backward, each (warps per
+tile 1/2/4/8, i.e. 8/4/2/1 pixels per thread, and 1 or 2 instances staged
+per thread per round = Gaussians per batch).
+
+For every tile shape the forward and the backward variants are chosen
+separately from their own kernel times (CUDA events around the two calls,
+on the workload itself); the tile shapes are then compared by full eager
 iterations (projection, binning, compositing, loss, backward, x-step) with
-CUDA events; the fastest is applied and cached per workload signature."""
+their chosen variants.  The fastest is applied and cached per workload
+signature."""
 from __future__ import annotations
 
 import json
 import os
-from typing import Dict, Optional, Sequence
+from typing import Dict, Sequence, Tuple
 
 import torch
 
@@ -28,8 +33,7 @@ def signature(tr) -> str:
 
 
 def _time_steps(tr, steps: int) -> float:
-    for _ in range(1):
-        tr.step(consensus=False, graph=False)
+    tr.step(consensus=False, graph=False)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -42,6 +46,40 @@ def _time_steps(tr, steps: int) -> float:
     return e0.elapsed_time(e1) / steps
 
 
+def _kernel_times(tr, steps: int) -> Tuple[float, float]:
+    """Mean forward and backward compositing times (ms) over the pool
+    entries, the model left unchanged."""
+    vb = tr.vb
+    fw = bw = 0.0
+    for i in range(steps + 1):
+        p = i % len(tr.view_sets)
+        vb.dev_cams.copy_(tr.cam_pool[p])
+        D.dg_project(tr.x, vb)
+        D.dg_bin_sort(vb)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        D.dg_rasterize_fwd(vb, tr.bg)
+        ev[1].record()
+        tr._loss(tr.targets[p])
+        ev[2].record()
+        D.dg_rasterize_bwd(vb, tr.x, tr.grad, bg=tr.bg)
+        ev[3].record()
+        torch.cuda.synchronize()
+        if i > 0:
+            fw += ev[0].elapsed_time(ev[1]) / steps
+            bw += ev[2].elapsed_time(ev[3]) / steps
+    if tr.overflowed():
+        return float("inf"), float("inf")
+    return fw, bw
+
+
+def _apply(tr, best: Dict) -> None:
+    tr.set_tile(tuple(best["tile"]))
+    v = list(best["fwd"]) + list(best["bwd"])
+    tr.set_variant(*v)
+    D.set_raster_variant(*v)
+
+
 def tune(tr, tiles: Sequence = TILES, warps: Sequence[int] = WARPS, stages: Sequence[int] = STAGES,
          steps: int = 3, use_cache: bool = True) -> Dict:
     key = signature(tr)
@@ -51,27 +89,31 @@ def tune(tr, tiles: Sequence = TILES, warps: Sequence[int] = WARPS, stages: Sequ
             cache = json.load(open(CACHE))
         except ValueError:
             cache = {}
-    if use_cache and key in cache:
+    if use_cache and key in cache and "fwd" in cache[key]:
         best = cache[key]
-        tr.set_tile(tuple(best["tile"]))
-        tr.set_variant(best["warps"], best["stage"])
-        D.set_raster_variant(best["warps"], best["stage"])
+        _apply(tr, best)
         return dict(best, cached=True)
     results = []
     for tile in tiles:
         tr.set_tile(tile)
+        per = {}
         for w in warps:
             for s in stages:
                 tr.set_variant(w, s)
-                ms = _time_steps(tr, steps)
-                results.append({"tile": list(tile), "warps": w, "stage": s, "ms": round(ms, 4)})
+                per[(w, s)] = _kernel_times(tr, steps)
+        bf = min(per, key=lambda v: per[v][0])
+        bb = min(per, key=lambda v: per[v][1])
+        tr.set_variant(*bf, *bb)
+        ms = _time_steps(tr, steps)
+        results.append({"tile": list(tile), "fwd": list(bf), "bwd": list(bb), "ms": round(ms, 4),
+                        "fwd_ms": round(per[bf][0], 4), "bwd_ms": round(per[bb][1], 4),
+                        "variants": {f"{w},{s}": [round(per[(w, s)][0], 4), round(per[(w, s)][1], 4)]
+                                     for (w, s) in per}})
     best = min(results, key=lambda r: r["ms"])
-    tr.set_tile(tuple(best["tile"]))
-    tr.set_variant(best["warps"], best["stage"])
-    D.set_raster_variant(best["warps"], best["stage"])
+    _apply(tr, best)
     out = dict(best, candidates=results, cached=False)
     if use_cache:
-        cache[key] = {k: best[k] for k in ("tile", "warps", "stage", "ms")}
+        cache[key] = {k: best[k] for k in ("tile", "fwd", "bwd", "ms")}
         with open(CACHE, "w") as f:
             json.dump(cache, f, indent=1)
     return out

@@ -61,6 +61,8 @@ static bool valid_plan(const dg_plan* p)
     if (p->n_rec < 0 || p->n_rec >= (int64_t)0xFFFFFFFFll || p->n_tiles < 0 || p->n_tiles > (int64_t)1 << 24) return false;
     if (!(p->raster_warps == 1 || p->raster_warps == 2 || p->raster_warps == 4 || p->raster_warps == 8)) return false;
     if (!(p->raster_stage == 1 || p->raster_stage == 2)) return false;
+    const int wb = p->raster_warps_bwd, sb = p->raster_stage_bwd;
+    if (!((wb == 0 && sb == 0) || ((wb == 1 || wb == 2 || wb == 4 || wb == 8) && (sb == 1 || sb == 2)))) return false;
     return true;
 }
 
@@ -106,6 +108,8 @@ int dg_plan_views(dg_camera* cams, int n_views, const int64_t* blk_off, int n_bl
     p.tile_h = tile_h;
     p.raster_warps = 4;
     p.raster_stage = 2;
+    p.raster_warps_bwd = 0;
+    p.raster_stage_bwd = 0;
     if (blk_off[0] != 0) return DG_ERR_INVALID;
     for (int k = 0; k <= n_blocks; k++) {
         if (k > 0 && blk_off[k] < blk_off[k - 1]) return DG_ERR_INVALID;

@@ -18,7 +18,8 @@
 // memory (NW sets of atomics per instance and tile).
 //
 // The variant (NW in {1, 2, 4, 8}, S in {1, 2}) and the tile shape are
-// chosen per workload by the autotuner (plan.raster_warps / raster_stage).
+// chosen per workload by the autotuner (plan.raster_warps / raster_stage,
+// and raster_warps_bwd / raster_stage_bwd for the backward).
 #include "common.cuh"
 
 namespace dg {
@@ -488,8 +489,8 @@ static void bwd_launch(const float4* rec, const uint32_t* vals, const uint32_t* 
                                                                  dL_dimage, drec);
 }
 
-#define DG_RASTER_DISPATCH(FN, ...)                                          \
-    switch (plan.raster_warps * 10 + plan.raster_stage) {                    \
+#define DG_RASTER_DISPATCH(P, FN, ...)                                       \
+    switch (P.raster_warps * 10 + P.raster_stage) {                          \
     case 11: FN<1, 1>(__VA_ARGS__); break;                                   \
     case 12: FN<1, 2>(__VA_ARGS__); break;                                   \
     case 21: FN<2, 1>(__VA_ARGS__); break;                                   \
@@ -506,7 +507,7 @@ int launch_raster_fwd(const float4* rec, const uint32_t* vals, const uint32_t* r
                       cudaStream_t st)
 {
     if (plan.n_tiles == 0) return DG_OK;
-    DG_RASTER_DISPATCH(fwd_launch, rec, vals, ranges, cams, plan, bg, image, T_final, last, st)
+    DG_RASTER_DISPATCH(plan, fwd_launch, rec, vals, ranges, cams, plan, bg, image, T_final, last, st)
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;
@@ -518,7 +519,7 @@ int launch_raster_count(const float4* rec, const uint32_t* vals, const uint32_t*
 {
     if (cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return DG_ERR_CUDA;
     if (plan.n_tiles == 0) return DG_OK;
-    DG_RASTER_DISPATCH(count_launch, rec, vals, ranges, cams, plan, bg, image, T_final, last, counts, st)
+    DG_RASTER_DISPATCH(plan, count_launch, rec, vals, ranges, cams, plan, bg, image, T_final, last, counts, st)
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;
@@ -529,7 +530,12 @@ int launch_raster_bwd(const float4* rec, const uint32_t* vals, const uint32_t* r
                       const float* dL_dimage, float* drec, cudaStream_t st)
 {
     if (plan.n_tiles == 0) return DG_OK;
-    DG_RASTER_DISPATCH(bwd_launch, rec, vals, ranges, cams, plan, bg, T_final, last, dL_dimage, drec, st)
+    dg_plan pb = plan;   // the backward's own variant, if set
+    if (plan.raster_warps_bwd != 0) {
+        pb.raster_warps = plan.raster_warps_bwd;
+        pb.raster_stage = plan.raster_stage_bwd;
+    }
+    DG_RASTER_DISPATCH(pb, bwd_launch, rec, vals, ranges, cams, pb, bg, T_final, last, dL_dimage, drec, st)
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;

@@ -117,13 +117,18 @@ def camera_array(cams: Sequence[S.Camera]):
     return arr
 
 
-# compositing variant (warps per tile, instances staged per thread) applied to
-# new plans; the autotuner sets it from measurements
-RASTER_VARIANT = [4, 2]
+# compositing variant (warps per tile, instances staged per thread) of the
+# forward and of the backward (0, 0 = the forward's) applied to new plans;
+# the autotuner sets it from measurements
+RASTER_VARIANT = [4, 2, 0, 0]
 
 
-def set_raster_variant(warps: int, stage: int) -> None:
-    RASTER_VARIANT[0], RASTER_VARIANT[1] = int(warps), int(stage)
+def set_raster_variant(warps: int, stage: int, warps_bwd: int = 0, stage_bwd: int = 0) -> None:
+    RASTER_VARIANT[:] = [int(warps), int(stage), int(warps_bwd), int(stage_bwd)]
+
+
+def apply_variant(plan, variant) -> None:
+    plan.raster_warps, plan.raster_stage, plan.raster_warps_bwd, plan.raster_stage_bwd = [int(v) for v in variant]
 
 
 def plan_views(cams: Sequence[S.Camera], blk_off: Sequence[int], tile_w=16, tile_h=16):
@@ -132,7 +137,7 @@ def plan_views(cams: Sequence[S.Camera], blk_off: Sequence[int], tile_w=16, tile
     plan = L.DgPlan()
     L.check(L.lib().dg_plan_views(arr, len(cams), off, len(blk_off) - 1, tile_w, tile_h, C.byref(plan)),
             "dg_plan_views")
-    plan.raster_warps, plan.raster_stage = RASTER_VARIANT
+    apply_variant(plan, RASTER_VARIANT)
     return arr, plan
 
 
@@ -140,7 +145,7 @@ def render_plan(cams: Sequence[S.Camera], n_gauss: int, tile_w=16, tile_h=16):
     arr = camera_array(cams)
     plan = L.DgPlan()
     L.check(L.lib().dg_render_plan(arr, len(cams), int(n_gauss), tile_w, tile_h, C.byref(plan)), "dg_render_plan")
-    plan.raster_warps, plan.raster_stage = RASTER_VARIANT
+    apply_variant(plan, RASTER_VARIANT)
     return arr, plan
 
 

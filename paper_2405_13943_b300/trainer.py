@@ -88,8 +88,8 @@ class DogsTrainer:
         self.graphs.clear()
         self.calibrate_capacity()
 
-    def set_variant(self, warps: int, stage: int) -> None:
-        self.vb.plan.raster_warps, self.vb.plan.raster_stage = int(warps), int(stage)
+    def set_variant(self, warps: int, stage: int, warps_bwd: int = 0, stage_bwd: int = 0) -> None:
+        D.apply_variant(self.vb.plan, (warps, stage, warps_bwd, stage_bwd))
         self.graphs.clear()
 
     # ---- capacity -------------------------------------------------------------

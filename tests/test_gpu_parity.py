@@ -367,6 +367,25 @@ def test_every_compositing_variant_matches_oracle(D, oracle, warps, stage):
         D.set_raster_variant(4, 2)
 
 
+@pytest.mark.parametrize("fwd,bwd", [((2, 1), (1, 1)), ((1, 2), (4, 1))])
+def test_separate_backward_variant(D, oracle, fwd, bwd):
+    """The backward runs its own variant (plan.raster_warps_bwd /
+    raster_stage_bwd) and still matches the oracle."""
+    O = oracle
+    cams = [S.cube_camera(90, 70, f=80.0), S.cube_camera(64, 64, f=60.0)]
+    g = curate_gaussians(O, S.cube_scene(3000, 93, sh_degree=1, log_scale_mu=-2.4), cams, 16, 16)
+    D.set_raster_variant(*fwd, *bwd)
+    try:
+        xbuf, vb, grads, f, ob, masks, plan = run_pair(D, O, g, cams, [(0, g.n), (0, g.n)], [0, g.n], 16, 16,
+                                                       (0.05, 0.1, 0.15))
+        p = vb.plan
+        assert (p.raster_warps, p.raster_stage, p.raster_warps_bwd, p.raster_stage_bwd) == (*fwd, *bwd)
+        check_forward(D, O, vb, f, masks, plan)
+        check_backward(D, O, g, grads, ob, 1)
+    finally:
+        D.set_raster_variant(4, 2)
+
+
 def test_consensus_with_many_copies_per_global(D, oracle):
     """Globals held by 1 to 7 blocks: the batched fast path (up to four
     copies) and the generic path (more) against the oracle."""
