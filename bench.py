@@ -205,6 +205,9 @@ def algorithmic_bytes(tr, vb_rect_visible: int, n_visible_copies: int):
     return {
         # x, g, m, v read + x, m, v written per float; anchor read per shared float
         "adam_admm_step": n_c * P * 28 + n_sc * P * 4,
+        # fused projection adjoint + x-step: x, m, v read and written per float, anchor per shared
+        # float, and per visible record its 2D gradients (48 B) and rectangle (8 B)
+        "xstep": n_c * P * 24 + n_sc * P * 4 + n_visible_copies * 56,
         # shared: x, u read + u, anchor written per copy float; z_prev read + z written per global float;
         # unshared: x read + z written
         "admm_consensus": P * (16 * sc + 8 * sg + 8 * ug),
@@ -280,7 +283,9 @@ def run_ours(args, dist, rank, world):
     ms = max_over_ranks(dist, ms)
 
     # ---- per-call durations (eager launches, events on the launching stream) ----------
-    names = ["project", "bin_sort", "rasterize_fwd", "loss", "rasterize_bwd", "adam_admm_step", "admm_consensus"]
+    fused = tr.fused and D.one_view_per_block(tr.vb.plan)
+    names = ["project", "bin_sort", "rasterize_fwd", "loss", "rasterize_bwd",
+             "xstep" if fused else "adam_admm_step", "admm_consensus"]
     acc = {n: 0.0 for n in names}
     vb = tr.vb
     n_eager = max(3, min(args.steps, 20))
@@ -297,9 +302,14 @@ def run_ours(args, dist, rank, world):
         D.dg_bin_sort(vb); ev[2].record()
         D.dg_rasterize_fwd(vb, tr.bg); ev[3].record()
         tr._loss(tr.targets[p]); ev[4].record()
-        D.dg_rasterize_bwd(vb, tr.x, tr.grad, bg=tr.bg); ev[5].record()
-        D.dg_adam_admm_step(tr.x, tr.grad, tr.m, tr.v, tr.anchor, tr.shared, tr.rho, tr.lr, step=1,
-                            dev_step=tr.dev_step); ev[6].record()
+        if fused:   # compositing adjoint, then projection adjoint + x-step fused
+            D.dg_rasterize_bwd_records(vb, bg=tr.bg); ev[5].record()
+            D.dg_xstep_from_records(vb, tr.x, tr.m, tr.v, tr.anchor, tr.shared, tr.rho, tr.lr, step=1,
+                                    dev_step=tr.dev_step); ev[6].record()
+        else:
+            D.dg_rasterize_bwd(vb, tr.x, tr.grad, bg=tr.bg); ev[5].record()
+            D.dg_adam_admm_step(tr.x, tr.grad, tr.m, tr.v, tr.anchor, tr.shared, tr.rho, tr.lr, step=1,
+                                dev_step=tr.dev_step); ev[6].record()
         D.dg_admm_consensus(tr.x, tr.u, tr.z, tr.anchor, tr.g_off, tr.g_copies, tr.rho, tr.alpha, tr.residuals)
         ev[7].record()
         torch.cuda.synchronize()
@@ -455,9 +465,7 @@ def run_e2e(tr, args, dist):
             D.dg_bin_sort(vb)
             D.dg_rasterize_fwd(vb, tr.bg)
             tr._loss(stage)
-            D.dg_rasterize_bwd(vb, tr.x, tr.grad, bg=tr.bg)
-            D.dg_adam_admm_step(tr.x, tr.grad, tr.m, tr.v, tr.anchor, tr.shared, tr.rho, tr.lr, step=1,
-                                dev_step=tr.dev_step)
+            tr.backward_step()
             D.dg_admm_consensus(tr.x, tr.u, tr.z, tr.anchor, tr.g_off, tr.g_copies, tr.rho, tr.alpha,
                                 tr.residuals)
             host_loss.copy_(vb.loss, non_blocking=True)

@@ -231,6 +231,29 @@ int dg_rasterize_bwd(const float* rec, const uint32_t* rect, const uint32_t* val
                      const float* dL_dimage, const dg_gaussians* x, float* drec,
                      dg_gaussians* grads, void* stream);
 
+/* The compositing adjoint alone (the first half of dg_rasterize_bwd): drec
+ * (12 floats per record) zeroed, then dL/d(mean2d, conic, opacity, colour)
+ * accumulated.  Feeds dg_xstep_from_records. */
+int dg_rasterize_bwd_records(const float* rec, const uint32_t* vals, const uint32_t* ranges,
+                             const dg_camera* dev_cams, const dg_plan* plan, const float* bg,
+                             const float* T_final, const uint32_t* last, const float* dL_dimage,
+                             float* drec, void* stream);
+
+/* The projection adjoint (K8) and the x-step (K9, Eq. 8a / 12a) in one pass,
+ * for batches whose blocks have at most one view each: every copy then has
+ * at most one record, so each thread finishes its copy's dL/dx from drec
+ * and takes the Adam + penalty step on it at once; the gradient never goes
+ * to memory.  Same result as dg_rasterize_bwd's second half followed by
+ * dg_adam_admm_step (x, m, v updated in place; the parameters before the
+ * step are the ones differentiated).  rect: the forward's rectangles.
+ * DG_ERR_INVALID if a block of the plan has more than one view (use those
+ * two calls then). */
+int dg_xstep_from_records(const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                          const float* drec, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v,
+                          const dg_gaussians* anchor, const uint8_t* copy_shared, const float* rho,
+                          const float* lr, float beta1, float beta2, float eps, int step,
+                          const int32_t* dev_step, void* stream);
+
 /* ---- ADMM (K9, K10) -------------------------------------------------------- */
 /* x-step (Eq. 8a / 12a): one Adam step on every local copy with gradient
  * g + rho_grp (x - anchor) on shared copies (copy_shared[c] != 0), where the

@@ -86,6 +86,12 @@ _SIGS = {
     "dg_admm_scale_duals": (C.c_int, [C.POINTER(DgGaussians), _vp, C.POINTER(C.c_float), _vp]),
     "dg_rasterize_count": (C.c_int, [_vp, _vp, _vp, _vp, C.POINTER(DgPlan), C.POINTER(C.c_float), _vp, _vp, _vp,
                                      _vp, _vp]),
+    "dg_rasterize_bwd_records": (C.c_int, [_vp, _vp, _vp, _vp, C.POINTER(DgPlan), C.POINTER(C.c_float), _vp, _vp,
+                                            _vp, _vp, _vp]),
+    "dg_xstep_from_records": (C.c_int, [_vp, _vp, C.POINTER(DgPlan), _vp, C.POINTER(DgGaussians),
+                                         C.POINTER(DgGaussians), C.POINTER(DgGaussians), C.POINTER(DgGaussians), _vp,
+                                         C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float,
+                                         C.c_int, _vp, _vp]),
     "dg_scene_split": (C.c_int, [_vp, C.c_int64, C.c_int, _vp, _vp]),
     "dg_scene_assign": (C.c_int, [_vp, C.c_int64, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp]),
     "dg_render_plan": (C.c_int, [C.POINTER(DgCamera), C.c_int, C.c_int64, C.c_int, C.c_int, C.POINTER(DgPlan)]),

@@ -62,7 +62,7 @@ def _kernel_times(tr, steps: int) -> Tuple[float, float]:
         ev[1].record()
         tr._loss(tr.targets[p])
         ev[2].record()
-        D.dg_rasterize_bwd(vb, tr.x, tr.grad, bg=tr.bg)
+        D.dg_rasterize_bwd_records(vb, bg=tr.bg)
         ev[3].record()
         torch.cuda.synchronize()
         if i > 0:

@@ -12,13 +12,6 @@
 
 namespace dg {
 
-struct AdamArgs {
-    float rho[5];
-    float lr[6];
-    float b1, b2, eps;
-    int step;
-};
-
 // The x-step runs as two launches with contiguous warp accesses and no
 // per-element index division: the float4 fields (four copies per thread,
 // copies strided by the CTA width) and the SH planes (a 2D grid of quads of
@@ -40,22 +33,11 @@ __device__ __forceinline__ void adam_unit(float4* __restrict__ x, const float4* 
             if (sh[i]) gs[i] += rho[i] * (xs[i] - as[i]);
     }
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        if (!act[i]) continue;
-        ms[i] = b1 * ms[i] + (1.f - b1) * gs[i];
-        vs[i] = b2 * vs[i] + (1.f - b2) * gs[i] * gs[i];
-        xs[i] -= lr[i] * __fdividef(ms[i] * ic1, sqrtf(vs[i] * ic2) + eps);
-    }
+    for (int i = 0; i < 4; i++)
+        if (act[i]) adam_scalar(xs[i], gs[i], ms[i], vs[i], lr[i], b1, b2, eps, ic1, ic2);
     x[u] = make_float4(xs[0], xs[1], xs[2], xs[3]);
     m[u] = make_float4(ms[0], ms[1], ms[2], ms[3]);
     v[u] = make_float4(vs[0], vs[1], vs[2], vs[3]);
-}
-
-__device__ __forceinline__ void bias_corr(const AdamArgs& a, const int32_t* dev_step, float& ic1, float& ic2)
-{
-    float t = (float)(dev_step ? *dev_step : a.step);
-    ic1 = 1.f / (1.f - powf(a.b1, t));
-    ic2 = 1.f / (1.f - powf(a.b2, t));
 }
 
 constexpr int kAdamThreads = 256, kAdamPer = 4;

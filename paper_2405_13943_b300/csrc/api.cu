@@ -34,6 +34,8 @@ int launch_consensus(const dg_gaussians*, dg_gaussians*, dg_gaussians*, dg_gauss
 int launch_anchor(const dg_gaussians*, const dg_gaussians*, const int32_t*, const uint8_t*, dg_gaussians*,
                   cudaStream_t);
 int launch_scale_duals(dg_gaussians*, const uint8_t*, const float*, cudaStream_t);
+int launch_xstep(dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*, const uint8_t*, const dg_camera*,
+                 const dg_plan&, const uint2*, const float4*, const AdamArgs&, const int32_t*, cudaStream_t);
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -269,6 +271,43 @@ int dg_adam_admm_step(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m, d
     if (x->n > 0 && anchor && !copy_shared) return DG_ERR_INVALID;
     return launch_adam_admm(x, g, m, v, anchor, anchor ? copy_shared : nullptr, rho, lr, beta1, beta2, eps, step,
                             dev_step, (cudaStream_t)stream);
+}
+
+int dg_rasterize_bwd_records(const float* rec, const uint32_t* vals, const uint32_t* ranges,
+                             const dg_camera* dev_cams, const dg_plan* plan, const float* bg, const float* T_final,
+                             const uint32_t* last, const float* dL_dimage, float* drec, void* stream)
+{
+    if (!valid_plan(plan) || !bg) return DG_ERR_INVALID;
+    if (plan->n_rec == 0) return DG_OK;
+    if (!rec || !vals || !ranges || !dev_cams || !T_final || !last || !dL_dimage || !drec) return DG_ERR_INVALID;
+    if (!aligned16(rec) || !aligned8(dev_cams) || !aligned16(drec)) return DG_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(drec, 0, (size_t)plan->n_rec * 12 * sizeof(float), st) != cudaSuccess) return DG_ERR_CUDA;
+    return launch_raster_bwd((const float4*)rec, vals, ranges, dev_cams, *plan, bg, T_final, last, dL_dimage, drec,
+                             st);
+}
+
+int dg_xstep_from_records(const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan, const float* drec,
+                          dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
+                          const uint8_t* copy_shared, const float* rho, const float* lr, float beta1, float beta2,
+                          float eps, int step, const int32_t* dev_step, void* stream)
+{
+    if (!valid_plan(plan) || !valid_gauss(x) || !valid_gauss(m) || !valid_gauss(v)) return DG_ERR_INVALID;
+    if (!same_layout(x, m) || !same_layout(x, v)) return DG_ERR_INVALID;
+    if (anchor && (!valid_gauss(anchor) || !same_layout(x, anchor))) return DG_ERR_INVALID;
+    if (!rho || !lr || (!dev_step && step < 1) || ((uintptr_t)dev_step & 3u)) return DG_ERR_INVALID;
+    if (x->n > 0 && anchor && !copy_shared) return DG_ERR_INVALID;
+    if (plan->blk_off[plan->n_blocks] > x->n) return DG_ERR_INVALID;
+    for (int k = 0; k < plan->n_blocks; k++)
+        if (plan->blk_view_off[k + 1] - plan->blk_view_off[k] > 1) return DG_ERR_INVALID;   // one view per block
+    if (plan->n_rec > 0 && (!rect || !dev_cams || !drec)) return DG_ERR_INVALID;
+    if (!aligned8(rect) || !aligned8(dev_cams) || !aligned16(drec)) return DG_ERR_INVALID;
+    AdamArgs a;
+    for (int i = 0; i < 5; i++) a.rho[i] = rho[i];
+    for (int i = 0; i < 6; i++) a.lr[i] = lr[i];
+    a.b1 = beta1; a.b2 = beta2; a.eps = eps; a.step = step;
+    return launch_xstep(x, m, v, anchor, anchor ? copy_shared : nullptr, dev_cams, *plan, (const uint2*)rect,
+                        (const float4*)drec, a, dev_step, (cudaStream_t)stream);
 }
 
 int dg_admm_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z, dg_gaussians* anchor,

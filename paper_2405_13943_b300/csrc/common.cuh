@@ -112,6 +112,30 @@ __device__ __forceinline__ float pair_alpha(float mx, float my, float A, float B
     return a;
 }
 
+// ---- Adam with the ADMM penalty (Eq. 8a / 12a), shared by the x-step kernels ----
+struct AdamArgs {
+    float rho[5];   // groups p, q, s, f, o
+    float lr[6];    // p, q, s, f_dc, f_rest, o
+    float b1, b2, eps;
+    int step;
+};
+
+__device__ __forceinline__ void bias_corr(const AdamArgs& a, const int32_t* dev_step, float& ic1, float& ic2)
+{
+    float t = (float)(dev_step ? *dev_step : a.step);
+    ic1 = 1.f / (1.f - powf(a.b1, t));
+    ic2 = 1.f / (1.f - powf(a.b2, t));
+}
+
+// one Adam step of one parameter; g already holds the penalty term
+__device__ __forceinline__ void adam_scalar(float& x, float g, float& m, float& v, float lr, float b1, float b2,
+                                            float eps, float ic1, float ic2)
+{
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    x -= lr * __fdividef(m * ic1, sqrtf(v * ic2) + eps);
+}
+
 }  // namespace dg
 
 #define DG_CHECK_LAUNCH()                                      \

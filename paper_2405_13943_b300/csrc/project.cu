@@ -247,6 +247,129 @@ __global__ void __launch_bounds__(256, 4) k_project(GView x, const dg_camera* __
 // ---------------------------------------------------------------------------
 // K8: adjoint of the projection, accumulated over the views of the block.
 // ---------------------------------------------------------------------------
+// Adjoint of one record (copy c seen by one view), in two parts.
+// colour_adjoint: from the record's colour gradient (d1.z, d1.w, d2.x) and
+// opacity gradient (d1.y), adds dL/d(opacity logit) to go and the view
+// direction's share of dL/d(mean) to gmu, and returns the colour gradient gc
+// (zero on clamped channels) and the SH basis Y of the view direction, so
+// that dL/d f_{k,ch} = gc[ch] Y[k].  f: the copy's SH coefficients (3 NK,
+// coefficient-major).
+template <int DEG>
+__device__ __forceinline__ void colour_adjoint(const CamL& cam, float3 mu, float opac, const float* f, float4 d1,
+                                               float4 d2, float* gmu, float& go, float* gc, float* Y)
+{
+    constexpr int NK = (DEG + 1) * (DEG + 1);
+    // opacity logit
+    go += d1.y * opac * (1.f - opac);
+    // colour -> SH coefficients and the view direction
+    float vx = mu.x - cam.cp[0], vy = mu.y - cam.cp[1], vz = mu.z - cam.cp[2];
+    float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+    float ux = vx * il, uy = vy * il, uz = vz * il;
+    sh_eval<DEG>(ux, uy, uz, Y);
+    gc[0] = d1.z; gc[1] = d1.w; gc[2] = d2.x;
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        float s = 0.5f;
+#pragma unroll
+        for (int kk = 0; kk < NK; kk++) s = fmaf(f[3 * kk + ch], Y[kk], s);
+        if (!(s > 0.f)) gc[ch] = 0.f;            // clamped channel
+    }
+    if (DEG > 0) {
+        float wk[NK];
+#pragma unroll
+        for (int kk = 0; kk < NK; kk++) wk[kk] = gc[0] * f[3 * kk] + gc[1] * f[3 * kk + 1] + gc[2] * f[3 * kk + 2];
+        float3 gd = sh_grad_dot<DEG>(ux, uy, uz, wk);
+        float dd = gd.x * ux + gd.y * uy + gd.z * uz;
+        gmu[0] += (gd.x - ux * dd) * il;
+        gmu[1] += (gd.y - uy * dd) * il;
+        gmu[2] += (gd.z - uz * dd) * il;
+    }
+}
+
+// geometry_adjoint: from the record's mean2d and conic gradients (d0), adds
+// dL/d(mean, rotation, log-scale) of the EWA projection to gmu, gq, gs.
+template <int DEG>
+__device__ __forceinline__ void geometry_adjoint(const CamL& cam, float3 mu, float4 q, float4 sc, float4 d0,
+                                                 float4 d1, int tile_w, int tile_h, float* gmu, float* gq,
+                                                 float* gs)
+{
+    Geom g;
+    geom(cam, cam_depth(cam, mu), mu, q, sc, tile_w, tile_h, g, nullptr);  // forward's rect decides
+    // conic (a, b, c) -> Sigma' entries (A, B, C)
+    float da = d0.z, db = d0.w, dc = d1.x;
+    float id2 = 1.f / (g.det * g.det);
+    float gA = (-g.C * g.C * da + g.B * g.C * db - g.B * g.B * dc) * id2;
+    float gB = (2.f * g.B * g.C * da - (g.A * g.C + g.B * g.B) * db + 2.f * g.A * g.B * dc) * id2;
+    float gC = (-g.B * g.B * da + g.A * g.B * db - g.A * g.A * dc) * id2;
+    // Sigma' = T Sigma T^T: dSigma = T^T G T, dT = 2 G T Sigma, G = [[gA, gB/2], [gB/2, gC]]
+    float U0[3], U1[3];
+    U0[0] = g.Sig[0] * g.T0[0] + g.Sig[1] * g.T0[1] + g.Sig[2] * g.T0[2];
+    U0[1] = g.Sig[1] * g.T0[0] + g.Sig[3] * g.T0[1] + g.Sig[4] * g.T0[2];
+    U0[2] = g.Sig[2] * g.T0[0] + g.Sig[4] * g.T0[1] + g.Sig[5] * g.T0[2];
+    U1[0] = g.Sig[0] * g.T1[0] + g.Sig[1] * g.T1[1] + g.Sig[2] * g.T1[2];
+    U1[1] = g.Sig[1] * g.T1[0] + g.Sig[3] * g.T1[1] + g.Sig[4] * g.T1[2];
+    U1[2] = g.Sig[2] * g.T1[0] + g.Sig[4] * g.T1[1] + g.Sig[5] * g.T1[2];
+    float dT0[3], dT1[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        dT0[j] = 2.f * gA * U0[j] + gB * U1[j];
+        dT1[j] = gB * U0[j] + 2.f * gC * U1[j];
+    }
+    float hB = 0.5f * gB;
+    float dS[6];   // dL/dSigma as a symmetric matrix: 00 01 02 11 12 22
+    dS[0] = gA * g.T0[0] * g.T0[0] + 2.f * hB * g.T0[0] * g.T1[0] + gC * g.T1[0] * g.T1[0];
+    dS[1] = gA * g.T0[0] * g.T0[1] + hB * (g.T0[0] * g.T1[1] + g.T1[0] * g.T0[1]) + gC * g.T1[0] * g.T1[1];
+    dS[2] = gA * g.T0[0] * g.T0[2] + hB * (g.T0[0] * g.T1[2] + g.T1[0] * g.T0[2]) + gC * g.T1[0] * g.T1[2];
+    dS[3] = gA * g.T0[1] * g.T0[1] + 2.f * hB * g.T0[1] * g.T1[1] + gC * g.T1[1] * g.T1[1];
+    dS[4] = gA * g.T0[1] * g.T0[2] + hB * (g.T0[1] * g.T1[2] + g.T1[1] * g.T0[2]) + gC * g.T1[1] * g.T1[2];
+    dS[5] = gA * g.T0[2] * g.T0[2] + 2.f * hB * g.T0[2] * g.T1[2] + gC * g.T1[2] * g.T1[2];
+    // rows of T depend on t through fx/tz and x/z; the mean through the pinhole
+    const float* W = cam.R;
+    float iz = 1.f / g.tz, iz2 = iz * iz, iz3 = iz2 * iz;
+    float dT0W0 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
+    float dT0W2 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
+    float dT1W1 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
+    float dT1W2 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
+    float dtx = -cam.fx * iz2 * dT0W2 + d0.x * cam.fx * iz;
+    float dty = -cam.fy * iz2 * dT1W2 + d0.y * cam.fy * iz;
+    float dtz = -cam.fx * iz2 * dT0W0 + 2.f * cam.fx * g.tx * iz3 * dT0W2
+              - cam.fy * iz2 * dT1W1 + 2.f * cam.fy * g.ty * iz3 * dT1W2
+              - d0.x * cam.fx * g.tx * iz2 - d0.y * cam.fy * g.ty * iz2;
+    gmu[0] += W[0] * dtx + W[3] * dty + W[6] * dtz;
+    gmu[1] += W[1] * dtx + W[4] * dty + W[7] * dtz;
+    gmu[2] += W[2] * dtx + W[5] * dty + W[8] * dtz;
+    // Sigma = M M^T, M = R diag(s): dM = 2 dSigma M
+    float Sf[9] = {dS[0], dS[1], dS[2], dS[1], dS[3], dS[4], dS[2], dS[4], dS[5]};
+    float M[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) M[3 * i + j] = g.Rq[3 * i + j] * g.s[j];
+    float dR[9];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        float ds = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            float dM = 2.f * (Sf[3 * i + 0] * M[0 + j] + Sf[3 * i + 1] * M[3 + j] + Sf[3 * i + 2] * M[6 + j]);
+            ds += dM * g.Rq[3 * i + j];
+            dR[3 * i + j] = dM * g.s[j];
+        }
+        gs[j] += ds * g.s[j];
+    }
+    // rotation partials w.r.t. the normalised quaternion, then the normalisation
+    float qw = g.qn[0], qx = g.qn[1], qy = g.qn[2], qz = g.qn[3];
+    float dqw = 2.f * (qz * (dR[3] - dR[1]) + qy * (dR[2] - dR[6]) + qx * (dR[7] - dR[5]));
+    float dqx = 2.f * (qy * (dR[1] + dR[3]) + qz * (dR[2] + dR[6]) + qw * (dR[7] - dR[5])) - 4.f * qx * (dR[4] + dR[8]);
+    float dqy = 2.f * (qx * (dR[1] + dR[3]) + qz * (dR[5] + dR[7]) + qw * (dR[2] - dR[6])) - 4.f * qy * (dR[0] + dR[8]);
+    float dqz = 2.f * (qx * (dR[2] + dR[6]) + qy * (dR[5] + dR[7]) + qw * (dR[3] - dR[1])) - 4.f * qz * (dR[0] + dR[4]);
+    float qd = dqw * qw + dqx * qx + dqy * qy + dqz * qz;
+    gq[0] += (dqw - qw * qd) * g.qinv;
+    gq[1] += (dqx - qx * qd) * g.qinv;
+    gq[2] += (dqy - qy * qd) * g.qinv;
+    gq[3] += (dqz - qz * qd) * g.qinv;
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(128, 4) k_project_bwd(GView x, const dg_camera* __restrict__ cams, dg_plan plan,
                                                         const uint2* __restrict__ rect,
@@ -278,119 +401,22 @@ __global__ void __launch_bounds__(128, 4) k_project_bwd(GView x, const dg_camera
             loaded = true;
         }
         const float4 d0 = drec[3 * r + 0], d1 = drec[3 * r + 1], d2 = drec[3 * r + 2];
-        Geom g;
-        geom(cam, cam_depth(cam, mu), mu, q, sc, plan.tile_w, plan.tile_h, g, nullptr);  // forward's rect decides
-        // opacity logit
-        go += d1.y * opac * (1.f - opac);
-        // colour -> SH coefficients and the view direction (coefficients streamed)
-        float vx = mu.x - cam.cp[0], vy = mu.y - cam.cp[1], vz = mu.z - cam.cp[2];
-        float il = rsqrtf(vx * vx + vy * vy + vz * vz);
-        float ux = vx * il, uy = vy * il, uz = vz * il;
-        float Y[NK];
-        sh_eval<DEG>(ux, uy, uz, Y);
-        float f[3 * NK];
+        {
+            float f[3 * NK], gc[3], Y[NK];
 #pragma unroll
-        for (int j = 0; j < 3 * NK; j++) f[j] = __ldg(shp + (int64_t)j * x.ld);
-        float gc[3] = {d1.z, d1.w, d2.x};
+            for (int j = 0; j < 3 * NK; j++) f[j] = __ldg(shp + (int64_t)j * x.ld);
+            colour_adjoint<DEG>(cam, mu, opac, f, d1, d2, gmu, go, gc, Y);
 #pragma unroll
-        for (int ch = 0; ch < 3; ch++) {
-            float s = 0.5f;
+            for (int kk = 0; kk < NK; kk++)
 #pragma unroll
-            for (int kk = 0; kk < NK; kk++) s = fmaf(f[3 * kk + ch], Y[kk], s);
-            if (!(s > 0.f)) gc[ch] = 0.f;            // clamped channel
+                for (int ch = 0; ch < 3; ch++) {
+                    const int64_t o = (int64_t)(3 * kk + ch) * gr.ld;
+                    const float val = gc[ch] * Y[kk];
+                    gsh[o] = sh_written ? gsh[o] + val : val;
+                }
+            sh_written = true;
         }
-        float wk[NK];
-#pragma unroll
-        for (int kk = 0; kk < NK; kk++) {
-#pragma unroll
-            for (int ch = 0; ch < 3; ch++) {
-                const int64_t o = (int64_t)(3 * kk + ch) * gr.ld;
-                const float val = gc[ch] * Y[kk];
-                gsh[o] = sh_written ? gsh[o] + val : val;
-            }
-            wk[kk] = gc[0] * f[3 * kk] + gc[1] * f[3 * kk + 1] + gc[2] * f[3 * kk + 2];
-        }
-        sh_written = true;
-        if (DEG > 0) {
-            float3 gd = sh_grad_dot<DEG>(ux, uy, uz, wk);
-            float dd = gd.x * ux + gd.y * uy + gd.z * uz;
-            gmu[0] += (gd.x - ux * dd) * il;
-            gmu[1] += (gd.y - uy * dd) * il;
-            gmu[2] += (gd.z - uz * dd) * il;
-        }
-        // conic (a, b, c) -> Sigma' entries (A, B, C)
-        float da = d0.z, db = d0.w, dc = d1.x;
-        float id2 = 1.f / (g.det * g.det);
-        float gA = (-g.C * g.C * da + g.B * g.C * db - g.B * g.B * dc) * id2;
-        float gB = (2.f * g.B * g.C * da - (g.A * g.C + g.B * g.B) * db + 2.f * g.A * g.B * dc) * id2;
-        float gC = (-g.B * g.B * da + g.A * g.B * db - g.A * g.A * dc) * id2;
-        // Sigma' = T Sigma T^T: dSigma = T^T G T, dT = 2 G T Sigma, G = [[gA, gB/2], [gB/2, gC]]
-        float U0[3], U1[3];
-        U0[0] = g.Sig[0] * g.T0[0] + g.Sig[1] * g.T0[1] + g.Sig[2] * g.T0[2];
-        U0[1] = g.Sig[1] * g.T0[0] + g.Sig[3] * g.T0[1] + g.Sig[4] * g.T0[2];
-        U0[2] = g.Sig[2] * g.T0[0] + g.Sig[4] * g.T0[1] + g.Sig[5] * g.T0[2];
-        U1[0] = g.Sig[0] * g.T1[0] + g.Sig[1] * g.T1[1] + g.Sig[2] * g.T1[2];
-        U1[1] = g.Sig[1] * g.T1[0] + g.Sig[3] * g.T1[1] + g.Sig[4] * g.T1[2];
-        U1[2] = g.Sig[2] * g.T1[0] + g.Sig[4] * g.T1[1] + g.Sig[5] * g.T1[2];
-        float dT0[3], dT1[3];
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            dT0[j] = 2.f * gA * U0[j] + gB * U1[j];
-            dT1[j] = gB * U0[j] + 2.f * gC * U1[j];
-        }
-        float hB = 0.5f * gB;
-        float dS[6];   // dL/dSigma as a symmetric matrix: 00 01 02 11 12 22
-        dS[0] = gA * g.T0[0] * g.T0[0] + 2.f * hB * g.T0[0] * g.T1[0] + gC * g.T1[0] * g.T1[0];
-        dS[1] = gA * g.T0[0] * g.T0[1] + hB * (g.T0[0] * g.T1[1] + g.T1[0] * g.T0[1]) + gC * g.T1[0] * g.T1[1];
-        dS[2] = gA * g.T0[0] * g.T0[2] + hB * (g.T0[0] * g.T1[2] + g.T1[0] * g.T0[2]) + gC * g.T1[0] * g.T1[2];
-        dS[3] = gA * g.T0[1] * g.T0[1] + 2.f * hB * g.T0[1] * g.T1[1] + gC * g.T1[1] * g.T1[1];
-        dS[4] = gA * g.T0[1] * g.T0[2] + hB * (g.T0[1] * g.T1[2] + g.T1[1] * g.T0[2]) + gC * g.T1[1] * g.T1[2];
-        dS[5] = gA * g.T0[2] * g.T0[2] + 2.f * hB * g.T0[2] * g.T1[2] + gC * g.T1[2] * g.T1[2];
-        // rows of T depend on t through fx/tz and x/z; the mean through the pinhole
-        const float* W = cam.R;
-        float iz = 1.f / g.tz, iz2 = iz * iz, iz3 = iz2 * iz;
-        float dT0W0 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
-        float dT0W2 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
-        float dT1W1 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
-        float dT1W2 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
-        float dtx = -cam.fx * iz2 * dT0W2 + d0.x * cam.fx * iz;
-        float dty = -cam.fy * iz2 * dT1W2 + d0.y * cam.fy * iz;
-        float dtz = -cam.fx * iz2 * dT0W0 + 2.f * cam.fx * g.tx * iz3 * dT0W2
-                  - cam.fy * iz2 * dT1W1 + 2.f * cam.fy * g.ty * iz3 * dT1W2
-                  - d0.x * cam.fx * g.tx * iz2 - d0.y * cam.fy * g.ty * iz2;
-        gmu[0] += W[0] * dtx + W[3] * dty + W[6] * dtz;
-        gmu[1] += W[1] * dtx + W[4] * dty + W[7] * dtz;
-        gmu[2] += W[2] * dtx + W[5] * dty + W[8] * dtz;
-        // Sigma = M M^T, M = R diag(s): dM = 2 dSigma M
-        float Sf[9] = {dS[0], dS[1], dS[2], dS[1], dS[3], dS[4], dS[2], dS[4], dS[5]};
-        float M[9];
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) M[3 * i + j] = g.Rq[3 * i + j] * g.s[j];
-        float dR[9];
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            float ds = 0.f;
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                float dM = 2.f * (Sf[3 * i + 0] * M[0 + j] + Sf[3 * i + 1] * M[3 + j] + Sf[3 * i + 2] * M[6 + j]);
-                ds += dM * g.Rq[3 * i + j];
-                dR[3 * i + j] = dM * g.s[j];
-            }
-            gs[j] += ds * g.s[j];
-        }
-        // rotation partials w.r.t. the normalised quaternion, then the normalisation
-        float qw = g.qn[0], qx = g.qn[1], qy = g.qn[2], qz = g.qn[3];
-        float dqw = 2.f * (qz * (dR[3] - dR[1]) + qy * (dR[2] - dR[6]) + qx * (dR[7] - dR[5]));
-        float dqx = 2.f * (qy * (dR[1] + dR[3]) + qz * (dR[2] + dR[6]) + qw * (dR[7] - dR[5])) - 4.f * qx * (dR[4] + dR[8]);
-        float dqy = 2.f * (qx * (dR[1] + dR[3]) + qz * (dR[5] + dR[7]) + qw * (dR[2] - dR[6])) - 4.f * qy * (dR[0] + dR[8]);
-        float dqz = 2.f * (qx * (dR[2] + dR[6]) + qy * (dR[5] + dR[7]) + qw * (dR[3] - dR[1])) - 4.f * qz * (dR[0] + dR[4]);
-        float qd = dqw * qw + dqx * qx + dqy * qy + dqz * qz;
-        gq[0] += (dqw - qw * qd) * g.qinv;
-        gq[1] += (dqx - qx * qd) * g.qinv;
-        gq[2] += (dqy - qy * qd) * g.qinv;
-        gq[3] += (dqz - qz * qd) * g.qinv;
+        geometry_adjoint<DEG>(cam, mu, q, sc, d0, d1, plan.tile_w, plan.tile_h, gmu, gq, gs);
     }
     gr.mo[c] = make_float4(gmu[0], gmu[1], gmu[2], go);
     gr.quat[c] = make_float4(gq[0], gq[1], gq[2], gq[3]);
@@ -399,6 +425,171 @@ __global__ void __launch_bounds__(128, 4) k_project_bwd(GView x, const dg_camera
 #pragma unroll
         for (int j = 0; j < 3 * NK; j++) gsh[(int64_t)j * gr.ld] = 0.f;
     }
+}
+
+// ---- K8 + K9 fused: the projection adjoint feeding the x-step ------------------------
+// For batches where every block has at most one view, each copy has at most
+// one record, so its gradient is complete once that record's adjoint is
+// done: the x-step (Adam + penalty, Eq. 8a / 12a) follows in the same CTA and
+// the gradient never goes to memory.  A thread differentiates its copy, steps
+// the copy's float4 fields, and leaves the colour gradient gc and SH basis Y
+// in shared memory (dL/d f_{k,ch} = gc[ch] Y[k]); the CTA then steps its
+// copies' SH planes with float4 accesses, four consecutive copies per thread
+// (the same arithmetic as the separate kernels).
+constexpr int kXsThreads = 128;
+
+template <int DEG>
+__global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView v, GView an,
+                                                        const uint8_t* __restrict__ shared,
+                                                        const dg_camera* __restrict__ cams, dg_plan plan,
+                                                        const uint2* __restrict__ rect,
+                                                        const float4* __restrict__ drec, AdamArgs a,
+                                                        const int32_t* __restrict__ dev_step)
+{
+    constexpr int NK = (DEG + 1) * (DEG + 1);
+    __shared__ float s_gc[3][kXsThreads];
+    __shared__ float s_Y[NK][kXsThreads];
+    const int tid = threadIdx.x;
+    const int64_t c0 = (int64_t)blockIdx.x * kXsThreads, c = c0 + tid;
+    float ic1, ic2;
+    bias_corr(a, dev_step, ic1, ic2);
+    float gc[3] = {0.f, 0.f, 0.f}, Y[NK];
+#pragma unroll
+    for (int kk = 0; kk < NK; kk++) Y[kk] = 0.f;
+    if (c < x.n) {
+        const bool s = shared != nullptr && shared[c] != 0;
+        const float4 mo = x.mo[c];
+        const float3 mu = make_float3(mo.x, mo.y, mo.z);
+        // the copy's record: its block's view, if the forward kept it
+        int64_t r = -1;
+        CamL cam;
+        if (c < plan.blk_off[plan.n_blocks]) {
+            const int k = find_block(plan, c);
+            const int v0 = plan.blk_view_off[k];
+            if (v0 < plan.blk_view_off[k + 1]) {
+                load_cam(cams, v0, cam);
+                const int64_t rr = cam.rec_off + (c - cam.gb);
+                const uint2 t = rect[rr];
+                if ((t.x & 0xFFFFu) != (t.y & 0xFFFFu)) r = rr;
+            }
+        }
+        float gmu[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gs[3] = {0, 0, 0}, go = 0.f;
+        const float4 q = x.quat[c], sc = x.scale[c];
+        if (r >= 0) {
+            {
+                float f[3 * NK];
+#pragma unroll
+                for (int j = 0; j < 3 * NK; j++) f[j] = x.sh[(int64_t)j * x.ld + c];
+                colour_adjoint<DEG>(cam, mu, 1.f / (1.f + __expf(-mo.w)), f, drec[3 * r + 1], drec[3 * r + 2], gmu,
+                                    go, gc, Y);
+            }
+            geometry_adjoint<DEG>(cam, mu, q, sc, drec[3 * r + 0], drec[3 * r + 1], plan.tile_w, plan.tile_h, gmu,
+                                  gq, gs);
+        }
+        // float4 fields: (mean, opacity logit), rotation, (log-scale, padding)
+        {
+            float xs[4] = {mo.x, mo.y, mo.z, mo.w}, gg[4] = {gmu[0], gmu[1], gmu[2], go};
+            const float4 mm = m.mo[c], vv = v.mo[c];
+            float ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
+            const float4 aa = s ? an.mo[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float as[4] = {aa.x, aa.y, aa.z, aa.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const float rho = i < 3 ? a.rho[0] : a.rho[4], lr = i < 3 ? a.lr[0] : a.lr[5];
+                if (s) gg[i] += rho * (xs[i] - as[i]);
+                adam_scalar(xs[i], gg[i], ms[i], vs[i], lr, a.b1, a.b2, a.eps, ic1, ic2);
+            }
+            x.mo[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+            m.mo[c] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+            v.mo[c] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        }
+        {
+            const float4 mm = m.quat[c], vv = v.quat[c];
+            float xs[4] = {q.x, q.y, q.z, q.w}, ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
+            const float4 aa = s ? an.quat[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float as[4] = {aa.x, aa.y, aa.z, aa.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                float g = gq[i];
+                if (s) g += a.rho[1] * (xs[i] - as[i]);
+                adam_scalar(xs[i], g, ms[i], vs[i], a.lr[1], a.b1, a.b2, a.eps, ic1, ic2);
+            }
+            x.quat[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+            m.quat[c] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+            v.quat[c] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        }
+        {
+            const float4 mm = m.scale[c], vv = v.scale[c];
+            float xs[4] = {sc.x, sc.y, sc.z, sc.w}, ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
+            const float4 aa = s ? an.scale[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float as[4] = {aa.x, aa.y, aa.z, aa.w};
+#pragma unroll
+            for (int i = 0; i < 3; i++) {   // lane 3 is padding
+                float g = gs[i];
+                if (s) g += a.rho[2] * (xs[i] - as[i]);
+                adam_scalar(xs[i], g, ms[i], vs[i], a.lr[2], a.b1, a.b2, a.eps, ic1, ic2);
+            }
+            x.scale[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+            m.scale[c] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+            v.scale[c] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        }
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) s_gc[ch][tid] = gc[ch];
+#pragma unroll
+    for (int kk = 0; kk < NK; kk++) s_Y[kk][tid] = Y[kk];
+    __syncthreads();
+    // SH planes: thread = (plane group tid / 32, quad tid % 32 of four copies)
+    const int quad = tid & 31;
+    const int64_t cq = c0 + 4 * quad;
+    if (cq >= x.ld) return;                       // the quad lies beyond the planes' stride
+    bool act[4], sh[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        act[i] = cq + i < x.n;
+        sh[i] = act[i] && shared != nullptr && shared[cq + i] != 0;
+    }
+    const bool any_sh = sh[0] || sh[1] || sh[2] || sh[3];
+    for (int j = tid >> 5; j < 3 * NK; j += kXsThreads / 32) {
+        const float lr = j < 3 ? a.lr[3] : a.lr[4];
+        const int64_t u = ((int64_t)j * x.ld + cq) >> 2;
+        float4* X = reinterpret_cast<float4*>(x.sh) + u;
+        float4* M = reinterpret_cast<float4*>(m.sh) + u;
+        float4* V = reinterpret_cast<float4*>(v.sh) + u;
+        const float4 xv = *X, mv = *M, vv = *V;
+        const float4 av = any_sh ? reinterpret_cast<const float4*>(an.sh)[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float xs[4] = {xv.x, xv.y, xv.z, xv.w}, ms[4] = {mv.x, mv.y, mv.z, mv.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
+        const float as[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            if (!act[i]) continue;
+            float g = s_gc[j % 3][4 * quad + i] * s_Y[j / 3][4 * quad + i];
+            if (sh[i]) g += a.rho[3] * (xs[i] - as[i]);
+            adam_scalar(xs[i], g, ms[i], vs[i], lr, a.b1, a.b2, a.eps, ic1, ic2);
+        }
+        *X = make_float4(xs[0], xs[1], xs[2], xs[3]);
+        *M = make_float4(ms[0], ms[1], ms[2], ms[3]);
+        *V = make_float4(vs[0], vs[1], vs[2], vs[3]);
+    }
+}
+
+int launch_xstep(dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
+                 const uint8_t* shared, const dg_camera* cams, const dg_plan& plan, const uint2* rect,
+                 const float4* drec, const AdamArgs& a, const int32_t* dev_step, cudaStream_t st)
+{
+    if (x->n == 0) return DG_OK;
+    GView xv = gview(x), mv = gview(m), vv = gview(v);
+    GView av = anchor ? gview(anchor) : xv;
+    dim3 grid((unsigned)((x->n + kXsThreads - 1) / kXsThreads));
+    switch (x->sh_degree) {
+    case 0: k_xstep<0><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a, dev_step); break;
+    case 1: k_xstep<1><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a, dev_step); break;
+    case 2: k_xstep<2><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a, dev_step); break;
+    default: k_xstep<3><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a, dev_step); break;
+    }
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
 }
 
 int launch_project(const dg_gaussians* x, const dg_camera* cams, const dg_plan& plan, float4* rec, uint2* rect,

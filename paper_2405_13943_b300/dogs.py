@@ -259,6 +259,37 @@ def dg_rasterize_bwd(vb: ViewBatch, x: GaussianBuffer, grads: GaussianBuffer, dL
                                      L.stream_handle(stream)), "dg_rasterize_bwd")
 
 
+def dg_rasterize_bwd_records(vb: ViewBatch, bg=(0.0, 0.0, 0.0), dL_dimage=None, stream=None) -> None:
+    g = vb.dL_dimage if dL_dimage is None else dL_dimage
+    L.check(L.lib().dg_rasterize_bwd_records(L.ptr(vb.rec), L.ptr(vb.vals), L.ptr(vb.ranges), L.ptr(vb.dev_cams),
+                                             C.byref(vb.plan), L.floats(bg), L.ptr(vb.T_final), L.ptr(vb.last),
+                                             L.ptr(g), L.ptr(vb.drec), L.stream_handle(stream)),
+            "dg_rasterize_bwd_records")
+
+
+def dg_xstep_from_records(vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer, v: GaussianBuffer,
+                          anchor: Optional[GaussianBuffer], shared: Optional[torch.Tensor], rho, lr, beta1=0.9,
+                          beta2=0.999, eps=1e-15, step=1, dev_step: Optional[torch.Tensor] = None,
+                          stream=None) -> None:
+    L.check(L.lib().dg_xstep_from_records(L.ptr(vb.rect), L.ptr(vb.dev_cams), C.byref(vb.plan), L.ptr(vb.drec),
+                                          x.ref, m.ref, v.ref, None if anchor is None else anchor.ref, L.ptr(shared),
+                                          L.floats(rho), L.floats(lr), beta1, beta2, eps, int(step),
+                                          L.ptr(dev_step), L.stream_handle(stream)), "dg_xstep_from_records")
+
+
+def dg_backward_xstep(vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer, v: GaussianBuffer,
+                      anchor: Optional[GaussianBuffer], shared: Optional[torch.Tensor], rho, lr, beta1=0.9,
+                      beta2=0.999, eps=1e-15, step=1, dev_step: Optional[torch.Tensor] = None, bg=(0.0, 0.0, 0.0),
+                      dL_dimage=None, stream=None) -> None:
+    """The compositing adjoint, then the fused projection adjoint + x-step."""
+    dg_rasterize_bwd_records(vb, bg, dL_dimage, stream)
+    dg_xstep_from_records(vb, x, m, v, anchor, shared, rho, lr, beta1, beta2, eps, step, dev_step, stream)
+
+
+def one_view_per_block(plan) -> bool:
+    return all(plan.blk_view_off[k + 1] - plan.blk_view_off[k] <= 1 for k in range(plan.n_blocks))
+
+
 def dg_adam_admm_step(x: GaussianBuffer, g: GaussianBuffer, m: GaussianBuffer, v: GaussianBuffer,
                       anchor: Optional[GaussianBuffer], shared: Optional[torch.Tensor], rho, lr,
                       beta1=0.9, beta2=0.999, eps=1e-15, step=1, dev_step: Optional[torch.Tensor] = None,

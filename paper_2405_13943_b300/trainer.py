@@ -43,8 +43,10 @@ class DogsTrainer:
     def __init__(self, split: S.BlockSplit, z0: D.GaussianBuffer, view_sets: Sequence[Sequence[S.Camera]],
                  targets: Sequence[torch.Tensor], rho=(1e-3,) * 5, lr=DEFAULT_LR, tile=(16, 16),
                  loss="dssim", w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0), alpha=1.0, intv=100,
-                 capacity: Optional[int] = None, device="cuda", adaptive: Optional[AdaptivePenalty] = None):
+                 capacity: Optional[int] = None, device="cuda", adaptive: Optional[AdaptivePenalty] = None,
+                 fused: bool = True):
         self.split, self.device = split, device
+        self.fused = fused
         self.adaptive = adaptive
         if adaptive is not None:
             adaptive.rho = [float(r) for r in rho]
@@ -126,12 +128,25 @@ class DogsTrainer:
         D.dg_bin_sort(vb)
         D.dg_rasterize_fwd(vb, self.bg)
         self._loss(self.targets[p] if target is None else target)
-        D.dg_rasterize_bwd(vb, self.x, self.grad, bg=self.bg)
-        D.dg_adam_admm_step(self.x, self.grad, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,
-                            step=1, dev_step=self.dev_step)
+        self.backward_step()
         if consensus:
             D.dg_admm_consensus(self.x, self.u, self.z, self.anchor, self.g_off, self.g_copies, self.rho,
                                 self.alpha, self.residuals)
+
+    def backward_step(self) -> None:
+        """Adjoint of the iteration's render and the x-step (Eq. 8a / 12a).
+        With at most one view per block the projection adjoint and the step
+        run fused (the gradient stays in registers); otherwise through the
+        gradient buffer."""
+        vb = self.vb
+        if self.fused and D.one_view_per_block(vb.plan):
+            D.dg_rasterize_bwd_records(vb, bg=self.bg)
+            D.dg_xstep_from_records(vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,
+                                    step=1, dev_step=self.dev_step)
+        else:
+            D.dg_rasterize_bwd(vb, self.x, self.grad, bg=self.bg)
+            D.dg_adam_admm_step(self.x, self.grad, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,
+                                step=1, dev_step=self.dev_step)
 
     def step(self, consensus: Optional[bool] = None, graph=True) -> None:
         """Iteration t (0-based) of Alg. 2: local steps, then the consensus
@@ -284,9 +299,14 @@ class SequentialTrainer:
                 D.dg_loss_dssim(vb, blk["targets"][p], self.w_l1, self.w_ssim)
             else:
                 D.dg_loss_l1(vb, blk["targets"][p], self.w_l1)
-            D.dg_rasterize_bwd(vb, blk["x"], blk["grad"], bg=self.bg)
-            D.dg_adam_admm_step(blk["x"], blk["grad"], blk["m"], blk["v"], blk["anchor"], blk["shared"], self.rho,
-                                self.lr, step=self.t + 1)
+            if D.one_view_per_block(vb.plan):      # the same fused adjoint + x-step as the batched form
+                D.dg_rasterize_bwd_records(vb, bg=self.bg)
+                D.dg_xstep_from_records(vb, blk["x"], blk["m"], blk["v"], blk["anchor"], blk["shared"], self.rho,
+                                        self.lr, step=self.t + 1)
+            else:
+                D.dg_rasterize_bwd(vb, blk["x"], blk["grad"], bg=self.bg)
+                D.dg_adam_admm_step(blk["x"], blk["grad"], blk["m"], blk["v"], blk["anchor"], blk["shared"],
+                                    self.rho, self.lr, step=self.t + 1)
         if c:
             for blk in self.blocks:
                 self._copy_rows(self.x_all, blk["x"], blk["b"], blk["e"], True)

@@ -440,3 +440,70 @@ def test_scale_duals_matches_oracle(D, oracle):
     for name in GROUPS:
         np.testing.assert_allclose(getattr(got, name), want[name], rtol=1e-6, atol=0, err_msg=name)
     assert torch.all(ub.pad_lane() == 0)
+
+
+def test_fused_backward_xstep_matches_oracle(D, oracle):
+    """dg_backward_xstep (adjoint and Adam + penalty step in one pass) equals
+    the oracle's backward followed by its x-step, on blocks with one view
+    each (one with none), shared and unshared copies, SH degree 3."""
+    O = oracle
+    g0 = S.cube_scene(700, 44, sh_degree=3, log_scale_mu=-2.6)
+    cams = [S.cube_camera(70, 45, f=60.0), S.cube_camera(128, 50, f=90.0)]
+    cams[0].block, cams[1].block = 0, 2
+    parts = [curate_gaussians(O, g0.subset(np.arange(0, 300)), cams[:1], 16, 16), g0.subset(np.arange(300, 450)),
+             curate_gaussians(O, g0.subset(np.arange(450, 700)), cams[1:], 16, 16)]
+    g = S.Gaussians.concat(parts)
+    off = np.cumsum([0] + [p.n for p in parts]).tolist()
+    rows = [(off[0], off[1]), (off[2], off[3])]
+    bg = (0.2, 0.1, 0.3)
+    deg, n = 3, g.n
+    xbuf = D.GaussianBuffer.from_synth(g)
+    vb = D.ViewBatch(cams, off, 16, 16)
+    assert D.one_view_per_block(vb.plan)
+    D.forward(xbuf, vb, bg)
+    torch.cuda.synchronize()
+    x = O.params_from(g)
+    plan = O.ViewPlan(cams, rows, 16, 16)
+    f = O.render(x, deg, plan, bg)
+    gmasks = pixel_mask(f["views"], 1e-4, grad=True)
+    rng = np.random.default_rng(6)
+    W = [rng.uniform(-1, 1, (3, c.height, c.width)) * m[None] for c, m in zip(cams, gmasks)]
+    dimg = torch.zeros_like(vb.image)
+    for v, w in enumerate(W):
+        vb.view_image(v, dimg).copy_(torch.from_numpy(w.astype(np.float32)))
+    ob = O.backward(x, deg, plan, f, W, bg)
+    # optimiser state, duals and the sharing flags
+    like = lambda seed, s: S.Gaussians(*(S.random_like(seed + i, a.shape, s) for i, a in
+                                         enumerate((g.means, g.quats, g.log_scales, g.opacity_logits, g.sh))))
+    m0 = like(50, 0.01)
+    v0 = S.Gaussians(*(np.abs(a) for a in (lambda t: (t.means, t.quats, t.log_scales, t.opacity_logits, t.sh))(like(60, 0.01))))
+    z0, u0 = like(70, 0.5), like(80, 0.05)
+    shared = (rng.uniform(size=n) < 0.4).astype(np.uint8)
+    mb, vb_, zb, ub = (D.GaussianBuffer.from_synth(a) for a in (m0, v0, z0, u0))
+    gid = torch.arange(n, dtype=torch.int32, device="cuda")
+    sh_t = torch.from_numpy(shared).cuda()
+    an = xbuf.like()
+    D.dg_admm_anchor(zb, ub, gid, sh_t, an)
+    rho = [1e4, 1e4, 1e4, 1e3, 1e4]
+    lr = [1.6e-4, 1e-3, 5e-3, 2.5e-3, 1.25e-4, 5e-2]
+    D.dg_backward_xstep(vb, xbuf, mb, vb_, an, sh_t, rho, lr, 0.9, 0.999, 1e-15, 3, bg=bg, dL_dimage=dimg)
+    torch.cuda.synchronize()
+    ox, om, ov = x.copy(), O.params_from(m0), O.params_from(v0)
+    O.adam_admm_step(ox, ob["dparams"], om, ov, O.params_from(z0), O.params_from(u0), np.arange(n),
+                     shared, rho, lr, deg, 0.9, 0.999, 1e-15, 3)
+    for buf, ref in ((xbuf, ox), (mb, om), (vb_, ov)):
+        got = buf.to_synth()
+        want = oracle_params_groups(O, ref, deg)
+        for name in GROUPS:
+            assert rel_l2(getattr(got, name), want[name]) < REL_L2, name
+    assert torch.all(xbuf.pad_lane() == 0)
+
+
+def test_fused_xstep_rejects_blocks_with_several_views(D):
+    cams = [S.cube_camera(32, 32), S.cube_camera(32, 32)]
+    g = S.cube_scene(50, 3)
+    xbuf = D.GaussianBuffer.from_synth(g)
+    vb = D.ViewBatch(cams, [0, g.n], 16, 16)
+    assert not D.one_view_per_block(vb.plan)
+    with pytest.raises(Exception):
+        D.dg_backward_xstep(vb, xbuf, xbuf.like(), xbuf.like(), None, None, [1.0] * 5, [1e-3] * 6)

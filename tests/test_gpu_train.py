@@ -236,3 +236,29 @@ def test_checkpoint_resume(mods, tmp_path):
         ga, gb = groups(getattr(a, buf)), groups(getattr(b, buf))
         for k in ga:
             assert rel_l2(gb[k], ga[k]) < REL_L2, (buf, k)
+
+
+def test_fused_xstep_equals_separate_calls(mods):
+    """The trainer's fused adjoint + x-step and the two separate calls,
+    iteration by iteration from identical state, agree up to the order of the
+    float atomics of the compositing adjoint."""
+    D, srv, T = mods
+    wl, z0, targets = small_setup(D, srv, seed=17)
+    kw = dict(rho=(1e-2,) * 5, loss="dssim", intv=2)
+    a = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, fused=True, **kw)
+    a.calibrate_capacity()
+    b = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, fused=False, **kw)
+    b.calibrate_capacity()
+    assert D.one_view_per_block(a.vb.plan)
+    for _ in range(3):
+        for n in ("x", "m", "v", "u", "z", "anchor"):
+            getattr(b, n).copy_(getattr(a, n))
+        b.t = a.t
+        a.step(graph=False)
+        b.step(graph=False)
+        torch.cuda.synchronize()
+        for n in ("x", "m", "v"):
+            ga, gb = groups(getattr(a, n)), groups(getattr(b, n))
+            for k in ga:
+                assert rel_l2(gb[k], ga[k]) < REL_L2, (n, k)
+    assert not a.overflowed()
