@@ -17,6 +17,7 @@ size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity);
 int launch_bin_sort(const float4*, const uint2*, const dg_camera*, const dg_plan&, int64_t, uint64_t*, uint32_t*,
                     uint32_t*, uint32_t*, void*, uint32_t*, cudaStream_t);
 int bin_sort_init();
+int loss_init();
 int launch_raster_fwd(const float4*, const uint32_t*, const uint32_t*, const dg_camera*, const dg_plan&,
                       const float*, float*, float*, uint32_t*, cudaStream_t);
 int launch_raster_count(const float4*, const uint32_t*, const uint32_t*, const dg_camera*, const dg_plan&,
@@ -77,6 +78,7 @@ static int ensure_init()
     uint64_t bit = 1ull << (dev & 63);
     if (done_mask.load() & bit) return DG_OK;
     int rc = bin_sort_init();
+    if (rc == DG_OK) rc = loss_init();
     if (rc == DG_OK) done_mask.fetch_or(bit);
     return rc;
 }
@@ -231,6 +233,8 @@ int dg_loss_dssim(const float* image, const float* target, const dg_camera* dev_
     if (!image || !target || !dev_cams || !loss || !dL_dimage) return DG_ERR_INVALID;
     if (!aligned8(dev_cams) || !aligned8(loss) || ((uintptr_t)ws & 7u)) return DG_ERR_INVALID;
     if (w_ssim != 0.f && (!ws || ws_bytes < loss_ws_bytes(*plan))) return DG_ERR_WORKSPACE;
+    int rc = ensure_init();
+    if (rc != DG_OK) return rc;
     return launch_loss(image, target, dev_cams, *plan, w_l1, w_ssim, loss, dL_dimage, ws, (cudaStream_t)stream);
 }
 

@@ -62,47 +62,57 @@ __global__ void k_loss_final(const dg_camera* __restrict__ cams, int n_views, fl
 }
 
 // ---- SSIM ------------------------------------------------------------------------
-// Output tile 32 x 32 per CTA (256 threads) with a 5-pixel halo.  Both passes
-// of the separable 11-tap filter are register-blocked: a thread produces 8
-// consecutive outputs from a window of 18 inputs held in registers, so each
-// input is read from shared memory once per pass instead of 11 times.
-constexpr int kTS = 32;                 // output tile side
-constexpr int kTI = kTS + 2 * kR;       // input tile side (42)
+// Output tile 32 x 54 per CTA (256 threads) with a 5-pixel halo, so the input
+// tile is 42 x 64: the horizontal pass is exactly one task per thread (64
+// input rows x 4 blocks of 8 columns) and the vertical pass 224 tasks (32
+// columns x 7 blocks of 8 rows).  Both passes are register-blocked: a thread
+// produces 8 consecutive outputs from a window of 18 inputs held in
+// registers, so each input is read from shared memory once per pass.
+constexpr int kTW = 32;                 // output tile width
+constexpr int kTH = 54;                 // output tile height
+constexpr int kIW = kTW + 2 * kR;       // input tile width (42)
+constexpr int kIH = kTH + 2 * kR;       // input tile height (64)
 constexpr int kBlk = 8;                 // outputs per thread per pass
 constexpr int kWin8 = kBlk + 2 * kR;    // 18 inputs per 8 outputs
+constexpr int kSsimThreads = 256;
+// shared-memory row strides, odd so that the passes' access patterns are
+// free of bank conflicts (8 rows x 4 column blocks per warp in the
+// horizontal pass, 32 consecutive columns in the vertical pass)
+constexpr int kIWP = kIW + 1;           // 43
+constexpr int kTWP = kTW + 1;           // 33
+constexpr int kVBlocks = (kTH + kBlk - 1) / kBlk;   // 7 row blocks in the vertical pass
 
-// horizontal pass over NM maps: for input rows [0, kTI) and output columns
-// [0, kTS): tmp[m][r][c] = sum_k w_k in_m[r][c + k]
+// horizontal pass over NM maps, one task per thread: input row r = tid / 4,
+// output columns c0 .. c0 + 7 with c0 = 8 (tid % 4): tmp[m][r][c] = sum_k w_k in_m[r][c + k]
 template <int NM, typename Load>
-__device__ __forceinline__ void hpass(const Win& g, float (*tmp)[kTI][kTS], Load load)
+__device__ __forceinline__ void hpass(const Win& g, float (*tmp)[kIH][kTWP], Load load)
 {
-    for (int task = threadIdx.x; task < kTI * (kTS / kBlk); task += blockDim.x) {
-        const int r = task / (kTS / kBlk), c0 = (task % (kTS / kBlk)) * kBlk;
-        float in[NM][kWin8];
+    const int r = threadIdx.x >> 2, c0 = (threadIdx.x & 3) * kBlk;
+    float in[NM][kWin8];
 #pragma unroll
-        for (int i = 0; i < kWin8; i++) load(r, c0 + i, in, i);
+    for (int i = 0; i < kWin8; i++) load(r, c0 + i, in, i);
 #pragma unroll
-        for (int m = 0; m < NM; m++)
+    for (int m = 0; m < NM; m++)
 #pragma unroll
-            for (int j = 0; j < kBlk; j++) {
-                float s = 0.f;
+        for (int j = 0; j < kBlk; j++) {
+            float s = 0.f;
 #pragma unroll
-                for (int k = 0; k < kWin; k++) s = fmaf(g.w[k], in[m][j + k], s);
-                tmp[m][r][c0 + j] = s;
-            }
-    }
+            for (int k = 0; k < kWin; k++) s = fmaf(g.w[k], in[m][j + k], s);
+            tmp[m][r][c0 + j] = s;
+        }
 }
 
-// vertical pass: out[m][j] = sum_k w_k tmp[m][r0 + j + k][c] for the thread's
-// column c and rows r0 .. r0 + 7
+// vertical pass: out[m][j] = sum_k w_k tmp[m][r0 + j + k][c] for column c and
+// rows r0 .. r0 + 7 (rows past the tile's input are read as the last row and
+// never stored)
 template <int NM>
-__device__ __forceinline__ void vpass(const Win& g, float (*tmp)[kTI][kTS], int c, int r0, float out[][kBlk])
+__device__ __forceinline__ void vpass(const Win& g, float (*tmp)[kIH][kTWP], int c, int r0, float out[][kBlk])
 {
 #pragma unroll
     for (int m = 0; m < NM; m++) {
         float col[kWin8];
 #pragma unroll
-        for (int i = 0; i < kWin8; i++) col[i] = tmp[m][r0 + i][c];
+        for (int i = 0; i < kWin8; i++) col[i] = tmp[m][min(r0 + i, kIH - 1)][c];
 #pragma unroll
         for (int j = 0; j < kBlk; j++) {
             float s = 0.f;
@@ -113,27 +123,29 @@ __device__ __forceinline__ void vpass(const Win& g, float (*tmp)[kTI][kTS], int 
     }
 }
 
-__global__ void __launch_bounds__(128) k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt,
-                                                  const dg_camera* __restrict__ cams, Win g, float w_ssim,
-                                                  double* __restrict__ sums, float* __restrict__ partial)
+__global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt,
+                                                          const dg_camera* __restrict__ cams, Win g, float w_ssim,
+                                                          double* __restrict__ sums, float* __restrict__ partial)
 {
-    __shared__ float s_x[kTI][kTI + 1];
-    __shared__ float s_y[kTI][kTI + 1];
-    __shared__ float s_tmp[5][kTI][kTS];
+    extern __shared__ float s_dyn[];
+    float (*s_x)[kIWP] = reinterpret_cast<float (*)[kIWP]>(s_dyn);
+    float (*s_y)[kIWP] = reinterpret_cast<float (*)[kIWP]>(s_dyn + kIH * kIWP);
+    float (*s_tmp)[kIH][kTWP] = reinterpret_cast<float (*)[kIH][kTWP]>(s_dyn + 2 * kIH * kIWP);
     const int v = blockIdx.z / 3, ch = blockIdx.z % 3;
     const int W = __ldg(&cams[v].width), H = __ldg(&cams[v].height);
-    const int x0 = blockIdx.x * kTS, y0 = blockIdx.y * kTS;
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
     if (x0 >= W || y0 >= H) return;
     const int64_t HW = (int64_t)W * H;
     const int64_t pix = __ldg(&cams[v].pix_off);
     const float* X = img + 3 * pix + ch * HW;
     const float* Y = tgt + 3 * pix + ch * HW;
-    for (int i = threadIdx.x; i < kTI * kTI; i += blockDim.x) {
-        const int r = i / kTI, c = i % kTI;
+    for (int i = threadIdx.x; i < kIH * kIW; i += kSsimThreads) {
+        const int r = i / kIW, c = i - r * kIW;
         const int gx = x0 + c - kR, gy = y0 + r - kR;
         const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        s_x[r][c] = ok ? X[(int64_t)gy * W + gx] : 0.f;
-        s_y[r][c] = ok ? Y[(int64_t)gy * W + gx] : 0.f;
+        const int64_t p = (int64_t)gy * W + gx;
+        s_x[r][c] = ok ? X[p] : 0.f;
+        s_y[r][c] = ok ? Y[p] : 0.f;
     }
     __syncthreads();
     hpass<5>(g, s_tmp, [&](int r, int c, float (*in)[kWin8], int i) {
@@ -145,23 +157,24 @@ __global__ void __launch_bounds__(128) k_ssim_fwd(const float* __restrict__ img,
     const float sc = -w_ssim / (float)(3 * HW);
     float acc = 0.f;
     float* P = partial + 9 * pix + 3 * ch * HW;
-    for (int task = threadIdx.x; task < kTS * (kTS / kBlk); task += blockDim.x) {
-        const int c = task % kTS, r0 = (task / kTS) * kBlk;
+    if (threadIdx.x < kTW * kVBlocks) {
+        const int c = threadIdx.x % kTW, r0 = (threadIdx.x / kTW) * kBlk;
         float mo[5][kBlk];
         vpass<5>(g, s_tmp, c, r0, mo);
         const int gx = x0 + c;
 #pragma unroll
         for (int j = 0; j < kBlk; j++) {
             const int gy = y0 + r0 + j;
-            if (gx >= W || gy >= H) continue;
+            if (r0 + j >= kTH || gx >= W || gy >= H) continue;
             const float m1 = mo[0][j], m2 = mo[1][j];
             const float s1 = mo[2][j] - m1 * m1, s2 = mo[3][j] - m2 * m2, s12 = mo[4][j] - m1 * m2;
             const float A1 = 2.f * m1 * m2 + C1, A2 = 2.f * s12 + C2;
             const float B1 = m1 * m1 + m2 * m2 + C1, B2 = s1 + s2 + C2;
-            const float iB = 1.f / (B1 * B2);
+            const float iB = __fdividef(1.f, B1 * B2);
             const float S = A1 * A2 * iB;
             acc += S;
-            const float dA1 = A2 * iB, dA2 = A1 * iB, dB1 = -S / B1, dB2 = -S / B2;
+            // dS/dA1, dS/dA2, dS/dB1 = -S / B1 = -S B2 iB, dS/dB2 = -S B1 iB
+            const float dA1 = A2 * iB, dA2 = A1 * iB, dB1 = -S * B2 * iB, dB2 = -S * B1 * iB;
             const float dm1 = 2.f * m2 * dA1 - 2.f * m2 * dA2 + 2.f * m1 * dB1 - 2.f * m1 * dB2;
             const int64_t p = (int64_t)gy * W + gx;
             P[p] = sc * dm1;
@@ -171,25 +184,33 @@ __global__ void __launch_bounds__(128) k_ssim_fwd(const float* __restrict__ img,
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    __shared__ float s_w[4];
+    __shared__ float s_w[kSsimThreads / 32];
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(&sums[v], (double)s_w[0] + s_w[1] + s_w[2] + s_w[3]);
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kSsimThreads / 32; i++) t += s_w[i];
+        atomicAdd(&sums[v], t);
+    }
 }
+
+constexpr size_t kSsimFwdSmem = sizeof(float) * (2 * kIH * kIWP + 5 * kIH * kTWP);
+constexpr size_t kSsimBwdSmem = sizeof(float) * (3 * kIH * kIWP + 3 * kIH * kTWP);
 
 // dL/dx = w_l1 sign(x - y) / N + F(a) + 2 x F(b) + y F(c); the L1 sum of the
 // tile is added to l1_sum[v].  The output pixels' x and y are loaded before the
 // filter passes so that their latency overlaps the shared-memory work.
-__global__ void __launch_bounds__(128) k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt,
-                                                  const dg_camera* __restrict__ cams, Win g, float w_l1,
-                                                  const float* __restrict__ partial, float* __restrict__ grad,
-                                                  double* __restrict__ l1_sum)
+__global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt,
+                                                          const dg_camera* __restrict__ cams, Win g, float w_l1,
+                                                          const float* __restrict__ partial, float* __restrict__ grad,
+                                                          double* __restrict__ l1_sum)
 {
-    __shared__ float s_p[3][kTI][kTI + 1];
-    __shared__ float s_tmp[3][kTI][kTS];
+    extern __shared__ float s_dyn[];
+    float (*s_p)[kIH][kIWP] = reinterpret_cast<float (*)[kIH][kIWP]>(s_dyn);
+    float (*s_tmp)[kIH][kTWP] = reinterpret_cast<float (*)[kIH][kTWP]>(s_dyn + 3 * kIH * kIWP);
     const int v = blockIdx.z / 3, ch = blockIdx.z % 3;
     const int W = __ldg(&cams[v].width), H = __ldg(&cams[v].height);
-    const int x0 = blockIdx.x * kTS, y0 = blockIdx.y * kTS;
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
     if (x0 >= W || y0 >= H) return;
     const int64_t HW = (int64_t)W * H;
     const int64_t pix = __ldg(&cams[v].pix_off);
@@ -197,21 +218,21 @@ __global__ void __launch_bounds__(128) k_ssim_bwd(const float* __restrict__ img,
     const float* X = img + 3 * pix + ch * HW;
     const float* Y = tgt + 3 * pix + ch * HW;
     float* G = grad + 3 * pix + ch * HW;
-    // this thread's outputs: column c, rows r0 .. r0 + 7 (one task per thread)
-    const int c = threadIdx.x % kTS, r0 = (threadIdx.x / kTS) * kBlk;
+    // this thread's outputs: column c, rows r0 .. r0 + 7
+    const bool has_out = threadIdx.x < kTW * kVBlocks;
+    const int c = threadIdx.x % kTW, r0 = (threadIdx.x / kTW) * kBlk;
     const int gx = x0 + c;
     float xv[kBlk], yv[kBlk];
 #pragma unroll
     for (int j = 0; j < kBlk; j++) {
         const int gy = y0 + r0 + j;
-        const bool ok = gx < W && gy < H;
+        const bool ok = has_out && r0 + j < kTH && gx < W && gy < H;
         const int64_t p = (int64_t)gy * W + gx;
         xv[j] = ok ? X[p] : 0.f;
         yv[j] = ok ? Y[p] : 0.f;
     }
-#pragma unroll 4
-    for (int i = threadIdx.x; i < kTI * kTI; i += blockDim.x) {
-        const int r = i / kTI, cc = i % kTI;
+    for (int i = threadIdx.x; i < kIH * kIW; i += kSsimThreads) {
+        const int r = i / kIW, cc = i - r * kIW;
         const int hx = x0 + cc - kR, hy = y0 + r - kR;
         const bool ok = hx >= 0 && hx < W && hy >= 0 && hy < H;
         const int64_t p = (int64_t)hy * W + hx;
@@ -223,26 +244,41 @@ __global__ void __launch_bounds__(128) k_ssim_bwd(const float* __restrict__ img,
         in[0][i] = s_p[0][r][cc]; in[1][i] = s_p[1][r][cc]; in[2][i] = s_p[2][r][cc];
     });
     __syncthreads();
-    float fo[3][kBlk];
-    vpass<3>(g, s_tmp, c, r0, fo);
-    const float wl = w_l1 / (float)(3 * HW);
     float acc = 0.f;
+    if (has_out) {
+        float fo[3][kBlk];
+        vpass<3>(g, s_tmp, c, r0, fo);
+        const float wl = w_l1 / (float)(3 * HW);
 #pragma unroll
-    for (int j = 0; j < kBlk; j++) {
-        const int gy = y0 + r0 + j;
-        if (gx >= W || gy >= H) continue;
-        const int64_t p = (int64_t)gy * W + gx;
-        const float d = xv[j] - yv[j];
-        acc += fabsf(d);
-        const float l1g = d > 0.f ? wl : (d < 0.f ? -wl : 0.f);
-        G[p] = l1g + fo[0][j] + 2.f * xv[j] * fo[1][j] + yv[j] * fo[2][j];
+        for (int j = 0; j < kBlk; j++) {
+            const int gy = y0 + r0 + j;
+            if (r0 + j >= kTH || gx >= W || gy >= H) continue;
+            const int64_t p = (int64_t)gy * W + gx;
+            const float d = xv[j] - yv[j];
+            acc += fabsf(d);
+            const float l1g = d > 0.f ? wl : (d < 0.f ? -wl : 0.f);
+            G[p] = l1g + fo[0][j] + 2.f * xv[j] * fo[1][j] + yv[j] * fo[2][j];
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    __shared__ float s_w[4];
+    __shared__ float s_w[kSsimThreads / 32];
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(&l1_sum[v], (double)s_w[0] + s_w[1] + s_w[2] + s_w[3]);
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kSsimThreads / 32; i++) t += s_w[i];
+        atomicAdd(&l1_sum[v], t);
+    }
+}
+
+int loss_init()
+{
+    if (cudaFuncSetAttribute(k_ssim_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSsimFwdSmem) != cudaSuccess)
+        return DG_ERR_CUDA;
+    if (cudaFuncSetAttribute(k_ssim_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSsimBwdSmem) != cudaSuccess)
+        return DG_ERR_CUDA;
+    return DG_OK;
 }
 
 static size_t sums_bytes(const dg_plan& plan) { return ((size_t)plan.n_views * sizeof(double) + 255) / 256 * 256; }
@@ -267,10 +303,10 @@ int launch_loss(const float* img, const float* tgt, const dg_camera* cams, const
         float* partial = (float*)((char*)ws + sums_bytes(plan));
         if (cudaMemsetAsync(ssum, 0, (size_t)plan.n_views * sizeof(double), st) != cudaSuccess) return DG_ERR_CUDA;
         Win g = gaussian_window();
-        dim3 grid((unsigned)((plan.max_width + kTS - 1) / kTS), (unsigned)((plan.max_height + kTS - 1) / kTS),
+        dim3 grid((unsigned)((plan.max_width + kTW - 1) / kTW), (unsigned)((plan.max_height + kTH - 1) / kTH),
                   (unsigned)(3 * plan.n_views));
-        k_ssim_fwd<<<grid, 128, 0, st>>>(img, tgt, cams, g, w_ssim, ssum, partial);
-        k_ssim_bwd<<<grid, 128, 0, st>>>(img, tgt, cams, g, w_l1, partial, grad, loss);
+        k_ssim_fwd<<<grid, kSsimThreads, kSsimFwdSmem, st>>>(img, tgt, cams, g, w_ssim, ssum, partial);
+        k_ssim_bwd<<<grid, kSsimThreads, kSsimBwdSmem, st>>>(img, tgt, cams, g, w_l1, partial, grad, loss);
         note_launch(2);
     }
     k_loss_final<<<(plan.n_views + 127) / 128, 128, 0, st>>>(cams, plan.n_views, w_l1, w_ssim, ssum, loss);
