@@ -299,11 +299,11 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float* v, float& v8,
 // walk at position last - 1; each thread keeps a mask of its joined pixels
 // and the next position at which another one joins, so the per-pair test is
 // one bit.
-// register budget: 20 resident single-warp CTAs per SM for NW = 1; for the
+// register budget: 24 resident single-warp CTAs per SM for NW = 1; for the
 // wider variants 32 warps per SM with one staged instance per thread and 24
 // with two (the budgets that compile without spilling)
 template <int NW, int S>
-constexpr int bwd_min_blocks() { return NW == 1 ? 20 : (S == 1 ? 32 : 24) / NW; }
+constexpr int bwd_min_blocks() { return NW == 1 ? 24 : (S == 1 ? 32 : 24) / NW; }
 
 template <int NW, int S>
 __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd(const float4* __restrict__ rec,
