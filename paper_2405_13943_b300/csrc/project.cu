@@ -550,26 +550,41 @@ __global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView
         sh[i] = act[i] && shared != nullptr && shared[cq + i] != 0;
     }
     const bool any_sh = sh[0] || sh[1] || sh[2] || sh[3];
-    for (int j = tid >> 5; j < 3 * NK; j += kXsThreads / 32) {
-        const float lr = j < 3 ? a.lr[3] : a.lr[4];
-        const int64_t u = ((int64_t)j * x.ld + cq) >> 2;
-        float4* X = reinterpret_cast<float4*>(x.sh) + u;
-        float4* M = reinterpret_cast<float4*>(m.sh) + u;
-        float4* V = reinterpret_cast<float4*>(v.sh) + u;
-        const float4 xv = *X, mv = *M, vv = *V;
-        const float4 av = any_sh ? reinterpret_cast<const float4*>(an.sh)[u] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float xs[4] = {xv.x, xv.y, xv.z, xv.w}, ms[4] = {mv.x, mv.y, mv.z, mv.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
-        const float as[4] = {av.x, av.y, av.z, av.w};
+    // four planes per batch, all loads of the batch issued before its stores
+    constexpr int G = kXsThreads / 32;          // plane groups (4)
+    constexpr int PB = 4;                       // planes per batch and thread
+    for (int j0 = tid >> 5; j0 < 3 * NK; j0 += G * PB) {
+        float4 xv[PB], mv[PB], vv[PB], av[PB];
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            if (!act[i]) continue;
-            float g = s_gc[j % 3][4 * quad + i] * s_Y[j / 3][4 * quad + i];
-            if (sh[i]) g += a.rho[3] * (xs[i] - as[i]);
-            adam_scalar(xs[i], g, ms[i], vs[i], lr, a.b1, a.b2, a.eps, ic1, ic2);
+        for (int b = 0; b < PB; b++) {
+            const int j = j0 + b * G;
+            if (j >= 3 * NK) break;
+            const int64_t u = ((int64_t)j * x.ld + cq) >> 2;
+            xv[b] = reinterpret_cast<const float4*>(x.sh)[u];
+            mv[b] = reinterpret_cast<const float4*>(m.sh)[u];
+            vv[b] = reinterpret_cast<const float4*>(v.sh)[u];
+            av[b] = any_sh ? reinterpret_cast<const float4*>(an.sh)[u] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        *X = make_float4(xs[0], xs[1], xs[2], xs[3]);
-        *M = make_float4(ms[0], ms[1], ms[2], ms[3]);
-        *V = make_float4(vs[0], vs[1], vs[2], vs[3]);
+#pragma unroll
+        for (int b = 0; b < PB; b++) {
+            const int j = j0 + b * G;
+            if (j >= 3 * NK) break;
+            const float lr = j < 3 ? a.lr[3] : a.lr[4];
+            float xs[4] = {xv[b].x, xv[b].y, xv[b].z, xv[b].w}, ms[4] = {mv[b].x, mv[b].y, mv[b].z, mv[b].w};
+            float vs[4] = {vv[b].x, vv[b].y, vv[b].z, vv[b].w};
+            const float as[4] = {av[b].x, av[b].y, av[b].z, av[b].w};
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                if (!act[i]) continue;
+                float g = s_gc[j % 3][4 * quad + i] * s_Y[j / 3][4 * quad + i];
+                if (sh[i]) g += a.rho[3] * (xs[i] - as[i]);
+                adam_scalar(xs[i], g, ms[i], vs[i], lr, a.b1, a.b2, a.eps, ic1, ic2);
+            }
+            const int64_t u = ((int64_t)j * x.ld + cq) >> 2;
+            reinterpret_cast<float4*>(x.sh)[u] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+            reinterpret_cast<float4*>(m.sh)[u] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+            reinterpret_cast<float4*>(v.sh)[u] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        }
     }
 }
 
