@@ -550,9 +550,9 @@ __global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView
         sh[i] = act[i] && shared != nullptr && shared[cq + i] != 0;
     }
     const bool any_sh = sh[0] || sh[1] || sh[2] || sh[3];
-    // four planes per batch, all loads of the batch issued before its stores
+    // six planes per batch, all loads of the batch issued before its stores
     constexpr int G = kXsThreads / 32;          // plane groups (4)
-    constexpr int PB = 4;                       // planes per batch and thread
+    constexpr int PB = 6;                       // planes per batch and thread
     for (int j0 = tid >> 5; j0 < 3 * NK; j0 += G * PB) {
         float4 xv[PB], mv[PB], vv[PB], av[PB];
 #pragma unroll
