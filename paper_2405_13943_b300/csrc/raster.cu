@@ -81,7 +81,9 @@ __device__ __forceinline__ float strip_p(const Strip& s, int k)
     return __fmaf_rn(__fmaf_rn(s.gamma, (float)k, s.beta), (float)k, s.p0);
 }
 
-template <int PPL>
+// BOUND = false skips the strip bound (pmax is left unset): the per-pixel
+// reach tests decide alone, the bound only ever skipped pixels they reject.
+template <int PPL, bool BOUND = true>
 __device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float B, float C, float fx, float fy0,
                                              float ddy)
 {
@@ -91,7 +93,9 @@ __device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float 
     st.p0 = __fmaf_rn(__fmul_rn(C, dy0), dy0, __fmul_rn(dx, t));
     st.beta = __fmul_rn(-ddy, __fmaf_rn(2.f * C, dy0, __fmul_rn(B, dx)));
     st.gamma = __fmul_rn(C, __fmul_rn(ddy, ddy));
-    if (PPL == 1) {
+    if (!BOUND) {
+        st.pmax = 0.f;
+    } else if (PPL == 1) {
         st.pmax = st.p0;
     } else {
         // concave in k (gamma < 0): largest at the vertex, clamped to [0, PPL-1]
@@ -213,8 +217,7 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
             const float4 g = s_g[j];
             const float2 h = s_h[j];
             if (CNT) n_seen += __popc(live);
-            Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, G.fx, G.fy0, G.dy);
-            if (__fadd_rn(sp.pmax, h.y) < -8.0f) continue;   // no pixel of the strip reaches 2^-8
+            const Strip sp = strip_setup<PPL, false>(g.x, g.y, g.z, g.w, h.x, G.fx, G.fy0, G.dy);
             const float4 c = s_c[j];
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
