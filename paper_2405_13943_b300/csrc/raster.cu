@@ -401,8 +401,8 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             }
             const float4 g = s_g[j];
             const float4 h = s_h[j];
-            Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, Lg.fx, Lg.fy0, Lg.dy);
-            const uint32_t todo = __fadd_rn(sp.pmax, h.y) >= -8.0f ? joined & strip_reach<PPL>(sp, h.y) : 0u;
+            const Strip sp = strip_setup<PPL, false>(g.x, g.y, g.z, g.w, h.x, Lg.fx, Lg.fy0, Lg.dy);
+            const uint32_t todo = joined & strip_reach<PPL>(sp, h.y);
             if (!__any_sync(0xffffffffu, todo != 0u)) continue;
             const float4 c = s_c[j];
             // colour sums and the moments of dL/dpower along the strip:
