@@ -123,79 +123,140 @@ __device__ __forceinline__ void vpass(const Win& g, float (*tmp)[kIH][kTWP], int
     }
 }
 
-__global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt,
-                                                          const dg_camera* __restrict__ cams, Win g, float w_ssim,
-                                                          double* __restrict__ sums, float* __restrict__ partial)
+// ---- persistent, double-buffered SSIM passes ---------------------------------------
+// Each CTA walks work items (view, channel, tile) with a stride of the grid;
+// the input halo of the next item is copied into the other shared-memory
+// buffer by cp.async (zero-filled outside the image) while the current item
+// is filtered, so the loads' latency hides behind the arithmetic.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok)
 {
-    extern __shared__ float s_dyn[];
-    float (*s_x)[kIWP] = reinterpret_cast<float (*)[kIWP]>(s_dyn);
-    float (*s_y)[kIWP] = reinterpret_cast<float (*)[kIWP]>(s_dyn + kIH * kIWP);
-    float (*s_tmp)[kIH][kTWP] = reinterpret_cast<float (*)[kIH][kTWP]>(s_dyn + 2 * kIH * kIWP);
-    const int v = blockIdx.z / 3, ch = blockIdx.z % 3;
-    const int W = __ldg(&cams[v].width), H = __ldg(&cams[v].height);
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-    if (x0 >= W || y0 >= H) return;
-    const int64_t HW = (int64_t)W * H;
-    const int64_t pix = __ldg(&cams[v].pix_off);
-    const float* X = img + 3 * pix + ch * HW;
-    const float* Y = tgt + 3 * pix + ch * HW;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+struct SsimItem {
+    int v, ch, x0, y0, W, H;
+    int64_t HW, pix;
+    bool ok;
+};
+
+__device__ __forceinline__ SsimItem ssim_item(const dg_camera* __restrict__ cams, int w, int TX, int TY)
+{
+    SsimItem it;
+    const int per = TX * TY, z = w / per, rem = w - z * per;
+    it.v = z / 3;
+    it.ch = z - 3 * it.v;
+    it.x0 = (rem % TX) * kTW;
+    it.y0 = (rem / TX) * kTH;
+    it.W = __ldg(&cams[it.v].width);
+    it.H = __ldg(&cams[it.v].height);
+    it.HW = (int64_t)it.W * it.H;
+    it.pix = __ldg(&cams[it.v].pix_off);
+    it.ok = it.x0 < it.W && it.y0 < it.H;
+    return it;
+}
+
+// copy NP planes (plane m at base + m * plane_stride) of item `it`'s input halo into dst[m][kIH][kIWP]
+template <int NP>
+__device__ __forceinline__ void ssim_issue(const SsimItem& it, const float* const* base, int64_t plane_stride,
+                                           float* dst)
+{
+    if (!it.ok) return;
     for (int i = threadIdx.x; i < kIH * kIW; i += kSsimThreads) {
         const int r = i / kIW, c = i - r * kIW;
-        const int gx = x0 + c - kR, gy = y0 + r - kR;
-        const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const int64_t p = (int64_t)gy * W + gx;
-        s_x[r][c] = ok ? X[p] : 0.f;
-        s_y[r][c] = ok ? Y[p] : 0.f;
-    }
-    __syncthreads();
-    hpass<5>(g, s_tmp, [&](int r, int c, float (*in)[kWin8], int i) {
-        const float a = s_x[r][c], b = s_y[r][c];
-        in[0][i] = a; in[1][i] = b; in[2][i] = a * a; in[3][i] = b * b; in[4][i] = a * b;
-    });
-    __syncthreads();
-    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-    const float sc = -w_ssim / (float)(3 * HW);
-    float acc = 0.f;
-    float* P = partial + 9 * pix + 3 * ch * HW;
-    if (threadIdx.x < kTW * kVBlocks) {
-        const int c = threadIdx.x % kTW, r0 = (threadIdx.x / kTW) * kBlk;
-        float mo[5][kBlk];
-        vpass<5>(g, s_tmp, c, r0, mo);
-        const int gx = x0 + c;
+        const int gx = it.x0 + c - kR, gy = it.y0 + r - kR;
+        const bool ok = gx >= 0 && gx < it.W && gy >= 0 && gy < it.H;
+        const int64_t p = ok ? (int64_t)gy * it.W + gx : 0;
 #pragma unroll
-        for (int j = 0; j < kBlk; j++) {
-            const int gy = y0 + r0 + j;
-            if (r0 + j >= kTH || gx >= W || gy >= H) continue;
-            const float m1 = mo[0][j], m2 = mo[1][j];
-            const float s1 = mo[2][j] - m1 * m1, s2 = mo[3][j] - m2 * m2, s12 = mo[4][j] - m1 * m2;
-            const float A1 = 2.f * m1 * m2 + C1, A2 = 2.f * s12 + C2;
-            const float B1 = m1 * m1 + m2 * m2 + C1, B2 = s1 + s2 + C2;
-            const float iB = __fdividef(1.f, B1 * B2);
-            const float S = A1 * A2 * iB;
-            acc += S;
-            // dS/dA1, dS/dA2, dS/dB1 = -S / B1 = -S B2 iB, dS/dB2 = -S B1 iB
-            const float dA1 = A2 * iB, dA2 = A1 * iB, dB1 = -S * B2 * iB, dB2 = -S * B1 * iB;
-            const float dm1 = 2.f * m2 * dA1 - 2.f * m2 * dA2 + 2.f * m1 * dB1 - 2.f * m1 * dB2;
-            const int64_t p = (int64_t)gy * W + gx;
-            P[p] = sc * dm1;
-            P[HW + p] = sc * dB2;
-            P[2 * HW + p] = sc * 2.f * dA2;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    __shared__ float s_w[kSsimThreads / 32];
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < kSsimThreads / 32; i++) t += s_w[i];
-        atomicAdd(&sums[v], t);
+        for (int m = 0; m < NP; m++)
+            cp_async4(dst + (m * kIH + r) * kIWP + c, base[m] + m * plane_stride + p, ok);
     }
 }
 
-constexpr size_t kSsimFwdSmem = sizeof(float) * (2 * kIH * kIWP + 5 * kIH * kTWP);
-constexpr size_t kSsimBwdSmem = sizeof(float) * (3 * kIH * kIWP + 3 * kIH * kTWP);
+__global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt,
+                                                          const dg_camera* __restrict__ cams, Win g, float w_ssim,
+                                                          double* __restrict__ sums, float* __restrict__ partial,
+                                                          int TX, int TY, int n_work)
+{
+    extern __shared__ float s_dyn[];
+    float* s_in = s_dyn;                                   // [2 buffers][x, y][kIH][kIWP]
+    float (*s_tmp)[kIH][kTWP] = reinterpret_cast<float (*)[kIH][kTWP]>(s_dyn + 4 * kIH * kIWP);
+    __shared__ float s_w[kSsimThreads / 32];
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    int buf = 0;
+    {
+        const int w = blockIdx.x;
+        if (w < n_work) {
+            const SsimItem it = ssim_item(cams, w, TX, TY);
+            const float* bp[2] = {img + 3 * it.pix + it.ch * it.HW, tgt + 3 * it.pix + it.ch * it.HW};
+            ssim_issue<2>(it, bp, 0, s_in);
+        }
+        cp_async_commit();
+    }
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x, buf ^= 1) {
+        const int wn = w + gridDim.x;
+        if (wn < n_work) {
+            const SsimItem nt = ssim_item(cams, wn, TX, TY);
+            const float* bp[2] = {img + 3 * nt.pix + nt.ch * nt.HW, tgt + 3 * nt.pix + nt.ch * nt.HW};
+            ssim_issue<2>(nt, bp, 0, s_in + (buf ^ 1) * 2 * kIH * kIWP);
+        }
+        cp_async_commit();
+        cp_async_wait_prev();
+        __syncthreads();
+        const SsimItem it = ssim_item(cams, w, TX, TY);
+        if (!it.ok) continue;                         // uniform over the CTA
+        const float (*s_x)[kIWP] = reinterpret_cast<const float (*)[kIWP]>(s_in + buf * 2 * kIH * kIWP);
+        const float (*s_y)[kIWP] = reinterpret_cast<const float (*)[kIWP]>(s_in + (buf * 2 + 1) * kIH * kIWP);
+        hpass<5>(g, s_tmp, [&](int r, int c, float (*in)[kWin8], int i) {
+            const float a = s_x[r][c], b = s_y[r][c];
+            in[0][i] = a; in[1][i] = b; in[2][i] = a * a; in[3][i] = b * b; in[4][i] = a * b;
+        });
+        __syncthreads();
+        const float sc = -w_ssim / (float)(3 * it.HW);
+        float acc = 0.f;
+        float* P = partial + 9 * it.pix + 3 * it.ch * it.HW;
+        if (threadIdx.x < kTW * kVBlocks) {
+            const int c = threadIdx.x % kTW, r0 = (threadIdx.x / kTW) * kBlk;
+            float mo[5][kBlk];
+            vpass<5>(g, s_tmp, c, r0, mo);
+            const int gx = it.x0 + c;
+#pragma unroll
+            for (int j = 0; j < kBlk; j++) {
+                const int gy = it.y0 + r0 + j;
+                if (r0 + j >= kTH || gx >= it.W || gy >= it.H) continue;
+                const float m1 = mo[0][j], m2 = mo[1][j];
+                const float s1 = mo[2][j] - m1 * m1, s2 = mo[3][j] - m2 * m2, s12 = mo[4][j] - m1 * m2;
+                const float A1 = 2.f * m1 * m2 + C1, A2 = 2.f * s12 + C2;
+                const float B1 = m1 * m1 + m2 * m2 + C1, B2 = s1 + s2 + C2;
+                const float iB = __fdividef(1.f, B1 * B2);
+                const float S = A1 * A2 * iB;
+                acc += S;
+                // dS/dA1, dS/dA2, dS/dB1 = -S / B1 = -S B2 iB, dS/dB2 = -S B1 iB
+                const float dA1 = A2 * iB, dA2 = A1 * iB, dB1 = -S * B2 * iB, dB2 = -S * B1 * iB;
+                const float dm1 = 2.f * m2 * dA1 - 2.f * m2 * dA2 + 2.f * m1 * dB1 - 2.f * m1 * dB2;
+                const int64_t p = (int64_t)gy * it.W + gx;
+                P[p] = sc * dm1;
+                P[it.HW + p] = sc * dB2;
+                P[2 * it.HW + p] = sc * 2.f * dA2;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int i = 0; i < kSsimThreads / 32; i++) t += s_w[i];
+            atomicAdd(&sums[it.v], t);
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+constexpr size_t kSsimFwdSmem = sizeof(float) * (4 * kIH * kIWP + 5 * kIH * kTWP);
+constexpr size_t kSsimBwdSmem = sizeof(float) * (6 * kIH * kIWP + 3 * kIH * kTWP);
 
 // dL/dx = w_l1 sign(x - y) / N + F(a) + 2 x F(b) + y F(c); the L1 sum of the
 // tile is added to l1_sum[v].  The output pixels' x and y are loaded before the
@@ -203,74 +264,87 @@ constexpr size_t kSsimBwdSmem = sizeof(float) * (3 * kIH * kIWP + 3 * kIH * kTWP
 __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt,
                                                           const dg_camera* __restrict__ cams, Win g, float w_l1,
                                                           const float* __restrict__ partial, float* __restrict__ grad,
-                                                          double* __restrict__ l1_sum)
+                                                          double* __restrict__ l1_sum, int TX, int TY, int n_work)
 {
     extern __shared__ float s_dyn[];
-    float (*s_p)[kIH][kIWP] = reinterpret_cast<float (*)[kIH][kIWP]>(s_dyn);
-    float (*s_tmp)[kIH][kTWP] = reinterpret_cast<float (*)[kIH][kTWP]>(s_dyn + 3 * kIH * kIWP);
-    const int v = blockIdx.z / 3, ch = blockIdx.z % 3;
-    const int W = __ldg(&cams[v].width), H = __ldg(&cams[v].height);
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-    if (x0 >= W || y0 >= H) return;
-    const int64_t HW = (int64_t)W * H;
-    const int64_t pix = __ldg(&cams[v].pix_off);
-    const float* P = partial + 9 * pix + 3 * ch * HW;
-    const float* X = img + 3 * pix + ch * HW;
-    const float* Y = tgt + 3 * pix + ch * HW;
-    float* G = grad + 3 * pix + ch * HW;
-    // this thread's outputs: column c, rows r0 .. r0 + 7
+    float* s_in = s_dyn;                                   // [2 buffers][3 maps][kIH][kIWP]
+    float (*s_tmp)[kIH][kTWP] = reinterpret_cast<float (*)[kIH][kTWP]>(s_dyn + 6 * kIH * kIWP);
+    __shared__ float s_w[kSsimThreads / 32];
     const bool has_out = threadIdx.x < kTW * kVBlocks;
     const int c = threadIdx.x % kTW, r0 = (threadIdx.x / kTW) * kBlk;
-    const int gx = x0 + c;
-    float xv[kBlk], yv[kBlk];
-#pragma unroll
-    for (int j = 0; j < kBlk; j++) {
-        const int gy = y0 + r0 + j;
-        const bool ok = has_out && r0 + j < kTH && gx < W && gy < H;
-        const int64_t p = (int64_t)gy * W + gx;
-        xv[j] = ok ? X[p] : 0.f;
-        yv[j] = ok ? Y[p] : 0.f;
+    int buf = 0;
+    {
+        const int w = blockIdx.x;
+        if (w < n_work) {
+            const SsimItem it = ssim_item(cams, w, TX, TY);
+            const float* P = partial + 9 * it.pix + 3 * it.ch * it.HW;
+            const float* bp[3] = {P, P, P};
+            ssim_issue<3>(it, bp, it.HW, s_in);
+        }
+        cp_async_commit();
     }
-    for (int i = threadIdx.x; i < kIH * kIW; i += kSsimThreads) {
-        const int r = i / kIW, cc = i - r * kIW;
-        const int hx = x0 + cc - kR, hy = y0 + r - kR;
-        const bool ok = hx >= 0 && hx < W && hy >= 0 && hy < H;
-        const int64_t p = (int64_t)hy * W + hx;
-#pragma unroll
-        for (int m = 0; m < 3; m++) s_p[m][r][cc] = ok ? P[m * HW + p] : 0.f;
-    }
-    __syncthreads();
-    hpass<3>(g, s_tmp, [&](int r, int cc, float (*in)[kWin8], int i) {
-        in[0][i] = s_p[0][r][cc]; in[1][i] = s_p[1][r][cc]; in[2][i] = s_p[2][r][cc];
-    });
-    __syncthreads();
-    float acc = 0.f;
-    if (has_out) {
-        float fo[3][kBlk];
-        vpass<3>(g, s_tmp, c, r0, fo);
-        const float wl = w_l1 / (float)(3 * HW);
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x, buf ^= 1) {
+        const int wn = w + gridDim.x;
+        if (wn < n_work) {
+            const SsimItem nt = ssim_item(cams, wn, TX, TY);
+            const float* P = partial + 9 * nt.pix + 3 * nt.ch * nt.HW;
+            const float* bp[3] = {P, P, P};
+            ssim_issue<3>(nt, bp, nt.HW, s_in + (buf ^ 1) * 3 * kIH * kIWP);
+        }
+        cp_async_commit();
+        const SsimItem it = ssim_item(cams, w, TX, TY);
+        // this thread's outputs: column c, rows r0 .. r0 + 7
+        const float* X = img + 3 * it.pix + it.ch * it.HW;
+        const float* Y = tgt + 3 * it.pix + it.ch * it.HW;
+        const int gx = it.x0 + c;
+        float xv[kBlk], yv[kBlk];
 #pragma unroll
         for (int j = 0; j < kBlk; j++) {
-            const int gy = y0 + r0 + j;
-            if (r0 + j >= kTH || gx >= W || gy >= H) continue;
-            const int64_t p = (int64_t)gy * W + gx;
-            const float d = xv[j] - yv[j];
-            acc += fabsf(d);
-            const float l1g = d > 0.f ? wl : (d < 0.f ? -wl : 0.f);
-            G[p] = l1g + fo[0][j] + 2.f * xv[j] * fo[1][j] + yv[j] * fo[2][j];
+            const int gy = it.y0 + r0 + j;
+            const bool ok = it.ok && has_out && r0 + j < kTH && gx < it.W && gy < it.H;
+            const int64_t p = (int64_t)gy * it.W + gx;
+            xv[j] = ok ? X[p] : 0.f;
+            yv[j] = ok ? Y[p] : 0.f;
+        }
+        cp_async_wait_prev();
+        __syncthreads();
+        if (!it.ok) continue;                         // uniform over the CTA
+        const float (*s_p)[kIH][kIWP] = reinterpret_cast<const float (*)[kIH][kIWP]>(s_in + buf * 3 * kIH * kIWP);
+        hpass<3>(g, s_tmp, [&](int r, int cc, float (*in)[kWin8], int i) {
+            in[0][i] = s_p[0][r][cc]; in[1][i] = s_p[1][r][cc]; in[2][i] = s_p[2][r][cc];
+        });
+        __syncthreads();
+        float acc = 0.f;
+        if (has_out) {
+            float fo[3][kBlk];
+            vpass<3>(g, s_tmp, c, r0, fo);
+            const float wl = w_l1 / (float)(3 * it.HW);
+            float* G = grad + 3 * it.pix + it.ch * it.HW;
+#pragma unroll
+            for (int j = 0; j < kBlk; j++) {
+                const int gy = it.y0 + r0 + j;
+                if (r0 + j >= kTH || gx >= it.W || gy >= it.H) continue;
+                const int64_t p = (int64_t)gy * it.W + gx;
+                const float d = xv[j] - yv[j];
+                acc += fabsf(d);
+                const float l1g = d > 0.f ? wl : (d < 0.f ? -wl : 0.f);
+                G[p] = l1g + fo[0][j] + 2.f * xv[j] * fo[1][j] + yv[j] * fo[2][j];
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int i = 0; i < kSsimThreads / 32; i++) t += s_w[i];
+            atomicAdd(&l1_sum[it.v], t);
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    __shared__ float s_w[kSsimThreads / 32];
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < kSsimThreads / 32; i++) t += s_w[i];
-        atomicAdd(&l1_sum[v], t);
-    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
+
+static int g_ssim_ctas[2] = {0, 0};   // resident CTAs per SM x SMs, for the forward and the backward
 
 int loss_init()
 {
@@ -278,6 +352,14 @@ int loss_init()
         return DG_ERR_CUDA;
     if (cudaFuncSetAttribute(k_ssim_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSsimBwdSmem) != cudaSuccess)
         return DG_ERR_CUDA;
+    int dev = 0, sms = 0, bf = 0, bb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_ssim_fwd, kSsimThreads, kSsimFwdSmem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_ssim_bwd, kSsimThreads, kSsimBwdSmem) != cudaSuccess)
+        return DG_ERR_CUDA;
+    g_ssim_ctas[0] = sms * (bf > 0 ? bf : 1);
+    g_ssim_ctas[1] = sms * (bb > 0 ? bb : 1);
     return DG_OK;
 }
 
@@ -303,10 +385,15 @@ int launch_loss(const float* img, const float* tgt, const dg_camera* cams, const
         float* partial = (float*)((char*)ws + sums_bytes(plan));
         if (cudaMemsetAsync(ssum, 0, (size_t)plan.n_views * sizeof(double), st) != cudaSuccess) return DG_ERR_CUDA;
         Win g = gaussian_window();
-        dim3 grid((unsigned)((plan.max_width + kTW - 1) / kTW), (unsigned)((plan.max_height + kTH - 1) / kTH),
-                  (unsigned)(3 * plan.n_views));
-        k_ssim_fwd<<<grid, kSsimThreads, kSsimFwdSmem, st>>>(img, tgt, cams, g, w_ssim, ssum, partial);
-        k_ssim_bwd<<<grid, kSsimThreads, kSsimBwdSmem, st>>>(img, tgt, cams, g, w_l1, partial, grad, loss);
+        const int TX = (plan.max_width + kTW - 1) / kTW, TY = (plan.max_height + kTH - 1) / kTH;
+        const int64_t n_work = 3 * (int64_t)plan.n_views * TX * TY;
+        if (n_work >= (int64_t)1 << 31) return DG_ERR_INVALID;
+        const int gf = (int)(n_work < g_ssim_ctas[0] ? n_work : g_ssim_ctas[0]);
+        const int gb = (int)(n_work < g_ssim_ctas[1] ? n_work : g_ssim_ctas[1]);
+        k_ssim_fwd<<<gf, kSsimThreads, kSsimFwdSmem, st>>>(img, tgt, cams, g, w_ssim, ssum, partial, TX, TY,
+                                                            (int)n_work);
+        k_ssim_bwd<<<gb, kSsimThreads, kSsimBwdSmem, st>>>(img, tgt, cams, g, w_l1, partial, grad, loss, TX, TY,
+                                                            (int)n_work);
         note_launch(2);
     }
     k_loss_final<<<(plan.n_views + 127) / 128, 128, 0, st>>>(cams, plan.n_views, w_l1, w_ssim, ssum, loss);
