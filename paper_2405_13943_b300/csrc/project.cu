@@ -128,6 +128,18 @@ struct Geom {
     float mx, my;
 };
 
+// The lateral frustum test of geom() on the mean alone (the same expressions,
+// so the same decisions), taken before the rest of a copy's parameters load.
+__device__ __forceinline__ bool in_frustum(const CamL& cam, double tzd, float3 mu)
+{
+    const float tz = (float)tzd;
+    const float tx = fmaf(cam.R[0], mu.x, fmaf(cam.R[1], mu.y, fmaf(cam.R[2], mu.z, cam.t[0])));
+    const float ty = fmaf(cam.R[3], mu.x, fmaf(cam.R[4], mu.y, fmaf(cam.R[5], mu.z, cam.t[1])));
+    const float xn = tx / tz, yn = ty / tz;
+    const float limx = 0.65f * (float)cam.W / cam.fx, limy = 0.65f * (float)cam.H / cam.fy;
+    return !(fabsf(xn) > limx || fabsf(yn) > limy);
+}
+
 // Computes every field; returns false if the Gaussian is culled in this
 // view.  The caller has already checked camera z > near_z (exact, in double),
 // so no division below is by a non-positive depth.  Fills rect if non-null.
@@ -217,8 +229,8 @@ __global__ void __launch_bounds__(256, 4) k_project(GView x, const dg_camera* __
         load_cam(cams, v, cam);
         int64_t r = cam.rec_off + (c - cam.gb);
         double tzd = cam_depth(cam, mu);
-        if (!(tzd > (double)cam.nearz)) { rect[r] = make_uint2(0, 0); continue; }
-        if (!loaded) {   // the rest of the parameters only for copies in front of some camera
+        if (!(tzd > (double)cam.nearz) || !in_frustum(cam, tzd, mu)) { rect[r] = make_uint2(0, 0); continue; }
+        if (!loaded) {   // the rest of the parameters only for copies inside some camera's frustum
             q = x.quat[c];
             sc = x.scale[c];
             opac = 1.f / (1.f + __expf(-mo.w));
