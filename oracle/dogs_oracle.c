@@ -418,7 +418,7 @@ static int composite_pixel_seen(int px, int py, const uint32_t* vals, uint32_t b
         const double* g = rec + (int64_t)vals[j] * REC_N;
         double dx = g[REC_MX] - (px + 0.5), dy = g[REC_MY] - (py + 0.5);
         double power = -0.5 * (g[REC_A] * dx * dx + g[REC_C] * dy * dy) - g[REC_B] * dx * dy;
-        if (power > 0.0) continue;
+        if (power > 0.0) power = 0.0;   /* positive-definite conic: only rounding makes it positive */
         double G = exp(power);
         double ar = g[REC_OP] * G;
         double alpha = ar < ALPHA_MAX ? ar : ALPHA_MAX;

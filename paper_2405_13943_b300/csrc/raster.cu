@@ -64,52 +64,41 @@ __device__ __forceinline__ LaneGeom lane_geom(const TileInfo& ti, int tw, int ti
     return L;
 }
 
-// The exponent (log2 units) of one instance along a thread's strip of PPL
-// pixels (fixed column, rows fy0 + k dy): p(k) = p0 + beta k + gamma k^2 with
-// dx = mx - fx, dy_k = my - fy0 - k dy.  Each p(k) is evaluated on its own
-// as p0 + k (beta + gamma k) (two fused multiply-adds, no chain across the
-// strip; the forward and the backward use the same instructions, so both
-// take the same decisions), and the strip's largest value bounds every
-// pixel of it: when even that gives alpha < 2^-8 the whole strip skips the
-// instance.
+// The exponent (log2 units) of one instance at pixel k of a thread's strip
+// (fixed column fx, rows fy0 + k dy): p = dx (A dx + B dy_k) + C dy_k^2 with
+// dx = mx - fx and dy_k = (my - fy0) - k dy, evaluated directly for every
+// pixel (no expansion from the strip's first pixel, whose large terms would
+// cancel near the Gaussian's centre).  The conic is positive definite, so p
+// is never positive in exact arithmetic; a positive value is rounding and is
+// taken as 0.  The forward and the backward use the same instructions, so
+// both take the same decisions.
 struct Strip {
-    float p0, beta, gamma, pmax;
+    float dx, Adx, B, C, dy0, ddy;
 };
 
 __device__ __forceinline__ float strip_p(const Strip& s, int k)
 {
-    return __fmaf_rn(__fmaf_rn(s.gamma, (float)k, s.beta), (float)k, s.p0);
+    const float dy = __fmaf_rn(-(float)k, s.ddy, s.dy0);
+    const float t = __fmaf_rn(s.B, dy, s.Adx);
+    return fminf(__fmaf_rn(__fmul_rn(s.C, dy), dy, __fmul_rn(s.dx, t)), 0.0f);
 }
 
-// BOUND = false skips the strip bound (pmax is left unset): the per-pixel
-// reach tests decide alone, the bound only ever skipped pixels they reject.
-template <int PPL, bool BOUND = true>
+template <int PPL>
 __device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float B, float C, float fx, float fy0,
                                              float ddy)
 {
     Strip st;
-    const float dx = __fsub_rn(mx, fx), dy0 = __fsub_rn(my, fy0);
-    const float t = __fmaf_rn(B, dy0, __fmul_rn(A, dx));
-    st.p0 = __fmaf_rn(__fmul_rn(C, dy0), dy0, __fmul_rn(dx, t));
-    st.beta = __fmul_rn(-ddy, __fmaf_rn(2.f * C, dy0, __fmul_rn(B, dx)));
-    st.gamma = __fmul_rn(C, __fmul_rn(ddy, ddy));
-    if (!BOUND) {
-        st.pmax = 0.f;
-    } else if (PPL == 1) {
-        st.pmax = st.p0;
-    } else {
-        // concave in k (gamma < 0): largest at the vertex, clamped to [0, PPL-1]
-        const float beta = st.beta, gamma = st.gamma;
-        float ks = gamma < 0.f ? fminf(fmaxf(__fdividef(-beta, 2.f * gamma), 0.f), (float)(PPL - 1)) : 0.f;
-        float pv = st.p0 + ks * (beta + gamma * ks);
-        float pe = st.p0 + (float)(PPL - 1) * (beta + gamma * (float)(PPL - 1));
-        st.pmax = fmaxf(fmaxf(pv, pe), st.p0) + 1e-3f;   // margin over rounding
-    }
+    st.dx = __fsub_rn(mx, fx);
+    st.Adx = __fmul_rn(A, st.dx);
+    st.B = B;
+    st.C = C;
+    st.dy0 = __fsub_rn(my, fy0);
+    st.ddy = ddy;
     return st;
 }
 
-// Pixels of the strip that pass the first two tests of a pair: exponent
-// p <= 0 and alpha bound 2^(p + log2 o) >= 2^-8 (below that alpha < 1/255).
+// Pixels of the strip that pass the first test of a pair: alpha bound
+// 2^(p + log2 o) >= 2^-8 (below that alpha < 1/255).
 // Evaluated for the whole strip without branches; only the pixels left in
 // the mask take the exponential and the exact 1/255 test (strip_alpha).
 template <int PPL>
@@ -118,8 +107,7 @@ __device__ __forceinline__ uint32_t strip_reach(const Strip& sp, float lo)
     uint32_t m = 0;
 #pragma unroll
     for (int k = 0; k < PPL; k++) {
-        const float p = strip_p(sp, k);
-        m |= (uint32_t)((p <= 0.0f) & (__fadd_rn(p, lo) >= -8.0f)) << k;
+        m |= (uint32_t)(__fadd_rn(strip_p(sp, k), lo) >= -8.0f) << k;
     }
     return m;
 }
@@ -217,7 +205,7 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
             const float4 g = s_g[j];
             const float2 h = s_h[j];
             if (CNT) n_seen += __popc(live);
-            const Strip sp = strip_setup<PPL, false>(g.x, g.y, g.z, g.w, h.x, G.fx, G.fy0, G.dy);
+            const Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, G.fx, G.fy0, G.dy);
             const float4 c = s_c[j];
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
@@ -225,7 +213,7 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
                 // the reach tests of strip_reach, taken pixel by pixel (the
                 // forward often stops early, so a mask up front would not pay)
                 const float p = strip_p(sp, k);
-                if (!(p <= 0.0f) || !(__fadd_rn(p, h.y) >= -8.0f)) continue;
+                if (!(__fadd_rn(p, h.y) >= -8.0f)) continue;
                 float raw;
                 const float a = strip_alpha(p, h.y, raw);
                 if (a == 0.f) continue;
@@ -401,7 +389,7 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             }
             const float4 g = s_g[j];
             const float4 h = s_h[j];
-            const Strip sp = strip_setup<PPL, false>(g.x, g.y, g.z, g.w, h.x, Lg.fx, Lg.fy0, Lg.dy);
+            const Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, Lg.fx, Lg.fy0, Lg.dy);
             const uint32_t todo = joined & strip_reach<PPL>(sp, h.y);
             if (!__any_sync(0xffffffffu, todo != 0u)) continue;
             const float4 c = s_c[j];
