@@ -151,3 +151,69 @@ def test_full_size_fused_xstep_matches_oracle(full):
             w = np.asarray(want[name], np.float64)[ok]
             r = np.linalg.norm(a - w) / max(np.linalg.norm(w), 1e-30)
             assert r <= 1e-3, (v, name, r)
+
+
+def test_full_size_consensus_sampled(full):
+    """The consensus over all 6.63M copies (over-relaxed, alpha = 1.6), with
+    perturbed copies and duals on the shared ones; 3,000 sampled globals
+    (shared and unshared) are recomputed by the oracle from their copies
+    alone: z, and u and the anchor of each of their copies."""
+    O, D, wl, z0, x, vb = full
+    sp = wl.split
+    n_c = sp.n_copies
+    rng = np.random.default_rng(12)
+    xs = x.clone()
+    xs.data.add_(torch.randn(xs.data.numel(), device="cuda", generator=torch.Generator("cuda").manual_seed(3)) * 0.01)
+    shared = torch.from_numpy(sp.copy_shared()).cuda()
+    u = x.like()
+    u.data.copy_(torch.randn(u.data.numel(), device="cuda", generator=torch.Generator("cuda").manual_seed(4)) * 0.01)
+    keep = np.zeros(n_c, np.float32)
+    keep[sp.copy_shared().astype(bool)] = 1.0
+    # duals live on shared copies only
+    ug = u.to_synth()
+    for name in ("means", "quats", "log_scales", "opacity_logits", "sh"):
+        arr = getattr(ug, name)
+        arr *= keep.reshape((-1,) + (1,) * (arr.ndim - 1))
+    u = D.GaussianBuffer.from_synth(ug, ld=x.ld)
+    u_in, x_in = u.to_synth(), xs.to_synth()
+    z = D.GaussianBuffer.from_synth(wl.z0)
+    an = x.like()
+    g_off = torch.from_numpy(sp.g_off.astype(np.int64)).cuda()
+    g_cp = torch.from_numpy(sp.g_copies.astype(np.int32)).cuda()
+    rho = [1e-3] * 5
+    D.dg_admm_consensus(xs, u, z, an, g_off, g_cp, rho, 1.6)
+    torch.cuda.synchronize()
+    zg, ug2, ag = z.to_synth(), u.to_synth(), an.to_synth()
+    ns = int(sp.n_shared_globals)
+    sample = np.concatenate([rng.choice(ns, 2000, replace=False),
+                             ns + rng.choice(wl.z0.n - ns, 1000, replace=False)])
+    # the sampled globals as a small problem of their own
+    offs, cps = [0], []
+    for g in sample:
+        c = sp.g_copies[sp.g_off[g]:sp.g_off[g + 1]]
+        cps.extend(c.tolist())
+        offs.append(len(cps))
+    cps = np.array(cps, np.int64)
+    sub = lambda gs, idx: S.Gaussians(gs.means[idx], gs.quats[idx], gs.log_scales[idx],
+                                      gs.opacity_logits[idx], gs.sh[idx])
+    ox = O.params_from(sub(x_in, cps))
+    ou = O.params_from(sub(u_in, cps))
+    oz = O.params_from(wl.z0.subset(sample))
+    O.consensus(ox, ou, oz, np.array(offs, np.int64), np.arange(len(cps), dtype=np.int32), 3, alpha=1.6, rho=rho)
+    got_z = O.params_from(sub(zg, sample))
+    got_u = O.params_from(sub(ug2, cps))
+    got_a = O.params_from(sub(ag, cps))
+    sh_c = sp.copy_shared()[cps].astype(bool)
+    zc = oz[np.repeat(np.arange(len(sample)), np.diff(offs))]
+    d = np.linalg.norm(got_z - oz) / np.linalg.norm(oz)
+    assert d <= 1e-5, d
+    # u = u + x_hat - z and the anchor z - u per group.  Positions are ~1e3 m
+    # while u is ~1e-2, so their FP32 error is bounded by a few ulps of the
+    # coordinates (absolute), the other groups by the 1e-3 relative L2 bar.
+    ulp_x = 2.0 ** -23 * np.abs(ox[:, 0:3]).max()
+    for got, want in ((got_u, ou), (got_a, zc - ou)):
+        gg, ww = O.split_params(got[sh_c], 3), O.split_params(want[sh_c], 3)
+        assert np.abs(gg["mean"] - ww["mean"]).max() <= 8 * ulp_x
+        for name in ("quat", "scale", "sh", "opacity"):
+            r = np.linalg.norm(gg[name] - ww[name]) / max(np.linalg.norm(ww[name]), 1e-30)
+            assert r <= 1e-3, (name, r)
