@@ -293,10 +293,9 @@ def run_ours(args, dist, rank, world):
     pairs = 0.0
     for i in range(n_eager):
         p = tr.t % len(tr.view_sets)
-        tr.host_step[0] = tr.t + 1
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         vb.dev_cams.copy_(tr.cam_pool[p], non_blocking=True)
-        tr.dev_step.copy_(tr.host_step, non_blocking=True)
+        tr.dev_step.add_(1)
         ev[0].record()
         D.dg_project(tr.x, vb); ev[1].record()
         D.dg_bin_sort(vb); ev[2].record()
@@ -442,62 +441,32 @@ def run_ours(args, dist, rank, world):
 
 
 def run_e2e(tr, args, dist):
-    """Same iterations through host buffers: every step copies its target
-    images and camera table from pinned host memory and the step counter in,
-    and reads the per-view losses back, all inside the timed region."""
+    """Same iterations through the trainer with its targets in pinned host
+    memory: every step's target images cross host -> device (copied one step
+    ahead on a side stream while the previous step computes) and every step's
+    per-view losses are read back on the host, all inside the timed region."""
     import torch
-    from paper_2405_13943_b300 import dogs as D
-    vb = tr.vb
-    pool = len(tr.view_sets)
     host_t = [t.cpu().pin_memory() for t in tr.targets]
-    host_c = [c.cpu().pin_memory() for c in tr.cam_pool]
-    stage = torch.empty_like(tr.targets[0])
-    host_loss = torch.empty(vb.loss.numel(), dtype=torch.float64).pin_memory()
-    graphs = {}
-
-    def capture(p):
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            stage.copy_(host_t[p], non_blocking=True)
-            vb.dev_cams.copy_(host_c[p], non_blocking=True)
-            tr.dev_step.copy_(tr.host_step, non_blocking=True)
-            D.dg_project(tr.x, vb)
-            D.dg_bin_sort(vb)
-            D.dg_rasterize_fwd(vb, tr.bg)
-            tr._loss(stage)
-            tr.backward_step()
-            D.dg_admm_consensus(tr.x, tr.u, tr.z, tr.anchor, tr.g_off, tr.g_copies, tr.rho, tr.alpha,
-                                tr.residuals)
-            host_loss.copy_(vb.loss, non_blocking=True)
-        return g
-
-    for p in range(pool):
-        graphs[p] = capture(p)
-    for i in range(2):
-        tr.host_step[0] = tr.t + 1
-        graphs[tr.t % pool].replay()
-        tr.t += 1
+    tr.use_host_targets(host_t)
+    for _ in range(2):
+        tr.step(consensus=True)
+        tr.last_loss()
     torch.cuda.synchronize()
     barrier(dist)
     t0 = time.perf_counter()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
     losses = []
-    for i in range(args.steps):
-        tr.host_step[0] = tr.t + 1
-        graphs[tr.t % pool].replay()
-        tr.t += 1
-        torch.cuda.current_stream().synchronize()      # the step's losses are on the host
-        losses.append(float(host_loss.sum()))
-    e1.record()
+    for _ in range(args.steps):
+        tr.step(consensus=True)
+        losses.append(float(tr.last_loss().sum()))    # the step's losses are on the host
     torch.cuda.synchronize()
     wall = (time.perf_counter() - t0) / args.steps
     ms = max_over_ranks(dist, wall * 1e3)
     world = 1 if dist is None else dist.get_world_size()
     return {"value": round(world * 1e3 / ms, 4), "unit": "iter/s", "ms_per_step": round(ms, 3),
-            "h2d_bytes_per_step": int(stage.numel() * 4 + host_c[0].numel() + 4),
-            "d2h_bytes_per_step": int(host_loss.numel() * 8), "loss_last": losses[-1],
-            "timing": "host wall clock per step, each step synchronised for its loss read-back"}
+            "h2d_bytes_per_step": tr.h2d_bytes_per_step(), "d2h_bytes_per_step": int(tr.host_loss.numel() * 8),
+            "loss_last": losses[-1],
+            "timing": "host wall clock per step; each step's target uploaded from pinned host memory one step "
+                      "ahead on a copy stream, each step synchronised for its loss read-back"}
 
 
 def run_serving(z, args, tile):

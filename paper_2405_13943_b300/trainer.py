@@ -67,11 +67,13 @@ class DogsTrainer:
                               capacity=capacity, loss_ws=(loss == "dssim"))
         self.cam_pool = [D.cams_to_device(D.plan_views(vs, split.blk_off, *tile)[0], device) for vs in self.view_sets]
         self.targets = list(targets)
+        # Adam's step counter lives on the device and each iteration advances
+        # it there, so replays queued back to back each see their own count
         self.dev_step = torch.zeros(1, dtype=torch.int32, device=device)
-        self.host_step = torch.zeros(1, dtype=torch.int32).pin_memory()
         self.residuals = torch.zeros(10, dtype=torch.float64, device=device)
         self.t = 0
         self.graphs = {}
+        self.host_targets = None
 
     # ---- rasteriser configuration (autotuner) ------------------------------------
     def set_tile(self, tile) -> None:
@@ -120,10 +122,11 @@ class DogsTrainer:
 
     def enqueue(self, p: int, consensus: bool, target: Optional[torch.Tensor] = None) -> None:
         """All launches of one iteration for pool entry p on the current stream.
-        The step counter for Adam's bias correction is read from dev_step."""
+        The step counter for Adam's bias correction (dev_step) is advanced
+        on the device first."""
         vb = self.vb
         vb.dev_cams.copy_(self.cam_pool[p], non_blocking=True)
-        self.dev_step.copy_(self.host_step, non_blocking=True)
+        self.dev_step.add_(1)
         D.dg_project(self.x, vb)
         D.dg_bin_sort(vb)
         D.dg_rasterize_fwd(vb, self.bg)
@@ -132,6 +135,41 @@ class DogsTrainer:
         if consensus:
             D.dg_admm_consensus(self.x, self.u, self.z, self.anchor, self.g_off, self.g_copies, self.rho,
                                 self.alpha, self.residuals)
+        if self.host_targets is not None:
+            self.host_loss.copy_(vb.loss, non_blocking=True)
+
+    # ---- targets in host memory ----------------------------------------------------
+    def use_host_targets(self, host_targets: Sequence[torch.Tensor]) -> None:
+        """Keep the pool's target images in pinned host memory.  Each step's
+        target is copied in on a side stream one step ahead, into one of two
+        device buffers, while the previous step computes; every step also
+        copies its per-view losses back (read them with last_loss())."""
+        self.host_targets = [t if t.is_pinned() else t.pin_memory() for t in host_targets]
+        self.stage = [torch.empty(self.host_targets[0].shape, dtype=self.host_targets[0].dtype, device=self.device)
+                      for _ in range(2)]
+        self.host_loss = torch.zeros(self.vb.loss.numel(), dtype=torch.float64).pin_memory()
+        self.copy_stream = torch.cuda.Stream()
+        self.copied = [torch.cuda.Event() for _ in range(2)]
+        self.used = [torch.cuda.Event() for _ in range(2)]
+        self.slot_entry = [None, None]
+        self.graphs.clear()
+        self._prefetch(self.t % len(self.view_sets), self.t % 2)
+
+    def _prefetch(self, p: int, slot: int) -> None:
+        self.copy_stream.wait_event(self.used[slot])           # the step that last read this buffer
+        with torch.cuda.stream(self.copy_stream):
+            self.stage[slot].copy_(self.host_targets[p], non_blocking=True)
+        self.copied[slot].record(self.copy_stream)
+        self.slot_entry[slot] = p
+
+    def h2d_bytes_per_step(self) -> int:
+        t = self.host_targets[0]
+        return int(t.numel() * t.element_size())
+
+    def last_loss(self) -> torch.Tensor:
+        """The per-view losses of the last step (waits for it)."""
+        torch.cuda.current_stream().synchronize()
+        return self.host_loss.clone()
 
     def backward_step(self) -> None:
         """Adjoint of the iteration's render and the x-step (Eq. 8a / 12a).
@@ -153,14 +191,24 @@ class DogsTrainer:
         when t mod intv == 0 (or as forced by `consensus`)."""
         p = self.t % len(self.view_sets)
         c = (self.t % self.intv == 0) if consensus is None else consensus
-        self.host_step[0] = self.t + 1
+        slot, target = None, None
+        if self.host_targets is not None:
+            slot = self.t % 2
+            if self.slot_entry[slot] != p:
+                self._prefetch(p, slot)
+            torch.cuda.current_stream().wait_event(self.copied[slot])
+            target = self.stage[slot]
         if graph:
-            key = (p, c)
+            key = (p, c, slot)
             if key not in self.graphs:
-                self.graphs[key] = self._capture(p, c)
+                self.graphs[key] = self._capture(p, c, target)
             self.graphs[key].replay()
         else:
-            self.enqueue(p, c)
+            self.enqueue(p, c, target)
+        if slot is not None:
+            self.used[slot].record(torch.cuda.current_stream())
+            nxt = self.t + 1
+            self._prefetch(nxt % len(self.view_sets), nxt % 2)
         if c and self.adaptive is not None and self.t < self.adaptive.freeze_after:
             self._adapt_penalty()
         self.t += 1
@@ -179,14 +227,14 @@ class DogsTrainer:
         self.rho = rho
         self.graphs.clear()
 
-    def _capture(self, p: int, c: bool) -> torch.cuda.CUDAGraph:
+    def _capture(self, p: int, c: bool, target: Optional[torch.Tensor] = None) -> torch.cuda.CUDAGraph:
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):       # warm the allocator-free launch path once
             torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            self.enqueue(p, c)
+            self.enqueue(p, c, target)
         return g
 
     def overflowed(self) -> bool:
@@ -194,8 +242,10 @@ class DogsTrainer:
 
     # ---- checkpoint / resume ------------------------------------------------------
     def refresh_anchor(self) -> None:
-        """Anchors z - u of the shared copies from the current z and u."""
+        """Anchors z - u of the shared copies from the current z and u (and
+        the device step counter from t, after t was set from outside)."""
         D.dg_admm_anchor(self.z, self.u, self.gid, self.shared, self.anchor)
+        self.dev_step.fill_(self.t)
         torch.cuda.synchronize()
 
     def save_checkpoint(self, path: str) -> None:

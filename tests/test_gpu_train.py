@@ -262,3 +262,27 @@ def test_fused_xstep_equals_separate_calls(mods):
             for k in ga:
                 assert rel_l2(gb[k], ga[k]) < REL_L2, (n, k)
     assert not a.overflowed()
+
+
+def test_host_targets_equal_device_targets(mods):
+    """Targets kept in pinned host memory and uploaded one step ahead give
+    the same iterations as device-resident targets (graph replays queued
+    back to back, the step counter advanced on the device)."""
+    D, srv, T = mods
+    wl, z0, targets = small_setup(D, srv, seed=19)
+    kw = dict(rho=(1e-2,) * 5, loss="l1", intv=2)
+    a = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, **kw)
+    a.calibrate_capacity()
+    b = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, **kw)
+    b.calibrate_capacity()
+    b.use_host_targets([t.cpu() for t in targets])
+    for _ in range(5):
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    assert int(a.dev_step.item()) == int(b.dev_step.item()) == 5
+    np.testing.assert_allclose(b.last_loss().numpy(), a.vb.loss.cpu().numpy(), rtol=1e-3)
+    for n in ("x", "z"):
+        ga, gb = groups(getattr(a, n)), groups(getattr(b, n))
+        for k in ga:
+            assert rel_l2(gb[k], ga[k]) < REL_L2, (n, k)
