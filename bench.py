@@ -295,7 +295,7 @@ def run_ours(args, dist, rank, world):
         p = tr.t % len(tr.view_sets)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         vb.dev_cams.copy_(tr.cam_pool[p], non_blocking=True)
-        tr.dev_step.add_(1)
+        D.dg_step_advance(tr.dev_step)
         ev[0].record()
         D.dg_project(tr.x, vb); ev[1].record()
         D.dg_bin_sort(vb); ev[2].record()

@@ -285,6 +285,12 @@ int dg_admm_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z,
                       dg_gaussians* anchor, const int64_t* g_off, const int32_t* g_copies,
                       const float* rho, float alpha, double* residuals, void* stream);
 
+/* Adds 1 to the device step counter *dev_step (int32, 4-byte aligned) on the
+ * stream: the x-step calls read their Adam step from it, so an iteration
+ * that advances it on the device before its x-step can be replayed from a
+ * graph, back to back, with each replay seeing its own count. */
+int dg_step_advance(int32_t* dev_step, void* stream);
+
 /* Adaptive penalty (Sec. 3.3, Eq. 10): when rho_grp changes to rho'_grp the
  * scaled duals u = y / rho follow as u_grp *= rho_grp / rho'_grp.  This call
  * multiplies each group of u on shared copies by factor[5] (host); rerun

@@ -97,6 +97,17 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam_planes(float4* __restrict
     }
 }
 
+// ---- the x-step's step counter ----------------------------------------------------------
+__global__ void k_step_advance(int32_t* __restrict__ dev_step) { *dev_step += 1; }
+
+int launch_step_advance(int32_t* dev_step, cudaStream_t st)
+{
+    k_step_advance<<<1, 1, 0, st>>>(dev_step);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
 // ---- consensus ---------------------------------------------------------------------
 struct ConsArgs {
     float rho[5];

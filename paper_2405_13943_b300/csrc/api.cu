@@ -35,6 +35,7 @@ int launch_consensus(const dg_gaussians*, dg_gaussians*, dg_gaussians*, dg_gauss
 int launch_anchor(const dg_gaussians*, const dg_gaussians*, const int32_t*, const uint8_t*, dg_gaussians*,
                   cudaStream_t);
 int launch_scale_duals(dg_gaussians*, const uint8_t*, const float*, cudaStream_t);
+int launch_step_advance(int32_t*, cudaStream_t);
 int launch_xstep(dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*, const uint8_t*, const dg_camera*,
                  const dg_plan&, const uint2*, const float4*, const AdamArgs&, const int32_t*, cudaStream_t);
 
@@ -334,6 +335,12 @@ int dg_admm_anchor(const dg_gaussians* z, const dg_gaussians* u, const int32_t* 
     if (u->n > 0 && (!copy_gid || !copy_shared)) return DG_ERR_INVALID;
     if ((uintptr_t)copy_gid & 3u) return DG_ERR_INVALID;
     return launch_anchor(z, u, copy_gid, copy_shared, anchor, (cudaStream_t)stream);
+}
+
+int dg_step_advance(int32_t* dev_step, void* stream)
+{
+    if (!dev_step || ((uintptr_t)dev_step & 3u)) return DG_ERR_INVALID;
+    return launch_step_advance(dev_step, (cudaStream_t)stream);
 }
 
 int dg_admm_scale_duals(dg_gaussians* u, const uint8_t* copy_shared, const float* factor, void* stream)

@@ -459,8 +459,8 @@ __global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView
                                                         const int32_t* __restrict__ dev_step)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
-    __shared__ float s_gc[3][kXsThreads];
-    __shared__ float s_Y[NK][kXsThreads];
+    __shared__ __align__(16) float s_gc[3][kXsThreads];
+    __shared__ __align__(16) float s_Y[NK][kXsThreads];
     const int tid = threadIdx.x;
     const int64_t c0 = (int64_t)blockIdx.x * kXsThreads, c = c0 + tid;
     float ic1, ic2;
@@ -582,13 +582,17 @@ __global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView
             const int j = j0 + b * G;
             if (j >= 3 * NK) break;
             const float lr = j < 3 ? a.lr[3] : a.lr[4];
+            // the quad's four colour gradients and basis values, one 16-byte load each
+            const float4 gc4 = *reinterpret_cast<const float4*>(&s_gc[j % 3][4 * quad]);
+            const float4 y4 = *reinterpret_cast<const float4*>(&s_Y[j / 3][4 * quad]);
+            const float gq4[4] = {gc4.x * y4.x, gc4.y * y4.y, gc4.z * y4.z, gc4.w * y4.w};
             float xs[4] = {xv[b].x, xv[b].y, xv[b].z, xv[b].w}, ms[4] = {mv[b].x, mv[b].y, mv[b].z, mv[b].w};
             float vs[4] = {vv[b].x, vv[b].y, vv[b].z, vv[b].w};
             const float as[4] = {av[b].x, av[b].y, av[b].z, av[b].w};
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 if (!act[i]) continue;
-                float g = s_gc[j % 3][4 * quad + i] * s_Y[j / 3][4 * quad + i];
+                float g = gq4[i];
                 if (sh[i]) g += a.rho[3] * (xs[i] - as[i]);
                 adam_scalar(xs[i], g, ms[i], vs[i], lr, a.b1, a.b2, a.eps, ic1, ic2);
             }

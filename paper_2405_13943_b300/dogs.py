@@ -286,6 +286,10 @@ def dg_backward_xstep(vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer, v: Ga
     dg_xstep_from_records(vb, x, m, v, anchor, shared, rho, lr, beta1, beta2, eps, step, dev_step, stream)
 
 
+def dg_step_advance(dev_step: torch.Tensor, stream=None) -> None:
+    L.check(L.lib().dg_step_advance(L.ptr(dev_step), L.stream_handle(stream)), "dg_step_advance")
+
+
 def one_view_per_block(plan) -> bool:
     return all(plan.blk_view_off[k + 1] - plan.blk_view_off[k] <= 1 for k in range(plan.n_blocks))
 

@@ -126,7 +126,7 @@ class DogsTrainer:
         on the device first."""
         vb = self.vb
         vb.dev_cams.copy_(self.cam_pool[p], non_blocking=True)
-        self.dev_step.add_(1)
+        D.dg_step_advance(self.dev_step)
         D.dg_project(self.x, vb)
         D.dg_bin_sort(vb)
         D.dg_rasterize_fwd(vb, self.bg)
