@@ -477,13 +477,14 @@ def run_serving(z, args, tile):
     res = [(640, 480), (1280, 720), (1920, 1080), (3840, 2160)]
     cams = S.random_pose_cameras(1006, len(arr), res, [0.4, 0.3, 0.2, 0.1])
     srv = serve.RenderServer(z, budget_bytes=20e9, tile=tile)
-    # warm the path on a few requests
-    serve.render_views(z, cams[:4], tile=tile)
+    # warm the path and size the instance capacity on sample poses of the
+    # same law (not the requests themselves)
+    ipp = srv.calibrate(S.random_pose_cameras(1007, 16, res, [0.4, 0.3, 0.2, 0.1]))
     out = srv.run(cams, arr)
     return {"p50_ms": round(out["p50_ms"], 3), "p99_ms": round(out["p99_ms"], 3),
             "views_per_s": round(out["views_per_s"], 2), "requests": out["requests"], "rate_hz": rate,
             "duration_s": args.serve_seconds, "budget_gb": 20, "max_inflight_batches": out["max_inflight_batches"],
-            "capacity_retries": out["capacity_retries"],
+            "capacity_retries": out["capacity_retries"], "instances_per_pixel_capacity": round(ipp, 3),
             "mix": "640x480/1280x720/1920x1080/3840x2160 at 0.4/0.3/0.2/0.1, Poisson 200/s"}
 
 

@@ -75,8 +75,24 @@ class RenderServer:
                  tile=(16, 16), bg=(0.0, 0.0, 0.0), inst_per_pixel: float = 2.0):
         self.z, self.budget, self.max_batch, self.tile, self.bg = z, budget_bytes, max_batch, tile, bg
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
-        self.host_bufs: List[Optional[torch.Tensor]] = [None] * n_streams
+        # pinned staging for each slot's images, allocated up front for two
+        # 3840x2160 views (a pinned allocation of this size takes tens of
+        # milliseconds; a larger batch grows its slot's buffer once)
+        self.host_bufs: List[Optional[torch.Tensor]] = [
+            torch.empty(2 * 3 * 3840 * 2160, dtype=torch.float32, pin_memory=True) for _ in range(n_streams)]
         self.inst_per_pixel = inst_per_pixel
+
+    def calibrate(self, cams: Sequence[S.Camera], margin: float = 1.25) -> float:
+        """Set the instance capacity per pixel from sample views of the model
+        (margin x the largest instances-per-pixel ratio among them), so that
+        serving rarely has to re-render a batch whose binning overflowed."""
+        worst = 0.0
+        for c in cams:
+            rb = render_views(self.z, [c], tile=self.tile, bg=self.bg)
+            m = int(rb.count.item()) & 0xFFFFFFFF
+            worst = max(worst, m / float(c.width * c.height))
+        self.inst_per_pixel = max(self.inst_per_pixel, margin * worst)
+        return self.inst_per_pixel
 
     def _est_bytes(self, cams) -> int:
         npix = sum(c.width * c.height for c in cams)
@@ -171,7 +187,7 @@ class RenderServer:
         need = rb.image.numel()
         hb = self.host_bufs[slot]
         if hb is None or hb.numel() < need:
-            hb = torch.empty(max(need, 3 * 3840 * 2160), dtype=torch.float32, pin_memory=True)
+            hb = torch.empty(max(need, 2 * 3 * 3840 * 2160), dtype=torch.float32, pin_memory=True)
             self.host_bufs[slot] = hb
         with torch.cuda.stream(s):
             rb.launch(s)

@@ -39,7 +39,11 @@ def test_server_completes_requests(mods):
     z = D.GaussianBuffer.from_synth(S.city_scene(100_000, 6))
     arr = S.poisson_arrivals(3, 100.0, 1.0)
     cams = S.random_pose_cameras(4, len(arr), [(320, 240), (640, 480)], [0.5, 0.5])
-    out = srv.RenderServer(z, budget_bytes=2e9, max_batch=4, n_streams=3).run(cams, arr)
+    server = srv.RenderServer(z, budget_bytes=2e9, max_batch=4, n_streams=3)
+    sample = S.random_pose_cameras(5, 4, [(320, 240), (640, 480)], [0.5, 0.5])
+    ipp = server.calibrate(sample)
+    assert ipp >= 2.0
+    out = server.run(cams, arr)
     lat = out["latency_s"]
     assert np.all(np.isfinite(lat)) and np.all(lat > 0)
     assert out["requests"] == len(arr)
