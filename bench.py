@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "medium", "small"])
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-seq", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -479,7 +479,7 @@ def run_serving(z, args, tile):
     srv = serve.RenderServer(z, budget_bytes=20e9, tile=tile)
     # warm the path and size the instance capacity on sample poses of the
     # same law (not the requests themselves)
-    ipp = srv.calibrate(S.random_pose_cameras(1007, 16, res, [0.4, 0.3, 0.2, 0.1]))
+    ipp = srv.calibrate(S.random_pose_cameras(1007, 64, res, [0.4, 0.3, 0.2, 0.1]))
     out = srv.run(cams, arr)
     return {"p50_ms": round(out["p50_ms"], 3), "p99_ms": round(out["p99_ms"], 3),
             "views_per_s": round(out["views_per_s"], 2), "requests": out["requests"], "rate_hz": rate,

@@ -72,14 +72,17 @@ def render_views(z: D.GaussianBuffer, cams: Sequence[S.Camera], capacity: Option
 
 class RenderServer:
     def __init__(self, z: D.GaussianBuffer, budget_bytes: float = 20e9, max_batch: int = 8, n_streams: int = 4,
-                 tile=(16, 16), bg=(0.0, 0.0, 0.0), inst_per_pixel: float = 2.0):
+                 tile=(16, 16), bg=(0.0, 0.0, 0.0), inst_per_pixel: float = 2.0,
+                 max_batch_pixels: int = 2 * 3840 * 2160):
         self.z, self.budget, self.max_batch, self.tile, self.bg = z, budget_bytes, max_batch, tile, bg
+        self.max_batch_pixels = int(max_batch_pixels)
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
-        # pinned staging for each slot's images, allocated up front for two
-        # 3840x2160 views (a pinned allocation of this size takes tens of
-        # milliseconds; a larger batch grows its slot's buffer once)
+        # pinned staging for each slot's images, allocated once up front: a
+        # pinned allocation of this size takes tens to hundreds of
+        # milliseconds, so batches are admitted only up to max_batch_pixels
+        # (a single request larger than that grows its slot's buffer once)
         self.host_bufs: List[Optional[torch.Tensor]] = [
-            torch.empty(2 * 3 * 3840 * 2160, dtype=torch.float32, pin_memory=True) for _ in range(n_streams)]
+            torch.empty(3 * self.max_batch_pixels, dtype=torch.float32, pin_memory=True) for _ in range(n_streams)]
         self.inst_per_pixel = inst_per_pixel
 
     def calibrate(self, cams: Sequence[S.Camera], margin: float = 1.25) -> float:
@@ -145,7 +148,11 @@ class RenderServer:
             # admit arrived requests into free slots under the HBM budget
             while free and pending and arrivals[pending[0]] <= now:
                 batch = []
+                npix = 0
                 while pending and arrivals[pending[0]] <= now and len(batch) < self.max_batch:
+                    c0 = cams[pending[0]]
+                    if batch and npix + c0.width * c0.height > self.max_batch_pixels:
+                        break
                     cand = batch + [pending[0]]
                     need = self._est_bytes([cams[i] for i in cand])
                     if used + need > self.budget and batch:
@@ -153,6 +160,7 @@ class RenderServer:
                     if used + need > self.budget and inflight:
                         break
                     batch.append(pending.popleft())
+                    npix += c0.width * c0.height
                 if not batch:
                     break
                 bc = [cams[i] for i in batch]
@@ -187,7 +195,7 @@ class RenderServer:
         need = rb.image.numel()
         hb = self.host_bufs[slot]
         if hb is None or hb.numel() < need:
-            hb = torch.empty(max(need, 2 * 3 * 3840 * 2160), dtype=torch.float32, pin_memory=True)
+            hb = torch.empty(max(need, 3 * self.max_batch_pixels), dtype=torch.float32, pin_memory=True)
             self.host_bufs[slot] = hb
         with torch.cuda.stream(s):
             rb.launch(s)

@@ -364,11 +364,31 @@ def block_split(xy: np.ndarray, cols: int, rows: int, loads: Sequence[float],
     return split_layout(xy, member, cells, band)
 
 
+def morton2d(xy: np.ndarray) -> np.ndarray:
+    """Z-order (Morton) code of ground positions: x and y quantised to 16
+    bits each over their bounding box, bits interleaved (x in the even
+    bits)."""
+    xy = np.asarray(xy, np.float64)
+    if xy.shape[0] == 0:
+        return np.zeros(0, np.uint64)
+    lo, hi = xy.min(0), xy.max(0)
+    q = np.clip((xy - lo) / np.maximum(hi - lo, 1e-30) * 65535.0, 0, 65535).astype(np.uint64)
+
+    def spread(v):
+        v = (v | (v << np.uint64(8))) & np.uint64(0x00FF00FF)
+        v = (v | (v << np.uint64(4))) & np.uint64(0x0F0F0F0F)
+        v = (v | (v << np.uint64(2))) & np.uint64(0x33333333)
+        return (v | (v << np.uint64(1))) & np.uint64(0x55555555)
+    return spread(q[:, 0]) | (spread(q[:, 1]) << np.uint64(1))
+
+
 def split_layout(xy: np.ndarray, member: np.ndarray, cells: np.ndarray, band: float) -> tuple:
     """Copy layout of a membership (n, K) bool (every point in at least one
     block).  Returns (BlockSplit, order), `order` mapping new global ids to
     the caller's point indices: shared globals first (by first block, then
-    x, y), then unshared globals block by block."""
+    Z-order of the ground position), then unshared globals block by block
+    in Z-order.  The Z-order keeps the copies one view sees in compact
+    index ranges, so that projection loads and record gathers coalesce."""
     K = member.shape[1]
     n = xy.shape[0]
     if not member.any(1).all():
@@ -376,8 +396,8 @@ def split_layout(xy: np.ndarray, member: np.ndarray, cells: np.ndarray, band: fl
     cnt = member.sum(1)
     shared = cnt >= 2
     first_blk = np.argmax(member, axis=1)
-    # renumber: shared first (sorted by first block, then x, y), unshared by block
-    key_sh = np.lexsort((xy[:, 1], xy[:, 0], first_blk))
+    # renumber: shared first (sorted by first block, then Z-order), unshared by block
+    key_sh = np.lexsort((morton2d(xy), first_blk))
     sh_pts = key_sh[shared[key_sh]]
     un_pts = key_sh[~shared[key_sh]]
     un_pts = un_pts[np.argsort(first_blk[un_pts], kind="stable")]
