@@ -65,22 +65,23 @@ __device__ __forceinline__ LaneGeom lane_geom(const TileInfo& ti, int tw, int ti
 }
 
 // The exponent (log2 units) of one instance at pixel k of a thread's strip
-// (fixed column fx, rows fy0 + k dy): p = dx (A dx + B dy_k) + C dy_k^2 with
-// dx = mx - fx and dy_k = (my - fy0) - k dy, evaluated directly for every
-// pixel (no expansion from the strip's first pixel, whose large terms would
-// cancel near the Gaussian's centre).  The conic is positive definite, so p
-// is never positive in exact arithmetic; a positive value is rounding and is
-// taken as 0.  The forward and the backward use the same instructions, so
-// both take the same decisions.
+// (fixed column fx, rows fy0 + k dy): p = A dx^2 + B dx dy_k + C dy_k^2 with
+// dx = mx - fx and dy_k = (my - fy0) - k dy, evaluated for every pixel from
+// its own dy_k by Horner's rule in dy_k, (C dy_k + B dx) dy_k + A dx^2, the
+// column terms A dx^2 and B dx formed once per instance (no expansion from
+// the strip's first pixel, whose large terms would cancel near the
+// Gaussian's centre).  The conic is positive definite, so p is never
+// positive in exact arithmetic; a positive value is rounding and is taken
+// as 0.  The forward and the backward use the same instructions, so both
+// take the same decisions.
 struct Strip {
-    float dx, Adx, B, C, dy0, ddy;
+    float Adx2, Bdx, C, dy0, ddy;
 };
 
 __device__ __forceinline__ float strip_p(const Strip& s, int k)
 {
     const float dy = __fmaf_rn(-(float)k, s.ddy, s.dy0);
-    const float t = __fmaf_rn(s.B, dy, s.Adx);
-    return fminf(__fmaf_rn(__fmul_rn(s.C, dy), dy, __fmul_rn(s.dx, t)), 0.0f);
+    return fminf(__fmaf_rn(__fmaf_rn(s.C, dy, s.Bdx), dy, s.Adx2), 0.0f);
 }
 
 template <int PPL>
@@ -88,9 +89,9 @@ __device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float 
                                              float ddy)
 {
     Strip st;
-    st.dx = __fsub_rn(mx, fx);
-    st.Adx = __fmul_rn(A, st.dx);
-    st.B = B;
+    const float dx = __fsub_rn(mx, fx);
+    st.Adx2 = __fmul_rn(__fmul_rn(A, dx), dx);
+    st.Bdx = __fmul_rn(B, dx);
     st.C = C;
     st.dy0 = __fsub_rn(my, fy0);
     st.ddy = ddy;
@@ -98,16 +99,21 @@ __device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float 
 }
 
 // Pixels of the strip that pass the first test of a pair: alpha bound
-// 2^(p + log2 o) >= 2^-8 (below that alpha < 1/255).
-// Evaluated for the whole strip without branches; only the pixels left in
-// the mask take the exponential and the exact 1/255 test (strip_alpha).
+// 2^(p + log2 o) >= 2^-8 (below that alpha < 1/255), taken as p >= -8 - log2 o
+// on the unclamped exponent.  Evaluated for the whole strip without
+// branches; it only filters (its rounding can let a pixel through whose
+// alpha is just below 2^-8, never drop one with alpha >= 1/255), and the
+// pixels left in the mask take the exponential and the exact 1/255 test
+// (strip_alpha), the decision the forward takes too.
 template <int PPL>
 __device__ __forceinline__ uint32_t strip_reach(const Strip& sp, float lo)
 {
+    const float thr = __fsub_rn(-8.0f, lo);
     uint32_t m = 0;
 #pragma unroll
     for (int k = 0; k < PPL; k++) {
-        m |= (uint32_t)(__fadd_rn(strip_p(sp, k), lo) >= -8.0f) << k;
+        const float dy = __fmaf_rn(-(float)k, sp.ddy, sp.dy0);
+        m |= (uint32_t)(__fmaf_rn(__fmaf_rn(sp.C, dy, sp.Bdx), dy, sp.Adx2) >= thr) << k;
     }
     return m;
 }
