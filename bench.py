@@ -444,7 +444,8 @@ def run_e2e(tr, args, dist):
     """Same iterations through the trainer with its targets in pinned host
     memory: every step's target images cross host -> device (copied one step
     ahead on a side stream while the previous step computes) and every step's
-    per-view losses are read back on the host, all inside the timed region."""
+    per-view losses are copied back and read on the host (step t's while step
+    t + 1 runs), all inside the timed region."""
     import torch
     host_t = [t.cpu().pin_memory() for t in tr.targets]
     tr.use_host_targets(host_t)
@@ -455,18 +456,22 @@ def run_e2e(tr, args, dist):
     barrier(dist)
     t0 = time.perf_counter()
     losses = []
-    for _ in range(args.steps):
+    tr.step(consensus=True)
+    for _ in range(args.steps - 1):
         tr.step(consensus=True)
-        losses.append(float(tr.last_loss().sum()))    # the step's losses are on the host
+        losses.append(float(tr.loss_of(tr.t - 2).sum()))    # the previous step's losses, on the host
+    losses.append(float(tr.last_loss().sum()))
     torch.cuda.synchronize()
     wall = (time.perf_counter() - t0) / args.steps
     ms = max_over_ranks(dist, wall * 1e3)
     world = 1 if dist is None else dist.get_world_size()
+    assert len(losses) == args.steps
     return {"value": round(world * 1e3 / ms, 4), "unit": "iter/s", "ms_per_step": round(ms, 3),
-            "h2d_bytes_per_step": tr.h2d_bytes_per_step(), "d2h_bytes_per_step": int(tr.host_loss.numel() * 8),
+            "h2d_bytes_per_step": tr.h2d_bytes_per_step(), "d2h_bytes_per_step": int(tr.host_loss[0].numel() * 8),
             "loss_last": losses[-1],
             "timing": "host wall clock per step; each step's target uploaded from pinned host memory one step "
-                      "ahead on a copy stream, each step synchronised for its loss read-back"}
+                      "ahead on a copy stream, each step's losses copied back and read on the host while the "
+                      "next step runs"}
 
 
 def run_serving(z, args, tile):

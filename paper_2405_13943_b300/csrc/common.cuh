@@ -91,27 +91,6 @@ __device__ __forceinline__ Staged stage_geometry(float4 r0, float4 r1)
     return s;
 }
 
-// Returns alpha (> 0) for a composited pair or 0 for a skipped one.  Fixed
-// rounding (no contraction) so that the forward and the backward take
-// identical decisions.  `raw` = opacity * G before the 0.99 clamp.
-__device__ __forceinline__ float pair_alpha(float mx, float my, float A, float B, float C, float lo,
-                                            float px, float py, float& dx, float& dy, float& raw)
-{
-    dx = __fsub_rn(mx, px);
-    dy = __fsub_rn(my, py);
-    float t = __fmul_rn(A, dx);
-    t = __fmaf_rn(B, dy, t);
-    float p = __fmul_rn(dx, t);
-    p = __fmaf_rn(__fmul_rn(C, dy), dy, p);
-    if (p > 0.0f) return 0.0f;
-    float e = __fadd_rn(p, lo);
-    if (e < -8.0f) return 0.0f;   // alpha <= 1/256 < 1/255: skip without the exponential
-    raw = exp2f(e);
-    float a = fminf(raw, kAlphaMax);
-    if (a < kAlphaMin) return 0.0f;
-    return a;
-}
-
 // ---- Adam with the ADMM penalty (Eq. 8a / 12a), shared by the x-step kernels ----
 struct AdamArgs {
     float rho[5];   // groups p, q, s, f, o

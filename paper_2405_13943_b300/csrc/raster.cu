@@ -64,58 +64,41 @@ __device__ __forceinline__ LaneGeom lane_geom(const TileInfo& ti, int tw, int ti
     return L;
 }
 
-// The exponent (log2 units) of one instance at pixel k of a thread's strip
-// (fixed column fx, rows fy0 + k dy): p = A dx^2 + B dx dy_k + C dy_k^2 with
-// dx = mx - fx and dy_k = (my - fy0) - k dy, evaluated for every pixel from
-// its own dy_k by Horner's rule in dy_k, (C dy_k + B dx) dy_k + A dx^2, the
-// column terms A dx^2 and B dx formed once per instance (no expansion from
-// the strip's first pixel, whose large terms would cancel near the
-// Gaussian's centre).  The conic is positive definite, so p is never
-// positive in exact arithmetic; a positive value is rounding and is taken
-// as 0.  The forward and the backward use the same instructions, so both
+// The exponent of alpha (log2 units) of one instance at pixel k of a
+// thread's strip (fixed column fx, rows fy0 + k dy): e = p + log2 o with
+// p = A dx^2 + B dx dy_k + C dy_k^2, dx = mx - fx and dy_k = (my - fy0) - k dy.
+// It is evaluated for every pixel from its own dy_k by Horner's rule in
+// dy_k, q = (C dy_k + B dx) dy_k + (A dx^2 + log2 o), the column terms formed
+// once per instance (no expansion from the strip's first pixel, whose large
+// terms would cancel near the Gaussian's centre).  The conic is positive
+// definite, so p is never positive in exact arithmetic; a positive value is
+// rounding and is taken as 0, i.e. e = min(q, log2 o).  q >= -8 is the
+// first test of a pair (below it alpha <= 2^-8 < 1/255): it only filters,
+// since e <= q and a pixel with alpha >= 1/255 has e > -8.  The forward
+// and the backward evaluate q, e and alpha by the same instructions, so both
 // take the same decisions.
 struct Strip {
-    float Adx2, Bdx, C, dy0, ddy;
+    float E0, Bdx, C, dy0, ddy;
 };
 
-__device__ __forceinline__ float strip_p(const Strip& s, int k)
+__device__ __forceinline__ float strip_q(const Strip& s, int k)
 {
     const float dy = __fmaf_rn(-(float)k, s.ddy, s.dy0);
-    return fminf(__fmaf_rn(__fmaf_rn(s.C, dy, s.Bdx), dy, s.Adx2), 0.0f);
+    return __fmaf_rn(__fmaf_rn(s.C, dy, s.Bdx), dy, s.E0);
 }
 
 template <int PPL>
-__device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float B, float C, float fx, float fy0,
-                                             float ddy)
+__device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float B, float C, float lo, float fx,
+                                             float fy0, float ddy)
 {
     Strip st;
     const float dx = __fsub_rn(mx, fx);
-    st.Adx2 = __fmul_rn(__fmul_rn(A, dx), dx);
+    st.E0 = __fmaf_rn(__fmul_rn(A, dx), dx, lo);
     st.Bdx = __fmul_rn(B, dx);
     st.C = C;
     st.dy0 = __fsub_rn(my, fy0);
     st.ddy = ddy;
     return st;
-}
-
-// Pixels of the strip that pass the first test of a pair: alpha bound
-// 2^(p + log2 o) >= 2^-8 (below that alpha < 1/255), taken as p >= -8 - log2 o
-// on the unclamped exponent.  Evaluated for the whole strip without
-// branches; it only filters (its rounding can let a pixel through whose
-// alpha is just below 2^-8, never drop one with alpha >= 1/255), and the
-// pixels left in the mask take the exponential and the exact 1/255 test
-// (strip_alpha), the decision the forward takes too.
-template <int PPL>
-__device__ __forceinline__ uint32_t strip_reach(const Strip& sp, float lo)
-{
-    const float thr = __fsub_rn(-8.0f, lo);
-    uint32_t m = 0;
-#pragma unroll
-    for (int k = 0; k < PPL; k++) {
-        const float dy = __fmaf_rn(-(float)k, sp.ddy, sp.dy0);
-        m |= (uint32_t)(__fmaf_rn(__fmaf_rn(sp.C, dy, sp.Bdx), dy, sp.Adx2) >= thr) << k;
-    }
-    return m;
 }
 
 // 2^x by the SFU (PTX ex2.approx.ftz; x >= -8 here, so no denormal result)
@@ -126,10 +109,10 @@ __device__ __forceinline__ float ex2(float x)
     return y;
 }
 
-// alpha of a pixel in the strip's reach mask (0 = skipped by the 1/255 rule)
-__device__ __forceinline__ float strip_alpha(float p, float lo, float& raw)
+// alpha of a pixel that passed q >= -8 (0 = skipped by the 1/255 rule)
+__device__ __forceinline__ float strip_alpha(float q, float lo, float& raw)
 {
-    raw = ex2(__fadd_rn(p, lo));
+    raw = ex2(fminf(q, lo));
     const float a = fminf(raw, kAlphaMax);
     return a < kAlphaMin ? 0.0f : a;
 }
@@ -211,17 +194,15 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
             const float4 g = s_g[j];
             const float2 h = s_h[j];
             if (CNT) n_seen += __popc(live);
-            const Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, G.fx, G.fy0, G.dy);
+            const Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, h.y, G.fx, G.fy0, G.dy);
             const float4 c = s_c[j];
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
                 if (!(live >> k & 1u)) continue;
-                // the reach tests of strip_reach, taken pixel by pixel (the
-                // forward often stops early, so a mask up front would not pay)
-                const float p = strip_p(sp, k);
-                if (!(__fadd_rn(p, h.y) >= -8.0f)) continue;
+                const float q = strip_q(sp, k);
+                if (!(q >= -8.0f)) continue;
                 float raw;
-                const float a = strip_alpha(p, h.y, raw);
+                const float a = strip_alpha(q, h.y, raw);
                 if (a == 0.f) continue;
                 const float Tn = T[k] * (1.f - a);
                 if (Tn < kTMin) { live &= ~(1u << k); continue; }
@@ -318,8 +299,7 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
     __shared__ float4 s_h[R];   // C, log2 o, 1 / o, record index (bits)
     __shared__ float4 s_k[R];   // conic a, b, c, -
     __shared__ float4 s_c[R];   // colour
-    __shared__ float s_G[3][256];       // dL/dpixel per slot
-    __shared__ uint32_t s_last[256];    // last per slot
+    __shared__ float4 s_Gl[256];        // dL/dpixel (3) and last (bits) per slot
     __shared__ uint32_t s_max;
     const int tid = threadIdx.x, lane = tid & 31;
     TileInfo ti;
@@ -343,8 +323,7 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             T[k] = T_final[ti.pix_off + p];
             lk = last_in[ti.pix_off + p];
         }
-        s_G[0][q] = g0; s_G[1][q] = g1; s_G[2][q] = g2;
-        s_last[q] = lk;
+        s_Gl[q] = make_float4(g0, g1, g2, __uint_as_float(lk));
         ml = max(ml, lk);
     }
     uint32_t maxlast = __reduce_max_sync(0xffffffffu, ml);
@@ -388,15 +367,23 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
                 next_join = 0;
 #pragma unroll
                 for (int k = 0; k < PPL; k++) {
-                    const uint32_t lk = s_last[tid + NT * k];
+                    const uint32_t lk = __float_as_uint(s_Gl[tid + NT * k].w);
                     if (pos < lk) joined |= 1u << k;
                     else next_join = max(next_join, lk);
                 }
             }
             const float4 g = s_g[j];
             const float4 h = s_h[j];
-            const Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, Lg.fx, Lg.fy0, Lg.dy);
-            const uint32_t todo = joined & strip_reach<PPL>(sp, h.y);
+            const Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, h.y, Lg.fx, Lg.fy0, Lg.dy);
+            // the first test for the whole strip, without branches
+            float qk[PPL];
+            uint32_t reach = 0;
+#pragma unroll
+            for (int k = 0; k < PPL; k++) {
+                qk[k] = strip_q(sp, k);
+                reach |= (uint32_t)(qk[k] >= -8.0f) << k;
+            }
+            const uint32_t todo = joined & reach;
             if (!__any_sync(0xffffffffu, todo != 0u)) continue;
             const float4 c = s_c[j];
             // colour sums and the moments of dL/dpower along the strip:
@@ -407,23 +394,23 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             for (int k = 0; k < PPL; k++) {
                 if (!(todo >> k & 1u)) continue;
                 float raw = 0.f;
-                const float a = strip_alpha(strip_p(sp, k), h.y, raw);
+                const float a = strip_alpha(qk[k], h.y, raw);
                 if (!(a > 0.f)) continue;
                 any = true;
-                const int q = tid + NT * k;
-                const float G0 = s_G[0][q], G1 = s_G[1][q], G2 = s_G[2][q];
+                const float4 Gk = s_Gl[tid + NT * k];
                 const float Tj = T[k] * __fdividef(1.f, 1.f - a);
                 const float wT = a * Tj;
-                c0 = fmaf(G0, wT, c0);
-                c1 = fmaf(G1, wT, c1);
-                c2 = fmaf(G2, wT, c2);
+                c0 = fmaf(Gk.x, wT, c0);
+                c1 = fmaf(Gk.y, wT, c1);
+                c2 = fmaf(Gk.z, wT, c2);
                 const float d0 = c.x - B0[k], d1 = c.y - B1[k], d2 = c.z - B2[k];
-                const float dLda = Tj * fmaf(G0, d0, fmaf(G1, d1, G2 * d2));
+                // dL/dalpha = T_j (G . (c - B)); d alpha / d power = alpha below the clamp
+                const float gd = fmaf(Gk.x, d0, fmaf(Gk.y, d1, Gk.z * d2));
                 B0[k] = fmaf(a, d0, B0[k]);      // B <- c a + (1 - a) B
                 B1[k] = fmaf(a, d1, B1[k]);
                 B2[k] = fmaf(a, d2, B2[k]);
                 T[k] = Tj;
-                const float dLdp = raw < kAlphaMax ? dLda * a : 0.f;   // d alpha / d power = alpha below the clamp
+                const float dLdp = raw < kAlphaMax ? wT * gd : 0.f;
                 S0 += dLdp;
                 S1 = fmaf(dLdp, (float)k, S1);
                 S2 = fmaf(dLdp, (float)(k * k), S2);

@@ -120,7 +120,8 @@ class DogsTrainer:
         else:
             D.dg_loss_l1(self.vb, target, self.w_l1)
 
-    def enqueue(self, p: int, consensus: bool, target: Optional[torch.Tensor] = None) -> None:
+    def enqueue(self, p: int, consensus: bool, target: Optional[torch.Tensor] = None,
+                slot: Optional[int] = None) -> None:
         """All launches of one iteration for pool entry p on the current stream.
         The step counter for Adam's bias correction (dev_step) is advanced
         on the device first."""
@@ -136,18 +137,22 @@ class DogsTrainer:
             D.dg_admm_consensus(self.x, self.u, self.z, self.anchor, self.g_off, self.g_copies, self.rho,
                                 self.alpha, self.residuals)
         if self.host_targets is not None:
-            self.host_loss.copy_(vb.loss, non_blocking=True)
+            self.host_loss[0 if slot is None else slot].copy_(vb.loss, non_blocking=True)
 
     # ---- targets in host memory ----------------------------------------------------
     def use_host_targets(self, host_targets: Sequence[torch.Tensor]) -> None:
         """Keep the pool's target images in pinned host memory.  Each step's
         target is copied in on a side stream one step ahead, into one of two
         device buffers, while the previous step computes; every step also
-        copies its per-view losses back (read them with last_loss())."""
+        copies its per-view losses back into one of two pinned host buffers
+        (read them with loss_of(t) or last_loss(), which wait only for that
+        step, so the host can read step t's losses while step t + 1 runs)."""
         self.host_targets = [t if t.is_pinned() else t.pin_memory() for t in host_targets]
         self.stage = [torch.empty(self.host_targets[0].shape, dtype=self.host_targets[0].dtype, device=self.device)
                       for _ in range(2)]
-        self.host_loss = torch.zeros(self.vb.loss.numel(), dtype=torch.float64).pin_memory()
+        self.host_loss = [torch.zeros(self.vb.loss.numel(), dtype=torch.float64).pin_memory() for _ in range(2)]
+        self.loss_ready = [torch.cuda.Event() for _ in range(2)]
+        self.loss_step = [-1, -1]
         self.copy_stream = torch.cuda.Stream()
         self.copied = [torch.cuda.Event() for _ in range(2)]
         self.used = [torch.cuda.Event() for _ in range(2)]
@@ -166,10 +171,18 @@ class DogsTrainer:
         t = self.host_targets[0]
         return int(t.numel() * t.element_size())
 
+    def loss_of(self, t: int) -> torch.Tensor:
+        """The per-view losses of iteration t, one of the last two (waits for
+        that iteration only)."""
+        slot = t % 2
+        if self.loss_step[slot] != t:
+            raise ValueError(f"losses of iteration {t} are no longer (or not yet) on the host")
+        self.loss_ready[slot].synchronize()
+        return self.host_loss[slot].clone()
+
     def last_loss(self) -> torch.Tensor:
         """The per-view losses of the last step (waits for it)."""
-        torch.cuda.current_stream().synchronize()
-        return self.host_loss.clone()
+        return self.loss_of(self.t - 1)
 
     def backward_step(self) -> None:
         """Adjoint of the iteration's render and the x-step (Eq. 8a / 12a).
@@ -201,12 +214,14 @@ class DogsTrainer:
         if graph:
             key = (p, c, slot)
             if key not in self.graphs:
-                self.graphs[key] = self._capture(p, c, target)
+                self.graphs[key] = self._capture(p, c, target, slot)
             self.graphs[key].replay()
         else:
-            self.enqueue(p, c, target)
+            self.enqueue(p, c, target, slot)
         if slot is not None:
             self.used[slot].record(torch.cuda.current_stream())
+            self.loss_ready[slot].record(torch.cuda.current_stream())
+            self.loss_step[slot] = self.t
             nxt = self.t + 1
             self._prefetch(nxt % len(self.view_sets), nxt % 2)
         if c and self.adaptive is not None and self.t < self.adaptive.freeze_after:
@@ -227,14 +242,15 @@ class DogsTrainer:
         self.rho = rho
         self.graphs.clear()
 
-    def _capture(self, p: int, c: bool, target: Optional[torch.Tensor] = None) -> torch.cuda.CUDAGraph:
+    def _capture(self, p: int, c: bool, target: Optional[torch.Tensor] = None,
+                 slot: Optional[int] = None) -> torch.cuda.CUDAGraph:
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):       # warm the allocator-free launch path once
             torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            self.enqueue(p, c, target)
+            self.enqueue(p, c, target, slot)
         return g
 
     def overflowed(self) -> bool:

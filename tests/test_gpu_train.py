@@ -276,12 +276,20 @@ def test_host_targets_equal_device_targets(mods):
     b = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, **kw)
     b.calibrate_capacity()
     b.use_host_targets([t.cpu() for t in targets])
-    for _ in range(5):
+    la, lb = [], []
+    for i in range(5):
         a.step()
+        la.append(a.vb.loss.cpu().numpy())
         b.step()
+        if i > 0:       # the previous step's losses, read while this one runs
+            lb.append(b.loss_of(b.t - 2).numpy())
+    lb.append(b.last_loss().numpy())
+    with pytest.raises(ValueError):
+        b.loss_of(b.t - 3)
     torch.cuda.synchronize()
     assert int(a.dev_step.item()) == int(b.dev_step.item()) == 5
-    np.testing.assert_allclose(b.last_loss().numpy(), a.vb.loss.cpu().numpy(), rtol=1e-3)
+    for x_, y_ in zip(la, lb):
+        np.testing.assert_allclose(y_, x_, rtol=1e-3)
     for n in ("x", "z"):
         ga, gb = groups(getattr(a, n)), groups(getattr(b, n))
         for k in ga:
