@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-autotune", action="store_true", help="keep --tile and the default compositing variant")
+    ap.add_argument("--idle-ctas", type=int, default=0,
+                    help="CTAs per SM of the x-step part that runs beside compositing (0: one per group of copies)")
+    ap.add_argument("--no-overlap", action="store_true", help="run that x-step part inline on the main stream")
     ap.add_argument("--variant", default=None,
                     help="compositing variant W,S[,Wb,Sb] (warps per tile, staged per thread; backward)")
     ap.add_argument("--loss", default="dssim", choices=["dssim", "l1"])
@@ -193,7 +196,22 @@ FLOPS_FWD_USED = 9
 FLOPS_BWD_USED = 53
 
 
-def algorithmic_bytes(tr, vb_rect_visible: int, n_visible_copies: int):
+def copy_groups(tr, rect):
+    """Per copy: kept record in its block's view (bool), and per group of 128
+    consecutive copies (the x-step's CTAs): any kept record."""
+    n_c = tr.split.n_copies
+    kept = np.zeros(n_c, bool)
+    vis = (rect[:, 0] & 0xFFFF) != (rect[:, 1] & 0xFFFF)
+    for c in tr.vb.host_cams:
+        b, e = int(c.gauss_begin), int(c.gauss_end)
+        kept[b:e] |= vis[int(c.rec_off):int(c.rec_off) + e - b]
+    ng = -(-n_c // 128)
+    grp = np.zeros(ng * 128, bool)
+    grp[:n_c] = kept
+    return kept, grp.reshape(ng, 128).any(1)
+
+
+def algorithmic_bytes(tr, vb_rect_visible: int, n_visible_copies: int, active_groups=None):
     sp = tr.split
     P = 59
     n_c = sp.n_copies
@@ -202,7 +220,7 @@ def algorithmic_bytes(tr, vb_rect_visible: int, n_visible_copies: int):
     sg = int((cnt > 1).sum())
     ug = int((cnt == 1).sum())
     sc = int(cnt[cnt > 1].sum())
-    return {
+    out = {
         # x, g, m, v read + x, m, v written per float; anchor read per shared float
         "adam_admm_step": n_c * P * 28 + n_sc * P * 4,
         # fused projection adjoint + x-step: x, m, v read and written per float, anchor per shared
@@ -215,6 +233,15 @@ def algorithmic_bytes(tr, vb_rect_visible: int, n_visible_copies: int):
         # + record (48 B)
         "project": n_c * 24 + n_visible_copies * 224 + vb_rect_visible * 48,
     }
+    if active_groups is not None:
+        # split x-step: part 2 over the groups of 128 copies with a kept record, part 1 over the
+        # others (plus the 8-byte rectangle of each of its copies, read to find them)
+        act = np.repeat(active_groups, 128)[:n_c]
+        sh = sp.copy_shared().astype(bool)
+        na, nsa = int(act.sum()), int((act & sh).sum())
+        out["xstep"] = na * P * 24 + nsa * P * 4 + n_visible_copies * 56
+        out["xstep_idle"] = (n_c - na) * (P * 24 + 8) + (n_sc - nsa) * P * 4
+    return out
 
 
 def run_ours(args, dist, rank, world):
@@ -238,7 +265,9 @@ def run_ours(args, dist, rank, world):
     del gt
     if args.variant:
         D.set_raster_variant(*[int(v) for v in args.variant.split(",")])
-    tr = T.DogsTrainer(wl.split, z0, wl.views, targets, rho=(1e-3,) * 5, tile=tile, loss=args.loss)
+    tr = T.DogsTrainer(wl.split, z0, wl.views, targets, rho=(1e-3,) * 5, tile=tile, loss=args.loss,
+                       overlap=not args.no_overlap)
+    tr.idle_ctas_per_sm = args.idle_ctas
     m_max = tr.calibrate_capacity()
     tuned = None
     if not args.no_autotune and not args.profile and not args.variant:
@@ -284,10 +313,31 @@ def run_ours(args, dist, rank, world):
 
     # ---- per-call durations (eager launches, events on the launching stream) ----------
     fused = tr.fused and D.one_view_per_block(tr.vb.plan)
-    names = ["project", "bin_sort", "rasterize_fwd", "loss", "rasterize_bwd",
-             "xstep" if fused else "adam_admm_step", "admm_consensus"]
-    acc = {n: 0.0 for n in names}
+    split = tr._split_xstep()
     vb = tr.vb
+    xs_args = (tr.x, tr.m, tr.v, tr.anchor, tr.shared, tr.rho, tr.lr)
+
+    def bwd_fused():
+        D.dg_rasterize_bwd_records(vb, bg=tr.bg)
+
+    calls = [("project", lambda: D.dg_project(tr.x, vb))]
+    if split:       # the part that the graph runs on a side stream, timed here in sequence
+        calls.append(("xstep_idle", lambda: D.dg_xstep_part(1, vb, *xs_args, step=1, dev_step=tr.dev_step)))
+    calls += [("bin_sort", lambda: D.dg_bin_sort(vb)),
+              ("rasterize_fwd", lambda: D.dg_rasterize_fwd(vb, tr.bg)),
+              ("loss", lambda: tr._loss(tr.targets[tr.t % len(tr.view_sets)]))]
+    if fused:       # compositing adjoint, then projection adjoint + x-step fused
+        calls += [("rasterize_bwd", bwd_fused),
+                  ("xstep", lambda: D.dg_xstep_part(2 if split else 0, vb, *xs_args, step=1,
+                                                    dev_step=tr.dev_step))]
+    else:
+        calls += [("rasterize_bwd", lambda: D.dg_rasterize_bwd(vb, tr.x, tr.grad, bg=tr.bg)),
+                  ("adam_admm_step", lambda: D.dg_adam_admm_step(*xs_args[:1], tr.grad, *xs_args[1:], step=1,
+                                                                 dev_step=tr.dev_step))]
+    calls.append(("admm_consensus", lambda: D.dg_admm_consensus(tr.x, tr.u, tr.z, tr.anchor, tr.g_off, tr.g_copies,
+                                                                tr.rho, tr.alpha, tr.residuals)))
+    names = [n for n, _ in calls]
+    acc = {n: 0.0 for n in names}
     n_eager = max(3, min(args.steps, 20))
     l0 = L.lib().dg_launch_count()
     pairs = 0.0
@@ -297,20 +347,9 @@ def run_ours(args, dist, rank, world):
         vb.dev_cams.copy_(tr.cam_pool[p], non_blocking=True)
         D.dg_step_advance(tr.dev_step)
         ev[0].record()
-        D.dg_project(tr.x, vb); ev[1].record()
-        D.dg_bin_sort(vb); ev[2].record()
-        D.dg_rasterize_fwd(vb, tr.bg); ev[3].record()
-        tr._loss(tr.targets[p]); ev[4].record()
-        if fused:   # compositing adjoint, then projection adjoint + x-step fused
-            D.dg_rasterize_bwd_records(vb, bg=tr.bg); ev[5].record()
-            D.dg_xstep_from_records(vb, tr.x, tr.m, tr.v, tr.anchor, tr.shared, tr.rho, tr.lr, step=1,
-                                    dev_step=tr.dev_step); ev[6].record()
-        else:
-            D.dg_rasterize_bwd(vb, tr.x, tr.grad, bg=tr.bg); ev[5].record()
-            D.dg_adam_admm_step(tr.x, tr.grad, tr.m, tr.v, tr.anchor, tr.shared, tr.rho, tr.lr, step=1,
-                                dev_step=tr.dev_step); ev[6].record()
-        D.dg_admm_consensus(tr.x, tr.u, tr.z, tr.anchor, tr.g_off, tr.g_copies, tr.rho, tr.alpha, tr.residuals)
-        ev[7].record()
+        for k, (n, fn) in enumerate(calls):
+            fn()
+            ev[k + 1].record()
         torch.cuda.synchronize()
         for k, n in enumerate(names):
             acc[n] += ev[k].elapsed_time(ev[k + 1]) / n_eager
@@ -324,7 +363,8 @@ def run_ours(args, dist, rank, world):
     rect = vb.rect.view(-1, 2)[:vb.n_rec].cpu().numpy().view(np.uint32)
     vis_rec = int(((rect[:, 0] & 0xFFFF) != (rect[:, 1] & 0xFFFF)).sum())
     instances = int(vb.count.item())
-    alg = algorithmic_bytes(tr, vis_rec, vis_rec)
+    _, active_groups = copy_groups(tr, rect)
+    alg = algorithmic_bytes(tr, vis_rec, vis_rec, active_groups if split else None)
     peaks, peak_src = measured_peaks()
     hbm_peak = float(peaks["hbm_gbs"])
     kern = {}
@@ -430,6 +470,9 @@ def run_ours(args, dist, rank, world):
                                      "variants_per_tile": len(tuned["candidates"][0]["variants"])}),
                        "loss": "0.8 L1 + 0.2 D-SSIM" if args.loss == "dssim" else "L1",
                        "consensus_every_timed_step": True, "cuda_graph": True,
+                       "xstep_split": (None if not split else
+                                       {"idle_groups_on_side_stream": round(1.0 - float(active_groups.mean()), 3),
+                                        "side_ctas_per_sm": tr.idle_ctas_per_sm}),
                        "l2": "working set > L2 (no flush needed)", "instances_per_step": instances,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "setup_s": round(setup_s, 1)},

@@ -254,6 +254,23 @@ int dg_xstep_from_records(const uint32_t* rect, const dg_camera* dev_cams, const
                           const float* lr, float beta1, float beta2, float eps, int step,
                           const int32_t* dev_step, void* stream);
 
+/* dg_xstep_from_records in two parts that together take the same step
+ * (bit for bit), by groups of 128 consecutive copies: part 1 steps the
+ * groups none of whose copies has a kept record (zero rendering gradient:
+ * Adam on the penalty alone; drec is not read and may be NULL), part 2 the
+ * others (the fused adjoint + step).  Part 1 reads only the rectangles of
+ * the projection, so it can run on another stream alongside binning,
+ * compositing and the loss; `ctas` > 0 bounds its grid (a grid-stride loop
+ * over the groups), so that it leaves most of each SM to the kernels beside
+ * it; 0 = one CTA per group.  part 0 = the whole step.  Same arguments and
+ * errors as dg_xstep_from_records; DG_ERR_INVALID for a part outside 0..2
+ * or a negative ctas. */
+int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                  const float* drec, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v,
+                  const dg_gaussians* anchor, const uint8_t* copy_shared, const float* rho,
+                  const float* lr, float beta1, float beta2, float eps, int step,
+                  const int32_t* dev_step, void* stream);
+
 /* ---- ADMM (K9, K10) -------------------------------------------------------- */
 /* x-step (Eq. 8a / 12a): one Adam step on every local copy with gradient
  * g + rho_grp (x - anchor) on shared copies (copy_shared[c] != 0), where the

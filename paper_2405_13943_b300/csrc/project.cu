@@ -448,110 +448,98 @@ __global__ void __launch_bounds__(128, 4) k_project_bwd(GView x, const dg_camera
 // in shared memory (dL/d f_{k,ch} = gc[ch] Y[k]); the CTA then steps its
 // copies' SH planes with float4 accesses, four consecutive copies per thread
 // (the same arithmetic as the separate kernels).
+//
+// The step can be taken in two parts, by CTA of kXsThreads consecutive
+// copies: a CTA none of whose copies has a kept record has a zero rendering
+// gradient, so its step depends only on x, m, v and the anchors and can run
+// as soon as the projection has written the rectangles (k_xstep_idle,
+// alongside the compositing kernels); the CTAs with a kept record run after
+// the compositing adjoint (k_xstep with PART = 2).  Both take the step by the
+// same device functions, so the result is the same as the one-part step.
 constexpr int kXsThreads = 128;
 
-template <int DEG>
-__global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView v, GView an,
-                                                        const uint8_t* __restrict__ shared,
-                                                        const dg_camera* __restrict__ cams, dg_plan plan,
-                                                        const uint2* __restrict__ rect,
-                                                        const float4* __restrict__ drec, AdamArgs a,
-                                                        const int32_t* __restrict__ dev_step)
+// the record of copy c in its block's view, or -1 if the forward kept none
+__device__ __forceinline__ int64_t copy_record(int64_t c, int64_t n, const dg_plan& plan,
+                                               const dg_camera* __restrict__ cams, const uint2* __restrict__ rect,
+                                               CamL& cam)
 {
-    constexpr int NK = (DEG + 1) * (DEG + 1);
-    __shared__ __align__(16) float s_gc[3][kXsThreads];
-    __shared__ __align__(16) float s_Y[NK][kXsThreads];
-    const int tid = threadIdx.x;
-    const int64_t c0 = (int64_t)blockIdx.x * kXsThreads, c = c0 + tid;
-    float ic1, ic2;
-    bias_corr(a, dev_step, ic1, ic2);
-    float gc[3] = {0.f, 0.f, 0.f}, Y[NK];
+    if (c >= n || c >= plan.blk_off[plan.n_blocks]) return -1;
+    const int k = find_block(plan, c);
+    const int v0 = plan.blk_view_off[k];
+    if (v0 >= plan.blk_view_off[k + 1]) return -1;
+    load_cam(cams, v0, cam);
+    const int64_t rr = cam.rec_off + (c - cam.gb);
+    const uint2 t = rect[rr];
+    return (t.x & 0xFFFFu) != (t.y & 0xFFFFu) ? rr : -1;
+}
+
+// Adam + penalty on copy c's float4 fields (mean, opacity logit), rotation,
+// (log-scale, padding) with gradients gmu, go, gq, gs
+__device__ __forceinline__ void step_fields(GView& x, GView& m, GView& v, const GView& an, int64_t c, bool s,
+                                            const float4& mo, const float4& q, const float4& sc, const float* gmu,
+                                            float go, const float* gq, const float* gs, const AdamArgs& a,
+                                            float ic1, float ic2)
+{
+    {
+        float xs[4] = {mo.x, mo.y, mo.z, mo.w}, gg[4] = {gmu[0], gmu[1], gmu[2], go};
+        const float4 mm = m.mo[c], vv = v.mo[c];
+        float ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
+        const float4 aa = s ? an.mo[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float as[4] = {aa.x, aa.y, aa.z, aa.w};
 #pragma unroll
-    for (int kk = 0; kk < NK; kk++) Y[kk] = 0.f;
-    if (c < x.n) {
-        const bool s = shared != nullptr && shared[c] != 0;
-        const float4 mo = x.mo[c];
-        const float3 mu = make_float3(mo.x, mo.y, mo.z);
-        // the copy's record: its block's view, if the forward kept it
-        int64_t r = -1;
-        CamL cam;
-        if (c < plan.blk_off[plan.n_blocks]) {
-            const int k = find_block(plan, c);
-            const int v0 = plan.blk_view_off[k];
-            if (v0 < plan.blk_view_off[k + 1]) {
-                load_cam(cams, v0, cam);
-                const int64_t rr = cam.rec_off + (c - cam.gb);
-                const uint2 t = rect[rr];
-                if ((t.x & 0xFFFFu) != (t.y & 0xFFFFu)) r = rr;
-            }
+        for (int i = 0; i < 4; i++) {
+            const float rho = i < 3 ? a.rho[0] : a.rho[4], lr = i < 3 ? a.lr[0] : a.lr[5];
+            if (s) gg[i] += rho * (xs[i] - as[i]);
+            adam_scalar(xs[i], gg[i], ms[i], vs[i], lr, a.b1, a.b2, a.eps, ic1, ic2);
         }
-        float gmu[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gs[3] = {0, 0, 0}, go = 0.f;
-        const float4 q = x.quat[c], sc = x.scale[c];
-        if (r >= 0) {
-            {
-                float f[3 * NK];
-#pragma unroll
-                for (int j = 0; j < 3 * NK; j++) f[j] = x.sh[(int64_t)j * x.ld + c];
-                colour_adjoint<DEG>(cam, mu, 1.f / (1.f + __expf(-mo.w)), f, drec[3 * r + 1], drec[3 * r + 2], gmu,
-                                    go, gc, Y);
-            }
-            geometry_adjoint<DEG>(cam, mu, q, sc, drec[3 * r + 0], drec[3 * r + 1], plan.tile_w, plan.tile_h, gmu,
-                                  gq, gs);
-        }
-        // float4 fields: (mean, opacity logit), rotation, (log-scale, padding)
-        {
-            float xs[4] = {mo.x, mo.y, mo.z, mo.w}, gg[4] = {gmu[0], gmu[1], gmu[2], go};
-            const float4 mm = m.mo[c], vv = v.mo[c];
-            float ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
-            const float4 aa = s ? an.mo[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float as[4] = {aa.x, aa.y, aa.z, aa.w};
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                const float rho = i < 3 ? a.rho[0] : a.rho[4], lr = i < 3 ? a.lr[0] : a.lr[5];
-                if (s) gg[i] += rho * (xs[i] - as[i]);
-                adam_scalar(xs[i], gg[i], ms[i], vs[i], lr, a.b1, a.b2, a.eps, ic1, ic2);
-            }
-            x.mo[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
-            m.mo[c] = make_float4(ms[0], ms[1], ms[2], ms[3]);
-            v.mo[c] = make_float4(vs[0], vs[1], vs[2], vs[3]);
-        }
-        {
-            const float4 mm = m.quat[c], vv = v.quat[c];
-            float xs[4] = {q.x, q.y, q.z, q.w}, ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
-            const float4 aa = s ? an.quat[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float as[4] = {aa.x, aa.y, aa.z, aa.w};
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                float g = gq[i];
-                if (s) g += a.rho[1] * (xs[i] - as[i]);
-                adam_scalar(xs[i], g, ms[i], vs[i], a.lr[1], a.b1, a.b2, a.eps, ic1, ic2);
-            }
-            x.quat[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
-            m.quat[c] = make_float4(ms[0], ms[1], ms[2], ms[3]);
-            v.quat[c] = make_float4(vs[0], vs[1], vs[2], vs[3]);
-        }
-        {
-            const float4 mm = m.scale[c], vv = v.scale[c];
-            float xs[4] = {sc.x, sc.y, sc.z, sc.w}, ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
-            const float4 aa = s ? an.scale[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float as[4] = {aa.x, aa.y, aa.z, aa.w};
-#pragma unroll
-            for (int i = 0; i < 3; i++) {   // lane 3 is padding
-                float g = gs[i];
-                if (s) g += a.rho[2] * (xs[i] - as[i]);
-                adam_scalar(xs[i], g, ms[i], vs[i], a.lr[2], a.b1, a.b2, a.eps, ic1, ic2);
-            }
-            x.scale[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
-            m.scale[c] = make_float4(ms[0], ms[1], ms[2], ms[3]);
-            v.scale[c] = make_float4(vs[0], vs[1], vs[2], vs[3]);
-        }
+        x.mo[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+        m.mo[c] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+        v.mo[c] = make_float4(vs[0], vs[1], vs[2], vs[3]);
     }
+    {
+        const float4 mm = m.quat[c], vv = v.quat[c];
+        float xs[4] = {q.x, q.y, q.z, q.w}, ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
+        const float4 aa = s ? an.quat[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float as[4] = {aa.x, aa.y, aa.z, aa.w};
 #pragma unroll
-    for (int ch = 0; ch < 3; ch++) s_gc[ch][tid] = gc[ch];
+        for (int i = 0; i < 4; i++) {
+            float g = gq[i];
+            if (s) g += a.rho[1] * (xs[i] - as[i]);
+            adam_scalar(xs[i], g, ms[i], vs[i], a.lr[1], a.b1, a.b2, a.eps, ic1, ic2);
+        }
+        x.quat[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+        m.quat[c] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+        v.quat[c] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+    }
+    {
+        const float4 mm = m.scale[c], vv = v.scale[c];
+        float xs[4] = {sc.x, sc.y, sc.z, sc.w}, ms[4] = {mm.x, mm.y, mm.z, mm.w}, vs[4] = {vv.x, vv.y, vv.z, vv.w};
+        const float4 aa = s ? an.scale[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float as[4] = {aa.x, aa.y, aa.z, aa.w};
 #pragma unroll
-    for (int kk = 0; kk < NK; kk++) s_Y[kk][tid] = Y[kk];
-    __syncthreads();
-    // SH planes: thread = (plane group tid / 32, quad tid % 32 of four copies)
+        for (int i = 0; i < 3; i++) {   // lane 3 is padding
+            float g = gs[i];
+            if (s) g += a.rho[2] * (xs[i] - as[i]);
+            adam_scalar(xs[i], g, ms[i], vs[i], a.lr[2], a.b1, a.b2, a.eps, ic1, ic2);
+        }
+        x.scale[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+        m.scale[c] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+        v.scale[c] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+    }
+}
+
+// The SH planes of the CTA's copies c0 .. c0 + kXsThreads - 1: thread = (plane
+// group tid / 32, quad tid % 32 of four copies), PB planes per batch and
+// thread with all loads of a batch issued before its stores.  The gradient of
+// plane j (channel j % 3, coefficient j / 3) at copy i of the quad is
+// gc[ch][i] Y[k][i] from shared memory, or 0 without a rendering gradient
+// (ZERO).
+template <int NK, int PB, bool ZERO>
+__device__ __forceinline__ void step_planes(GView& x, GView& m, GView& v, const GView& an,
+                                            const uint8_t* __restrict__ shared, int64_t c0, const float* s_gc,
+                                            const float* s_Y, const AdamArgs& a, float ic1, float ic2)
+{
+    const int tid = threadIdx.x;
     const int quad = tid & 31;
     const int64_t cq = c0 + 4 * quad;
     if (cq >= x.ld) return;                       // the quad lies beyond the planes' stride
@@ -562,9 +550,7 @@ __global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView
         sh[i] = act[i] && shared != nullptr && shared[cq + i] != 0;
     }
     const bool any_sh = sh[0] || sh[1] || sh[2] || sh[3];
-    // six planes per batch, all loads of the batch issued before its stores
     constexpr int G = kXsThreads / 32;          // plane groups (4)
-    constexpr int PB = 6;                       // planes per batch and thread
     for (int j0 = tid >> 5; j0 < 3 * NK; j0 += G * PB) {
         float4 xv[PB], mv[PB], vv[PB], av[PB];
 #pragma unroll
@@ -582,10 +568,13 @@ __global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView
             const int j = j0 + b * G;
             if (j >= 3 * NK) break;
             const float lr = j < 3 ? a.lr[3] : a.lr[4];
-            // the quad's four colour gradients and basis values, one 16-byte load each
-            const float4 gc4 = *reinterpret_cast<const float4*>(&s_gc[j % 3][4 * quad]);
-            const float4 y4 = *reinterpret_cast<const float4*>(&s_Y[j / 3][4 * quad]);
-            const float gq4[4] = {gc4.x * y4.x, gc4.y * y4.y, gc4.z * y4.z, gc4.w * y4.w};
+            float gq4[4] = {0.f, 0.f, 0.f, 0.f};
+            if (!ZERO) {
+                // the quad's four colour gradients and basis values, one 16-byte load each
+                const float4 gc4 = *reinterpret_cast<const float4*>(&s_gc[(j % 3) * kXsThreads + 4 * quad]);
+                const float4 y4 = *reinterpret_cast<const float4*>(&s_Y[(j / 3) * kXsThreads + 4 * quad]);
+                gq4[0] = gc4.x * y4.x; gq4[1] = gc4.y * y4.y; gq4[2] = gc4.z * y4.z; gq4[3] = gc4.w * y4.w;
+            }
             float xs[4] = {xv[b].x, xv[b].y, xv[b].z, xv[b].w}, ms[4] = {mv[b].x, mv[b].y, mv[b].z, mv[b].w};
             float vs[4] = {vv[b].x, vv[b].y, vv[b].z, vv[b].w};
             const float as[4] = {av[b].x, av[b].y, av[b].z, av[b].w};
@@ -604,20 +593,125 @@ __global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView
     }
 }
 
-int launch_xstep(dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
+// PART 0: every CTA; PART 2: only the CTAs with at least one kept record
+template <int DEG, int PART>
+__global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView v, GView an,
+                                                        const uint8_t* __restrict__ shared,
+                                                        const dg_camera* __restrict__ cams, dg_plan plan,
+                                                        const uint2* __restrict__ rect,
+                                                        const float4* __restrict__ drec, AdamArgs a,
+                                                        const int32_t* __restrict__ dev_step)
+{
+    constexpr int NK = (DEG + 1) * (DEG + 1);
+    __shared__ __align__(16) float s_gc[3][kXsThreads];
+    __shared__ __align__(16) float s_Y[NK][kXsThreads];
+    const int tid = threadIdx.x;
+    const int64_t c0 = (int64_t)blockIdx.x * kXsThreads, c = c0 + tid;
+    CamL cam;
+    const int64_t r = copy_record(c, x.n, plan, cams, rect, cam);
+    if (PART == 2 && !__syncthreads_or(r >= 0)) return;    // uniform: the CTA is stepped by k_xstep_idle
+    float ic1, ic2;
+    bias_corr(a, dev_step, ic1, ic2);
+    float gc[3] = {0.f, 0.f, 0.f}, Y[NK];
+#pragma unroll
+    for (int kk = 0; kk < NK; kk++) Y[kk] = 0.f;
+    if (c < x.n) {
+        const bool s = shared != nullptr && shared[c] != 0;
+        const float4 mo = x.mo[c];
+        const float3 mu = make_float3(mo.x, mo.y, mo.z);
+        float gmu[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gs[3] = {0, 0, 0}, go = 0.f;
+        const float4 q = x.quat[c], sc = x.scale[c];
+        if (r >= 0) {
+            {
+                float f[3 * NK];
+#pragma unroll
+                for (int j = 0; j < 3 * NK; j++) f[j] = x.sh[(int64_t)j * x.ld + c];
+                colour_adjoint<DEG>(cam, mu, 1.f / (1.f + __expf(-mo.w)), f, drec[3 * r + 1], drec[3 * r + 2], gmu,
+                                    go, gc, Y);
+            }
+            geometry_adjoint<DEG>(cam, mu, q, sc, drec[3 * r + 0], drec[3 * r + 1], plan.tile_w, plan.tile_h, gmu,
+                                  gq, gs);
+        }
+        step_fields(x, m, v, an, c, s, mo, q, sc, gmu, go, gq, gs, a, ic1, ic2);
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) s_gc[ch][tid] = gc[ch];
+#pragma unroll
+    for (int kk = 0; kk < NK; kk++) s_Y[kk][tid] = Y[kk];
+    __syncthreads();
+    step_planes<NK, 6, false>(x, m, v, an, shared, c0, &s_gc[0][0], &s_Y[0][0], a, ic1, ic2);
+}
+
+// the groups of k_xstep<PART 2>'s complement: no copy with a kept record, so
+// a zero rendering gradient (the penalty alone on shared copies).  A
+// grid-stride loop over the groups of kXsThreads copies, so that a small
+// grid (a CTA or two per SM) can run alongside the compositing kernels
+// without taking their registers.
+template <int DEG>
+__global__ void __launch_bounds__(kXsThreads, 6) k_xstep_idle(GView x, GView m, GView v, GView an,
+                                                             const uint8_t* __restrict__ shared,
+                                                             const dg_camera* __restrict__ cams, dg_plan plan,
+                                                             const uint2* __restrict__ rect, AdamArgs a,
+                                                             const int32_t* __restrict__ dev_step)
+{
+    constexpr int NK = (DEG + 1) * (DEG + 1);
+    const int tid = threadIdx.x;
+    float ic1, ic2;
+    bias_corr(a, dev_step, ic1, ic2);
+    const int64_t n_groups = (x.n + kXsThreads - 1) / kXsThreads;
+    for (int64_t grp = blockIdx.x; grp < n_groups; grp += gridDim.x) {
+        const int64_t c0 = grp * kXsThreads, c = c0 + tid;
+        bool kept = false;                          // the test of copy_record, without the camera
+        if (c < x.n && c < plan.blk_off[plan.n_blocks]) {
+            const int k = find_block(plan, c);
+            const int v0 = plan.blk_view_off[k];
+            if (v0 < plan.blk_view_off[k + 1]) {
+                const uint2 t = rect[__ldg(&cams[v0].rec_off) + (c - __ldg(&cams[v0].gauss_begin))];
+                kept = (t.x & 0xFFFFu) != (t.y & 0xFFFFu);
+            }
+        }
+        if (__syncthreads_or(kept)) continue;       // uniform: the group is stepped by k_xstep<PART 2>
+        if (c < x.n) {
+            const bool s = shared != nullptr && shared[c] != 0;
+            const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+            step_fields(x, m, v, an, c, s, x.mo[c], x.quat[c], x.scale[c], zero, 0.f, zero, zero, a, ic1, ic2);
+        }
+        step_planes<NK, 2, true>(x, m, v, an, shared, c0, nullptr, nullptr, a, ic1, ic2);
+    }
+}
+
+// part 0: the whole step; 1: the groups without a kept record (drec unused;
+// `ctas` CTAs, 0 = one per group); 2: the groups with one
+int launch_xstep(int part, int ctas, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
                  const uint8_t* shared, const dg_camera* cams, const dg_plan& plan, const uint2* rect,
                  const float4* drec, const AdamArgs& a, const int32_t* dev_step, cudaStream_t st)
 {
     if (x->n == 0) return DG_OK;
     GView xv = gview(x), mv = gview(m), vv = gview(v);
     GView av = anchor ? gview(anchor) : xv;
-    dim3 grid((unsigned)((x->n + kXsThreads - 1) / kXsThreads));
+    const int64_t n_groups = (x->n + kXsThreads - 1) / kXsThreads;
+    dim3 grid((unsigned)n_groups);
+    dim3 grid_idle((unsigned)(ctas > 0 && ctas < n_groups ? ctas : n_groups));
+#define DG_XSTEP_CASE(DEG)                                                                                      \
+    case DEG:                                                                                                   \
+        if (part == 0)                                                                                          \
+            k_xstep<DEG, 0><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a,     \
+                                                         dev_step);                                             \
+        else if (part == 2)                                                                                     \
+            k_xstep<DEG, 2><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a,     \
+                                                         dev_step);                                             \
+        else                                                                                                    \
+            k_xstep_idle<DEG><<<grid_idle, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, a,      \
+                                                                dev_step);                                      \
+        break;
     switch (x->sh_degree) {
-    case 0: k_xstep<0><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a, dev_step); break;
-    case 1: k_xstep<1><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a, dev_step); break;
-    case 2: k_xstep<2><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a, dev_step); break;
-    default: k_xstep<3><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a, dev_step); break;
+    DG_XSTEP_CASE(0)
+    DG_XSTEP_CASE(1)
+    DG_XSTEP_CASE(2)
+    default:
+    DG_XSTEP_CASE(3)
     }
+#undef DG_XSTEP_CASE
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;

@@ -294,3 +294,68 @@ def test_host_targets_equal_device_targets(mods):
         ga, gb = groups(getattr(a, n)), groups(getattr(b, n))
         for k in ga:
             assert rel_l2(gb[k], ga[k]) < REL_L2, (n, k)
+
+
+def test_split_xstep_equals_one_part(mods):
+    """dg_xstep_part: part 1 (groups of 128 copies without a kept record)
+    then part 2 (the rest) takes the step of part 0 bit for bit; part 1
+    alone leaves the groups with a kept record untouched."""
+    D, srv, T = mods
+    wl, z0, targets = small_setup(D, srv, seed=23)
+    tr = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, rho=(1e-2,) * 5, loss="dssim", overlap=False)
+    tr.calibrate_capacity()
+    tr.step(graph=False)                       # non-zero moments and anchors
+    vb = tr.vb
+    vb.dev_cams.copy_(tr.cam_pool[tr.t % len(tr.view_sets)])
+    D.dg_project(tr.x, vb)
+    D.dg_bin_sort(vb)
+    D.dg_rasterize_fwd(vb, tr.bg)
+    tr._loss(tr.targets[tr.t % len(tr.view_sets)])
+    D.dg_rasterize_bwd_records(vb, bg=tr.bg)
+    torch.cuda.synchronize()
+    st = {n: getattr(tr, n).clone() for n in ("x", "m", "v")}
+    args = (tr.anchor, tr.shared, tr.rho, tr.lr)
+    one = {n: st[n].clone() for n in st}
+    D.dg_xstep_part(0, vb, one["x"], one["m"], one["v"], *args, step=2)
+    two = {n: st[n].clone() for n in st}
+    D.dg_xstep_part(1, vb, two["x"], two["m"], two["v"], *args, step=2)
+    torch.cuda.synchronize()
+    rect = vb.rect.view(-1, 2)[:vb.n_rec].cpu().numpy().view(np.uint32)
+    kept = np.zeros(wl.split.n_copies, bool)
+    vis = (rect[:, 0] & 0xFFFF) != (rect[:, 1] & 0xFFFF)
+    for c in vb.host_cams:
+        b, e = int(c.gauss_begin), int(c.gauss_end)
+        kept[b:e] |= vis[int(c.rec_off):int(c.rec_off) + e - b]
+    ng = -(-len(kept) // 128)
+    act = np.repeat(np.pad(kept, (0, ng * 128 - len(kept))).reshape(ng, 128).any(1), 128)[:len(kept)]
+    assert 0 < act.mean() < 1
+    x0, x1 = groups(st["x"]), groups(two["x"])
+    for k in x0:
+        np.testing.assert_array_equal(x1[k][act], x0[k][act])
+        assert not np.array_equal(x1[k][~act], x0[k][~act])
+    D.dg_xstep_part(2, vb, two["x"], two["m"], two["v"], *args, step=2)
+    torch.cuda.synchronize()
+    for n in ("x", "m", "v"):
+        assert torch.equal(one[n].data, two[n].data), n
+
+
+def test_overlapped_xstep_trainer_matches(mods):
+    """Graph replays with the idle part of the x-step on a side stream equal
+    the one-part step (up to the float atomics of the compositing adjoint)."""
+    D, srv, T = mods
+    wl, z0, targets = small_setup(D, srv, seed=29)
+    kw = dict(rho=(1e-2,) * 5, loss="dssim", intv=2)
+    a = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, overlap=True, **kw)
+    a.calibrate_capacity()
+    b = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, overlap=False, **kw)
+    b.calibrate_capacity()
+    assert a._split_xstep() and not b._split_xstep()
+    for _ in range(5):
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    for n in ("x", "z", "m"):
+        ga, gb = groups(getattr(a, n)), groups(getattr(b, n))
+        for k in ga:
+            assert rel_l2(ga[k], gb[k]) < REL_L2, (n, k)
+    assert not a.overflowed()
