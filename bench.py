@@ -211,7 +211,7 @@ def copy_groups(tr, rect):
     return kept, grp.reshape(ng, 128).any(1)
 
 
-def algorithmic_bytes(tr, vb_rect_visible: int, n_visible_copies: int, active_groups=None):
+def algorithmic_bytes(tr, vb_rect_visible: int, n_visible_copies: int, active_groups=None, zfuse=False):
     sp = tr.split
     P = 59
     n_c = sp.n_copies
@@ -241,6 +241,12 @@ def algorithmic_bytes(tr, vb_rect_visible: int, n_visible_copies: int, active_gr
         na, nsa = int(act.sum()), int((act & sh).sum())
         out["xstep"] = na * P * 24 + nsa * P * 4 + n_visible_copies * 56
         out["xstep_idle"] = (n_c - na) * (P * 24 + 8) + (n_sc - nsa) * P * 4
+        if zfuse:
+            # the unshared copies' values stored into z (4 B per float) with their global ids (4 B)
+            # here, so the consensus moves the shared globals' bytes only
+            out["xstep"] += (na - nsa) * (P * 4 + 4)
+            out["xstep_idle"] += (n_c - na - (n_sc - nsa)) * (P * 4 + 4)
+            out["admm_consensus"] = P * (16 * sc + 8 * sg)
     return out
 
 
@@ -314,6 +320,8 @@ def run_ours(args, dist, rank, world):
     # ---- per-call durations (eager launches, events on the launching stream) ----------
     fused = tr.fused and D.one_view_per_block(tr.vb.plan)
     split = tr._split_xstep()
+    zf = tr._zfuse(True)        # the x-step stores the unshared copies into z, as in the graph
+    zargs = tr._zargs(zf)
     vb = tr.vb
     xs_args = (tr.x, tr.m, tr.v, tr.anchor, tr.shared, tr.rho, tr.lr)
 
@@ -322,19 +330,21 @@ def run_ours(args, dist, rank, world):
 
     calls = [("project", lambda: D.dg_project(tr.x, vb))]
     if split:       # the part that the graph runs on a side stream, timed here in sequence
-        calls.append(("xstep_idle", lambda: D.dg_xstep_part(1, vb, *xs_args, step=1, dev_step=tr.dev_step)))
+        calls.append(("xstep_idle", lambda: D.dg_xstep_part(1, vb, *xs_args, step=1, dev_step=tr.dev_step,
+                                                            **zargs)))
     calls += [("bin_sort", lambda: D.dg_bin_sort(vb)),
               ("rasterize_fwd", lambda: D.dg_rasterize_fwd(vb, tr.bg)),
               ("loss", lambda: tr._loss(tr.targets[tr.t % len(tr.view_sets)]))]
     if fused:       # compositing adjoint, then projection adjoint + x-step fused
         calls += [("rasterize_bwd", bwd_fused),
                   ("xstep", lambda: D.dg_xstep_part(2 if split else 0, vb, *xs_args, step=1,
-                                                    dev_step=tr.dev_step))]
+                                                    dev_step=tr.dev_step, **zargs))]
     else:
         calls += [("rasterize_bwd", lambda: D.dg_rasterize_bwd(vb, tr.x, tr.grad, bg=tr.bg)),
                   ("adam_admm_step", lambda: D.dg_adam_admm_step(*xs_args[:1], tr.grad, *xs_args[1:], step=1,
                                                                  dev_step=tr.dev_step))]
-    calls.append(("admm_consensus", lambda: D.dg_admm_consensus(tr.x, tr.u, tr.z, tr.anchor, tr.g_off, tr.g_copies,
+    zc = tr.z_shared() if zf else tr.z
+    calls.append(("admm_consensus", lambda: D.dg_admm_consensus(tr.x, tr.u, zc, tr.anchor, tr.g_off, tr.g_copies,
                                                                 tr.rho, tr.alpha, tr.residuals)))
     names = [n for n, _ in calls]
     acc = {n: 0.0 for n in names}
@@ -364,7 +374,7 @@ def run_ours(args, dist, rank, world):
     vis_rec = int(((rect[:, 0] & 0xFFFF) != (rect[:, 1] & 0xFFFF)).sum())
     instances = int(vb.count.item())
     _, active_groups = copy_groups(tr, rect)
-    alg = algorithmic_bytes(tr, vis_rec, vis_rec, active_groups if split else None)
+    alg = algorithmic_bytes(tr, vis_rec, vis_rec, active_groups if split else None, zf)
     peaks, peak_src = measured_peaks()
     hbm_peak = float(peaks["hbm_gbs"])
     kern = {}
@@ -473,6 +483,7 @@ def run_ours(args, dist, rank, world):
                        "xstep_split": (None if not split else
                                        {"idle_groups_on_side_stream": round(1.0 - float(active_groups.mean()), 3),
                                         "side_ctas_per_sm": tr.idle_ctas_per_sm}),
+                       "unshared_z_stored_by_xstep": bool(zf),
                        "l2": "working set > L2 (no flush needed)", "instances_per_step": instances,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "setup_s": round(setup_s, 1)},

@@ -262,14 +262,23 @@ int dg_xstep_from_records(const uint32_t* rect, const dg_camera* dev_cams, const
  * the projection, so it can run on another stream alongside binning,
  * compositing and the loss; `ctas` > 0 bounds its grid (a grid-stride loop
  * over the groups), so that it leaves most of each SM to the kernels beside
- * it; 0 = one CTA per group.  part 0 = the whole step.  Same arguments and
- * errors as dg_xstep_from_records; DG_ERR_INVALID for a part outside 0..2
- * or a negative ctas. */
+ * it; 0 = one CTA per group.  part 0 = the whole step.
+ * z_unshared (may be NULL): the global model of an iteration whose
+ * consensus follows; every copy with copy_shared[c] == 0 then also stores
+ * its stepped value at z_unshared[copy_gid[c]] (int32, device) -- the
+ * consensus's z = x for a global held by one block, taken in this pass, so
+ * that dg_admm_consensus can be given the shared globals alone (a z whose n
+ * counts them, when they come first in the global order).  copy_gid[c]
+ * must be < z_unshared->n for those copies.
+ * Same arguments and errors as dg_xstep_from_records; DG_ERR_INVALID for a
+ * part outside 0..2, a negative ctas, or z_unshared with another SH degree
+ * or without copy_gid / copy_shared. */
 int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
                   const float* drec, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v,
                   const dg_gaussians* anchor, const uint8_t* copy_shared, const float* rho,
                   const float* lr, float beta1, float beta2, float eps, int step,
-                  const int32_t* dev_step, void* stream);
+                  const int32_t* dev_step, dg_gaussians* z_unshared, const int32_t* copy_gid,
+                  void* stream);
 
 /* ---- ADMM (K9, K10) -------------------------------------------------------- */
 /* x-step (Eq. 8a / 12a): one Adam step on every local copy with gradient

@@ -95,7 +95,7 @@ _SIGS = {
     "dg_xstep_part": (C.c_int, [C.c_int, C.c_int, _vp, _vp, C.POINTER(DgPlan), _vp, C.POINTER(DgGaussians),
                                  C.POINTER(DgGaussians), C.POINTER(DgGaussians), C.POINTER(DgGaussians), _vp,
                                  C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float,
-                                 C.c_int, _vp, _vp]),
+                                 C.c_int, _vp, C.POINTER(DgGaussians), _vp, _vp]),
     "dg_step_advance": (C.c_int, [_vp, _vp]),
     "dg_scene_split": (C.c_int, [_vp, C.c_int64, C.c_int, _vp, _vp]),
     "dg_scene_assign": (C.c_int, [_vp, C.c_int64, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp]),

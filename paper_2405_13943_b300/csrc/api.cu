@@ -38,7 +38,7 @@ int launch_scale_duals(dg_gaussians*, const uint8_t*, const float*, cudaStream_t
 int launch_step_advance(int32_t*, cudaStream_t);
 int launch_xstep(int, int, dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*, const uint8_t*,
                  const dg_camera*, const dg_plan&, const uint2*, const float4*, const AdamArgs&, const int32_t*,
-                 cudaStream_t);
+                 dg_gaussians*, const int32_t*, cudaStream_t);
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -293,10 +293,11 @@ int dg_rasterize_bwd_records(const float* rec, const uint32_t* vals, const uint3
                              st);
 }
 
-int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan, const float* drec,
-                  dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
+int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                  const float* drec, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
                   const uint8_t* copy_shared, const float* rho, const float* lr, float beta1, float beta2, float eps,
-                  int step, const int32_t* dev_step, void* stream)
+                  int step, const int32_t* dev_step, dg_gaussians* z_unshared, const int32_t* copy_gid,
+                  void* stream)
 {
     if (part < 0 || part > 2 || ctas < 0) return DG_ERR_INVALID;
     if (!valid_plan(plan) || !valid_gauss(x) || !valid_gauss(m) || !valid_gauss(v)) return DG_ERR_INVALID;
@@ -304,6 +305,9 @@ int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev
     if (anchor && (!valid_gauss(anchor) || !same_layout(x, anchor))) return DG_ERR_INVALID;
     if (!rho || !lr || (!dev_step && step < 1) || ((uintptr_t)dev_step & 3u)) return DG_ERR_INVALID;
     if (x->n > 0 && anchor && !copy_shared) return DG_ERR_INVALID;
+    if (z_unshared && (!valid_gauss(z_unshared) || z_unshared->sh_degree != x->sh_degree ||
+                       (x->n > 0 && (!copy_gid || !copy_shared)) || ((uintptr_t)copy_gid & 3u)))
+        return DG_ERR_INVALID;
     if (plan->blk_off[plan->n_blocks] > x->n) return DG_ERR_INVALID;
     for (int k = 0; k < plan->n_blocks; k++)
         if (plan->blk_view_off[k + 1] - plan->blk_view_off[k] > 1) return DG_ERR_INVALID;   // one view per block
@@ -313,8 +317,9 @@ int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev
     for (int i = 0; i < 5; i++) a.rho[i] = rho[i];
     for (int i = 0; i < 6; i++) a.lr[i] = lr[i];
     a.b1 = beta1; a.b2 = beta2; a.eps = eps; a.step = step;
-    return launch_xstep(part, ctas, x, m, v, anchor, anchor ? copy_shared : nullptr, dev_cams, *plan, (const uint2*)rect,
-                        (const float4*)drec, a, dev_step, (cudaStream_t)stream);
+    return launch_xstep(part, ctas, x, m, v, anchor, (anchor || z_unshared) ? copy_shared : nullptr, dev_cams, *plan,
+                        (const uint2*)rect, (const float4*)drec, a, dev_step, z_unshared, copy_gid,
+                        (cudaStream_t)stream);
 }
 
 int dg_xstep_from_records(const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan, const float* drec,
@@ -323,7 +328,7 @@ int dg_xstep_from_records(const uint32_t* rect, const dg_camera* dev_cams, const
                           float eps, int step, const int32_t* dev_step, void* stream)
 {
     return dg_xstep_part(0, 0, rect, dev_cams, plan, drec, x, m, v, anchor, copy_shared, rho, lr, beta1, beta2, eps,
-                         step, dev_step, stream);
+                         step, dev_step, nullptr, nullptr, stream);
 }
 
 int dg_admm_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z, dg_gaussians* anchor,

@@ -475,11 +475,19 @@ __device__ __forceinline__ int64_t copy_record(int64_t c, int64_t n, const dg_pl
 
 // Adam + penalty on copy c's float4 fields (mean, opacity logit), rotation,
 // (log-scale, padding) with gradients gmu, go, gq, gs
+// ZOut: where an unshared copy's stepped value also goes (the consensus's
+// z = x for a global held by one block, taken here): z at the copy's global id
+struct ZOut {
+    GView z;
+    const int32_t* gid;   // NULL: no store
+};
+
 __device__ __forceinline__ void step_fields(GView& x, GView& m, GView& v, const GView& an, int64_t c, bool s,
                                             const float4& mo, const float4& q, const float4& sc, const float* gmu,
                                             float go, const float* gq, const float* gs, const AdamArgs& a,
-                                            float ic1, float ic2)
+                                            float ic1, float ic2, const ZOut& zo)
 {
+    const int64_t zg = (zo.gid != nullptr && !s) ? (int64_t)zo.gid[c] : -1;
     {
         float xs[4] = {mo.x, mo.y, mo.z, mo.w}, gg[4] = {gmu[0], gmu[1], gmu[2], go};
         const float4 mm = m.mo[c], vv = v.mo[c];
@@ -495,6 +503,7 @@ __device__ __forceinline__ void step_fields(GView& x, GView& m, GView& v, const 
         x.mo[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
         m.mo[c] = make_float4(ms[0], ms[1], ms[2], ms[3]);
         v.mo[c] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        if (zg >= 0) zo.z.mo[zg] = make_float4(xs[0], xs[1], xs[2], xs[3]);
     }
     {
         const float4 mm = m.quat[c], vv = v.quat[c];
@@ -510,6 +519,7 @@ __device__ __forceinline__ void step_fields(GView& x, GView& m, GView& v, const 
         x.quat[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
         m.quat[c] = make_float4(ms[0], ms[1], ms[2], ms[3]);
         v.quat[c] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        if (zg >= 0) zo.z.quat[zg] = make_float4(xs[0], xs[1], xs[2], xs[3]);
     }
     {
         const float4 mm = m.scale[c], vv = v.scale[c];
@@ -525,6 +535,7 @@ __device__ __forceinline__ void step_fields(GView& x, GView& m, GView& v, const 
         x.scale[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
         m.scale[c] = make_float4(ms[0], ms[1], ms[2], ms[3]);
         v.scale[c] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        if (zg >= 0) zo.z.scale[zg] = make_float4(xs[0], xs[1], xs[2], xs[3]);
     }
 }
 
@@ -537,7 +548,8 @@ __device__ __forceinline__ void step_fields(GView& x, GView& m, GView& v, const 
 template <int NK, int PB, bool ZERO>
 __device__ __forceinline__ void step_planes(GView& x, GView& m, GView& v, const GView& an,
                                             const uint8_t* __restrict__ shared, int64_t c0, const float* s_gc,
-                                            const float* s_Y, const AdamArgs& a, float ic1, float ic2)
+                                            const float* s_Y, const AdamArgs& a, float ic1, float ic2,
+                                            const ZOut& zo)
 {
     const int tid = threadIdx.x;
     const int quad = tid & 31;
@@ -550,6 +562,9 @@ __device__ __forceinline__ void step_planes(GView& x, GView& m, GView& v, const 
         sh[i] = act[i] && shared != nullptr && shared[cq + i] != 0;
     }
     const bool any_sh = sh[0] || sh[1] || sh[2] || sh[3];
+    int64_t zg[4];                                // global ids of the quad's unshared copies (-1: none)
+#pragma unroll
+    for (int i = 0; i < 4; i++) zg[i] = (zo.gid != nullptr && act[i] && !sh[i]) ? (int64_t)zo.gid[cq + i] : -1;
     constexpr int G = kXsThreads / 32;          // plane groups (4)
     for (int j0 = tid >> 5; j0 < 3 * NK; j0 += G * PB) {
         float4 xv[PB], mv[PB], vv[PB], av[PB];
@@ -589,6 +604,9 @@ __device__ __forceinline__ void step_planes(GView& x, GView& m, GView& v, const 
             reinterpret_cast<float4*>(x.sh)[u] = make_float4(xs[0], xs[1], xs[2], xs[3]);
             reinterpret_cast<float4*>(m.sh)[u] = make_float4(ms[0], ms[1], ms[2], ms[3]);
             reinterpret_cast<float4*>(v.sh)[u] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                if (zg[i] >= 0) zo.z.sh[(int64_t)j * zo.z.ld + zg[i]] = xs[i];
         }
     }
 }
@@ -600,7 +618,7 @@ __global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView
                                                         const dg_camera* __restrict__ cams, dg_plan plan,
                                                         const uint2* __restrict__ rect,
                                                         const float4* __restrict__ drec, AdamArgs a,
-                                                        const int32_t* __restrict__ dev_step)
+                                                        const int32_t* __restrict__ dev_step, ZOut zo)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
     __shared__ __align__(16) float s_gc[3][kXsThreads];
@@ -632,14 +650,14 @@ __global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView
             geometry_adjoint<DEG>(cam, mu, q, sc, drec[3 * r + 0], drec[3 * r + 1], plan.tile_w, plan.tile_h, gmu,
                                   gq, gs);
         }
-        step_fields(x, m, v, an, c, s, mo, q, sc, gmu, go, gq, gs, a, ic1, ic2);
+        step_fields(x, m, v, an, c, s, mo, q, sc, gmu, go, gq, gs, a, ic1, ic2, zo);
     }
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) s_gc[ch][tid] = gc[ch];
 #pragma unroll
     for (int kk = 0; kk < NK; kk++) s_Y[kk][tid] = Y[kk];
     __syncthreads();
-    step_planes<NK, 6, false>(x, m, v, an, shared, c0, &s_gc[0][0], &s_Y[0][0], a, ic1, ic2);
+    step_planes<NK, 6, false>(x, m, v, an, shared, c0, &s_gc[0][0], &s_Y[0][0], a, ic1, ic2, zo);
 }
 
 // the groups of k_xstep<PART 2>'s complement: no copy with a kept record, so
@@ -652,7 +670,7 @@ __global__ void __launch_bounds__(kXsThreads, 6) k_xstep_idle(GView x, GView m, 
                                                              const uint8_t* __restrict__ shared,
                                                              const dg_camera* __restrict__ cams, dg_plan plan,
                                                              const uint2* __restrict__ rect, AdamArgs a,
-                                                             const int32_t* __restrict__ dev_step)
+                                                             const int32_t* __restrict__ dev_step, ZOut zo)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
     const int tid = threadIdx.x;
@@ -674,21 +692,27 @@ __global__ void __launch_bounds__(kXsThreads, 6) k_xstep_idle(GView x, GView m, 
         if (c < x.n) {
             const bool s = shared != nullptr && shared[c] != 0;
             const float zero[4] = {0.f, 0.f, 0.f, 0.f};
-            step_fields(x, m, v, an, c, s, x.mo[c], x.quat[c], x.scale[c], zero, 0.f, zero, zero, a, ic1, ic2);
+            step_fields(x, m, v, an, c, s, x.mo[c], x.quat[c], x.scale[c], zero, 0.f, zero, zero, a, ic1, ic2,
+                        zo);
         }
-        step_planes<NK, 2, true>(x, m, v, an, shared, c0, nullptr, nullptr, a, ic1, ic2);
+        step_planes<NK, 2, true>(x, m, v, an, shared, c0, nullptr, nullptr, a, ic1, ic2, zo);
     }
 }
 
 // part 0: the whole step; 1: the groups without a kept record (drec unused;
-// `ctas` CTAs, 0 = one per group); 2: the groups with one
+// `ctas` CTAs, 0 = one per group); 2: the groups with one.  z / gid not NULL:
+// unshared copies also stored to z at their global ids.
 int launch_xstep(int part, int ctas, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
                  const uint8_t* shared, const dg_camera* cams, const dg_plan& plan, const uint2* rect,
-                 const float4* drec, const AdamArgs& a, const int32_t* dev_step, cudaStream_t st)
+                 const float4* drec, const AdamArgs& a, const int32_t* dev_step, dg_gaussians* z,
+                 const int32_t* gid, cudaStream_t st)
 {
     if (x->n == 0) return DG_OK;
     GView xv = gview(x), mv = gview(m), vv = gview(v);
     GView av = anchor ? gview(anchor) : xv;
+    ZOut zo;
+    zo.z = z ? gview(z) : xv;
+    zo.gid = z ? gid : nullptr;
     const int64_t n_groups = (x->n + kXsThreads - 1) / kXsThreads;
     dim3 grid((unsigned)n_groups);
     dim3 grid_idle((unsigned)(ctas > 0 && ctas < n_groups ? ctas : n_groups));
@@ -696,13 +720,13 @@ int launch_xstep(int part, int ctas, dg_gaussians* x, dg_gaussians* m, dg_gaussi
     case DEG:                                                                                                   \
         if (part == 0)                                                                                          \
             k_xstep<DEG, 0><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a,     \
-                                                         dev_step);                                             \
+                                                         dev_step, zo);                                         \
         else if (part == 2)                                                                                     \
             k_xstep<DEG, 2><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a,     \
-                                                         dev_step);                                             \
+                                                         dev_step, zo);                                         \
         else                                                                                                    \
             k_xstep_idle<DEG><<<grid_idle, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, a,      \
-                                                                dev_step);                                      \
+                                                                dev_step, zo);                                  \
         break;
     switch (x->sh_degree) {
     DG_XSTEP_CASE(0)

@@ -280,13 +280,16 @@ def dg_xstep_from_records(vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer, v
 def dg_xstep_part(part: int, vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer, v: GaussianBuffer,
                   anchor: Optional[GaussianBuffer], shared: Optional[torch.Tensor], rho, lr, beta1=0.9,
                   beta2=0.999, eps=1e-15, step=1, dev_step: Optional[torch.Tensor] = None, stream=None,
-                  ctas: int = 0) -> None:
+                  ctas: int = 0, z_unshared: Optional[GaussianBuffer] = None,
+                  gid: Optional[torch.Tensor] = None) -> None:
     """part 1: the x-step of the groups of copies without a kept record (after
     dg_project only; `ctas` > 0 bounds its grid); part 2: the rest (after
-    dg_rasterize_bwd_records); part 0: both (= dg_xstep_from_records)."""
+    dg_rasterize_bwd_records); part 0: both (= dg_xstep_from_records).
+    z_unshared / gid: also store every unshared copy's stepped value in z."""
     L.check(L.lib().dg_xstep_part(int(part), int(ctas), L.ptr(vb.rect), L.ptr(vb.dev_cams), C.byref(vb.plan), L.ptr(vb.drec),
                                   x.ref, m.ref, v.ref, None if anchor is None else anchor.ref, L.ptr(shared),
                                   L.floats(rho), L.floats(lr), beta1, beta2, eps, int(step), L.ptr(dev_step),
+                                  None if z_unshared is None else z_unshared.ref, L.ptr(gid),
                                   L.stream_handle(stream)), "dg_xstep_part")
 
 

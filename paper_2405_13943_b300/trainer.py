@@ -54,6 +54,13 @@ class DogsTrainer:
         self.overlap = overlap
         self.side = torch.cuda.Stream(device=device) if overlap and str(device).startswith("cuda") else None
         self._idle_queued = False
+        # globals held by several blocks numbered first: then, in an iteration
+        # with a consensus, the x-step stores the unshared copies' values into
+        # z itself and the consensus runs over the shared globals alone
+        cnt = np.diff(split.g_off)
+        ns = int(split.n_shared_globals)
+        self._shared_first = bool((cnt[:ns] > 1).all() and (cnt[ns:] <= 1).all())
+        self.n_shared_globals = ns
         # CTAs per SM of the side-stream part (a grid-stride loop), or 0 for
         # one CTA per group of copies.  Measured on the 6M-Gaussian step:
         # one per group 9.15 ms, 3 per SM 9.43, 2 per SM 10.03, 1 per SM
@@ -143,15 +150,16 @@ class DogsTrainer:
         vb.dev_cams.copy_(self.cam_pool[p], non_blocking=True)
         D.dg_step_advance(self.dev_step)
         D.dg_project(self.x, vb)
+        zf = self._zfuse(consensus)
         if self._split_xstep():
-            self.idle_xstep()
+            self.idle_xstep(zf)
         D.dg_bin_sort(vb)
         D.dg_rasterize_fwd(vb, self.bg)
         self._loss(self.targets[p] if target is None else target)
-        self.backward_step()
+        self.backward_step(zf)
         if consensus:
-            D.dg_admm_consensus(self.x, self.u, self.z, self.anchor, self.g_off, self.g_copies, self.rho,
-                                self.alpha, self.residuals)
+            D.dg_admm_consensus(self.x, self.u, self.z_shared() if zf else self.z, self.anchor, self.g_off,
+                                self.g_copies, self.rho, self.alpha, self.residuals)
         if self.host_targets is not None:
             self.host_loss[0 if slot is None else slot].copy_(vb.loss, non_blocking=True)
 
@@ -203,7 +211,17 @@ class DogsTrainer:
     def _split_xstep(self) -> bool:
         return self.side is not None and self.fused and D.one_view_per_block(self.vb.plan)
 
-    def idle_xstep(self) -> None:
+    def _zfuse(self, consensus: bool) -> bool:
+        return bool(consensus) and self.fused and self._shared_first and D.one_view_per_block(self.vb.plan)
+
+    def _zargs(self, zfuse: bool) -> dict:
+        return dict(z_unshared=self.z, gid=self.gid) if zfuse else {}
+
+    def z_shared(self) -> D.GaussianBuffer:
+        """z restricted to the shared globals (a view of the same memory)."""
+        return D.GaussianBuffer(self.n_shared_globals, self.z.deg, self.z.data.device, self.z.ld, self.z.data)
+
+    def idle_xstep(self, zfuse: bool = False) -> None:
         """Part 1 of the split x-step (the groups of copies without a kept
         record) on the side stream, after the work queued so far on the
         current stream (the projection)."""
@@ -211,26 +229,29 @@ class DogsTrainer:
         self.side.wait_stream(cur)
         with torch.cuda.stream(self.side):
             D.dg_xstep_part(1, self.vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,
-                            step=1, dev_step=self.dev_step, ctas=self.n_sm * self.idle_ctas_per_sm)
+                            step=1, dev_step=self.dev_step, ctas=self.n_sm * self.idle_ctas_per_sm,
+                            **self._zargs(zfuse))
         self._idle_queued = True
 
-    def backward_step(self) -> None:
+    def backward_step(self, zfuse: bool = False) -> None:
         """Adjoint of the iteration's render and the x-step (Eq. 8a / 12a).
         With at most one view per block the projection adjoint and the step
         run fused (the gradient stays in registers); otherwise through the
         gradient buffer.  With the split x-step, its second part here and the
-        side stream joined back."""
+        side stream joined back.  zfuse: the x-step also stores the unshared
+        copies into z (an iteration whose consensus then covers the shared
+        globals only)."""
         vb = self.vb
         if self._split_xstep() and self._idle_queued:
             D.dg_rasterize_bwd_records(vb, bg=self.bg)
             D.dg_xstep_part(2, vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,
-                            step=1, dev_step=self.dev_step)
+                            step=1, dev_step=self.dev_step, **self._zargs(zfuse))
             torch.cuda.current_stream().wait_stream(self.side)
             self._idle_queued = False
         elif self.fused and D.one_view_per_block(vb.plan):
             D.dg_rasterize_bwd_records(vb, bg=self.bg)
-            D.dg_xstep_from_records(vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,
-                                    step=1, dev_step=self.dev_step)
+            D.dg_xstep_part(0, vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,
+                            step=1, dev_step=self.dev_step, **self._zargs(zfuse))
         else:
             D.dg_rasterize_bwd(vb, self.x, self.grad, bg=self.bg)
             D.dg_adam_admm_step(self.x, self.grad, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,

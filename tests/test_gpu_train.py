@@ -359,3 +359,52 @@ def test_overlapped_xstep_trainer_matches(mods):
         for k in ga:
             assert rel_l2(ga[k], gb[k]) < REL_L2, (n, k)
     assert not a.overflowed()
+
+
+def test_xstep_stores_unshared_copies_into_z(mods):
+    """With z_unshared, the x-step's parts store every unshared copy's
+    stepped value at its global id (what the consensus's z = x would write)
+    and leave the shared globals of z alone; the trainer's consensus over the
+    shared globals then gives the z of the full consensus."""
+    D, srv, T = mods
+    wl, z0, targets = small_setup(D, srv, seed=31)
+    kw = dict(rho=(1e-2,) * 5, loss="dssim", intv=1)
+    tr = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, **kw)
+    tr.calibrate_capacity()
+    assert tr._shared_first and tr._zfuse(True)
+    tr.step(graph=False)
+    vb = tr.vb
+    vb.dev_cams.copy_(tr.cam_pool[tr.t % len(tr.view_sets)])
+    D.dg_project(tr.x, vb)
+    D.dg_bin_sort(vb)
+    D.dg_rasterize_fwd(vb, tr.bg)
+    tr._loss(tr.targets[tr.t % len(tr.view_sets)])
+    D.dg_rasterize_bwd_records(vb, bg=tr.bg)
+    torch.cuda.synchronize()
+    args = (tr.anchor, tr.shared, tr.rho, tr.lr)
+    z_before = tr.z.clone()
+    x1, m1, v1 = tr.x.clone(), tr.m.clone(), tr.v.clone()
+    D.dg_xstep_part(1, vb, x1, m1, v1, *args, step=2, z_unshared=tr.z, gid=tr.gid)
+    D.dg_xstep_part(2, vb, x1, m1, v1, *args, step=2, z_unshared=tr.z, gid=tr.gid)
+    torch.cuda.synchronize()
+    xs, zs, zb = groups(x1), groups(tr.z), groups(z_before)
+    sh = wl.split.copy_shared().astype(bool)
+    gid = wl.split.copy_gid
+    ns = int(wl.split.n_shared_globals)
+    for k in xs:
+        np.testing.assert_array_equal(zs[k][gid[~sh]], xs[k][~sh])
+        np.testing.assert_array_equal(zs[k][:ns], zb[k][:ns])
+    # trainer: consensus over the shared globals after the fused store equals the full consensus
+    a = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, **kw)
+    b = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, **kw)
+    b._shared_first = False
+    for t_ in (a, b):
+        t_.calibrate_capacity()
+    for _ in range(3):
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    for n in ("z", "x", "u"):
+        ga, gb = groups(getattr(a, n)), groups(getattr(b, n))
+        for k in ga:
+            assert rel_l2(ga[k], gb[k]) < REL_L2, (n, k)
