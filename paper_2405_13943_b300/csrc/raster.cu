@@ -87,6 +87,16 @@ __device__ __forceinline__ float strip_q(const Strip& s, int k)
     return __fmaf_rn(__fmaf_rn(s.C, dy, s.Bdx), dy, s.E0);
 }
 
+// the same with the row offset k dy given (k dy is exact, so dy0 - off rounds
+// exactly as the fused multiply-add above); an offset of -kDeadRow moves a
+// pixel so far from every instance that it fails q >= -8
+constexpr float kDeadRow = 1e15f;
+__device__ __forceinline__ float strip_q_off(const Strip& s, float off)
+{
+    const float dy = __fsub_rn(s.dy0, off);
+    return __fmaf_rn(__fmaf_rn(s.C, dy, s.Bdx), dy, s.E0);
+}
+
 template <int PPL>
 __device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float B, float C, float lo, float fx,
                                              float fy0, float ddy)
@@ -161,13 +171,20 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
     TileInfo ti;
     tile_info(cams, n_views, blockIdx.x, tw, th, ranges, ti);
     const LaneGeom G = lane_geom(ti, tw, tid, NT);
-    float T[PPL], C0[PPL], C1[PPL], C2[PPL];
+    float T[PPL], C0[PPL], C1[PPL], C2[PPL], off[PPL];
     uint32_t last[PPL];
     uint32_t live = 0;   // bit k: pixel k inside the image and not yet stopped
+    // row offset of pixel k, or -kDeadRow once it is outside the image or
+    // stopped: a dead pixel then fails the first test like a distant one,
+    // with no per-pixel live test in the loop
 #pragma unroll
     for (int k = 0; k < PPL; k++) {
         T[k] = 1.f; C0[k] = C1[k] = C2[k] = 0.f; last[k] = 0;
-        if (G.px < ti.W && G.py0 + k * G.dpy < ti.H) live |= 1u << k;
+        off[k] = -kDeadRow;
+        if (G.px < ti.W && G.py0 + k * G.dpy < ti.H) {
+            live |= 1u << k;
+            off[k] = (float)k * G.dy;
+        }
     }
     const uint32_t n = ti.end - ti.start;
     Fetch nx[S];
@@ -198,14 +215,13 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
             const float4 c = s_c[j];
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
-                if (!(live >> k & 1u)) continue;
-                const float q = strip_q(sp, k);
+                const float q = strip_q_off(sp, off[k]);
                 if (!(q >= -8.0f)) continue;
                 float raw;
                 const float a = strip_alpha(q, h.y, raw);
                 if (a == 0.f) continue;
                 const float Tn = T[k] * (1.f - a);
-                if (Tn < kTMin) { live &= ~(1u << k); continue; }
+                if (Tn < kTMin) { live &= ~(1u << k); off[k] = -kDeadRow; continue; }
                 const float wt = a * T[k];
                 C0[k] = fmaf(c.x, wt, C0[k]);
                 C1[k] = fmaf(c.y, wt, C1[k]);
