@@ -70,27 +70,41 @@ __global__ void k_loss_final(const dg_camera* __restrict__ cams, int n_views, fl
 // registers, so each input is read from shared memory once per pass.
 constexpr int kTW = 32;                 // output tile width
 constexpr int kTH = 54;                 // output tile height
-constexpr int kIW = kTW + 2 * kR;       // input tile width (42)
 constexpr int kIH = kTH + 2 * kR;       // input tile height (64)
 constexpr int kBlk = 8;                 // outputs per thread per pass
 constexpr int kWin8 = kBlk + 2 * kR;    // 18 inputs per 8 outputs
 constexpr int kSsimThreads = 256;
-// shared-memory row strides, odd so that the passes' access patterns are
-// free of bank conflicts (8 rows x 4 column blocks per warp in the
-// horizontal pass, 32 consecutive columns in the vertical pass)
-constexpr int kIWP = kIW + 1;           // 43
-constexpr int kTWP = kTW + 1;           // 33
+// The input rows are staged from global column x0 - 8 (16-byte aligned when
+// the image width is a multiple of 4) over 48 columns, 12 chunks of four;
+// tile column c (global x0 - 5 + c) sits at staged column c + 3.  Row stride
+// 52 floats: a multiple of four for the 16-byte copies, and with it the
+// horizontal pass's 16-byte reads (two rows x four column blocks per
+// quarter-warp) fall in distinct banks.
+constexpr int kIWv = 48;                // staged columns
+constexpr int kIWP = 52;                // staged row stride
+constexpr int kTWP = kTW + 1;           // 33: horizontal-pass output stride (odd: conflict-free columns)
 constexpr int kVBlocks = (kTH + kBlk - 1) / kBlk;   // 7 row blocks in the vertical pass
+constexpr int kTHP = kVBlocks * kBlk + 2 * kR;      // 66 rows of horizontal output read by the vertical pass
 
 // horizontal pass over NM maps, one task per thread: input row r = tid / 4,
-// output columns c0 .. c0 + 7 with c0 = 8 (tid % 4): tmp[m][r][c] = sum_k w_k in_m[r][c + k]
-template <int NM, typename Load>
-__device__ __forceinline__ void hpass(const Win& g, float (*tmp)[kIH][kTWP], Load load)
+// output columns c0 .. c0 + 7 with c0 = 8 (tid % 4): tmp[m][r][c] = sum_k w_k in_m[r][c + k].
+// The 18 inputs of the task are staged columns c0 + 3 .. c0 + 20, read as six
+// 16-byte chunks (staged columns c0 .. c0 + 23).
+template <int NM, int NIN, typename Make>
+__device__ __forceinline__ void hpass(const Win& g, const float* const* in_maps, float (*tmp)[kTHP][kTWP], Make make)
 {
     const int r = threadIdx.x >> 2, c0 = (threadIdx.x & 3) * kBlk;
+    float raw[NIN][24];
+#pragma unroll
+    for (int n = 0; n < NIN; n++)
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+            const float4 v = *reinterpret_cast<const float4*>(in_maps[n] + r * kIWP + c0 + 4 * q);
+            raw[n][4 * q] = v.x; raw[n][4 * q + 1] = v.y; raw[n][4 * q + 2] = v.z; raw[n][4 * q + 3] = v.w;
+        }
     float in[NM][kWin8];
 #pragma unroll
-    for (int i = 0; i < kWin8; i++) load(r, c0 + i, in, i);
+    for (int i = 0; i < kWin8; i++) make(raw, 3 + i, in, i);
 #pragma unroll
     for (int m = 0; m < NM; m++)
 #pragma unroll
@@ -103,16 +117,16 @@ __device__ __forceinline__ void hpass(const Win& g, float (*tmp)[kIH][kTWP], Loa
 }
 
 // vertical pass: out[m][j] = sum_k w_k tmp[m][r0 + j + k][c] for column c and
-// rows r0 .. r0 + 7 (rows past the tile's input are read as the last row and
-// never stored)
+// rows r0 .. r0 + 7 (rows past the tile's input are read from the padding
+// rows and never stored)
 template <int NM>
-__device__ __forceinline__ void vpass(const Win& g, float (*tmp)[kIH][kTWP], int c, int r0, float out[][kBlk])
+__device__ __forceinline__ void vpass(const Win& g, float (*tmp)[kTHP][kTWP], int c, int r0, float out[][kBlk])
 {
 #pragma unroll
     for (int m = 0; m < NM; m++) {
         float col[kWin8];
 #pragma unroll
-        for (int i = 0; i < kWin8; i++) col[i] = tmp[m][min(r0 + i, kIH - 1)][c];
+        for (int i = 0; i < kWin8; i++) col[i] = tmp[m][r0 + i][c];
 #pragma unroll
         for (int j = 0; j < kBlk; j++) {
             float s = 0.f;
@@ -132,6 +146,11 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok)
 {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool ok)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -158,20 +177,39 @@ __device__ __forceinline__ SsimItem ssim_item(const dg_camera* __restrict__ cams
     return it;
 }
 
-// copy NP planes (plane m at base + m * plane_stride) of item `it`'s input halo into dst[m][kIH][kIWP]
+// copy NP planes (plane m at base[m] + m * plane_stride) of item `it`'s
+// input rows, global columns x0 - 8 .. x0 + 39, into dst[m][kIH][kIWP]: by
+// 16-byte chunks when the width and the planes allow it (a chunk is then
+// wholly inside or wholly outside the image), else element by element
 template <int NP>
 __device__ __forceinline__ void ssim_issue(const SsimItem& it, const float* const* base, int64_t plane_stride,
                                            float* dst)
 {
     if (!it.ok) return;
-    for (int i = threadIdx.x; i < kIH * kIW; i += kSsimThreads) {
-        const int r = i / kIW, c = i - r * kIW;
-        const int gx = it.x0 + c - kR, gy = it.y0 + r - kR;
-        const bool ok = gx >= 0 && gx < it.W && gy >= 0 && gy < it.H;
-        const int64_t p = ok ? (int64_t)gy * it.W + gx : 0;
+    const int gx0 = it.x0 - 8, gy0 = it.y0 - kR;
+    bool vec = (it.W & 3) == 0;
 #pragma unroll
-        for (int m = 0; m < NP; m++)
-            cp_async4(dst + (m * kIH + r) * kIWP + c, base[m] + m * plane_stride + p, ok);
+    for (int m = 0; m < NP; m++) vec = vec && (((uintptr_t)(base[m] + m * plane_stride) & 15u) == 0);
+    if (vec) {
+        constexpr int CH = kIWv / 4;
+        for (int i = threadIdx.x; i < NP * kIH * CH; i += kSsimThreads) {
+            const int m = i / (kIH * CH), rem = i - m * (kIH * CH);
+            const int r = rem / CH, q = rem - r * CH;
+            const int gx = gx0 + 4 * q, gy = gy0 + r;
+            const bool ok = gx >= 0 && gx < it.W && gy >= 0 && gy < it.H;
+            const float* src = base[m] + m * plane_stride + (ok ? (int64_t)gy * it.W + gx : 0);
+            cp_async16(dst + (m * kIH + r) * kIWP + 4 * q, src, ok);
+        }
+    } else {
+        for (int i = threadIdx.x; i < kIH * kIWv; i += kSsimThreads) {
+            const int r = i / kIWv, c = i - r * kIWv;
+            const int gx = gx0 + c, gy = gy0 + r;
+            const bool ok = gx >= 0 && gx < it.W && gy >= 0 && gy < it.H;
+            const int64_t p = ok ? (int64_t)gy * it.W + gx : 0;
+#pragma unroll
+            for (int m = 0; m < NP; m++)
+                cp_async4(dst + (m * kIH + r) * kIWP + c, base[m] + m * plane_stride + p, ok);
+        }
     }
 }
 
@@ -182,7 +220,7 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restri
 {
     extern __shared__ float s_dyn[];
     float* s_in = s_dyn;                                   // [2 buffers][x, y][kIH][kIWP]
-    float (*s_tmp)[kIH][kTWP] = reinterpret_cast<float (*)[kIH][kTWP]>(s_dyn + 4 * kIH * kIWP);
+    float (*s_tmp)[kTHP][kTWP] = reinterpret_cast<float (*)[kTHP][kTWP]>(s_dyn + 4 * kIH * kIWP);
     __shared__ float s_w[kSsimThreads / 32];
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
     int buf = 0;
@@ -207,10 +245,9 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restri
         __syncthreads();
         const SsimItem it = ssim_item(cams, w, TX, TY);
         if (!it.ok) continue;                         // uniform over the CTA
-        const float (*s_x)[kIWP] = reinterpret_cast<const float (*)[kIWP]>(s_in + buf * 2 * kIH * kIWP);
-        const float (*s_y)[kIWP] = reinterpret_cast<const float (*)[kIWP]>(s_in + (buf * 2 + 1) * kIH * kIWP);
-        hpass<5>(g, s_tmp, [&](int r, int c, float (*in)[kWin8], int i) {
-            const float a = s_x[r][c], b = s_y[r][c];
+        const float* maps[2] = {s_in + buf * 2 * kIH * kIWP, s_in + (buf * 2 + 1) * kIH * kIWP};
+        hpass<5, 2>(g, maps, s_tmp, [&](float (*raw)[24], int c, float (*in)[kWin8], int i) {
+            const float a = raw[0][c], b = raw[1][c];
             in[0][i] = a; in[1][i] = b; in[2][i] = a * a; in[3][i] = b * b; in[4][i] = a * b;
         });
         __syncthreads();
@@ -255,8 +292,8 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restri
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-constexpr size_t kSsimFwdSmem = sizeof(float) * (4 * kIH * kIWP + 5 * kIH * kTWP);
-constexpr size_t kSsimBwdSmem = sizeof(float) * (6 * kIH * kIWP + 3 * kIH * kTWP);
+constexpr size_t kSsimFwdSmem = sizeof(float) * (4 * kIH * kIWP + 5 * kTHP * kTWP);
+constexpr size_t kSsimBwdSmem = sizeof(float) * (6 * kIH * kIWP + 3 * kTHP * kTWP);
 
 // dL/dx = w_l1 sign(x - y) / N + F(a) + 2 x F(b) + y F(c); the L1 sum of the
 // tile is added to l1_sum[v].  The output pixels' x and y are loaded before the
@@ -268,7 +305,7 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const float* __restri
 {
     extern __shared__ float s_dyn[];
     float* s_in = s_dyn;                                   // [2 buffers][3 maps][kIH][kIWP]
-    float (*s_tmp)[kIH][kTWP] = reinterpret_cast<float (*)[kIH][kTWP]>(s_dyn + 6 * kIH * kIWP);
+    float (*s_tmp)[kTHP][kTWP] = reinterpret_cast<float (*)[kTHP][kTWP]>(s_dyn + 6 * kIH * kIWP);
     __shared__ float s_w[kSsimThreads / 32];
     const bool has_out = threadIdx.x < kTW * kVBlocks;
     const int c = threadIdx.x % kTW, r0 = (threadIdx.x / kTW) * kBlk;
@@ -309,9 +346,10 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const float* __restri
         cp_async_wait_prev();
         __syncthreads();
         if (!it.ok) continue;                         // uniform over the CTA
-        const float (*s_p)[kIH][kIWP] = reinterpret_cast<const float (*)[kIH][kIWP]>(s_in + buf * 3 * kIH * kIWP);
-        hpass<3>(g, s_tmp, [&](int r, int cc, float (*in)[kWin8], int i) {
-            in[0][i] = s_p[0][r][cc]; in[1][i] = s_p[1][r][cc]; in[2][i] = s_p[2][r][cc];
+        const float* sp0 = s_in + buf * 3 * kIH * kIWP;
+        const float* maps[3] = {sp0, sp0 + kIH * kIWP, sp0 + 2 * kIH * kIWP};
+        hpass<3, 3>(g, maps, s_tmp, [&](float (*raw)[24], int c, float (*in)[kWin8], int i) {
+            in[0][i] = raw[0][c]; in[1][i] = raw[1][c]; in[2][i] = raw[2][c];
         });
         __syncthreads();
         float acc = 0.f;

@@ -181,25 +181,33 @@ def check_counts(D, O, vb, f, masks, plan, bg):
         assert abs(counts[0] - seen) <= 1e-3 * seen and abs(counts[1] - used) <= 1e-3 * used
 
 
-def test_losses_match_oracle(D, oracle):
+# (width, height) per view: odd widths and offsets take the element-wise
+# staging of the D-SSIM passes; widths and plane offsets that are multiples of
+# four take the 16-byte copies (views 0 and 1 of the second set)
+LOSS_VIEWS = [[(75, 41), (40, 64)], [(64, 48), (40, 64), (75, 41), (132, 70)]]
+
+
+@pytest.mark.parametrize("sizes", LOSS_VIEWS)
+def test_losses_match_oracle(D, oracle, sizes):
     O = oracle
-    cams = [S.cube_camera(75, 41), S.cube_camera(40, 64)]
+    cams = [S.cube_camera(w, h) for w, h in sizes]
+    nv = len(cams)
     vb = D.ViewBatch(cams, [0, 0], 16, 16, loss_ws=True)
     imgs = [S.random_image(7 + v, c.height, c.width) for v, c in enumerate(cams)]
     tgts = [np.clip(im + S.random_like(20 + v, im.shape, 0.2), 0, 1) for v, im in enumerate(imgs)]
     target = torch.zeros_like(vb.image)
-    for v in range(2):
+    for v in range(nv):
         vb.view_image(v).copy_(torch.from_numpy(imgs[v]))
         vb.view_image(v, target).copy_(torch.from_numpy(tgts[v]))
     D.dg_loss_l1(vb, target, 1.0)
     torch.cuda.synchronize()
-    for v in range(2):
+    for v in range(nv):
         L1, g1 = O.l1(imgs[v], tgts[v])
         assert vb.loss[v].item() == pytest.approx(L1, rel=1e-5)
         assert rel_l2(vb.view_image(v, vb.dL_dimage).cpu().numpy(), g1) < 1e-6
     D.dg_loss_dssim(vb, target, 0.8, 0.2)
     torch.cuda.synchronize()
-    for v in range(2):
+    for v in range(nv):
         Ld, gd = O.dssim_loss(imgs[v], tgts[v], 0.2)
         assert vb.loss[v].item() == pytest.approx(Ld, rel=1e-5)
         assert rel_l2(vb.view_image(v, vb.dL_dimage).cpu().numpy(), gd) < REL_L2
