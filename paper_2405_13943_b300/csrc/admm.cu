@@ -228,8 +228,11 @@ __device__ __noinline__ void cons_generic(GView x, GView u, GView z, GView an, i
     }
 }
 
+#ifndef DG_CONS_CTAS
+#define DG_CONS_CTAS 6   // 80 registers: 24 warps per SM (measured best of 1, 6, 8)
+#endif
 template <int NP>
-__global__ void __launch_bounds__(128) k_consensus(GView x, GView u, GView z, GView an,
+__global__ void __launch_bounds__(128, DG_CONS_CTAS) k_consensus(GView x, GView u, GView z, GView an,
                                                    const int64_t* __restrict__ g_off,
                                                    const int32_t* __restrict__ g_copies, int64_t n_glob,
                                                    ConsArgs a, double* __restrict__ res)

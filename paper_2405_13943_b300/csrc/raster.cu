@@ -296,8 +296,11 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float* v, float& v8,
 // register budget: 24 resident single-warp CTAs per SM for NW = 1; for the
 // wider variants 32 warps per SM with one staged instance per thread and 24
 // with two (the budgets that compile without spilling)
+#ifndef DG_BWD_CTAS_1W
+#define DG_BWD_CTAS_1W 24   // measured best of 20, 24, 28
+#endif
 template <int NW, int S>
-constexpr int bwd_min_blocks() { return NW == 1 ? 24 : (S == 1 ? 32 : 24) / NW; }
+constexpr int bwd_min_blocks() { return NW == 1 ? DG_BWD_CTAS_1W : (S == 1 ? 32 : 24) / NW; }
 
 template <int NW, int S>
 __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd(const float4* __restrict__ rec,
