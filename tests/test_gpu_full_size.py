@@ -1,8 +1,9 @@
 """Parity at the benchmark's full size, in its launch configuration.
 
 The 6M-Gaussian, K = 8 workload with eight 1920x1080 views is rendered on
-the GPU exactly as bench.py times it: 16x16 tiles, forward compositing with
-2 warps per tile, backward with 1, the fused adjoint + x-step.  The FP64
+the GPU as bench.py times it: 16x16 or 8x32 tiles (the two shapes its
+autotuner picks between on this workload), forward compositing with 2 warps
+per tile, backward with 1, the fused adjoint + x-step.  The FP64
 oracle renders two of the eight views completely (projection of the view's
 block, binning, compositing) and differentiates them; the test compares
 every pixel of those views, their tile ranges and `last`, and the gradient of
@@ -34,7 +35,7 @@ THR = 1e-3
 
 
 @pytest.fixture(scope="module")
-def full():
+def workload():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import bench
@@ -47,23 +48,32 @@ def full():
     z0 = D.GaussianBuffer.from_synth(wl.z0)
     gid = torch.from_numpy(wl.split.copy_gid.astype(np.int32)).cuda()
     x = T.gather_copies(z0, gid)
+    return O, D, wl, z0, x
+
+
+@pytest.fixture(scope="module", params=[(16, 16), (8, 32)], ids=["16x16", "8x32"])
+def full(workload, request):
+    O, D, wl, z0, x = workload
+    tw, th = request.param
     D.set_raster_variant(2, 1, 1, 1)
     try:
-        vb = D.ViewBatch(wl.views[0], wl.split.blk_off, 16, 16)
+        vb = D.ViewBatch(wl.views[0], wl.split.blk_off, tw, th)
     finally:
         D.set_raster_variant(4, 2)
     D.forward(x, vb, (0.0, 0.0, 0.0))
     torch.cuda.synchronize()
-    return O, D, wl, z0, x, vb
+    yield O, D, wl, z0, x, vb
+    del vb
+    torch.cuda.empty_cache()
 
 
-def oracle_view(O, wl, v, deg=3):
+def oracle_view(O, wl, v, tile, deg=3):
     cam = wl.views[0][v]
     k = cam.block
     b, e = int(wl.split.blk_off[k]), int(wl.split.blk_off[k + 1])
     copies = wl.z0.subset(wl.split.copy_gid[b:e])
     xo = O.params_from(copies)
-    plan = O.ViewPlan([cam], [(0, e - b)], 16, 16)
+    plan = O.ViewPlan([cam], [(0, e - b)], tile[0], tile[1])
     f = O.render(xo, deg, plan, (0.0, 0.0, 0.0))
     return cam, (b, e), xo, plan, f
 
@@ -73,7 +83,8 @@ def tile_lists(vb, v, f, plan):
     record numbers in (depth, record) order).  Returns the mask of tiles
     whose lists differ and the records that make the difference."""
     cam = plan.cams[0]
-    n_t = plan.tiles_x[0] * ((cam.height + 15) // 16)
+    th = vb.plan.tile_h
+    n_t = plan.tiles_x[0] * ((cam.height + th - 1) // th)
     t0 = vb.host_cams[v].tile_off
     rg = vb.ranges.cpu().numpy().view(np.uint32)[2 * t0:2 * (t0 + n_t)].reshape(-1, 2).astype(np.int64)
     org = f["bins"]["ranges"].reshape(-1, 2).astype(np.int64)
@@ -89,10 +100,16 @@ def tile_lists(vb, v, f, plan):
     return diff.reshape(-1, plan.tiles_x[0]), np.array(sorted(odd), np.int64)
 
 
+def tile_pixels(vb, bad, H, W):
+    """The per-pixel mask of the tiles flagged in bad."""
+    return np.repeat(np.repeat(bad, vb.plan.tile_h, 0), vb.plan.tile_w, 1)[:H, :W]
+
+
 def test_full_size_forward_matches_oracle(full):
     O, D, wl, z0, x, vb = full
+    tile = (vb.plan.tile_w, vb.plan.tile_h)
     for v in VIEWS:
-        cam, (b, e), xo, plan, f = oracle_view(O, wl, v)
+        cam, (b, e), xo, plan, f = oracle_view(O, wl, v, tile)
         ov = f["views"][0]
         bad, odd = tile_lists(vb, v, f, plan)
         # lists may differ only by records whose projection decisions (tile
@@ -100,7 +117,7 @@ def test_full_size_forward_matches_oracle(full):
         assert np.all(f["proj"]["margin"][odd] < THR), odd[f["proj"]["margin"][odd] >= THR][:10]
         assert bad.mean() < 0.02, bad.mean()
         H, W = cam.height, cam.width
-        badpix = np.repeat(np.repeat(bad, 16, 0), 16, 1)[:H, :W]
+        badpix = tile_pixels(vb, bad, H, W)
         m = (ov["margin"] >= THR) & ~badpix
         assert m.mean() > 0.95, m.mean()
         img = vb.view_image(v).cpu().numpy()
@@ -122,12 +139,13 @@ def test_full_size_fused_xstep_matches_oracle(full):
     rng = np.random.default_rng(9)
     dimg = torch.zeros_like(vb.image)
     per_view = {}
+    tile = (vb.plan.tile_w, vb.plan.tile_h)
     for v in VIEWS:
-        cam, (b, e), xo, plan, f = oracle_view(O, wl, v)
+        cam, (b, e), xo, plan, f = oracle_view(O, wl, v, tile)
         ov = f["views"][0]
         bad, _ = tile_lists(vb, v, f, plan)
         H, W = cam.height, cam.width
-        badpix = np.repeat(np.repeat(bad, 16, 0), 16, 1)[:H, :W]
+        badpix = tile_pixels(vb, bad, H, W)
         gm = (ov["margin"] >= THR) & (ov["margin_grad"] >= THR) & ~badpix
         Wv = rng.uniform(-1, 1, (3, H, W)) * gm[None] * 1e-3
         vb.view_image(v, dimg).copy_(torch.from_numpy(Wv.astype(np.float32)))
@@ -153,12 +171,12 @@ def test_full_size_fused_xstep_matches_oracle(full):
             assert r <= 1e-3, (v, name, r)
 
 
-def test_full_size_consensus_sampled(full):
+def test_full_size_consensus_sampled(workload):
     """The consensus over all 6.63M copies (over-relaxed, alpha = 1.6), with
     perturbed copies and duals on the shared ones; 3,000 sampled globals
     (shared and unshared) are recomputed by the oracle from their copies
     alone: z, and u and the anchor of each of their copies."""
-    O, D, wl, z0, x, vb = full
+    O, D, wl, z0, x = workload
     sp = wl.split
     n_c = sp.n_copies
     rng = np.random.default_rng(12)
