@@ -303,10 +303,13 @@ int dg_adam_admm_step(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m,
  *   z    = (1/n_i) sum_k (xh_k + u_k)    (complete form of Eq. 8b)
  *   u_k += xh_k - z                      (Eq. 8c)
  *   anchor_k = z - u_k                   (for the next x-steps)
- * A global held by one block gets z = x.  residuals (device double[10], may
- * be NULL, overwritten): per group the squared primal residual
- * sum ||x_k - z||^2 (0..4) and squared dual residual rho^2 n_i ||z - z_prev||^2
- * (5..9), shared globals only (Eq. 9). */
+ * A global held by one block gets z = x.  The globals processed are the
+ * first z->n of the CSR: a caller whose x-step already stored the unshared
+ * globals (dg_xstep_part with z_unshared) and numbers the shared globals
+ * first passes a z whose n counts the shared ones (the same memory).
+ * residuals (device double[10], may be NULL, overwritten): per group the
+ * squared primal residual sum ||x_k - z||^2 (0..4) and squared dual residual
+ * rho^2 n_i ||z - z_prev||^2 (5..9), shared globals only (Eq. 9). */
 int dg_admm_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z,
                       dg_gaussians* anchor, const int64_t* g_off, const int32_t* g_copies,
                       const float* rho, float alpha, double* residuals, void* stream);
