@@ -68,12 +68,15 @@ WORKLOADS = {
 
 
 def dist_setup():
+    """One process per GPU under torchrun (replicas: every rank runs the whole
+    workload on its own GPU; the only collectives are the timing barrier and
+    the max over ranks).  NCCL with GPUs, gloo without (the CPU tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         return dist, rank, ws
     return None, 0, 1
 
@@ -87,7 +90,8 @@ def max_over_ranks(dist, v: float) -> float:
     if dist is None:
         return v
     import torch
-    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], device=dev, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
