@@ -68,7 +68,7 @@ size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity) { return bin_ws_layo
 // edge's unconstrained minimiser clamped to the edge.  Rounding is pinned
 // (no contraction) so that the count and the scatter decide alike.
 struct CullRec {
-    float mx, my, a, b, c, tau;
+    float mx, my, a, b, c, tau, b_c, b_a;   // b_c = b / c, b_a = b / a: one division each per record
 };
 
 __device__ __forceinline__ CullRec cull_rec(const float4* __restrict__ rec, int64_t r)
@@ -77,13 +77,16 @@ __device__ __forceinline__ CullRec cull_rec(const float4* __restrict__ rec, int6
     CullRec k;
     k.mx = g0.x; k.my = g0.y; k.a = g0.z; k.b = g0.w; k.c = g1.x;
     k.tau = __fmaf_rn(__fmul_rn(2.f, __logf(__fmul_rn(255.f, g1.y))), 1.f + 1.f / 1024.f, 1.f / 64.f);
+    k.b_c = __fdiv_rn(k.b, k.c);
+    k.b_a = __fdiv_rn(k.b, k.a);
     return k;
 }
 
-// minimum over t in [lo, hi] of a X^2 + 2 b X t + c t^2
-__device__ __forceinline__ float edge_qmin(float a, float b, float c, float X, float lo, float hi)
+// minimum over t in [lo, hi] of a X^2 + 2 b X t + c t^2 (b_c = b / c: the
+// unconstrained minimiser is -X b / c)
+__device__ __forceinline__ float edge_qmin(float a, float b, float c, float b_c, float X, float lo, float hi)
 {
-    const float t = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, X), c), lo), hi);
+    const float t = fminf(fmaxf(-__fmul_rn(X, b_c), lo), hi);
     return __fmaf_rn(__fmul_rn(c, t), t, __fmul_rn(X, __fmaf_rn(__fmul_rn(2.f, b), t, __fmul_rn(a, X))));
 }
 
@@ -94,8 +97,9 @@ __device__ __forceinline__ bool tile_reached(const CullRec& k, uint32_t tx, uint
     const float Y0 = __fsub_rn(__fadd_rn((float)(ty * th), 0.5f), k.my);
     const float Y1 = __fsub_rn(__fsub_rn((float)(ty * th + th), 0.5f), k.my);
     if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return 0.f <= k.tau;
-    const float m = fminf(fminf(edge_qmin(k.a, k.b, k.c, X0, Y0, Y1), edge_qmin(k.a, k.b, k.c, X1, Y0, Y1)),
-                          fminf(edge_qmin(k.c, k.b, k.a, Y0, X0, X1), edge_qmin(k.c, k.b, k.a, Y1, X0, X1)));
+    const float qx = fminf(edge_qmin(k.a, k.b, k.c, k.b_c, X0, Y0, Y1), edge_qmin(k.a, k.b, k.c, k.b_c, X1, Y0, Y1));
+    const float qy = fminf(edge_qmin(k.c, k.b, k.a, k.b_a, Y0, X0, X1), edge_qmin(k.c, k.b, k.a, k.b_a, Y1, X0, X1));
+    const float m = fminf(qx, qy);
     return m <= k.tau;
 }
 
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(256) k_expand(const uint2* __restrict__ rect, 
     const int lane = threadIdx.x & 31;
     if (SCATTER && (int64_t)(*dev_count) > capacity) return;   // uniform over the grid
     uint32_t x0 = 0, y0 = 0, w = 0, n = 0, toff = 0, TX = 0, dbits = 0;
-    CullRec k = {0.f, 0.f, 0.f, 0.f, 0.f, -1.f};
+    CullRec k = {0.f, 0.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f};
     if (r < n_rec) {
         const uint2 rr = rect[r];
         x0 = rr.x & 0xFFFFu; y0 = rr.x >> 16;
@@ -162,6 +166,8 @@ __global__ void __launch_bounds__(256) k_expand(const uint2* __restrict__ rect, 
         ok.b = __shfl_sync(0xffffffffu, k.b, src);
         ok.c = __shfl_sync(0xffffffffu, k.c, src);
         ok.tau = __shfl_sync(0xffffffffu, k.tau, src);
+        ok.b_c = __shfl_sync(0xffffffffu, k.b_c, src);
+        ok.b_a = __shfl_sync(0xffffffffu, k.b_a, src);
         uint32_t od = 0, orec = 0;
         if (SCATTER) {
             od = __shfl_sync(0xffffffffu, dbits, src);
