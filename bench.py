@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "medium", "small"])
+    ap.add_argument("--views-per-block", type=int, default=1,
+                    help="views of each block per iteration (8: the V=64 variant; gradients then go through "
+                         "the gradient buffer and the separate x-step)")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-seq", action="store_true")
@@ -147,27 +150,28 @@ def measured_peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def traffic_for(kernel: str):
-    """dram bytes per launch from the committed ncu summary, if the kernel's
-    source has not changed since it was taken."""
+def traffic_for(kernel: str, workload: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on this workload and the kernel's source has not changed since."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p)).get(kernel)
-    if not d:
-        return None
-    src = os.path.join(ROOT, "paper_2405_13943_b300", "csrc", d["source"])
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d["source_sha"]:
-        return None
-    return d
+    entries = json.load(open(p)).get(kernel) or []
+    for d in (entries if isinstance(entries, list) else [entries]):
+        if d.get("workload") != workload:
+            continue
+        src = os.path.join(ROOT, "paper_2405_13943_b300", "csrc", d["source"])
+        if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == d["source_sha"]:
+            return d
+    return None
 
 
 # ---------------------------------------------------------------------------
-def build_workload(name: str):
+def build_workload(name: str, views_per_block: int = 1):
     from paper_2405_13943_b300 import synth as S
     w = WORKLOADS[name]
-    return S.dogs_workload(w["n_global"], w["cols"], w["rows"], w["shared"], w["seed"], views_per_step=1,
-                           pool=w["pool"], width=w["width"], height=w["height"])
+    return S.dogs_workload(w["n_global"], w["cols"], w["rows"], w["shared"], w["seed"],
+                           views_per_step=views_per_block, pool=w["pool"], width=w["width"], height=w["height"])
 
 
 def render_targets(gt_buf, views, tile):
@@ -268,7 +272,7 @@ def run_ours(args, dist, rank, world):
     torch.cuda.set_device(local)
     tile = tuple(int(v) for v in args.tile.split("x"))
     t_setup = time.time()
-    wl = build_workload(args.workload)
+    wl = build_workload(args.workload, args.views_per_block)
     z0 = D.GaussianBuffer.from_synth(wl.z0)
     gt = D.GaussianBuffer.from_synth(wl.gt)
     targets = render_targets(gt, wl.views, tile)
@@ -410,7 +414,7 @@ def run_ours(args, dist, rank, world):
         tf = flops / (acc[n] * 1e-3) / 1e12
         kern[n].update({"tflops": round(tf, 2), "frac_fp32": round(tf / fp32_peak, 3), **info})
     dom = max(names, key=lambda n: acc[n])
-    tinfo = traffic_for(dom)
+    tinfo = traffic_for(dom, f"{args.workload}:V{len(wl.views[0])}:{vb.plan.tile_w}x{vb.plan.tile_h}")
     traffic = tinfo["bytes_per_launch"] if tinfo else None
     if dom in ("rasterize_fwd", "rasterize_bwd"):
         achieved = kern[dom]["tflops"]
@@ -471,7 +475,7 @@ def run_ours(args, dist, rank, world):
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (city-law aerial scene, seeded)",
             "config": {"workload": f"DOGS K=8 batched, {WORKLOADS[args.workload]['n_global']} Gaussians SH3, "
-                                   f"{wl.split.n_copies} copies, 10% shared, V=8 x "
+                                   f"{wl.split.n_copies} copies, 10% shared, V={len(wl.views[0])} x "
                                    f"{WORKLOADS[args.workload]['width']}x{WORKLOADS[args.workload]['height']}",
                        "blocks": wl.split.K, "copies": wl.split.n_copies, "views_per_step": len(wl.views[0]),
                        "tile": f"{tr.tile[0]}x{tr.tile[1]}",
@@ -598,7 +602,7 @@ def run_reference(args, dist, rank, world):
     iteration, reported on the full-iteration scale (rank 0 only)."""
     if rank != 0:
         return
-    wl = build_workload(args.workload)
+    wl = build_workload(args.workload, getattr(args, "views_per_block", 1))
     steps = max(1, min(args.steps, 3))
     vals = []
     for _ in range(min(args.warmup, 1)):
