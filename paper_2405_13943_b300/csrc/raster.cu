@@ -119,13 +119,10 @@ __device__ __forceinline__ float ex2(float x)
     return y;
 }
 
-// alpha of a pixel that passed q >= -8 (0 = skipped by the 1/255 rule)
-__device__ __forceinline__ float strip_alpha(float q, float lo, float& raw)
-{
-    raw = ex2(fminf(q, lo));
-    const float a = fminf(raw, kAlphaMax);
-    return a < kAlphaMin ? 0.0f : a;
-}
+// o G of a pixel that passed q >= -8: the pair is composited iff
+// raw >= 1/255 (alpha = min(raw, 0.99) is below 1/255 exactly when raw is,
+// 0.99 being above it), with alpha = min(raw, 0.99)
+__device__ __forceinline__ float strip_raw(float q, float lo) { return ex2(fminf(q, lo)); }
 
 struct Fetch {
     float4 r0, r1, r2;
@@ -217,9 +214,9 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
             for (int k = 0; k < PPL; k++) {
                 const float q = strip_q_off(sp, off[k]);
                 if (!(q >= -8.0f)) continue;
-                float raw;
-                const float a = strip_alpha(q, h.y, raw);
-                if (a == 0.f) continue;
+                const float raw = strip_raw(q, h.y);
+                if (!(raw >= kAlphaMin)) continue;
+                const float a = fminf(raw, kAlphaMax);
                 const float Tn = T[k] * (1.f - a);
                 if (Tn < kTMin) { live &= ~(1u << k); off[k] = -kDeadRow; continue; }
                 const float wt = a * T[k];
@@ -412,9 +409,9 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
                 if (!(todo >> k & 1u)) continue;
-                float raw = 0.f;
-                const float a = strip_alpha(qk[k], h.y, raw);
-                if (!(a > 0.f)) continue;
+                const float raw = strip_raw(qk[k], h.y);
+                if (!(raw >= kAlphaMin)) continue;
+                const float a = fminf(raw, kAlphaMax);
                 any = true;
                 const float4 Gk = s_Gl[tid + NT * k];
                 const float Tj = T[k] * __fdividef(1.f, 1.f - a);
