@@ -12,7 +12,8 @@
 // backward walks the tile back to front from the stored T_final and last
 // index, recovering T_i = T_{i+1} / (1 - alpha_i) and the colour behind each
 // instance by the recurrence B_{i-1} = c_i alpha_i + (1 - alpha_i) B_i (B =
-// background behind the last composited instance); each lane sums its
+// background behind the last composited instance), kept as its projection
+// G . B on the pixel's dL/dpixel G, the only form the adjoint needs; each lane sums its
 // pixels' gradients, the nine per-instance gradients are reduced across the
 // warp by a shuffle reduce-scatter, and nine lanes add them to global
 // memory (NW sets of atomics per instance and tile).
@@ -323,14 +324,17 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
     const LaneGeom Lg = lane_geom(ti, tw, tid, NT);
     const int64_t HW = (int64_t)ti.W * ti.H;
     const float* gi = dL_dimage + 3 * ti.pix_off;
-    float T[PPL], B0[PPL], B1[PPL], B2[PPL];
+    // per pixel: T and, in place of the colour B behind the walk, its
+    // projection Bg = G . B on the pixel's dL/dpixel G, the only form of B
+    // the adjoint uses (dL/dalpha = T_j G . (c - B)); its recurrence
+    // Bg <- alpha (G . c) + (1 - alpha) Bg follows from B's
+    float T[PPL], Bg[PPL];
     uint32_t ml = 0;
 #pragma unroll
     for (int k = 0; k < PPL; k++) {
         const int q = tid + NT * k;
         int py = Lg.py0 + k * Lg.dpy;
         T[k] = 1.f;
-        B0[k] = bg0; B1[k] = bg1; B2[k] = bg2;
         float g0 = 0.f, g1 = 0.f, g2 = 0.f;
         uint32_t lk = 0;
         if (Lg.px < ti.W && py < ti.H) {
@@ -339,6 +343,7 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             T[k] = T_final[ti.pix_off + p];
             lk = last_in[ti.pix_off + p];
         }
+        Bg[k] = fmaf(g0, bg0, fmaf(g1, bg1, g2 * bg2));
         s_Gl[q] = make_float4(g0, g1, g2, __uint_as_float(lk));
         ml = max(ml, lk);
     }
@@ -419,12 +424,9 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
                 c0 = fmaf(Gk.x, wT, c0);
                 c1 = fmaf(Gk.y, wT, c1);
                 c2 = fmaf(Gk.z, wT, c2);
-                const float d0 = c.x - B0[k], d1 = c.y - B1[k], d2 = c.z - B2[k];
-                // dL/dalpha = T_j (G . (c - B)); d alpha / d power = alpha below the clamp
-                const float gd = fmaf(Gk.x, d0, fmaf(Gk.y, d1, Gk.z * d2));
-                B0[k] = fmaf(a, d0, B0[k]);      // B <- c a + (1 - a) B
-                B1[k] = fmaf(a, d1, B1[k]);
-                B2[k] = fmaf(a, d2, B2[k]);
+                // dL/dalpha = T_j (G . c - G . B); d alpha / d power = alpha below the clamp
+                const float gd = fmaf(Gk.x, c.x, fmaf(Gk.y, c.y, Gk.z * c.z)) - Bg[k];
+                Bg[k] = fmaf(a, gd, Bg[k]);      // G . B <- a G . c + (1 - a) G . B
                 T[k] = Tj;
                 const float dLdp = raw < kAlphaMax ? wT * gd : 0.f;
                 S0 += dLdp;
