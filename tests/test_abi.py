@@ -118,3 +118,26 @@ def test_misaligned_pointers_are_rejected_before_launch(lib):
     lr = L.floats([1] * 6)
     assert lib.dg_adam_admm_step(C.byref(x), C.byref(x), C.byref(x), C.byref(x), None, None, rho, lr,
                                  0.9, 0.999, 1e-15, 1, 0x50002, None) == L.DG_ERR_INVALID
+
+
+def test_xstep_part_rejects_bad_arguments_before_launch(lib):
+    """dg_xstep_part validates its part, grid bound and z store on the host."""
+    from paper_2405_13943_b300 import dogs as D
+    arr, plan = D.plan_views([S.cube_camera(32, 32)], [0, 64], 16, 16)
+    x = L.DgGaussians(0x10000, 64, 64, 0, 0)
+    z = L.DgGaussians(0x20000, 32, 64, 0, 0)
+    z1 = L.DgGaussians(0x20000, 32, 64, 1, 0)          # another SH degree
+    rho, lr = L.floats([1] * 5), L.floats([1] * 6)
+    rect, cams, drec, shared, gid = 0x30000, 0x40000, 0x50000, 0x60000, 0x70000
+
+    def call(part, ctas, zz=None, g=None, sh=shared, d=drec):
+        return lib.dg_xstep_part(part, ctas, rect, cams, C.byref(plan), d, C.byref(x), C.byref(x), C.byref(x),
+                                 None, sh, rho, lr, 0.9, 0.999, 1e-15, 1, None,
+                                 None if zz is None else C.byref(zz), g, None)
+    for part, ctas in ((-1, 0), (3, 0), (1, -1)):
+        assert call(part, ctas) == L.DG_ERR_INVALID
+    assert call(2, 0, d=None) == L.DG_ERR_INVALID             # part 2 needs the record gradients
+    assert call(0, 0, z, None) == L.DG_ERR_INVALID            # a z store needs the global ids
+    assert call(0, 0, z, gid, sh=None) == L.DG_ERR_INVALID    # ... and the shared flags
+    assert call(0, 0, z1, gid) == L.DG_ERR_INVALID            # ... and the same SH degree
+    assert call(0, 0, z, gid + 2) == L.DG_ERR_INVALID         # misaligned ids
