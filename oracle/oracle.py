@@ -10,7 +10,8 @@ is written here in numpy, from its definition.
 
 Parity status: pinned by tests/test_oracle_*.py (closed forms, brute force,
 central finite differences, hand-worked ADMM examples, textbook ADMM
-convergence on quadratics).
+convergence on quadratics; densification by hand-worked decisions and the
+split children's distribution against scipy's rotation).
 """
 from __future__ import annotations
 
@@ -531,3 +532,110 @@ def scene_assign(xy, boxes, s, own=None, nearest=False):
             if best >= 0:
                 member[i, best] = True
     return member
+
+
+# ---------------------------------------------------------------------------
+# Densification under consensus (Sec. 4, Implementation Details: densified
+# at the intervals of 3DGS; Sec. 5: small Gaussians pruned).  The paper
+# follows the 3DGS adaptive density control; its rules are restated here:
+#   statistic  per Gaussian, over the iterations since the last densification,
+#              the mean over its visible records of the norm of the screen
+#              gradient of its projected mean in normalised device units
+#              (pixels scaled by W/2 and H/2);
+#   prune      opacity sigmoid(o) < min_opacity (the Gaussian and anything
+#              it would spawn are dropped);
+#   clone      mean statistic >= grad_threshold and largest scale
+#              <= percent_dense * extent: the Gaussian and an exact copy;
+#   split      mean statistic >= grad_threshold and largest scale larger:
+#              two children replace it, each with mean mu + R(q) (S xi)
+#              (xi ~ N(0, I), drawn by the caller), scales S / 1.6, the
+#              other parameters copied.
+# Under consensus the decision is taken on the global model z right after
+# a consensus, from the statistics of all copies of each Gaussian summed,
+# so every block holding a Gaussian gets the same children; the children
+# inherit the parent's sharing set.  The thresholds on sigmoid(o) and on
+# the largest scale are compared as thresholds on the raw parameters (the
+# logit and the log-scale), and the gradient rule as sum >= tau * count; the
+# decisions are taken in FP32, the precision of the GPU path.
+# ---------------------------------------------------------------------------
+DENSIFY_KEEP, DENSIFY_PRUNE, DENSIFY_CLONE, DENSIFY_SPLIT = 0, 1, 2, 3
+
+
+def quat_rotation(q) -> np.ndarray:
+    """Rotation matrix of the unit quaternion q / |q| (w, x, y, z)."""
+    q = np.asarray(q, np.float64)
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def densify_stats(kept: np.ndarray, dmean2d: np.ndarray, view_wh: np.ndarray, copy_of_record: np.ndarray,
+                  n_copies: int):
+    """One iteration's contribution to the statistic: for every kept record
+    r (copy copy_of_record[r] in a view of size view_wh[r]), the norm of its
+    mean gradient in normalised device units.  Returns (sum, count) per copy."""
+    s = np.zeros(n_copies, np.float64)
+    c = np.zeros(n_copies, np.float64)
+    g = np.asarray(dmean2d, np.float64) * (0.5 * np.asarray(view_wh, np.float64))
+    nrm = np.sqrt((g * g).sum(1))
+    for r in np.nonzero(np.asarray(kept, bool))[0]:
+        s[copy_of_record[r]] += nrm[r]
+        c[copy_of_record[r]] += 1.0
+    return s, c
+
+
+def densify_decide(z: np.ndarray, sh_degree: int, stat_sum, stat_cnt, g_off, g_copies,
+                   grad_threshold=2e-4, percent_dense=0.01, extent=1.0, min_opacity=0.005) -> np.ndarray:
+    """The decision per global Gaussian (DENSIFY_* codes) from the summed
+    statistics of its copies (FP32 sums in the CSR order of the copies)."""
+    f32 = np.float32
+    zz = split_params(z, sh_degree)
+    logit_min = f32(np.log(f32(min_opacity) / (f32(1.0) - f32(min_opacity))))
+    log_big = f32(np.log(f32(percent_dense) * f32(extent)))
+    n = z.shape[0]
+    codes = np.zeros(n, np.int32)
+    for i in range(n):
+        ssum, scnt = f32(0.0), f32(0.0)
+        for c in g_copies[g_off[i]:g_off[i + 1]]:
+            ssum = f32(ssum + f32(stat_sum[c]))
+            scnt = f32(scnt + f32(stat_cnt[c]))
+        if f32(zz["opacity"][i]) < logit_min:
+            codes[i] = DENSIFY_PRUNE
+        elif scnt > 0 and ssum >= f32(f32(grad_threshold) * scnt):
+            big = max(f32(v) for v in zz["scale"][i]) > log_big
+            codes[i] = DENSIFY_SPLIT if big else DENSIFY_CLONE
+        else:
+            codes[i] = DENSIFY_KEEP
+    return codes
+
+
+def densify_emit(z: np.ndarray, sh_degree: int, codes: np.ndarray, normals: np.ndarray):
+    """The densified global set in order (each Gaussian's outputs in place:
+    keep -> itself, clone -> itself and its copy, split -> its two children,
+    prune -> nothing).  normals: (n, 2, 3) standard normals, row i used if i
+    splits.  Returns (z_new, src, original) with src the parent of every new
+    Gaussian and original true where it is the parent itself (kept, or the
+    first of a clone pair), whose optimiser state and duals carry over."""
+    zz = split_params(z, sh_degree)
+    out, src, orig = [], [], []
+    ln16 = np.log(1.6)
+    for i in range(z.shape[0]):
+        c = codes[i]
+        if c == DENSIFY_PRUNE:
+            continue
+        if c in (DENSIFY_KEEP, DENSIFY_CLONE):
+            out.append(z[i].copy()); src.append(i); orig.append(True)
+            if c == DENSIFY_CLONE:
+                out.append(z[i].copy()); src.append(i); orig.append(False)
+            continue
+        R = quat_rotation(zz["quat"][i])
+        S = np.exp(zz["scale"][i])
+        for h in range(2):
+            child = z[i].copy()
+            child[0:3] = zz["mean"][i] + R @ (S * normals[i, h])
+            child[7:10] = zz["scale"][i] - ln16
+            out.append(child); src.append(i); orig.append(False)
+    P = z.shape[1]
+    z_new = np.array(out, np.float64).reshape(-1, P)
+    return z_new, np.array(src, np.int64), np.array(orig, bool)
