@@ -320,6 +320,59 @@ int dg_admm_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z,
  * graph, back to back, with each replay seeing its own count. */
 int dg_step_advance(int32_t* dev_step, void* stream);
 
+/* ---- Densification under consensus (Sec. 4, 3DGS adaptive density control) ---
+ * Decision codes of dg_densify_decide. */
+#define DG_DENSIFY_KEEP 0
+#define DG_DENSIFY_PRUNE 1
+#define DG_DENSIFY_CLONE 2
+#define DG_DENSIFY_SPLIT 3
+
+/* Adds one iteration's densification statistic: for every record r of the
+ * plan whose rectangle is non-empty, copy c of r (its view's gauss_begin +
+ * r - rec_off) gets stats[2c] += |(drec[12r] W/2, drec[12r+1] H/2)| (the norm
+ * of its projected mean's gradient in normalised device units, W x H its
+ * view) and stats[2c+1] += 1.  stats: device float[2 n_copies], accumulated
+ * (the caller zeroes it after each densification); rect / drec: the forward's
+ * rectangles and dg_rasterize_bwd_records' gradients. */
+int dg_densify_stats(const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                     const float* drec, float* stats, void* stream);
+
+/* Bytes of workspace dg_densify_decide needs for n globals. */
+size_t dg_densify_workspace_size(int64_t n_global);
+
+/* The densification decision per global Gaussian of z, from the summed
+ * statistics of its copies (CSR g_off / g_copies as for dg_admm_consensus,
+ * summed in that order in FP32): DG_DENSIFY_PRUNE if the opacity logit is
+ * below log(min_opacity / (1 - min_opacity)); else, if count > 0 and
+ * sum >= grad_threshold * count, DG_DENSIFY_SPLIT when the largest
+ * log-scale exceeds log(percent_dense * extent) and DG_DENSIFY_CLONE
+ * otherwise; else DG_DENSIFY_KEEP.  codes: device int32[n]; counts: device
+ * uint32[n] (outputs of each Gaussian: 0, 1, 2, 2); offsets: device
+ * uint32[n + 1], their exclusive scan with the total at offsets[n] (n + 1
+ * entries; must fit in 32 bits).  ws: dg_densify_workspace_size bytes. */
+int dg_densify_decide(const dg_gaussians* z, const int64_t* g_off, const int32_t* g_copies,
+                      const float* stats, float grad_threshold, float percent_dense, float extent,
+                      float min_opacity, int32_t* codes, uint32_t* counts, uint32_t* offsets,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* The densified set: global i writes its outputs at out[offsets[i] ..]:
+ * KEEP itself; CLONE itself and an exact copy; SPLIT two children with mean
+ * mu + R(q) (S xi_h) (R of the normalised quaternion, S = exp(log-scale),
+ * xi_h = normals[6i + 3h .. 6i + 3h + 2], standard normals drawn by the
+ * caller) and log-scales reduced by ln 1.6, the other parameters copied;
+ * PRUNE nothing.  src[o]: the parent of output o; original[o] = 1 where o is
+ * the parent itself (KEEP, or the first output of CLONE), whose optimiser
+ * state and duals carry over.  out: same SH degree, n >= offsets[n]. */
+int dg_densify_emit(const dg_gaussians* z, const int32_t* codes, const uint32_t* offsets,
+                    const float* normals, dg_gaussians* out, int32_t* src, uint8_t* original,
+                    void* stream);
+
+/* dst row r = src row idx[r] (all fields and SH planes) for r < dst->n;
+ * rows with idx[r] < 0 are left unchanged.  The rows move between the
+ * library layouts of the two sets (same SH degree, any ld); idx[r] must be
+ * < src->n. */
+int dg_gather_rows(const dg_gaussians* src, const int32_t* idx, dg_gaussians* dst, void* stream);
+
 /* Adaptive penalty (Sec. 3.3, Eq. 10): when rho_grp changes to rho'_grp the
  * scaled duals u = y / rho follow as u_grp *= rho_grp / rho'_grp.  This call
  * multiplies each group of u on shared copies by factor[5] (host); rerun

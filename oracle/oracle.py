@@ -591,8 +591,11 @@ def densify_decide(z: np.ndarray, sh_degree: int, stat_sum, stat_cnt, g_off, g_c
     statistics of its copies (FP32 sums in the CSR order of the copies)."""
     f32 = np.float32
     zz = split_params(z, sh_degree)
-    logit_min = f32(np.log(f32(min_opacity) / (f32(1.0) - f32(min_opacity))))
-    log_big = f32(np.log(f32(percent_dense) * f32(extent)))
+    # thresholds on the raw parameters, formed in double from the FP32
+    # inputs and rounded once to FP32
+    m = np.float64(f32(min_opacity))
+    logit_min = f32(np.log(m / (1.0 - m)))
+    log_big = f32(np.log(np.float64(f32(percent_dense)) * np.float64(f32(extent))))
     n = z.shape[0]
     codes = np.zeros(n, np.int32)
     for i in range(n):

@@ -19,6 +19,7 @@ DG_OK, DG_ERR_INVALID, DG_ERR_WORKSPACE, DG_ERR_CAPACITY, DG_ERR_CUDA = 0, -1, -
 DG_ERR_TOO_LARGE = -6
 DG_NOALLOC_MAX_TILES, DG_NOALLOC_MAX_INSTANCES = 262144, 4194304
 DG_STATUS_CAPACITY = 1
+DG_DENSIFY_KEEP, DG_DENSIFY_PRUNE, DG_DENSIFY_CLONE, DG_DENSIFY_SPLIT = 0, 1, 2, 3
 DG_MAX_BLOCKS = 64
 DG_MAX_VIEWS = 4096
 
@@ -97,6 +98,12 @@ _SIGS = {
                                  C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float,
                                  C.c_int, _vp, C.POINTER(DgGaussians), _vp, _vp]),
     "dg_step_advance": (C.c_int, [_vp, _vp]),
+    "dg_densify_stats": (C.c_int, [_vp, _vp, C.POINTER(DgPlan), _vp, _vp, _vp]),
+    "dg_densify_workspace_size": (C.c_size_t, [C.c_int64]),
+    "dg_densify_decide": (C.c_int, [C.POINTER(DgGaussians), _vp, _vp, _vp, C.c_float, C.c_float, C.c_float,
+                                    C.c_float, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "dg_densify_emit": (C.c_int, [C.POINTER(DgGaussians), _vp, _vp, _vp, C.POINTER(DgGaussians), _vp, _vp, _vp]),
+    "dg_gather_rows": (C.c_int, [C.POINTER(DgGaussians), _vp, C.POINTER(DgGaussians), _vp]),
     "dg_scene_split": (C.c_int, [_vp, C.c_int64, C.c_int, _vp, _vp]),
     "dg_scene_assign": (C.c_int, [_vp, C.c_int64, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp]),
     "dg_render_plan": (C.c_int, [C.POINTER(DgCamera), C.c_int, C.c_int64, C.c_int, C.c_int, C.POINTER(DgPlan)]),

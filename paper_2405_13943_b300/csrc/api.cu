@@ -36,6 +36,13 @@ int launch_anchor(const dg_gaussians*, const dg_gaussians*, const int32_t*, cons
                   cudaStream_t);
 int launch_scale_duals(dg_gaussians*, const uint8_t*, const float*, cudaStream_t);
 int launch_step_advance(int32_t*, cudaStream_t);
+int launch_densify_stats(const uint2*, const float*, const dg_camera*, const dg_plan&, float*, cudaStream_t);
+size_t densify_scan_ws_bytes(int64_t);
+int launch_densify_decide(const dg_gaussians*, const int64_t*, const int32_t*, const float*, float, float, float,
+                          int32_t*, uint32_t*, uint32_t*, void*, cudaStream_t);
+int launch_densify_emit(const dg_gaussians*, const int32_t*, const uint32_t*, const float*, dg_gaussians*, int32_t*,
+                        uint8_t*, cudaStream_t);
+int launch_gather_rows(const dg_gaussians*, const int32_t*, dg_gaussians*, cudaStream_t);
 int launch_xstep(int, int, dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*, const uint8_t*,
                  const dg_camera*, const dg_plan&, const uint2*, const float4*, const AdamArgs&, const int32_t*,
                  dg_gaussians*, const int32_t*, cudaStream_t);
@@ -357,6 +364,49 @@ int dg_step_advance(int32_t* dev_step, void* stream)
 {
     if (!dev_step || ((uintptr_t)dev_step & 3u)) return DG_ERR_INVALID;
     return launch_step_advance(dev_step, (cudaStream_t)stream);
+}
+
+int dg_densify_stats(const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan, const float* drec,
+                     float* stats, void* stream)
+{
+    if (!valid_plan(plan)) return DG_ERR_INVALID;
+    if (plan->n_rec > 0 && (!rect || !dev_cams || !drec || !stats)) return DG_ERR_INVALID;
+    if (!aligned8(rect) || !aligned8(dev_cams) || !aligned16(drec) || ((uintptr_t)stats & 3u)) return DG_ERR_INVALID;
+    return launch_densify_stats((const uint2*)rect, drec, dev_cams, *plan, stats, (cudaStream_t)stream);
+}
+
+size_t dg_densify_workspace_size(int64_t n_global) { return densify_scan_ws_bytes(n_global < 0 ? 0 : n_global); }
+
+int dg_densify_decide(const dg_gaussians* z, const int64_t* g_off, const int32_t* g_copies, const float* stats,
+                      float grad_threshold, float percent_dense, float extent, float min_opacity, int32_t* codes,
+                      uint32_t* counts, uint32_t* offsets, void* ws, size_t ws_bytes, void* stream)
+{
+    if (!valid_gauss(z) || !offsets) return DG_ERR_INVALID;
+    if (z->n > 0 && (!g_off || !g_copies || !stats || !codes || !counts || !ws)) return DG_ERR_INVALID;
+    if (z->n >= ((int64_t)1 << 31) || ws_bytes < densify_scan_ws_bytes(z->n)) return DG_ERR_INVALID;
+    if (!(percent_dense > 0.f) || !(extent > 0.f) || !(min_opacity > 0.f && min_opacity < 1.f))
+        return DG_ERR_INVALID;
+    // thresholds on the raw parameters, formed in double and rounded once
+    const double m = (double)min_opacity;
+    const float logit_min = (float)log(m / (1.0 - m));
+    const float log_big = (float)log((double)percent_dense * (double)extent);
+    return launch_densify_decide(z, g_off, g_copies, stats, grad_threshold, logit_min, log_big, codes, counts,
+                                 offsets, ws, (cudaStream_t)stream);
+}
+
+int dg_densify_emit(const dg_gaussians* z, const int32_t* codes, const uint32_t* offsets, const float* normals,
+                    dg_gaussians* out, int32_t* src, uint8_t* original, void* stream)
+{
+    if (!valid_gauss(z) || !valid_gauss(out) || out->sh_degree != z->sh_degree) return DG_ERR_INVALID;
+    if (z->n > 0 && (!codes || !offsets || !normals || !src || !original)) return DG_ERR_INVALID;
+    return launch_densify_emit(z, codes, offsets, normals, out, src, original, (cudaStream_t)stream);
+}
+
+int dg_gather_rows(const dg_gaussians* src, const int32_t* idx, dg_gaussians* dst, void* stream)
+{
+    if (!valid_gauss(src) || !valid_gauss(dst) || src->sh_degree != dst->sh_degree) return DG_ERR_INVALID;
+    if (dst->n > 0 && !idx) return DG_ERR_INVALID;
+    return launch_gather_rows(src, idx, dst, (cudaStream_t)stream);
 }
 
 int dg_admm_scale_duals(dg_gaussians* u, const uint8_t* copy_shared, const float* factor, void* stream)

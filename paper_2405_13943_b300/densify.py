@@ -1,0 +1,127 @@
+"""Densification under consensus (Sec. 4: densified at the intervals and
+until the iteration of 3DGS, with its adaptive density control; Sec. 5: small
+Gaussians pruned).
+
+The trainer accumulates the statistic every iteration (dg_densify_stats in
+the captured iteration).  At a densification iteration, right after its
+consensus, `densify(trainer, cfg)`:
+  1. decides per global Gaussian of z from the summed statistics of all its
+     copies (dg_densify_decide) and writes the densified global set in place
+     order (dg_densify_emit, split children from seeded normals);
+  2. gives every new Gaussian its parent's sharing set (the blocks that held
+     the parent) and rebuilds the copy layout with the same numbering rule
+     as the initial split (shared globals first, Z-order; synth.split_layout);
+  3. moves the state (dg_gather_rows): z from the emitted set; for every new
+     copy whose Gaussian is its parent itself and whose parent had a copy in
+     the same block, that copy's x, Adam moments and scaled dual; other
+     copies start from their Gaussian's z with zero moments and duals (as
+     3DGS zeroes the optimiser state of new points);
+  4. rebuilds the anchors, the batch plan and the capacity; captured graphs
+     are dropped.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import dogs as D
+from . import synth as S
+
+
+@dataclass
+class DensifyConfig:
+    interval: int = 200             # densify every `interval` iterations (a multiple of the consensus interval)
+    start: int = 500                # first densification iteration
+    until: int = 30000              # no densification from this iteration on
+    grad_threshold: float = 2e-4    # mean screen-gradient norm (normalised device units)
+    percent_dense: float = 0.01     # clone / split boundary on the largest scale, as a fraction of the extent
+    min_opacity: float = 0.005      # prune below this opacity
+    extent: Optional[float] = None  # scene extent; None: from the camera centres (scene_extent)
+    seed: int = 0                   # seed of the split normals (advanced per densification)
+
+    def due(self, t: int) -> bool:
+        return self.start <= t < self.until and t % self.interval == 0
+
+
+def scene_extent(cams: Sequence[S.Camera]) -> float:
+    """The extent 3DGS scales its split rule by: 1.1 times the largest
+    distance of a camera centre from their mean."""
+    c = np.stack([np.asarray(cam.campos, np.float64) for cam in cams])
+    return float(1.1 * np.linalg.norm(c - c.mean(0), axis=1).max())
+
+
+def membership(split: S.BlockSplit) -> np.ndarray:
+    """(n_global, K) bool: the blocks that hold each global Gaussian."""
+    K = split.K
+    m = np.zeros((split.n_globals, K), bool)
+    for k in range(K):
+        m[split.copy_gid[split.blk_off[k]:split.blk_off[k + 1]], k] = True
+    return m
+
+
+def carried_copies(old: S.BlockSplit, new: S.BlockSplit, src_of_new_global: np.ndarray,
+                   original: np.ndarray) -> np.ndarray:
+    """For every copy of the new layout, the copy of the old layout whose
+    state it takes over (-1: none): the same block and the parent Gaussian,
+    when the new Gaussian is its parent itself."""
+    K = old.K
+    old_blk = np.repeat(np.arange(K), np.diff(old.blk_off))
+    key_old = old.copy_gid.astype(np.int64) * K + old_blk
+    order = np.argsort(key_old, kind="stable")
+    key_sorted = key_old[order]
+    new_blk = np.repeat(np.arange(K), np.diff(new.blk_off))
+    g_new = new.copy_gid.astype(np.int64)
+    parent = src_of_new_global[g_new].astype(np.int64)
+    want = parent * K + new_blk
+    pos = np.searchsorted(key_sorted, want)
+    pos_c = np.minimum(pos, len(key_sorted) - 1)
+    found = (len(key_sorted) > 0) & (key_sorted[pos_c] == want) & original[g_new]
+    return np.where(found, order[pos_c], -1).astype(np.int32)
+
+
+def densify(tr, cfg: DensifyConfig, extent: float, step_seed: int) -> Dict:
+    """One densification of DogsTrainer `tr` (after a consensus).  Returns
+    counts of the decisions and the sizes before and after."""
+    dev = tr.z.data.device
+    torch.cuda.synchronize()
+    z = tr.z
+    codes, offsets = D.dg_densify_decide(z, tr.g_off, tr.g_copies, tr.dstats, cfg.grad_threshold,
+                                         cfg.percent_dense, extent, cfg.min_opacity)
+    n_out = int(offsets[-1].item()) & 0xFFFFFFFF
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(cfg.seed) * 1000003 + int(step_seed))
+    normals = torch.randn(max(z.n, 1) * 6, device=dev, generator=gen, dtype=torch.float32)
+    z_tmp, src, orig = D.dg_densify_emit(z, codes, offsets, normals, n_out)
+    c = np.bincount(codes.cpu().numpy(), minlength=4)
+    src_h = src.cpu().numpy().astype(np.int64)
+    orig_h = orig.cpu().numpy().astype(bool)
+    # the new layout: every Gaussian in its parent's blocks
+    old = tr.split
+    member = membership(old)[src_h]
+    xy = z_tmp.data[:4 * z_tmp.ld].view(z_tmp.ld, 4)[:n_out, :2].double().cpu().numpy()
+    new_split, order = S.split_layout(xy, member, old.cells, old.band)
+    order_t = torch.from_numpy(order.astype(np.int32)).to(dev)
+    z_new = D.GaussianBuffer(n_out, z.deg, dev)
+    D.dg_gather_rows(z_tmp, order_t, z_new)
+    src_new = src_h[order]
+    orig_new = orig_h[order]
+    carry = torch.from_numpy(carried_copies(old, new_split, src_new, orig_new)).to(dev)
+    gid_new = torch.from_numpy(new_split.copy_gid.astype(np.int32)).to(dev)
+    n_c = new_split.n_copies
+    x_new = D.GaussianBuffer(n_c, z.deg, dev)
+    D.dg_gather_rows(z_new, gid_new, x_new)           # every copy from its Gaussian ...
+    D.dg_gather_rows(tr.x, carry, x_new)              # ... the carried ones from their old copy
+    bufs = {}
+    for name in ("m", "v", "u"):
+        b = D.GaussianBuffer(n_c, z.deg, dev)         # zeros where nothing is carried
+        D.dg_gather_rows(getattr(tr, name), carry, b)
+        bufs[name] = b
+    del z_tmp
+    tr.install_split(new_split, z_new, x_new, bufs["m"], bufs["v"], bufs["u"])
+    return {"before": int(z.n), "after": int(n_out), "keep": int(c[D.L.DG_DENSIFY_KEEP]),
+            "prune": int(c[D.L.DG_DENSIFY_PRUNE]), "clone": int(c[D.L.DG_DENSIFY_CLONE]),
+            "split": int(c[D.L.DG_DENSIFY_SPLIT]), "copies": int(n_c),
+            "carried_copies": int((carry >= 0).sum().item())}

@@ -293,6 +293,51 @@ def dg_xstep_part(part: int, vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer
                                   L.stream_handle(stream)), "dg_xstep_part")
 
 
+def dg_densify_stats(vb: ViewBatch, stats: torch.Tensor, stream=None) -> None:
+    """Adds one iteration's densification statistic of every kept record into
+    stats (float32, 2 per copy): the norm of its projected mean's gradient in
+    normalised device units (from vb.drec) and a count."""
+    L.check(L.lib().dg_densify_stats(L.ptr(vb.rect), L.ptr(vb.dev_cams), C.byref(vb.plan), L.ptr(vb.drec),
+                                     L.ptr(stats), L.stream_handle(stream)), "dg_densify_stats")
+
+
+def dg_densify_decide(z: GaussianBuffer, g_off: torch.Tensor, g_copies: torch.Tensor, stats: torch.Tensor,
+                      grad_threshold: float, percent_dense: float, extent: float, min_opacity: float,
+                      stream=None):
+    """Decision codes (int32) and output offsets (uint32 in an int32 tensor,
+    n + 1 entries, total last) per global Gaussian of z."""
+    n = z.n
+    dev = z.data.device
+    codes = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    counts = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    offsets = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    wsb = int(L.lib().dg_densify_workspace_size(n))
+    ws = torch.empty(max(wsb, 4), dtype=torch.uint8, device=dev)
+    L.check(L.lib().dg_densify_decide(z.ref, L.ptr(g_off), L.ptr(g_copies), L.ptr(stats), float(grad_threshold),
+                                      float(percent_dense), float(extent), float(min_opacity), L.ptr(codes),
+                                      L.ptr(counts), L.ptr(offsets), L.ptr(ws), wsb, L.stream_handle(stream)),
+            "dg_densify_decide")
+    return codes[:n], offsets
+
+
+def dg_densify_emit(z: GaussianBuffer, codes: torch.Tensor, offsets: torch.Tensor, normals: torch.Tensor,
+                    n_out: int, stream=None):
+    """The densified set (n_out = offsets[n]) with each output's parent and
+    whether it is the parent itself."""
+    dev = z.data.device
+    out = GaussianBuffer(n_out, z.deg, dev)
+    src = torch.empty(max(n_out, 1), dtype=torch.int32, device=dev)
+    orig = torch.empty(max(n_out, 1), dtype=torch.uint8, device=dev)
+    L.check(L.lib().dg_densify_emit(z.ref, L.ptr(codes), L.ptr(offsets), L.ptr(normals), out.ref, L.ptr(src),
+                                    L.ptr(orig), L.stream_handle(stream)), "dg_densify_emit")
+    return out, src[:n_out], orig[:n_out]
+
+
+def dg_gather_rows(src: GaussianBuffer, idx: torch.Tensor, dst: GaussianBuffer, stream=None) -> None:
+    """dst row r = src row idx[r]; rows with idx[r] < 0 are left unchanged."""
+    L.check(L.lib().dg_gather_rows(src.ref, L.ptr(idx), dst.ref, L.stream_handle(stream)), "dg_gather_rows")
+
+
 def dg_backward_xstep(vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer, v: GaussianBuffer,
                       anchor: Optional[GaussianBuffer], shared: Optional[torch.Tensor], rho, lr, beta1=0.9,
                       beta2=0.999, eps=1e-15, step=1, dev_step: Optional[torch.Tensor] = None, bg=(0.0, 0.0, 0.0),

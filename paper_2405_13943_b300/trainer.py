@@ -12,13 +12,14 @@ gathering their copies into one buffer and scattering the duals back.
 from __future__ import annotations
 
 import ctypes as C
-from typing import List, Optional, Sequence
+from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 import torch
 
 from . import _lib as L
 from . import dogs as D
+from . import densify as DZ
 from . import synth as S
 from .admm import AdaptivePenalty
 
@@ -44,8 +45,8 @@ class DogsTrainer:
                  targets: Sequence[torch.Tensor], rho=(1e-3,) * 5, lr=DEFAULT_LR, tile=(16, 16),
                  loss="dssim", w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0), alpha=1.0, intv=100,
                  capacity: Optional[int] = None, device="cuda", adaptive: Optional[AdaptivePenalty] = None,
-                 fused: bool = True, overlap: bool = True):
-        self.split, self.device = split, device
+                 fused: bool = True, overlap: bool = True, densify: Optional["DZ.DensifyConfig"] = None):
+        self.device = device
         self.fused = fused
         # with the fused x-step: the groups of copies that no view sees are
         # stepped on a side stream right after the projection, alongside
@@ -54,13 +55,6 @@ class DogsTrainer:
         self.overlap = overlap
         self.side = torch.cuda.Stream(device=device) if overlap and str(device).startswith("cuda") else None
         self._idle_queued = False
-        # globals held by several blocks numbered first: then, in an iteration
-        # with a consensus, the x-step stores the unshared copies' values into
-        # z itself and the consensus runs over the shared globals alone
-        cnt = np.diff(split.g_off)
-        ns = int(split.n_shared_globals)
-        self._shared_first = bool((cnt[:ns] > 1).all() and (cnt[ns:] <= 1).all())
-        self.n_shared_globals = ns
         # CTAs per SM of the side-stream part (a grid-stride loop), or 0 for
         # one CTA per group of copies.  Measured on the 6M-Gaussian step:
         # one per group 9.15 ms, 3 per SM 9.43, 2 per SM 10.03, 1 per SM
@@ -73,20 +67,20 @@ class DogsTrainer:
             adaptive.rho = [float(r) for r in rho]
         self.rho, self.lr, self.bg, self.alpha, self.intv = list(rho), list(lr), bg, alpha, intv
         self.loss_kind, self.w_l1, self.w_ssim = loss, w_l1, w_ssim
-        self.gid = torch.from_numpy(split.copy_gid.astype(np.int32)).to(device)
-        self.shared = torch.from_numpy(split.copy_shared()).to(device)
-        self.g_off = torch.from_numpy(split.g_off.astype(np.int64)).to(device)
-        self.g_copies = torch.from_numpy(split.g_copies.astype(np.int32)).to(device)
-        self.z = z0
-        self.x = gather_copies(z0, self.gid)
-        self.grad, self.m, self.v = self.x.like(), self.x.like(), self.x.like()
-        self.u, self.anchor = self.x.like(), self.x.like()
-        D.dg_admm_anchor(self.z, self.u, self.gid, self.shared, self.anchor)
         self.view_sets = [list(v) for v in view_sets]
         self.tile = tuple(tile)
-        self.vb = D.ViewBatch(self.view_sets[0], split.blk_off, tile[0], tile[1], device=device,
-                              capacity=capacity, loss_ws=(loss == "dssim"))
-        self.cam_pool = [D.cams_to_device(D.plan_views(vs, split.blk_off, *tile)[0], device) for vs in self.view_sets]
+        # densification under consensus (densify.DensifyConfig), statistics per copy
+        self.densify_cfg = densify
+        if densify is not None and densify.interval % intv != 0:
+            raise ValueError("the densification interval must be a multiple of the consensus interval")
+        self.extent = None
+        if densify is not None:
+            self.extent = densify.extent if densify.extent is not None else \
+                DZ.scene_extent([c for vs in self.view_sets for c in vs])
+        self.densify_log: List[Dict] = []
+        gid = torch.from_numpy(split.copy_gid.astype(np.int32)).to(device)
+        x = gather_copies(z0, gid)
+        self.install_split(split, z0, x, x.like(), x.like(), x.like(), capacity=capacity)
         self.targets = list(targets)
         # Adam's step counter lives on the device and each iteration advances
         # it there, so replays queued back to back each see their own count
@@ -95,6 +89,48 @@ class DogsTrainer:
         self.t = 0
         self.graphs = {}
         self.host_targets = None
+
+    # ---- the block layout and the state on it --------------------------------------
+    def install_split(self, split: S.BlockSplit, z: D.GaussianBuffer, x: D.GaussianBuffer, m: D.GaussianBuffer,
+                      v: D.GaussianBuffer, u: D.GaussianBuffer, capacity: Optional[int] = None) -> None:
+        """Take a block layout with its global model, copies, Adam moments and
+        scaled duals: the sharing map, the anchors z - u, the batch plan for
+        the view sets and (after a first install) the instance capacity are
+        rebuilt; captured graphs are dropped."""
+        dev = self.device
+        first = not hasattr(self, "split")
+        variant = None if first else (self.vb.plan.raster_warps, self.vb.plan.raster_stage,
+                                      self.vb.plan.raster_warps_bwd, self.vb.plan.raster_stage_bwd)
+        self.split = split
+        # globals held by several blocks numbered first: then, in an iteration
+        # with a consensus, the x-step stores the unshared copies' values into
+        # z itself and the consensus runs over the shared globals alone
+        cnt = np.diff(split.g_off)
+        ns = int(split.n_shared_globals)
+        self._shared_first = bool((cnt[:ns] > 1).all() and (cnt[ns:] <= 1).all())
+        self.n_shared_globals = ns
+        self.gid = torch.from_numpy(split.copy_gid.astype(np.int32)).to(dev)
+        self.shared = torch.from_numpy(split.copy_shared()).to(dev)
+        self.g_off = torch.from_numpy(split.g_off.astype(np.int64)).to(dev)
+        self.g_copies = torch.from_numpy(split.g_copies.astype(np.int32)).to(dev)
+        self.z, self.x, self.m, self.v, self.u = z, x, m, v, u
+        self.grad, self.anchor = x.like(), x.like()
+        D.dg_admm_anchor(self.z, self.u, self.gid, self.shared, self.anchor)
+        self.dstats = (torch.zeros(2 * max(split.n_copies, 1), dtype=torch.float32, device=dev)
+                       if self.densify_cfg is not None else None)
+        self.vb = None
+        if not first:
+            torch.cuda.empty_cache()
+        self.vb = D.ViewBatch(self.view_sets[0], split.blk_off, self.tile[0], self.tile[1], device=dev,
+                              capacity=capacity, loss_ws=(self.loss_kind == "dssim"))
+        if variant is not None:
+            D.apply_variant(self.vb.plan, variant)
+        self.cam_pool = [D.cams_to_device(D.plan_views(vs, split.blk_off, *self.tile)[0], dev)
+                         for vs in self.view_sets]
+        self.graphs = {}
+        self._idle_queued = False
+        if not first:
+            self.calibrate_capacity()
 
     # ---- rasteriser configuration (autotuner) ------------------------------------
     def set_tile(self, tile) -> None:
@@ -157,6 +193,8 @@ class DogsTrainer:
         D.dg_rasterize_fwd(vb, self.bg)
         self._loss(self.targets[p] if target is None else target)
         self.backward_step(zf)
+        if self._stats_on():
+            D.dg_densify_stats(vb, self.dstats)
         if consensus:
             D.dg_admm_consensus(self.x, self.u, self.z_shared() if zf else self.z, self.anchor, self.g_off,
                                 self.g_copies, self.rho, self.alpha, self.residuals)
@@ -269,8 +307,9 @@ class DogsTrainer:
                 self._prefetch(p, slot)
             torch.cuda.current_stream().wait_event(self.copied[slot])
             target = self.stage[slot]
+        ds = self._stats_on()
         if graph:
-            key = (p, c, slot)
+            key = (p, c, slot, ds)
             if key not in self.graphs:
                 self.graphs[key] = self._capture(p, c, target, slot)
             self.graphs[key].replay()
@@ -284,7 +323,13 @@ class DogsTrainer:
             self._prefetch(nxt % len(self.view_sets), nxt % 2)
         if c and self.adaptive is not None and self.t < self.adaptive.freeze_after:
             self._adapt_penalty()
+        if c and self.densify_cfg is not None and self.densify_cfg.due(self.t):
+            self.densify_log.append(dict(DZ.densify(self, self.densify_cfg, self.extent, self.t), t=self.t))
         self.t += 1
+
+    def _stats_on(self) -> bool:
+        """Whether this iteration adds to the densification statistic."""
+        return self.densify_cfg is not None and self.t < self.densify_cfg.until
 
     def _adapt_penalty(self) -> None:
         """Eq. 10 after a consensus: read the residuals (one synchronisation),

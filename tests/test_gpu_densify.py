@@ -1,0 +1,157 @@
+"""Densification under consensus on the GPU against the FP64 oracle
+(decisions and offsets bit-exact, both in FP32; parameters within the
+parity bar), and in the trainer: the rebuilt layout keeps every invariant of
+the consensus and training goes on."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2405_13943_b300 import synth as S
+
+pytestmark = pytest.mark.gpu
+REL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_13943_b300 import build as B
+    B.build()
+    from oracle import oracle as O
+    from paper_2405_13943_b300 import dogs, serve, trainer
+    return dogs, O, serve, trainer
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def problem(seed, n_pts=4000, deg=1):
+    rng = np.random.default_rng(seed)
+    xy = rng.uniform(0, 100, (n_pts, 2))
+    split, order = S.block_split(xy, 2, 2, [0.3, 0.2, 0.35, 0.15], 0.1)
+    z = S.cube_scene(n_pts, seed, sh_degree=deg).subset(order)
+    # spread the decisions: opacity logits around logit(0.005), log-scales around log(0.01)
+    z.opacity_logits[:] = rng.normal(-5.3, 1.0, n_pts).astype(np.float32)
+    z.log_scales[:] = rng.normal(np.log(0.01), 0.7, (n_pts, 3)).astype(np.float32)
+    stats = np.empty(2 * split.n_copies, np.float32)
+    stats[1::2] = rng.integers(0, 4, split.n_copies).astype(np.float32)
+    stats[0::2] = (stats[1::2] * rng.uniform(0, 4e-4, split.n_copies)).astype(np.float32)
+    return split, z, stats
+
+
+def test_statistic_matches_oracle(mods):
+    D, O, _, _ = mods
+    cams = [S.cube_camera(64, 48), S.cube_camera(40, 40)]
+    cams[1].block = 1
+    vb = D.ViewBatch(cams, [0, 300, 500], 16, 16)
+    rng = np.random.default_rng(3)
+    n_rec = vb.n_rec
+    rect = np.zeros((n_rec, 2), np.uint32)
+    kept = rng.random(n_rec) < 0.6
+    rect[kept, 1] = 1 | (1 << 16)                      # a one-tile rectangle [0,1) x [0,1)
+    drec = rng.normal(0, 1e-3, (n_rec, 12)).astype(np.float32)
+    vb.rect.copy_(torch.from_numpy(rect.view(np.int32).reshape(-1)))
+    vb.drec.copy_(torch.from_numpy(drec.reshape(-1)))
+    stats = torch.zeros(2 * 500, dtype=torch.float32, device="cuda")
+    for _ in range(2):                                  # two iterations accumulate
+        D.dg_densify_stats(vb, stats)
+    torch.cuda.synchronize()
+    owner = np.concatenate([np.arange(0, 300), np.arange(300, 500)])
+    wh = np.array([[64, 48]] * 300 + [[40, 40]] * 200)
+    s, c = O.densify_stats(kept, drec[:, :2], wh, owner, 500)
+    got = stats.cpu().numpy()
+    np.testing.assert_allclose(got[0::2], 2 * s, rtol=1e-5, atol=1e-9)
+    np.testing.assert_array_equal(got[1::2], 2 * c)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_decisions_offsets_and_emission_match_oracle(mods, seed):
+    D, O, _, _ = mods
+    split, z, stats = problem(seed)
+    zb = D.GaussianBuffer.from_synth(z)
+    g_off = torch.from_numpy(split.g_off).cuda()
+    g_cp = torch.from_numpy(split.g_copies).cuda()
+    st = torch.from_numpy(stats).cuda()
+    kw = dict(grad_threshold=2e-4, percent_dense=0.01, extent=1.0, min_opacity=0.005)
+    codes, offsets = D.dg_densify_decide(zb, g_off, g_cp, st, **kw)
+    torch.cuda.synchronize()
+    oz = O.params_from(z)
+    want = O.densify_decide(oz, 1, stats[0::2], stats[1::2], split.g_off, split.g_copies, **kw)
+    got = codes.cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    assert len(set(want.tolist())) == 4                 # every branch taken
+    counts = np.where(want == O.DENSIFY_PRUNE, 0, np.where(want == O.DENSIFY_KEEP, 1, 2))
+    off = offsets.cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(off, np.concatenate([[0], np.cumsum(counts)]))
+    # emission from seeded normals
+    xi = np.random.default_rng(seed + 100).normal(size=(z.n, 2, 3)).astype(np.float32)
+    n_out = int(off[-1])
+    zn, src, orig = D.dg_densify_emit(zb, codes, offsets, torch.from_numpy(xi.reshape(-1)).cuda(), n_out)
+    torch.cuda.synchronize()
+    ozn, osrc, oorig = O.densify_emit(oz, 1, want, xi.astype(np.float64))
+    np.testing.assert_array_equal(src.cpu().numpy(), osrc)
+    np.testing.assert_array_equal(orig.cpu().numpy().astype(bool), oorig)
+    g, w = O.split_params(O.params_from(zn.to_synth()), 1), O.split_params(ozn, 1)
+    for name in ("mean", "quat", "scale", "sh", "opacity"):
+        assert rel_l2(g[name], w[name]) <= 1e-6, name
+    # copied rows are exact
+    same = ~np.isin(np.arange(n_out), np.nonzero(want[osrc] == O.DENSIFY_SPLIT)[0])
+    np.testing.assert_array_equal(O.params_from(zn.to_synth())[same], ozn[same].astype(np.float32))
+
+
+def test_gather_rows_leaves_negative_rows(mods):
+    D, O, _, _ = mods
+    a = D.GaussianBuffer.from_synth(S.cube_scene(50, 4, sh_degree=2))
+    b = D.GaussianBuffer.from_synth(S.cube_scene(30, 5, sh_degree=2))
+    before = b.to_synth()
+    idx = np.where(np.arange(30) % 3 == 0, -1, (np.arange(30) * 7) % 50).astype(np.int32)
+    D.dg_gather_rows(a, torch.from_numpy(idx).cuda(), b)
+    torch.cuda.synchronize()
+    pa, pb, p0 = O.params_from(a.to_synth()), O.params_from(b.to_synth()), O.params_from(before)
+    for r in range(30):
+        np.testing.assert_array_equal(pb[r], p0[r] if idx[r] < 0 else pa[idx[r]])
+
+
+def test_trainer_densifies_under_consensus(mods):
+    D, O, srv, T = mods
+    from paper_2405_13943_b300 import densify as DZ
+    wl = S.dogs_workload(40_000, 2, 2, 0.1, 41, views_per_step=1, pool=2, width=200, height=150)
+    z0 = D.GaussianBuffer.from_synth(wl.z0)
+    gt = D.GaussianBuffer.from_synth(wl.gt)
+    targets = [srv.render_views(gt, vs).image.clone() for vs in wl.views]
+    cfg = DZ.DensifyConfig(interval=2, start=2, until=7, grad_threshold=1e-6, min_opacity=0.3)
+    tr = T.DogsTrainer(wl.split, z0, wl.views, targets, rho=(1e-2,) * 5, loss="l1", intv=1, densify=cfg)
+    tr.calibrate_capacity()
+    n0 = tr.z.n
+    for _ in range(8):
+        tr.step()
+        torch.cuda.synchronize()
+        assert not tr.overflowed()
+    log = tr.densify_log
+    assert [e["t"] for e in log] == [2, 4, 6]
+    for e in log:
+        assert e["after"] == e["keep"] + 2 * (e["clone"] + e["split"])
+        assert e["prune"] > 0 and e["clone"] + e["split"] > 0
+    assert tr.z.n == log[-1]["after"] and tr.z.n != n0
+    sp = tr.split
+    # layout invariants: every global held, shared ones first and held by several blocks
+    cnt = np.diff(sp.g_off)
+    assert (cnt >= 1).all() and tr._shared_first
+    assert int(sp.copy_shared().sum()) == int(cnt[cnt > 1].sum())
+    # after the consensus of the last iteration the duals of each shared global
+    # sum to zero, up to a few ulps of the parameters (positions are ~1e3 m)
+    u = O.params_from(tr.u.to_synth())
+    zz = O.params_from(tr.z.to_synth())
+    tol = 8 * 2.0 ** -23 * np.abs(zz).max(0) + 1e-6
+    for i in np.nonzero(cnt > 1)[0][:500]:
+        cps = sp.g_copies[sp.g_off[i]:sp.g_off[i + 1]]
+        assert (np.abs(u[cps].sum(0)) <= tol).all()
+    # unshared copies equal their global after the consensus
+    un = np.nonzero(cnt == 1)[0]
+    x = O.params_from(tr.x.to_synth())
+    z = O.params_from(tr.z.to_synth())
+    np.testing.assert_array_equal(x[sp.g_copies[sp.g_off[un]]], z[un])
+    assert np.isfinite(tr.vb.loss.cpu().numpy()).all()
