@@ -78,6 +78,10 @@ class DogsTrainer:
             self.extent = densify.extent if densify.extent is not None else \
                 DZ.scene_extent([c for vs in self.view_sets for c in vs])
         self.densify_log: List[Dict] = []
+        # the layout the run starts from: a checkpoint of a later (densified)
+        # layout of the same run can be resumed on a trainer built on it
+        from .checkpoint import split_fingerprint
+        self.split_origin = split_fingerprint(split)
         gid = torch.from_numpy(split.copy_gid.astype(np.int32)).to(device)
         x = gather_copies(z0, gid)
         self.install_split(split, z0, x, x.like(), x.like(), x.like(), capacity=capacity)
@@ -92,10 +96,12 @@ class DogsTrainer:
 
     # ---- the block layout and the state on it --------------------------------------
     def install_split(self, split: S.BlockSplit, z: D.GaussianBuffer, x: D.GaussianBuffer, m: D.GaussianBuffer,
-                      v: D.GaussianBuffer, u: D.GaussianBuffer, capacity: Optional[int] = None) -> None:
+                      v: D.GaussianBuffer, u: D.GaussianBuffer, capacity: Optional[int] = None,
+                      calibrate: bool = True) -> None:
         """Take a block layout with its global model, copies, Adam moments and
         scaled duals: the sharing map, the anchors z - u, the batch plan for
-        the view sets and (after a first install) the instance capacity are
+        the view sets and (after a first install, unless the caller fills the
+        buffers afterwards and calibrates then) the instance capacity are
         rebuilt; captured graphs are dropped."""
         dev = self.device
         first = not hasattr(self, "split")
@@ -129,7 +135,7 @@ class DogsTrainer:
                          for vs in self.view_sets]
         self.graphs = {}
         self._idle_queued = False
-        if not first:
+        if not first and calibrate:
             self.calibrate_capacity()
 
     # ---- rasteriser configuration (autotuner) ------------------------------------

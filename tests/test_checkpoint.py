@@ -127,3 +127,51 @@ def test_header_is_plain_json(tmp_path):
         h = json.loads(f.read(hlen))
     assert h["t"] == 1234 and [e["name"] for e in h["buffers"]] == list(CK.BUFFERS)
     assert start == -(-(24 + hlen) // 4096) * 4096
+
+
+class DensifiedRun(HostRun):
+    """A run whose layout changed after it started (a densification): it
+    keeps the fingerprint of its original layout and installs a stored one."""
+
+    def __init__(self, seed, layout_seed):
+        super().__init__(seed, split_seed=1)
+        self.split_origin = CK.split_fingerprint(self.split)
+        if layout_seed != 1:                           # the run after its layout changed
+            rng = np.random.default_rng(layout_seed)
+            xy = rng.uniform(0, 100, (620, 2))
+            self._install(S.block_split(xy, 2, 2, [0.25] * 4, 0.1)[0])
+            g = torch.Generator().manual_seed(seed + 100)
+            for name in ("z", "x", "u", "m", "v"):
+                getattr(self, name).data.copy_(torch.randn(getattr(self, name).data.numel(), generator=g))
+        self.dstats = torch.arange(2 * self.split.n_copies, dtype=torch.float32)
+        self.installs = 0
+
+    def _install(self, split):
+        self.split = split
+        self.z = D.GaussianBuffer(split.n_globals, 1, "cpu")
+        for name in ("x", "u", "m", "v", "anchor"):
+            setattr(self, name, D.GaussianBuffer(split.n_copies, 1, "cpu"))
+
+    def install_split(self, split, z, x, m, v, u, calibrate=True):
+        self.split, self.z, self.x, self.m, self.v, self.u = split, z, x, m, v, u
+        self.dstats = torch.zeros(2 * split.n_copies, dtype=torch.float32)
+        self.installs += 1
+
+
+def test_densified_layout_is_stored_and_installed(tmp_path):
+    a = DensifiedRun(21, layout_seed=7)
+    p = str(tmp_path / "d.ckpt")
+    CK.save(a, p)
+    hdr = CK.read_header(p)
+    assert {e["name"] for e in hdr["arrays"]} >= {"split.copy_gid", "split.g_copies", "dstats"}
+    b = DensifiedRun(22, layout_seed=1)               # built on the original layout
+    CK.load(b, p)
+    assert b.installs == 1 and CK.split_fingerprint(b.split) == CK.split_fingerprint(a.split)
+    for name in ("z", "x", "u", "m", "v"):
+        assert torch.equal(getattr(a, name).data.view(torch.int32), getattr(b, name).data.view(torch.int32))
+    assert torch.equal(a.dstats, b.dstats)
+    # a run from another original layout refuses it
+    c = DensifiedRun(23, layout_seed=1)
+    c.split_origin = "another run"
+    with pytest.raises(CK.CheckpointError, match="split"):
+        CK.load(c, p)

@@ -155,3 +155,36 @@ def test_trainer_densifies_under_consensus(mods):
     z = O.params_from(tr.z.to_synth())
     np.testing.assert_array_equal(x[sp.g_copies[sp.g_off[un]]], z[un])
     assert np.isfinite(tr.vb.loss.cpu().numpy()).all()
+
+
+def test_checkpoint_after_densification_resumes(mods, tmp_path):
+    """A checkpoint taken after a densification carries the new layout and
+    the statistics; a trainer built on the run's original layout takes them
+    and continues as the original run does."""
+    D, O, srv, T = mods
+    from paper_2405_13943_b300 import densify as DZ
+    wl = S.dogs_workload(30_000, 2, 2, 0.1, 43, views_per_step=1, pool=2, width=160, height=120)
+    gt = D.GaussianBuffer.from_synth(wl.gt)
+    targets = [srv.render_views(gt, vs).image.clone() for vs in wl.views]
+    cfg = DZ.DensifyConfig(interval=2, start=2, until=9, grad_threshold=1e-6, min_opacity=0.3)
+    kw = dict(rho=(1e-2,) * 5, loss="l1", intv=1, densify=cfg)
+    a = T.DogsTrainer(wl.split, D.GaussianBuffer.from_synth(wl.z0), wl.views, targets, **kw)
+    a.calibrate_capacity()
+    for _ in range(4):                                  # densifies at t = 2
+        a.step()
+    p = str(tmp_path / "dens.ckpt")
+    a.save_checkpoint(p)
+    b = T.DogsTrainer(wl.split, D.GaussianBuffer.from_synth(wl.z0), wl.views, targets, **kw)
+    b.load_checkpoint(p)
+    torch.cuda.synchronize()
+    assert b.t == a.t and b.z.n == a.z.n and b.split.n_copies == a.split.n_copies
+    for n in ("z", "x", "u", "m", "v"):
+        assert torch.equal(getattr(a, n).data, getattr(b, n).data), n
+    assert torch.equal(a.dstats, b.dstats)
+    for _ in range(3):                                  # densifies again at t = 4 and 6 on both
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    assert a.z.n == b.z.n
+    ga, gb = O.params_from(a.z.to_synth()), O.params_from(b.z.to_synth())
+    assert rel_l2(gb, ga) <= REL
