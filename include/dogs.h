@@ -367,6 +367,23 @@ int dg_densify_emit(const dg_gaussians* z, const int32_t* codes, const uint32_t*
                     const float* normals, dg_gaussians* out, int32_t* src, uint8_t* original,
                     void* stream);
 
+/* ---- Copy layout of a block membership (host, no GPU) ---------------------
+ * member[i]: bit k set when point i belongs to block k (K <= DG_MAX_BLOCKS,
+ * every point in at least one block).  dg_layout_copies returns the number
+ * of copies (the set bits), -1 on bad arguments.  dg_layout numbers the
+ * globals (order[g] = the point that becomes global g): those in two or more
+ * blocks first (*n_shared of them), each part by (lowest block, Z-order of
+ * (x, y) = xy[2i], xy[2i+1] quantised to 16 bits over their bounding box);
+ * copy_gid lists block k's copies in [blk_off[k], blk_off[k+1]), its shared
+ * globals in ascending id then its unshared ones (blk_nshared[k] shared);
+ * g_off[n + 1] / g_copies: each global's copies in ascending block.  Arrays
+ * are host memory sized n (order, g_off: n + 1), K + 1, K and the copy count.
+ * DG_ERR_INVALID on bad sizes, null pointers or a point in no block. */
+int64_t dg_layout_copies(const uint64_t* member, int64_t n);
+int dg_layout(const double* xy, const uint64_t* member, int64_t n, int K, int32_t* order,
+              int32_t* copy_gid, int64_t* blk_off, int64_t* blk_nshared, int64_t* g_off,
+              int32_t* g_copies, int64_t* n_shared);
+
 /* dst row r = src row idx[r] (all fields and SH planes) for r < dst->n;
  * rows with idx[r] < 0 are left unchanged.  The rows move between the
  * library layouts of the two sets (same SH degree, any ld); idx[r] must be

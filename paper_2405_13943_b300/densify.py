@@ -21,6 +21,7 @@ consensus, `densify(trainer, cfg)`:
 """
 from __future__ import annotations
 
+import time
 from dataclasses import dataclass
 from typing import Dict, Optional, Sequence
 
@@ -54,32 +55,32 @@ def scene_extent(cams: Sequence[S.Camera]) -> float:
 
 
 def membership(split: S.BlockSplit) -> np.ndarray:
-    """(n_global, K) bool: the blocks that hold each global Gaussian."""
-    K = split.K
-    m = np.zeros((split.n_globals, K), bool)
-    for k in range(K):
-        m[split.copy_gid[split.blk_off[k]:split.blk_off[k + 1]], k] = True
+    """uint64 per global Gaussian: bit k set when block k holds it."""
+    m = np.zeros(split.n_globals, np.uint64)
+    for k in range(split.K):
+        m[split.copy_gid[split.blk_off[k]:split.blk_off[k + 1]]] |= np.uint64(1) << np.uint64(k)
     return m
 
 
 def carried_copies(old: S.BlockSplit, new: S.BlockSplit, src_of_new_global: np.ndarray,
                    original: np.ndarray) -> np.ndarray:
     """For every copy of the new layout, the copy of the old layout whose
-    state it takes over (-1: none): the same block and the parent Gaussian,
-    when the new Gaussian is its parent itself."""
+    state it takes over (-1: none): the parent Gaussian's copy in the same
+    block, when the new Gaussian is its parent itself.  The parent's copies
+    are looked up through the old sharing map (a few per Gaussian)."""
     K = old.K
-    old_blk = np.repeat(np.arange(K), np.diff(old.blk_off))
-    key_old = old.copy_gid.astype(np.int64) * K + old_blk
-    order = np.argsort(key_old, kind="stable")
-    key_sorted = key_old[order]
-    new_blk = np.repeat(np.arange(K), np.diff(new.blk_off))
+    old_blk = np.repeat(np.arange(K, dtype=np.int32), np.diff(old.blk_off))
+    new_blk = np.repeat(np.arange(K, dtype=np.int32), np.diff(new.blk_off))
     g_new = new.copy_gid.astype(np.int64)
     parent = src_of_new_global[g_new].astype(np.int64)
-    want = parent * K + new_blk
-    pos = np.searchsorted(key_sorted, want)
-    pos_c = np.minimum(pos, len(key_sorted) - 1)
-    found = (len(key_sorted) > 0) & (key_sorted[pos_c] == want) & original[g_new]
-    return np.where(found, order[pos_c], -1).astype(np.int32)
+    start, cnt = old.g_off[parent], np.diff(old.g_off)[parent]
+    carry = np.full(new.n_copies, -1, np.int64)
+    for j in range(int(cnt.max()) if cnt.size else 0):
+        has = cnt > j
+        cand = np.where(has, old.g_copies[np.minimum(start + j, len(old.g_copies) - 1)], 0)
+        hit = has & (old_blk[cand] == new_blk)
+        carry = np.where(hit, cand, carry)
+    return np.where(original[g_new], carry, -1).astype(np.int32)
 
 
 def densify(tr, cfg: DensifyConfig, extent: float, step_seed: int) -> Dict:
@@ -87,6 +88,7 @@ def densify(tr, cfg: DensifyConfig, extent: float, step_seed: int) -> Dict:
     counts of the decisions and the sizes before and after."""
     dev = tr.z.data.device
     torch.cuda.synchronize()
+    t0 = time.perf_counter()
     z = tr.z
     codes, offsets = D.dg_densify_decide(z, tr.g_off, tr.g_copies, tr.dstats, cfg.grad_threshold,
                                          cfg.percent_dense, extent, cfg.min_opacity)
@@ -98,11 +100,13 @@ def densify(tr, cfg: DensifyConfig, extent: float, step_seed: int) -> Dict:
     c = np.bincount(codes.cpu().numpy(), minlength=4)
     src_h = src.cpu().numpy().astype(np.int64)
     orig_h = orig.cpu().numpy().astype(bool)
+    t1 = time.perf_counter()
     # the new layout: every Gaussian in its parent's blocks
     old = tr.split
     member = membership(old)[src_h]
     xy = z_tmp.data[:4 * z_tmp.ld].view(z_tmp.ld, 4)[:n_out, :2].double().cpu().numpy()
-    new_split, order = S.split_layout(xy, member, old.cells, old.band)
+    new_split, order = native_layout(xy, member, old.cells, old.band, K=old.K)
+    t2 = time.perf_counter()
     order_t = torch.from_numpy(order.astype(np.int32)).to(dev)
     z_new = D.GaussianBuffer(n_out, z.deg, dev)
     D.dg_gather_rows(z_tmp, order_t, z_new)
@@ -120,8 +124,45 @@ def densify(tr, cfg: DensifyConfig, extent: float, step_seed: int) -> Dict:
         D.dg_gather_rows(getattr(tr, name), carry, b)
         bufs[name] = b
     del z_tmp
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
     tr.install_split(new_split, z_new, x_new, bufs["m"], bufs["v"], bufs["u"])
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
     return {"before": int(z.n), "after": int(n_out), "keep": int(c[D.L.DG_DENSIFY_KEEP]),
             "prune": int(c[D.L.DG_DENSIFY_PRUNE]), "clone": int(c[D.L.DG_DENSIFY_CLONE]),
             "split": int(c[D.L.DG_DENSIFY_SPLIT]), "copies": int(n_c),
-            "carried_copies": int((carry >= 0).sum().item())}
+            "carried_copies": int((carry >= 0).sum().item()),
+            "seconds": {"decide_emit": round(t1 - t0, 3), "layout": round(t2 - t1, 3), "state": round(t3 - t2, 3),
+                        "install": round(t4 - t3, 3)}}
+
+
+def native_layout(xy: np.ndarray, member: np.ndarray, cells: np.ndarray, band: float, K: Optional[int] = None):
+    """synth.split_layout's layout, computed by the library's host code
+    (dg_layout, linear passes): (BlockSplit, order).  member: (n, K) bool,
+    or uint64 bit masks with K given."""
+    from . import _lib as L
+    if member.dtype == np.uint64:
+        bits, n = np.ascontiguousarray(member), member.shape[0]
+    else:
+        n, K = member.shape
+        packed = np.packbits(member, axis=1, bitorder="little")
+        pad = np.zeros((n, 8), np.uint8)
+        pad[:, :packed.shape[1]] = packed
+        bits = pad.view(np.uint64).reshape(n)
+    xy = np.ascontiguousarray(xy[:, :2], np.float64)
+    nc = int(L.lib().dg_layout_copies(bits.ctypes.data, n))
+    if nc < 0:
+        raise ValueError("bad membership")
+    order = np.empty(max(n, 1), np.int32)
+    copy_gid = np.empty(max(nc, 1), np.int32)
+    blk_off = np.empty(K + 1, np.int64)
+    blk_nsh = np.empty(K, np.int64)
+    g_off = np.empty(n + 1, np.int64)
+    g_cp = np.empty(max(nc, 1), np.int32)
+    ns = np.zeros(1, np.int64)
+    L.check(L.lib().dg_layout(xy.ctypes.data, bits.ctypes.data, n, K, order.ctypes.data, copy_gid.ctypes.data,
+                              blk_off.ctypes.data, blk_nsh.ctypes.data, g_off.ctypes.data, g_cp.ctypes.data,
+                              ns.ctypes.data), "dg_layout")
+    split = S.BlockSplit(copy_gid[:nc], blk_off, blk_nsh, g_off, g_cp[:nc], int(ns[0]), cells, band)
+    return split, order[:n].astype(np.int64)

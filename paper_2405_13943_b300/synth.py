@@ -397,7 +397,7 @@ def split_layout(xy: np.ndarray, member: np.ndarray, cells: np.ndarray, band: fl
     shared = cnt >= 2
     first_blk = np.argmax(member, axis=1)
     # renumber: shared first (sorted by first block, then Z-order), unshared by block
-    key_sh = np.lexsort((morton2d(xy), first_blk))
+    key_sh = np.argsort((first_blk.astype(np.uint64) << np.uint64(32)) | morton2d(xy), kind="stable")
     sh_pts = key_sh[shared[key_sh]]
     un_pts = key_sh[~shared[key_sh]]
     un_pts = un_pts[np.argsort(first_blk[un_pts], kind="stable")]

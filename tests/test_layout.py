@@ -1,0 +1,68 @@
+"""The library's host layout builder (dg_layout) gives the same global
+numbering, block-local copies and sharing map as the reference numpy layout
+of the input generator (synth.split_layout), and rejects a point in no
+block."""
+import numpy as np
+import pytest
+
+from paper_2405_13943_b300 import build as B
+from paper_2405_13943_b300 import synth as S
+
+
+@pytest.fixture(scope="module")
+def DZ():
+    B.build()
+    from paper_2405_13943_b300 import densify
+    return densify
+
+
+@pytest.mark.parametrize("n,K,seed", [(1, 1, 0), (500, 1, 1), (3000, 4, 2), (20000, 8, 3), (4000, 37, 4),
+                                      (5000, 64, 5)])
+def test_native_layout_equals_reference(DZ, n, K, seed):
+    rng = np.random.default_rng(seed)
+    xy = rng.uniform(-50, 900, (n, 2))
+    xy[: n // 10] = xy[0]                           # ties in position
+    member = np.zeros((n, K), bool)
+    member[np.arange(n), rng.integers(0, K, n)] = True
+    extra = rng.random((n, K)) < (0.15 / K)
+    member |= extra
+    a, oa = S.split_layout(xy, member, np.zeros((K, 4)), 1.0)
+    b, ob = DZ.native_layout(xy, member, np.zeros((K, 4)), 1.0)
+    np.testing.assert_array_equal(oa, ob)
+    for f in ("copy_gid", "blk_off", "blk_nshared", "g_off", "g_copies"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f), err_msg=f)
+    assert a.n_shared_globals == b.n_shared_globals
+
+
+def test_native_layout_rejects_a_point_in_no_block(DZ):
+    member = np.zeros((3, 2), bool)
+    member[0, 0] = member[2, 1] = True
+    with pytest.raises(Exception):
+        DZ.native_layout(np.zeros((3, 2)), member, np.zeros((2, 4)), 1.0)
+
+
+def test_carried_copies_by_brute_force(DZ):
+    """The copy whose state a new copy takes over: the parent's copy in the
+    same block when the new Gaussian is its parent itself, else none."""
+    rng = np.random.default_rng(6)
+    n, K = 3000, 6
+    xy = rng.uniform(0, 100, (n, 2))
+    member = np.zeros((n, K), bool)
+    member[np.arange(n), rng.integers(0, K, n)] = True
+    member[rng.random(n) < 0.2, 2] = True
+    old, _ = S.split_layout(xy, member, np.zeros((K, 4)), 1.0)
+    outs = rng.integers(0, 3, n)                        # pruned, kept or cloned
+    src = np.repeat(np.arange(n), outs)
+    orig = np.ones(len(src), bool)
+    orig[1:] &= src[1:] != src[:-1]                     # the second of a pair is the copy
+    new, order = DZ.native_layout(rng.uniform(0, 100, (len(src), 2)), DZ.membership(old)[src],
+                                  np.zeros((K, 4)), 1.0, K=K)
+    src_new, orig_new = src[order], orig[order]
+    got = DZ.carried_copies(old, new, src_new, orig_new)
+    oblk = np.repeat(np.arange(K), np.diff(old.blk_off))
+    nblk = np.repeat(np.arange(K), np.diff(new.blk_off))
+    where = {(int(old.copy_gid[i]), int(oblk[i])): i for i in range(old.n_copies)}
+    want = [where.get((int(src_new[g]), int(nblk[i])), -1) if orig_new[g] else -1
+            for i, g in enumerate(new.copy_gid)]
+    np.testing.assert_array_equal(got, want)
+    assert 0 < (got >= 0).mean() < 1
