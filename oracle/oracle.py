@@ -642,3 +642,13 @@ def densify_emit(z: np.ndarray, sh_degree: int, codes: np.ndarray, normals: np.n
     P = z.shape[1]
     z_new = np.array(out, np.float64).reshape(-1, P)
     return z_new, np.array(src, np.int64), np.array(orig, bool)
+
+
+def reset_opacity(x: np.ndarray, sh_degree: int, cap: float = 0.01) -> np.ndarray:
+    """The opacity reset of the 3DGS density control the densification
+    follows: every opacity above `cap` is brought down to it (on the logit:
+    min(o, logit(cap))).  Returns a new parameter array."""
+    y = x.copy()
+    o = split_params(y, sh_degree)["opacity"]
+    o[:] = np.minimum(o, np.log(cap / (1.0 - cap)))
+    return y

@@ -103,3 +103,14 @@ def test_split_children_follow_the_parent_distribution():
     got = d.T @ d / d.shape[0]
     assert np.abs(got - want).max() <= 0.02 * np.abs(want).max()
     assert np.abs(d.mean(0)).max() <= 0.01 * np.sqrt(np.diag(want)).max()
+
+
+def test_opacity_reset_by_hand():
+    z = gaussians(3)
+    P = O.split_params(z, 1)
+    P["opacity"][:] = [-10.0, 0.0, 3.0]
+    r = O.split_params(O.reset_opacity(z, 1, 0.01), 1)
+    cap = np.log(0.01 / 0.99)
+    np.testing.assert_allclose(r["opacity"], [-10.0, cap, cap])
+    np.testing.assert_allclose(1 / (1 + np.exp(-r["opacity"][1:])), 0.01)
+    np.testing.assert_array_equal(r["mean"], P["mean"])
