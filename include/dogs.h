@@ -367,6 +367,13 @@ int dg_densify_emit(const dg_gaussians* z, const int32_t* codes, const uint32_t*
                     const float* normals, dg_gaussians* out, int32_t* src, uint8_t* original,
                     void* stream);
 
+/* The opacity reset of the density control: every opacity of g above `cap`
+ * (0 < cap < 1) is brought down to it, i.e. the logit becomes
+ * min(logit, log(cap / (1 - cap))) (formed in double, rounded once); where m
+ * / v are given (Adam's moments in g's layout, may be NULL) their opacity
+ * lanes are zeroed. */
+int dg_reset_opacity(dg_gaussians* g, float cap, dg_gaussians* m, dg_gaussians* v, void* stream);
+
 /* ---- Copy layout of a block membership (host, no GPU) ---------------------
  * member[i]: bit k set when point i belongs to block k (K <= DG_MAX_BLOCKS,
  * every point in at least one block).  dg_layout_copies returns the number

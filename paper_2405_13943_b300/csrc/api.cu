@@ -43,6 +43,7 @@ int launch_densify_decide(const dg_gaussians*, const int64_t*, const int32_t*, c
 int launch_densify_emit(const dg_gaussians*, const int32_t*, const uint32_t*, const float*, dg_gaussians*, int32_t*,
                         uint8_t*, cudaStream_t);
 int launch_gather_rows(const dg_gaussians*, const int32_t*, dg_gaussians*, cudaStream_t);
+int launch_reset_opacity(dg_gaussians*, float, dg_gaussians*, dg_gaussians*, cudaStream_t);
 int launch_xstep(int, int, dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*, const uint8_t*,
                  const dg_camera*, const dg_plan&, const uint2*, const float4*, const AdamArgs&, const int32_t*,
                  dg_gaussians*, const int32_t*, cudaStream_t);
@@ -407,6 +408,14 @@ int dg_gather_rows(const dg_gaussians* src, const int32_t* idx, dg_gaussians* ds
     if (!valid_gauss(src) || !valid_gauss(dst) || src->sh_degree != dst->sh_degree) return DG_ERR_INVALID;
     if (dst->n > 0 && !idx) return DG_ERR_INVALID;
     return launch_gather_rows(src, idx, dst, (cudaStream_t)stream);
+}
+
+int dg_reset_opacity(dg_gaussians* g, float cap, dg_gaussians* m, dg_gaussians* v, void* stream)
+{
+    if (!valid_gauss(g) || !(cap > 0.f && cap < 1.f)) return DG_ERR_INVALID;
+    if ((m && !same_layout(g, m)) || (v && !same_layout(g, v))) return DG_ERR_INVALID;
+    const double c = (double)cap;
+    return launch_reset_opacity(g, (float)log(c / (1.0 - c)), m, v, (cudaStream_t)stream);
 }
 
 int dg_admm_scale_duals(dg_gaussians* u, const uint8_t* copy_shared, const float* factor, void* stream)

@@ -221,6 +221,20 @@ __global__ void __launch_bounds__(kDensifyThreads) k_gather_rows(GView s, const 
     if (i >= 0) copy_row(s, i, d, r, np);
 }
 
+// opacity reset: logit = min(logit, cap) on every row; where the moments are
+// given, their opacity lanes restart from zero
+__global__ void __launch_bounds__(kDensifyThreads) k_reset_opacity(GView g, float cap, float4* __restrict__ m,
+                                                                   float4* __restrict__ v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    float4 mo = g.mo[i];
+    mo.w = fminf(mo.w, cap);
+    g.mo[i] = mo;
+    if (m) m[i].w = 0.f;
+    if (v) v[i].w = 0.f;
+}
+
 static unsigned blocks_of(int64_t n) { return (unsigned)((n + kDensifyThreads - 1) / kDensifyThreads); }
 
 int launch_densify_stats(const uint2* rect, const float* drec, const dg_camera* cams, const dg_plan& plan,
@@ -276,4 +290,16 @@ int launch_gather_rows(const dg_gaussians* s, const int32_t* idx, dg_gaussians* 
     return DG_OK;
 }
 
+}  // namespace dg
+
+namespace dg {
+int launch_reset_opacity(dg_gaussians* g, float cap, dg_gaussians* m, dg_gaussians* v, cudaStream_t st)
+{
+    if (g->n == 0) return DG_OK;
+    k_reset_opacity<<<blocks_of(g->n), kDensifyThreads, 0, st>>>(gview(g), cap, m ? gview(m).mo : nullptr,
+                                                                 v ? gview(v).mo : nullptr);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
 }  // namespace dg

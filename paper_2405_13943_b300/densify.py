@@ -42,9 +42,23 @@ class DensifyConfig:
     min_opacity: float = 0.005      # prune below this opacity
     extent: Optional[float] = None  # scene extent; None: from the camera centres (scene_extent)
     seed: int = 0                   # seed of the split normals (advanced per densification)
+    opacity_reset: int = 3000       # cap every opacity at reset_cap every this many iterations (0: never)
+    reset_cap: float = 0.01
 
     def due(self, t: int) -> bool:
         return self.start <= t < self.until and t % self.interval == 0
+
+    def reset_due(self, t: int) -> bool:
+        return self.opacity_reset > 0 and 0 < t < self.until and t % self.opacity_reset == 0
+
+
+def reset_opacity(tr, cfg: DensifyConfig) -> None:
+    """The opacity reset of the density control on z and on every copy (their
+    moments' opacity lanes restart from zero), after a consensus; the anchors
+    z - u are rebuilt."""
+    D.dg_reset_opacity(tr.z, cfg.reset_cap)
+    D.dg_reset_opacity(tr.x, cfg.reset_cap, tr.m, tr.v)
+    D.dg_admm_anchor(tr.z, tr.u, tr.gid, tr.shared, tr.anchor)
 
 
 def scene_extent(cams: Sequence[S.Camera]) -> float:

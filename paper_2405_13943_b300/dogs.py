@@ -338,6 +338,13 @@ def dg_gather_rows(src: GaussianBuffer, idx: torch.Tensor, dst: GaussianBuffer, 
     L.check(L.lib().dg_gather_rows(src.ref, L.ptr(idx), dst.ref, L.stream_handle(stream)), "dg_gather_rows")
 
 
+def dg_reset_opacity(g: GaussianBuffer, cap: float = 0.01, m: Optional[GaussianBuffer] = None,
+                     v: Optional[GaussianBuffer] = None, stream=None) -> None:
+    """Opacities above cap brought down to it; the moments' opacity lanes zeroed."""
+    L.check(L.lib().dg_reset_opacity(g.ref, float(cap), None if m is None else m.ref, None if v is None else v.ref,
+                                     L.stream_handle(stream)), "dg_reset_opacity")
+
+
 def dg_backward_xstep(vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer, v: GaussianBuffer,
                       anchor: Optional[GaussianBuffer], shared: Optional[torch.Tensor], rho, lr, beta1=0.9,
                       beta2=0.999, eps=1e-15, step=1, dev_step: Optional[torch.Tensor] = None, bg=(0.0, 0.0, 0.0),

@@ -71,8 +71,9 @@ class DogsTrainer:
         self.tile = tuple(tile)
         # densification under consensus (densify.DensifyConfig), statistics per copy
         self.densify_cfg = densify
-        if densify is not None and densify.interval % intv != 0:
-            raise ValueError("the densification interval must be a multiple of the consensus interval")
+        if densify is not None and (densify.interval % intv != 0 or densify.opacity_reset % intv != 0):
+            raise ValueError("the densification and opacity-reset intervals must be multiples of the "
+                             "consensus interval")
         self.extent = None
         if densify is not None:
             self.extent = densify.extent if densify.extent is not None else \
@@ -331,6 +332,8 @@ class DogsTrainer:
             self._adapt_penalty()
         if c and self.densify_cfg is not None and self.densify_cfg.due(self.t):
             self.densify_log.append(dict(DZ.densify(self, self.densify_cfg, self.extent, self.t), t=self.t))
+        if c and self.densify_cfg is not None and self.densify_cfg.reset_due(self.t):
+            DZ.reset_opacity(self, self.densify_cfg)
         self.t += 1
 
     def _stats_on(self) -> bool:

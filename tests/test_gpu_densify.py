@@ -188,3 +188,38 @@ def test_checkpoint_after_densification_resumes(mods, tmp_path):
     assert a.z.n == b.z.n
     ga, gb = O.params_from(a.z.to_synth()), O.params_from(b.z.to_synth())
     assert rel_l2(gb, ga) <= REL
+
+
+def test_opacity_reset_matches_oracle_and_runs_on_schedule(mods):
+    D, O, srv, T = mods
+    g = S.cube_scene(3000, 8, sh_degree=1)
+    g.opacity_logits[:] = np.random.default_rng(8).normal(-3.0, 2.0, g.n).astype(np.float32)
+    gb = D.GaussianBuffer.from_synth(g)
+    m, v = gb.like(), gb.like()
+    m.data.fill_(1.0)
+    v.data.fill_(2.0)
+    D.dg_reset_opacity(gb, 0.01, m, v)
+    torch.cuda.synchronize()
+    want = O.reset_opacity(O.params_from(g), 1, 0.01)
+    got = O.params_from(gb.to_synth())
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-6)
+    assert (got[:, -1] < want[:, -1] + 1e-6).all() and (g.opacity_logits < np.log(0.01 / 0.99)).any()
+    mm = O.params_from(m.to_synth())
+    assert (mm[:, -1] == 0).all() and (mm[:, :-1] == 1).all()
+    from paper_2405_13943_b300 import densify as DZ
+    wl = S.dogs_workload(20_000, 2, 2, 0.1, 47, views_per_step=1, pool=2, width=128, height=96)
+    gt = D.GaussianBuffer.from_synth(wl.gt)
+    targets = [srv.render_views(gt, vs).image.clone() for vs in wl.views]
+    cfg = DZ.DensifyConfig(interval=1000, start=1000, until=100, opacity_reset=3)
+    tr = T.DogsTrainer(wl.split, D.GaussianBuffer.from_synth(wl.z0), wl.views, targets, loss="l1", intv=1,
+                       densify=cfg)
+    tr.calibrate_capacity()
+    cap = np.log(0.01 / 0.99)
+    for t in range(4):
+        tr.step()
+        torch.cuda.synchronize()
+        zo = O.params_from(tr.z.to_synth())[:, -1]
+        if t == 3:
+            assert (zo <= cap + 1e-6).all()          # reset after the consensus of iteration 3
+        else:
+            assert (zo > cap + 1e-3).any()
