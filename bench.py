@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-seq", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-densify-probe", action="store_true", help="skip timing one densification at the end")
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-autotune", action="store_true", help="keep --tile and the default compositing variant")
     ap.add_argument("--idle-ctas", type=int, default=0,
@@ -468,6 +469,11 @@ def run_ours(args, dist, rank, world):
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline(wl, args)
 
+    # ---- one densification of the trained state (off the per-iteration path: every 200 iterations) --
+    densify = None
+    if not args.no_densify_probe:
+        densify = densify_probe(tr, wl, D)
+
     value = world * 1e3 / ms
     if rank == 0:
         line = {
@@ -497,7 +503,7 @@ def run_ours(args, dist, rank, world):
                        "setup_s": round(setup_s, 1)},
             "kernels_ms": kern, "eager_ms_per_step": round(eager_ms, 3),
             "roofline": roofline, "clocks": clk, "gpu_launches": int(launches_per_step * args.steps),
-            "e2e": e2e, "comparator": comparator, "render": render, "cpu_baseline": cpu,
+            "e2e": e2e, "comparator": comparator, "render": render, "cpu_baseline": cpu, "densify": densify,
         }
         print(json.dumps(line))
 
@@ -534,6 +540,35 @@ def run_e2e(tr, args, dist):
             "timing": "host wall clock per step; each step's target uploaded from pinned host memory one step "
                       "ahead on a copy stream, each step's losses copied back and read on the host while the "
                       "next step runs"}
+
+
+def densify_probe(tr, wl, D):
+    """The statistic over a few eager iterations (its kernel timed by CUDA
+    events), then one densification of the 6M-Gaussian state timed on the
+    host clock: decisions, emission, the layout rebuild and the state moved."""
+    import torch
+    from paper_2405_13943_b300 import densify as DZ
+    cfg = DZ.DensifyConfig(interval=tr.intv * 10007, start=0, until=1 << 30)   # due only when called below
+    tr.densify_cfg = cfg
+    tr.extent = DZ.scene_extent([c for vs in tr.view_sets for c in vs])
+    tr.dstats = torch.zeros(2 * tr.split.n_copies, dtype=torch.float32, device=tr.z.data.device)
+    ms = []
+    for _ in range(4):
+        tr.step(consensus=True, graph=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        D.dg_densify_stats(tr.vb, tr.dstats)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t0 = time.perf_counter()
+    out = DZ.densify(tr, cfg, tr.extent, tr.t)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return {"stats_kernel_ms": round(float(np.median(ms)), 4), "densify_s": round(wall, 3),
+            "extent_m": round(tr.extent, 1), **{k: v for k, v in out.items()},
+            "rule": "3DGS adaptive density control on the global model after a consensus: grad 2e-4, "
+                    "percent_dense 0.01, min_opacity 0.005 (statistics of 4 iterations)"}
 
 
 def run_serving(z, args, tile):
