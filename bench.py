@@ -177,16 +177,24 @@ def build_workload(name: str, views_per_block: int = 1):
 
 def render_targets(gt_buf, views, tile):
     """Targets: the ground-truth set rendered at each pool entry's views, laid
-    out as the training batch lays out its images (same view order/sizes)."""
+    out as the training batch lays out its images (same view order/sizes),
+    as 8-bit images like the training photographs they stand for.  Returns
+    (float32 device targets = bytes / 255, uint8 device targets)."""
     import torch
+    from paper_2405_13943_b300 import dogs as D
     from paper_2405_13943_b300 import serve
-    out = []
+    out, out8 = [], []
     for vs in views:
         rb = serve.render_views(gt_buf, vs, tile=tile)
-        out.append(rb.image.clone())
+        b = torch.empty(rb.image.numel(), dtype=torch.uint8, device=rb.image.device)
+        D.dg_image_f32_to_u8(rb.image, b)
+        f = torch.empty_like(rb.image)
+        D.dg_image_u8_to_f32(b, f)
+        out.append(f)
+        out8.append(b)
         del rb
     torch.cuda.synchronize()
-    return out
+    return out, out8
 
 
 # FP32 operations of the method per (pixel, Gaussian) pair, a multiply-add
@@ -276,7 +284,7 @@ def run_ours(args, dist, rank, world):
     wl = build_workload(args.workload, args.views_per_block)
     z0 = D.GaussianBuffer.from_synth(wl.z0)
     gt = D.GaussianBuffer.from_synth(wl.gt)
-    targets = render_targets(gt, wl.views, tile)
+    targets, targets8 = render_targets(gt, wl.views, tile)
     del gt
     if args.variant:
         D.set_raster_variant(*[int(v) for v in args.variant.split(",")])
@@ -433,7 +441,7 @@ def run_ours(args, dist, rank, world):
     # ---- end to end through host buffers ---------------------------------------------------
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(tr, args, dist)
+        e2e = run_e2e(tr, args, dist, targets8)
 
     # ---- sequential per-block comparator -----------------------------------------------------
     comparator = None
@@ -479,7 +487,7 @@ def run_ours(args, dist, rank, world):
         line = {
             "metric": METRIC, "value": round(value, 4), "unit": "iter/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (city-law aerial scene, seeded)",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (city-law aerial scene, seeded; targets 8-bit images)",
             "config": {"workload": f"DOGS K=8 batched, {WORKLOADS[args.workload]['n_global']} Gaussians SH3, "
                                    f"{wl.split.n_copies} copies, 10% shared, V={len(wl.views[0])} x "
                                    f"{WORKLOADS[args.workload]['width']}x{WORKLOADS[args.workload]['height']}",
@@ -508,14 +516,14 @@ def run_ours(args, dist, rank, world):
         print(json.dumps(line))
 
 
-def run_e2e(tr, args, dist):
+def run_e2e(tr, args, dist, targets8):
     """Same iterations through the trainer with its targets in pinned host
     memory: every step's target images cross host -> device (copied one step
     ahead on a side stream while the previous step computes) and every step's
     per-view losses are copied back and read on the host (step t's while step
     t + 1 runs), all inside the timed region."""
     import torch
-    host_t = [t.cpu().pin_memory() for t in tr.targets]
+    host_t = [t.cpu().pin_memory() for t in targets8]
     tr.use_host_targets(host_t)
     for _ in range(2):
         tr.step(consensus=True)
@@ -537,9 +545,9 @@ def run_e2e(tr, args, dist):
     return {"value": round(world * 1e3 / ms, 4), "unit": "iter/s", "ms_per_step": round(ms, 3),
             "h2d_bytes_per_step": tr.h2d_bytes_per_step(), "d2h_bytes_per_step": int(tr.host_loss[0].numel() * 8),
             "loss_last": losses[-1],
-            "timing": "host wall clock per step; each step's target uploaded from pinned host memory one step "
-                      "ahead on a copy stream, each step's losses copied back and read on the host while the "
-                      "next step runs"}
+            "timing": "host wall clock per step; each step's target (8-bit images) uploaded from pinned host "
+                      "memory one step ahead on a copy stream and widened on the device, each step's losses "
+                      "copied back and read on the host while the next step runs"}
 
 
 def densify_probe(tr, wl, D):

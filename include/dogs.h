@@ -367,6 +367,13 @@ int dg_densify_emit(const dg_gaussians* z, const int32_t* codes, const uint32_t*
                     const float* normals, dg_gaussians* out, int32_t* src, uint8_t* original,
                     void* stream);
 
+/* ---- 8-bit images (training targets cross the host link as bytes) -------
+ * dg_image_u8_to_f32: dst[i] = src[i] / 255 for i < n (device; src 4-byte
+ * and dst 16-byte aligned).  dg_image_f32_to_u8:
+ * dst[i] = round(clamp(src[i], 0, 1) * 255). */
+int dg_image_u8_to_f32(const uint8_t* src, float* dst, int64_t n, void* stream);
+int dg_image_f32_to_u8(const float* src, uint8_t* dst, int64_t n, void* stream);
+
 /* The opacity reset of the density control: every opacity of g above `cap`
  * (0 < cap < 1) is brought down to it, i.e. the logit becomes
  * min(logit, log(cap / (1 - cap))) (formed in double, rounded once); where m

@@ -105,6 +105,8 @@ _SIGS = {
     "dg_densify_emit": (C.c_int, [C.POINTER(DgGaussians), _vp, _vp, _vp, C.POINTER(DgGaussians), _vp, _vp, _vp]),
     "dg_gather_rows": (C.c_int, [C.POINTER(DgGaussians), _vp, C.POINTER(DgGaussians), _vp]),
     "dg_layout_copies": (C.c_int64, [_vp, C.c_int64]),
+    "dg_image_u8_to_f32": (C.c_int, [_vp, _vp, C.c_int64, _vp]),
+    "dg_image_f32_to_u8": (C.c_int, [_vp, _vp, C.c_int64, _vp]),
     "dg_reset_opacity": (C.c_int, [C.POINTER(DgGaussians), C.c_float, C.POINTER(DgGaussians),
                                    C.POINTER(DgGaussians), _vp]),
     "dg_layout": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),

@@ -44,6 +44,8 @@ int launch_densify_emit(const dg_gaussians*, const int32_t*, const uint32_t*, co
                         uint8_t*, cudaStream_t);
 int launch_gather_rows(const dg_gaussians*, const int32_t*, dg_gaussians*, cudaStream_t);
 int launch_reset_opacity(dg_gaussians*, float, dg_gaussians*, dg_gaussians*, cudaStream_t);
+int launch_u8_to_f32(const uint8_t*, float*, int64_t, cudaStream_t);
+int launch_f32_to_u8(const float*, uint8_t*, int64_t, cudaStream_t);
 int launch_xstep(int, int, dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*, const uint8_t*,
                  const dg_camera*, const dg_plan&, const uint2*, const float4*, const AdamArgs&, const int32_t*,
                  dg_gaussians*, const int32_t*, cudaStream_t);
@@ -408,6 +410,19 @@ int dg_gather_rows(const dg_gaussians* src, const int32_t* idx, dg_gaussians* ds
     if (!valid_gauss(src) || !valid_gauss(dst) || src->sh_degree != dst->sh_degree) return DG_ERR_INVALID;
     if (dst->n > 0 && !idx) return DG_ERR_INVALID;
     return launch_gather_rows(src, idx, dst, (cudaStream_t)stream);
+}
+
+int dg_image_u8_to_f32(const uint8_t* src, float* dst, int64_t n, void* stream)
+{
+    if (n < 0 || (n > 0 && (!src || !dst)) || ((uintptr_t)src & 3u) || !aligned16(dst))
+        return DG_ERR_INVALID;
+    return launch_u8_to_f32(src, dst, n, (cudaStream_t)stream);
+}
+
+int dg_image_f32_to_u8(const float* src, uint8_t* dst, int64_t n, void* stream)
+{
+    if (n < 0 || (n > 0 && (!src || !dst))) return DG_ERR_INVALID;
+    return launch_f32_to_u8(src, dst, n, (cudaStream_t)stream);
 }
 
 int dg_reset_opacity(dg_gaussians* g, float cap, dg_gaussians* m, dg_gaussians* v, void* stream)

@@ -7,6 +7,8 @@
 // map, and the three per-pixel partials dS/d(mean_x), dS/d(E[x^2]),
 // dS/d(E[xy]); the backward applies the same (symmetric) filter to those
 // partials: dL/dx = F(a) + 2 x F(b) + y F(c).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace dg {
@@ -380,6 +382,50 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const float* __restri
         }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// ---- 8-bit images ---------------------------------------------------------------
+// Training images are 8-bit; they cross the host link as bytes and widen on
+// the device (v / 255, correctly rounded), four per thread.
+__global__ void __launch_bounds__(256) k_u8_to_f32(const uint8_t* __restrict__ src, float* __restrict__ dst,
+                                                   int64_t n)
+{
+    const int64_t n4 = n / 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const uchar4 b = reinterpret_cast<const uchar4*>(src)[i];
+        reinterpret_cast<float4*>(dst)[i] = make_float4(__fdiv_rn((float)b.x, 255.f), __fdiv_rn((float)b.y, 255.f),
+                                                        __fdiv_rn((float)b.z, 255.f), __fdiv_rn((float)b.w, 255.f));
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (unsigned)(n - 4 * n4))   // the last n mod 4 bytes
+        dst[4 * n4 + threadIdx.x] = __fdiv_rn((float)src[4 * n4 + threadIdx.x], 255.f);
+}
+
+// round(clamp(v, 0, 1) * 255)
+__global__ void __launch_bounds__(256) k_f32_to_u8(const float* __restrict__ src, uint8_t* __restrict__ dst,
+                                                   int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (uint8_t)__float2int_rn(fminf(fmaxf(src[i], 0.f), 1.f) * 255.f);
+}
+
+int launch_u8_to_f32(const uint8_t* src, float* dst, int64_t n, cudaStream_t st)
+{
+    if (n == 0) return DG_OK;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n / 4 + 255) / 256, 148 * 16));
+    k_u8_to_f32<<<g, 256, 0, st>>>(src, dst, n);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
+int launch_f32_to_u8(const float* src, uint8_t* dst, int64_t n, cudaStream_t st)
+{
+    if (n == 0) return DG_OK;
+    const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    k_f32_to_u8<<<g, 256, 0, st>>>(src, dst, n);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
 }
 
 static int g_ssim_ctas[2] = {0, 0};   // resident CTAs per SM x SMs, for the forward and the backward

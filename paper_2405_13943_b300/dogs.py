@@ -345,6 +345,20 @@ def dg_reset_opacity(g: GaussianBuffer, cap: float = 0.01, m: Optional[GaussianB
                                      L.stream_handle(stream)), "dg_reset_opacity")
 
 
+def dg_image_u8_to_f32(src: torch.Tensor, dst: torch.Tensor, stream=None) -> None:
+    """dst (float32) = src (uint8) / 255, element by element."""
+    assert src.dtype == torch.uint8 and dst.dtype == torch.float32 and src.numel() == dst.numel()
+    L.check(L.lib().dg_image_u8_to_f32(L.ptr(src), L.ptr(dst), src.numel(), L.stream_handle(stream)),
+            "dg_image_u8_to_f32")
+
+
+def dg_image_f32_to_u8(src: torch.Tensor, dst: torch.Tensor, stream=None) -> None:
+    """dst (uint8) = round(clamp(src, 0, 1) * 255)."""
+    assert src.dtype == torch.float32 and dst.dtype == torch.uint8 and src.numel() == dst.numel()
+    L.check(L.lib().dg_image_f32_to_u8(L.ptr(src), L.ptr(dst), src.numel(), L.stream_handle(stream)),
+            "dg_image_f32_to_u8")
+
+
 def dg_backward_xstep(vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer, v: GaussianBuffer,
                       anchor: Optional[GaussianBuffer], shared: Optional[torch.Tensor], rho, lr, beta1=0.9,
                       beta2=0.999, eps=1e-15, step=1, dev_step: Optional[torch.Tensor] = None, bg=(0.0, 0.0, 0.0),

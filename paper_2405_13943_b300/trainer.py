@@ -210,14 +210,21 @@ class DogsTrainer:
 
     # ---- targets in host memory ----------------------------------------------------
     def use_host_targets(self, host_targets: Sequence[torch.Tensor]) -> None:
-        """Keep the pool's target images in pinned host memory.  Each step's
-        target is copied in on a side stream one step ahead, into one of two
-        device buffers, while the previous step computes; every step also
+        """Keep the pool's target images in pinned host memory (float32, or
+        uint8 as training images come: then 1/4 of the bytes cross the link
+        and a kernel widens them on the device).  Each step's target is
+        copied in on a side stream one step ahead, into one of two device
+        buffers, while the previous step computes; every step also
         copies its per-view losses back into one of two pinned host buffers
         (read them with loss_of(t) or last_loss(), which wait only for that
         step, so the host can read step t's losses while step t + 1 runs)."""
         self.host_targets = [t if t.is_pinned() else t.pin_memory() for t in host_targets]
-        self.stage = [torch.empty(self.host_targets[0].shape, dtype=self.host_targets[0].dtype, device=self.device)
+        # 8-bit targets cross the link as bytes and widen to float on the copy stream
+        self.stage_u8 = None
+        if self.host_targets[0].dtype == torch.uint8:
+            self.stage_u8 = [torch.empty(self.host_targets[0].shape, dtype=torch.uint8, device=self.device)
+                             for _ in range(2)]
+        self.stage = [torch.empty(self.host_targets[0].shape, dtype=torch.float32, device=self.device)
                       for _ in range(2)]
         self.host_loss = [torch.zeros(self.vb.loss.numel(), dtype=torch.float64).pin_memory() for _ in range(2)]
         self.loss_ready = [torch.cuda.Event() for _ in range(2)]
@@ -232,7 +239,11 @@ class DogsTrainer:
     def _prefetch(self, p: int, slot: int) -> None:
         self.copy_stream.wait_event(self.used[slot])           # the step that last read this buffer
         with torch.cuda.stream(self.copy_stream):
-            self.stage[slot].copy_(self.host_targets[p], non_blocking=True)
+            if self.stage_u8 is not None:
+                self.stage_u8[slot].copy_(self.host_targets[p], non_blocking=True)
+                D.dg_image_u8_to_f32(self.stage_u8[slot], self.stage[slot])
+            else:
+                self.stage[slot].copy_(self.host_targets[p], non_blocking=True)
         self.copied[slot].record(self.copy_stream)
         self.slot_entry[slot] = p
 

@@ -408,3 +408,38 @@ def test_xstep_stores_unshared_copies_into_z(mods):
         ga, gb = groups(getattr(a, n)), groups(getattr(b, n))
         for k in ga:
             assert rel_l2(ga[k], gb[k]) < REL_L2, (n, k)
+
+
+def test_u8_host_targets_equal_device_targets(mods):
+    """8-bit targets in pinned host memory (a quarter of the bytes over the
+    link, widened to v / 255 on the device) give the losses and state of the
+    same targets resident as float32."""
+    D, srv, T = mods
+    wl, z0, targets = small_setup(D, srv, seed=37)
+    t8 = []
+    for t in targets:
+        b = torch.empty(t.numel(), dtype=torch.uint8, device="cuda")
+        D.dg_image_f32_to_u8(t, b)
+        t8.append(b)
+    tf = []
+    for b in t8:
+        f = torch.empty(b.numel(), dtype=torch.float32, device="cuda")
+        D.dg_image_u8_to_f32(b, f)
+        tf.append(f)
+    torch.cuda.synchronize()
+    # the conversions: round(clamp(v) 255) and exactly v / 255
+    ref8 = np.clip(np.rint(np.clip(targets[0].cpu().numpy(), 0, 1) * np.float32(255)), 0, 255).astype(np.uint8)
+    np.testing.assert_array_equal(t8[0].cpu().numpy(), ref8)
+    np.testing.assert_array_equal(tf[0].cpu().numpy(), ref8.astype(np.float32) / np.float32(255))
+    kw = dict(rho=(1e-2,) * 5, loss="dssim", intv=2)
+    a = T.DogsTrainer(wl.split, z0.clone(), wl.views, tf, **kw)
+    a.calibrate_capacity()
+    b = T.DogsTrainer(wl.split, z0.clone(), wl.views, tf, **kw)
+    b.calibrate_capacity()
+    b.use_host_targets([x.cpu() for x in t8])
+    assert b.h2d_bytes_per_step() == t8[0].numel()
+    for _ in range(4):
+        a.step()
+        b.step()
+        # equal up to the order of the floating-point atomics of the loss sums and the adjoint
+        np.testing.assert_allclose(b.last_loss().numpy(), a.vb.loss.cpu().numpy(), rtol=1e-6)
