@@ -410,14 +410,12 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             // colour sums and the moments of dL/dpower along the strip:
             // S0 = sum dLdp, S1 = sum k dLdp, S2 = sum k^2 dLdp (dy_k = dy0 - k dy)
             float c0 = 0.f, c1 = 0.f, c2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
-            bool any = false;
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
                 if (!(todo >> k & 1u)) continue;
                 const float raw = strip_raw(qk[k], h.y);
                 if (!(raw >= kAlphaMin)) continue;
                 const float a = fminf(raw, kAlphaMax);
-                any = true;
                 const float4 Gk = s_Gl[tid + NT * k];
                 const float Tj = T[k] * __fdividef(1.f, 1.f - a);
                 const float wT = a * Tj;
@@ -435,7 +433,7 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             }
             float gr[8] = {0, 0, 0, 0, 0, 0, c0, c1};
             float g8 = c2;
-            if (any) {
+            if (todo) {                         // lanes with no composited pixel give zeros
                 // power = -(a dx^2 + 2 b dx dy + c dy^2) / 2 with dx = mx - px,
                 // dy = my - py; its gradients summed over the strip's pixels
                 const float4 kc = s_k[j];
@@ -449,7 +447,6 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
                 gr[4] = -0.5f * Syy;
                 gr[5] = S0 * h.z;                       // d alpha / d opacity = alpha / opacity
             }
-            if (!__any_sync(0xffffffffu, any)) continue;
             const float sred = warp_reduce_scatter8(gr, g8, lane);
             float* d = drec + 12 * (int64_t)__float_as_uint(h.w);
             if ((lane & 3) == 0) {
