@@ -140,6 +140,37 @@ __device__ __forceinline__ bool in_frustum(const CamL& cam, double tzd, float3 m
     return !(fabsf(xn) > limx || fabsf(yn) > limy);
 }
 
+// A float pre-test that is true only where the test above (with the double
+// depth) culls as well, so that most culled copies skip the FP64 arithmetic,
+// which is slow on this part.  The float depth tzf (three rounded FMAs) and
+// the double sum tzd both lie within 3u S (u = 2^-24 for tzf, 2^-53 for tzd)
+// of the exact depth, S = |R6 x| + |R7 y| + |R8 z| + |t2|; so
+// |tzf - tzd| < 4u S.  With the margin m = 16u S (each comparison's own
+// rounding adds at most u S):
+//   tzf + m < near          =>  tzd < near, culled by the near test;
+//   tzf - m > max(near, 0)  =>  tzd > near and tzd > 0, and the depth the
+//     lateral test divides by, tz = rn(tzd) <= (tzf + m) (1 + u); then
+//     |tx| > lim (tzf + m) (1 + 2^-18), rounded three times, still gives
+//     |tx| / tz > lim (1 + 58u), whose rounding is above lim, so the lateral
+//     test culls.  tx, ty are the same expressions as in in_frustum.
+// S >= 2^-100 keeps every rounding error relative (a subnormal partial sum
+// errs by 2^-150 at most, far below u S); smaller S, NaN or infinite inputs
+// fail a comparison here and take the exact path.
+__device__ __forceinline__ bool surely_culled(const CamL& cam, float3 mu)
+{
+    const float S = fabsf(cam.R[6] * mu.x) + fabsf(cam.R[7] * mu.y) + fabsf(cam.R[8] * mu.z) + fabsf(cam.t[2]);
+    if (!(S >= 0x1p-100f)) return false;
+    const float m = S * 0x1p-20f;
+    const float tzf = fmaf(cam.R[6], mu.x, fmaf(cam.R[7], mu.y, fmaf(cam.R[8], mu.z, cam.t[2])));
+    if (tzf + m < cam.nearz) return true;
+    if (!(tzf - m > fmaxf(cam.nearz, 0.f))) return false;
+    const float tx = fmaf(cam.R[0], mu.x, fmaf(cam.R[1], mu.y, fmaf(cam.R[2], mu.z, cam.t[0])));
+    const float ty = fmaf(cam.R[3], mu.x, fmaf(cam.R[4], mu.y, fmaf(cam.R[5], mu.z, cam.t[1])));
+    const float limx = 0.65f * (float)cam.W / cam.fx, limy = 0.65f * (float)cam.H / cam.fy;
+    const float zb = (tzf + m) * (1.f + 0x1p-18f);
+    return fabsf(tx) > limx * zb || fabsf(ty) > limy * zb;
+}
+
 // Computes every field; returns false if the Gaussian is culled in this
 // view.  The caller has already checked camera z > near_z (exact, in double),
 // so no division below is by a non-positive depth.  Fills rect if non-null.
@@ -228,6 +259,7 @@ __global__ void __launch_bounds__(256, 4) k_project(GView x, const dg_camera* __
         CamL cam;
         load_cam(cams, v, cam);
         int64_t r = cam.rec_off + (c - cam.gb);
+        if (surely_culled(cam, mu)) { rect[r] = make_uint2(0, 0); continue; }
         double tzd = cam_depth(cam, mu);
         if (!(tzd > (double)cam.nearz) || !in_frustum(cam, tzd, mu)) { rect[r] = make_uint2(0, 0); continue; }
         if (!loaded) {   // the rest of the parameters only for copies inside some camera's frustum

@@ -1,0 +1,155 @@
+"""The projection's culling decision at its thresholds.
+
+The kernel decides most culled copies with a float pre-test and leaves the
+rest to the exact test (camera depth summed in double, then the lateral
+frustum test on it).  The pre-test must never cull a copy the exact test
+keeps, nor keep one it would cull in a way that changes the output.  These
+copies sit within a few rounding errors of the near plane and of the
+lateral frustum edges, in world coordinates of magnitude 1e3 (so the float
+depth errs by ~1e-4), and are large enough that every copy passing the
+exact test has a non-empty tile rectangle.  The expected decision is the
+exact test evaluated on the CPU with correctly rounded float operations
+(fma and division emulated exactly), so culled <=> empty rectangle, bit
+for bit."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2405_13943_b300 import synth as S
+
+F32 = np.float32
+
+
+def rn32(q: Fraction) -> F32:
+    """q rounded to the nearest float32, ties to even (normal and subnormal
+    range; no overflow handling: the test's values are far from it)."""
+    if q == 0:
+        return F32(0.0)
+    sign = -1 if q < 0 else 1
+    a = abs(q)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    e = max(e, -126)
+    quantum = Fraction(2) ** (e - 23)
+    n = a / quantum
+    fl = n.numerator // n.denominator
+    rem = n - fl
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and fl % 2 == 1):
+        fl += 1
+    return F32(sign * float(fl * quantum))
+
+
+def fma32(a, b, c) -> F32:
+    return rn32(Fraction(float(a)) * Fraction(float(b)) + Fraction(float(c)))
+
+
+def test_rn32_and_fma32_round_correctly():
+    rng = np.random.default_rng(3)
+    for x in rng.standard_normal(2000) * 10.0 ** rng.integers(-40, 30, 2000):
+        assert rn32(Fraction(float(x))) == F32(x)        # one rounding from double: numpy's is correct
+    assert rn32(Fraction(1) + Fraction(1, 2 ** 24)) == F32(1.0)                        # tie to even, down
+    assert rn32(Fraction(1) + Fraction(3, 2 ** 24)) == F32(1.0) + F32(2.0 ** -22)       # tie to even, up
+    assert rn32(Fraction(1, 2 ** 149)) == F32(2.0 ** -149)
+    # an fma whose single rounding differs from rounding the product first
+    a = F32(1.0) + F32(2.0 ** -12)
+    assert fma32(a, a, F32(-1.0)) == F32(2.0 ** -11 + 2.0 ** -24)
+    assert F32(a * a) - F32(1.0) != fma32(a, a, F32(-1.0))
+
+
+def exact_culled(cam: S.Camera, mu: np.ndarray) -> np.ndarray:
+    """The projection's exact culling test: depth = ((R6 x + R7 y) + R8 z) + t2
+    in double (exact products), culled if depth <= near; else tz = float(depth),
+    tx, ty by the float fma chains, culled if |tx / tz| or |ty / tz| exceeds
+    0.65 W / fx or 0.65 H / fy."""
+    R = cam.R.astype(F32)
+    t = cam.t.astype(F32)
+    limx = F32(F32(0.65) * F32(cam.width)) / F32(cam.fx)
+    limy = F32(F32(0.65) * F32(cam.height)) / F32(cam.fy)
+    near = np.float64(F32(cam.near))
+    out = np.empty(len(mu), bool)
+    for i, (x, y, z) in enumerate(mu.astype(F32)):
+        d = np.float64(R[2, 0]) * np.float64(x)
+        d = d + np.float64(R[2, 1]) * np.float64(y)
+        d = d + np.float64(R[2, 2]) * np.float64(z)
+        d = d + np.float64(t[2])
+        if not d > near:
+            out[i] = True
+            continue
+        tz = F32(d)
+        tx = fma32(R[0, 0], x, fma32(R[0, 1], y, fma32(R[0, 2], z, t[0])))
+        ty = fma32(R[1, 0], x, fma32(R[1, 1], y, fma32(R[1, 2], z, t[1])))
+        out[i] = bool(abs(tx / tz) > limx or abs(ty / tz) > limy)
+    return out
+
+
+def boundary_scene(cam: S.Camera, seed: int, n: int = 4000):
+    """Copies near the near plane and the four lateral edges, given in camera
+    coordinates and mapped to float32 world coordinates (whose rounding
+    scatters them across the thresholds)."""
+    rng = np.random.default_rng(seed)
+    limx = 0.65 * cam.width / cam.fx
+    limy = 0.65 * cam.height / cam.fy
+    pc = []
+    # offsets from a threshold: half within +- 8e-4 (the float depth errs by
+    # up to ~5e-4 here), half within +- 0.01 (beyond the pre-test's margin)
+    def off():
+        return rng.uniform(-1, 1, n) * np.where(rng.random(n) < 0.5, 8e-4, 1e-2)
+    # near plane: on axis
+    tz = cam.near + off()
+    pc.append(np.stack([rng.uniform(-0.05, 0.05, n) * tz, rng.uniform(-0.05, 0.05, n) * tz, tz], 1))
+    # lateral edges at depths 1..40
+    for axis, lim in ((0, limx), (1, limy)):
+        tz = rng.uniform(1.0, 40.0, n)
+        side = rng.choice([-1.0, 1.0], n)
+        p = np.zeros((n, 3))
+        p[:, 2] = tz
+        p[:, axis] = side * lim * tz + off()
+        p[:, 1 - axis] = rng.uniform(-0.1, 0.1, n) * tz
+        pc.append(p)
+    pc = np.concatenate(pc)
+    R = cam.R.astype(np.float64)
+    world = (R.T @ (pc - cam.t.astype(np.float64)).T).T.astype(F32)
+    m = len(world)
+    # isotropic, a quarter of the depth: screen radius 3 fx s / tz >= 0.75 W
+    log_s = np.log(np.maximum(pc[:, 2], cam.near) / 4.0).astype(F32)
+    quats = np.tile(np.array([1.0, 0.0, 0.0, 0.0], F32), (m, 1))
+    g = S.Gaussians(world, quats, np.repeat(log_s[:, None], 3, 1), np.full(m, 2.0, F32),
+                    np.full((m, 1, 3), 0.5, F32))
+    return g
+
+
+def rotated_far_camera():
+    from scipy.spatial.transform import Rotation
+    R = Rotation.from_rotvec([0.7, -0.4, 0.25]).as_matrix().astype(np.float32)
+    campos = np.array([1000.5, -2000.25, 500.125], np.float32)
+    t = (-(R.astype(np.float64) @ campos.astype(np.float64))).astype(np.float32)
+    return S.Camera(64, 48, 64.0, 64.0, 32.0, 24.0, R, t, campos, 0.2)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("seed", [0, 1])
+def test_projection_culling_at_its_thresholds(seed):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_13943_b300 import build as B
+    B.build()
+    from paper_2405_13943_b300 import dogs as D
+    cam = rotated_far_camera()
+    g = boundary_scene(cam, seed)
+    expect = exact_culled(cam, g.means)
+    xb = D.GaussianBuffer.from_synth(g)
+    vb = D.ViewBatch([cam], [0, g.n], 16, 16)
+    D.dg_project(xb, vb)
+    torch.cuda.synchronize()
+    r = vb.rect.cpu().numpy()[:2 * g.n].reshape(-1, 2).astype(np.uint32)
+    x0, y0, x1, y1 = r[:, 0] & 0xFFFF, r[:, 0] >> 16, r[:, 1] & 0xFFFF, r[:, 1] >> 16
+    empty = ~((x1 > x0) & (y1 > y0))
+    n = g.n // 3
+    for fam, name in enumerate(("near", "x edge", "y edge")):
+        sl = slice(fam * n, (fam + 1) * n)
+        assert 0.2 * n < expect[sl].sum() < 0.8 * n, name        # both sides well populated
+        bad = np.flatnonzero(empty[sl] != expect[sl])
+        assert bad.size == 0, (name, bad[:10])
