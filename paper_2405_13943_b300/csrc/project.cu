@@ -239,16 +239,15 @@ __device__ __forceinline__ bool geom(const CamL& cam, double tzd, float3 mu, flo
     return true;
 }
 
+// Projects copy c into every view of its block: a record and a tile
+// rectangle per view (an empty rectangle where it is culled).
 template <int DEG>
-__global__ void __launch_bounds__(256, 4) k_project(GView x, const dg_camera* __restrict__ cams, dg_plan plan,
-                                                    float4* __restrict__ rec, uint2* __restrict__ rect)
+__device__ __forceinline__ void project_copy(const GView& x, const dg_camera* __restrict__ cams, const dg_plan& plan,
+                                             int64_t c, float4* __restrict__ rec, uint2* __restrict__ rect)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= plan.blk_off[plan.n_blocks]) return;
     int k = find_block(plan, c);
     int v0 = plan.blk_view_off[k], v1 = plan.blk_view_off[k + 1];
-    if (v0 == v1) return;
     const float4 mo = x.mo[c];
     const float3 mu = make_float3(mo.x, mo.y, mo.z);
     bool loaded = false;
@@ -286,6 +285,81 @@ __global__ void __launch_bounds__(256, 4) k_project(GView x, const dg_camera* __
         rec[3 * r + 2] = make_float4(fmaxf(col[2], 0.f), g.tz, 0.f, 0.f);
         rect[r] = rr;
     }
+}
+
+// Copies per thread in the culling pass of k_project.
+#ifndef DG_PROJECT_PER
+#define DG_PROJECT_PER 4
+#endif
+constexpr int kProjThreads = 256;
+constexpr int kProjPer = DG_PROJECT_PER;
+static_assert(kProjPer >= 1 && kProjPer * (kProjThreads / 32) <= 32, "one warp scans the per-warp counts");
+
+// One CTA per kProjThreads * kProjPer consecutive copies, in two passes.
+// Culling pass: each thread loads the means of its kProjPer copies at once
+// (more loads in flight than one copy per thread) and runs the float
+// pre-test in every view of the copy's block; a copy culled in all of them
+// gets its empty rectangles here.  The others are listed in shared memory
+// in ascending copy order (warp ballots, then one warp's scan of the
+// per-warp counts), and the CTA projects the list densely with
+// project_copy, whose exact test decides them.
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads, 4) k_project(GView x, const dg_camera* __restrict__ cams, dg_plan plan,
+                                                             float4* __restrict__ rec, uint2* __restrict__ rect)
+{
+    constexpr int NW = kProjThreads / 32;
+    __shared__ int s_list[kProjThreads * kProjPer];
+    __shared__ int s_off[NW * kProjPer + 1];
+    const int64_t n = plan.blk_off[plan.n_blocks];
+    const int64_t base = (int64_t)blockIdx.x * (kProjThreads * kProjPer);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 mo[kProjPer];
+#pragma unroll
+    for (int j = 0; j < kProjPer; j++) {
+        const int64_t c = base + threadIdx.x + kProjThreads * j;
+        mo[j] = c < n ? x.mo[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    unsigned bal[kProjPer];
+#pragma unroll
+    for (int j = 0; j < kProjPer; j++) {
+        const int64_t c = base + threadIdx.x + kProjThreads * j;
+        bool need = false;
+        if (c < n) {
+            const int k = find_block(plan, c);
+            const int v0 = plan.blk_view_off[k], v1 = plan.blk_view_off[k + 1];
+            const float3 mu = make_float3(mo[j].x, mo[j].y, mo[j].z);
+            for (int v = v0; v < v1 && !need; v++) {
+                CamL cam;
+                load_cam(cams, v, cam);
+                need = !surely_culled(cam, mu);
+            }
+            if (!need)
+                for (int v = v0; v < v1; v++)
+                    rect[__ldg(&cams[v].rec_off) + (c - __ldg(&cams[v].gauss_begin))] = make_uint2(0, 0);
+        }
+        bal[j] = __ballot_sync(0xffffffffu, need);
+        if (lane == 0) s_off[j * NW + warp] = __popc(bal[j]);
+    }
+    __syncthreads();
+    if (warp == 0) {   // exclusive scan of the counts in (pass, warp) order: the list ascends in c
+        const int v = lane < NW * kProjPer ? s_off[lane] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane < NW * kProjPer) s_off[lane] = incl - v;
+        if (lane == 31) s_off[NW * kProjPer] = incl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kProjPer; j++)
+        if ((bal[j] >> lane) & 1u)
+            s_list[s_off[j * NW + warp] + __popc(bal[j] & ((1u << lane) - 1u))] = threadIdx.x + kProjThreads * j;
+    __syncthreads();
+    const int cnt = s_off[NW * kProjPer];
+    for (int i = threadIdx.x; i < cnt; i += kProjThreads) project_copy<DEG>(x, cams, plan, base + s_list[i], rec, rect);
 }
 
 // ---------------------------------------------------------------------------
@@ -779,12 +853,13 @@ int launch_project(const dg_gaussians* x, const dg_camera* cams, const dg_plan& 
     int64_t n = plan.blk_off[plan.n_blocks];
     if (n == 0) return DG_OK;
     GView xv = gview(x);
-    dim3 grid((unsigned)((n + 255) / 256));
+    const int64_t per_cta = (int64_t)kProjThreads * kProjPer;
+    dim3 grid((unsigned)((n + per_cta - 1) / per_cta));
     switch (x->sh_degree) {
-    case 0: k_project<0><<<grid, 256, 0, st>>>(xv, cams, plan, rec, rect); break;
-    case 1: k_project<1><<<grid, 256, 0, st>>>(xv, cams, plan, rec, rect); break;
-    case 2: k_project<2><<<grid, 256, 0, st>>>(xv, cams, plan, rec, rect); break;
-    default: k_project<3><<<grid, 256, 0, st>>>(xv, cams, plan, rec, rect); break;
+    case 0: k_project<0><<<grid, kProjThreads, 0, st>>>(xv, cams, plan, rec, rect); break;
+    case 1: k_project<1><<<grid, kProjThreads, 0, st>>>(xv, cams, plan, rec, rect); break;
+    case 2: k_project<2><<<grid, kProjThreads, 0, st>>>(xv, cams, plan, rec, rect); break;
+    default: k_project<3><<<grid, kProjThreads, 0, st>>>(xv, cams, plan, rec, rect); break;
     }
     note_launch();
     DG_CHECK_LAUNCH();
