@@ -239,20 +239,21 @@ __device__ __forceinline__ bool geom(const CamL& cam, double tzd, float3 mu, flo
     return true;
 }
 
-// Projects copy c into every view of its block: a record and a tile
-// rectangle per view (an empty rectangle where it is culled).
+// Projects copy c (mean and opacity logit mo) into every view of its block:
+// a record and a tile rectangle per view (an empty rectangle where it is
+// culled).  Called for the copies the float pre-test could not cull, which
+// are nearly all kept, so the rotation and scales load up front, in flight
+// during the exact depth test.
 template <int DEG>
 __device__ __forceinline__ void project_copy(const GView& x, const dg_camera* __restrict__ cams, const dg_plan& plan,
-                                             int64_t c, float4* __restrict__ rec, uint2* __restrict__ rect)
+                                             int64_t c, float4 mo, float4* __restrict__ rec, uint2* __restrict__ rect)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
     int k = find_block(plan, c);
     int v0 = plan.blk_view_off[k], v1 = plan.blk_view_off[k + 1];
-    const float4 mo = x.mo[c];
     const float3 mu = make_float3(mo.x, mo.y, mo.z);
-    bool loaded = false;
-    float4 q = make_float4(0, 0, 0, 0), sc = make_float4(0, 0, 0, 0);
-    float opac = 0.f;
+    const float4 q = x.quat[c], sc = x.scale[c];
+    const float opac = 1.f / (1.f + __expf(-mo.w));
     const float* __restrict__ shp = x.sh + c;
     for (int v = v0; v < v1; v++) {
         CamL cam;
@@ -261,12 +262,6 @@ __device__ __forceinline__ void project_copy(const GView& x, const dg_camera* __
         if (surely_culled(cam, mu)) { rect[r] = make_uint2(0, 0); continue; }
         double tzd = cam_depth(cam, mu);
         if (!(tzd > (double)cam.nearz) || !in_frustum(cam, tzd, mu)) { rect[r] = make_uint2(0, 0); continue; }
-        if (!loaded) {   // the rest of the parameters only for copies inside some camera's frustum
-            q = x.quat[c];
-            sc = x.scale[c];
-            opac = 1.f / (1.f + __expf(-mo.w));
-            loaded = true;
-        }
         Geom g;
         uint2 rr;
         if (!geom(cam, tzd, mu, q, sc, plan.tile_w, plan.tile_h, g, &rr)) { rect[r] = make_uint2(0, 0); continue; }
@@ -287,27 +282,26 @@ __device__ __forceinline__ void project_copy(const GView& x, const dg_camera* __
     }
 }
 
-// Copies per thread in the culling pass of k_project.
-#ifndef DG_PROJECT_PER
-#define DG_PROJECT_PER 4
-#endif
 constexpr int kProjThreads = 256;
-constexpr int kProjPer = DG_PROJECT_PER;
-static_assert(kProjPer >= 1 && kProjPer * (kProjThreads / 32) <= 32, "one warp scans the per-warp counts");
+constexpr int kProjCtasPerSm = 4;     // the register budget of __launch_bounds__ below
 
-// One CTA per kProjThreads * kProjPer consecutive copies, in two passes.
-// Culling pass: each thread loads the means of its kProjPer copies at once
+// One CTA per kProjThreads * PER consecutive copies, in two passes.
+// Culling pass: each thread loads the means of its PER copies at once
 // (more loads in flight than one copy per thread) and runs the float
 // pre-test in every view of the copy's block; a copy culled in all of them
 // gets its empty rectangles here.  The others are listed in shared memory
 // in ascending copy order (warp ballots, then one warp's scan of the
-// per-warp counts), and the CTA projects the list densely with
-// project_copy, whose exact test decides them.
-template <int DEG>
-__global__ void __launch_bounds__(kProjThreads, 4) k_project(GView x, const dg_camera* __restrict__ cams, dg_plan plan,
-                                                             float4* __restrict__ rec, uint2* __restrict__ rect)
+// per-warp counts) with their means, and the CTA projects the list densely
+// with project_copy, whose exact test decides them.
+template <int DEG, int PER>
+__global__ void __launch_bounds__(kProjThreads, kProjCtasPerSm) k_project(GView x, const dg_camera* __restrict__ cams,
+                                                                          dg_plan plan, float4* __restrict__ rec,
+                                                                          uint2* __restrict__ rect)
 {
     constexpr int NW = kProjThreads / 32;
+    constexpr int kProjPer = PER;
+    static_assert(PER >= 1 && PER * NW <= 32, "one warp scans the per-warp counts");
+    __shared__ float4 s_mo[kProjThreads * kProjPer];
     __shared__ int s_list[kProjThreads * kProjPer];
     __shared__ int s_off[NW * kProjPer + 1];
     const int64_t n = plan.blk_off[plan.n_blocks];
@@ -355,11 +349,15 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(GView x, const dg_c
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kProjPer; j++)
-        if ((bal[j] >> lane) & 1u)
-            s_list[s_off[j * NW + warp] + __popc(bal[j] & ((1u << lane) - 1u))] = threadIdx.x + kProjThreads * j;
+        if ((bal[j] >> lane) & 1u) {
+            const int at = s_off[j * NW + warp] + __popc(bal[j] & ((1u << lane) - 1u));
+            s_list[at] = threadIdx.x + kProjThreads * j;
+            s_mo[at] = mo[j];
+        }
     __syncthreads();
     const int cnt = s_off[NW * kProjPer];
-    for (int i = threadIdx.x; i < cnt; i += kProjThreads) project_copy<DEG>(x, cams, plan, base + s_list[i], rec, rect);
+    for (int i = threadIdx.x; i < cnt; i += kProjThreads)
+        project_copy<DEG>(x, cams, plan, base + s_list[i], s_mo[i], rec, rect);
 }
 
 // ---------------------------------------------------------------------------
@@ -853,14 +851,30 @@ int launch_project(const dg_gaussians* x, const dg_camera* cams, const dg_plan& 
     int64_t n = plan.blk_off[plan.n_blocks];
     if (n == 0) return DG_OK;
     GView xv = gview(x);
-    const int64_t per_cta = (int64_t)kProjThreads * kProjPer;
+    // Four copies per thread while the grid still spans 8 waves of resident
+    // CTAs; below that the CTAs whose copies are mostly kept, which project
+    // four copies per thread one after another, would form the tail, so one.
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return DG_ERR_CUDA;
+    const int64_t slots = (int64_t)sms * kProjCtasPerSm;
+    const bool four = (n + 4 * kProjThreads - 1) / (4 * kProjThreads) >= 8 * slots;
+    const int64_t per_cta = (int64_t)kProjThreads * (four ? 4 : 1);
     dim3 grid((unsigned)((n + per_cta - 1) / per_cta));
+#define DG_PROJECT_CASE(D)                                                                    \
+    case D:                                                                                   \
+        if (four) k_project<D, 4><<<grid, kProjThreads, 0, st>>>(xv, cams, plan, rec, rect);  \
+        else k_project<D, 1><<<grid, kProjThreads, 0, st>>>(xv, cams, plan, rec, rect);       \
+        break;
     switch (x->sh_degree) {
-    case 0: k_project<0><<<grid, kProjThreads, 0, st>>>(xv, cams, plan, rec, rect); break;
-    case 1: k_project<1><<<grid, kProjThreads, 0, st>>>(xv, cams, plan, rec, rect); break;
-    case 2: k_project<2><<<grid, kProjThreads, 0, st>>>(xv, cams, plan, rec, rect); break;
-    default: k_project<3><<<grid, kProjThreads, 0, st>>>(xv, cams, plan, rec, rect); break;
+    DG_PROJECT_CASE(0)
+    DG_PROJECT_CASE(1)
+    DG_PROJECT_CASE(2)
+    default:
+    DG_PROJECT_CASE(3)
     }
+#undef DG_PROJECT_CASE
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;
