@@ -490,9 +490,7 @@ def run_ours(args, dist, rank, world):
             "metric": METRIC, "value": round(value, 4), "unit": "iter/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (city-law aerial scene, seeded; targets 8-bit images)",
-            "config": {"workload": f"DOGS K=8 batched, {WORKLOADS[args.workload]['n_global']} Gaussians SH3, "
-                                   f"{wl.split.n_copies} copies, 10% shared, V={len(wl.views[0])} x "
-                                   f"{WORKLOADS[args.workload]['width']}x{WORKLOADS[args.workload]['height']}",
+            "config": {"workload": workload_name(args, wl),
                        "blocks": wl.split.K, "copies": wl.split.n_copies, "views_per_step": len(wl.views[0]),
                        "tile": f"{tr.tile[0]}x{tr.tile[1]}",
                        "raster_variant": {"fwd": {"warps_per_tile": tr.vb.plan.raster_warps,
@@ -637,9 +635,15 @@ def cpu_baseline(wl, args, frac=64):
     rest = (t1 - t0) + (t3 - t2)
     full = (t2 - t1) + frac * rest
     return {"value": round(1.0 / full, 6), "unit": "iter/s", "cores": 1, "kind": "oracle",
-            "sample": f"1/{frac} of each block's copies ({x.shape[0]}), 8 full-size views and loss; "
+            "sample": f"1/{frac} of each block's copies ({x.shape[0]}), {len(plan.cams)} full-size views and loss; "
                       f"measured {t3 - t0:.1f} s, extrapolated {full:.1f} s per iteration",
             "sample_seconds": round(t3 - t0, 2)}
+
+
+def workload_name(args, wl) -> str:
+    w = WORKLOADS[args.workload]
+    return (f"DOGS K={wl.split.K} batched, {w['n_global']} Gaussians SH3, {wl.split.n_copies} copies, 10% shared, "
+            f"V={len(wl.views[0])} x {w['width']}x{w['height']}")
 
 
 def run_reference(args, dist, rank, world):
@@ -659,7 +663,8 @@ def run_reference(args, dist, rank, world):
             "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": round(1e3 / v, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (city-law aerial scene, seeded)",
-            "config": {"workload": "same as the GPU arm (bounded sample, extrapolated)"},
+            "config": {"workload": workload_name(args, wl), "blocks": wl.split.K, "copies": wl.split.n_copies,
+                       "views_per_step": len(wl.views[0]), "timing": "bounded sample per step, extrapolated"},
             "cpu_baseline": {"value": round(v, 6), "unit": "iter/s", "cores": 1, "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": round(v, 6), "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
