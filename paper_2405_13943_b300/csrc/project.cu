@@ -4,10 +4,12 @@
 // conics with the EWA local-affine approximation J W Sigma W^T J^T + 0.3 I,
 // real SH colour of degree <= 3, sigmoid opacity; and its analytic adjoint.
 //
-// One thread per local copy.  A copy is loaded once (coalesced float4 SoA for
-// mean/opacity, rotation, scale; planar SH) and projected into every view of
-// its block, so the parameters are read once per step however many views a
-// block has.  HBM-bound.
+// Forward: a CTA takes a run of consecutive local copies, culls them with a
+// float pre-test on their means, and projects the rest densely (k_project).
+// A copy is loaded once (coalesced float4 SoA for mean/opacity, rotation,
+// scale; planar SH) and projected into every view of its block, so the
+// parameters are read once per step however many views a block has.
+// HBM- and latency-bound.  The adjoint takes one thread per copy.
 #include "common.cuh"
 
 namespace dg {
