@@ -229,7 +229,7 @@ __device__ __noinline__ void cons_generic(GView x, GView u, GView z, GView an, i
 }
 
 #ifndef DG_CONS_CTAS
-#define DG_CONS_CTAS 6   // 80 registers: 24 warps per SM (measured best of 1, 6, 8)
+#define DG_CONS_CTAS 8   // 64 registers: 32 warps per SM (with CH = 2 below; measured best, see CH)
 #endif
 template <int NP>
 __global__ void __launch_bounds__(128, DG_CONS_CTAS) k_consensus(GView x, GView u, GView z, GView an,
@@ -266,7 +266,10 @@ __global__ void __launch_bounds__(128, DG_CONS_CTAS) k_consensus(GView x, GView 
             cons_field4(x.quat, u.quat, an.quat, z.quat, i, cp, n, g_q, a.alpha, a.rho, r);
             cons_field4(x.scale, u.scale, an.scale, z.scale, i, cp, n, g_s, a.alpha, a.rho, r);
             const float inv = 1.f / (float)n;
-            constexpr int CH = 4;   // planes per batch of loads
+            // planes per batch of loads; same-box A/B on the 6M step (CTAs per SM, CH):
+            // (6, 4) 0.359 ms, (6, 2) 0.351, (7, 3) 0.336, (8, 2) 0.329.  Larger batches
+            // at a given register budget spill more than their extra loads in flight gain.
+            constexpr int CH = 2;
 #pragma unroll
             for (int j0 = 0; j0 < NP; j0 += CH) {
                 float xs[CH][kFast], us[CH][kFast], zo[CH];
