@@ -111,9 +111,19 @@ class ClockSampler:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "50", "-i", str(dev)], stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+
+    def wait_first(self, timeout: float = 3.0) -> None:
+        """Return once nvidia-smi has written its first sample (it takes a few
+        hundred ms to start), so that the samples cover the timed region; at
+        most `timeout` seconds, and at once if the sampler is not running."""
+        t0 = time.time()
+        while self.p is not None and self.p.poll() is None and time.time() - t0 < timeout:
+            if os.path.getsize(self.f.name) > 0:
+                return
+            time.sleep(0.02)
 
     def stop(self) -> dict:
         if self.p is None:
@@ -319,6 +329,7 @@ def run_ours(args, dist, rank, world):
 
     # ---- timed region: graph replays ------------------------------------------------
     clocks = ClockSampler(local)
+    clocks.wait_first()
     barrier(dist)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
