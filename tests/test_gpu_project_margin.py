@@ -10,7 +10,8 @@ depth errs by ~1e-4), and are large enough that every copy passing the
 exact test has a non-empty tile rectangle.  The expected decision is the
 exact test evaluated on the CPU with correctly rounded float operations
 (fma and division emulated exactly), so culled <=> empty rectangle, bit
-for bit."""
+for bit.  On the CPU, the pre-test itself, evaluated operation for operation
+in float32, is checked against the same exact test on the same copies."""
 from fractions import Fraction
 
 import numpy as np
@@ -119,6 +120,53 @@ def boundary_scene(cam: S.Camera, seed: int, n: int = 4000):
     g = S.Gaussians(world, quats, np.repeat(log_s[:, None], 3, 1), np.full(m, 2.0, F32),
                     np.full((m, 1, 3), 0.5, F32))
     return g
+
+
+def pretest_culled(cam: S.Camera, mu: np.ndarray, margin: float = 2.0 ** -20,
+                   widen: float = 1.0 + 2.0 ** -18) -> np.ndarray:
+    """The projection's float pre-test, operation for operation in float32
+    (fma rounded once): S = |R6 x| + |R7 y| + |R8 z| + |t2|, m = margin S,
+    tzf the fma chain; culled if tzf + m < near, or, when tzf - m > max(near, 0),
+    if |tx| or |ty| exceeds lim (tzf + m) widen."""
+    R = cam.R.astype(F32)
+    t = cam.t.astype(F32)
+    limx = F32(F32(0.65) * F32(cam.width)) / F32(cam.fx)
+    limy = F32(F32(0.65) * F32(cam.height)) / F32(cam.fy)
+    near = F32(cam.near)
+    out = np.zeros(len(mu), bool)
+    for i, (x, y, z) in enumerate(mu.astype(F32)):
+        Sm = ((abs(R[2, 0] * x) + abs(R[2, 1] * y)) + abs(R[2, 2] * z)) + abs(t[2])
+        if not Sm >= F32(2.0 ** -100):
+            continue
+        m = Sm * F32(margin)
+        tzf = fma32(R[2, 0], x, fma32(R[2, 1], y, fma32(R[2, 2], z, t[2])))
+        if tzf + m < near:
+            out[i] = True
+            continue
+        if not tzf - m > max(near, F32(0.0)):
+            continue
+        tx = fma32(R[0, 0], x, fma32(R[0, 1], y, fma32(R[0, 2], z, t[0])))
+        ty = fma32(R[1, 0], x, fma32(R[1, 1], y, fma32(R[1, 2], z, t[1])))
+        zb = (tzf + m) * F32(widen)
+        out[i] = bool(abs(tx) > limx * zb or abs(ty) > limy * zb)
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_pretest_culls_only_where_the_exact_test_culls(seed):
+    """The margin argument of the pre-test, on the CPU: on copies at the
+    thresholds it never culls a copy the exact test keeps, and it still
+    decides most copies beyond its margin.  With no margin and no widening
+    it does cull kept copies on the same data, so the data reaches the
+    cases the margin is there for."""
+    cam = rotated_far_camera()
+    g = boundary_scene(cam, seed)
+    exact = exact_culled(cam, g.means)
+    pre = pretest_culled(cam, g.means)
+    assert not np.any(pre & ~exact), np.flatnonzero(pre & ~exact)[:10]
+    assert pre.sum() > 0.3 * exact.sum()
+    bare = pretest_culled(cam, g.means, margin=0.0, widen=1.0)
+    assert np.any(bare & ~exact)
 
 
 def rotated_far_camera():
