@@ -49,6 +49,7 @@ extern "C" {
 #define DG_ERR_CAPACITY (-3)  /* reserved: host-visible capacity failure */
 #define DG_ERR_CUDA (-4)      /* a CUDA launch or memset failed */
 #define DG_ERR_TOO_LARGE (-6) /* sizes beyond the fixed limits of dg_bin_sort_noalloc */
+#define DG_ERR_HOST_MEMORY (-7) /* host memory for a host-side pass could not be allocated */
 
 /* bits OR-ed into *dev_status by device code */
 #define DG_STATUS_CAPACITY 1u /* tile instances exceed `capacity`; ranges were emptied */

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libdogs.so")
 
 DG_OK, DG_ERR_INVALID, DG_ERR_WORKSPACE, DG_ERR_CAPACITY, DG_ERR_CUDA = 0, -1, -2, -3, -4
 DG_ERR_TOO_LARGE = -6
+DG_ERR_HOST_MEMORY = -7
 DG_NOALLOC_MAX_TILES, DG_NOALLOC_MAX_INSTANCES = 262144, 4194304
 DG_STATUS_CAPACITY = 1
 DG_DENSIFY_KEEP, DG_DENSIFY_PRUNE, DG_DENSIFY_CLONE, DG_DENSIFY_SPLIT = 0, 1, 2, 3
@@ -25,7 +26,8 @@ DG_MAX_VIEWS = 4096
 
 _ERR = {DG_ERR_INVALID: "invalid argument", DG_ERR_WORKSPACE: "workspace too small",
         DG_ERR_CAPACITY: "capacity", DG_ERR_CUDA: "CUDA launch failed",
-        DG_ERR_TOO_LARGE: "beyond the fixed limits of the allocation-free entry point"}
+        DG_ERR_TOO_LARGE: "beyond the fixed limits of the allocation-free entry point",
+        DG_ERR_HOST_MEMORY: "host memory could not be allocated"}
 
 
 class DogsError(RuntimeError):

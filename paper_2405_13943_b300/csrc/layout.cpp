@@ -1,7 +1,7 @@
 // The copy layout of a block membership (host): global numbering, the
 // block-local copies and the sharing map, as the batched trainer lays them
 // out.  Run when the global set changes (a densification): the same rule as
-// the initial layout, in linear passes.
+// the initial layout, in linear passes spread over host threads.
 //
 // Rule: globals held by two or more blocks are numbered first, then the
 // others; within each part by (first holding block, Z-order of the ground
@@ -9,9 +9,21 @@
 // over the points' bounding box (x in the even bits).  Block k's copies are
 // its shared globals in ascending id, then its unshared ones; the sharing
 // map lists each global's copies in ascending block.
+//
+// Passes: the points are bucketed by first block (stable counting pass over
+// contiguous chunks, one per thread), each bucket is sorted by Morton code
+// (stable radix sort) and split into its shared and unshared globals, whose
+// places follow from the bucket counts; the copies and the sharing map are
+// then written chunk by chunk of globals, the place of each copy known from
+// per-chunk counts (no pass over all globals per block).  Every pass is
+// deterministic, so the result does not depend on the thread count.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <memory>
+#include <new>
+#include <thread>
 #include <vector>
 
 #include "dogs.h"
@@ -25,24 +37,58 @@ uint64_t spread16(uint64_t v) {
     return (v | (v << 1)) & 0x55555555ull;
 }
 
-// stable LSD radix sort of idx by key (8-bit digits over the key's used bytes)
-void radix_sort(std::vector<uint64_t>& key, std::vector<int32_t>& idx, int bytes) {
-    const size_t n = key.size();
-    std::vector<uint64_t> k2(n);
-    std::vector<int32_t> i2(n);
-    for (int b = 0; b < bytes; b++) {
-        const int sh = 8 * b;
-        size_t cnt[257] = {0};
-        for (size_t i = 0; i < n; i++) cnt[((key[i] >> sh) & 0xFF) + 1]++;
-        for (int d = 0; d < 256; d++) cnt[d + 1] += cnt[d];
-        for (size_t i = 0; i < n; i++) {
-            const size_t p = cnt[(key[i] >> sh) & 0xFF]++;
-            k2[p] = key[i];
-            i2[p] = idx[i];
+// Threads for a host pass over n items: one per 64K items, at most 16.
+unsigned threads_for(int64_t n) {
+    unsigned h = std::thread::hardware_concurrency();
+    if (h == 0) h = 1;
+    const int64_t want = n / 65536 + 1;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(std::min<unsigned>(h, 16u), want));
+}
+
+// f(t) for t in [0, T): T - 1 threads and the caller.  A task whose thread
+// cannot be started runs on the caller.  f must not throw.
+template <class F>
+void parallel_for(unsigned T, const F& f) {
+    std::vector<std::thread> th;
+    unsigned started = 1;
+    try {
+        th.reserve(T);
+        for (unsigned t = 1; t < T; t++) {
+            th.emplace_back([&f, t] { f(t); });
+            started++;
         }
-        key.swap(k2);
-        idx.swap(i2);
+    } catch (...) {
     }
+    f(0u);
+    for (unsigned t = started; t < T; t++) f(t);
+    for (auto& x : th) x.join();
+}
+
+// [lo, hi) of chunk t of T over n items
+inline int64_t chunk_lo(int64_t n, unsigned T, unsigned t) { return n * (int64_t)t / (int64_t)T; }
+
+// Stable LSD radix sort of (key, idx)[0, n) by the 32-bit key: three passes
+// of 11 bits through the scratch arrays k2, i2 (n each); the result ends in
+// key, idx.
+void radix32(uint32_t* key, int32_t* idx, uint32_t* k2, int32_t* i2, int64_t n) {
+    uint32_t *ka = key, *kb = k2;
+    int32_t *ia = idx, *ib = i2;
+    for (int pass = 0; pass < 3; pass++) {
+        const int sh = 11 * pass;
+        int64_t cnt[2049] = {0};
+        for (int64_t i = 0; i < n; i++) cnt[((ka[i] >> sh) & 2047u) + 1]++;
+        for (int d = 0; d < 2048; d++) cnt[d + 1] += cnt[d];
+        for (int64_t i = 0; i < n; i++) {
+            const int64_t p = cnt[(ka[i] >> sh) & 2047u]++;
+            kb[p] = ka[i];
+            ib[p] = ia[i];
+        }
+        std::swap(ka, kb);
+        std::swap(ia, ib);
+    }
+    // three passes: the sorted data is in the scratch arrays
+    std::copy(ka, ka + n, key);
+    std::copy(ia, ia + n, idx);
 }
 
 }  // namespace
@@ -54,6 +100,183 @@ extern "C" int64_t dg_layout_copies(const uint64_t* member, int64_t n) {
     return c;
 }
 
+namespace {
+
+template <class T>
+std::unique_ptr<T[]> host_array(int64_t n) {   // uninitialised; every element is written before it is read
+    return std::unique_ptr<T[]>(new T[(size_t)std::max<int64_t>(n, 1)]);
+}
+
+void layout_impl(const double* xy, const uint64_t* member, int64_t n, int K, int32_t* order, int32_t* copy_gid,
+                 int64_t* blk_off, int64_t* blk_nshared, int64_t* g_off, int32_t* g_copies, int64_t* n_shared) {
+    const unsigned T = threads_for(n);
+    const size_t TK = (size_t)T * (size_t)K;
+    // bounding box: per chunk, then combined (min and max do not depend on the split)
+    std::vector<double> box((size_t)T * 4);
+    parallel_for(T, [&](unsigned t) {
+        double l0 = INFINITY, l1 = INFINITY, h0 = -INFINITY, h1 = -INFINITY;
+        for (int64_t i = chunk_lo(n, T, t); i < chunk_lo(n, T, t + 1); i++) {
+            l0 = std::min(l0, xy[2 * i]);
+            h0 = std::max(h0, xy[2 * i]);
+            l1 = std::min(l1, xy[2 * i + 1]);
+            h1 = std::max(h1, xy[2 * i + 1]);
+        }
+        box[4 * t] = l0; box[4 * t + 1] = l1; box[4 * t + 2] = h0; box[4 * t + 3] = h1;
+    });
+    double lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
+    for (unsigned t = 0; t < T; t++)
+        for (int a = 0; a < 2; a++) {
+            lo[a] = std::min(lo[a], box[4 * t + a]);
+            hi[a] = std::max(hi[a], box[4 * t + 2 + a]);
+        }
+    // Morton codes (the quantisation (v - lo) / max(hi - lo, 1e-30) * 65535, clipped to
+    // [0, 65535], truncated), first blocks, and per chunk the count of each first block
+    auto mort = host_array<uint32_t>(n);
+    auto first = host_array<uint8_t>(n);
+    std::vector<int64_t> ccount(TK, 0);
+    parallel_for(T, [&](unsigned t) {
+        int64_t* cc = &ccount[(size_t)t * K];
+        for (int64_t i = chunk_lo(n, T, t); i < chunk_lo(n, T, t + 1); i++) {
+            uint64_t q[2];
+            for (int a = 0; a < 2; a++) {
+                double v = (xy[2 * i + a] - lo[a]) / std::max(hi[a] - lo[a], 1e-30) * 65535.0;
+                v = std::min(std::max(v, 0.0), 65535.0);
+                q[a] = (uint64_t)v;
+            }
+            mort[i] = (uint32_t)(spread16(q[0]) | (spread16(q[1]) << 1));
+            const int f = __builtin_ctzll(member[i]);
+            first[i] = (uint8_t)f;
+            cc[f]++;
+        }
+    });
+    // stable bucketing by first block: bucket f holds its points in ascending index
+    std::vector<int64_t> boff((size_t)K + 1, 0);
+    for (int f = 0; f < K; f++) {
+        int64_t s = 0;
+        for (unsigned t = 0; t < T; t++) s += ccount[(size_t)t * K + f];
+        boff[f + 1] = boff[f] + s;
+    }
+    std::vector<int64_t> cpos(TK);
+    for (int f = 0; f < K; f++) {
+        int64_t p = boff[f];
+        for (unsigned t = 0; t < T; t++) {
+            cpos[(size_t)t * K + f] = p;
+            p += ccount[(size_t)t * K + f];
+        }
+    }
+    auto bkey = host_array<uint32_t>(n), k2 = host_array<uint32_t>(n);
+    auto bidx = host_array<int32_t>(n), i2 = host_array<int32_t>(n);
+    parallel_for(T, [&](unsigned t) {
+        int64_t pos[64];
+        for (int f = 0; f < K; f++) pos[f] = cpos[(size_t)t * K + f];
+        for (int64_t i = chunk_lo(n, T, t); i < chunk_lo(n, T, t + 1); i++) {
+            const int64_t p = pos[first[i]]++;
+            bkey[p] = mort[i];
+            bidx[p] = (int32_t)i;
+        }
+    });
+    // each bucket by Morton code (stable: ties keep ascending index), then split into
+    // its shared and unshared globals; buckets go to threads round-robin
+    const unsigned TB = std::max(1u, std::min<unsigned>(T, (unsigned)K));
+    std::vector<int64_t> nsh((size_t)K, 0);
+    parallel_for(TB, [&](unsigned t) {
+        for (int f = (int)t; f < K; f += (int)TB) {
+            const int64_t b = boff[f], m = boff[f + 1] - b;
+            radix32(&bkey[b], &bidx[b], &k2[b], &i2[b], m);
+            int64_t s = 0;
+            for (int64_t j = b; j < b + m; j++) s += __builtin_popcountll(member[bidx[j]]) >= 2;
+            nsh[f] = s;
+        }
+    });
+    int64_t ns = 0;
+    for (int f = 0; f < K; f++) ns += nsh[f];
+    std::vector<int64_t> sh_at((size_t)K), un_at((size_t)K);
+    {
+        int64_t s = 0, u = ns;
+        for (int f = 0; f < K; f++) {
+            sh_at[f] = s;
+            un_at[f] = u;
+            s += nsh[f];
+            u += boff[f + 1] - boff[f] - nsh[f];
+        }
+    }
+    auto mg = host_array<uint64_t>(n);   // mg[g]: the membership of global g
+    parallel_for(TB, [&](unsigned t) {
+        for (int f = (int)t; f < K; f += (int)TB) {
+            int64_t s = sh_at[f], u = un_at[f];
+            for (int64_t j = boff[f]; j < boff[f + 1]; j++) {
+                const int32_t i = bidx[j];
+                const uint64_t m = member[i];
+                const int64_t g = __builtin_popcountll(m) >= 2 ? s++ : u++;
+                order[g] = i;
+                mg[g] = m;
+            }
+        }
+    });
+    *n_shared = ns;
+    // per chunk of globals and per block: how many shared and unshared copies
+    std::vector<int64_t> cs(TK, 0), cu(TK, 0), gc(T, 0);
+    parallel_for(T, [&](unsigned t) {
+        int64_t* s = &cs[(size_t)t * K];
+        int64_t* u = &cu[(size_t)t * K];
+        int64_t c = 0;
+        for (int64_t g = chunk_lo(n, T, t); g < chunk_lo(n, T, t + 1); g++) {
+            uint64_t m = mg[g];
+            c += __builtin_popcountll(m);
+            int64_t* d = g < ns ? s : u;
+            for (; m; m &= m - 1) d[__builtin_ctzll(m)]++;
+        }
+        gc[t] = c;
+    });
+    // block offsets; each chunk's first place in each block's shared and unshared parts
+    blk_off[0] = 0;
+    for (int k = 0; k < K; k++) {
+        int64_t a = 0, b = 0;
+        for (unsigned t = 0; t < T; t++) {
+            a += cs[(size_t)t * K + k];
+            b += cu[(size_t)t * K + k];
+        }
+        blk_nshared[k] = a;
+        blk_off[k + 1] = blk_off[k] + a + b;
+        int64_t ps = blk_off[k], pu = blk_off[k] + a;
+        for (unsigned t = 0; t < T; t++) {
+            const int64_t x = cs[(size_t)t * K + k], y = cu[(size_t)t * K + k];
+            cs[(size_t)t * K + k] = ps;
+            cu[(size_t)t * K + k] = pu;
+            ps += x;
+            pu += y;
+        }
+    }
+    if (n == 0) {
+        if (g_off) g_off[0] = 0;
+        return;
+    }
+    std::vector<int64_t> gstart(T, 0);
+    for (unsigned t = 1; t < T; t++) gstart[t] = gstart[t - 1] + gc[t - 1];
+    // copies (block-major) and the sharing map: the copy of global g in block k is
+    // g_copies[g_off[g] + (the number of g's blocks below k)]
+    parallel_for(T, [&](unsigned t) {
+        int64_t ps[64], pu[64];
+        for (int k = 0; k < K; k++) {
+            ps[k] = cs[(size_t)t * K + k];
+            pu[k] = cu[(size_t)t * K + k];
+        }
+        int64_t go = gstart[t];
+        for (int64_t g = chunk_lo(n, T, t); g < chunk_lo(n, T, t + 1); g++) {
+            g_off[g] = go;
+            int64_t* p = g < ns ? ps : pu;
+            for (uint64_t m = mg[g]; m; m &= m - 1) {
+                const int64_t e = p[__builtin_ctzll(m)]++;
+                copy_gid[e] = (int32_t)g;
+                g_copies[go++] = (int32_t)e;
+            }
+        }
+    });
+    g_off[n] = blk_off[K];
+}
+
+}  // namespace
+
 extern "C" int dg_layout(const double* xy, const uint64_t* member, int64_t n, int K, int32_t* order,
                          int32_t* copy_gid, int64_t* blk_off, int64_t* blk_nshared, int64_t* g_off,
                          int32_t* g_copies, int64_t* n_shared) {
@@ -63,60 +286,12 @@ extern "C" int dg_layout(const double* xy, const uint64_t* member, int64_t n, in
     const uint64_t valid = K == 64 ? ~0ull : ((1ull << K) - 1);
     for (int64_t i = 0; i < n; i++)
         if (member[i] == 0 || (member[i] & ~valid)) return DG_ERR_INVALID;   // every point in some block
-    // Morton codes over the bounding box (the quantisation of the numpy rule:
-    // (v - lo) / max(hi - lo, 1e-30) * 65535, clipped to [0, 65535], truncated)
-    double lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
-    for (int64_t i = 0; i < n; i++)
-        for (int a = 0; a < 2; a++) {
-            lo[a] = std::min(lo[a], xy[2 * i + a]);
-            hi[a] = std::max(hi[a], xy[2 * i + a]);
-        }
-    std::vector<uint64_t> key((size_t)n);
-    std::vector<int32_t> idx((size_t)n);
-    for (int64_t i = 0; i < n; i++) {
-        uint64_t q[2];
-        for (int a = 0; a < 2; a++) {
-            double v = (xy[2 * i + a] - lo[a]) / std::max(hi[a] - lo[a], 1e-30) * 65535.0;
-            v = std::min(std::max(v, 0.0), 65535.0);
-            q[a] = (uint64_t)v;
-        }
-        const uint64_t first = (uint64_t)__builtin_ctzll(member[i]);
-        key[i] = (first << 32) | spread16(q[0]) | (spread16(q[1]) << 1);
-        idx[i] = (int32_t)i;
-    }
-    radix_sort(key, idx, 5);                      // 32 Morton bits + 6 block bits
-    // shared first, each part in key order; mg[g]: the membership of global g
-    std::vector<uint64_t> ms((size_t)n);
-    for (int64_t j = 0; j < n; j++) ms[j] = member[idx[j]];
-    std::vector<uint64_t> mg((size_t)n);
-    int64_t ns = 0, o = 0;
-    for (int64_t j = 0; j < n; j++)
-        if (__builtin_popcountll(ms[j]) >= 2) { mg[o] = ms[j]; order[o++] = idx[j]; }
-    ns = o;
-    for (int64_t j = 0; j < n; j++)
-        if (__builtin_popcountll(ms[j]) < 2) { mg[o] = ms[j]; order[o++] = idx[j]; }
-    *n_shared = ns;
-    // block-local copies: shared globals of the block, then unshared, ascending id
-    int64_t c = 0;
-    blk_off[0] = 0;
-    for (int k = 0; k < K; k++) {
-        const uint64_t bit = 1ull << k;
-        int64_t nsh = 0;
-        for (int64_t g = 0; g < ns; g++)
-            if (mg[g] & bit) { copy_gid[c++] = (int32_t)g; nsh++; }
-        for (int64_t g = ns; g < n; g++)
-            if (mg[g] & bit) copy_gid[c++] = (int32_t)g;
-        blk_nshared[k] = nsh;
-        blk_off[k + 1] = c;
-    }
-    // sharing map: each global's copies in ascending block (copies are block-major)
-    if (n == 0 && g_off) g_off[0] = 0;
-    if (n > 0) {
-        std::fill(g_off, g_off + n + 1, 0);
-        for (int64_t e = 0; e < c; e++) g_off[copy_gid[e] + 1]++;
-        for (int64_t g = 0; g < n; g++) g_off[g + 1] += g_off[g];
-        std::vector<int64_t> cur(g_off, g_off + n);
-        for (int64_t e = 0; e < c; e++) g_copies[cur[copy_gid[e]]++] = (int32_t)e;
+    try {
+        layout_impl(xy, member, n, K, order, copy_gid, blk_off, blk_nshared, g_off, g_copies, n_shared);
+    } catch (const std::bad_alloc&) {
+        return DG_ERR_HOST_MEMORY;
+    } catch (...) {
+        return DG_ERR_INVALID;
     }
     return DG_OK;
 }

@@ -16,8 +16,10 @@ def DZ():
     return densify
 
 
+# (300000, 8): past 65,536 points per thread, so the builder's passes run on
+# several host threads where the machine has them
 @pytest.mark.parametrize("n,K,seed", [(1, 1, 0), (500, 1, 1), (3000, 4, 2), (20000, 8, 3), (4000, 37, 4),
-                                      (5000, 64, 5)])
+                                      (5000, 64, 5), (300000, 8, 7)])
 def test_native_layout_equals_reference(DZ, n, K, seed):
     rng = np.random.default_rng(seed)
     xy = rng.uniform(-50, 900, (n, 2))
