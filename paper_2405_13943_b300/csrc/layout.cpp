@@ -295,3 +295,41 @@ extern "C" int dg_layout(const double* xy, const uint64_t* member, int64_t n, in
     }
     return DG_OK;
 }
+
+extern "C" int dg_layout_carry(const int64_t* old_blk_off, const int64_t* old_g_off, const int32_t* old_g_copies,
+                               int64_t n_old, int K, const int64_t* new_blk_off, const int32_t* new_copy_gid,
+                               const int32_t* parent, const uint8_t* original, int64_t n_new, int32_t* carry) {
+    if (K < 1 || K > DG_MAX_BLOCKS || n_old < 0 || n_new < 0 || !old_blk_off || !new_blk_off || !old_g_off)
+        return DG_ERR_INVALID;
+    const int64_t nc = new_blk_off[K], oc = old_blk_off[K];
+    if (new_blk_off[0] != 0 || old_blk_off[0] != 0 || nc < 0 || oc < 0 || old_g_off[n_old] != oc)
+        return DG_ERR_INVALID;
+    for (int k = 0; k < K; k++)
+        if (new_blk_off[k + 1] < new_blk_off[k] || old_blk_off[k + 1] < old_blk_off[k]) return DG_ERR_INVALID;
+    if (nc > 0 && (!new_copy_gid || !parent || !original || !carry)) return DG_ERR_INVALID;
+    if (oc > 0 && !old_g_copies) return DG_ERR_INVALID;
+    std::atomic<bool> bad{false};
+    const unsigned T = threads_for(nc);
+    parallel_for(T, [&](unsigned t) {
+        const int64_t lo = chunk_lo(nc, T, t), hi = chunk_lo(nc, T, t + 1);
+        int b = (int)(std::upper_bound(new_blk_off, new_blk_off + K + 1, lo) - new_blk_off) - 1;
+        for (int64_t e = lo; e < hi; e++) {
+            while (e >= new_blk_off[b + 1]) b++;   // block of copy e
+            carry[e] = -1;
+            const int32_t g = new_copy_gid[e];
+            if (g < 0 || g >= n_new) { bad = true; continue; }
+            if (!original[g]) continue;
+            const int32_t p = parent[g];
+            if (p < 0 || p >= n_old) { bad = true; continue; }
+            if (old_g_off[p] < 0 || old_g_off[p + 1] > oc) { bad = true; continue; }
+            for (int64_t j = old_g_off[p]; j < old_g_off[p + 1]; j++) {
+                const int32_t c = old_g_copies[j];
+                if (c < 0 || c >= oc) { bad = true; break; }
+                const int cb = (int)(std::upper_bound(old_blk_off, old_blk_off + K + 1, (int64_t)c) - old_blk_off) - 1;
+                if (cb == b) { carry[e] = c; break; }
+                if (cb > b) break;   // the copies are in ascending block
+            }
+        }
+    });
+    return bad ? DG_ERR_INVALID : DG_OK;
+}

@@ -81,20 +81,21 @@ def carried_copies(old: S.BlockSplit, new: S.BlockSplit, src_of_new_global: np.n
     """For every copy of the new layout, the copy of the old layout whose
     state it takes over (-1: none): the parent Gaussian's copy in the same
     block, when the new Gaussian is its parent itself.  The parent's copies
-    are looked up through the old sharing map (a few per Gaussian)."""
-    K = old.K
-    old_blk = np.repeat(np.arange(K, dtype=np.int32), np.diff(old.blk_off))
-    new_blk = np.repeat(np.arange(K, dtype=np.int32), np.diff(new.blk_off))
-    g_new = new.copy_gid.astype(np.int64)
-    parent = src_of_new_global[g_new].astype(np.int64)
-    start, cnt = old.g_off[parent], np.diff(old.g_off)[parent]
-    carry = np.full(new.n_copies, -1, np.int64)
-    for j in range(int(cnt.max()) if cnt.size else 0):
-        has = cnt > j
-        cand = np.where(has, old.g_copies[np.minimum(start + j, len(old.g_copies) - 1)], 0)
-        hit = has & (old_blk[cand] == new_blk)
-        carry = np.where(hit, cand, carry)
-    return np.where(original[g_new], carry, -1).astype(np.int32)
+    are looked up through the old sharing map (dg_layout_carry, host C++)."""
+    from . import _lib as L
+    old_blk = np.ascontiguousarray(old.blk_off, np.int64)
+    old_goff = np.ascontiguousarray(old.g_off, np.int64)
+    old_gcp = np.ascontiguousarray(old.g_copies, np.int32)
+    new_blk = np.ascontiguousarray(new.blk_off, np.int64)
+    new_gid = np.ascontiguousarray(new.copy_gid, np.int32)
+    parent = np.ascontiguousarray(src_of_new_global, np.int32)
+    orig = np.ascontiguousarray(original, np.uint8)
+    carry = np.empty(max(new.n_copies, 1), np.int32)
+    L.check(L.lib().dg_layout_carry(old_blk.ctypes.data, old_goff.ctypes.data, old_gcp.ctypes.data,
+                                    old_goff.shape[0] - 1, old.K, new_blk.ctypes.data, new_gid.ctypes.data,
+                                    parent.ctypes.data, orig.ctypes.data, parent.shape[0], carry.ctypes.data),
+            "dg_layout_carry")
+    return carry[:new.n_copies]
 
 
 def densify(tr, cfg: DensifyConfig, extent: float, step_seed: int) -> Dict:

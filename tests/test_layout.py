@@ -43,11 +43,12 @@ def test_native_layout_rejects_a_point_in_no_block(DZ):
         DZ.native_layout(np.zeros((3, 2)), member, np.zeros((2, 4)), 1.0)
 
 
-def test_carried_copies_by_brute_force(DZ):
+@pytest.mark.parametrize("n", [3000, 200000])     # the larger one spans several host threads
+def test_carried_copies_by_brute_force(DZ, n):
     """The copy whose state a new copy takes over: the parent's copy in the
     same block when the new Gaussian is its parent itself, else none."""
     rng = np.random.default_rng(6)
-    n, K = 3000, 6
+    K = 6
     xy = rng.uniform(0, 100, (n, 2))
     member = np.zeros((n, K), bool)
     member[np.arange(n), rng.integers(0, K, n)] = True
@@ -68,3 +69,15 @@ def test_carried_copies_by_brute_force(DZ):
             for i, g in enumerate(new.copy_gid)]
     np.testing.assert_array_equal(got, want)
     assert 0 < (got >= 0).mean() < 1
+
+
+def test_carry_rejects_an_id_out_of_range(DZ):
+    rng = np.random.default_rng(8)
+    n, K = 200, 3
+    member = np.zeros((n, K), bool)
+    member[np.arange(n), rng.integers(0, K, n)] = True
+    old, _ = S.split_layout(rng.uniform(0, 10, (n, 2)), member, np.zeros((K, 4)), 1.0)
+    src = np.arange(n)
+    src[5] = n + 3                                      # a parent that the old layout does not have
+    with pytest.raises(Exception):
+        DZ.carried_copies(old, old, src, np.ones(n, bool))
