@@ -10,13 +10,13 @@
 // its shared globals in ascending id, then its unshared ones; the sharing
 // map lists each global's copies in ascending block.
 //
-// Passes: the points are bucketed by first block (stable counting pass over
-// contiguous chunks, one per thread), each bucket is sorted by Morton code
-// (stable radix sort) and split into its shared and unshared globals, whose
-// places follow from the bucket counts; the copies and the sharing map are
-// then written chunk by chunk of globals, the place of each copy known from
-// per-chunk counts (no pass over all globals per block).  Every pass is
-// deterministic, so the result does not depend on the thread count.
+// Passes: the points are bucketed by (shared or not, first block) in a
+// stable counting pass over contiguous chunks, one per thread; each bucket is
+// sorted by Morton code (stable radix sort), and the buckets in sequence are
+// the global numbering.  The copies and the sharing map are then written
+// chunk by chunk of globals, the place of each copy known from per-chunk
+// counts (no pass over all globals per block).  Every pass is deterministic,
+// so the result does not depend on the thread count.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -25,6 +25,8 @@
 #include <new>
 #include <thread>
 #include <vector>
+
+#include <sched.h>
 
 #include "dogs.h"
 
@@ -37,10 +39,21 @@ uint64_t spread16(uint64_t v) {
     return (v | (v << 1)) & 0x55555555ull;
 }
 
-// Threads for a host pass over n items: one per 64K items, at most 16.
+// CPUs this process may run on (its affinity mask), else the online count.
+unsigned usable_cpus() {
+    cpu_set_t set;
+    if (sched_getaffinity(0, sizeof(set), &set) == 0) {
+        const int c = CPU_COUNT(&set);
+        if (c > 0) return (unsigned)c;
+    }
+    const unsigned h = std::thread::hardware_concurrency();
+    return h ? h : 1u;
+}
+
+// Threads for a host pass over n items: one per 64K items, at most 16 and at
+// most the usable CPUs.
 unsigned threads_for(int64_t n) {
-    unsigned h = std::thread::hardware_concurrency();
-    if (h == 0) h = 1;
+    const unsigned h = usable_cpus();
     const int64_t want = n / 65536 + 1;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(std::min<unsigned>(h, 16u), want));
 }
@@ -67,28 +80,40 @@ void parallel_for(unsigned T, const F& f) {
 // [lo, hi) of chunk t of T over n items
 inline int64_t chunk_lo(int64_t n, unsigned T, unsigned t) { return n * (int64_t)t / (int64_t)T; }
 
-// Stable LSD radix sort of (key, idx)[0, n) by the 32-bit key: three passes
-// of 11 bits through the scratch arrays k2, i2 (n each); the result ends in
-// key, idx.
+// Stable LSD radix sort of (key, idx)[0, n) by the 32-bit key, in digits of
+// BITS bits: one read pass counts every digit, then one scatter pass per
+// digit through the scratch arrays k2, i2 (n each), skipping a digit that
+// all keys share; the result ends in key, idx.
+template <int BITS>
 void radix32(uint32_t* key, int32_t* idx, uint32_t* k2, int32_t* i2, int64_t n) {
+    constexpr int P = (32 + BITS - 1) / BITS, R = 1 << BITS;
+    int64_t cnt[P][R + 1];
+    for (int p = 0; p < P; p++) std::fill(cnt[p], cnt[p] + R + 1, (int64_t)0);
+    for (int64_t i = 0; i < n; i++) {
+        const uint32_t k = key[i];
+        for (int p = 0; p < P; p++) cnt[p][((k >> (p * BITS)) & (R - 1)) + 1]++;
+    }
     uint32_t *ka = key, *kb = k2;
     int32_t *ia = idx, *ib = i2;
-    for (int pass = 0; pass < 3; pass++) {
-        const int sh = 11 * pass;
-        int64_t cnt[2049] = {0};
-        for (int64_t i = 0; i < n; i++) cnt[((ka[i] >> sh) & 2047u) + 1]++;
-        for (int d = 0; d < 2048; d++) cnt[d + 1] += cnt[d];
+    for (int p = 0; p < P; p++) {
+        int64_t* c = cnt[p];
+        bool shared_digit = false;
+        for (int d = 0; d < R && !shared_digit; d++) shared_digit = c[d + 1] == n;
+        if (shared_digit) continue;
+        for (int d = 0; d < R; d++) c[d + 1] += c[d];
+        const int sh = p * BITS;
         for (int64_t i = 0; i < n; i++) {
-            const int64_t p = cnt[(ka[i] >> sh) & 2047u]++;
-            kb[p] = ka[i];
-            ib[p] = ia[i];
+            const int64_t q = c[(ka[i] >> sh) & (R - 1)]++;
+            kb[q] = ka[i];
+            ib[q] = ia[i];
         }
         std::swap(ka, kb);
         std::swap(ia, ib);
     }
-    // three passes: the sorted data is in the scratch arrays
-    std::copy(ka, ka + n, key);
-    std::copy(ia, ia + n, idx);
+    if (ka != key) {
+        std::copy(ka, ka + n, key);
+        std::copy(ia, ia + n, idx);
+    }
 }
 
 }  // namespace
@@ -130,12 +155,15 @@ void layout_impl(const double* xy, const uint64_t* member, int64_t n, int K, int
             hi[a] = std::max(hi[a], box[4 * t + 2 + a]);
         }
     // Morton codes (the quantisation (v - lo) / max(hi - lo, 1e-30) * 65535, clipped to
-    // [0, 65535], truncated), first blocks, and per chunk the count of each first block
+    // [0, 65535], truncated) and buckets: bucket f < K holds the shared points whose
+    // first block is f, bucket K + f the unshared ones; per chunk the count of each
+    const int NB = 2 * K;
+    const size_t TB2 = (size_t)T * (size_t)NB;
     auto mort = host_array<uint32_t>(n);
-    auto first = host_array<uint8_t>(n);
-    std::vector<int64_t> ccount(TK, 0);
+    auto bucket = host_array<uint8_t>(n);
+    std::vector<int64_t> ccount(TB2, 0);
     parallel_for(T, [&](unsigned t) {
-        int64_t* cc = &ccount[(size_t)t * K];
+        int64_t* cc = &ccount[(size_t)t * NB];
         for (int64_t i = chunk_lo(n, T, t); i < chunk_lo(n, T, t + 1); i++) {
             uint64_t q[2];
             for (int a = 0; a < 2; a++) {
@@ -144,74 +172,50 @@ void layout_impl(const double* xy, const uint64_t* member, int64_t n, int K, int
                 q[a] = (uint64_t)v;
             }
             mort[i] = (uint32_t)(spread16(q[0]) | (spread16(q[1]) << 1));
-            const int f = __builtin_ctzll(member[i]);
-            first[i] = (uint8_t)f;
-            cc[f]++;
+            const uint64_t m = member[i];
+            const int b = __builtin_ctzll(m) + (__builtin_popcountll(m) >= 2 ? 0 : K);
+            bucket[i] = (uint8_t)b;
+            cc[b]++;
         }
     });
-    // stable bucketing by first block: bucket f holds its points in ascending index
-    std::vector<int64_t> boff((size_t)K + 1, 0);
-    for (int f = 0; f < K; f++) {
+    // stable bucketing: bucket b holds its points in ascending index
+    std::vector<int64_t> boff((size_t)NB + 1, 0);
+    for (int b = 0; b < NB; b++) {
         int64_t s = 0;
-        for (unsigned t = 0; t < T; t++) s += ccount[(size_t)t * K + f];
-        boff[f + 1] = boff[f] + s;
+        for (unsigned t = 0; t < T; t++) s += ccount[(size_t)t * NB + b];
+        boff[b + 1] = boff[b] + s;
     }
-    std::vector<int64_t> cpos(TK);
-    for (int f = 0; f < K; f++) {
-        int64_t p = boff[f];
+    std::vector<int64_t> cpos(TB2);
+    for (int b = 0; b < NB; b++) {
+        int64_t p = boff[b];
         for (unsigned t = 0; t < T; t++) {
-            cpos[(size_t)t * K + f] = p;
-            p += ccount[(size_t)t * K + f];
+            cpos[(size_t)t * NB + b] = p;
+            p += ccount[(size_t)t * NB + b];
         }
     }
     auto bkey = host_array<uint32_t>(n), k2 = host_array<uint32_t>(n);
-    auto bidx = host_array<int32_t>(n), i2 = host_array<int32_t>(n);
+    auto k2i = host_array<int32_t>(n);
     parallel_for(T, [&](unsigned t) {
-        int64_t pos[64];
-        for (int f = 0; f < K; f++) pos[f] = cpos[(size_t)t * K + f];
+        int64_t pos[2 * DG_MAX_BLOCKS];
+        for (int b = 0; b < NB; b++) pos[b] = cpos[(size_t)t * NB + b];
         for (int64_t i = chunk_lo(n, T, t); i < chunk_lo(n, T, t + 1); i++) {
-            const int64_t p = pos[first[i]]++;
+            const int64_t p = pos[bucket[i]]++;
             bkey[p] = mort[i];
-            bidx[p] = (int32_t)i;
+            order[p] = (int32_t)i;
         }
     });
-    // each bucket by Morton code (stable: ties keep ascending index), then split into
-    // its shared and unshared globals; buckets go to threads round-robin
-    const unsigned TB = std::max(1u, std::min<unsigned>(T, (unsigned)K));
-    std::vector<int64_t> nsh((size_t)K, 0);
-    parallel_for(TB, [&](unsigned t) {
-        for (int f = (int)t; f < K; f += (int)TB) {
-            const int64_t b = boff[f], m = boff[f + 1] - b;
-            radix32(&bkey[b], &bidx[b], &k2[b], &i2[b], m);
-            int64_t s = 0;
-            for (int64_t j = b; j < b + m; j++) s += __builtin_popcountll(member[bidx[j]]) >= 2;
-            nsh[f] = s;
-        }
+    // each bucket by Morton code (stable: ties keep ascending index); buckets go to
+    // threads round-robin.  The buckets in sequence are the global numbering: the
+    // shared globals (by first block, then Z-order), then the unshared ones.
+    const unsigned TS = std::max(1u, std::min<unsigned>(T, (unsigned)NB));
+    parallel_for(TS, [&](unsigned t) {
+        for (int b = (int)t; b < NB; b += (int)TS)
+            radix32<8>(&bkey[boff[b]], &order[boff[b]], &k2[boff[b]], &k2i[boff[b]], boff[b + 1] - boff[b]);
     });
-    int64_t ns = 0;
-    for (int f = 0; f < K; f++) ns += nsh[f];
-    std::vector<int64_t> sh_at((size_t)K), un_at((size_t)K);
-    {
-        int64_t s = 0, u = ns;
-        for (int f = 0; f < K; f++) {
-            sh_at[f] = s;
-            un_at[f] = u;
-            s += nsh[f];
-            u += boff[f + 1] - boff[f] - nsh[f];
-        }
-    }
+    const int64_t ns = boff[K];
     auto mg = host_array<uint64_t>(n);   // mg[g]: the membership of global g
-    parallel_for(TB, [&](unsigned t) {
-        for (int f = (int)t; f < K; f += (int)TB) {
-            int64_t s = sh_at[f], u = un_at[f];
-            for (int64_t j = boff[f]; j < boff[f + 1]; j++) {
-                const int32_t i = bidx[j];
-                const uint64_t m = member[i];
-                const int64_t g = __builtin_popcountll(m) >= 2 ? s++ : u++;
-                order[g] = i;
-                mg[g] = m;
-            }
-        }
+    parallel_for(T, [&](unsigned t) {
+        for (int64_t g = chunk_lo(n, T, t); g < chunk_lo(n, T, t + 1); g++) mg[g] = member[order[g]];
     });
     *n_shared = ns;
     // per chunk of globals and per block: how many shared and unshared copies
