@@ -81,3 +81,22 @@ def test_carry_rejects_an_id_out_of_range(DZ):
     src[5] = n + 3                                      # a parent that the old layout does not have
     with pytest.raises(Exception):
         DZ.carried_copies(old, old, src, np.ones(n, bool))
+
+
+@pytest.mark.parametrize("n,K,pattern", [(70000, 3, "all"), (70000, 64, "one"), (2, 64, "all")])
+def test_native_layout_extreme_memberships(DZ, n, K, pattern):
+    """Every point in every block (all globals shared), or all points in the
+    last of many blocks (every other block empty), against the reference."""
+    rng = np.random.default_rng(9)
+    xy = rng.uniform(0, 50, (n, 2))
+    member = np.zeros((n, K), bool)
+    if pattern == "all":
+        member[:] = True
+    else:
+        member[:, K - 1] = True
+    a, oa = S.split_layout(xy, member, np.zeros((K, 4)), 1.0)
+    b, ob = DZ.native_layout(xy, member, np.zeros((K, 4)), 1.0)
+    np.testing.assert_array_equal(oa, ob)
+    for f in ("copy_gid", "blk_off", "blk_nshared", "g_off", "g_copies"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f), err_msg=f)
+    assert a.n_shared_globals == b.n_shared_globals == (n if pattern == "all" else 0)
