@@ -400,18 +400,19 @@ int dg_layout(const double* xy, const uint64_t* member, int64_t n, int K, int32_
               int32_t* g_copies, int64_t* n_shared);
 
 /* The state carried across a re-layout (densification, Sec. 4, under the
- * consensus): for every copy e of a new layout (blocks new_blk_off[K + 1],
- * global ids new_copy_gid[new_blk_off[K]]), carry[e] = the copy of the old
- * layout, in the same block, of old global parent[g] when original[g] != 0
- * (g = new_copy_gid[e], a Gaussian that is its parent itself), else -1.
- * The old copy is found through the old sharing map (old_g_off[n_old + 1],
- * old_g_copies: each global's copies in ascending block) and old_blk_off
- * [K + 1].  parent, original: n_new entries.  Host memory; no GPU.
- * DG_ERR_INVALID on bad sizes, null pointers or an id out of range (carry
- * then partly written). */
+ * consensus): for every copy e of a new layout, carry[e] = the copy of the
+ * old layout, in the same block, of old global parent[g] when original[g]
+ * != 0 (g = the new global of e, a Gaussian that is its parent itself),
+ * else -1.  Both layouts are given by their block offsets (old_blk_off,
+ * new_blk_off: K + 1) and sharing maps (old_g_off[n_old + 1] /
+ * old_g_copies, new_g_off[n_new + 1] / new_g_copies: each global's copies
+ * in ascending block); parent, original: n_new entries; carry: the new
+ * copy count.  Host memory; no GPU.  DG_ERR_INVALID on bad sizes, null
+ * pointers or an id out of range (carry then partly written). */
 int dg_layout_carry(const int64_t* old_blk_off, const int64_t* old_g_off, const int32_t* old_g_copies,
-                    int64_t n_old, int K, const int64_t* new_blk_off, const int32_t* new_copy_gid,
-                    const int32_t* parent, const uint8_t* original, int64_t n_new, int32_t* carry);
+                    int64_t n_old, int K, const int64_t* new_blk_off, const int64_t* new_g_off,
+                    const int32_t* new_g_copies, const int32_t* parent, const uint8_t* original,
+                    int64_t n_new, int32_t* carry);
 
 /* dst row r = src row idx[r] (all fields and SH planes) for r < dst->n;
  * rows with idx[r] < 0 are left unchanged.  The rows move between the

@@ -301,37 +301,57 @@ extern "C" int dg_layout(const double* xy, const uint64_t* member, int64_t n, in
 }
 
 extern "C" int dg_layout_carry(const int64_t* old_blk_off, const int64_t* old_g_off, const int32_t* old_g_copies,
-                               int64_t n_old, int K, const int64_t* new_blk_off, const int32_t* new_copy_gid,
-                               const int32_t* parent, const uint8_t* original, int64_t n_new, int32_t* carry) {
-    if (K < 1 || K > DG_MAX_BLOCKS || n_old < 0 || n_new < 0 || !old_blk_off || !new_blk_off || !old_g_off)
+                               int64_t n_old, int K, const int64_t* new_blk_off, const int64_t* new_g_off,
+                               const int32_t* new_g_copies, const int32_t* parent, const uint8_t* original,
+                               int64_t n_new, int32_t* carry) {
+    if (K < 1 || K > DG_MAX_BLOCKS || n_old < 0 || n_new < 0 || !old_blk_off || !new_blk_off || !old_g_off ||
+        !new_g_off)
         return DG_ERR_INVALID;
     const int64_t nc = new_blk_off[K], oc = old_blk_off[K];
-    if (new_blk_off[0] != 0 || old_blk_off[0] != 0 || nc < 0 || oc < 0 || old_g_off[n_old] != oc)
+    if (new_blk_off[0] != 0 || old_blk_off[0] != 0 || nc < 0 || oc < 0 || old_g_off[n_old] != oc ||
+        new_g_off[0] != 0 || new_g_off[n_new] != nc)
         return DG_ERR_INVALID;
     for (int k = 0; k < K; k++)
         if (new_blk_off[k + 1] < new_blk_off[k] || old_blk_off[k + 1] < old_blk_off[k]) return DG_ERR_INVALID;
-    if (nc > 0 && (!new_copy_gid || !parent || !original || !carry)) return DG_ERR_INVALID;
+    if (nc > 0 && (!new_g_copies || !parent || !original || !carry)) return DG_ERR_INVALID;
     if (oc > 0 && !old_g_copies) return DG_ERR_INVALID;
+    auto block_of = [K](const int64_t* off, int64_t c) {
+        return (int)(std::upper_bound(off, off + K + 1, c) - off) - 1;
+    };
     std::atomic<bool> bad{false};
+    // by new global: its copies (new sharing map, ascending block) against its
+    // parent's copies (old sharing map, ascending block), merged by block
     const unsigned T = threads_for(nc);
     parallel_for(T, [&](unsigned t) {
-        const int64_t lo = chunk_lo(nc, T, t), hi = chunk_lo(nc, T, t + 1);
-        int b = (int)(std::upper_bound(new_blk_off, new_blk_off + K + 1, lo) - new_blk_off) - 1;
-        for (int64_t e = lo; e < hi; e++) {
-            while (e >= new_blk_off[b + 1]) b++;   // block of copy e
-            carry[e] = -1;
-            const int32_t g = new_copy_gid[e];
-            if (g < 0 || g >= n_new) { bad = true; continue; }
-            if (!original[g]) continue;
-            const int32_t p = parent[g];
-            if (p < 0 || p >= n_old) { bad = true; continue; }
-            if (old_g_off[p] < 0 || old_g_off[p + 1] > oc) { bad = true; continue; }
-            for (int64_t j = old_g_off[p]; j < old_g_off[p + 1]; j++) {
-                const int32_t c = old_g_copies[j];
-                if (c < 0 || c >= oc) { bad = true; break; }
-                const int cb = (int)(std::upper_bound(old_blk_off, old_blk_off + K + 1, (int64_t)c) - old_blk_off) - 1;
-                if (cb == b) { carry[e] = c; break; }
-                if (cb > b) break;   // the copies are in ascending block
+        for (int64_t g = chunk_lo(n_new, T, t); g < chunk_lo(n_new, T, t + 1); g++) {
+            const int64_t a0 = new_g_off[g], a1 = new_g_off[g + 1];
+            if (a0 < 0 || a1 < a0 || a1 > nc) { bad = true; continue; }
+            int64_t j = 0, j1 = 0;
+            const int32_t p = original[g] ? parent[g] : -1;
+            if (original[g]) {
+                if (p < 0 || p >= n_old || old_g_off[p] < 0 || old_g_off[p + 1] < old_g_off[p] ||
+                    old_g_off[p + 1] > oc) {
+                    bad = true;
+                    continue;
+                }
+                j = old_g_off[p];
+                j1 = old_g_off[p + 1];
+            }
+            int ob = -1;                             // block of old copy j
+            for (int64_t a = a0; a < a1; a++) {
+                const int32_t e = new_g_copies[a];
+                if (e < 0 || e >= nc) { bad = true; break; }
+                const int b = block_of(new_blk_off, e);
+                int32_t hit = -1;
+                while (j < j1) {
+                    const int32_t c = old_g_copies[j];
+                    if (c < 0 || c >= oc) { bad = true; j = j1; break; }
+                    if (ob < 0) ob = block_of(old_blk_off, c);
+                    if (ob < b) { j++; ob = -1; continue; }
+                    if (ob == b) hit = c;
+                    break;
+                }
+                carry[e] = hit;
             }
         }
     });

@@ -87,14 +87,17 @@ def carried_copies(old: S.BlockSplit, new: S.BlockSplit, src_of_new_global: np.n
     old_goff = np.ascontiguousarray(old.g_off, np.int64)
     old_gcp = np.ascontiguousarray(old.g_copies, np.int32)
     new_blk = np.ascontiguousarray(new.blk_off, np.int64)
-    new_gid = np.ascontiguousarray(new.copy_gid, np.int32)
+    new_goff = np.ascontiguousarray(new.g_off, np.int64)
+    new_gcp = np.ascontiguousarray(new.g_copies, np.int32)
     parent = np.ascontiguousarray(src_of_new_global, np.int32)
     orig = np.ascontiguousarray(original, np.uint8)
+    if parent.shape[0] != new_goff.shape[0] - 1 or orig.shape[0] != parent.shape[0]:
+        raise ValueError("one parent and one flag per new global")
     carry = np.empty(max(new.n_copies, 1), np.int32)
     L.check(L.lib().dg_layout_carry(old_blk.ctypes.data, old_goff.ctypes.data, old_gcp.ctypes.data,
-                                    old_goff.shape[0] - 1, old.K, new_blk.ctypes.data, new_gid.ctypes.data,
-                                    parent.ctypes.data, orig.ctypes.data, parent.shape[0], carry.ctypes.data),
-            "dg_layout_carry")
+                                    old_goff.shape[0] - 1, old.K, new_blk.ctypes.data, new_goff.ctypes.data,
+                                    new_gcp.ctypes.data, parent.ctypes.data, orig.ctypes.data, parent.shape[0],
+                                    carry.ctypes.data), "dg_layout_carry")
     return carry[:new.n_copies]
 
 
