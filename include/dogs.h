@@ -399,6 +399,15 @@ int dg_layout(const double* xy, const uint64_t* member, int64_t n, int K, int32_
               int32_t* copy_gid, int64_t* blk_off, int64_t* blk_nshared, int64_t* g_off,
               int32_t* g_copies, int64_t* n_shared);
 
+/* The block membership of a re-laid-out set: member[j] = the bitmask of the
+ * blocks (bit k: block k) that hold a copy of old global parent[j], read
+ * from the old block offsets (old_blk_off, K + 1) and sharing map
+ * (old_g_off[n_old + 1] / old_g_copies).  parent, member: n_new entries.
+ * Host memory; no GPU.  DG_ERR_INVALID on bad sizes, null pointers or an
+ * id out of range (member then partly written). */
+int dg_layout_membership(const int64_t* old_blk_off, const int64_t* old_g_off, const int32_t* old_g_copies,
+                         int64_t n_old, int K, const int32_t* parent, int64_t n_new, uint64_t* member);
+
 /* The state carried across a re-layout (densification, Sec. 4, under the
  * consensus): for every copy e of a new layout, carry[e] = the copy of the
  * old layout, in the same block, of old global parent[g] when original[g]

@@ -112,6 +112,7 @@ _SIGS = {
     "dg_reset_opacity": (C.c_int, [C.POINTER(DgGaussians), C.c_float, C.POINTER(DgGaussians),
                                    C.POINTER(DgGaussians), _vp]),
     "dg_layout": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "dg_layout_membership": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int, _vp, C.c_int64, _vp]),
     "dg_layout_carry": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_int64, _vp]),
     "dg_scene_split": (C.c_int, [_vp, C.c_int64, C.c_int, _vp, _vp]),
     "dg_scene_assign": (C.c_int, [_vp, C.c_int64, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp]),

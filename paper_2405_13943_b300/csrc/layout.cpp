@@ -357,3 +357,34 @@ extern "C" int dg_layout_carry(const int64_t* old_blk_off, const int64_t* old_g_
     });
     return bad ? DG_ERR_INVALID : DG_OK;
 }
+
+extern "C" int dg_layout_membership(const int64_t* old_blk_off, const int64_t* old_g_off, const int32_t* old_g_copies,
+                                    int64_t n_old, int K, const int32_t* parent, int64_t n_new, uint64_t* member) {
+    if (K < 1 || K > DG_MAX_BLOCKS || n_old < 0 || n_new < 0 || !old_blk_off || !old_g_off) return DG_ERR_INVALID;
+    const int64_t oc = old_blk_off[K];
+    if (old_blk_off[0] != 0 || oc < 0 || old_g_off[n_old] != oc) return DG_ERR_INVALID;
+    for (int k = 0; k < K; k++)
+        if (old_blk_off[k + 1] < old_blk_off[k]) return DG_ERR_INVALID;
+    if (n_new > 0 && (!parent || !member)) return DG_ERR_INVALID;
+    if (oc > 0 && !old_g_copies) return DG_ERR_INVALID;
+    std::atomic<bool> bad{false};
+    const unsigned T = threads_for(n_new);
+    parallel_for(T, [&](unsigned t) {
+        for (int64_t j = chunk_lo(n_new, T, t); j < chunk_lo(n_new, T, t + 1); j++) {
+            uint64_t m = 0;
+            const int32_t p = parent[j];
+            if (p < 0 || p >= n_old || old_g_off[p] < 0 || old_g_off[p + 1] < old_g_off[p] || old_g_off[p + 1] > oc) {
+                bad = true;
+                member[j] = 0;
+                continue;
+            }
+            for (int64_t a = old_g_off[p]; a < old_g_off[p + 1]; a++) {
+                const int32_t c = old_g_copies[a];
+                if (c < 0 || c >= oc) { bad = true; break; }
+                m |= 1ull << ((std::upper_bound(old_blk_off, old_blk_off + K + 1, (int64_t)c) - old_blk_off) - 1);
+            }
+            member[j] = m;
+        }
+    });
+    return bad ? DG_ERR_INVALID : DG_OK;
+}

@@ -76,6 +76,21 @@ def membership(split: S.BlockSplit) -> np.ndarray:
     return m
 
 
+def parent_membership(old: S.BlockSplit, parent: np.ndarray) -> np.ndarray:
+    """uint64 per new Gaussian: the blocks that hold its parent (old global
+    parent[j]) in the old layout (dg_layout_membership, host C++)."""
+    from . import _lib as L
+    old_blk = np.ascontiguousarray(old.blk_off, np.int64)
+    old_goff = np.ascontiguousarray(old.g_off, np.int64)
+    old_gcp = np.ascontiguousarray(old.g_copies, np.int32)
+    par = np.ascontiguousarray(parent, np.int32)
+    out = np.empty(max(par.shape[0], 1), np.uint64)
+    L.check(L.lib().dg_layout_membership(old_blk.ctypes.data, old_goff.ctypes.data, old_gcp.ctypes.data,
+                                         old_goff.shape[0] - 1, old.K, par.ctypes.data, par.shape[0],
+                                         out.ctypes.data), "dg_layout_membership")
+    return out[:par.shape[0]]
+
+
 def carried_copies(old: S.BlockSplit, new: S.BlockSplit, src_of_new_global: np.ndarray,
                    original: np.ndarray) -> np.ndarray:
     """For every copy of the new layout, the copy of the old layout whose
@@ -121,7 +136,7 @@ def densify(tr, cfg: DensifyConfig, extent: float, step_seed: int) -> Dict:
     t1 = time.perf_counter()
     # the new layout: every Gaussian in its parent's blocks
     old = tr.split
-    member = membership(old)[src_h]
+    member = parent_membership(old, src_h)
     xy = z_tmp.data[:4 * z_tmp.ld].view(z_tmp.ld, 4)[:n_out, :2].double().cpu().numpy()
     new_split, order = native_layout(xy, member, old.cells, old.band, K=old.K)
     t2 = time.perf_counter()

@@ -100,3 +100,18 @@ def test_native_layout_extreme_memberships(DZ, n, K, pattern):
     for f in ("copy_gid", "blk_off", "blk_nshared", "g_off", "g_copies"):
         np.testing.assert_array_equal(getattr(a, f), getattr(b, f), err_msg=f)
     assert a.n_shared_globals == b.n_shared_globals == (n if pattern == "all" else 0)
+
+
+@pytest.mark.parametrize("n,K", [(3000, 5), (150000, 64)])
+def test_parent_membership_equals_the_old_membership(DZ, n, K):
+    """dg_layout_membership gives each new Gaussian its parent's blocks, as
+    the membership of the old layout indexed by the parents."""
+    rng = np.random.default_rng(10)
+    member = np.zeros((n, K), bool)
+    member[np.arange(n), rng.integers(0, K, n)] = True
+    member |= rng.random((n, K)) < 2.0 / K
+    old, _ = S.split_layout(rng.uniform(0, 10, (n, 2)), member, np.zeros((K, 4)), 1.0)
+    parent = np.concatenate([np.arange(n), rng.integers(0, n, n // 3)])
+    np.testing.assert_array_equal(DZ.parent_membership(old, parent), DZ.membership(old)[parent])
+    with pytest.raises(Exception):
+        DZ.parent_membership(old, np.array([0, n]))
