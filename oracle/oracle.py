@@ -553,10 +553,11 @@ def scene_assign(xy, boxes, s, own=None, nearest=False):
 # Under consensus the decision is taken on the global model z right after
 # a consensus, from the statistics of all copies of each Gaussian summed,
 # so every block holding a Gaussian gets the same children; the children
-# inherit the parent's sharing set.  The thresholds on sigmoid(o) and on
-# the largest scale are compared as thresholds on the raw parameters (the
-# logit and the log-scale), and the gradient rule as sum >= tau * count; the
-# decisions are taken in FP32, the precision of the GPU path.
+# inherit the parent's sharing set.  Every quantity is formed in FP64 from
+# its definition: the mean statistic sum / count, sigmoid(o) and the largest
+# scale exp(s).  Each decision reports its relative margin, the distance of
+# the compared quantity from its threshold over the threshold, so a test can
+# leave out the Gaussians whose decision another precision could flip.
 # ---------------------------------------------------------------------------
 DENSIFY_KEEP, DENSIFY_PRUNE, DENSIFY_CLONE, DENSIFY_SPLIT = 0, 1, 2, 3
 
@@ -586,31 +587,46 @@ def densify_stats(kept: np.ndarray, dmean2d: np.ndarray, view_wh: np.ndarray, co
 
 
 def densify_decide(z: np.ndarray, sh_degree: int, stat_sum, stat_cnt, g_off, g_copies,
-                   grad_threshold=2e-4, percent_dense=0.01, extent=1.0, min_opacity=0.005) -> np.ndarray:
-    """The decision per global Gaussian (DENSIFY_* codes) from the summed
-    statistics of its copies (FP32 sums in the CSR order of the copies)."""
-    f32 = np.float32
+                   grad_threshold=2e-4, percent_dense=0.01, extent=1.0, min_opacity=0.005,
+                   return_margin: bool = False):
+    """The decision per global Gaussian (DENSIFY_* codes), in FP64: prune when
+    sigmoid(o) < min_opacity; otherwise, when its copies were seen at all and
+    the mean of their summed statistic (sum / count over every copy) reaches
+    grad_threshold, split if its largest scale exp(s) exceeds
+    percent_dense * extent and clone if not; keep in every other case.
+
+    With return_margin, also the relative margin of the decision: the least,
+    over the comparisons on the path that led to the code, of
+    |quantity - threshold| / threshold (the opacity comparison always; the
+    gradient comparison unless pruned; the scale comparison when the gradient
+    rule holds)."""
     zz = split_params(z, sh_degree)
-    # thresholds on the raw parameters, formed in double from the FP32
-    # inputs and rounded once to FP32
-    m = np.float64(f32(min_opacity))
-    logit_min = f32(np.log(m / (1.0 - m)))
-    log_big = f32(np.log(np.float64(f32(percent_dense)) * np.float64(f32(extent))))
     n = z.shape[0]
     codes = np.zeros(n, np.int32)
+    margin = np.full(n, np.inf)
+    big_scale = float(percent_dense) * float(extent)
     for i in range(n):
-        ssum, scnt = f32(0.0), f32(0.0)
-        for c in g_copies[g_off[i]:g_off[i + 1]]:
-            ssum = f32(ssum + f32(stat_sum[c]))
-            scnt = f32(scnt + f32(stat_cnt[c]))
-        if f32(zz["opacity"][i]) < logit_min:
+        cps = g_copies[g_off[i]:g_off[i + 1]]
+        ssum = float(np.sum(np.asarray(stat_sum, np.float64)[cps]))
+        scnt = float(np.sum(np.asarray(stat_cnt, np.float64)[cps]))
+        opacity = 1.0 / (1.0 + np.exp(-float(zz["opacity"][i])))
+        m = abs(opacity - min_opacity) / min_opacity
+        if opacity < min_opacity:
             codes[i] = DENSIFY_PRUNE
-        elif scnt > 0 and ssum >= f32(f32(grad_threshold) * scnt):
-            big = max(f32(v) for v in zz["scale"][i]) > log_big
-            codes[i] = DENSIFY_SPLIT if big else DENSIFY_CLONE
         else:
-            codes[i] = DENSIFY_KEEP
-    return codes
+            grad_ok = False
+            if scnt > 0:
+                mean = ssum / scnt
+                m = min(m, abs(mean - grad_threshold) / grad_threshold)
+                grad_ok = mean >= grad_threshold
+            if grad_ok:
+                largest = float(np.exp(np.max(np.asarray(zz["scale"][i], np.float64))))
+                m = min(m, abs(largest - big_scale) / big_scale)
+                codes[i] = DENSIFY_SPLIT if largest > big_scale else DENSIFY_CLONE
+            else:
+                codes[i] = DENSIFY_KEEP
+        margin[i] = m
+    return (codes, margin) if return_margin else codes
 
 
 def densify_emit(z: np.ndarray, sh_degree: int, codes: np.ndarray, normals: np.ndarray):

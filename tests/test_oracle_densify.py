@@ -54,6 +54,26 @@ def test_decisions_at_their_thresholds():
                            O.DENSIFY_KEEP, O.DENSIFY_CLONE]
 
 
+def test_decision_margins_by_hand():
+    """The margin is the least relative distance from a threshold among the
+    comparisons that led to the code, each quantity formed in FP64."""
+    z = gaussians(4)
+    P = O.split_params(z, 1)
+    g_off, g_cp = one_copy_csr(4)
+    logit = lambda p: np.log(p / (1.0 - p))
+    P["opacity"][:] = [logit(0.006), logit(0.004), logit(0.5), logit(0.5)]
+    P["scale"][:] = np.log(0.001)
+    P["scale"][0, 2] = np.log(0.015)                   # largest scale 1.5x the split size
+    s = np.array([2.2e-4 * 4, 2e-4 * 4, 0.0, 2e-4 * 4 * (1 - 1e-9)])
+    c = np.array([4.0, 4.0, 0.0, 4.0])
+    codes, m = O.densify_decide(z, 1, s, c, g_off, g_cp, return_margin=True)
+    assert list(codes) == [O.DENSIFY_SPLIT, O.DENSIFY_PRUNE, O.DENSIFY_KEEP, O.DENSIFY_KEEP]
+    np.testing.assert_allclose(m[0], 0.1, rtol=1e-9)   # gradient 2.2e-4 vs 2e-4; opacity 0.2, scale 0.5
+    np.testing.assert_allclose(m[1], 0.2, rtol=1e-9)   # pruned: the opacity comparison alone
+    np.testing.assert_allclose(m[2], (0.5 - 0.005) / 0.005, rtol=1e-9)   # never seen: opacity only
+    assert m[3] < 1e-6                                 # a mean 1e-9 below its threshold: too near to test
+
+
 def test_statistics_of_all_copies_decide_together():
     z = gaussians(2)
     O.split_params(z, 1)["opacity"][:] = 0.0
