@@ -101,37 +101,42 @@ def test_transmittance_product_no_stop(oracle):
     assert v["last"][16, 16] == 4
 
 
+def brute_force_view(O, rec, rect, dk, vis, cam, tw, th, bg):
+    """One view: per pixel, gather exactly the records whose tile rectangle
+    contains the pixel's tile, order them by (float depth, record index) and
+    composite front to back.  No keys, no sort of a global list, no ranges.
+    A positive exponent (a conic that is not positive definite, or rounding)
+    is taken as 0, as the compositing rule states."""
+    img = np.zeros((3, cam.height, cam.width))
+    n = rec.shape[0]
+    for py in range(cam.height):
+        for px in range(cam.width):
+            tx, ty = px // tw, py // th
+            cand = [i for i in range(n) if vis[i] and rect[i, 0] <= tx < rect[i, 2]
+                    and rect[i, 1] <= ty < rect[i, 3]]
+            cand.sort(key=lambda i: (float(dk[i]), i))
+            T, C = 1.0, np.zeros(3)
+            for i in cand:
+                r = rec[i]
+                dx, dy = r[O.REC_MX] - (px + 0.5), r[O.REC_MY] - (py + 0.5)
+                pw = -0.5 * (r[O.REC_A] * dx * dx + r[O.REC_C] * dy * dy) - r[O.REC_B] * dx * dy
+                pw = min(pw, 0.0)
+                a = min(0.99, r[O.REC_OP] * math.exp(pw))
+                if a < 1 / 255:
+                    continue
+                if T * (1 - a) < 1e-4:
+                    break
+                C += r[O.REC_R:O.REC_R + 3] * a * T
+                T *= 1 - a
+            img[:, py, px] = C + T * np.asarray(bg)
+    return img
+
+
 def brute_force(O, x, deg, cams, rows, tw, th, bg):
-    """Per pixel: gather exactly the records whose tile rectangle contains
-    the pixel's tile, order them by (float depth, record index) and
-    composite front to back.  No keys, no sort of a global list, no ranges."""
     out = []
-    for v, (cam, (b, e)) in enumerate(zip(cams, rows)):
+    for cam, (b, e) in zip(cams, rows):
         p = O.project(x[b:e], deg, cam, tw, th)
-        rec, rect, dk, vis = p["rec"], p["rect"], p["depth_key"], p["visible"]
-        img = np.zeros((3, cam.height, cam.width))
-        for py in range(cam.height):
-            for px in range(cam.width):
-                tx, ty = px // tw, py // th
-                cand = [i for i in range(e - b) if vis[i] and rect[i, 0] <= tx < rect[i, 2]
-                        and rect[i, 1] <= ty < rect[i, 3]]
-                cand.sort(key=lambda i: (float(dk[i]), i))
-                T, C = 1.0, np.zeros(3)
-                for i in cand:
-                    r = rec[i]
-                    dx, dy = r[O.REC_MX] - (px + 0.5), r[O.REC_MY] - (py + 0.5)
-                    pw = -0.5 * (r[O.REC_A] * dx * dx + r[O.REC_C] * dy * dy) - r[O.REC_B] * dx * dy
-                    if pw > 0:
-                        continue
-                    a = min(0.99, r[O.REC_OP] * math.exp(pw))
-                    if a < 1 / 255:
-                        continue
-                    if T * (1 - a) < 1e-4:
-                        break
-                    C += r[O.REC_R:O.REC_R + 3] * a * T
-                    T *= 1 - a
-                img[:, py, px] = C + T * np.asarray(bg)
-        out.append(img)
+        out.append(brute_force_view(O, p["rec"], p["rect"], p["depth_key"], p["visible"], cam, tw, th, bg))
     return out
 
 
@@ -150,6 +155,38 @@ def test_tiled_equals_per_pixel_brute_force(oracle):
         want = brute_force(O, x, 0, cams, rows, tw, th, bg)
         for v in range(2):
             np.testing.assert_allclose(f["views"][v]["image"], want[v], atol=1e-12)
+
+
+def test_positive_exponent_is_clamped_not_skipped(oracle):
+    """A record whose conic is indefinite (b^2 > a c) has a positive exponent
+    at pixels along its negative diagonal: those pairs composite with
+    alpha = min(0.99, o), not skipped.  Its mean sits exactly on a pixel
+    centre.  The tiled oracle and the brute force agree, and the pixel one
+    step down the diagonal shows the clamped alpha."""
+    O = oracle
+    cam = S.cube_camera(24, 20, f=30.0)
+    g = S.cube_scene(12, 5, log_scale_mu=-2.3)
+    plan = O.ViewPlan([cam], [(0, 12)], 8, 8)
+    x = O.params_from(g)
+    proj = O.project_views(x, 0, plan)
+    vis = np.nonzero(proj["rec"][:, O.REC_VIS] == 1)[0]
+    i = int(vis[0])
+    r = proj["rec"][i]
+    r[O.REC_MX], r[O.REC_MY] = 10.5, 9.5                # the centre of pixel (10, 9)
+    r[O.REC_A], r[O.REC_B], r[O.REC_C] = 0.5, 1.0, 0.5  # indefinite
+    r[O.REC_OP] = 0.6
+    r[O.REC_R:O.REC_R + 3] = (0.9, 0.4, 0.2)
+    proj["depth_key"][i] = np.float32(1e-3)             # in front of every other record
+    proj["rect"][i] = (0, 0, 3, 3)                      # every tile of the view
+    b = O.bin_sort(proj, plan, cull=False)
+    f = O.rasterize_fwd(proj, b, plan)[0]
+    want = brute_force_view(O, proj["rec"], proj["rect"], proj["depth_key"], proj["rec"][:, O.REC_VIS] == 1,
+                            cam, 8, 8, (0.0, 0.0, 0.0))
+    np.testing.assert_allclose(f["image"], want, atol=1e-12)
+    # pixel (11, 8): dx = -1, dy = 1, exponent -0.5 (0.5 + 0.5) + 1 = 0.5 > 0 -> alpha = 0.6 in front
+    front = 0.6 * np.array([0.9, 0.4, 0.2])
+    assert np.all(f["image"][:, 8, 11] >= front - 1e-12)
+    assert f["T_final"][8, 11] <= 0.4 + 1e-12
 
 
 def test_keys_values_ranges_properties(oracle):
