@@ -22,6 +22,7 @@ import pytest
 import torch
 
 from paper_2405_13943_b300 import synth as S
+from tests._util import report
 
 pytestmark = pytest.mark.gpu
 
@@ -115,13 +116,17 @@ def test_full_size_forward_matches_oracle(full):
         # lists may differ only by records whose projection decisions (tile
         # rectangle, culling bounds) sit within THR of a threshold
         assert np.all(f["proj"]["margin"][odd] < THR), odd[f["proj"]["margin"][odd] >= THR][:10]
-        assert bad.mean() < 0.02, bad.mean()
         H, W = cam.height, cam.width
         badpix = tile_pixels(vb, bad, H, W)
         m = (ov["margin"] >= THR) & ~badpix
-        assert m.mean() > 0.95, m.mean()
         img = vb.view_image(v).cpu().numpy()
         err = np.abs(img - ov["image"]).max(0)
+        flipped = int((err > 1e-4).sum())
+        report("full_size_forward", view=v, tile=list(tile), tiles=int(bad.size), tiles_differing=int(bad.sum()),
+               pixels=int(m.size), kept=int(m.sum()), flipped=flipped)
+        assert bad.mean() < 2e-3, bad.mean()
+        assert m.mean() > 0.995, m.mean()
+        assert flipped <= 1e-4 * m.size, flipped        # decisions taken the other way: < 0.01 % of pixels
         assert err[m].max() <= 1e-4, (v, err[m].max())
         Tf = vb.view_pixels(v, vb.T_final).cpu().numpy()
         assert np.abs(Tf - ov["T_final"])[m].max() <= 1e-4

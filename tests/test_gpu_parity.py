@@ -9,14 +9,21 @@ import pytest
 import torch
 
 from paper_2405_13943_b300 import synth as S
-from tests._util import curate_gaussians, pixel_mask
+from tests._util import curate_gaussians, pixel_mask, report
 
 pytestmark = pytest.mark.gpu
 
 IMG_TOL = 1e-4
 REL_L2 = 1e-3
 FLIP_TOL = 2e-2          # one flipped decision moves a pixel by at most ~alpha T |c|
-EXCLUDE_FRAC = 5e-3
+# Pixels whose value decisions lie within relative 1e-4 of a threshold are
+# left out of the 1e-4 comparison.  A Gaussian of screen std s puts about
+# 2 pi s^2 eps pixels within eps of its 1/255 cut, ~0.1 % of the pixels of
+# these scenes at eps = 1e-4; the budget sits just above that.
+EXCLUDE_FRAC = 2e-3
+# Pixels where the two sides actually differ beyond 1e-4 (a decision taken
+# the other way): at most 0.01 % of the pixels, and only where excluded.
+FLIP_FRAC = 1e-4
 GROUPS = ("means", "quats", "log_scales", "sh", "opacity_logits")
 
 
@@ -92,12 +99,13 @@ def check_forward(D, O, vb, f, masks, plan):
     np.testing.assert_array_equal(vb.vals.cpu().numpy()[:M].view(np.uint32), f["bins"]["vals"])
     np.testing.assert_array_equal(vb.ranges.cpu().numpy()[:2 * plan.n_tiles].view(np.uint32),
                                   f["bins"]["ranges"].reshape(-1))
-    excluded = 0
+    excluded = flipped = 0
     for v, ov in enumerate(f["views"]):
         img = vb.view_image(v).cpu().numpy()
         m = masks[v]
         excluded += int((~m).sum())
         err = np.abs(img - ov["image"]).max(0)
+        flipped += int((err > IMG_TOL).sum())
         assert err[m].max(initial=0.0) <= IMG_TOL, (v, err[m].max())
         # excluded pixels: at most one flipped 1/255-skip or T-stop decision
         assert err[~m].max(initial=0.0) <= FLIP_TOL, (v, err[~m].max())
@@ -106,9 +114,9 @@ def check_forward(D, O, vb, f, masks, plan):
         last = vb.view_pixels(v, vb.last).cpu().numpy().view(np.uint32)
         np.testing.assert_array_equal(last[m], ov["last"][m])
     total = sum(c.width * c.height for c in plan.cams)
-    # a Gaussian of screen std s puts about 2 pi s^2 eps pixels within relative
-    # eps of the 1/255 cut; with eps = 1e-4 that is ~0.1 % of pixels here
+    report("forward", pixels=total, excluded=excluded, flipped=flipped)
     assert excluded <= max(2, EXCLUDE_FRAC * total), excluded
+    assert flipped <= max(1, FLIP_FRAC * total), flipped
 
 
 def check_backward(D, O, g, grads, ob, deg):
