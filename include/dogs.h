@@ -172,8 +172,10 @@ int dg_bin_sort(const float* rec, const uint32_t* rect, const dg_camera* dev_cam
  * loop that must not pay cudaMalloc's implicit synchronisation.  Same inputs,
  * outputs and results as dg_bin_sort, but the scratch comes from a static
  * device array of 40 MiB that the library reserves on every GPU that loads it,
- * for the life of the process.  Limits: plan->n_tiles <= DG_NOALLOC_MAX_TILES
- * and capacity <= DG_NOALLOC_MAX_INSTANCES, else DG_ERR_TOO_LARGE before any
+ * for the life of the process.  Its arguments are checked as dg_bin_sort's are
+ * (plan, capacity, null and misaligned pointers: DG_ERR_INVALID before any
+ * launch).  Limits: plan->n_tiles <= DG_NOALLOC_MAX_TILES and
+ * capacity <= DG_NOALLOC_MAX_INSTANCES, else DG_ERR_TOO_LARGE before any
  * launch.  The first call on a device looks up the array's device address
  * (once per device, with that device current); make that first call before
  * any stream capture.  Every call shares the array: calls whose work overlaps

@@ -82,7 +82,7 @@ static bool valid_plan(const dg_plan* p)
 }
 
 // per-device one-time function attributes
-static int ensure_init()
+int ensure_init()
 {
     static std::atomic<uint64_t> done_mask{0};
     int dev = 0;
@@ -93,6 +93,22 @@ static int ensure_init()
     if (rc == DG_OK) rc = loss_init();
     if (rc == DG_OK) done_mask.fetch_or(bit);
     return rc;
+}
+
+// The host-side argument checks of the binning entry points (every one
+// before any launch): the plan, the capacity (instance numbers are 32-bit),
+// the buffers a non-empty plan needs, and the alignment of every buffer the
+// kernels read as vectors.
+int bin_sort_args(const float* rec, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                  int64_t capacity, const uint64_t* keys, const uint32_t* vals, const uint32_t* ranges,
+                  const uint32_t* dev_count, const uint32_t* dev_status)
+{
+    if (!valid_plan(plan) || capacity < 0 || capacity >= (int64_t)0xFFFFFFFFll) return DG_ERR_INVALID;
+    if (plan->n_tiles == 0) return DG_OK;
+    if (!dev_cams || !ranges || !dev_count || !dev_status || !vals) return DG_ERR_INVALID;
+    if (plan->n_rec > 0 && (!rec || !rect)) return DG_ERR_INVALID;
+    if (!aligned16(rec) || !aligned8(rect) || !aligned8(dev_cams) || !aligned8(keys)) return DG_ERR_INVALID;
+    return DG_OK;
 }
 
 }  // namespace dg
@@ -188,14 +204,11 @@ int dg_bin_sort(const float* rec, const uint32_t* rect, const dg_camera* dev_cam
                 int64_t capacity, uint64_t* keys, uint32_t* vals, uint32_t* ranges, uint32_t* dev_count, void* ws,
                 size_t ws_bytes, uint32_t* dev_status, void* stream)
 {
-    if (!valid_plan(plan) || capacity < 0 || capacity >= (int64_t)0xFFFFFFFFll) return DG_ERR_INVALID;
-    if (plan->n_tiles == 0) return DG_OK;
-    if (!dev_cams || !ranges || !dev_count || !dev_status || !ws || !vals) return DG_ERR_INVALID;
-    if (plan->n_rec > 0 && (!rec || !rect)) return DG_ERR_INVALID;
-    if (!aligned16(rec) || !aligned8(rect) || !aligned8(dev_cams) || !aligned8(keys) || ((uintptr_t)ws & 255u))
-        return DG_ERR_INVALID;
+    int rc = bin_sort_args(rec, rect, dev_cams, plan, capacity, keys, vals, ranges, dev_count, dev_status);
+    if (rc != DG_OK || plan->n_tiles == 0) return rc;
+    if (!ws || ((uintptr_t)ws & 255u)) return DG_ERR_INVALID;
     if (ws_bytes < bin_sort_ws_bytes(plan->n_tiles, capacity)) return DG_ERR_WORKSPACE;
-    int rc = ensure_init();
+    rc = ensure_init();
     if (rc != DG_OK) return rc;
     return launch_bin_sort((const float4*)rec, (const uint2*)rect, dev_cams, *plan, capacity, keys, vals, ranges,
                            dev_count, ws, dev_status, (cudaStream_t)stream);

@@ -23,7 +23,10 @@ namespace dg {
 size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity);
 int launch_bin_sort(const float4*, const uint2*, const dg_camera*, const dg_plan&, int64_t, uint64_t*, uint32_t*,
                     uint32_t*, uint32_t*, void*, uint32_t*, cudaStream_t);
-int bin_sort_init();
+int ensure_init();
+int bin_sort_args(const float* rec, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                  int64_t capacity, const uint64_t* keys, const uint32_t* vals, const uint32_t* ranges,
+                  const uint32_t* dev_count, const uint32_t* dev_status);
 
 // Sized for DG_NOALLOC_MAX_TILES tiles and DG_NOALLOC_MAX_INSTANCES instances
 // (the pairs take 8 bytes each; the per-tile arrays 16 bytes per tile).
@@ -58,19 +61,15 @@ extern "C" int dg_bin_sort_noalloc(const float* rec, const uint32_t* rect, const
                                    uint32_t* ranges, uint32_t* dev_count, uint32_t* dev_status, void* stream)
 {
     using namespace dg;
-    if (!plan || capacity < 0) return DG_ERR_INVALID;
+    // the same host-side checks as dg_bin_sort, then the fixed limits
+    int rc = bin_sort_args(rec, rect, dev_cams, plan, capacity, keys, vals, ranges, dev_count, dev_status);
+    if (rc != DG_OK || plan->n_tiles == 0) return rc;
     if (plan->n_tiles > DG_NOALLOC_MAX_TILES || capacity > DG_NOALLOC_MAX_INSTANCES) return DG_ERR_TOO_LARGE;
     if (bin_sort_ws_bytes(plan->n_tiles, capacity) > kNoallocScratchBytes) return DG_ERR_TOO_LARGE;
-    if (plan->n_views < 0 || plan->n_views > DG_MAX_VIEWS || plan->n_blocks < 1 || plan->n_blocks > DG_MAX_BLOCKS ||
-        plan->n_rec < 0 || plan->n_tiles < 0)
-        return DG_ERR_INVALID;
-    if (plan->n_tiles == 0) return DG_OK;
-    if (!dev_cams || !ranges || !dev_count || !dev_status || !vals) return DG_ERR_INVALID;
-    if (plan->n_rec > 0 && (!rec || !rect)) return DG_ERR_INVALID;
     void* ws = nullptr;
-    int rc = scratch_address(&ws);
+    rc = scratch_address(&ws);
     if (rc != DG_OK) return rc;
-    rc = bin_sort_init();
+    rc = ensure_init();
     if (rc != DG_OK) return rc;
     return launch_bin_sort((const float4*)rec, (const uint2*)rect, dev_cams, *plan, capacity, keys, vals, ranges,
                            dev_count, ws, dev_status, (cudaStream_t)stream);
