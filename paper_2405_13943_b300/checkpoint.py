@@ -199,17 +199,32 @@ def load(tr, path: str) -> Dict:
         raise CheckpointError("adaptive penalty on in one of checkpoint and trainer only")
     if ("dstats" in arrays) != (getattr(tr, "dstats", None) is not None):
         raise CheckpointError("densification on in one of checkpoint and trainer only")
-    if new_split is not None:
-        # every buffer is verified below against the stored sizes; the layout is installed first
-        dev = tr.z.data.device
-        shapes = {e["name"]: e for e in header["buffers"]}
-        fresh = {n: D.GaussianBuffer(shapes[n]["n"], shapes[n]["deg"], dev, shapes[n]["ld"]) for n in BUFFERS}
-        tr.install_split(new_split, fresh["z"], fresh["x"], fresh["m"], fresh["v"], fresh["u"], calibrate=False)
+    # the shape each buffer must have: the trainer's own, or for a stored
+    # layout the one that layout implies (globals for z, copies for the rest)
+    if new_split is None:
+        want_shape = {n: (getattr(tr, n).n, getattr(tr, n).ld, getattr(tr, n).deg, getattr(tr, n).data.numel() * 4)
+                      for n in BUFFERS}
+        n_copies = tr.split.n_copies
+    else:
+        deg = tr.z.deg
+        n_glob = len(new_split.g_off) - 1
+        n_copies = new_split.n_copies
+        want_shape = {}
+        for e in header["buffers"]:
+            n = n_glob if e["name"] == "z" else n_copies
+            ld = int(e["ld"])
+            if ld < n or ld % 4:
+                raise CheckpointError(f"buffer {e['name']}: leading dimension {ld} does not fit {n}")
+            want_shape[e["name"]] = (n, ld, deg, ld * (12 + 3 * (deg + 1) ** 2) * 4)
+    if sorted(e["name"] for e in header["buffers"]) != sorted(BUFFERS):
+        raise CheckpointError("checkpoint does not hold every parameter buffer")
+    if "dstats" in arrays and arrays["dstats"].size != 2 * max(n_copies, 1):
+        raise CheckpointError("densification statistics: size differs from the layout's")
+    # every buffer read and verified on the host before anything of the trainer changes
     host: Dict[str, np.ndarray] = {}
     with open(path, "rb") as f:
         for e in header["buffers"]:
-            b = getattr(tr, e["name"])
-            if (e["n"], e["ld"], e["deg"], e["nbytes"]) != (b.n, b.ld, b.deg, b.data.numel() * 4):
+            if (e["n"], e["ld"], e["deg"], e["nbytes"]) != want_shape[e["name"]]:
                 raise CheckpointError(f"buffer {e['name']}: shape differs from the trainer's")
             at = header["data_start"] + e["offset"]
             if at + e["nbytes"] > size:
@@ -219,11 +234,13 @@ def load(tr, path: str) -> Dict:
             if f"{zlib.crc32(raw):08x}" != e["crc32"]:
                 raise CheckpointError(f"buffer {e['name']}: CRC mismatch")
             host[e["name"]] = np.frombuffer(raw, np.float32)
+    if new_split is not None:
+        dev = tr.z.data.device
+        fresh = {e["name"]: D.GaussianBuffer(e["n"], e["deg"], dev, e["ld"]) for e in header["buffers"]}
+        tr.install_split(new_split, fresh["z"], fresh["x"], fresh["m"], fresh["v"], fresh["u"], calibrate=False)
     for name, a in host.items():
         getattr(tr, name).data.copy_(torch.from_numpy(a.copy()))
     if "dstats" in arrays and getattr(tr, "dstats", None) is not None:
-        if arrays["dstats"].size != tr.dstats.numel():
-            raise CheckpointError("densification statistics: size differs from the trainer's")
         tr.dstats.copy_(torch.from_numpy(arrays["dstats"]))
     tr.t = int(header["t"])
     tr.rho = [float(r) for r in header["rho"]]

@@ -290,6 +290,11 @@ extern "C" int dg_layout(const double* xy, const uint64_t* member, int64_t n, in
     const uint64_t valid = K == 64 ? ~0ull : ((1ull << K) - 1);
     for (int64_t i = 0; i < n; i++)
         if (member[i] == 0 || (member[i] & ~valid)) return DG_ERR_INVALID;   // every point in some block
+    // copy numbers are int32 throughout the layout
+    if (n > 0 && dg_layout_copies(member, n) >= ((int64_t)1 << 31)) return DG_ERR_INVALID;
+    // the Z-order key converts the ground position to an integer
+    for (int64_t i = 0; i < 2 * n; i++)
+        if (!std::isfinite(xy[i])) return DG_ERR_INVALID;
     try {
         layout_impl(xy, member, n, K, order, copy_gid, blk_off, blk_nshared, g_off, g_copies, n_shared);
     } catch (const std::bad_alloc&) {

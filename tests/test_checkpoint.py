@@ -175,3 +175,34 @@ def test_densified_layout_is_stored_and_installed(tmp_path):
     c.split_origin = "another run"
     with pytest.raises(CK.CheckpointError, match="split"):
         CK.load(c, p)
+
+
+def test_damaged_densified_checkpoint_leaves_the_trainer_untouched(tmp_path):
+    """A densified checkpoint with one damaged buffer is refused before the
+    stored layout is installed: the trainer keeps its layout and state."""
+    a = DensifiedRun(31, layout_seed=7)
+    p = str(tmp_path / "bad.ckpt")
+    CK.save(a, p)
+    hdr = CK.read_header(p)
+    e = [b for b in hdr["buffers"] if b["name"] == "v"][0]
+    with open(p, "r+b") as f:                         # flip one byte of the last buffer
+        f.seek(hdr["data_start"] + e["offset"] + 100)
+        byte = f.read(1)
+        f.seek(hdr["data_start"] + e["offset"] + 100)
+        f.write(bytes([byte[0] ^ 0x40]))
+    b = DensifiedRun(32, layout_seed=1)
+    split0, z0 = b.split, b.z.data.clone()
+    with pytest.raises(CK.CheckpointError, match="CRC"):
+        CK.load(b, p)
+    assert b.installs == 0 and b.split is split0 and torch.equal(b.z.data, z0)
+
+
+def test_densified_checkpoint_with_wrong_statistics_size_is_refused(tmp_path):
+    a = DensifiedRun(33, layout_seed=7)
+    a.dstats = torch.zeros(2 * a.split.n_copies + 2, dtype=torch.float32)
+    p = str(tmp_path / "st.ckpt")
+    CK.save(a, p)
+    b = DensifiedRun(34, layout_seed=1)
+    with pytest.raises(CK.CheckpointError, match="statistics"):
+        CK.load(b, p)
+    assert b.installs == 0

@@ -115,3 +115,30 @@ def test_parent_membership_equals_the_old_membership(DZ, n, K):
     np.testing.assert_array_equal(DZ.parent_membership(old, parent), DZ.membership(old)[parent])
     with pytest.raises(Exception):
         DZ.parent_membership(old, np.array([0, n]))
+
+
+def test_native_layout_rejects_non_finite_positions(DZ):
+    member = np.ones((4, 2), bool)
+    for bad in (np.nan, np.inf, -np.inf):
+        xy = np.zeros((4, 2))
+        xy[2, 1] = bad
+        with pytest.raises(Exception):
+            DZ.native_layout(xy, member, np.zeros((2, 4)), 1.0)
+
+
+def test_layout_rejects_copy_counts_beyond_int32(DZ):
+    """2^25 points each held by all 64 blocks make 2^31 copies, more than the
+    layout's 32-bit copy numbers hold: refused before any output is written
+    (the outputs here are one element long; a write would overrun them)."""
+    import ctypes as C
+    from paper_2405_13943_b300 import _lib as L
+    n, K = 1 << 25, 64
+    member = np.full(n, np.uint64(0xFFFFFFFFFFFFFFFF))
+    xy = np.zeros((n, 2))
+    one32, one64 = np.zeros(1, np.int32), np.zeros(K + 1, np.int64)
+    ns = np.zeros(1, np.int64)
+    rc = L.lib().dg_layout(xy.ctypes.data, member.ctypes.data, n, K, one32.ctypes.data, one32.ctypes.data,
+                           one64.ctypes.data, one64.ctypes.data, one64.ctypes.data, one32.ctypes.data,
+                           ns.ctypes.data)
+    assert rc == L.DG_ERR_INVALID
+    assert L.lib().dg_layout_copies(member.ctypes.data, n) == 1 << 31
