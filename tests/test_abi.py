@@ -141,3 +141,31 @@ def test_xstep_part_rejects_bad_arguments_before_launch(lib):
     assert call(0, 0, z, gid, sh=None) == L.DG_ERR_INVALID    # ... and the shared flags
     assert call(0, 0, z1, gid) == L.DG_ERR_INVALID            # ... and the same SH degree
     assert call(0, 0, z, gid + 2) == L.DG_ERR_INVALID         # misaligned ids
+
+
+def test_render_slot_workspace_bounds_every_admissible_batch(lib):
+    """The render server sizes a slot's workspace once, on the host, for any
+    batch of at most max_batch views and max_batch_pixels pixels: random mixes
+    of the served resolutions never need more (host-only queries, no GPU)."""
+    from paper_2405_13943_b300 import dogs as D
+    from paper_2405_13943_b300 import serve
+
+    class Z:
+        n = 6_000_000
+    res = [(640, 480), (1280, 720), (1920, 1080), (3840, 2160)]
+    server = serve.RenderServer(Z(), max_batch=8, resolutions=res, inst_per_pixel=2.5)
+    bound = server._slot_ws_bytes()
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        k = int(rng.integers(1, 9))
+        pick = [res[i] for i in rng.integers(0, 4, k)]
+        cams, npix = [], 0
+        for w, h in pick:
+            if cams and npix + w * h > server.max_batch_pixels:
+                break
+            cams.append(S.Camera(w, h, float(w), float(w), w / 2, h / 2, np.eye(3, dtype=np.float32),
+                                 np.zeros(3, np.float32), np.zeros(3, np.float32)))
+            npix += w * h
+        _, plan = D.render_plan(cams, Z.n)
+        need = lib.dg_render_workspace_size(C.byref(plan), server._capacity_for(npix))
+        assert 0 < need <= bound
