@@ -36,6 +36,22 @@
 
 #define OC_PI 3.14159265358979323846
 
+/* Host threads for the per-Gaussian and per-pixel loops (OpenMP when built  */
+/* with it).  The default is one: results are then bit-for-bit reproducible; */
+/* with more threads only the order of the FP64 additions into a record's    */
+/* gradient changes.  The CPU baseline of the benchmark times both.           */
+static int g_threads = 1;
+void oc_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+int oc_get_threads(void) { return g_threads; }
+int oc_have_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 typedef struct {
     int32_t width, height;
     double fx, fy, cx, cy;
@@ -323,6 +339,7 @@ int oc_project(int n, int sh_degree, const double* params, const oc_cam* cam,
                double* margin)
 {
     int K = (sh_degree + 1) * (sh_degree + 1), P = 11 + 3 * K, vis = 0;
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1024) reduction(+ : vis)
     for (int i = 0; i < n; i++)
         vis += project_one(params + (int64_t)i * P, K, cam, tile_w, tile_h, rec + (int64_t)i * REC_N,
                            rect + 4 * (int64_t)i, depth_key + i, margin + i, NULL);
@@ -482,6 +499,7 @@ void oc_rasterize_fwd(int width, int height, int tile_w, int tile_h, int64_t til
                       double* margin, double* margin_grad)
 {
     int TX = (width + tile_w - 1) / tile_w;
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 4)
     for (int py = 0; py < height; py++)
         for (int px = 0; px < width; px++) {
             int64_t tile = tile_off + (int64_t)(py / tile_h) * TX + px / tile_w;
@@ -503,8 +521,11 @@ void oc_rasterize_bwd(int width, int height, int tile_w, int tile_h, int64_t til
     int64_t maxlen = 0;
     for (int64_t t = tile_off; t < tile_off + (int64_t)TX * ((height + tile_h - 1) / tile_h); t++)
         if (ranges[2 * t + 1] - ranges[2 * t] > maxlen) maxlen = ranges[2 * t + 1] - ranges[2 * t];
+#pragma omp parallel num_threads(g_threads)
+    {
     pair_t* pairs = (pair_t*)malloc(sizeof(pair_t) * (maxlen > 0 ? maxlen : 1));
     double* S = (double*)malloc(sizeof(double) * 3 * (maxlen + 1));
+#pragma omp for schedule(dynamic, 4)
     for (int py = 0; py < height; py++)
         for (int px = 0; px < width; px++) {
             int64_t tile = tile_off + (int64_t)(py / tile_h) * TX + px / tile_w;
@@ -525,23 +546,31 @@ void oc_rasterize_bwd(int width, int height, int tile_w, int tile_h, int64_t til
                 const pair_t* pr = &pairs[i];
                 const double* g = rec + (int64_t)pr->rec * REC_N;
                 double* dg = drec + (int64_t)pr->rec * 9;
-                double dalpha = 0.0;
+                double dalpha = 0.0, d[9];
                 for (int ch = 0; ch < 3; ch++) {
-                    dg[6 + ch] += gpix[ch] * pr->alpha * pr->T;
+                    d[6 + ch] = gpix[ch] * pr->alpha * pr->T;
                     dalpha += gpix[ch] * (g[REC_R + ch] * pr->T - S[3 * i + ch] / (1.0 - pr->alpha));
                 }
-                if (pr->alpha_raw >= ALPHA_MAX) continue;       /* clamp active: no gradient */
-                dg[5] += dalpha * pr->G;
-                double dpower = dalpha * g[REC_OP] * pr->G;
-                double dx = pr->dx, dy = pr->dy;
-                dg[0] += dpower * (-(g[REC_A] * dx + g[REC_B] * dy));
-                dg[1] += dpower * (-(g[REC_C] * dy + g[REC_B] * dx));
-                dg[2] += dpower * (-0.5 * dx * dx);
-                dg[3] += dpower * (-dx * dy);
-                dg[4] += dpower * (-0.5 * dy * dy);
+                int nd = 6;
+                if (pr->alpha_raw < ALPHA_MAX) {                /* clamp active: no gradient */
+                    d[5] = dalpha * pr->G;
+                    double dpower = dalpha * g[REC_OP] * pr->G;
+                    double dx = pr->dx, dy = pr->dy;
+                    d[0] = dpower * (-(g[REC_A] * dx + g[REC_B] * dy));
+                    d[1] = dpower * (-(g[REC_C] * dy + g[REC_B] * dx));
+                    d[2] = dpower * (-0.5 * dx * dx);
+                    d[3] = dpower * (-dx * dy);
+                    d[4] = dpower * (-0.5 * dy * dy);
+                    nd = 0;
+                }
+                for (int j = nd; j < 9; j++) {
+#pragma omp atomic
+                    dg[j] += d[j];
+                }
             }
         }
     free(pairs); free(S);
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -630,6 +659,7 @@ void oc_project_bwd(int n, int sh_degree, const double* params, const oc_cam* ca
                     int tile_w, int tile_h, const double* drec, double* dparams)
 {
     int K = (sh_degree + 1) * (sh_degree + 1), P = 11 + 3 * K;
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1024)
     for (int i = 0; i < n; i++)
         project_bwd_one(params + (int64_t)i * P, K, cam, tile_w, tile_h, drec + (int64_t)i * 9,
                         dparams + (int64_t)i * P);

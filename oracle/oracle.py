@@ -31,7 +31,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (IEEE FP64, no contraction, no fast-math)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", _LIB, _SRC, "-lm"])
+                               "-fno-fast-math", "-fopenmp", "-o", _LIB, _SRC, "-lm"])
     return _LIB
 
 
@@ -78,9 +78,21 @@ def lib():
         _lib.oc_adam_admm_step.restype = None
         _lib.oc_adam_admm_step.argtypes = [C.c_int64, C.c_int, dp, dp, dp, dp, dp, dp, ip, u8p, dp, dp,
                                            C.c_double, C.c_double, C.c_double, C.c_int]
+        _lib.oc_set_threads.restype = None
+        _lib.oc_set_threads.argtypes = [C.c_int]
+        _lib.oc_get_threads.restype = C.c_int
+        _lib.oc_have_openmp.restype = C.c_int
         _lib.oc_consensus.restype = None
         _lib.oc_consensus.argtypes = [C.c_int64, C.c_int, i64p, ip, dp, dp, dp, C.c_double, dp, dp]
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the per-Gaussian and per-pixel loops (1 by default,
+    which keeps every result bit-for-bit reproducible).  Returns the count in
+    effect: 1 when the library was built without OpenMP."""
+    lib().oc_set_threads(int(n) if lib().oc_have_openmp() else 1)
+    return int(lib().oc_get_threads())
 
 
 def _p(a: np.ndarray, ct):

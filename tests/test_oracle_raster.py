@@ -339,3 +339,28 @@ def test_culling_changes_no_image_or_gradient(oracle):
     W = [np.random.default_rng(3 + v).uniform(-1, 1, (3, c.height, c.width)) for v, c in enumerate(cams)]
     bc, bu = O.backward(x, 1, plan, fc, W, bg), O.backward(x, 1, plan, fu, W, bg)
     np.testing.assert_allclose(bc["dparams"], bu["dparams"], rtol=1e-12, atol=1e-15)
+
+
+def test_threaded_oracle_equals_one_thread(oracle):
+    """The oracle's host threads split pixels and Gaussians only: images, T,
+    last and the record gradients agree with the one-thread run (the
+    gradients up to the order of their FP64 sums)."""
+    O = oracle
+    g = S.cube_scene(400, 31, sh_degree=2, log_scale_mu=-2.4)
+    cams = [S.cube_camera(64, 48, f=60.0), S.cube_camera(40, 56, f=40.0)]
+    plan = O.ViewPlan(cams, [(0, 400), (100, 400)], 16, 16)
+    x = O.params_from(g)
+    W = [np.random.default_rng(2 + v).uniform(-1, 1, (3, c.height, c.width)) for v, c in enumerate(cams)]
+    try:
+        O.set_threads(1)
+        f1 = O.render(x, 2, plan)
+        b1 = O.backward(x, 2, plan, f1, W)
+        assert O.set_threads(4) in (1, 4)
+        f4 = O.render(x, 2, plan)
+        b4 = O.backward(x, 2, plan, f4, W)
+    finally:
+        O.set_threads(1)
+    for v in range(2):
+        for k in ("image", "T_final", "last"):
+            np.testing.assert_array_equal(f1["views"][v][k], f4["views"][v][k])
+    np.testing.assert_allclose(b4["dparams"], b1["dparams"], rtol=1e-12, atol=1e-15)
