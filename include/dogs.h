@@ -490,6 +490,15 @@ const char* dg_version(void);
 /* number of kernel launches this library has enqueued since load (monotone) */
 uint64_t dg_launch_count(void);
 
+/* ---- measurement helper (not part of the method) -------------------------- */
+/* dg_probe_fma: launches blocks x 256 threads, each running 8 independent
+ * chains of iters x 16 FP32 fused multiply-adds, and writes one float per
+ * thread to out (device, blocks x 256 floats, caller-owned).  Returns the
+ * FLOPs the launch performs (2 per multiply-add), or -1 on a bad argument or
+ * launch error.  Timing the launch on `stream` gives the device's FP32 rate,
+ * the denominator of the compositing kernels' roofline. */
+int64_t dg_probe_fma(int iters, int blocks, float* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,7 @@ _vp = C.c_void_p
 _SIGS = {
     "dg_version": (C.c_char_p, []),
     "dg_launch_count": (C.c_uint64, []),
+    "dg_probe_fma": (C.c_int64, [C.c_int, C.c_int, _vp, _vp]),
     "dg_gaussian_floats": (C.c_int64, [C.c_int64, C.c_int]),
     "dg_plan_views": (C.c_int, [C.POINTER(DgCamera), C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_int, C.c_int,
                                 C.POINTER(DgPlan)]),
