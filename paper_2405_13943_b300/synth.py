@@ -451,6 +451,33 @@ def block_views(split: BlockSplit, seed: int, per_block: int, width: int, height
     return cams
 
 
+def street_views(split: BlockSplit, seed: int, per_block: int, width: int, height: int, lot: float = 20.0,
+                 eye: float = 1.7, pitch_deg: tuple = (0.0, 10.0), hfov_deg: float = 90.0,
+                 jitter: float = 0.2) -> List[Camera]:
+    """`per_block` street-level views per block: the camera stands at eye
+    height on a street of the city law (the gaps between building lots run
+    along the lot borders, x or y a multiple of `lot`) inside the block's
+    cell, looks along the street in one of its two directions, pitched down
+    by U(pitch_deg); views are returned grouped by block."""
+    rng = _rng(seed)
+    f = focal_for_hfov(width, hfov_deg)
+    cams = []
+    for k in range(split.K):
+        x0, x1, y0, y1 = split.cells[k]
+        for _ in range(per_block):
+            tx = x0 + (x1 - x0) * rng.uniform(jitter, 1 - jitter)
+            ty = y0 + (y1 - y0) * rng.uniform(jitter, 1 - jitter)
+            if rng.uniform() < 0.5:             # a street along y, at a lot border in x
+                pos = (round(tx / lot) * lot, ty, eye)
+                yaw = math.pi / 2 if rng.uniform() < 0.5 else -math.pi / 2
+            else:                                # a street along x
+                pos = (tx, round(ty / lot) * lot, eye)
+                yaw = 0.0 if rng.uniform() < 0.5 else math.pi
+            p = math.radians(rng.uniform(*pitch_deg))
+            cams.append(look_camera(pos, yaw, p, width, height, f, near=0.5, block=k))
+    return cams
+
+
 def random_pose_cameras(seed: int, n: int, resolutions: Sequence[tuple],
                         probs: Sequence[float], size: float = 1000.0,
                         alt: tuple = (50.0, 150.0), pitch_deg: tuple = (30.0, 90.0),
@@ -503,24 +530,40 @@ class DogsWorkload:
 def dogs_workload(n_global: int, cols: int, rows: int, shared_frac: float, seed: int,
                   views_per_step: int = 1, pool: int = 4, width: int = 1920, height: int = 1080,
                   pitch_deg: float = 45.0, altitude: float = 120.0, sh_degree: int = 3,
-                  loads: Optional[Sequence[float]] = None) -> DogsWorkload:
+                  loads: Optional[Sequence[float]] = None, cameras: str = "aerial",
+                  log_scale_mu: float = -1.0) -> DogsWorkload:
     """City-law scene of n_global Gaussians split on a cols x rows ground
     grid at load quantiles (Dirichlet(2) from the seed unless given), with
     shared_frac of the Gaussians on interior borders shared by 2-4 blocks;
-    `pool` steps' worth of aerial views, views_per_step per block each."""
+    `pool` steps' worth of views, views_per_step per block each:
+      cameras="aerial"  block_views at pitch_deg and altitude;
+      cameras="grid"    (one block) views drawn from a 10 x 10 grid of
+                        cameras at `altitude`, pitch U(45, 90) deg;
+      cameras="street"  street_views at eye height along the streets."""
     K = cols * rows
-    z = city_scene(n_global, seed, sh_degree=sh_degree)
+    z = city_scene(n_global, seed, sh_degree=sh_degree, log_scale_mu=log_scale_mu)
     if loads is None:
         loads = dirichlet_loads(seed + 3, K)
     split, order = block_split(z.means[:, :2], cols, rows, loads, shared_frac)
     z = z.subset(order)
-    allv = block_views(split, seed + 2, views_per_step * pool, width, height, pitch_deg, altitude)
     per = views_per_step * pool
+    if cameras == "aerial":
+        allv = block_views(split, seed + 2, per, width, height, pitch_deg, altitude)
+    elif cameras == "street":
+        allv = street_views(split, seed + 2, per, width, height)
+    elif cameras == "grid":
+        if K != 1:
+            raise ValueError("grid cameras serve a single block")
+        grid = grid_cameras(seed + 2, 10, altitude=altitude, width=width, height=height)
+        pick = _rng(seed + 5).choice(len(grid), size=per, replace=per > len(grid))
+        allv = [grid[i] for i in pick]
+    else:
+        raise ValueError(f"unknown camera law {cameras!r}")
     views = []
     for p in range(pool):
         vs = []
         for k in range(K):
             vs.extend(allv[k * per + p * views_per_step: k * per + (p + 1) * views_per_step])
         views.append(vs)
-    gt = city_scene(n_global, seed + 1, sh_degree=sh_degree, layout_seed=seed)
+    gt = city_scene(n_global, seed + 1, sh_degree=sh_degree, layout_seed=seed, log_scale_mu=log_scale_mu)
     return DogsWorkload(split, z, views, gt)

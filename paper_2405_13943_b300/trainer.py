@@ -376,6 +376,23 @@ class DogsTrainer:
             self.enqueue(p, c, target, slot)
         return g
 
+    def prepare_graphs(self, consensus_values=(True,)) -> int:
+        """Capture, ahead of time, the graph of every (pool entry, consensus
+        or not, target slot) combination that later steps can replay, so no
+        capture falls inside a timed loop.  Returns the number captured."""
+        slots = [None] if self.host_targets is None else [0, 1]
+        ds = self._stats_on()
+        n = 0
+        for p in range(len(self.view_sets)):
+            for c in consensus_values:
+                for slot in slots:
+                    key = (p, bool(c), slot, ds)
+                    if key not in self.graphs:
+                        target = None if slot is None else self.stage[slot]
+                        self.graphs[key] = self._capture(p, bool(c), target, slot)
+                        n += 1
+        return n
+
     def overflowed(self) -> bool:
         return bool(int(self.vb.status.item()) & L.DG_STATUS_CAPACITY)
 

@@ -34,5 +34,27 @@ def test_both_arms_name_the_workload_alike():
     import types
     wl = bench.build_workload("small")
     name = bench.workload_name(types.SimpleNamespace(workload="small"), wl)
-    assert name == (f"DOGS K={wl.split.K} batched, 200000 Gaussians SH3, {wl.split.n_copies} copies, 10% shared, "
-                    f"V={len(wl.views[0])} x 640x480")
+    assert name == (f"DOGS K={wl.split.K} batched, 200000 Gaussians SH3, {wl.split.n_copies} copies, 5% shared, "
+                    f"V={len(wl.views[0])} x 640x480 aerial 45 deg, consensus every step")
+
+
+def test_every_workload_has_its_metric_and_consensus_rule():
+    sys.path.insert(0, ROOT)
+    import bench
+    import types
+    for name, w in bench.WORKLOADS.items():
+        args = types.SimpleNamespace(workload=name)
+        m = bench.metric_of(args)
+        assert (m == bench.METRIC) == (name == "large"), name
+        if w["kind"] == "dogs":
+            c = bench.consensus_arg(w)
+            assert c is (False if w["intv"] is None else True if w["intv"] == 1 else None), name
+
+
+def test_reference_arm_of_the_rasteriser_config():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--workload", "raster4k"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
+    assert d["impl"] == "reference" and d["unit"] == "views/s" and d["value"] > 0
+    assert d["cpu_baseline"]["cores"] >= 1 and d["e2e"]["h2d_bytes_per_step"] == 0
