@@ -117,6 +117,63 @@ __device__ __forceinline__ double cam_depth(const CamL& c, float3 mu)
     return __dadd_rn(s, (double)c.t[2]);
 }
 
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// The decisions cam_depth feeds -- depth > near, and the depth's float
+// rounding tz -- taken in float arithmetic, FP64 only where that cannot
+// decide.  Each product splits exactly into hi + lo (the error of a float
+// product is itself a float, given by an FMA); the his are summed by TwoSum
+// with their errors, so s + lo lies within 2^-43 S of the exact sum, and
+// cam_depth's double within 3 2^-53 S of it (S = |R6 x| + |R7 y| + |R8 z| +
+// |t2|).  With the margin M = 2^-40 S:
+//   (s - near) + lo > M      =>  depth > near      (s - near is exact when
+//   (s - near) + lo < -M     =>  depth <= near      s is within 2x of near;
+//                                                    farther, 2^-22 |s - near|
+//                                                    covers its rounding);
+//   |(s - f) + lo| < ulp/2 - M, f = rn(s + lo), ulp the spacing below f
+//                            =>  rn(depth) = f     (no float rounding
+//                                                    boundary within M).
+// Otherwise (near a threshold or a boundary, S outside [2^-80, 2^100], NaN)
+// the FP64 sum decides.  Returns depth > near; tz is set when it is true.
+__device__ __forceinline__ bool cam_depth_front(const CamL& c, float3 mu, float& tz)
+{
+    const float h6 = __fmul_rn(c.R[6], mu.x), h7 = __fmul_rn(c.R[7], mu.y), h8 = __fmul_rn(c.R[8], mu.z);
+    const float l6 = __fmaf_rn(c.R[6], mu.x, -h6), l7 = __fmaf_rn(c.R[7], mu.y, -h7);
+    const float l8 = __fmaf_rn(c.R[8], mu.z, -h8);
+    float s, e1, e2, e3;
+    two_sum(h6, h7, s, e1);
+    two_sum(s, h8, s, e2);
+    two_sum(s, c.t[2], s, e3);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(l6, l7), __fadd_rn(l8, e1)), __fadd_rn(e2, e3));
+    const float S = __fadd_rn(__fadd_rn(fabsf(h6), fabsf(h7)), __fadd_rn(fabsf(h8), fabsf(c.t[2])));
+    if (S >= 0x1p-80f && S <= 0x1p100f) {
+        const float M = __fmul_rn(S, 0x1p-40f);
+        const float dn = __fsub_rn(s, c.nearz);
+        const float gap = __fadd_rn(dn, lo);
+        const float Mn = __fmaf_rn(fabsf(dn), 0x1p-22f, M);
+        if (gap < -Mn) return false;
+        if (gap > Mn) {
+            const float f = __fadd_rn(s, lo);
+            if (f >= 0x1p-100f) {
+                const float r = __fadd_rn(__fsub_rn(s, f), lo);
+                const float below = __fsub_rn(f, __int_as_float(__float_as_int(f) - 1));
+                if (fabsf(r) < __fsub_rn(__fmul_rn(0.5f, below), __fmul_rn(M, 1.0625f))) {
+                    tz = f;
+                    return true;
+                }
+            }
+        }
+    }
+    const double d = cam_depth(c, mu);
+    tz = (float)d;
+    return d > (double)c.nearz;
+}
+
 // Screen-space geometry of one Gaussian in one view.
 struct Geom {
     float tx, ty, tz, xn, yn;
@@ -132,9 +189,8 @@ struct Geom {
 
 // The lateral frustum test of geom() on the mean alone (the same expressions,
 // so the same decisions), taken before the rest of a copy's parameters load.
-__device__ __forceinline__ bool in_frustum(const CamL& cam, double tzd, float3 mu)
+__device__ __forceinline__ bool in_frustum(const CamL& cam, float tz, float3 mu)
 {
-    const float tz = (float)tzd;
     const float tx = fmaf(cam.R[0], mu.x, fmaf(cam.R[1], mu.y, fmaf(cam.R[2], mu.z, cam.t[0])));
     const float ty = fmaf(cam.R[3], mu.x, fmaf(cam.R[4], mu.y, fmaf(cam.R[5], mu.z, cam.t[1])));
     const float xn = tx / tz, yn = ty / tz;
@@ -176,10 +232,10 @@ __device__ __forceinline__ bool surely_culled(const CamL& cam, float3 mu)
 // Computes every field; returns false if the Gaussian is culled in this
 // view.  The caller has already checked camera z > near_z (exact, in double),
 // so no division below is by a non-positive depth.  Fills rect if non-null.
-__device__ __forceinline__ bool geom(const CamL& cam, double tzd, float3 mu, float4 q, float4 sc, int tw,
+__device__ __forceinline__ bool geom(const CamL& cam, float tz, float3 mu, float4 q, float4 sc, int tw,
                                      int th, Geom& g, uint2* rect_out)
 {
-    g.tz = (float)tzd;
+    g.tz = tz;
     g.tx = fmaf(cam.R[0], mu.x, fmaf(cam.R[1], mu.y, fmaf(cam.R[2], mu.z, cam.t[0])));
     g.ty = fmaf(cam.R[3], mu.x, fmaf(cam.R[4], mu.y, fmaf(cam.R[5], mu.z, cam.t[1])));
     g.xn = g.tx / g.tz;
@@ -262,11 +318,11 @@ __device__ __forceinline__ void project_copy(const GView& x, const dg_camera* __
         load_cam(cams, v, cam);
         int64_t r = cam.rec_off + (c - cam.gb);
         if (surely_culled(cam, mu)) { rect[r] = make_uint2(0, 0); continue; }
-        double tzd = cam_depth(cam, mu);
-        if (!(tzd > (double)cam.nearz) || !in_frustum(cam, tzd, mu)) { rect[r] = make_uint2(0, 0); continue; }
+        float tz;
+        if (!cam_depth_front(cam, mu, tz) || !in_frustum(cam, tz, mu)) { rect[r] = make_uint2(0, 0); continue; }
         Geom g;
         uint2 rr;
-        if (!geom(cam, tzd, mu, q, sc, plan.tile_w, plan.tile_h, g, &rr)) { rect[r] = make_uint2(0, 0); continue; }
+        if (!geom(cam, tz, mu, q, sc, plan.tile_w, plan.tile_h, g, &rr)) { rect[r] = make_uint2(0, 0); continue; }
         float dx = mu.x - cam.cp[0], dy = mu.y - cam.cp[1], dz = mu.z - cam.cp[2];
         float il = rsqrtf(dx * dx + dy * dy + dz * dz);
         float Y[NK];
@@ -412,7 +468,9 @@ __device__ __forceinline__ void geometry_adjoint(const CamL& cam, float3 mu, flo
                                                  float* gs)
 {
     Geom g;
-    geom(cam, cam_depth(cam, mu), mu, q, sc, tile_w, tile_h, g, nullptr);  // forward's rect decides
+    float tz;
+    cam_depth_front(cam, mu, tz);          // a kept record: in front, tz its float depth
+    geom(cam, tz, mu, q, sc, tile_w, tile_h, g, nullptr);  // forward's rect decides
     // conic (a, b, c) -> Sigma' entries (A, B, C)
     float da = d0.z, db = d0.w, dc = d1.x;
     float id2 = 1.f / (g.det * g.det);
@@ -602,7 +660,7 @@ __device__ __forceinline__ void step_fields(GView& x, GView& m, GView& v, const 
         const float as[4] = {aa.x, aa.y, aa.z, aa.w};
 #pragma unroll
         for (int i = 0; i < 4; i++) {
-            const float rho = i < 3 ? a.rho[0] : a.rho[4], lr = i < 3 ? a.lr[0] : a.lr[5];
+            const float rho = rho_of(a, i < 3 ? 0 : 4), lr = i < 3 ? a.lr[0] : a.lr[5];
             if (s) gg[i] += rho * (xs[i] - as[i]);
             adam_scalar(xs[i], gg[i], ms[i], vs[i], lr, a.b1, a.b2, a.eps, ic1, ic2);
         }
@@ -619,7 +677,7 @@ __device__ __forceinline__ void step_fields(GView& x, GView& m, GView& v, const 
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             float g = gq[i];
-            if (s) g += a.rho[1] * (xs[i] - as[i]);
+            if (s) g += rho_of(a, 1) * (xs[i] - as[i]);
             adam_scalar(xs[i], g, ms[i], vs[i], a.lr[1], a.b1, a.b2, a.eps, ic1, ic2);
         }
         x.quat[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
@@ -635,7 +693,7 @@ __device__ __forceinline__ void step_fields(GView& x, GView& m, GView& v, const 
 #pragma unroll
         for (int i = 0; i < 3; i++) {   // lane 3 is padding
             float g = gs[i];
-            if (s) g += a.rho[2] * (xs[i] - as[i]);
+            if (s) g += rho_of(a, 2) * (xs[i] - as[i]);
             adam_scalar(xs[i], g, ms[i], vs[i], a.lr[2], a.b1, a.b2, a.eps, ic1, ic2);
         }
         x.scale[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
@@ -703,7 +761,7 @@ __device__ __forceinline__ void step_planes(GView& x, GView& m, GView& v, const 
             for (int i = 0; i < 4; i++) {
                 if (!act[i]) continue;
                 float g = gq4[i];
-                if (sh[i]) g += a.rho[3] * (xs[i] - as[i]);
+                if (sh[i]) g += rho_of(a, 3) * (xs[i] - as[i]);
                 adam_scalar(xs[i], g, ms[i], vs[i], lr, a.b1, a.b2, a.eps, ic1, ic2);
             }
             const int64_t u = ((int64_t)j * x.ld + cq) >> 2;

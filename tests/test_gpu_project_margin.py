@@ -201,3 +201,147 @@ def test_projection_culling_at_its_thresholds(seed):
         assert 0.2 * n < expect[sl].sum() < 0.8 * n, name        # both sides well populated
         bad = np.flatnonzero(empty[sl] != expect[sl])
         assert bad.size == 0, (name, bad[:10])
+
+
+# ---- the depth in float arithmetic with an FP64 fallback --------------------
+def add32(a, b) -> F32:
+    return rn32(Fraction(float(a)) + Fraction(float(b)))
+
+
+def sub32(a, b) -> F32:
+    return rn32(Fraction(float(a)) - Fraction(float(b)))
+
+
+def mul32(a, b) -> F32:
+    return rn32(Fraction(float(a)) * Fraction(float(b)))
+
+
+def two_sum32(a, b):
+    s = add32(a, b)
+    bb = sub32(s, a)
+    return s, add32(sub32(a, sub32(s, bb)), sub32(b, bb))
+
+
+def depth_double(R6, R7, R8, t2, near, x, y, z):
+    """The FP64 depth as the kernel sums it: (front, float depth)."""
+    d = np.float64(R6) * np.float64(x)
+    d = d + np.float64(R7) * np.float64(y)
+    d = d + np.float64(R8) * np.float64(z)
+    d = d + np.float64(t2)
+    return bool(d > np.float64(near)), F32(d)
+
+
+def depth_fast32(R6, R7, R8, t2, near, x, y, z):
+    """The kernel's float path, operation for operation with each operation
+    rounded once: (front, float depth) where it decides, None where the FP64
+    sum must."""
+    h6, h7, h8 = mul32(R6, x), mul32(R7, y), mul32(R8, z)
+    l6, l7, l8 = fma32(R6, x, -h6), fma32(R7, y, -h7), fma32(R8, z, -h8)
+    s, e1 = two_sum32(h6, h7)
+    s, e2 = two_sum32(s, h8)
+    s, e3 = two_sum32(s, t2)
+    lo = add32(add32(add32(l6, l7), add32(l8, e1)), add32(e2, e3))
+    S_ = add32(add32(abs(h6), abs(h7)), add32(abs(h8), abs(t2)))
+    if not (F32(2.0 ** -80) <= S_ <= F32(2.0 ** 100)):
+        return None
+    M = mul32(S_, F32(2.0 ** -40))
+    dn = sub32(s, near)
+    gap = add32(dn, lo)
+    Mn = fma32(abs(dn), F32(2.0 ** -22), M)
+    if gap < -Mn:
+        return False, None
+    if not gap > Mn:
+        return None
+    f = add32(s, lo)
+    if not f >= F32(2.0 ** -100):
+        return None
+    r = add32(sub32(s, f), lo)
+    below = sub32(f, np.nextafter(f, F32(0.0)))
+    if abs(r) < sub32(mul32(F32(0.5), below), mul32(M, F32(1.0625))):
+        return True, f
+    return None
+
+
+def depth_cases(seed, n=1500):
+    """Camera rows and means whose FP64 depth lies within 2^-12 of a float
+    ulp of a float rounding boundary or within 1e-6 of the near plane (kept
+    from many random draws), plus exact ties: R8 = 1 with z + t2 a float
+    midpoint."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        m = 200000
+        R = rng.standard_normal((m, 3))
+        R /= np.linalg.norm(R, axis=1, keepdims=True)
+        R = R.astype(F32)
+        mu = (rng.uniform(-1500, 1500, (m, 3))).astype(F32)
+        t2 = rng.uniform(-2000, 2000, m).astype(F32)
+        d = ((R[:, 0].astype(np.float64) * mu[:, 0] + R[:, 1].astype(np.float64) * mu[:, 1])
+             + R[:, 2].astype(np.float64) * mu[:, 2]) + t2.astype(np.float64)
+        f = d.astype(F32).astype(np.float64)
+        ulp = np.abs(np.spacing(d.astype(F32))).astype(np.float64)
+        frac = np.abs(np.abs(d - f) / ulp - 0.5)           # 0 at a rounding boundary
+        near = np.where(rng.random(m) < 0.5, 0.2, np.abs(d) * (1 + rng.uniform(-1e-6, 1e-6, m))).astype(F32)
+        pick = np.flatnonzero((frac < 2.0 ** -12) | (np.abs(d - near) < 1e-6 * np.abs(d)))
+        for i in pick[: n - len(out)]:
+            out.append((R[i, 0], R[i, 1], R[i, 2], t2[i], near[i], mu[i, 0], mu[i, 1], mu[i, 2]))
+    one, zero = F32(1.0), F32(0.0)
+    for z, t in ((F32(1.0), F32(2.0 ** -24)), (F32(3.0), F32(2.0 ** -23)), (F32(100.0), F32(2.0 ** -18)),
+                 (F32(1.0), F32(3 * 2.0 ** -24))):
+        out.append((zero, zero, one, t, F32(0.2), F32(5.0), F32(-7.0), z))
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_float_depth_decides_only_where_it_equals_the_fp64_sum(seed):
+    """The float path's margin argument, on the CPU: wherever it decides, its
+    near-plane decision and float depth equal those of the FP64 sum, on
+    depths at float rounding boundaries (exact ties included) and at the
+    near plane; it decides most of them and leaves the ties to FP64."""
+    decided = fell = 0
+    for c in depth_cases(seed):
+        want = depth_double(*c)
+        got = depth_fast32(*c)
+        if got is None:
+            fell += 1
+            continue
+        decided += 1
+        assert got[0] == want[0], c
+        if want[0]:
+            assert got[1].view(np.uint32) == want[1].view(np.uint32), c
+    assert decided > 0.5 * (decided + fell) and fell >= 4
+
+
+@pytest.mark.gpu
+def test_projected_depth_bits_at_rounding_ties():
+    """On the GPU: copies whose FP64 depth is an exact float midpoint (ties
+    to even) or a hair beside one, seen by an axis-aligned camera: the
+    record's depth and the keys' depth bits equal the FP64 sum's rounding."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_13943_b300 import build as B
+    B.build()
+    from paper_2405_13943_b300 import dogs as D
+    R = np.eye(3, dtype=F32)
+    cam = S.Camera(64, 48, 64.0, 64.0, 32.0, 24.0, R, np.array([0.0, 0.0, 2.0 ** -24], F32),
+                   np.array([0.0, 0.0, -(2.0 ** -24)], F32), 0.2)
+    zs = []
+    for base in (1.0, 3.0, 10.0, 100.0, 1000.0):
+        f = F32(base)
+        for k in range(-3, 4):
+            zs.append(np.nextafter(f, F32(np.inf)) if k > 0 else f)
+            f = np.nextafter(f, F32(np.inf))
+    zs = np.array(zs, F32)
+    n = len(zs)
+    means = np.stack([np.zeros(n, F32), np.zeros(n, F32), zs], 1)
+    g = S.Gaussians(means, np.tile(np.array([1.0, 0, 0, 0], F32), (n, 1)), np.full((n, 3), -3.0, F32),
+                    np.full(n, 2.0, F32), np.full((n, 1, 3), 0.5, F32))
+    xb = D.GaussianBuffer.from_synth(g)
+    vb = D.ViewBatch([cam], [0, n], 16, 16)
+    D.dg_project(xb, vb)
+    torch.cuda.synchronize()
+    rec = vb.rec.cpu().numpy()[:12 * n].reshape(n, 12)
+    for i in range(n):
+        front, tz = depth_double(F32(0), F32(0), F32(1), cam.t[2], F32(cam.near), F32(0), F32(0), zs[i])
+        assert front
+        assert rec[i, 9].astype(F32).view(np.uint32) == tz.view(np.uint32), (i, zs[i], rec[i, 9], tz)
