@@ -242,6 +242,28 @@ int dg_rasterize_bwd_records(const float* rec, const uint32_t* vals, const uint3
                              const float* T_final, const uint32_t* last, const float* dL_dimage,
                              float* drec, void* stream);
 
+/* Deterministic form of dg_rasterize_bwd_records: the same adjoint with the
+ * same tile walk, but the backward of each (record, tile) pair is stored in
+ * its own slot of part (9 floats per slot) instead of being added to drec
+ * by atomics, and drec[r] is then summed from record r's slots in tile
+ * order; drec (12 floats per record, the last 3 zero) is therefore the same
+ * bit for bit from run to run, which makes a resumed run repeat an
+ * uninterrupted one exactly.  A record's slots are one per tile of its
+ * rectangle: the slot offsets are the exclusive sum of the rectangle areas
+ * (computed here into ws, size dg_rasterize_bwd_slots_workspace_size), and
+ * the total is written to *dev_slots (device uint64).  part: device,
+ * 9 * slot_capacity floats, zeroed here.  If the total exceeds
+ * slot_capacity, DG_STATUS_CAPACITY is set in *dev_status and the records
+ * whose slots fall beyond it get zero gradients (retry with a larger part).
+ * Always one warp per tile (the plan's backward staging depth is kept). */
+size_t dg_rasterize_bwd_slots_workspace_size(const dg_plan* plan);
+int dg_rasterize_bwd_slots(const float* rec, const uint32_t* rect, const uint32_t* vals,
+                           const uint32_t* ranges, const dg_camera* dev_cams, const dg_plan* plan,
+                           const float* bg, const float* T_final, const uint32_t* last,
+                           const float* dL_dimage, float* part, int64_t slot_capacity, void* ws,
+                           size_t ws_bytes, uint64_t* dev_slots, uint32_t* dev_status, float* drec,
+                           void* stream);
+
 /* The projection adjoint (K8) and the x-step (K9, Eq. 8a / 12a) in one pass,
  * for batches whose blocks have at most one view each: every copy then has
  * at most one record, so each thread finishes its copy's dL/dx from drec
@@ -288,7 +310,9 @@ int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev
  * g + rho_grp (x - anchor) on shared copies (copy_shared[c] != 0), where the
  * anchor of a shared copy is z_{g(c)} - u_c, kept by dg_admm_consensus and
  * dg_admm_anchor.  Groups in the paper's order (Eq. 12): 0 p (mean),
- * 1 q (rotation), 2 s (scale), 3 f (SH), 4 o (opacity): rho[5] (host).
+ * 1 q (rotation), 2 s (scale), 3 f (SH), 4 o (opacity): rho[5], in host
+ * memory (read at the call) or device memory (read when the kernels run,
+ * e.g. as dg_admm_adapt leaves it).
  * lr[6] (host): p, q, s, SH DC, SH rest, o.  Moments m, v updated in place;
  * bias correction with the iteration number `step` >= 1, or, if dev_step is
  * not NULL, with the int32 it points to in device memory (read when the
@@ -436,6 +460,29 @@ int dg_gather_rows(const dg_gaussians* src, const int32_t* idx, dg_gaussians* ds
  * multiplies each group of u on shared copies by factor[5] (host); rerun
  * dg_admm_anchor afterwards. */
 int dg_admm_scale_duals(dg_gaussians* u, const uint8_t* copy_shared, const float* factor, void* stream);
+
+/* Adaptive penalty on the device (Sec. 3.3, Eq. 10), for a loop that keeps
+ * rho in device memory: rho (device, float[5]) may then be passed as the rho
+ * of dg_adam_admm_step, dg_xstep_part and dg_admm_consensus, which read it
+ * when their kernels run.  After a consensus that wrote `residuals` (device,
+ * double[10]: squared primal per group, then squared dual), per group g
+ * with r = sqrt(primal_g) and s = sqrt(dual_g): rho_g *= tau_inc when
+ * r > mu s, rho_g /= tau_dec when s > mu r, unchanged otherwise -- only
+ * while the iteration t = *dev_step - 1 is below freeze_after (dev_step:
+ * the Adam step counter, advanced at the start of each iteration).  Writes
+ * factor (device, float[5]) = old rho_g / new rho_g.  No host
+ * synchronisation: the whole rule runs in one small kernel, so it can sit
+ * inside a captured graph.  DG_ERR_INVALID on a null or misaligned pointer
+ * or mu, tau_inc, tau_dec below 1. */
+int dg_admm_adapt(const double* residuals, float* rho, float* factor, const int32_t* dev_step, float mu,
+                  float tau_inc, float tau_dec, int freeze_after, void* stream);
+
+/* The scaled duals and anchors after dg_admm_adapt: on every shared copy
+ * u_grp *= factor[grp] (factor: device, float[5]) and anchor = z_{g(c)} - u,
+ * in one pass; when every factor is 1 the kernel returns without touching
+ * memory.  u, anchor: same layout; z: the global set (same SH degree). */
+int dg_admm_rescale(dg_gaussians* u, const dg_gaussians* z, dg_gaussians* anchor, const int32_t* copy_gid,
+                    const uint8_t* copy_shared, const float* factor, void* stream);
 
 /* anchor_c = z_{copy_gid[c]} - u_c for every shared copy (initialisation). */
 int dg_admm_anchor(const dg_gaussians* z, const dg_gaussians* u, const int32_t* copy_gid,

@@ -64,6 +64,12 @@ _vp = C.c_void_p
 _SIGS = {
     "dg_version": (C.c_char_p, []),
     "dg_launch_count": (C.c_uint64, []),
+    "dg_rasterize_bwd_slots_workspace_size": (C.c_size_t, [C.POINTER(DgPlan)]),
+    "dg_rasterize_bwd_slots": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(DgPlan), C.POINTER(C.c_float), _vp, _vp,
+                                         _vp, _vp, C.c_int64, _vp, C.c_size_t, _vp, _vp, _vp, _vp]),
+    "dg_admm_adapt": (C.c_int, [_vp, _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_int, _vp]),
+    "dg_admm_rescale": (C.c_int, [C.POINTER(DgGaussians), C.POINTER(DgGaussians), C.POINTER(DgGaussians), _vp, _vp,
+                                  _vp, _vp]),
     "dg_probe_fma": (C.c_int64, [C.c_int, C.c_int, _vp, _vp]),
     "dg_gaussian_floats": (C.c_int64, [C.c_int64, C.c_int]),
     "dg_plan_views": (C.c_int, [C.POINTER(DgCamera), C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_int, C.c_int,
@@ -161,6 +167,17 @@ def stream_handle(stream=None) -> int:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return s.cuda_stream
+
+
+def rho_arg(rho):
+    """rho[5] for an ABI call: a float array in host memory, or the address
+    of a float32 device tensor (read by the kernels when they run)."""
+    if hasattr(rho, "data_ptr"):
+        import torch
+        if rho.dtype != torch.float32 or rho.numel() != 5 or not rho.is_cuda:
+            raise ValueError("a device rho is a CUDA float32 tensor of 5 elements")
+        return C.cast(C.c_void_p(rho.data_ptr()), C.POINTER(C.c_float))
+    return floats(rho)
 
 
 def floats(vals) -> C.Array:

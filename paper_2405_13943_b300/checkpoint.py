@@ -96,6 +96,8 @@ def save(tr, path: str) -> None:
     on_gpu = bufs["z"].data.is_cuda
     if on_gpu:
         torch.cuda.synchronize()
+    if hasattr(tr, "current_rho"):
+        tr.current_rho()                 # rho as Eq. 10 left it on the device
     entries: List[Dict] = []
     off = 0
     for name, b in bufs.items():

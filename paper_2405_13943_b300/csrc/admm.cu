@@ -50,9 +50,10 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam_fields(float4* __restrict
 {
     float ic1, ic2;
     bias_corr(a, dev_step, ic1, ic2);
-    const float rho0[4] = {a.rho[0], a.rho[0], a.rho[0], a.rho[4]}, lr0[4] = {a.lr[0], a.lr[0], a.lr[0], a.lr[5]};
-    const float rho1[4] = {a.rho[1], a.rho[1], a.rho[1], a.rho[1]}, lr1[4] = {a.lr[1], a.lr[1], a.lr[1], a.lr[1]};
-    const float rho2[4] = {a.rho[2], a.rho[2], a.rho[2], a.rho[2]}, lr2[4] = {a.lr[2], a.lr[2], a.lr[2], a.lr[2]};
+    const float p0 = rho_of(a, 0), p1 = rho_of(a, 1), p2 = rho_of(a, 2), p4 = rho_of(a, 4);
+    const float rho0[4] = {p0, p0, p0, p4}, lr0[4] = {a.lr[0], a.lr[0], a.lr[0], a.lr[5]};
+    const float rho1[4] = {p1, p1, p1, p1}, lr1[4] = {a.lr[1], a.lr[1], a.lr[1], a.lr[1]};
+    const float rho2[4] = {p2, p2, p2, p2}, lr2[4] = {a.lr[2], a.lr[2], a.lr[2], a.lr[2]};
     const bool all4[4] = {true, true, true, true}, three[4] = {true, true, true, false};
     int64_t base = (int64_t)blockIdx.x * (kAdamThreads * kAdamPer) + threadIdx.x;
 #pragma unroll
@@ -77,7 +78,8 @@ __global__ void __launch_bounds__(kAdamThreads) k_adam_planes(float4* __restrict
     bias_corr(a, dev_step, ic1, ic2);
     const int p = blockIdx.y;
     const float l = p < 3 ? a.lr[3] : a.lr[4];
-    const float rho[4] = {a.rho[3], a.rho[3], a.rho[3], a.rho[3]}, lr[4] = {l, l, l, l};
+    const float p3 = rho_of(a, 3);
+    const float rho[4] = {p3, p3, p3, p3}, lr[4] = {l, l, l, l};
     const int64_t q4 = ld >> 2;
     const int64_t row = 3 * ld + (int64_t)p * q4;
     int64_t base = (int64_t)blockIdx.x * (kAdamThreads * kAdamPer) + threadIdx.x;
@@ -113,6 +115,7 @@ struct ConsArgs {
     float rho[5];
     float alpha;
     int n_planes;
+    const float* dev_rho;   // non-null: rho read from this device array when the kernel runs
 };
 
 // Up to kFast copies per global are handled with all their loads issued
@@ -212,7 +215,8 @@ __device__ __noinline__ void cons_generic(GView x, GView u, GView z, GView an, i
             if (!(f == 2 && l == 3)) {
                 r.rp[grp] += rr;
                 float dz = zn[l] - zp[l];
-                r.rd[grp] += a.rho[grp] * a.rho[grp] * (float)n * dz * dz;
+                const float rg = rho_of(a, grp);
+                r.rd[grp] += rg * rg * (float)n * dz * dz;
             }
         }
         zf[f][i] = make_float4(zn[0], zn[1], zn[2], zn[3]);
@@ -224,7 +228,8 @@ __device__ __noinline__ void cons_generic(GView x, GView u, GView z, GView an, i
                              1, zo, a.alpha, rr);
         z.sh[(int64_t)j * z.ld + i] = zn;
         r.rp[3] += rr;
-        r.rd[3] += a.rho[3] * a.rho[3] * (float)n * (zn - zo) * (zn - zo);
+        const float r3 = rho_of(a, 3);
+        r.rd[3] += r3 * r3 * (float)n * (zn - zo) * (zn - zo);
     }
 }
 
@@ -262,9 +267,13 @@ __global__ void __launch_bounds__(128, DG_CONS_CTAS) k_consensus(GView x, GView 
 #pragma unroll
             for (int k = 0; k < kFast; k++) cp[k] = k < n ? cpg[k] : 0;
             const int g_mo[4] = {0, 0, 0, 4}, g_q[4] = {1, 1, 1, 1}, g_s[4] = {2, 2, 2, -1};
-            cons_field4(x.mo, u.mo, an.mo, z.mo, i, cp, n, g_mo, a.alpha, a.rho, r);
-            cons_field4(x.quat, u.quat, an.quat, z.quat, i, cp, n, g_q, a.alpha, a.rho, r);
-            cons_field4(x.scale, u.scale, an.scale, z.scale, i, cp, n, g_s, a.alpha, a.rho, r);
+            float rh[5];
+#pragma unroll
+            for (int k = 0; k < 5; k++) rh[k] = rho_of(a, k);
+            cons_field4(x.mo, u.mo, an.mo, z.mo, i, cp, n, g_mo, a.alpha, rh, r);
+            cons_field4(x.quat, u.quat, an.quat, z.quat, i, cp, n, g_q, a.alpha, rh, r);
+            cons_field4(x.scale, u.scale, an.scale, z.scale, i, cp, n, g_s, a.alpha, rh, r);
+            const float rho3 = rh[3];
             const float inv = 1.f / (float)n;
             // planes per batch of loads; same-box A/B on the 6M step (CTAs per SM, CH):
             // (6, 4) 0.359 ms, (6, 2) 0.351, (7, 3) 0.336, (8, 2) 0.329.  Larger batches
@@ -303,7 +312,7 @@ __global__ void __launch_bounds__(128, DG_CONS_CTAS) k_consensus(GView x, GView 
                             r.rp[3] += (xs[jj][k] - zn) * (xs[jj][k] - zn);
                         }
                     z.sh[(int64_t)j * z.ld + i] = zn;
-                    r.rd[3] += a.rho[3] * a.rho[3] * (float)n * (zn - zo[jj]) * (zn - zo[jj]);
+                    r.rd[3] += rho3 * rho3 * (float)n * (zn - zo[jj]) * (zn - zo[jj]);
                 }
             }
         } else if (n > kFast) {
@@ -373,13 +382,93 @@ int launch_scale_duals(dg_gaussians* u, const uint8_t* shared, const float* f, c
     return DG_OK;
 }
 
+// ---- Eq. 10 on the device ------------------------------------------------------------
+// One thread per group g: with r = sqrt(primal_g), s = sqrt(dual_g) from
+// the consensus just run, rho_g *= tau_inc when r > mu s, rho_g /= tau_dec
+// when s > mu r, unchanged otherwise, and only while the iteration
+// t = *dev_step - 1 is below freeze_after; factor_g = old rho_g / new rho_g,
+// the rescale of the scaled duals (u = y / rho).  Compared in FP64 as the
+// host rule does.
+__global__ void k_admm_adapt(const double* __restrict__ res, float* __restrict__ rho, float* __restrict__ factor,
+                             const int32_t* __restrict__ dev_step, float mu, float tau_inc, float tau_dec,
+                             int freeze_after)
+{
+    const int g = threadIdx.x;
+    if (g >= 5) return;
+    const int t = *dev_step - 1;
+    const float old = rho[g];
+    float nw = old;
+    if (t < freeze_after) {
+        const double r = sqrt(fmax(res[g], 0.0)), s = sqrt(fmax(res[5 + g], 0.0));
+        if (r > (double)mu * s)
+            nw = (float)((double)old * (double)tau_inc);
+        else if (s > (double)mu * r)
+            nw = (float)((double)old / (double)tau_dec);
+    }
+    rho[g] = nw;
+    factor[g] = old / nw;
+}
+
+// After a change of rho: u_grp *= factor[grp] on the shared copies and their
+// anchors z - u rebuilt, in one pass; returns at once when every factor is 1.
+__global__ void __launch_bounds__(256) k_admm_rescale(GView u, GView z, GView an, const int32_t* __restrict__ gid,
+                                                      const uint8_t* __restrict__ shared, int64_t n, int n_planes,
+                                                      const float* __restrict__ factor)
+{
+    const float f0 = __ldg(factor), f1 = __ldg(factor + 1), f2 = __ldg(factor + 2), f3 = __ldg(factor + 3),
+                f4 = __ldg(factor + 4);
+    if (f0 == 1.f && f1 == 1.f && f2 == 1.f && f3 == 1.f && f4 == 1.f) return;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n || !shared[c]) return;
+    const int64_t gI = gid[c];
+    float4 m = u.mo[c], a = z.mo[gI];
+    m = make_float4(m.x * f0, m.y * f0, m.z * f0, m.w * f4);
+    u.mo[c] = m;
+    an.mo[c] = make_float4(a.x - m.x, a.y - m.y, a.z - m.z, a.w - m.w);
+    float4 q = u.quat[c];
+    a = z.quat[gI];
+    q = make_float4(q.x * f1, q.y * f1, q.z * f1, q.w * f1);
+    u.quat[c] = q;
+    an.quat[c] = make_float4(a.x - q.x, a.y - q.y, a.z - q.z, a.w - q.w);
+    float4 sc = u.scale[c];
+    a = z.scale[gI];
+    sc = make_float4(sc.x * f2, sc.y * f2, sc.z * f2, sc.w * f2);
+    u.scale[c] = sc;
+    an.scale[c] = make_float4(a.x - sc.x, a.y - sc.y, a.z - sc.z, a.w - sc.w);
+    for (int j = 0; j < n_planes; j++) {
+        const float un = u.sh[(int64_t)j * u.ld + c] * f3;
+        u.sh[(int64_t)j * u.ld + c] = un;
+        an.sh[(int64_t)j * an.ld + c] = z.sh[(int64_t)j * z.ld + gI] - un;
+    }
+}
+
+int launch_admm_adapt(const double* res, float* rho, float* factor, const int32_t* dev_step, float mu,
+                      float tau_inc, float tau_dec, int freeze_after, cudaStream_t st)
+{
+    k_admm_adapt<<<1, 32, 0, st>>>(res, rho, factor, dev_step, mu, tau_inc, tau_dec, freeze_after);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
+int launch_admm_rescale(dg_gaussians* u, const dg_gaussians* z, dg_gaussians* an, const int32_t* gid,
+                        const uint8_t* shared, const float* factor, cudaStream_t st)
+{
+    if (u->n == 0) return DG_OK;
+    k_admm_rescale<<<(unsigned)((u->n + 255) / 256), 256, 0, st>>>(gview(u), gview(z), gview(an), gid, shared, u->n,
+                                                                   3 * sh_coefs(u->sh_degree), factor);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
 int launch_adam_admm(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m, dg_gaussians* v,
                      const dg_gaussians* anchor, const uint8_t* shared, const float* rho, const float* lr,
                      float b1, float b2, float eps, int step, const int32_t* dev_step, cudaStream_t st)
 {
     if (x->n == 0) return DG_OK;
     AdamArgs a;
-    for (int i = 0; i < 5; i++) a.rho[i] = rho[i];
+    take_rho(rho, a.rho, &a.dev_rho);
     for (int i = 0; i < 6; i++) a.lr[i] = lr[i];
     a.b1 = b1; a.b2 = b2; a.eps = eps; a.step = step;
     const float4* an = anchor ? reinterpret_cast<const float4*>(anchor->data) : nullptr;
@@ -404,7 +493,7 @@ int launch_consensus(const dg_gaussians* x, dg_gaussians* u, dg_gaussians* z, dg
     if (res && cudaMemsetAsync(res, 0, 10 * sizeof(double), st) != cudaSuccess) return DG_ERR_CUDA;
     if (z->n == 0) return DG_OK;
     ConsArgs a;
-    for (int i = 0; i < 5; i++) a.rho[i] = rho[i];
+    take_rho(rho, a.rho, &a.dev_rho);
     a.alpha = alpha;
     a.n_planes = 3 * sh_coefs(x->sh_degree);
     const unsigned grid = (unsigned)((z->n + 127) / 128);

@@ -17,6 +17,15 @@ size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity);
 int launch_bin_sort(const float4*, const uint2*, const dg_camera*, const dg_plan&, int64_t, uint64_t*, uint32_t*,
                     uint32_t*, uint32_t*, void*, uint32_t*, cudaStream_t);
 int bin_sort_init();
+size_t raster_slots_ws_bytes(int64_t n_rec);
+int launch_raster_bwd_slots(const float4* rec, const uint2* rect, const uint32_t* vals, const uint32_t* ranges,
+                            const dg_camera* cams, const dg_plan& plan, const float* bg, const float* T_final,
+                            const uint32_t* last, const float* dL_dimage, float* part, int64_t cap, void* ws,
+                            uint64_t* dev_slots, uint32_t* dev_status, float* drec, cudaStream_t st);
+int launch_admm_adapt(const double* res, float* rho, float* factor, const int32_t* dev_step, float mu,
+                      float tau_inc, float tau_dec, int freeze_after, cudaStream_t st);
+int launch_admm_rescale(dg_gaussians* u, const dg_gaussians* z, dg_gaussians* an, const int32_t* gid,
+                        const uint8_t* shared, const float* factor, cudaStream_t st);
 int loss_init();
 int launch_raster_fwd(const float4*, const uint32_t*, const uint32_t*, const dg_camera*, const dg_plan&,
                       const float*, float*, float*, uint32_t*, cudaStream_t);
@@ -316,6 +325,33 @@ int dg_rasterize_bwd_records(const float* rec, const uint32_t* vals, const uint3
                              st);
 }
 
+size_t dg_rasterize_bwd_slots_workspace_size(const dg_plan* plan)
+{
+    if (!valid_plan(plan)) return 0;
+    return raster_slots_ws_bytes(plan->n_rec);
+}
+
+int dg_rasterize_bwd_slots(const float* rec, const uint32_t* rect, const uint32_t* vals, const uint32_t* ranges,
+                           const dg_camera* dev_cams, const dg_plan* plan, const float* bg, const float* T_final,
+                           const uint32_t* last, const float* dL_dimage, float* part, int64_t slot_capacity,
+                           void* ws, size_t ws_bytes, uint64_t* dev_slots, uint32_t* dev_status, float* drec,
+                           void* stream)
+{
+    if (!valid_plan(plan) || !bg || slot_capacity < 0) return DG_ERR_INVALID;
+    if (!dev_slots || !dev_status || !ws || ((uintptr_t)dev_slots & 7u) || ((uintptr_t)ws & 7u))
+        return DG_ERR_INVALID;
+    if (plan->n_rec > 0) {
+        if (!rec || !rect || !vals || !ranges || !dev_cams || !T_final || !last || !dL_dimage || !drec)
+            return DG_ERR_INVALID;
+        if (slot_capacity > 0 && (!part || ((uintptr_t)part & 3u))) return DG_ERR_INVALID;
+        if (!aligned16(rec) || !aligned8(rect) || !aligned8(dev_cams) || !aligned16(drec)) return DG_ERR_INVALID;
+    }
+    if (ws_bytes < raster_slots_ws_bytes(plan->n_rec)) return DG_ERR_WORKSPACE;
+    return launch_raster_bwd_slots((const float4*)rec, (const uint2*)rect, vals, ranges, dev_cams, *plan, bg, T_final,
+                                   last, dL_dimage, part, slot_capacity, ws, dev_slots, dev_status, drec,
+                                   (cudaStream_t)stream);
+}
+
 int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
                   const float* drec, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
                   const uint8_t* copy_shared, const float* rho, const float* lr, float beta1, float beta2, float eps,
@@ -337,7 +373,7 @@ int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev
     if (plan->n_rec > 0 && (!rect || !dev_cams || (part != 1 && !drec))) return DG_ERR_INVALID;
     if (!aligned8(rect) || !aligned8(dev_cams) || !aligned16(drec)) return DG_ERR_INVALID;
     AdamArgs a;
-    for (int i = 0; i < 5; i++) a.rho[i] = rho[i];
+    take_rho(rho, a.rho, &a.dev_rho);
     for (int i = 0; i < 6; i++) a.lr[i] = lr[i];
     a.b1 = beta1; a.b2 = beta2; a.eps = eps; a.step = step;
     return launch_xstep(part, ctas, x, m, v, anchor, (anchor || z_unshared) ? copy_shared : nullptr, dev_cams, *plan,
@@ -451,6 +487,27 @@ int dg_admm_scale_duals(dg_gaussians* u, const uint8_t* copy_shared, const float
     if (!valid_gauss(u) || !factor) return DG_ERR_INVALID;
     if (u->n > 0 && !copy_shared) return DG_ERR_INVALID;
     return launch_scale_duals(u, copy_shared, factor, (cudaStream_t)stream);
+}
+
+int dg_admm_adapt(const double* residuals, float* rho, float* factor, const int32_t* dev_step, float mu,
+                  float tau_inc, float tau_dec, int freeze_after, void* stream)
+{
+    if (!residuals || !rho || !factor || !dev_step) return DG_ERR_INVALID;
+    if (((uintptr_t)residuals & 7u) || ((uintptr_t)rho & 3u) || ((uintptr_t)factor & 3u) || ((uintptr_t)dev_step & 3u))
+        return DG_ERR_INVALID;
+    if (!(mu >= 1.f) || !(tau_inc >= 1.f) || !(tau_dec >= 1.f)) return DG_ERR_INVALID;
+    return launch_admm_adapt(residuals, rho, factor, dev_step, mu, tau_inc, tau_dec, freeze_after,
+                             (cudaStream_t)stream);
+}
+
+int dg_admm_rescale(dg_gaussians* u, const dg_gaussians* z, dg_gaussians* anchor, const int32_t* copy_gid,
+                    const uint8_t* copy_shared, const float* factor, void* stream)
+{
+    if (!valid_gauss(u) || !valid_gauss(z) || !valid_gauss(anchor) || !same_layout(u, anchor) || !factor)
+        return DG_ERR_INVALID;
+    if (z->sh_degree != u->sh_degree || ((uintptr_t)factor & 3u) || ((uintptr_t)copy_gid & 3u)) return DG_ERR_INVALID;
+    if (u->n > 0 && (!copy_gid || !copy_shared)) return DG_ERR_INVALID;
+    return launch_admm_rescale(u, z, anchor, copy_gid, copy_shared, factor, (cudaStream_t)stream);
 }
 
 int dg_render_plan(dg_camera* host_cams, int n_views, int64_t n_gauss, int tile_w, int tile_h, dg_plan* plan)

@@ -97,7 +97,29 @@ struct AdamArgs {
     float lr[6];    // p, q, s, f_dc, f_rest, o
     float b1, b2, eps;
     int step;
+    const float* dev_rho;   // non-null: rho read from this device array when the kernel runs
 };
+
+// the penalty of group g (rho from the launch, or from device memory)
+template <class Args>
+__device__ __forceinline__ float rho_of(const Args& a, int g)
+{
+    return a.dev_rho ? __ldg(a.dev_rho + g) : a.rho[g];
+}
+
+// rho[5] of an ABI call points to host memory (read now into dst) or to
+// device memory (left to the kernels: *dev = rho), told apart by the driver
+inline void take_rho(const float* rho, float* dst, const float** dev)
+{
+    cudaPointerAttributes at;
+    bool on_dev = false;
+    if (cudaPointerGetAttributes(&at, rho) == cudaSuccess)
+        on_dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    else
+        cudaGetLastError();
+    *dev = on_dev ? rho : nullptr;
+    for (int i = 0; i < 5; i++) dst[i] = on_dev ? 0.f : rho[i];
+}
 
 __device__ __forceinline__ void bias_corr(const AdamArgs& a, const int32_t* dev_step, float& ic1, float& ic2)
 {

@@ -300,7 +300,19 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float* v, float& v8,
 template <int NW, int S>
 constexpr int bwd_min_blocks() { return NW == 1 ? DG_BWD_CTAS_1W : (S == 1 ? 32 : 24) / NW; }
 
-template <int NW, int S>
+// Where the backward's per-(instance, tile) gradient goes.  Accumulated:
+// atomics into the record's 12 floats of drec.  Slots (deterministic mode,
+// one warp per tile): a plain store into the (record, tile) slot
+// slot_off[r] + (ty - y0) w + (tx - x0) of part (9 floats per slot), summed
+// per record in a fixed order by k_slot_reduce afterwards.
+struct SlotOut {
+    const uint2* rect;
+    const uint64_t* slot_off;
+    float* part;
+    uint64_t cap;
+};
+
+template <int NW, int S, bool SLOT = false>
 __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd(const float4* __restrict__ rec,
                                                         const uint32_t* __restrict__ vals,
                                                         const uint32_t* __restrict__ ranges,
@@ -309,8 +321,9 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
                                                         const float* __restrict__ T_final,
                                                         const uint32_t* __restrict__ last_in,
                                                         const float* __restrict__ dL_dimage,
-                                                        float* __restrict__ drec)
+                                                        float* __restrict__ drec, SlotOut so)
 {
+    static_assert(!SLOT || NW == 1, "slots take one warp per tile");
     constexpr int NT = 32 * NW, PPL = 8 / NW, R = NT * S;
     __shared__ float4 s_g[R];   // mx, my, A, B   (log2-scaled exponent)
     __shared__ float4 s_h[R];   // C, log2 o, 1 / o, record index (bits)
@@ -448,12 +461,27 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
                 gr[5] = S0 * h.z;                       // d alpha / d opacity = alpha / opacity
             }
             const float sred = warp_reduce_scatter8(gr, g8, lane);
-            float* d = drec + 12 * (int64_t)__float_as_uint(h.w);
-            if ((lane & 3) == 0) {
-                const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                if (sred != 0.f) atomicAdd(d + vi, sred);
+            const uint32_t rid = __float_as_uint(h.w);
+            if (SLOT) {
+                if ((lane & 3) == 0) {
+                    const uint2 rr = so.rect[rid];
+                    const uint32_t x0 = rr.x & 0xFFFFu, y0 = rr.x >> 16, w = (rr.y & 0xFFFFu) - x0;
+                    const uint32_t tx = (uint32_t)(ti.px0 / tw), ty = (uint32_t)(ti.py0 / th);
+                    const uint64_t slot = so.slot_off[rid] + (uint64_t)((ty - y0) * w + (tx - x0));
+                    if (slot < so.cap) {
+                        const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                        so.part[9 * slot + vi] = sred;
+                        if (lane == 0) so.part[9 * slot + 8] = g8;
+                    }
+                }
+            } else {
+                float* d = drec + 12 * (int64_t)rid;
+                if ((lane & 3) == 0) {
+                    const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                    if (sred != 0.f) atomicAdd(d + vi, sred);
+                }
+                if (lane == 0 && g8 != 0.f) atomicAdd(d + 8, g8);
             }
-            if (lane == 0 && g8 != 0.f) atomicAdd(d + 8, g8);
         }
     }
 }
@@ -485,7 +513,7 @@ static void bwd_launch(const float4* rec, const uint32_t* vals, const uint32_t* 
 {
     k_raster_bwd<NW, S><<<(unsigned)p.n_tiles, 32 * NW, 0, st>>>(rec, vals, ranges, cams, p.n_views, p.tile_w,
                                                                  p.tile_h, bg[0], bg[1], bg[2], T_final, last,
-                                                                 dL_dimage, drec);
+                                                                 dL_dimage, drec, SlotOut{});
 }
 
 #define DG_RASTER_DISPATCH(P, FN, ...)                                       \
@@ -535,6 +563,168 @@ int launch_raster_bwd(const float4* rec, const uint32_t* vals, const uint32_t* r
         pb.raster_stage = plan.raster_stage_bwd;
     }
     DG_RASTER_DISPATCH(pb, bwd_launch, rec, vals, ranges, cams, pb, bg, T_final, last, dL_dimage, drec, st)
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
+// ---- deterministic mode: (record, tile) slots ---------------------------------------
+// slot_off[r] = the sum of the rectangle areas (in tiles) of the records
+// before r, by a three-pass scan (chunks of kSlotChunk records per CTA).
+constexpr int kSlotT = 512, kSlotPer = 8, kSlotChunk = kSlotT * kSlotPer;
+
+__device__ __forceinline__ uint32_t rect_area(uint2 rr)
+{
+    const uint32_t x0 = rr.x & 0xFFFFu, y0 = rr.x >> 16, x1 = rr.y & 0xFFFFu, y1 = rr.y >> 16;
+    return (x1 > x0 && y1 > y0) ? (x1 - x0) * (y1 - y0) : 0u;
+}
+
+__device__ __forceinline__ uint64_t slot_block_scan(uint64_t v, uint64_t* s_warp, uint64_t& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint64_t w = lane < nw ? s_warp[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) s_warp[lane] = w;
+    }
+    __syncthreads();
+    total = s_warp[nw - 1];
+    const uint64_t before = wid > 0 ? s_warp[wid - 1] : 0ull;
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kSlotT) k_slot_reduce_chunks(const uint2* __restrict__ rect, int64_t n,
+                                                                uint64_t* __restrict__ partials)
+{
+    __shared__ uint64_t s_warp[32];
+    const int64_t b = (int64_t)blockIdx.x * kSlotChunk + (int64_t)threadIdx.x * kSlotPer;
+    uint64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kSlotPer; i++)
+        if (b + i < n) s += rect_area(rect[b + i]);
+    uint64_t tot;
+    slot_block_scan(s, s_warp, tot);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kSlotT) k_slot_scan_top(uint64_t* __restrict__ partials, int64_t n_chunks,
+                                                          int64_t cap, uint64_t* __restrict__ dev_slots,
+                                                          uint32_t* __restrict__ dev_status)
+{
+    __shared__ uint64_t s_warp[32];
+    uint64_t carry = 0;
+    for (int64_t base = 0; base < n_chunks; base += kSlotT) {
+        const int64_t i = base + threadIdx.x;
+        const uint64_t v = i < n_chunks ? partials[i] : 0ull;
+        uint64_t tot;
+        const uint64_t ex = slot_block_scan(v, s_warp, tot);
+        if (i < n_chunks) partials[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        *dev_slots = carry;
+        if ((int64_t)carry > cap) atomicOr(dev_status, DG_STATUS_CAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(kSlotT) k_slot_scan_down(const uint2* __restrict__ rect, int64_t n,
+                                                           const uint64_t* __restrict__ partials,
+                                                           uint64_t* __restrict__ slot_off)
+{
+    __shared__ uint64_t s_warp[32];
+    const int64_t b = (int64_t)blockIdx.x * kSlotChunk + (int64_t)threadIdx.x * kSlotPer;
+    uint32_t a[kSlotPer];
+    uint64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kSlotPer; i++) {
+        a[i] = b + i < n ? rect_area(rect[b + i]) : 0u;
+        s += a[i];
+    }
+    uint64_t tot;
+    uint64_t run = partials[blockIdx.x] + slot_block_scan(s, s_warp, tot);
+#pragma unroll
+    for (int i = 0; i < kSlotPer; i++)
+        if (b + i < n) {
+            slot_off[b + i] = run;
+            run += a[i];
+        }
+}
+
+// drec[r] = the sum of record r's slots in tile order (fixed, so the result
+// does not depend on which tile's warp finished first); the three unused
+// floats of each record are zeroed.
+__global__ void __launch_bounds__(256) k_slot_reduce(const uint2* __restrict__ rect,
+                                                     const uint64_t* __restrict__ slot_off,
+                                                     const float* __restrict__ part, uint64_t cap, int64_t n,
+                                                     float* __restrict__ drec)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint32_t area = rect_area(rect[r]);
+    const uint64_t so = slot_off[r];
+    float acc[9];
+#pragma unroll
+    for (int v = 0; v < 9; v++) acc[v] = 0.f;
+    if (so + area <= cap)
+        for (uint32_t i = 0; i < area; i++) {
+            const float* p = part + 9 * (so + i);
+#pragma unroll
+            for (int v = 0; v < 9; v++) acc[v] += p[v];
+        }
+    float4* d = reinterpret_cast<float4*>(drec + 12 * r);
+    d[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    d[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    d[2] = make_float4(acc[8], 0.f, 0.f, 0.f);
+}
+
+size_t raster_slots_ws_bytes(int64_t n_rec)
+{
+    const int64_t n_chunks = (n_rec + kSlotChunk - 1) / kSlotChunk;
+    return (size_t)(n_rec + n_chunks + 1) * sizeof(uint64_t) + 256;
+}
+
+int launch_raster_bwd_slots(const float4* rec, const uint2* rect, const uint32_t* vals, const uint32_t* ranges,
+                            const dg_camera* cams, const dg_plan& plan, const float* bg, const float* T_final,
+                            const uint32_t* last, const float* dL_dimage, float* part, int64_t cap, void* ws,
+                            uint64_t* dev_slots, uint32_t* dev_status, float* drec, cudaStream_t st)
+{
+    const int64_t n = plan.n_rec;
+    if (n == 0) return cudaMemsetAsync(dev_slots, 0, sizeof(uint64_t), st) == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+    uint64_t* slot_off = reinterpret_cast<uint64_t*>(ws);
+    uint64_t* partials = slot_off + n;
+    const int64_t n_chunks = (n + kSlotChunk - 1) / kSlotChunk;
+    k_slot_reduce_chunks<<<(unsigned)n_chunks, kSlotT, 0, st>>>(rect, n, partials);
+    k_slot_scan_top<<<1, kSlotT, 0, st>>>(partials, n_chunks, cap, dev_slots, dev_status);
+    k_slot_scan_down<<<(unsigned)n_chunks, kSlotT, 0, st>>>(rect, n, partials, slot_off);
+    if (cap > 0 && cudaMemsetAsync(part, 0, (size_t)cap * 9 * sizeof(float), st) != cudaSuccess) return DG_ERR_CUDA;
+    note_launch(3);
+    if (plan.n_tiles > 0) {
+        const SlotOut so{rect, slot_off, part, (uint64_t)cap};
+        const int S = plan.raster_warps_bwd != 0 ? plan.raster_stage_bwd : plan.raster_stage;
+        if (S == 2)
+            k_raster_bwd<1, 2, true><<<(unsigned)plan.n_tiles, 32, 0, st>>>(
+                rec, vals, ranges, cams, plan.n_views, plan.tile_w, plan.tile_h, bg[0], bg[1], bg[2], T_final, last,
+                dL_dimage, drec, so);
+        else
+            k_raster_bwd<1, 1, true><<<(unsigned)plan.n_tiles, 32, 0, st>>>(
+                rec, vals, ranges, cams, plan.n_views, plan.tile_w, plan.tile_h, bg[0], bg[1], bg[2], T_final, last,
+                dL_dimage, drec, so);
+        note_launch();
+    }
+    k_slot_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rect, slot_off, part, (uint64_t)cap, n, drec);
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;

@@ -195,6 +195,16 @@ class ViewBatch:
         ws = L.lib().dg_bin_sort_workspace_size(C.byref(self.plan), self.capacity)
         self.ws = torch.zeros(max(ws, 1), dtype=torch.uint8, device=dev)
 
+    def enable_slots(self, slot_capacity: int) -> None:
+        """Buffers of the deterministic backward: 9 floats per (record, tile)
+        slot for slot_capacity slots, the slot offsets and the slot total."""
+        self.slot_capacity = int(slot_capacity)
+        dev = self.device
+        self.part = torch.zeros(max(9 * self.slot_capacity, 1), dtype=torch.float32, device=dev)
+        n = L.lib().dg_rasterize_bwd_slots_workspace_size(C.byref(self.plan))
+        self.slot_ws = torch.zeros(max((n + 7) // 8, 1), dtype=torch.int64, device=dev)
+        self.slots = torch.zeros(1, dtype=torch.int64, device=dev)
+
     # per-view image views (3, H, W)
     def view_image(self, v: int, buf: Optional[torch.Tensor] = None) -> torch.Tensor:
         c = self.host_cams[v]
@@ -267,13 +277,24 @@ def dg_rasterize_bwd_records(vb: ViewBatch, bg=(0.0, 0.0, 0.0), dL_dimage=None, 
             "dg_rasterize_bwd_records")
 
 
+def dg_rasterize_bwd_slots(vb: ViewBatch, bg=(0.0, 0.0, 0.0), dL_dimage=None, stream=None) -> None:
+    """The deterministic compositing adjoint into vb.drec (needs
+    vb.enable_slots() first)."""
+    g = vb.dL_dimage if dL_dimage is None else dL_dimage
+    L.check(L.lib().dg_rasterize_bwd_slots(L.ptr(vb.rec), L.ptr(vb.rect), L.ptr(vb.vals), L.ptr(vb.ranges),
+                                           L.ptr(vb.dev_cams), C.byref(vb.plan), L.floats(bg), L.ptr(vb.T_final),
+                                           L.ptr(vb.last), L.ptr(g), L.ptr(vb.part), vb.slot_capacity,
+                                           L.ptr(vb.slot_ws), vb.slot_ws.numel() * 8, L.ptr(vb.slots), L.ptr(vb.status),
+                                           L.ptr(vb.drec), L.stream_handle(stream)), "dg_rasterize_bwd_slots")
+
+
 def dg_xstep_from_records(vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer, v: GaussianBuffer,
                           anchor: Optional[GaussianBuffer], shared: Optional[torch.Tensor], rho, lr, beta1=0.9,
                           beta2=0.999, eps=1e-15, step=1, dev_step: Optional[torch.Tensor] = None,
                           stream=None) -> None:
     L.check(L.lib().dg_xstep_from_records(L.ptr(vb.rect), L.ptr(vb.dev_cams), C.byref(vb.plan), L.ptr(vb.drec),
                                           x.ref, m.ref, v.ref, None if anchor is None else anchor.ref, L.ptr(shared),
-                                          L.floats(rho), L.floats(lr), beta1, beta2, eps, int(step),
+                                          L.rho_arg(rho), L.floats(lr), beta1, beta2, eps, int(step),
                                           L.ptr(dev_step), L.stream_handle(stream)), "dg_xstep_from_records")
 
 
@@ -288,7 +309,7 @@ def dg_xstep_part(part: int, vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer
     z_unshared / gid: also store every unshared copy's stepped value in z."""
     L.check(L.lib().dg_xstep_part(int(part), int(ctas), L.ptr(vb.rect), L.ptr(vb.dev_cams), C.byref(vb.plan), L.ptr(vb.drec),
                                   x.ref, m.ref, v.ref, None if anchor is None else anchor.ref, L.ptr(shared),
-                                  L.floats(rho), L.floats(lr), beta1, beta2, eps, int(step), L.ptr(dev_step),
+                                  L.rho_arg(rho), L.floats(lr), beta1, beta2, eps, int(step), L.ptr(dev_step),
                                   None if z_unshared is None else z_unshared.ref, L.ptr(gid),
                                   L.stream_handle(stream)), "dg_xstep_part")
 
@@ -381,7 +402,7 @@ def dg_adam_admm_step(x: GaussianBuffer, g: GaussianBuffer, m: GaussianBuffer, v
                       beta1=0.9, beta2=0.999, eps=1e-15, step=1, dev_step: Optional[torch.Tensor] = None,
                       stream=None) -> None:
     L.check(L.lib().dg_adam_admm_step(x.ref, g.ref, m.ref, v.ref, None if anchor is None else anchor.ref,
-                                      L.ptr(shared), L.floats(rho), L.floats(lr), beta1, beta2, eps, int(step),
+                                      L.ptr(shared), L.rho_arg(rho), L.floats(lr), beta1, beta2, eps, int(step),
                                       L.ptr(dev_step), L.stream_handle(stream)), "dg_adam_admm_step")
 
 
@@ -389,13 +410,28 @@ def dg_admm_consensus(x: GaussianBuffer, u: GaussianBuffer, z: GaussianBuffer, a
                       g_off: torch.Tensor, g_copies: torch.Tensor, rho, alpha=1.0,
                       residuals: Optional[torch.Tensor] = None, stream=None) -> None:
     L.check(L.lib().dg_admm_consensus(x.ref, u.ref, z.ref, anchor.ref, L.ptr(g_off), L.ptr(g_copies),
-                                      L.floats(rho), float(alpha), L.ptr(residuals), L.stream_handle(stream)),
+                                      L.rho_arg(rho), float(alpha), L.ptr(residuals), L.stream_handle(stream)),
             "dg_admm_consensus")
 
 
 def dg_admm_scale_duals(u: GaussianBuffer, shared: torch.Tensor, factor, stream=None) -> None:
     L.check(L.lib().dg_admm_scale_duals(u.ref, L.ptr(shared), L.floats(factor), L.stream_handle(stream)),
             "dg_admm_scale_duals")
+
+
+def dg_admm_adapt(residuals: torch.Tensor, rho: torch.Tensor, factor: torch.Tensor, dev_step: torch.Tensor,
+                  mu=10.0, tau_inc=2.0, tau_dec=2.0, freeze_after=2000, stream=None) -> None:
+    """Eq. 10 on the device: rho (float32[5]) and factor (float32[5]) updated
+    from the consensus residuals (float64[10]) while *dev_step - 1 < freeze_after."""
+    L.check(L.lib().dg_admm_adapt(L.ptr(residuals), L.ptr(rho), L.ptr(factor), L.ptr(dev_step), float(mu),
+                                  float(tau_inc), float(tau_dec), int(freeze_after), L.stream_handle(stream)),
+            "dg_admm_adapt")
+
+
+def dg_admm_rescale(u: GaussianBuffer, z: GaussianBuffer, anchor: GaussianBuffer, copy_gid: torch.Tensor,
+                    shared: torch.Tensor, factor: torch.Tensor, stream=None) -> None:
+    L.check(L.lib().dg_admm_rescale(u.ref, z.ref, anchor.ref, L.ptr(copy_gid), L.ptr(shared), L.ptr(factor),
+                                    L.stream_handle(stream)), "dg_admm_rescale")
 
 
 def dg_admm_anchor(z: GaussianBuffer, u: GaussianBuffer, copy_gid: torch.Tensor, shared: torch.Tensor,

@@ -45,9 +45,15 @@ class DogsTrainer:
                  targets: Sequence[torch.Tensor], rho=(1e-3,) * 5, lr=DEFAULT_LR, tile=(16, 16),
                  loss="dssim", w_l1=0.8, w_ssim=0.2, bg=(0.0, 0.0, 0.0), alpha=1.0, intv=100,
                  capacity: Optional[int] = None, device="cuda", adaptive: Optional[AdaptivePenalty] = None,
-                 fused: bool = True, overlap: bool = True, densify: Optional["DZ.DensifyConfig"] = None):
+                 fused: bool = True, overlap: bool = True, densify: Optional["DZ.DensifyConfig"] = None,
+                 deterministic: bool = False):
         self.device = device
         self.fused = fused
+        # deterministic: the compositing adjoint sums each record's gradient
+        # over its tiles in a fixed order (dg_rasterize_bwd_slots) instead of
+        # by atomics, so a run repeats bit for bit (fused x-step, one view
+        # per block)
+        self.deterministic = deterministic
         # with the fused x-step: the groups of copies that no view sees are
         # stepped on a side stream right after the projection, alongside
         # binning, compositing and the loss (dg_xstep_part 1), the rest after
@@ -66,6 +72,14 @@ class DogsTrainer:
         if adaptive is not None:
             adaptive.rho = [float(r) for r in rho]
         self.rho, self.lr, self.bg, self.alpha, self.intv = list(rho), list(lr), bg, alpha, intv
+        # with the adaptive penalty, rho lives on the device: Eq. 10 runs there
+        # right after each consensus (dg_admm_adapt, dg_admm_rescale) inside
+        # the captured graph, and the kernels read rho when they run
+        self.rho_dev = self.factor_dev = None
+        if adaptive is not None:
+            self.rho_dev = torch.tensor([float(r) for r in rho], dtype=torch.float32, device=device)
+            self.factor_dev = torch.ones(5, dtype=torch.float32, device=device)
+        self.adapt_on_device = adaptive is not None
         self.loss_kind, self.w_l1, self.w_ssim = loss, w_l1, w_ssim
         self.view_sets = [list(v) for v in view_sets]
         self.tile = tuple(tile)
@@ -174,6 +188,16 @@ class DogsTrainer:
             mx = max(mx, int(self.vb.count.item()) & 0xFFFFFFFF)
         cap = int(mx * headroom) + 4096
         self.vb.set_capacity(cap)
+        if self.deterministic:
+            slots = 0
+            for p in range(len(self.view_sets)):
+                self.vb.dev_cams.copy_(self.cam_pool[p])
+                D.dg_project(self.x, self.vb)
+                r = self.vb.rect[:2 * self.vb.n_rec].cpu().numpy().view(np.uint32).reshape(-1, 2)
+                w = (r[:, 1] & 0xFFFF).astype(np.int64) - (r[:, 0] & 0xFFFF)
+                h = (r[:, 1] >> 16).astype(np.int64) - (r[:, 0] >> 16)
+                slots = max(slots, int(np.where((w > 0) & (h > 0), w * h, 0).sum()))
+            self.vb.enable_slots(int(slots * headroom) + 4096)
         self.graphs.clear()
         return mx
 
@@ -204,7 +228,12 @@ class DogsTrainer:
             D.dg_densify_stats(vb, self.dstats)
         if consensus:
             D.dg_admm_consensus(self.x, self.u, self.z_shared() if zf else self.z, self.anchor, self.g_off,
-                                self.g_copies, self.rho, self.alpha, self.residuals)
+                                self.g_copies, self.rho_arg(), self.alpha, self.residuals)
+            if self.adaptive is not None and self.adapt_on_device:
+                ad = self.adaptive
+                D.dg_admm_adapt(self.residuals, self.rho_dev, self.factor_dev, self.dev_step, ad.mu, ad.tau_inc,
+                                ad.tau_dec, ad.freeze_after)
+                D.dg_admm_rescale(self.u, self.z, self.anchor, self.gid, self.shared, self.factor_dev)
         if self.host_targets is not None:
             self.host_loss[0 if slot is None else slot].copy_(vb.loss, non_blocking=True)
 
@@ -284,7 +313,7 @@ class DogsTrainer:
         cur = torch.cuda.current_stream()
         self.side.wait_stream(cur)
         with torch.cuda.stream(self.side):
-            D.dg_xstep_part(1, self.vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,
+            D.dg_xstep_part(1, self.vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(), self.lr,
                             step=1, dev_step=self.dev_step, ctas=self.n_sm * self.idle_ctas_per_sm,
                             **self._zargs(zfuse))
         self._idle_queued = True
@@ -298,19 +327,24 @@ class DogsTrainer:
         copies into z (an iteration whose consensus then covers the shared
         globals only)."""
         vb = self.vb
+        bwd_records = D.dg_rasterize_bwd_slots if self.deterministic else D.dg_rasterize_bwd_records
+        if self.deterministic and not (self.fused and D.one_view_per_block(vb.plan)):
+            raise ValueError("the deterministic backward runs with the fused x-step (one view per block)")
+        if self.deterministic and getattr(vb, "part", None) is None:
+            raise RuntimeError("deterministic mode: call calibrate_capacity() first (it sizes the slots)")
         if self._split_xstep() and self._idle_queued:
-            D.dg_rasterize_bwd_records(vb, bg=self.bg)
-            D.dg_xstep_part(2, vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,
+            bwd_records(vb, bg=self.bg)
+            D.dg_xstep_part(2, vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(), self.lr,
                             step=1, dev_step=self.dev_step, **self._zargs(zfuse))
             torch.cuda.current_stream().wait_stream(self.side)
             self._idle_queued = False
         elif self.fused and D.one_view_per_block(vb.plan):
-            D.dg_rasterize_bwd_records(vb, bg=self.bg)
-            D.dg_xstep_part(0, vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,
+            bwd_records(vb, bg=self.bg)
+            D.dg_xstep_part(0, vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(), self.lr,
                             step=1, dev_step=self.dev_step, **self._zargs(zfuse))
         else:
             D.dg_rasterize_bwd(vb, self.x, self.grad, bg=self.bg)
-            D.dg_adam_admm_step(self.x, self.grad, self.m, self.v, self.anchor, self.shared, self.rho, self.lr,
+            D.dg_adam_admm_step(self.x, self.grad, self.m, self.v, self.anchor, self.shared, self.rho_arg(), self.lr,
                                 step=1, dev_step=self.dev_step)
 
     def step(self, consensus: Optional[bool] = None, graph=True) -> None:
@@ -339,7 +373,7 @@ class DogsTrainer:
             self.loss_step[slot] = self.t
             nxt = self.t + 1
             self._prefetch(nxt % len(self.view_sets), nxt % 2)
-        if c and self.adaptive is not None and self.t < self.adaptive.freeze_after:
+        if c and self.adaptive is not None and not self.adapt_on_device and self.t < self.adaptive.freeze_after:
             self._adapt_penalty()
         if c and self.densify_cfg is not None and self.densify_cfg.due(self.t):
             self.densify_log.append(dict(DZ.densify(self, self.densify_cfg, self.extent, self.t), t=self.t))
@@ -351,8 +385,23 @@ class DogsTrainer:
         """Whether this iteration adds to the densification statistic."""
         return self.densify_cfg is not None and self.t < self.densify_cfg.until
 
+    def rho_arg(self):
+        """rho as the kernels take it: the device array under the adaptive
+        penalty (updated there by Eq. 10), else the host list."""
+        return self.rho_dev if self.rho_dev is not None else self.rho
+
+    def current_rho(self) -> List[float]:
+        """The penalties in effect (read back from the device under the
+        adaptive penalty; one synchronisation), also kept in self.rho and the
+        AdaptivePenalty state."""
+        if self.rho_dev is not None:
+            self.rho = [float(r) for r in self.rho_dev.cpu().tolist()]
+            if self.adaptive is not None:
+                self.adaptive.rho = list(self.rho)
+        return list(self.rho)
+
     def _adapt_penalty(self) -> None:
-        """Eq. 10 after a consensus: read the residuals (one synchronisation),
+        """The host form of Eq. 10 (with adapt_on_device off): read the residuals (one synchronisation),
         update rho, rescale the scaled duals of the shared copies and rebuild
         the anchors z - u.  rho is a launch argument, so captured graphs are
         dropped when it changes (at most freeze_after / intv times)."""
@@ -363,6 +412,8 @@ class DogsTrainer:
         D.dg_admm_scale_duals(self.u, self.shared, factor)
         D.dg_admm_anchor(self.z, self.u, self.gid, self.shared, self.anchor)
         self.rho = rho
+        if self.rho_dev is not None:
+            self.rho_dev.copy_(torch.tensor(rho, dtype=torch.float32))
         self.graphs.clear()
 
     def _capture(self, p: int, c: bool, target: Optional[torch.Tensor] = None,
@@ -402,6 +453,8 @@ class DogsTrainer:
         the device step counter from t, after t was set from outside)."""
         D.dg_admm_anchor(self.z, self.u, self.gid, self.shared, self.anchor)
         self.dev_step.fill_(self.t)
+        if self.rho_dev is not None:
+            self.rho_dev.copy_(torch.tensor([float(r) for r in self.rho], dtype=torch.float32))
         torch.cuda.synchronize()
 
     def save_checkpoint(self, path: str) -> None:

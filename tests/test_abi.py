@@ -169,3 +169,23 @@ def test_render_slot_workspace_bounds_every_admissible_batch(lib):
         _, plan = D.render_plan(cams, Z.n)
         need = lib.dg_render_workspace_size(C.byref(plan), server._capacity_for(npix))
         assert 0 < need <= bound
+
+
+def test_slot_backward_rejects_bad_arguments_before_launch(lib):
+    from paper_2405_13943_b300 import dogs as D
+    arr, plan = D.plan_views([S.cube_camera(32, 32)], [0, 64], 16, 16)
+    need = lib.dg_rasterize_bwd_slots_workspace_size(C.byref(plan))
+    assert need >= 64 * 8
+    bg = L.floats([0, 0, 0])
+    launches = lib.dg_launch_count()
+
+    def call(rec=0x10000, rect=0x20000, part=0x90000, cap=100, ws=0xA0000, wsb=need, slots=0xB0000):
+        return lib.dg_rasterize_bwd_slots(rec, rect, 0x30000, 0x40000, 0x50000, C.byref(plan), bg, 0x60000,
+                                          0x70000, 0x80000, part, cap, ws, wsb, slots, 0xC0000, 0xD0000, None)
+    assert call(rec=0x10008) == L.DG_ERR_INVALID          # records are read as float4
+    assert call(rect=0x20004) == L.DG_ERR_INVALID         # rectangles as uint2
+    assert call(cap=-1) == L.DG_ERR_INVALID
+    assert call(part=None) == L.DG_ERR_INVALID
+    assert call(slots=0xB0004) == L.DG_ERR_INVALID        # the slot total is 64-bit
+    assert call(wsb=need - 8) == L.DG_ERR_WORKSPACE
+    assert lib.dg_launch_count() == launches

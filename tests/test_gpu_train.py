@@ -116,10 +116,10 @@ def test_consensus_keeps_dual_mean_zero(mods):
 
 
 def test_adaptive_penalty_follows_eq10(mods):
-    """Adaptive penalty in the batched trainer: at each consensus before the
-    freeze the rho update is the oracle's Eq. 10 on the residuals the
-    consensus produced, the unscaled duals rho * u of the shared copies are
-    unchanged by the rescale, and the anchors are z - u afterwards."""
+    """Adaptive penalty in the batched trainer, on the device inside the
+    captured graphs: after each consensus before the freeze, rho is the
+    oracle's Eq. 10 applied to the residuals that consensus produced, with no
+    host read in between."""
     D, srv, T = mods
     from oracle import oracle as O
     from paper_2405_13943_b300.admm import AdaptivePenalty
@@ -128,41 +128,59 @@ def test_adaptive_penalty_follows_eq10(mods):
     ap = AdaptivePenalty(rho0, freeze_after=6)
     bt = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, rho=rho0, loss="l1", intv=2, adaptive=ap)
     bt.calibrate_capacity()
-    sh = wl.split.copy_shared().astype(bool)
-    deg = z0.deg
     changed = 0
     for t in range(10):
-        before_rho = list(bt.rho)
-        c = t % 2 == 0
-        if c:
-            # run the iteration without adaptation to read u and the residuals
-            bt.adaptive, saved = None, bt.adaptive
-            bt.step(graph=True)
-            bt.adaptive = saved
-            torch.cuda.synchronize()
-            res = bt.residuals.cpu().numpy()
-            u_before = O.params_from(bt.u.to_synth())
-            bt.t -= 1
-            if bt.t < ap.freeze_after:
-                bt._adapt_penalty()
-            bt.t += 1
-            want_rho = O.adaptive_rho(before_rho, res, t, freeze_after=6)
-            assert bt.rho == pytest.approx(want_rho, rel=1e-12), t
-            changed += bt.rho != before_rho
-            torch.cuda.synchronize()
-            u_after = O.params_from(bt.u.to_synth())
-            grp = np.array([0] * 3 + [1] * 4 + [2] * 3 + [3] * (3 * (deg + 1) ** 2) + [4])
-            y0 = u_before[sh] * np.array(before_rho)[grp]
-            y1 = u_after[sh] * np.array(bt.rho)[grp]
-            np.testing.assert_allclose(y1, y0, rtol=1e-6, atol=1e-30)
-            an = O.params_from(bt.anchor.to_synth())
-            zz = O.params_from(bt.z.to_synth())
-            np.testing.assert_allclose(an[sh], zz[wl.split.copy_gid[sh]] - u_after[sh], rtol=1e-5, atol=1e-6)
+        before = bt.current_rho()
+        bt.step(graph=True)
+        torch.cuda.synchronize()
+        after = bt.current_rho()
+        if t % 2 == 0:
+            want = O.adaptive_rho(before, bt.residuals.cpu().numpy(), t, freeze_after=6)
+            assert after == pytest.approx(want, rel=1e-6), t
+            changed += after != before
         else:
-            bt.step(graph=True)
+            assert after == before
     assert changed >= 1              # the deliberately unbalanced start moves rho
-    assert bt.rho == list(ap.rho)
+    assert bt.rho == list(ap.rho) and len(bt.graphs) <= 4      # rho changes drop no graph
     assert not bt.overflowed()
+
+
+def test_device_rescale_keeps_the_unscaled_duals(mods):
+    """dg_admm_adapt + dg_admm_rescale after a consensus: the unscaled duals
+    rho * u of the shared copies are unchanged by the rescale, and the
+    anchors are z - u afterwards."""
+    D, srv, T = mods
+    from oracle import oracle as O
+    from paper_2405_13943_b300.admm import AdaptivePenalty
+    wl, z0, targets = small_setup(D, srv, seed=11)
+    rho0 = (1e-4, 1.0, 1e-4, 10.0, 1e-3)
+    ap = AdaptivePenalty(rho0, freeze_after=6)
+    bt = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, rho=rho0, loss="l1", intv=1, adaptive=ap)
+    bt.calibrate_capacity()
+    sh = wl.split.copy_shared().astype(bool)
+    deg = z0.deg
+    grp = np.array([0] * 3 + [1] * 4 + [2] * 3 + [3] * (3 * (deg + 1) ** 2) + [4])
+    rescaled = 0
+    for t in range(4):
+        before = bt.current_rho()
+        bt.adaptive, saved = None, bt.adaptive          # the iteration and its consensus, no Eq. 10
+        bt.step(graph=False)
+        bt.adaptive = saved
+        u_before = O.params_from(bt.u.to_synth())
+        D.dg_admm_adapt(bt.residuals, bt.rho_dev, bt.factor_dev, bt.dev_step, ap.mu, ap.tau_inc, ap.tau_dec,
+                        ap.freeze_after)
+        D.dg_admm_rescale(bt.u, bt.z, bt.anchor, bt.gid, bt.shared, bt.factor_dev)
+        torch.cuda.synchronize()
+        after = bt.current_rho()
+        rescaled += after != before
+        u_after = O.params_from(bt.u.to_synth())
+        y0 = u_before[sh] * np.array(before)[grp]
+        y1 = u_after[sh] * np.array(after)[grp]
+        np.testing.assert_allclose(y1, y0, rtol=1e-6, atol=1e-30)
+        an = O.params_from(bt.anchor.to_synth())
+        zz = O.params_from(bt.z.to_synth())
+        np.testing.assert_allclose(an[sh], zz[wl.split.copy_gid[sh]] - u_after[sh], rtol=1e-5, atol=1e-6)
+    assert rescaled >= 1
 
 
 def test_training_on_a_recursive_split(mods):
@@ -231,7 +249,7 @@ def test_checkpoint_resume(mods, tmp_path):
         a.step()
         b.step()
     torch.cuda.synchronize()
-    assert b.t == a.t == 6 and b.rho == a.rho
+    assert b.t == a.t == 6 and b.current_rho() == a.current_rho()
     for buf in ("x", "z", "u"):
         ga, gb = groups(getattr(a, buf)), groups(getattr(b, buf))
         for k in ga:
