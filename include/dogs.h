@@ -394,6 +394,33 @@ int dg_densify_emit(const dg_gaussians* z, const int32_t* codes, const uint32_t*
                     const float* normals, dg_gaussians* out, int32_t* src, uint8_t* original,
                     void* stream);
 
+/* The copy layout of the densified set, built on the device in the old
+ * layout's order: each Gaussian's outputs take its place.  From the old
+ * layout (n_global globals with their sharing map g_off[n_global + 1] /
+ * g_copies, and copy_gid[n_copies] listing the blocks' copies, blocks
+ * concatenated) and dg_densify_decide's codes and offsets:
+ *   copy_offsets[c] (uint32[n_copies + 1]): exclusive sum over the old
+ *     copies of their Gaussian's output count, total last; old copy c of
+ *     global p becomes the new copies copy_offsets[c] + h, h < outputs of p,
+ *     in the same block (block k's new range starts at
+ *     copy_offsets[old blk_off[k]]; its shared copies still come first);
+ *   new_copy_gid[copy_offsets[c] + h] = offsets[p] + h;
+ *   new_g_off / new_g_copies: the new sharing map (int64[n_new + 1] /
+ *     int32), each new global's copies in ascending block;
+ *   carry[new copy] = the old copy whose optimiser state and dual it takes
+ *     over (the Gaussian is its parent itself: KEEP, or the first output of
+ *     CLONE), else -1.
+ * Shared globals stay numbered first (their outputs are shared, with the
+ * parent's blocks).  new_g_copies, new_copy_gid and carry hold
+ * copy_offsets[n_copies] entries (at most 2 n_copies).  ws:
+ * dg_densify_layout_workspace_size bytes, 256-byte aligned.  Device
+ * pointers; n_global and n_copies below 2^30. */
+size_t dg_densify_layout_workspace_size(int64_t n_global, int64_t n_copies);
+int dg_densify_layout(const int32_t* codes, const uint32_t* offsets, int64_t n_global, const int64_t* g_off,
+                      const int32_t* g_copies, const int32_t* copy_gid, int64_t n_copies,
+                      int64_t* new_g_off, int32_t* new_g_copies, int32_t* new_copy_gid, int32_t* carry,
+                      uint32_t* copy_offsets, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- 8-bit images (training targets cross the host link as bytes) -------
  * dg_image_u8_to_f32: dst[i] = src[i] / 255 for i < n (device; src 4-byte
  * and dst 16-byte aligned).  dg_image_f32_to_u8:

@@ -64,6 +64,9 @@ _vp = C.c_void_p
 _SIGS = {
     "dg_version": (C.c_char_p, []),
     "dg_launch_count": (C.c_uint64, []),
+    "dg_densify_layout_workspace_size": (C.c_size_t, [C.c_int64, C.c_int64]),
+    "dg_densify_layout": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp,
+                                    C.c_size_t, _vp]),
     "dg_rasterize_bwd_slots_workspace_size": (C.c_size_t, [C.POINTER(DgPlan)]),
     "dg_rasterize_bwd_slots": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(DgPlan), C.POINTER(C.c_float), _vp, _vp,
                                          _vp, _vp, C.c_int64, _vp, C.c_size_t, _vp, _vp, _vp, _vp]),

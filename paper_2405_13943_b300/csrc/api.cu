@@ -18,6 +18,11 @@ int launch_bin_sort(const float4*, const uint2*, const dg_camera*, const dg_plan
                     uint32_t*, uint32_t*, void*, uint32_t*, cudaStream_t);
 int bin_sort_init();
 size_t raster_slots_ws_bytes(int64_t n_rec);
+size_t densify_layout_ws_bytes(int64_t n_g, int64_t n_c);
+int launch_densify_layout(const int32_t* codes, const uint32_t* offsets, int64_t n_g, const int64_t* g_off,
+                          const int32_t* g_copies, const int32_t* copy_gid, int64_t n_c, int64_t* new_g_off,
+                          int32_t* new_g_copies, int32_t* new_copy_gid, int32_t* carry, uint32_t* copy_off,
+                          void* ws, cudaStream_t st);
 int launch_raster_bwd_slots(const float4* rec, const uint2* rect, const uint32_t* vals, const uint32_t* ranges,
                             const dg_camera* cams, const dg_plan& plan, const float* bg, const float* T_final,
                             const uint32_t* last, const float* dL_dimage, float* part, int64_t cap, void* ws,
@@ -452,6 +457,28 @@ int dg_densify_emit(const dg_gaussians* z, const int32_t* codes, const uint32_t*
     if (!valid_gauss(z) || !valid_gauss(out) || out->sh_degree != z->sh_degree) return DG_ERR_INVALID;
     if (z->n > 0 && (!codes || !offsets || !normals || !src || !original)) return DG_ERR_INVALID;
     return launch_densify_emit(z, codes, offsets, normals, out, src, original, (cudaStream_t)stream);
+}
+
+size_t dg_densify_layout_workspace_size(int64_t n_global, int64_t n_copies)
+{
+    if (n_global < 0 || n_copies < 0) return 0;
+    return densify_layout_ws_bytes(n_global, n_copies);
+}
+
+int dg_densify_layout(const int32_t* codes, const uint32_t* offsets, int64_t n_global, const int64_t* g_off,
+                      const int32_t* g_copies, const int32_t* copy_gid, int64_t n_copies, int64_t* new_g_off,
+                      int32_t* new_g_copies, int32_t* new_copy_gid, int32_t* carry, uint32_t* copy_offsets,
+                      void* ws, size_t ws_bytes, void* stream)
+{
+    if (n_global < 0 || n_copies < 0 || n_global >= ((int64_t)1 << 30) || n_copies >= ((int64_t)1 << 30))
+        return DG_ERR_INVALID;
+    if (!offsets || !new_g_off || !copy_offsets || !ws) return DG_ERR_INVALID;
+    if (n_global > 0 && (!codes || !g_off || !g_copies)) return DG_ERR_INVALID;
+    if (n_copies > 0 && (!copy_gid || !new_g_copies || !new_copy_gid || !carry)) return DG_ERR_INVALID;
+    if (((uintptr_t)new_g_off & 7u) || ((uintptr_t)g_off & 7u) || ((uintptr_t)ws & 255u)) return DG_ERR_INVALID;
+    if (ws_bytes < densify_layout_ws_bytes(n_global, n_copies)) return DG_ERR_WORKSPACE;
+    return launch_densify_layout(codes, offsets, n_global, g_off, g_copies, copy_gid, n_copies, new_g_off,
+                                 new_g_copies, new_copy_gid, carry, copy_offsets, ws, (cudaStream_t)stream);
 }
 
 int dg_gather_rows(const dg_gaussians* src, const int32_t* idx, dg_gaussians* dst, void* stream)

@@ -237,6 +237,12 @@ __global__ void __launch_bounds__(kDensifyThreads) k_reset_opacity(GView g, floa
 
 static unsigned blocks_of(int64_t n) { return (unsigned)((n + kDensifyThreads - 1) / kDensifyThreads); }
 
+__global__ void k_dl_close(const uint32_t* __restrict__ offsets, int64_t n_g, const uint32_t* __restrict__ copy_off,
+                           int64_t n_c, int64_t* __restrict__ new_g_off)
+{
+    new_g_off[offsets[n_g]] = (int64_t)copy_off[n_c];
+}
+
 int launch_densify_stats(const uint2* rect, const float* drec, const dg_camera* cams, const dg_plan& plan,
                          float* stats, cudaStream_t st)
 {
@@ -275,6 +281,112 @@ int launch_densify_emit(const dg_gaussians* z, const int32_t* codes, const uint3
     const int np = 3 * (z->sh_degree + 1) * (z->sh_degree + 1);
     k_densify_emit<<<blocks_of(z->n), kDensifyThreads, 0, st>>>(gview(z), codes, offsets, normals, gview(out), src,
                                                                 original, np);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
+// ---- the densified copy layout, in place of the old one ------------------------------
+// Each Gaussian's outputs take its place: global p's outputs are the new
+// globals offsets[p] + h, and each of p's copies c (block k) becomes the new
+// copies copy_off[c] + h of block k, copy_off being the exclusive scan over
+// the old copies (blocks concatenated) of their Gaussian's output count.
+__device__ __forceinline__ uint32_t n_outputs(int32_t code)
+{
+    return code == DG_DENSIFY_PRUNE ? 0u : (code == DG_DENSIFY_KEEP ? 1u : 2u);
+}
+
+__global__ void __launch_bounds__(kDensifyThreads) k_dl_copy_counts(const int32_t* __restrict__ copy_gid, int64_t n_c,
+                                                                    const int32_t* __restrict__ codes,
+                                                                    uint32_t* __restrict__ cnt)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n_c) cnt[c] = n_outputs(codes[copy_gid[c]]);
+}
+
+__global__ void __launch_bounds__(kDensifyThreads) k_dl_global_counts(const int64_t* __restrict__ g_off, int64_t n_g,
+                                                                      const int32_t* __restrict__ codes,
+                                                                      uint32_t* __restrict__ cnt)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n_g) cnt[p] = n_outputs(codes[p]) * (uint32_t)(g_off[p + 1] - g_off[p]);
+}
+
+__global__ void __launch_bounds__(kDensifyThreads) k_dl_emit(const int64_t* __restrict__ g_off,
+                                                             const int32_t* __restrict__ g_copies, int64_t n_g,
+                                                             const int32_t* __restrict__ codes,
+                                                             const uint32_t* __restrict__ offsets,
+                                                             const uint32_t* __restrict__ copy_off,
+                                                             const uint32_t* __restrict__ gscan,
+                                                             int64_t* __restrict__ new_g_off,
+                                                             int32_t* __restrict__ new_g_copies,
+                                                             int32_t* __restrict__ new_copy_gid,
+                                                             int32_t* __restrict__ carry)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_g) return;
+    const int32_t code = codes[p];
+    const uint32_t nout = n_outputs(code);
+    const int64_t b = g_off[p];
+    const uint32_t np = (uint32_t)(g_off[p + 1] - b);
+    for (uint32_t h = 0; h < nout; h++) {
+        const int64_t j = (int64_t)offsets[p] + h;
+        const int64_t base = (int64_t)gscan[p] + (int64_t)h * np;
+        new_g_off[j] = base;
+        for (uint32_t i = 0; i < np; i++) {
+            const int32_t c = g_copies[b + i];
+            const int64_t nc = (int64_t)copy_off[c] + h;
+            new_g_copies[base + i] = (int32_t)nc;
+            new_copy_gid[nc] = (int32_t)j;
+            carry[nc] = (h == 0 && code != DG_DENSIFY_SPLIT) ? c : -1;
+        }
+    }
+}
+
+// exclusive scan of n uint32 into out[0..n] (total at out[n]), ws: partials
+static void scan_u32(const uint32_t* cnt, int64_t n, uint32_t* out, uint32_t* partials, cudaStream_t st)
+{
+    const int64_t n_chunks = (n + kScanChunkN - 1) / kScanChunkN;
+    k_dscan_reduce<<<(unsigned)n_chunks, kScanT, 0, st>>>(cnt, n, partials);
+    k_dscan_top<<<1, kScanT, 0, st>>>(partials, n_chunks);
+    k_dscan_down<<<(unsigned)n_chunks, kScanT, 0, st>>>(cnt, n, partials, out);
+    note_launch(3);
+}
+
+size_t densify_layout_ws_bytes(int64_t n_g, int64_t n_c)
+{
+    const auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    return up(sizeof(uint32_t) * (size_t)(n_c > n_g ? n_c : n_g)) + up(sizeof(uint32_t) * (size_t)(n_g + 1)) +
+           up(densify_scan_ws_bytes(n_c > n_g ? n_c : n_g));
+}
+
+int launch_densify_layout(const int32_t* codes, const uint32_t* offsets, int64_t n_g, const int64_t* g_off,
+                          const int32_t* g_copies, const int32_t* copy_gid, int64_t n_c, int64_t* new_g_off,
+                          int32_t* new_g_copies, int32_t* new_copy_gid, int32_t* carry, uint32_t* copy_off,
+                          void* ws, cudaStream_t st)
+{
+    const auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    char* w = (char*)ws;
+    uint32_t* cnt = (uint32_t*)w;
+    uint32_t* gscan = (uint32_t*)(w + up(sizeof(uint32_t) * (size_t)(n_c > n_g ? n_c : n_g)));
+    uint32_t* partials = (uint32_t*)((char*)gscan + up(sizeof(uint32_t) * (size_t)(n_g + 1)));
+    if (n_c == 0) {
+        if (cudaMemsetAsync(copy_off, 0, sizeof(uint32_t), st) != cudaSuccess) return DG_ERR_CUDA;
+    } else {
+        k_dl_copy_counts<<<blocks_of(n_c), kDensifyThreads, 0, st>>>(copy_gid, n_c, codes, cnt);
+        note_launch();
+        scan_u32(cnt, n_c, copy_off, partials, st);
+    }
+    if (n_g > 0) {
+        k_dl_global_counts<<<blocks_of(n_g), kDensifyThreads, 0, st>>>(g_off, n_g, codes, cnt);
+        note_launch();
+        scan_u32(cnt, n_g, gscan, partials, st);
+        k_dl_emit<<<blocks_of(n_g), kDensifyThreads, 0, st>>>(g_off, g_copies, n_g, codes, offsets, copy_off, gscan,
+                                                              new_g_off, new_g_copies, new_copy_gid, carry);
+        note_launch();
+    }
+    // the closing offset of the new sharing map: the total of the new copies
+    k_dl_close<<<1, 1, 0, st>>>(offsets, n_g, copy_off, n_c, new_g_off);
     note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;

@@ -9,8 +9,12 @@ consensus, `densify(trainer, cfg)`:
      copies (dg_densify_decide) and writes the densified global set in place
      order (dg_densify_emit, split children from seeded normals);
   2. gives every new Gaussian its parent's sharing set (the blocks that held
-     the parent) and rebuilds the copy layout with the same numbering rule
-     as the initial split (shared globals first, Z-order; synth.split_layout);
+     the parent) and builds the copy layout: by default on the device in the
+     old layout's order, each Gaussian's outputs in its place
+     (dg_densify_layout: a few linear passes; shared globals stay first and
+     each block's copies keep their order), or with layout="resort" on the
+     host with the initial split's numbering rule (shared globals first,
+     Z-order of the new positions; dg_layout, as synth.split_layout);
   3. moves the state (dg_gather_rows): z from the emitted set; for every new
      copy whose Gaussian is its parent itself and whose parent had a copy in
      the same block, that copy's x, Adam moments and scaled dual; other
@@ -44,6 +48,7 @@ class DensifyConfig:
     seed: int = 0                   # seed of the split normals (advanced per densification)
     opacity_reset: int = 3000       # cap every opacity at reset_cap every this many iterations (0: never)
     reset_cap: float = 0.01
+    layout: str = "inplace"         # "inplace": device, old order kept; "resort": host, initial numbering rule
 
     def due(self, t: int) -> bool:
         return self.start <= t < self.until and t % self.interval == 0
@@ -130,7 +135,12 @@ def densify(tr, cfg: DensifyConfig, extent: float, step_seed: int) -> Dict:
     gen.manual_seed(int(cfg.seed) * 1000003 + int(step_seed))
     normals = torch.randn(max(z.n, 1) * 6, device=dev, generator=gen, dtype=torch.float32)
     z_tmp, src, orig = D.dg_densify_emit(z, codes, offsets, normals, n_out)
+    if cfg.layout == "inplace":
+        c = torch.bincount(codes.long(), minlength=4).cpu().numpy()
+        return _densify_inplace(tr, z, codes, offsets, z_tmp, n_out, c, t0)
     c = np.bincount(codes.cpu().numpy(), minlength=4)
+    if cfg.layout != "resort":
+        raise ValueError(f"unknown densification layout {cfg.layout!r}")
     src_h = src.cpu().numpy().astype(np.int64)
     orig_h = orig.cpu().numpy().astype(bool)
     t1 = time.perf_counter()
@@ -168,6 +178,47 @@ def densify(tr, cfg: DensifyConfig, extent: float, step_seed: int) -> Dict:
             "carried_copies": int((carry >= 0).sum().item()),
             "seconds": {"decide_emit": round(t1 - t0, 3), "layout": round(t2 - t1, 3), "state": round(t3 - t2, 3),
                         "install": round(t4 - t3, 3)}}
+
+
+def _densify_inplace(tr, z, codes, offsets, z_new, n_out: int, c, t0: float) -> Dict:
+    """Steps 2-4 with the layout built on the device in the old order: z_new
+    (the emitted set) is already in the new numbering."""
+    dev = z.data.device
+    old = tr.split
+    torch.cuda.synchronize()
+    t_de = time.perf_counter()
+    new_g_off, new_g_cp, new_gid, carry, copy_off = D.dg_densify_layout(codes, offsets, tr.g_off, tr.g_copies,
+                                                                        tr.gid)
+    blk_old = torch.from_numpy(np.asarray(old.blk_off, np.int64)).to(dev)
+    nsh_old = torch.from_numpy(np.asarray(old.blk_nshared, np.int64)).to(dev)
+    bo = copy_off[blk_old].cpu().numpy().astype(np.int64)
+    sh_end = copy_off[blk_old[:-1] + nsh_old].cpu().numpy().astype(np.int64)
+    n_shared = int(offsets[int(old.n_shared_globals)].item()) & 0xFFFFFFFF
+    new_split = S.BlockSplit(new_gid.cpu().numpy(), bo, sh_end - bo[:-1], new_g_off.cpu().numpy(),
+                             new_g_cp.cpu().numpy(), n_shared, old.cells, old.band)
+    t1 = time.perf_counter()
+    n_c = new_split.n_copies
+    x_new = D.GaussianBuffer(n_c, z.deg, dev)
+    D.dg_gather_rows(z_new, new_gid, x_new)           # every copy from its Gaussian ...
+    D.dg_gather_rows(tr.x, carry, x_new)              # ... the carried ones from their old copy
+    bufs = {}
+    for name in ("m", "v", "u"):
+        b = D.GaussianBuffer(n_c, z.deg, dev)         # zeros where nothing is carried
+        D.dg_gather_rows(getattr(tr, name), carry, b)
+        bufs[name] = b
+    carried = int((carry >= 0).sum().item())
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    tr.install_split(new_split, z_new, x_new, bufs["m"], bufs["v"], bufs["u"],
+                     device_maps={"gid": new_gid, "g_off": new_g_off, "g_copies": new_g_cp})
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    return {"before": int(z.n), "after": int(n_out), "keep": int(c[D.L.DG_DENSIFY_KEEP]),
+            "prune": int(c[D.L.DG_DENSIFY_PRUNE]), "clone": int(c[D.L.DG_DENSIFY_CLONE]),
+            "split": int(c[D.L.DG_DENSIFY_SPLIT]), "copies": int(n_c), "carried_copies": carried,
+            "layout": "inplace",
+            "seconds": {"decide_emit": round(t_de - t0, 3), "layout": round(t1 - t_de, 3),
+                        "state": round(t3 - t1, 3), "install": round(t4 - t3, 3)}}
 
 
 def native_layout(xy: np.ndarray, member: np.ndarray, cells: np.ndarray, band: float, K: Optional[int] = None):

@@ -354,6 +354,31 @@ def dg_densify_emit(z: GaussianBuffer, codes: torch.Tensor, offsets: torch.Tenso
     return out, src[:n_out], orig[:n_out]
 
 
+def dg_densify_layout(codes: torch.Tensor, offsets: torch.Tensor, g_off: torch.Tensor, g_copies: torch.Tensor,
+                      copy_gid: torch.Tensor, stream=None):
+    """The densified copy layout in the old layout's order (device tensors):
+    (new_g_off int64[n_new + 1], new_g_copies, new_copy_gid, carry int32[n_new_copies],
+    copy_offsets uint32-in-int32[n_copies + 1])."""
+    n_g, n_c = int(g_off.numel()) - 1, int(copy_gid.numel())
+    dev = g_off.device
+    n_new = int(offsets[n_g].item()) & 0xFFFFFFFF
+    cap = max(2 * n_c, 1)
+    new_g_off = torch.empty(n_new + 1, dtype=torch.int64, device=dev)
+    new_g_copies = torch.empty(cap, dtype=torch.int32, device=dev)
+    new_copy_gid = torch.empty(cap, dtype=torch.int32, device=dev)
+    carry = torch.empty(cap, dtype=torch.int32, device=dev)
+    copy_off = torch.empty(n_c + 1, dtype=torch.int32, device=dev)
+    wsb = int(L.lib().dg_densify_layout_workspace_size(n_g, n_c))
+    ws = torch.empty(max(wsb, 256) + 256, dtype=torch.uint8, device=dev)
+    wp = (ws.data_ptr() + 255) & ~255
+    L.check(L.lib().dg_densify_layout(L.ptr(codes), L.ptr(offsets), n_g, L.ptr(g_off), L.ptr(g_copies),
+                                      L.ptr(copy_gid), n_c, L.ptr(new_g_off), L.ptr(new_g_copies),
+                                      L.ptr(new_copy_gid), L.ptr(carry), L.ptr(copy_off), wp, wsb,
+                                      L.stream_handle(stream)), "dg_densify_layout")
+    n_new_c = int(copy_off[n_c].item()) & 0xFFFFFFFF
+    return new_g_off, new_g_copies[:n_new_c], new_copy_gid[:n_new_c], carry[:n_new_c], copy_off
+
+
 def dg_gather_rows(src: GaussianBuffer, idx: torch.Tensor, dst: GaussianBuffer, stream=None) -> None:
     """dst row r = src row idx[r]; rows with idx[r] < 0 are left unchanged."""
     L.check(L.lib().dg_gather_rows(src.ref, L.ptr(idx), dst.ref, L.stream_handle(stream)), "dg_gather_rows")

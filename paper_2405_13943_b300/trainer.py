@@ -112,7 +112,7 @@ class DogsTrainer:
     # ---- the block layout and the state on it --------------------------------------
     def install_split(self, split: S.BlockSplit, z: D.GaussianBuffer, x: D.GaussianBuffer, m: D.GaussianBuffer,
                       v: D.GaussianBuffer, u: D.GaussianBuffer, capacity: Optional[int] = None,
-                      calibrate: bool = True) -> None:
+                      calibrate: bool = True, device_maps: Optional[Dict[str, torch.Tensor]] = None) -> None:
         """Take a block layout with its global model, copies, Adam moments and
         scaled duals: the sharing map, the anchors z - u, the batch plan for
         the view sets and (after a first install, unless the caller fills the
@@ -130,10 +130,18 @@ class DogsTrainer:
         ns = int(split.n_shared_globals)
         self._shared_first = bool((cnt[:ns] > 1).all() and (cnt[ns:] <= 1).all())
         self.n_shared_globals = ns
-        self.gid = torch.from_numpy(split.copy_gid.astype(np.int32)).to(dev)
-        self.shared = torch.from_numpy(split.copy_shared()).to(dev)
-        self.g_off = torch.from_numpy(split.g_off.astype(np.int64)).to(dev)
-        self.g_copies = torch.from_numpy(split.g_copies.astype(np.int32)).to(dev)
+        if device_maps is not None:
+            # the layout's arrays already on the device (as the split holds them): no upload
+            self.gid, self.g_off, self.g_copies = device_maps["gid"], device_maps["g_off"], device_maps["g_copies"]
+            self.shared = torch.zeros(split.n_copies, dtype=torch.uint8, device=dev)
+            for k in range(split.K):
+                b = int(split.blk_off[k])
+                self.shared[b:b + int(split.blk_nshared[k])] = 1
+        else:
+            self.gid = torch.from_numpy(split.copy_gid.astype(np.int32)).to(dev)
+            self.shared = torch.from_numpy(split.copy_shared()).to(dev)
+            self.g_off = torch.from_numpy(split.g_off.astype(np.int64)).to(dev)
+            self.g_copies = torch.from_numpy(split.g_copies.astype(np.int32)).to(dev)
         self.z, self.x, self.m, self.v, self.u = z, x, m, v, u
         self.grad, self.anchor = x.like(), x.like()
         D.dg_admm_anchor(self.z, self.u, self.gid, self.shared, self.anchor)

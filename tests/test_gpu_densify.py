@@ -159,14 +159,15 @@ def test_gather_rows_leaves_negative_rows(mods):
         np.testing.assert_array_equal(pb[r], p0[r] if idx[r] < 0 else pa[idx[r]])
 
 
-def test_trainer_densifies_under_consensus(mods):
+@pytest.mark.parametrize("layout", ["inplace", "resort"])
+def test_trainer_densifies_under_consensus(mods, layout):
     D, O, srv, T = mods
     from paper_2405_13943_b300 import densify as DZ
     wl = S.dogs_workload(40_000, 2, 2, 0.1, 41, views_per_step=1, pool=2, width=200, height=150)
     z0 = D.GaussianBuffer.from_synth(wl.z0)
     gt = D.GaussianBuffer.from_synth(wl.gt)
     targets = [srv.render_views(gt, vs).image.clone() for vs in wl.views]
-    cfg = DZ.DensifyConfig(interval=2, start=2, until=7, grad_threshold=1e-6, min_opacity=0.3)
+    cfg = DZ.DensifyConfig(interval=2, start=2, until=7, grad_threshold=1e-6, min_opacity=0.3, layout=layout)
     tr = T.DogsTrainer(wl.split, z0, wl.views, targets, rho=(1e-2,) * 5, loss="l1", intv=1, densify=cfg)
     tr.calibrate_capacity()
     n0 = tr.z.n
@@ -267,3 +268,59 @@ def test_opacity_reset_matches_oracle_and_runs_on_schedule(mods):
             assert (zo <= cap + 1e-6).all()          # reset after the consensus of iteration 3
         else:
             assert (zo > cap + 1e-3).any()
+
+
+def inplace_layout_reference(O, split, codes):
+    """The densified layout in the old order, written out plainly: block by
+    block, every old copy replaced by its Gaussian's outputs (children after
+    their parent); a new copy carries the old copy's state when its Gaussian
+    is the parent itself; each new global's copies listed in block order."""
+    outs = np.where(codes == O.DENSIFY_PRUNE, 0, np.where(codes == O.DENSIFY_KEEP, 1, 2))
+    offsets = np.concatenate([[0], np.cumsum(outs)])
+    gid, carry, blk_off, blk_nsh = [], [], [0], []
+    for k in range(split.K):
+        for c in range(split.blk_off[k], split.blk_off[k + 1]):
+            if c == split.blk_off[k] + split.blk_nshared[k]:
+                blk_nsh.append(len(gid) - blk_off[-1])
+            g = split.copy_gid[c]
+            for h in range(outs[g]):
+                gid.append(offsets[g] + h)
+                carry.append(c if h == 0 and codes[g] != O.DENSIFY_SPLIT else -1)
+        if len(blk_nsh) == k:
+            blk_nsh.append(len(gid) - blk_off[-1])
+        blk_off.append(len(gid))
+    lists = [[] for _ in range(int(offsets[-1]))]
+    for nc, j in enumerate(gid):
+        lists[j].append(nc)
+    g_off = np.concatenate([[0], np.cumsum([len(l) for l in lists])])
+    g_copies = np.array([c for l in lists for c in l], np.int64)
+    return (np.array(gid), np.array(carry), np.array(blk_off), np.array(blk_nsh), g_off, g_copies,
+            int(offsets[split.n_shared_globals]))
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_inplace_layout_matches_reference(mods, seed):
+    D, O, _, _ = mods
+    rng = np.random.default_rng(seed)
+    n = 5000
+    xy = rng.uniform(0, 100, (n, 2))
+    split, _ = S.block_split(xy, 2, 3, rng.dirichlet(np.full(6, 2.0)), 0.15)
+    codes = rng.choice(4, size=n, p=[0.6, 0.1, 0.2, 0.1]).astype(np.int32)
+    outs = np.where(codes == O.DENSIFY_PRUNE, 0, np.where(codes == O.DENSIFY_KEEP, 1, 2))
+    offsets = np.concatenate([[0], np.cumsum(outs)]).astype(np.uint32)
+    dev = "cuda"
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dt)).to(dev)
+    g_off, g_cp, cp_off, gid, carry = None, None, None, None, None
+    g_off, g_cp, gid, carry, cp_off = D.dg_densify_layout(t(codes, np.int32), t(offsets.view(np.int32), np.int32),
+                                                          t(split.g_off, np.int64), t(split.g_copies, np.int32),
+                                                          t(split.copy_gid, np.int32))
+    torch.cuda.synchronize()
+    w_gid, w_carry, w_blk, w_nsh, w_goff, w_gcp, w_nshg = inplace_layout_reference(O, split, codes)
+    np.testing.assert_array_equal(gid.cpu().numpy(), w_gid)
+    np.testing.assert_array_equal(carry.cpu().numpy(), w_carry)
+    np.testing.assert_array_equal(g_off.cpu().numpy(), w_goff)
+    np.testing.assert_array_equal(g_cp.cpu().numpy(), w_gcp)
+    co = cp_off.cpu().numpy().view(np.uint32).astype(np.int64)
+    np.testing.assert_array_equal(co[split.blk_off], w_blk)
+    np.testing.assert_array_equal(co[split.blk_off[:-1] + split.blk_nshared] - co[split.blk_off[:-1]], w_nsh)
+    assert int(offsets[split.n_shared_globals]) == w_nshg
