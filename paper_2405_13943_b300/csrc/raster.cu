@@ -98,6 +98,31 @@ __device__ __forceinline__ float strip_q_off(const Strip& s, float off)
     return __fmaf_rn(__fmaf_rn(s.C, dy, s.Bdx), dy, s.E0);
 }
 
+// q of every pixel of the strip, two pixels per paired instruction where PPL
+// is even (each lane rounded exactly as strip_q / strip_q_off round).
+// off == nullptr: row offsets k dy (strip_q); else off[k] (strip_q_off).
+template <int PPL>
+__device__ __forceinline__ void strip_q_all(const Strip& s, const float* off, float* q)
+{
+    if constexpr (PPL % 2 == 0) {
+        const f32x2 C2 = f2_pack(s.C, s.C), B2 = f2_pack(s.Bdx, s.Bdx), E2 = f2_pack(s.E0, s.E0);
+        const f32x2 D2 = f2_pack(s.dy0, s.dy0);
+#pragma unroll
+        for (int j = 0; j < PPL / 2; j++) {
+            f32x2 dy;
+            if (off)
+                dy = f2_sub(D2, f2_pack(off[2 * j], off[2 * j + 1]));
+            else
+                dy = f2_fma(f2_pack(-(float)(2 * j), -(float)(2 * j + 1)), f2_pack(s.ddy, s.ddy), D2);
+            const f32x2 qq = f2_fma(f2_fma(C2, dy, B2), dy, E2);
+            f2_unpack(qq, q[2 * j], q[2 * j + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < PPL; k++) q[k] = off ? strip_q_off(s, off[k]) : strip_q(s, k);
+    }
+}
+
 template <int PPL>
 __device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float B, float C, float lo, float fx,
                                              float fy0, float ddy)
@@ -211,9 +236,11 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
             if (CNT) n_seen += __popc(live);
             const Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, h.y, G.fx, G.fy0, G.dy);
             const float4 c = s_c[j];
+            float qs[PPL];
+            strip_q_all<PPL>(sp, off, qs);
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
-                const float q = strip_q_off(sp, off[k]);
+                const float q = qs[k];
                 if (!(q >= -8.0f)) continue;
                 const float raw = strip_raw(q, h.y);
                 if (!(raw >= kAlphaMin)) continue;
@@ -411,12 +438,10 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             const Strip sp = strip_setup<PPL>(g.x, g.y, g.z, g.w, h.x, h.y, Lg.fx, Lg.fy0, Lg.dy);
             // the first test for the whole strip, without branches
             float qk[PPL];
+            strip_q_all<PPL>(sp, nullptr, qk);
             uint32_t reach = 0;
 #pragma unroll
-            for (int k = 0; k < PPL; k++) {
-                qk[k] = strip_q(sp, k);
-                reach |= (uint32_t)(qk[k] >= -8.0f) << k;
-            }
+            for (int k = 0; k < PPL; k++) reach |= (uint32_t)(qk[k] >= -8.0f) << k;
             const uint32_t todo = joined & reach;
             if (!__any_sync(0xffffffffu, todo != 0u)) continue;
             const float4 c = s_c[j];
