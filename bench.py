@@ -675,6 +675,35 @@ def run_raster(args, dist, rank, world):
     D.forward(xb, vb, bg)                     # sizes the instance capacity once
     tgt_dev = target.clone()
 
+    def best_variant(call, fwd: bool):
+        """The compositing variant (warps per tile, staged per thread) of the
+        forward or the backward with the shortest time on this view."""
+        best = None
+        for w in (1, 2, 4, 8):
+            for st in (1, 2):
+                cur = [vb.plan.raster_warps, vb.plan.raster_stage, vb.plan.raster_warps_bwd, vb.plan.raster_stage_bwd]
+                if fwd:
+                    cur[0], cur[1] = w, st
+                else:
+                    cur[2], cur[3] = w, st
+                D.apply_variant(vb.plan, cur)
+                for _ in range(3):
+                    call()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(20):
+                    call()
+                e1.record()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1)
+                if best is None or t < best[0]:
+                    best = (t, list(cur))
+        D.apply_variant(vb.plan, best[1])
+
+    D.dg_loss_l1(vb, tgt_dev, 1.0)
+    best_variant(lambda: D.dg_rasterize_fwd(vb, bg), True)
+    best_variant(lambda: D.dg_rasterize_bwd(vb, xb, grads, bg=bg), False)
+
     def step():
         D.dg_project(xb, vb)
         D.dg_bin_sort(vb)
@@ -771,6 +800,8 @@ def run_raster(args, dist, rank, world):
             "steps": reps, "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (cube law, seeded)",
             "config": {"workload": workload_name(args, None), "tile": "16x16", "cuda_graph": True,
+                       "raster_variant": {"fwd": [vb.plan.raster_warps, vb.plan.raster_stage],
+                                          "bwd": [vb.plan.raster_warps_bwd, vb.plan.raster_stage_bwd]},
                        "instances": int(vb.count.item()),
                        "l2": "working set < L2: replays run warm, as a one-view training loop would"},
             "kernels_ms": kern, "roofline": roofline, "fp32_peak": fp32, "clocks": clk,
@@ -826,7 +857,7 @@ def densify_probe(tr, wl, D):
     tr.densify_cfg = cfg
     tr.extent = DZ.scene_extent([c for vs in tr.view_sets for c in vs])
     tr.dstats = torch.zeros(2 * tr.split.n_copies, dtype=torch.float32, device=tr.z.data.device)
-    ms, walls = [], []
+    ms, walls, parts = [], [], []
     for rep in range(2):            # the first densification also pays one-time set-up (allocator, RNG)
         for _ in range(4):
             tr.step(consensus=True, graph=False)
@@ -840,9 +871,10 @@ def densify_probe(tr, wl, D):
         out = DZ.densify(tr, cfg, tr.extent, tr.t)
         torch.cuda.synchronize()
         walls.append(time.perf_counter() - t0)
+        parts.append(out.get("seconds"))
         tr.dstats.zero_()
     return {"stats_kernel_ms": round(float(np.median(ms)), 4), "densify_s": round(walls[-1], 3),
-            "densify_s_first": round(walls[0], 3),
+            "densify_s_first": round(walls[0], 3), "seconds_first": parts[0],
             "extent_m": round(tr.extent, 1), **{k: v for k, v in out.items()},
             "rule": "3DGS adaptive density control on the global model after a consensus: grad 2e-4, "
                     "percent_dense 0.01, min_opacity 0.005 (statistics of 4 iterations)"}

@@ -421,6 +421,11 @@ int dg_densify_layout(const int32_t* codes, const uint32_t* offsets, int64_t n_g
                       int64_t* new_g_off, int32_t* new_g_copies, int32_t* new_copy_gid, int32_t* carry,
                       uint32_t* copy_offsets, void* ws, size_t ws_bytes, void* stream);
 
+/* counts[b] = #{i < n : v[i] == lo + b} for b < n_bins (1..64; device int32
+ * v, device uint32 counts, overwritten); values outside the bins are not
+ * counted.  The densification's tallies (codes per kind, carried copies). */
+int dg_histogram_i32(const int32_t* v, int64_t n, int32_t lo, int n_bins, uint32_t* counts, void* stream);
+
 /* ---- 8-bit images (training targets cross the host link as bytes) -------
  * dg_image_u8_to_f32: dst[i] = src[i] / 255 for i < n (device; src 4-byte
  * and dst 16-byte aligned).  dg_image_f32_to_u8:

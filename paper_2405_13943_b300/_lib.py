@@ -64,6 +64,7 @@ _vp = C.c_void_p
 _SIGS = {
     "dg_version": (C.c_char_p, []),
     "dg_launch_count": (C.c_uint64, []),
+    "dg_histogram_i32": (C.c_int, [_vp, C.c_int64, C.c_int32, C.c_int, _vp, _vp]),
     "dg_densify_layout_workspace_size": (C.c_size_t, [C.c_int64, C.c_int64]),
     "dg_densify_layout": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp,
                                     C.c_size_t, _vp]),

@@ -19,6 +19,7 @@ int launch_bin_sort(const float4*, const uint2*, const dg_camera*, const dg_plan
 int bin_sort_init();
 size_t raster_slots_ws_bytes(int64_t n_rec);
 size_t densify_layout_ws_bytes(int64_t n_g, int64_t n_c);
+int launch_histogram(const int32_t* v, int64_t n, int32_t lo, int nb, uint32_t* counts, cudaStream_t st);
 int launch_densify_layout(const int32_t* codes, const uint32_t* offsets, int64_t n_g, const int64_t* g_off,
                           const int32_t* g_copies, const int32_t* copy_gid, int64_t n_c, int64_t* new_g_off,
                           int32_t* new_g_copies, int32_t* new_copy_gid, int32_t* carry, uint32_t* copy_off,
@@ -479,6 +480,14 @@ int dg_densify_layout(const int32_t* codes, const uint32_t* offsets, int64_t n_g
     if (ws_bytes < densify_layout_ws_bytes(n_global, n_copies)) return DG_ERR_WORKSPACE;
     return launch_densify_layout(codes, offsets, n_global, g_off, g_copies, copy_gid, n_copies, new_g_off,
                                  new_g_copies, new_copy_gid, carry, copy_offsets, ws, (cudaStream_t)stream);
+}
+
+int dg_histogram_i32(const int32_t* v, int64_t n, int32_t lo, int n_bins, uint32_t* counts, void* stream)
+{
+    if (n < 0 || n_bins < 1 || n_bins > 64 || !counts || (n > 0 && !v) || ((uintptr_t)v & 3u) ||
+        ((uintptr_t)counts & 3u))
+        return DG_ERR_INVALID;
+    return launch_histogram(v, n, lo, n_bins, counts, (cudaStream_t)stream);
 }
 
 int dg_gather_rows(const dg_gaussians* src, const int32_t* idx, dg_gaussians* dst, void* stream)

@@ -343,6 +343,35 @@ __global__ void __launch_bounds__(kDensifyThreads) k_dl_emit(const int64_t* __re
     }
 }
 
+// counts[b] += #{i : v[i] == lo + b} for b < nb (values outside [lo, lo + nb) are not
+// counted); a shared-memory histogram per CTA, then one atomic per bin and CTA
+__global__ void __launch_bounds__(kDensifyThreads) k_histogram(const int32_t* __restrict__ v, int64_t n, int32_t lo,
+                                                               int nb, uint32_t* __restrict__ counts)
+{
+    __shared__ uint32_t s_h[64];
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s_h[b] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = v[i] - lo;
+        if (b >= 0 && b < nb) atomicAdd(&s_h[b], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        if (s_h[b]) atomicAdd(&counts[b], s_h[b]);
+}
+
+int launch_histogram(const int32_t* v, int64_t n, int32_t lo, int nb, uint32_t* counts, cudaStream_t st)
+{
+    if (cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)nb, st) != cudaSuccess) return DG_ERR_CUDA;
+    if (n == 0) return DG_OK;
+    const int64_t want = (n + kDensifyThreads - 1) / kDensifyThreads;
+    const unsigned grid = (unsigned)(want < 148 * 8 ? want : 148 * 8);
+    k_histogram<<<grid, kDensifyThreads, 0, st>>>(v, n, lo, nb, counts);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
 // exclusive scan of n uint32 into out[0..n] (total at out[n]), ws: partials
 static void scan_u32(const uint32_t* cnt, int64_t n, uint32_t* out, uint32_t* partials, cudaStream_t st)
 {

@@ -136,7 +136,7 @@ def densify(tr, cfg: DensifyConfig, extent: float, step_seed: int) -> Dict:
     normals = torch.randn(max(z.n, 1) * 6, device=dev, generator=gen, dtype=torch.float32)
     z_tmp, src, orig = D.dg_densify_emit(z, codes, offsets, normals, n_out)
     if cfg.layout == "inplace":
-        c = torch.bincount(codes.long(), minlength=4).cpu().numpy()
+        c = D.dg_histogram_i32(codes, 0, 4)
         return _densify_inplace(tr, z, codes, offsets, z_tmp, n_out, c, t0)
     c = np.bincount(codes.cpu().numpy(), minlength=4)
     if cfg.layout != "resort":
@@ -189,10 +189,10 @@ def _densify_inplace(tr, z, codes, offsets, z_new, n_out: int, c, t0: float) -> 
     t_de = time.perf_counter()
     new_g_off, new_g_cp, new_gid, carry, copy_off = D.dg_densify_layout(codes, offsets, tr.g_off, tr.g_copies,
                                                                         tr.gid)
-    blk_old = torch.from_numpy(np.asarray(old.blk_off, np.int64)).to(dev)
-    nsh_old = torch.from_numpy(np.asarray(old.blk_nshared, np.int64)).to(dev)
-    bo = copy_off[blk_old].cpu().numpy().astype(np.int64)
-    sh_end = copy_off[blk_old[:-1] + nsh_old].cpu().numpy().astype(np.int64)
+    # the new block offsets: the copy offsets at the old block starts and shared ends (a few scalars)
+    at = lambda i: int(copy_off[int(i)].item()) & 0xFFFFFFFF
+    bo = np.array([at(b) for b in old.blk_off], np.int64)
+    sh_end = np.array([at(old.blk_off[k] + old.blk_nshared[k]) for k in range(old.K)], np.int64)
     n_shared = int(offsets[int(old.n_shared_globals)].item()) & 0xFFFFFFFF
     new_split = S.BlockSplit(new_gid.cpu().numpy(), bo, sh_end - bo[:-1], new_g_off.cpu().numpy(),
                              new_g_cp.cpu().numpy(), n_shared, old.cells, old.band)
@@ -206,7 +206,7 @@ def _densify_inplace(tr, z, codes, offsets, z_new, n_out: int, c, t0: float) -> 
         b = D.GaussianBuffer(n_c, z.deg, dev)         # zeros where nothing is carried
         D.dg_gather_rows(getattr(tr, name), carry, b)
         bufs[name] = b
-    carried = int((carry >= 0).sum().item())
+    carried = int(n_c - D.dg_histogram_i32(carry, -1, 1)[0])
     torch.cuda.synchronize()
     t3 = time.perf_counter()
     tr.install_split(new_split, z_new, x_new, bufs["m"], bufs["v"], bufs["u"],

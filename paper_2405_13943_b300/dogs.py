@@ -379,6 +379,14 @@ def dg_densify_layout(codes: torch.Tensor, offsets: torch.Tensor, g_off: torch.T
     return new_g_off, new_g_copies[:n_new_c], new_copy_gid[:n_new_c], carry[:n_new_c], copy_off
 
 
+def dg_histogram_i32(v: torch.Tensor, lo: int, n_bins: int, stream=None) -> np.ndarray:
+    """Host array of counts of v == lo + b, b < n_bins (one small copy back)."""
+    counts = torch.empty(n_bins, dtype=torch.int32, device=v.device)
+    L.check(L.lib().dg_histogram_i32(L.ptr(v), int(v.numel()), int(lo), int(n_bins), L.ptr(counts),
+                                     L.stream_handle(stream)), "dg_histogram_i32")
+    return counts.cpu().numpy().view(np.uint32).astype(np.int64)
+
+
 def dg_gather_rows(src: GaussianBuffer, idx: torch.Tensor, dst: GaussianBuffer, stream=None) -> None:
     """dst row r = src row idx[r]; rows with idx[r] < 0 are left unchanged."""
     L.check(L.lib().dg_gather_rows(src.ref, L.ptr(idx), dst.ref, L.stream_handle(stream)), "dg_gather_rows")

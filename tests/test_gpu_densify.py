@@ -324,3 +324,13 @@ def test_inplace_layout_matches_reference(mods, seed):
     np.testing.assert_array_equal(co[split.blk_off], w_blk)
     np.testing.assert_array_equal(co[split.blk_off[:-1] + split.blk_nshared] - co[split.blk_off[:-1]], w_nsh)
     assert int(offsets[split.n_shared_globals]) == w_nshg
+
+
+def test_histogram_counts_values_in_range(mods):
+    D, O, _, _ = mods
+    rng = np.random.default_rng(12)
+    v = rng.integers(-3, 9, 100_003).astype(np.int32)
+    got = D.dg_histogram_i32(torch.from_numpy(v).cuda(), -1, 6)
+    want = np.array([(v == b).sum() for b in range(-1, 5)])
+    np.testing.assert_array_equal(got, want)
+    assert D.dg_histogram_i32(torch.zeros(0, dtype=torch.int32, device="cuda"), 0, 4).sum() == 0
