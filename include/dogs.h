@@ -154,8 +154,12 @@ int dg_project(const dg_gaussians* x, const dg_camera* dev_cams, const dg_plan* 
  * 2 b dx dy + c dy^2 is at most 2 ln(255 o) (1 + 2^-10) + 2^-6 (a widened
  * form of Eq. 2's 1/255 skip; the compositing would skip every pair of the
  * other tiles, so no image or gradient depends on it).  Outputs: vals
- * (capacity entries), keys (optional, NULL to skip), ranges[2 t] = first
- * and end index of tile t (empty tiles: start == end), dev_count[0] = number
+ * (capacity entries), keys (optional, NULL to skip), ranges (device
+ * uint32[3 n_tiles]): ranges[2 t], ranges[2 t + 1] = first and end index of
+ * tile t (empty tiles: start == end), then ranges[2 n_tiles + i] = the i-th
+ * tile of the compositing's work order (every tile once, by descending
+ * binary order of magnitude of its instance count, empty tiles last; the
+ * order among tiles of one magnitude is unspecified), dev_count[0] = number
  * of instances M.  If M > capacity the DG_STATUS_CAPACITY bit is set and
  * every range is emptied (nothing is rendered); retry with capacity >= M.
  * Workspace: dg_bin_sort_workspace_size bytes of device memory. */
@@ -193,7 +197,8 @@ int dg_bin_sort_noalloc(const float* rec, const uint32_t* rect, const dg_camera*
  * are skipped; the pass stops before T (1 - alpha) < 1e-4; pixel = sum + T bg.
  * image: [3][H][W] per view at 3 * pix_off; T_final, last: [H][W] at pix_off
  * (last = list position + 1 of the last composited instance, 0 if none).
- * bg: host float[3]. */
+ * bg: host float[3].  ranges: as dg_bin_sort wrote them, work order
+ * included (the tiles are composited in that order). */
 int dg_rasterize_fwd(const float* rec, const uint32_t* vals, const uint32_t* ranges,
                      const dg_camera* dev_cams, const dg_plan* plan, const float* bg,
                      float* image, float* T_final, uint32_t* last, void* stream);

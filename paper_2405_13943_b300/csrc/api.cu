@@ -573,7 +573,7 @@ static size_t render_ws_layout(const dg_plan& p, int64_t capacity, char* base, R
     r.rec = (float4*)take((size_t)p.n_rec * 48 + 16);
     r.rect = (uint2*)take((size_t)p.n_rec * 8 + 8);
     r.vals = (uint32_t*)take((size_t)(capacity > 0 ? capacity : 1) * 4);
-    r.ranges = (uint32_t*)take((size_t)p.n_tiles * 8 + 8);
+    r.ranges = (uint32_t*)take((size_t)p.n_tiles * 12 + 8);   // ranges, then the work order
     r.T_final = (float*)take((size_t)p.n_pixels * 4 + 4);
     r.last = (uint32_t*)take((size_t)p.n_pixels * 4 + 4);
     r.bin_bytes = bin_sort_ws_bytes(p.n_tiles, capacity);

@@ -16,6 +16,8 @@
 // fall back to the same network in global memory).  Instance data crosses
 // HBM about three times (scatter write, sort read, value write) instead of
 // twice per digit of an LSD sort.  No kernel waits on another CTA.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace dg {
@@ -26,6 +28,15 @@ constexpr int kScanChunk = kScanThreads * kScanPer;   // tiles per scan CTA
 constexpr int kSmallCap = 2048;                       // segment sorted by a 256-thread CTA
 constexpr int kBigCap = 16384;                        // segment sorted by a 1024-thread CTA in smem
 
+// The compositing's work order: tiles by descending instance count, in the
+// buckets of clz(count) (the count's binary order of magnitude; empty tiles
+// last), written after the ranges as ranges[2 n_tiles + i].  Heavy tiles
+// then start first instead of in image order, so no long tile is left to run
+// alone at the end of a compositing launch.
+constexpr int kOrderBuckets = 33;
+
+__device__ __forceinline__ int order_bucket(uint32_t n) { return n ? __clz(n) : 32; }
+
 struct BinWs {
     uint32_t* counts;     // n_tiles + 3 (three list counters at the end), zeroed
     uint32_t* cursor;     // n_tiles
@@ -34,6 +45,7 @@ struct BinWs {
     uint32_t* huge_list;  // n_tiles
     uint32_t* mid_list;   // n_tiles
     uint64_t* pairs;      // capacity
+    uint32_t* order_ctr;  // 2 kOrderBuckets: tiles per bucket, then the buckets' fill cursors
 };
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -51,6 +63,7 @@ static size_t bin_ws_layout(int64_t n_tiles, int64_t capacity, BinWs* w, char* b
     t.huge_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.mid_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.pairs = (uint64_t*)take(8 * (size_t)(capacity > 0 ? capacity : 1));
+    t.order_ctr = (uint32_t*)take(4 * (size_t)(2 * kOrderBuckets));
     if (w) *w = t;
     return off;
 }
@@ -476,6 +489,36 @@ __global__ void __launch_bounds__(1024) k_sort_huge(const uint32_t* __restrict__
     }
 }
 
+__global__ void __launch_bounds__(256) k_order_hist(const uint32_t* __restrict__ ranges, int64_t n_tiles,
+                                                    uint32_t* __restrict__ ctr)
+{
+    __shared__ uint32_t s_h[kOrderBuckets];
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_h[b] = 0;
+    __syncthreads();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&s_h[order_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
+        if (s_h[b]) atomicAdd(&ctr[b], s_h[b]);
+}
+
+__global__ void __launch_bounds__(256) k_order_scatter(uint32_t* __restrict__ ranges, int64_t n_tiles,
+                                                       uint32_t* __restrict__ ctr)
+{
+    __shared__ uint32_t s_off[kOrderBuckets];
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < kOrderBuckets; b++) { s_off[b] = run; run += ctr[b]; }
+    }
+    __syncthreads();
+    uint32_t* order = ranges + 2 * n_tiles;
+    uint32_t* cursor = ctr + kOrderBuckets;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += (int64_t)gridDim.x * blockDim.x) {
+        const int b = order_bucket(ranges[2 * t + 1] - ranges[2 * t]);
+        order[s_off[b] + atomicAdd(&cursor[b], 1u)] = (uint32_t)t;
+    }
+}
+
 int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams, const dg_plan& plan,
                     int64_t capacity, uint64_t* keys, uint32_t* vals, uint32_t* ranges, uint32_t* dev_count,
                     void* ws, uint32_t* dev_status, cudaStream_t st)
@@ -508,6 +551,12 @@ int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams,
     k_sort_big<<<148, 1024, kBigCap * sizeof(uint64_t), st>>>(ranges, w.pairs, vals, keys, counters, w.big_list);
     k_sort_huge<<<148, 1024, 0, st>>>(ranges, w.pairs, vals, keys, counters, w.huge_list);
     note_launch(4);
+    // the compositing's work order, after the ranges
+    if (cudaMemsetAsync(w.order_ctr, 0, 4 * (size_t)(2 * kOrderBuckets), st) != cudaSuccess) return DG_ERR_CUDA;
+    const unsigned og = (unsigned)std::min<int64_t>((plan.n_tiles + 255) / 256, 148 * 2);
+    k_order_hist<<<og, 256, 0, st>>>(ranges, plan.n_tiles, w.order_ctr);
+    k_order_scatter<<<og, 256, 0, st>>>(ranges, plan.n_tiles, w.order_ctr);
+    note_launch(2);
     DG_CHECK_LAUNCH();
     return DG_OK;
 }

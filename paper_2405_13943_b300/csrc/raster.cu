@@ -1,7 +1,9 @@
 // K5 blend_fwd and K7 blend_bwd: per-tile front-to-back alpha compositing
 // (Sec. 3.1, Eq. 2) and its adjoint.
 //
-// One CTA per (view, tile) of 256 pixels with NW warps; each thread owns
+// One CTA per (view, tile) of 256 pixels with NW warps, the tiles taken in
+// the work order dg_bin_sort leaves after the ranges (descending instance
+// count, so the heavy tiles start first); each thread owns
 // PPL = 8 / NW pixels of the tile (pixel q = tid + 32 NW k), so a thread's
 // pixels share a column and need no coordinate registers.  Rounds of
 // 32 NW S instances (S per thread) are staged in shared memory -- fetched
@@ -179,6 +181,7 @@ template <int NW, int S, bool CNT = false>
 __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict__ rec,
                                                         const uint32_t* __restrict__ vals,
                                                         const uint32_t* __restrict__ ranges,
+                                                        const uint32_t* __restrict__ order,
                                                         const dg_camera* __restrict__ cams, int n_views, int tw,
                                                         int th, float bg0, float bg1, float bg2,
                                                         float* __restrict__ image, float* __restrict__ T_final,
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
     __shared__ float4 s_c[R];   // colour
     const int tid = threadIdx.x;
     TileInfo ti;
-    tile_info(cams, n_views, blockIdx.x, tw, th, ranges, ti);
+    tile_info(cams, n_views, order[blockIdx.x], tw, th, ranges, ti);
     const LaneGeom G = lane_geom(ti, tw, tid, NT);
     float T[PPL], C0[PPL], C1[PPL], C2[PPL], off[PPL];
     uint32_t last[PPL];
@@ -343,6 +346,7 @@ template <int NW, int S, bool SLOT = false>
 __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd(const float4* __restrict__ rec,
                                                         const uint32_t* __restrict__ vals,
                                                         const uint32_t* __restrict__ ranges,
+                                                        const uint32_t* __restrict__ order,
                                                         const dg_camera* __restrict__ cams, int n_views, int tw,
                                                         int th, float bg0, float bg1, float bg2,
                                                         const float* __restrict__ T_final,
@@ -360,7 +364,7 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
     __shared__ uint32_t s_max;
     const int tid = threadIdx.x, lane = tid & 31;
     TileInfo ti;
-    tile_info(cams, n_views, blockIdx.x, tw, th, ranges, ti);
+    tile_info(cams, n_views, order[blockIdx.x], tw, th, ranges, ti);
     const LaneGeom Lg = lane_geom(ti, tw, tid, NT);
     const int64_t HW = (int64_t)ti.W * ti.H;
     const float* gi = dL_dimage + 3 * ti.pix_off;
@@ -516,7 +520,8 @@ static void fwd_launch(const float4* rec, const uint32_t* vals, const uint32_t* 
                        const dg_plan& p, const float* bg, float* image, float* T_final, uint32_t* last,
                        cudaStream_t st)
 {
-    k_raster_fwd<NW, S><<<(unsigned)p.n_tiles, 32 * NW, 0, st>>>(rec, vals, ranges, cams, p.n_views, p.tile_w,
+    k_raster_fwd<NW, S><<<(unsigned)p.n_tiles, 32 * NW, 0, st>>>(rec, vals, ranges, ranges + 2 * p.n_tiles, cams,
+                                                                 p.n_views, p.tile_w,
                                                                  p.tile_h, bg[0], bg[1], bg[2], image, T_final, last,
                                                                  nullptr);
 }
@@ -526,7 +531,8 @@ static void count_launch(const float4* rec, const uint32_t* vals, const uint32_t
                          const dg_plan& p, const float* bg, float* image, float* T_final, uint32_t* last,
                          unsigned long long* counts, cudaStream_t st)
 {
-    k_raster_fwd<NW, S, true><<<(unsigned)p.n_tiles, 32 * NW, 0, st>>>(rec, vals, ranges, cams, p.n_views,
+    k_raster_fwd<NW, S, true><<<(unsigned)p.n_tiles, 32 * NW, 0, st>>>(rec, vals, ranges, ranges + 2 * p.n_tiles,
+                                                                       cams, p.n_views,
                                                                        p.tile_w, p.tile_h, bg[0], bg[1], bg[2],
                                                                        image, T_final, last, counts);
 }
@@ -536,7 +542,8 @@ static void bwd_launch(const float4* rec, const uint32_t* vals, const uint32_t* 
                        const dg_plan& p, const float* bg, const float* T_final, const uint32_t* last,
                        const float* dL_dimage, float* drec, cudaStream_t st)
 {
-    k_raster_bwd<NW, S><<<(unsigned)p.n_tiles, 32 * NW, 0, st>>>(rec, vals, ranges, cams, p.n_views, p.tile_w,
+    k_raster_bwd<NW, S><<<(unsigned)p.n_tiles, 32 * NW, 0, st>>>(rec, vals, ranges, ranges + 2 * p.n_tiles, cams,
+                                                                 p.n_views, p.tile_w,
                                                                  p.tile_h, bg[0], bg[1], bg[2], T_final, last,
                                                                  dL_dimage, drec, SlotOut{});
 }
@@ -741,11 +748,13 @@ int launch_raster_bwd_slots(const float4* rec, const uint2* rect, const uint32_t
         const int S = plan.raster_warps_bwd != 0 ? plan.raster_stage_bwd : plan.raster_stage;
         if (S == 2)
             k_raster_bwd<1, 2, true><<<(unsigned)plan.n_tiles, 32, 0, st>>>(
-                rec, vals, ranges, cams, plan.n_views, plan.tile_w, plan.tile_h, bg[0], bg[1], bg[2], T_final, last,
+                rec, vals, ranges, ranges + 2 * plan.n_tiles, cams, plan.n_views, plan.tile_w, plan.tile_h, bg[0], bg[1],
+                bg[2], T_final, last,
                 dL_dimage, drec, so);
         else
             k_raster_bwd<1, 1, true><<<(unsigned)plan.n_tiles, 32, 0, st>>>(
-                rec, vals, ranges, cams, plan.n_views, plan.tile_w, plan.tile_h, bg[0], bg[1], bg[2], T_final, last,
+                rec, vals, ranges, ranges + 2 * plan.n_tiles, cams, plan.n_views, plan.tile_w, plan.tile_h, bg[0], bg[1],
+                bg[2], T_final, last,
                 dL_dimage, drec, so);
         note_launch();
     }

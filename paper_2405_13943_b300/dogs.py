@@ -171,7 +171,7 @@ class ViewBatch:
         i32 = dict(dtype=torch.int32, device=device)
         self.rec = torch.zeros(max(p.n_rec, 1) * 12, dtype=torch.float32, device=device)
         self.rect = torch.zeros(max(p.n_rec, 1) * 2, **i32)
-        self.ranges = torch.zeros(max(p.n_tiles, 1) * 2, **i32)
+        self.ranges = torch.zeros(max(p.n_tiles, 1) * 3, **i32)     # [start, end) per tile, then the work order
         self.count = torch.zeros(1, **i32)
         self.status = torch.zeros(1, **i32)
         self.image = torch.zeros(max(p.n_pixels, 1) * 3, dtype=torch.float32, device=device)

@@ -99,6 +99,7 @@ def check_forward(D, O, vb, f, masks, plan):
     np.testing.assert_array_equal(vb.vals.cpu().numpy()[:M].view(np.uint32), f["bins"]["vals"])
     np.testing.assert_array_equal(vb.ranges.cpu().numpy()[:2 * plan.n_tiles].view(np.uint32),
                                   f["bins"]["ranges"].reshape(-1))
+    check_work_order(vb.ranges.cpu().numpy().view(np.uint32), plan.n_tiles)
     excluded = flipped = 0
     for v, ov in enumerate(f["views"]):
         img = vb.view_image(v).cpu().numpy()
@@ -117,6 +118,16 @@ def check_forward(D, O, vb, f, masks, plan):
     report("forward", pixels=total, excluded=excluded, flipped=flipped)
     assert excluded <= max(2, EXCLUDE_FRAC * total), excluded
     assert flipped <= max(1, FLIP_FRAC * total), flipped
+
+
+def check_work_order(r, n_tiles):
+    """The tiles after the ranges: a permutation, by descending binary
+    magnitude of the instance count (empty tiles last)."""
+    order = r[2 * n_tiles:3 * n_tiles].astype(np.int64)
+    np.testing.assert_array_equal(np.sort(order), np.arange(n_tiles))
+    cnt = (r[1:2 * n_tiles:2] - r[0:2 * n_tiles:2]).astype(np.int64)[order]
+    mag = np.where(cnt > 0, np.floor(np.log2(np.maximum(cnt, 1))), -1)
+    assert np.all(np.diff(mag) <= 0)
 
 
 def check_backward(D, O, g, grads, ob, deg):
@@ -323,7 +334,7 @@ def test_empty_scene_and_capacity_overflow(D, oracle):
     torch.cuda.synchronize()
     assert int(vb.status.item()) & 1
     assert int(vb.count.item()) > 10
-    assert np.all(vb.ranges.cpu().numpy() == 0)
+    assert np.all(vb.ranges.cpu().numpy()[:2 * vb.n_tiles] == 0)
     D.forward(xb, vb, bg, retry=True)
     f = O.render(O.params_from(g), 0, O.ViewPlan([cam], [(0, g.n)], 16, 16), bg)
     m = f["views"][0]["margin"] >= 1e-4
