@@ -158,9 +158,9 @@ int dg_project(const dg_gaussians* x, const dg_camera* dev_cams, const dg_plan* 
  * uint32[3 n_tiles]): ranges[2 t], ranges[2 t + 1] = first and end index of
  * tile t (empty tiles: start == end), then ranges[2 n_tiles + i] = the i-th
  * tile of the compositing's work order (every tile once, by descending
- * binary order of magnitude of its instance count, empty tiles last; the
- * order among tiles of one magnitude is unspecified), dev_count[0] = number
- * of instances M.  If M > capacity the DG_STATUS_CAPACITY bit is set and
+ * instance count n in buckets set by n's leading one bit and the two bits
+ * after it, empty tiles last; the order within a bucket is unspecified),
+ * dev_count[0] = number of instances M.  If M > capacity the DG_STATUS_CAPACITY bit is set and
  * every range is emptied (nothing is rendered); retry with capacity >= M.
  * Workspace: dg_bin_sort_workspace_size bytes of device memory. */
 size_t dg_bin_sort_workspace_size(const dg_plan* plan, int64_t capacity);

@@ -28,14 +28,22 @@ constexpr int kScanChunk = kScanThreads * kScanPer;   // tiles per scan CTA
 constexpr int kSmallCap = 2048;                       // segment sorted by a 256-thread CTA
 constexpr int kBigCap = 16384;                        // segment sorted by a 1024-thread CTA in smem
 
-// The compositing's work order: tiles by descending instance count, in the
-// buckets of clz(count) (the count's binary order of magnitude; empty tiles
-// last), written after the ranges as ranges[2 n_tiles + i].  Heavy tiles
+// The compositing's work order: tiles by descending instance count, in
+// buckets a quarter octave wide (clz(count) and the two bits after the
+// leading one; empty tiles last), written after the ranges as
+// ranges[2 n_tiles + i].  Heavy tiles
 // then start first instead of in image order, so no long tile is left to run
 // alone at the end of a compositing launch.
-constexpr int kOrderBuckets = 33;
+constexpr int kOrderBuckets = 129;
 
-__device__ __forceinline__ int order_bucket(uint32_t n) { return n ? __clz(n) : 32; }
+// bucket 4 clz(n) + (3 - the two bits after n's leading one): a quarter
+// octave wide, ascending as n descends; 128 for an empty tile
+__device__ __forceinline__ int order_bucket(uint32_t n)
+{
+    if (n == 0) return 128;
+    const int z = __clz(n);
+    return 4 * z + 3 - (int)(((n << z) >> 29) & 3u);
+}
 
 struct BinWs {
     uint32_t* counts;     // n_tiles + 3 (three list counters at the end), zeroed
@@ -505,10 +513,30 @@ __global__ void __launch_bounds__(256) k_order_hist(const uint32_t* __restrict__
 __global__ void __launch_bounds__(256) k_order_scatter(uint32_t* __restrict__ ranges, int64_t n_tiles,
                                                        uint32_t* __restrict__ ctr)
 {
+    // exclusive scan of the bucket counts by warp 0, five buckets a lane
+    constexpr int kPer = (kOrderBuckets + 31) / 32;
     __shared__ uint32_t s_off[kOrderBuckets];
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int b = 0; b < kOrderBuckets; b++) { s_off[b] = run; run += ctr[b]; }
+    if (threadIdx.x < 32) {
+        uint32_t c[kPer], sum = 0;
+#pragma unroll
+        for (int j = 0; j < kPer; j++) {
+            const int b = threadIdx.x * kPer + j;
+            c[j] = b < kOrderBuckets ? ctr[b] : 0u;
+            sum += c[j];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+            if ((int)threadIdx.x >= d) incl += v;
+        }
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (int j = 0; j < kPer; j++) {
+            const int b = threadIdx.x * kPer + j;
+            if (b < kOrderBuckets) s_off[b] = run;
+            run += c[j];
+        }
     }
     __syncthreads();
     uint32_t* order = ranges + 2 * n_tiles;

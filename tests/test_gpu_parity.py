@@ -121,12 +121,15 @@ def check_forward(D, O, vb, f, masks, plan):
 
 
 def check_work_order(r, n_tiles):
-    """The tiles after the ranges: a permutation, by descending binary
-    magnitude of the instance count (empty tiles last)."""
+    """The tiles after the ranges: a permutation, by descending instance
+    count n in quarter-octave buckets (the leading one of n and the two bits
+    after it), empty tiles last."""
     order = r[2 * n_tiles:3 * n_tiles].astype(np.int64)
     np.testing.assert_array_equal(np.sort(order), np.arange(n_tiles))
     cnt = (r[1:2 * n_tiles:2] - r[0:2 * n_tiles:2]).astype(np.int64)[order]
-    mag = np.where(cnt > 0, np.floor(np.log2(np.maximum(cnt, 1))), -1)
+    e = np.array([int(c).bit_length() - 1 for c in cnt])
+    top = np.array([(int(c) << 2) >> int(k) if c > 0 else 0 for c, k in zip(cnt, e)])   # 4..7: 1.xx in binary
+    mag = np.where(cnt > 0, 4 * e + top, -1)
     assert np.all(np.diff(mag) <= 0)
 
 
