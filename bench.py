@@ -55,7 +55,11 @@ def parse():
     ap.add_argument("--tile", default="16x16")
     ap.add_argument("--no-autotune", action="store_true", help="keep --tile and the default compositing variant")
     ap.add_argument("--idle-ctas", type=int, default=0,
-                    help="CTAs per SM of the x-step part that runs beside compositing (0: one per group of copies)")
+                    help="CTAs per SM of the x-step part that runs beside compositing (0: one per SM streamed, "
+                         "one per group of copies as a grid)")
+    ap.add_argument("--idle-mode", default="stream", choices=["stream", "grid"],
+                    help="that x-step part: streamed by persistent CTAs beside the compositing adjoint, or a grid "
+                         "launched after the projection")
     ap.add_argument("--no-overlap", action="store_true", help="run that x-step part inline on the main stream")
     ap.add_argument("--variant", default=None,
                     help="compositing variant W,S[,Wb,Sb] (warps per tile, staged per thread; backward)")
@@ -381,6 +385,7 @@ def run_ours(args, dist, rank, world):
     tr = T.DogsTrainer(wl.split, z0, wl.views, targets, rho=(W["rho"],) * 5, tile=tile, loss=args.loss,
                        overlap=not args.no_overlap, intv=W["intv"] or 100)
     tr.idle_ctas_per_sm = args.idle_ctas
+    tr.idle_mode = args.idle_mode
     m_max = tr.calibrate_capacity()
     tuned = None
     if not args.no_autotune and not args.profile and not args.variant:
@@ -440,8 +445,12 @@ def run_ours(args, dist, rank, world):
 
     calls = [("project", lambda: D.dg_project(tr.x, vb))]
     if split:       # the part that the graph runs on a side stream, timed here in sequence
-        calls.append(("xstep_idle", lambda: D.dg_xstep_part(1, vb, *xs_args, step=1, dev_step=tr.dev_step,
-                                                            **zargs)))
+        if tr.idle_mode == "stream":
+            calls.append(("xstep_idle", lambda: D.dg_xstep_stream(vb, *xs_args, tr.xs_ws, step=1, dev_step=tr.dev_step,
+                                                                  ctas=tr.n_sm * tr.idle_ctas_per_sm, **zargs)))
+        else:
+            calls.append(("xstep_idle", lambda: D.dg_xstep_part(1, vb, *xs_args, step=1, dev_step=tr.dev_step,
+                                                                ctas=tr.n_sm * tr.idle_ctas_per_sm, **zargs)))
     calls += [("bin_sort", lambda: D.dg_bin_sort(vb)),
               ("rasterize_fwd", lambda: D.dg_rasterize_fwd(vb, tr.bg)),
               ("loss", lambda: tr._loss(tr.targets[tr.t % len(tr.view_sets)]))]
@@ -601,7 +610,7 @@ def run_ours(args, dist, rank, world):
                        "cuda_graph": True,
                        "xstep_split": (None if not split else
                                        {"idle_groups_on_side_stream": round(1.0 - float(active_groups.mean()), 3),
-                                        "side_ctas_per_sm": tr.idle_ctas_per_sm}),
+                                        "mode": tr.idle_mode, "side_ctas_per_sm": tr.idle_ctas_per_sm}),
                        "unshared_z_stored_by_xstep": bool(zf),
                        "l2": "working set > L2 (no flush needed)", "instances_per_step": instances,
                        "parallelism": "replicas" if world > 1 else "single GPU",

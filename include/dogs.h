@@ -310,6 +310,27 @@ int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev
                   const int32_t* dev_step, dg_gaussians* z_unshared, const int32_t* copy_gid,
                   void* stream);
 
+/* Part 1 of dg_xstep_part (the groups of 128 copies without a kept record,
+ * Eq. 8a / 12a with a zero rendering gradient), streamed: the same result
+ * bit for bit, taken by `ctas` persistent CTAs (0 = one per SM) that move
+ * each listed group's x, m, v and anchors through shared memory by
+ * asynchronous copies.  A few CTAs then keep HBM busy in the registers and
+ * shared memory that the compositing adjoint leaves free, so the call can
+ * run on another stream beside dg_rasterize_bwd_records.  Two launches on
+ * `stream`: the list of those groups (it reads the projection's rectangles),
+ * then the step over it at the device's highest stream priority.
+ * ws: device memory of dg_xstep_stream_workspace_size(x) bytes, 16-byte
+ * aligned, owned by the caller and not used by another call in flight
+ * (a counter pair, then the list).  Same arguments and errors as
+ * dg_xstep_part with part 1; DG_ERR_INVALID for ctas outside 0..65535 or a
+ * missing or misaligned ws, DG_ERR_WORKSPACE if ws_bytes is too small. */
+size_t dg_xstep_stream_workspace_size(const dg_gaussians* x);
+int dg_xstep_stream(int ctas, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                    dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
+                    const uint8_t* copy_shared, const float* rho, const float* lr, float beta1, float beta2,
+                    float eps, int step, const int32_t* dev_step, dg_gaussians* z_unshared,
+                    const int32_t* copy_gid, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- ADMM (K9, K10) -------------------------------------------------------- */
 /* x-step (Eq. 8a / 12a): one Adam step on every local copy with gradient
  * g + rho_grp (x - anchor) on shared copies (copy_shared[c] != 0), where the

@@ -30,7 +30,7 @@ __device__ __forceinline__ void adam_unit(float4* __restrict__ x, const float4* 
         float as[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
         for (int i = 0; i < 4; i++)
-            if (sh[i]) gs[i] += rho[i] * (xs[i] - as[i]);
+            if (sh[i]) gs[i] = penalty_add(gs[i], rho[i], xs[i], as[i]);
     }
 #pragma unroll
     for (int i = 0; i < 4; i++)

@@ -64,6 +64,11 @@ int launch_f32_to_u8(const float*, uint8_t*, int64_t, cudaStream_t);
 int launch_xstep(int, int, dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*, const uint8_t*,
                  const dg_camera*, const dg_plan&, const uint2*, const float4*, const AdamArgs&, const int32_t*,
                  dg_gaussians*, const int32_t*, cudaStream_t);
+int xstep_stream_init();
+size_t xstep_stream_ws_bytes(int64_t n);
+int launch_xstep_stream(int, dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*, const uint8_t*,
+                        const dg_camera*, const dg_plan&, const uint2*, const AdamArgs&, const int32_t*,
+                        dg_gaussians*, const int32_t*, void*, cudaStream_t);
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -106,6 +111,7 @@ int ensure_init()
     if (done_mask.load() & bit) return DG_OK;
     int rc = bin_sort_init();
     if (rc == DG_OK) rc = loss_init();
+    if (rc == DG_OK) rc = xstep_stream_init();
     if (rc == DG_OK) done_mask.fetch_or(bit);
     return rc;
 }
@@ -358,6 +364,12 @@ int dg_rasterize_bwd_slots(const float* rec, const uint32_t* rect, const uint32_
                                    (cudaStream_t)stream);
 }
 
+static int xstep_args(int part, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                      const float* drec, const dg_gaussians* x, const dg_gaussians* m, const dg_gaussians* v,
+                      const dg_gaussians* anchor, const uint8_t* copy_shared, const float* rho, const float* lr,
+                      float beta1, float beta2, float eps, int step, const int32_t* dev_step,
+                      const dg_gaussians* z_unshared, const int32_t* copy_gid, AdamArgs& a);
+
 int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
                   const float* drec, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
                   const uint8_t* copy_shared, const float* rho, const float* lr, float beta1, float beta2, float eps,
@@ -365,6 +377,23 @@ int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev
                   void* stream)
 {
     if (part < 0 || part > 2 || ctas < 0) return DG_ERR_INVALID;
+    AdamArgs a;
+    const int rc = xstep_args(part, rect, dev_cams, plan, drec, x, m, v, anchor, copy_shared, rho, lr, beta1, beta2,
+                              eps, step, dev_step, z_unshared, copy_gid, a);
+    if (rc != DG_OK) return rc;
+    return launch_xstep(part, ctas, x, m, v, anchor, (anchor || z_unshared) ? copy_shared : nullptr, dev_cams, *plan,
+                        (const uint2*)rect, (const float4*)drec, a, dev_step, z_unshared, copy_gid,
+                        (cudaStream_t)stream);
+}
+
+// the host-side checks shared by dg_xstep_part and dg_xstep_stream (part 1:
+// drec is not read), and the Adam arguments they launch with
+static int xstep_args(int part, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                      const float* drec, const dg_gaussians* x, const dg_gaussians* m, const dg_gaussians* v,
+                      const dg_gaussians* anchor, const uint8_t* copy_shared, const float* rho, const float* lr,
+                      float beta1, float beta2, float eps, int step, const int32_t* dev_step,
+                      const dg_gaussians* z_unshared, const int32_t* copy_gid, AdamArgs& a)
+{
     if (!valid_plan(plan) || !valid_gauss(x) || !valid_gauss(m) || !valid_gauss(v)) return DG_ERR_INVALID;
     if (!same_layout(x, m) || !same_layout(x, v)) return DG_ERR_INVALID;
     if (anchor && (!valid_gauss(anchor) || !same_layout(x, anchor))) return DG_ERR_INVALID;
@@ -378,13 +407,35 @@ int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev
         if (plan->blk_view_off[k + 1] - plan->blk_view_off[k] > 1) return DG_ERR_INVALID;   // one view per block
     if (plan->n_rec > 0 && (!rect || !dev_cams || (part != 1 && !drec))) return DG_ERR_INVALID;
     if (!aligned8(rect) || !aligned8(dev_cams) || !aligned16(drec)) return DG_ERR_INVALID;
-    AdamArgs a;
     take_rho(rho, a.rho, &a.dev_rho);
     for (int i = 0; i < 6; i++) a.lr[i] = lr[i];
     a.b1 = beta1; a.b2 = beta2; a.eps = eps; a.step = step;
-    return launch_xstep(part, ctas, x, m, v, anchor, (anchor || z_unshared) ? copy_shared : nullptr, dev_cams, *plan,
-                        (const uint2*)rect, (const float4*)drec, a, dev_step, z_unshared, copy_gid,
-                        (cudaStream_t)stream);
+    return DG_OK;
+}
+
+size_t dg_xstep_stream_workspace_size(const dg_gaussians* x)
+{
+    return valid_gauss(x) ? xstep_stream_ws_bytes(x->n) : 0;
+}
+
+int dg_xstep_stream(int ctas, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan, dg_gaussians* x,
+                    dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor, const uint8_t* copy_shared,
+                    const float* rho, const float* lr, float beta1, float beta2, float eps, int step,
+                    const int32_t* dev_step, dg_gaussians* z_unshared, const int32_t* copy_gid, void* ws,
+                    size_t ws_bytes, void* stream)
+{
+    if (ctas < 0 || ctas > 65535) return DG_ERR_INVALID;
+    AdamArgs a;
+    int rc = xstep_args(1, rect, dev_cams, plan, nullptr, x, m, v, anchor, copy_shared, rho, lr, beta1, beta2, eps,
+                        step, dev_step, z_unshared, copy_gid, a);
+    if (rc != DG_OK) return rc;
+    if (x->n > 0 && (!ws || !aligned16(ws))) return DG_ERR_INVALID;
+    if (ws_bytes < xstep_stream_ws_bytes(x->n)) return DG_ERR_WORKSPACE;
+    rc = ensure_init();
+    if (rc != DG_OK) return rc;
+    return launch_xstep_stream(ctas, x, m, v, anchor, (anchor || z_unshared) ? copy_shared : nullptr, dev_cams,
+                               *plan, (const uint2*)rect, a, dev_step, z_unshared, copy_gid, ws,
+                               (cudaStream_t)stream);
 }
 
 int dg_xstep_from_records(const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan, const float* drec,

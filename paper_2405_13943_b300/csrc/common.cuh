@@ -158,13 +158,34 @@ __device__ __forceinline__ void bias_corr(const AdamArgs& a, const int32_t* dev_
     ic2 = 1.f / (1.f - powf(a.b2, t));
 }
 
+// The rounding of every operation below is pinned (explicit fused or
+// unfused intrinsics, no contraction left to the compiler), so that each
+// x-step kernel -- whatever code surrounds the inlined step -- gives a
+// parameter the same bits.
+
+// g + rho (x - a): the gradient of the ADMM penalty rho/2 |x - a|^2 added to g
+__device__ __forceinline__ float penalty_add(float g, float rho, float x, float a)
+{
+    return __fmaf_rn(rho, __fsub_rn(x, a), g);
+}
+
+// square root by the SFU (PTX sqrt.approx.ftz: about 1 ulp, one instruction
+// and no branch, so that the updates of several parameters interleave; the
+// quotient beside it is the approximate division too)
+__device__ __forceinline__ float sqrt_sfu(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // one Adam step of one parameter; g already holds the penalty term
 __device__ __forceinline__ void adam_scalar(float& x, float g, float& m, float& v, float lr, float b1, float b2,
                                             float eps, float ic1, float ic2)
 {
-    m = b1 * m + (1.f - b1) * g;
-    v = b2 * v + (1.f - b2) * g * g;
-    x -= lr * __fdividef(m * ic1, sqrtf(v * ic2) + eps);
+    m = __fmaf_rn(b1, m, __fmul_rn(1.f - b1, g));
+    v = __fmaf_rn(b2, v, __fmul_rn(__fmul_rn(1.f - b2, g), g));
+    x = __fmaf_rn(-lr, __fdividef(__fmul_rn(m, ic1), __fadd_rn(sqrt_sfu(__fmul_rn(v, ic2)), eps)), x);
 }
 
 }  // namespace dg

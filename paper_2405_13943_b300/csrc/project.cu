@@ -661,7 +661,7 @@ __device__ __forceinline__ void step_fields(GView& x, GView& m, GView& v, const 
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             const float rho = rho_of(a, i < 3 ? 0 : 4), lr = i < 3 ? a.lr[0] : a.lr[5];
-            if (s) gg[i] += rho * (xs[i] - as[i]);
+            if (s) gg[i] = penalty_add(gg[i], rho, xs[i], as[i]);
             adam_scalar(xs[i], gg[i], ms[i], vs[i], lr, a.b1, a.b2, a.eps, ic1, ic2);
         }
         x.mo[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
@@ -677,7 +677,7 @@ __device__ __forceinline__ void step_fields(GView& x, GView& m, GView& v, const 
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             float g = gq[i];
-            if (s) g += rho_of(a, 1) * (xs[i] - as[i]);
+            if (s) g = penalty_add(g, rho_of(a, 1), xs[i], as[i]);
             adam_scalar(xs[i], g, ms[i], vs[i], a.lr[1], a.b1, a.b2, a.eps, ic1, ic2);
         }
         x.quat[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
@@ -693,7 +693,7 @@ __device__ __forceinline__ void step_fields(GView& x, GView& m, GView& v, const 
 #pragma unroll
         for (int i = 0; i < 3; i++) {   // lane 3 is padding
             float g = gs[i];
-            if (s) g += rho_of(a, 2) * (xs[i] - as[i]);
+            if (s) g = penalty_add(g, rho_of(a, 2), xs[i], as[i]);
             adam_scalar(xs[i], g, ms[i], vs[i], a.lr[2], a.b1, a.b2, a.eps, ic1, ic2);
         }
         x.scale[c] = make_float4(xs[0], xs[1], xs[2], xs[3]);
@@ -761,7 +761,7 @@ __device__ __forceinline__ void step_planes(GView& x, GView& m, GView& v, const 
             for (int i = 0; i < 4; i++) {
                 if (!act[i]) continue;
                 float g = gq4[i];
-                if (sh[i]) g += rho_of(a, 3) * (xs[i] - as[i]);
+                if (sh[i]) g = penalty_add(g, rho_of(a, 3), xs[i], as[i]);
                 adam_scalar(xs[i], g, ms[i], vs[i], lr, a.b1, a.b2, a.eps, ic1, ic2);
             }
             const int64_t u = ((int64_t)j * x.ld + cq) >> 2;
@@ -861,6 +861,361 @@ __global__ void __launch_bounds__(kXsThreads, 6) k_xstep_idle(GView x, GView m, 
         }
         step_planes<NK, 2, true>(x, m, v, an, shared, c0, nullptr, nullptr, a, ic1, ic2, zo);
     }
+}
+
+// ---- part 1 streamed through shared memory -------------------------------------------
+// The groups without a kept record are listed first (k_idle_groups), then
+// stepped by a few persistent CTAs (one per SM by default) that take groups
+// in a fixed order.  A group's x, m, v and anchors pass through a ring of shared
+// memory by cp.async in segments of 2 KB per array: the three float4 field
+// rows of its 128 copies, then its SH planes four at a time.  A thread copies
+// and later steps the same 16-byte chunk of every segment, so the ring needs
+// no barrier, and kStStages - 1 segments (40 KB a CTA) stay in flight while
+// one is stepped: enough for HBM speed from one CTA per SM, in registers and
+// shared memory that the compositing adjoint leaves free, so this part runs
+// beside it.  Each element's arithmetic is k_xstep_idle's, so the result is
+// the same bit for bit.
+constexpr int kStThreads = 128;
+#ifndef DG_XSTEP_STAGES
+#define DG_XSTEP_STAGES 6
+#endif
+constexpr int kStStages = DG_XSTEP_STAGES;
+
+// one warp per group of kXsThreads copies: appends the group to list if none
+// of its copies has a kept record (the order of the list is unspecified);
+// ctr[0] counts the listed groups
+__global__ void __launch_bounds__(256) k_idle_groups(int64_t n, const dg_camera* __restrict__ cams, dg_plan plan,
+                                                     const uint2* __restrict__ rect, int32_t* __restrict__ list,
+                                                     uint32_t* __restrict__ ctr)
+{
+    const int64_t grp = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (grp * kXsThreads >= n) return;          // uniform over the warp
+    bool kept = false;
+#pragma unroll
+    for (int i = 0; i < kXsThreads / 32; i++) {
+        const int64_t c = grp * kXsThreads + lane + 32 * i;
+        if (c < n && c < plan.blk_off[plan.n_blocks]) {
+            const int k = find_block(plan, c);
+            const int v0 = plan.blk_view_off[k];
+            if (v0 < plan.blk_view_off[k + 1]) {
+                const uint2 t = rect[__ldg(&cams[v0].rec_off) + (c - __ldg(&cams[v0].gauss_begin))];
+                kept = kept || (t.x & 0xFFFFu) != (t.y & 0xFFFFu);
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, kept)) return;
+    if (lane == 0) list[atomicAdd(ctr, 1u)] = (int32_t)grp;
+}
+
+// what a thread needs of its group: the copy c0 + tid of the field rows and
+// the quad c0 + 4 (tid % 32) .. + 3 of the SH planes
+struct StMeta {
+    int64_t c0;       // first copy of the group; -1: none (past the end of the list)
+    uint32_t bits;    // 1: copy active (c < n), 2: copy shared; 1 << (4 + i): quad copy i active, 1 << (8 + i): shared
+    int32_t zf;       // global id of an unshared copy for the z store, else -1
+    int32_t zq[4];    // the same for the quad's copies
+};
+
+__device__ __forceinline__ void st_meta(StMeta& M, int64_t c0, const GView& x, const uint8_t* __restrict__ shared,
+                                        const ZOut& zo)
+{
+    const int tid = threadIdx.x;
+    M.c0 = c0;
+    M.bits = 0;
+    M.zf = -1;
+#pragma unroll
+    for (int i = 0; i < 4; i++) M.zq[i] = -1;
+    if (c0 < 0) return;
+    const int64_t c = c0 + tid;
+    if (c < x.n) {
+        const bool s = shared != nullptr && shared[c] != 0;
+        M.bits |= 1u | (s ? 2u : 0u);
+        if (zo.gid != nullptr && !s) M.zf = zo.gid[c];
+    }
+    const int64_t cq = c0 + 4 * (tid & 31);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if (cq + i >= x.n) continue;
+        const bool s = shared != nullptr && shared[cq + i] != 0;
+        M.bits |= (1u << (4 + i)) | (s ? 1u << (8 + i) : 0u);
+        if (zo.gid != nullptr && !s) M.zq[i] = zo.gid[cq + i];
+    }
+}
+
+__device__ __forceinline__ void st_copy16(float4* dst, const float4* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// The float4 index (within the row or planes st_row returns) of the chunk
+// of segment SEG that this thread copies and steps, or -1 for none.
+// Segments 0..2: the field rows (mean and opacity, rotation, scale), one
+// copy per thread; from 3 on: SH planes 4 (SEG - 3) .. + 3, a plane per warp
+// and a quad of copies per lane.
+template <int SEG, int NP>
+__device__ __forceinline__ int64_t st_chunk(const StMeta& M, const GView& x)
+{
+    const int tid = threadIdx.x;
+    if (M.c0 < 0) return -1;
+    if (SEG < 3) return (M.bits & 1u) ? M.c0 + tid : -1;
+    const int j = 4 * (SEG - 3) + (tid >> 5);
+    const int64_t cq = M.c0 + 4 * (tid & 31);
+    if (4 * (SEG - 3) + 3 >= NP && j >= NP) return -1;    // the last segment may hold fewer planes
+    return cq < x.ld ? (((int64_t)j * x.ld + cq) >> 2) : -1;
+}
+
+template <int SEG>
+__device__ __forceinline__ float4* st_row(const GView& g)
+{
+    return SEG == 0 ? g.mo : SEG == 1 ? g.quat : SEG == 2 ? g.scale : reinterpret_cast<float4*>(g.sh);
+}
+
+// producer: this thread's chunk of x, m, v (and the anchors where its copies
+// are shared) of segment SEG into ring stage s
+template <int SEG, int NP>
+__device__ __forceinline__ void st_issue(float4* s, const StMeta& M, const GView& x, const GView& m,
+                                         const GView& v, const GView& an)
+{
+    const int64_t u = st_chunk<SEG, NP>(M, x);
+    if (u < 0) return;
+    const int tid = threadIdx.x;
+    st_copy16(s + tid, st_row<SEG>(x) + u);
+    st_copy16(s + kStThreads + tid, st_row<SEG>(m) + u);
+    st_copy16(s + 2 * kStThreads + tid, st_row<SEG>(v) + u);
+    const bool need_a = SEG < 3 ? (M.bits & 2u) != 0 : ((M.bits >> 8) & 15u) != 0;
+    if (need_a) st_copy16(s + 3 * kStThreads + tid, st_row<SEG>(an) + u);
+}
+
+// consumer: the Adam + penalty step of this thread's chunk of segment SEG
+// from ring stage s, written back to x, m, v (and z for unshared copies).
+// Branch-free over the chunk's four elements: each is stepped as
+// k_xstep_idle steps it, then kept or discarded by a select (an element that
+// is not stepped -- a copy past n, the scale's padding lane -- keeps its
+// value), so the four updates interleave.
+struct Rho5 {
+    float r[5];   // the penalties of the five groups, read once per CTA
+};
+
+template <int SEG, int NP>
+__device__ __forceinline__ void st_step(const float4* s, const StMeta& M, GView& x, GView& m, GView& v,
+                                        const AdamArgs& a, const Rho5& rh, float ic1, float ic2, const ZOut& zo)
+{
+    const int64_t u = st_chunk<SEG, NP>(M, x);
+    if (u < 0) return;
+    const int tid = threadIdx.x;
+    const float4 X = s[tid], Mo = s[kStThreads + tid], V = s[2 * kStThreads + tid], A = s[3 * kStThreads + tid];
+    const float x0[4] = {X.x, X.y, X.z, X.w}, m0[4] = {Mo.x, Mo.y, Mo.z, Mo.w}, v0[4] = {V.x, V.y, V.z, V.w};
+    const float as[4] = {A.x, A.y, A.z, A.w};        // read only for shared copies (loaded then)
+    float xs[4], ms[4], vs[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        // step, penalty group and learning rate of element i (constants of SEG and i)
+        bool step;
+        float rho, lr;
+        if (SEG == 0) {
+            step = (M.bits & 1u) != 0;
+            rho = rh.r[i < 3 ? 0 : 4];
+            lr = i < 3 ? a.lr[0] : a.lr[5];
+        } else if (SEG == 1) {
+            step = (M.bits & 1u) != 0;
+            rho = rh.r[1];
+            lr = a.lr[1];
+        } else if (SEG == 2) {
+            step = i < 3 && (M.bits & 1u) != 0;
+            rho = rh.r[2];
+            lr = a.lr[2];
+        } else {
+            step = ((M.bits >> (4 + i)) & 1u) != 0;
+            rho = rh.r[3];
+            lr = 4 * (SEG - 3) + (tid >> 5) < 3 ? a.lr[3] : a.lr[4];
+        }
+        const bool sh = SEG < 3 ? (M.bits & 2u) != 0 : ((M.bits >> (8 + i)) & 1u) != 0;
+        const float g = sh ? penalty_add(0.f, rho, x0[i], as[i]) : 0.f;
+        float xi = x0[i], mi = m0[i], vi = v0[i];
+        adam_scalar(xi, g, mi, vi, lr, a.b1, a.b2, a.eps, ic1, ic2);
+        xs[i] = step ? xi : x0[i];
+        ms[i] = step ? mi : m0[i];
+        vs[i] = step ? vi : v0[i];
+    }
+    st_row<SEG>(x)[u] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+    st_row<SEG>(m)[u] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+    st_row<SEG>(v)[u] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+    if (SEG < 3) {
+        if (M.zf >= 0) st_row<SEG>(zo.z)[M.zf] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+    } else {
+        const int j = 4 * (SEG - 3) + (tid >> 5);
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            if (M.zq[i] >= 0) zo.z.sh[(int64_t)j * zo.z.ld + M.zq[i]] = xs[i];
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void st_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void st_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// unit k of a CTA's sequence (group k / NSEG, segment k % NSEG) lives in
+// ring stage k mod NS; a group starts at stage `base`
+template <int NS>
+__device__ __forceinline__ float4* st_stage(float4* ring, int base, int k)
+{
+    return ring + ((base + k) % NS) * 4 * kStThreads;
+}
+
+// segment SEG of a group: the producer's unit SEG + NS - 1 (of this group,
+// or past its last segment the next group's, with nm), then the consumer's
+template <int SEG, int NSEG, int NS, int NP>
+__device__ __forceinline__ void st_segment(float4* ring, int base, const StMeta& cm, const StMeta& nm, GView& x,
+                                           GView& m, GView& v, const GView& an, const AdamArgs& a, const Rho5& rh,
+                                           float ic1, float ic2, const ZOut& zo)
+{
+    constexpr int P = SEG + NS - 1;
+    if constexpr (P < NSEG)
+        st_issue<P, NP>(st_stage<NS>(ring, base, P), cm, x, m, v, an);
+    else
+        st_issue<P - NSEG, NP>(st_stage<NS>(ring, base, P), nm, x, m, v, an);
+    st_commit();
+    st_wait<NS - 1>();
+    st_step<SEG, NP>(st_stage<NS>(ring, base, SEG), cm, x, m, v, a, rh, ic1, ic2, zo);
+    if constexpr (SEG + 1 < NSEG)
+        st_segment<SEG + 1, NSEG, NS, NP>(ring, base, cm, nm, x, m, v, an, a, rh, ic1, ic2, zo);
+}
+
+template <int SEG, int NS, int NP>
+__device__ __forceinline__ void st_prologue(float4* ring, const StMeta& cm, const GView& x, const GView& m,
+                                            const GView& v, const GView& an)
+{
+    if constexpr (SEG < NS - 1) {
+        st_issue<SEG, NP>(ring + SEG * 4 * kStThreads, cm, x, m, v, an);
+        st_commit();
+        st_prologue<SEG + 1, NS, NP>(ring, cm, x, m, v, an);
+    }
+}
+
+// the persistent streamed part 1 over list[0 .. ctr[0]) (ctr[0] written by
+// k_idle_groups): CTA b takes the entries b, b + G, b + 2 G, ... (G CTAs),
+// one group per iteration with its NSEG segments unrolled.  Producer and
+// consumer are the same threads, the producer NS - 1 segments ahead (NS <=
+// NSEG), so the producer's last NS - 1 units of an iteration are the next
+// group's first.  The next group's metadata (nm) and the list entry after it
+// are loaded a group ahead, so no load waits.
+template <int DEG>
+__global__ void __launch_bounds__(kStThreads) k_xstep_stream(GView x, GView m, GView v, GView an,
+                                                            const uint8_t* __restrict__ shared,
+                                                            const int32_t* __restrict__ list,
+                                                            const uint32_t* __restrict__ ctr, AdamArgs a,
+                                                            const int32_t* __restrict__ dev_step, ZOut zo)
+{
+    constexpr int NK = (DEG + 1) * (DEG + 1), NP = 3 * NK, NSEG = 3 + (NP + 3) / 4;
+    constexpr int NS = kStStages < NSEG ? kStStages : NSEG;
+    extern __shared__ __align__(16) float4 s_ring[];   // [NS][x, m, v, anchor][kStThreads]
+    float ic1, ic2;
+    bias_corr(a, dev_step, ic1, ic2);
+    Rho5 rh;
+#pragma unroll
+    for (int k = 0; k < 5; k++) rh.r[k] = rho_of(a, k);
+    const uint32_t n_list = ctr[0], G = gridDim.x;
+    uint32_t li = blockIdx.x;
+    auto entry = [&](uint32_t i) { return i < n_list ? (int64_t)list[i] * kXsThreads : (int64_t)-1; };
+    StMeta cm, nm;
+    st_meta(cm, entry(li), x, shared, zo);
+    st_meta(nm, entry(li + G), x, shared, zo);
+    int64_t c0_ahead = entry(li + 2 * G);
+    li += 3 * G;
+    st_prologue<0, NS, NP>(s_ring, cm, x, m, v, an);
+    int base = 0;
+#pragma unroll 1
+    while (cm.c0 >= 0) {
+        st_segment<0, NSEG, NS, NP>(s_ring, base, cm, nm, x, m, v, an, a, rh, ic1, ic2, zo);
+        base = (base + NSEG) % NS;
+        cm = nm;
+        st_meta(nm, c0_ahead, x, shared, zo);
+        c0_ahead = entry(li);
+        li += G;
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+template <int DEG>
+constexpr size_t st_smem_bytes()
+{
+    constexpr int NK = (DEG + 1) * (DEG + 1), NSEG = 3 + (3 * NK + 3) / 4;
+    return (size_t)(kStStages < NSEG ? kStStages : NSEG) * 4 * kStThreads * sizeof(float4);
+}
+
+// once per device (ensure_init): the ring's dynamic shared memory, and the
+// shared-memory carveout at its maximum so that a CTA fits beside the
+// compositing adjoint's
+int xstep_stream_init()
+{
+#define DG_ST_INIT(D)                                                                                   \
+    if (cudaFuncSetAttribute(k_xstep_stream<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                             (int)st_smem_bytes<D>()) != cudaSuccess ||                                 \
+        cudaFuncSetAttribute(k_xstep_stream<D>, cudaFuncAttributePreferredSharedMemoryCarveout,       \
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)                       \
+        return DG_ERR_CUDA;
+    DG_ST_INIT(0) DG_ST_INIT(1) DG_ST_INIT(2) DG_ST_INIT(3)
+#undef DG_ST_INIT
+    return DG_OK;
+}
+
+// workspace of the streamed part 1: two counters (16 bytes), then the list
+size_t xstep_stream_ws_bytes(int64_t n)
+{
+    return 16 + 4 * (size_t)((n + kXsThreads - 1) / kXsThreads);
+}
+
+int launch_xstep_stream(int ctas, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
+                        const uint8_t* shared, const dg_camera* cams, const dg_plan& plan, const uint2* rect,
+                        const AdamArgs& a, const int32_t* dev_step, dg_gaussians* z, const int32_t* gid, void* ws,
+                        cudaStream_t st)
+{
+    if (x->n == 0) return DG_OK;
+    GView xv = gview(x), mv = gview(m), vv = gview(v);
+    GView av = anchor ? gview(anchor) : xv;
+    ZOut zo;
+    zo.z = z ? gview(z) : xv;
+    zo.gid = z ? gid : nullptr;
+    uint32_t* ctr = static_cast<uint32_t*>(ws);
+    int32_t* list = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + 16);
+    const int64_t n_groups = (x->n + kXsThreads - 1) / kXsThreads;
+    if (cudaMemsetAsync(ctr, 0, 8, st) != cudaSuccess) return DG_ERR_CUDA;
+    k_idle_groups<<<(unsigned)((n_groups + 7) / 8), 256, 0, st>>>(x->n, cams, plan, rect, list, ctr);
+    int dev = 0, sms = 0, least = 0, greatest = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess)
+        return DG_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ctas > 0 ? ctas : sms));
+    cfg.blockDim = dim3(kStThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;       // ahead of the compositing's CTAs for the free slots
+    attr[0].val.priority = greatest;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaSuccess;
+    const int32_t* cl = list;
+#define DG_ST_CASE(D)                                                                                        \
+    case D:                                                                                                  \
+        cfg.dynamicSmemBytes = st_smem_bytes<D>();                                                           \
+        e = cudaLaunchKernelEx(&cfg, k_xstep_stream<D>, xv, mv, vv, av, shared, cl, ctr, a, dev_step, zo);   \
+        break;
+    switch (x->sh_degree) {
+    DG_ST_CASE(0)
+    DG_ST_CASE(1)
+    DG_ST_CASE(2)
+    default:
+    DG_ST_CASE(3)
+    }
+#undef DG_ST_CASE
+    note_launch(2);
+    if (e != cudaSuccess) return DG_ERR_CUDA;
+    DG_CHECK_LAUNCH();
+    return DG_OK;
 }
 
 // part 0: the whole step; 1: the groups without a kept record (drec unused;

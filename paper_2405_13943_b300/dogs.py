@@ -314,6 +314,27 @@ def dg_xstep_part(part: int, vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer
                                   L.stream_handle(stream)), "dg_xstep_part")
 
 
+def xstep_stream_workspace(x: GaussianBuffer) -> torch.Tensor:
+    """Device workspace of dg_xstep_stream for copies laid out as x."""
+    nb = int(L.lib().dg_xstep_stream_workspace_size(x.ref))
+    return torch.empty((nb + 15) // 16 * 4, dtype=torch.int32, device=x.data.device)
+
+
+def dg_xstep_stream(vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer, v: GaussianBuffer,
+                    anchor: Optional[GaussianBuffer], shared: Optional[torch.Tensor], rho, lr, ws: torch.Tensor,
+                    beta1=0.9, beta2=0.999, eps=1e-15, step=1, dev_step: Optional[torch.Tensor] = None,
+                    stream=None, ctas: int = 0, z_unshared: Optional[GaussianBuffer] = None,
+                    gid: Optional[torch.Tensor] = None) -> None:
+    """Part 1 of dg_xstep_part (the groups without a kept record) streamed by
+    `ctas` persistent CTAs (0: one per SM), the same step bit for bit; ws from
+    xstep_stream_workspace(x)."""
+    L.check(L.lib().dg_xstep_stream(int(ctas), L.ptr(vb.rect), L.ptr(vb.dev_cams), C.byref(vb.plan), x.ref, m.ref,
+                                    v.ref, None if anchor is None else anchor.ref, L.ptr(shared), L.rho_arg(rho),
+                                    L.floats(lr), beta1, beta2, eps, int(step), L.ptr(dev_step),
+                                    None if z_unshared is None else z_unshared.ref, L.ptr(gid), L.ptr(ws),
+                                    ws.numel() * ws.element_size(), L.stream_handle(stream)), "dg_xstep_stream")
+
+
 def dg_densify_stats(vb: ViewBatch, stats: torch.Tensor, stream=None) -> None:
     """Adds one iteration's densification statistic of every kept record into
     stats (float32, 2 per copy): the norm of its projected mean's gradient in

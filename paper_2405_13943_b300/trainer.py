@@ -67,6 +67,11 @@ class DogsTrainer:
         # 11.93 (the compositing kernels leave few registers free, so a
         # small grid only drags the step), the one-part x-step 9.24
         self.idle_ctas_per_sm = 0
+        # how that part runs: "stream" -- dg_xstep_stream, one persistent CTA
+        # per SM (idle_ctas_per_sm: 0 = one) moving the groups through shared
+        # memory, launched with the compositing adjoint, beside which it fits;
+        # "grid" -- dg_xstep_part 1 right after the projection
+        self.idle_mode = "stream"
         self.n_sm = torch.cuda.get_device_properties(device).multi_processor_count if self.side is not None else 0
         self.adaptive = adaptive
         if adaptive is not None:
@@ -144,6 +149,7 @@ class DogsTrainer:
             self.g_copies = torch.from_numpy(split.g_copies.astype(np.int32)).to(dev)
         self.z, self.x, self.m, self.v, self.u = z, x, m, v, u
         self.grad, self.anchor = x.like(), x.like()
+        self.xs_ws = D.xstep_stream_workspace(x) if self.side is not None else None
         D.dg_admm_anchor(self.z, self.u, self.gid, self.shared, self.anchor)
         self.dstats = (torch.zeros(2 * max(split.n_copies, 1), dtype=torch.float32, device=dev)
                        if self.densify_cfg is not None else None)
@@ -226,7 +232,7 @@ class DogsTrainer:
         D.dg_step_advance(self.dev_step)
         D.dg_project(self.x, vb)
         zf = self._zfuse(consensus)
-        if self._split_xstep():
+        if self._split_xstep() and self.idle_mode == "grid":
             self.idle_xstep(zf)
         D.dg_bin_sort(vb)
         D.dg_rasterize_fwd(vb, self.bg)
@@ -317,13 +323,19 @@ class DogsTrainer:
     def idle_xstep(self, zfuse: bool = False) -> None:
         """Part 1 of the split x-step (the groups of copies without a kept
         record) on the side stream, after the work queued so far on the
-        current stream (the projection)."""
+        current stream (the projection for "grid", everything up to the
+        loss for "stream")."""
         cur = torch.cuda.current_stream()
         self.side.wait_stream(cur)
         with torch.cuda.stream(self.side):
-            D.dg_xstep_part(1, self.vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(), self.lr,
-                            step=1, dev_step=self.dev_step, ctas=self.n_sm * self.idle_ctas_per_sm,
-                            **self._zargs(zfuse))
+            if self.idle_mode == "stream":
+                D.dg_xstep_stream(self.vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(), self.lr,
+                                  self.xs_ws, step=1, dev_step=self.dev_step, ctas=self.n_sm * self.idle_ctas_per_sm,
+                                  **self._zargs(zfuse))
+            else:
+                D.dg_xstep_part(1, self.vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(),
+                                self.lr, step=1, dev_step=self.dev_step, ctas=self.n_sm * self.idle_ctas_per_sm,
+                                **self._zargs(zfuse))
         self._idle_queued = True
 
     def backward_step(self, zfuse: bool = False) -> None:
@@ -340,6 +352,8 @@ class DogsTrainer:
             raise ValueError("the deterministic backward runs with the fused x-step (one view per block)")
         if self.deterministic and getattr(vb, "part", None) is None:
             raise RuntimeError("deterministic mode: call calibrate_capacity() first (it sizes the slots)")
+        if self._split_xstep() and self.idle_mode == "stream":
+            self.idle_xstep(zfuse)                 # beside the compositing adjoint
         if self._split_xstep() and self._idle_queued:
             bwd_records(vb, bg=self.bg)
             D.dg_xstep_part(2, vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(), self.lr,

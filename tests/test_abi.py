@@ -143,6 +143,33 @@ def test_xstep_part_rejects_bad_arguments_before_launch(lib):
     assert call(0, 0, z, gid + 2) == L.DG_ERR_INVALID         # misaligned ids
 
 
+def test_xstep_stream_rejects_bad_arguments_before_launch(lib):
+    """dg_xstep_stream makes dg_xstep_part's checks and checks its grid bound
+    and workspace on the host; the workspace is two counters and one list
+    entry per group of 128 copies."""
+    from paper_2405_13943_b300 import dogs as D
+    arr, plan = D.plan_views([S.cube_camera(32, 32)], [0, 300], 16, 16)
+    x = L.DgGaussians(0x10000, 300, 300, 0, 0)
+    z = L.DgGaussians(0x20000, 32, 64, 0, 0)
+    rho, lr = L.floats([1] * 5), L.floats([1] * 6)
+    rect, cams, shared, gid, ws = 0x30000, 0x40000, 0x60000, 0x70000, 0x80000
+    need = lib.dg_xstep_stream_workspace_size(C.byref(x))
+    assert need == 16 + 4 * 3
+    assert lib.dg_xstep_stream_workspace_size(C.byref(L.DgGaussians(0x10000, 300, 298, 0, 0))) == 0   # ld < n
+
+    def call(ctas=0, zz=None, g=None, w=ws, nb=need, sh=shared):
+        return lib.dg_xstep_stream(ctas, rect, cams, C.byref(plan), C.byref(x), C.byref(x), C.byref(x), None, sh,
+                                   rho, lr, 0.9, 0.999, 1e-15, 1, None, None if zz is None else C.byref(zz), g,
+                                   w, nb, None)
+    assert call(ctas=-1) == L.DG_ERR_INVALID
+    assert call(ctas=65536) == L.DG_ERR_INVALID
+    assert call(zz=z) == L.DG_ERR_INVALID                    # a z store needs the global ids
+    assert call(zz=z, g=gid, sh=None) == L.DG_ERR_INVALID    # ... and the shared flags
+    assert call(w=None) == L.DG_ERR_INVALID
+    assert call(w=ws + 8) == L.DG_ERR_INVALID                # misaligned workspace
+    assert call(nb=need - 1) == L.DG_ERR_WORKSPACE
+
+
 def test_render_slot_workspace_bounds_every_admissible_batch(lib):
     """The render server sizes a slot's workspace once, on the host, for any
     batch of at most max_batch views and max_batch_pixels pixels: random mixes

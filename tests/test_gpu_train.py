@@ -357,13 +357,61 @@ def test_split_xstep_equals_one_part(mods):
         assert torch.equal(one[n].data, two[n].data), n
 
 
-def test_overlapped_xstep_trainer_matches(mods):
+@pytest.mark.parametrize("ctas", [0, 3])
+def test_streamed_idle_xstep_equals_part1(mods, ctas):
+    """dg_xstep_stream (the groups without a kept record, streamed by
+    persistent CTAs through shared memory) takes part 1's step bit for bit,
+    with the unshared copies' store into z, and part 2 after it completes
+    the one-part step."""
+    D, srv, T = mods
+    wl, z0, targets = small_setup(D, srv, seed=37)
+    tr = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, rho=(1e-2,) * 5, loss="dssim", intv=1)
+    tr.calibrate_capacity()
+    assert tr._zfuse(True)
+    tr.step(graph=False)                       # non-zero moments and anchors
+    vb = tr.vb
+    vb.dev_cams.copy_(tr.cam_pool[tr.t % len(tr.view_sets)])
+    D.dg_project(tr.x, vb)
+    D.dg_bin_sort(vb)
+    D.dg_rasterize_fwd(vb, tr.bg)
+    tr._loss(tr.targets[tr.t % len(tr.view_sets)])
+    D.dg_rasterize_bwd_records(vb, bg=tr.bg)
+    torch.cuda.synchronize()
+    args = (tr.anchor, tr.shared, tr.rho, tr.lr)
+    ref = {n: getattr(tr, n).clone() for n in ("x", "m", "v", "z")}
+    out = {n: getattr(tr, n).clone() for n in ("x", "m", "v", "z")}
+    D.dg_xstep_part(1, vb, ref["x"], ref["m"], ref["v"], *args, step=2, z_unshared=ref["z"], gid=tr.gid)
+    ws = D.xstep_stream_workspace(tr.x)
+    ws.fill_(-1)                               # the call zeroes its own counters
+    D.dg_xstep_stream(vb, out["x"], out["m"], out["v"], *args, ws, step=2, ctas=ctas, z_unshared=out["z"],
+                      gid=tr.gid)
+    torch.cuda.synchronize()
+    for n in ref:
+        assert torch.equal(ref[n].data, out[n].data), n
+    n_groups = -(-tr.x.n // 128)
+    n_idle = int(ws[0].item())
+    assert 0 < n_idle < n_groups
+    listed = ws[4:4 + n_idle].cpu().numpy()
+    assert len(np.unique(listed)) == n_idle and listed.min() >= 0 and listed.max() < n_groups
+    # a second call with the same workspace takes the next step the same way
+    D.dg_xstep_part(1, vb, ref["x"], ref["m"], ref["v"], *args, step=3)
+    D.dg_xstep_stream(vb, out["x"], out["m"], out["v"], *args, ws, step=3, ctas=ctas)
+    D.dg_xstep_part(2, vb, ref["x"], ref["m"], ref["v"], *args, step=3)
+    D.dg_xstep_part(2, vb, out["x"], out["m"], out["v"], *args, step=3)
+    torch.cuda.synchronize()
+    for n in ("x", "m", "v"):
+        assert torch.equal(ref[n].data, out[n].data), n
+
+
+@pytest.mark.parametrize("mode", ["stream", "grid"])
+def test_overlapped_xstep_trainer_matches(mods, mode):
     """Graph replays with the idle part of the x-step on a side stream equal
     the one-part step (up to the float atomics of the compositing adjoint)."""
     D, srv, T = mods
     wl, z0, targets = small_setup(D, srv, seed=29)
     kw = dict(rho=(1e-2,) * 5, loss="dssim", intv=2)
     a = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, overlap=True, **kw)
+    a.idle_mode = mode
     a.calibrate_capacity()
     b = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, overlap=False, **kw)
     b.calibrate_capacity()
