@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--idle-ctas", type=int, default=0,
                     help="CTAs per SM of the x-step part that runs beside compositing (0: one per SM streamed, "
                          "one per group of copies as a grid)")
-    ap.add_argument("--idle-mode", default="stream", choices=["stream", "grid"],
+    ap.add_argument("--idle-mode", default="stream", choices=["stream", "stream_early", "grid"],
                     help="that x-step part: streamed by persistent CTAs beside the compositing adjoint, or a grid "
                          "launched after the projection")
     ap.add_argument("--no-overlap", action="store_true", help="run that x-step part inline on the main stream")
@@ -445,7 +445,7 @@ def run_ours(args, dist, rank, world):
 
     calls = [("project", lambda: D.dg_project(tr.x, vb))]
     if split:       # the part that the graph runs on a side stream, timed here in sequence
-        if tr.idle_mode == "stream":
+        if tr.idle_mode.startswith("stream"):
             calls.append(("xstep_idle", lambda: D.dg_xstep_stream(vb, *xs_args, tr.xs_ws, step=1, dev_step=tr.dev_step,
                                                                   ctas=tr.n_sm * tr.idle_ctas_per_sm, **zargs)))
         else:

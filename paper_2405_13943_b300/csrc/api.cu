@@ -65,6 +65,7 @@ int launch_xstep(int, int, dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg
                  const dg_camera*, const dg_plan&, const uint2*, const float4*, const AdamArgs&, const int32_t*,
                  dg_gaussians*, const int32_t*, cudaStream_t);
 int xstep_stream_init();
+int raster_bwd_init();
 size_t xstep_stream_ws_bytes(int64_t n);
 int launch_xstep_stream(int, dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*, const uint8_t*,
                         const dg_camera*, const dg_plan&, const uint2*, const AdamArgs&, const int32_t*,
@@ -112,6 +113,7 @@ int ensure_init()
     int rc = bin_sort_init();
     if (rc == DG_OK) rc = loss_init();
     if (rc == DG_OK) rc = xstep_stream_init();
+    if (rc == DG_OK) rc = raster_bwd_init();
     if (rc == DG_OK) done_mask.fetch_or(bit);
     return rc;
 }

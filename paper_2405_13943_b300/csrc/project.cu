@@ -866,20 +866,22 @@ __global__ void __launch_bounds__(kXsThreads, 6) k_xstep_idle(GView x, GView m, 
 // ---- part 1 streamed through shared memory -------------------------------------------
 // The groups without a kept record are listed first (k_idle_groups), then
 // stepped by a few persistent CTAs (one per SM by default) that take groups
-// in a fixed order.  A group's x, m, v and anchors pass through a ring of shared
-// memory by cp.async in segments of 2 KB per array: the three float4 field
-// rows of its 128 copies, then its SH planes four at a time.  A thread copies
-// and later steps the same 16-byte chunk of every segment, so the ring needs
-// no barrier, and kStStages - 1 segments (40 KB a CTA) stay in flight while
-// one is stepped: enough for HBM speed from one CTA per SM, in registers and
-// shared memory that the compositing adjoint leaves free, so this part runs
-// beside it.  Each element's arithmetic is k_xstep_idle's, so the result is
-// the same bit for bit.
+// in a fixed order.  A group's x, m, v and anchors pass through a ring of
+// shared memory by cp.async in segments of 2 KB per array -- the three
+// float4 field rows of its 128 copies, then its SH planes four at a time --
+// two segments to a pipeline unit.  A thread copies and later steps the same
+// 16-byte chunk of every segment, so the ring needs no barrier, and
+// kStStages - 1 units (32 KB a CTA) stay in flight while one is stepped:
+// enough for HBM speed from one CTA per SM, in registers and shared memory
+// that the compositing adjoint leaves free, so this part runs beside it.
+// Each element's arithmetic is k_xstep_idle's, so the result is the same bit
+// for bit.
 constexpr int kStThreads = 128;
 #ifndef DG_XSTEP_STAGES
-#define DG_XSTEP_STAGES 6
+#define DG_XSTEP_STAGES 3   // ring slots of one unit (16 KB each)
 #endif
 constexpr int kStStages = DG_XSTEP_STAGES;
+static_assert(kStStages >= 2, "the ring needs a unit in flight beside the one stepped");
 
 // one warp per group of kXsThreads copies: appends the group to list if none
 // of its copies has a kept record (the order of the list is unspecified);
@@ -909,37 +911,67 @@ __global__ void __launch_bounds__(256) k_idle_groups(int64_t n, const dg_camera*
 }
 
 // what a thread needs of its group: the copy c0 + tid of the field rows and
-// the quad c0 + 4 (tid % 32) .. + 3 of the SH planes
-struct StMeta {
+// the quad c0 + 4 (tid % 32) .. + 3 of the SH planes.  Loaded raw a group
+// ahead (StRaw: the loads only, so that nothing waits on them), decoded
+// where first used (StMeta).
+struct StRaw {
     int64_t c0;       // first copy of the group; -1: none (past the end of the list)
+    uint32_t fs, qs;  // shared flag of the copy; of the quad's copies, a byte each
+    int32_t fg;       // global id of the copy
+    int32_t qg[4];    // of the quad's copies
+};
+
+struct StMeta {
+    int64_t c0;       // as in StRaw
     uint32_t bits;    // 1: copy active (c < n), 2: copy shared; 1 << (4 + i): quad copy i active, 1 << (8 + i): shared
     int32_t zf;       // global id of an unshared copy for the z store, else -1
     int32_t zq[4];    // the same for the quad's copies
 };
 
-__device__ __forceinline__ void st_meta(StMeta& M, int64_t c0, const GView& x, const uint8_t* __restrict__ shared,
+__device__ __forceinline__ void st_load(StRaw& R, int64_t c0, const GView& x, const uint8_t* __restrict__ shared,
                                         const ZOut& zo)
 {
     const int tid = threadIdx.x;
-    M.c0 = c0;
+    R.c0 = c0;
+    R.fs = R.qs = 0;
+    R.fg = -1;
+#pragma unroll
+    for (int i = 0; i < 4; i++) R.qg[i] = -1;
+    if (c0 < 0) return;
+    const int64_t c = c0 + tid, cq = c0 + 4 * (tid & 31);
+    if (c < x.n) {
+        if (shared != nullptr) R.fs = shared[c];
+        if (zo.gid != nullptr) R.fg = zo.gid[c];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if (cq + i >= x.n) continue;
+        if (shared != nullptr) R.qs |= (uint32_t)shared[cq + i] << (8 * i);
+        if (zo.gid != nullptr) R.qg[i] = zo.gid[cq + i];
+    }
+}
+
+__device__ __forceinline__ void st_decode(StMeta& M, const StRaw& R, const GView& x, const ZOut& zo)
+{
+    const int tid = threadIdx.x;
+    M.c0 = R.c0;
     M.bits = 0;
     M.zf = -1;
 #pragma unroll
     for (int i = 0; i < 4; i++) M.zq[i] = -1;
-    if (c0 < 0) return;
-    const int64_t c = c0 + tid;
+    if (R.c0 < 0) return;
+    const int64_t c = R.c0 + tid, cq = R.c0 + 4 * (tid & 31);
     if (c < x.n) {
-        const bool s = shared != nullptr && shared[c] != 0;
+        const bool s = R.fs != 0;
         M.bits |= 1u | (s ? 2u : 0u);
-        if (zo.gid != nullptr && !s) M.zf = zo.gid[c];
+        if (zo.gid != nullptr && !s) M.zf = R.fg;
     }
-    const int64_t cq = c0 + 4 * (tid & 31);
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         if (cq + i >= x.n) continue;
-        const bool s = shared != nullptr && shared[cq + i] != 0;
+        const bool s = ((R.qs >> (8 * i)) & 0xFFu) != 0;
         M.bits |= (1u << (4 + i)) | (s ? 1u << (8 + i) : 0u);
-        if (zo.gid != nullptr && !s) M.zq[i] = zo.gid[cq + i];
+        if (zo.gid != nullptr && !s) M.zq[i] = R.qg[i];
     }
 }
 
@@ -973,82 +1005,90 @@ __device__ __forceinline__ float4* st_row(const GView& g)
 }
 
 // producer: this thread's chunk of x, m, v (and the anchors where its copies
-// are shared) of segment SEG into ring stage s
-template <int SEG, int NP>
+// are shared) of segment SEG into the ring slot s (segments past the
+// group's last have none)
+template <int SEG, int NSEG, int NP>
 __device__ __forceinline__ void st_issue(float4* s, const StMeta& M, const GView& x, const GView& m,
                                          const GView& v, const GView& an)
 {
-    const int64_t u = st_chunk<SEG, NP>(M, x);
-    if (u < 0) return;
-    const int tid = threadIdx.x;
-    st_copy16(s + tid, st_row<SEG>(x) + u);
-    st_copy16(s + kStThreads + tid, st_row<SEG>(m) + u);
-    st_copy16(s + 2 * kStThreads + tid, st_row<SEG>(v) + u);
-    const bool need_a = SEG < 3 ? (M.bits & 2u) != 0 : ((M.bits >> 8) & 15u) != 0;
-    if (need_a) st_copy16(s + 3 * kStThreads + tid, st_row<SEG>(an) + u);
+    if constexpr (SEG < NSEG) {
+        const int64_t u = st_chunk<SEG, NP>(M, x);
+        if (u < 0) return;
+        const int tid = threadIdx.x;
+        st_copy16(s + tid, st_row<SEG>(x) + u);
+        st_copy16(s + kStThreads + tid, st_row<SEG>(m) + u);
+        st_copy16(s + 2 * kStThreads + tid, st_row<SEG>(v) + u);
+        const bool need_a = SEG < 3 ? (M.bits & 2u) != 0 : ((M.bits >> 8) & 15u) != 0;
+        if (need_a) st_copy16(s + 3 * kStThreads + tid, st_row<SEG>(an) + u);
+    }
 }
 
-// consumer: the Adam + penalty step of this thread's chunk of segment SEG
-// from ring stage s, written back to x, m, v (and z for unshared copies).
-// Branch-free over the chunk's four elements: each is stepped as
-// k_xstep_idle steps it, then kept or discarded by a select (an element that
-// is not stepped -- a copy past n, the scale's padding lane -- keeps its
-// value), so the four updates interleave.
 struct Rho5 {
     float r[5];   // the penalties of the five groups, read once per CTA
 };
 
-template <int SEG, int NP>
+// consumer: the Adam + penalty step of this thread's chunk of segment SEG
+// from ring slot s, written back to x, m, v (and z for unshared copies).
+// Without branches: each of the chunk's four elements is stepped as
+// k_xstep_idle steps it, then kept or discarded by a select (an element that
+// is not stepped -- a copy past n, the scale's padding lane -- keeps its
+// value), and only the stores depend on whether the chunk exists, so the
+// updates of a unit's two chunks interleave.
+template <int SEG, int NSEG, int NP>
 __device__ __forceinline__ void st_step(const float4* s, const StMeta& M, GView& x, GView& m, GView& v,
                                         const AdamArgs& a, const Rho5& rh, float ic1, float ic2, const ZOut& zo)
 {
-    const int64_t u = st_chunk<SEG, NP>(M, x);
-    if (u < 0) return;
-    const int tid = threadIdx.x;
-    const float4 X = s[tid], Mo = s[kStThreads + tid], V = s[2 * kStThreads + tid], A = s[3 * kStThreads + tid];
-    const float x0[4] = {X.x, X.y, X.z, X.w}, m0[4] = {Mo.x, Mo.y, Mo.z, Mo.w}, v0[4] = {V.x, V.y, V.z, V.w};
-    const float as[4] = {A.x, A.y, A.z, A.w};        // read only for shared copies (loaded then)
-    float xs[4], ms[4], vs[4];
+    if constexpr (SEG < NSEG) {
+        const int64_t u = st_chunk<SEG, NP>(M, x);
+        const int tid = threadIdx.x;
+        const float4 X = s[tid], Mo = s[kStThreads + tid], V = s[2 * kStThreads + tid];
+        const float4 A = s[3 * kStThreads + tid];
+        const float x0[4] = {X.x, X.y, X.z, X.w}, m0[4] = {Mo.x, Mo.y, Mo.z, Mo.w}, v0[4] = {V.x, V.y, V.z, V.w};
+        const float as[4] = {A.x, A.y, A.z, A.w};    // read only for shared copies (loaded then)
+        float xs[4], ms[4], vs[4];
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        // step, penalty group and learning rate of element i (constants of SEG and i)
-        bool step;
-        float rho, lr;
-        if (SEG == 0) {
-            step = (M.bits & 1u) != 0;
-            rho = rh.r[i < 3 ? 0 : 4];
-            lr = i < 3 ? a.lr[0] : a.lr[5];
-        } else if (SEG == 1) {
-            step = (M.bits & 1u) != 0;
-            rho = rh.r[1];
-            lr = a.lr[1];
-        } else if (SEG == 2) {
-            step = i < 3 && (M.bits & 1u) != 0;
-            rho = rh.r[2];
-            lr = a.lr[2];
-        } else {
-            step = ((M.bits >> (4 + i)) & 1u) != 0;
-            rho = rh.r[3];
-            lr = 4 * (SEG - 3) + (tid >> 5) < 3 ? a.lr[3] : a.lr[4];
+        for (int i = 0; i < 4; i++) {
+            // step, penalty and learning rate of element i (constants of SEG and i)
+            bool step;
+            float rho, lr;
+            if (SEG == 0) {
+                step = (M.bits & 1u) != 0;
+                rho = rh.r[i < 3 ? 0 : 4];
+                lr = i < 3 ? a.lr[0] : a.lr[5];
+            } else if (SEG == 1) {
+                step = (M.bits & 1u) != 0;
+                rho = rh.r[1];
+                lr = a.lr[1];
+            } else if (SEG == 2) {
+                step = i < 3 && (M.bits & 1u) != 0;
+                rho = rh.r[2];
+                lr = a.lr[2];
+            } else {
+                step = ((M.bits >> (4 + i)) & 1u) != 0;
+                rho = rh.r[3];
+                lr = 4 * (SEG - 3) + (tid >> 5) < 3 ? a.lr[3] : a.lr[4];
+            }
+            const bool sh = SEG < 3 ? (M.bits & 2u) != 0 : ((M.bits >> (8 + i)) & 1u) != 0;
+            const float g = sh ? penalty_add(0.f, rho, x0[i], as[i]) : 0.f;
+            float xi = x0[i], mi = m0[i], vi = v0[i];
+            adam_scalar(xi, g, mi, vi, lr, a.b1, a.b2, a.eps, ic1, ic2);
+            xs[i] = step ? xi : x0[i];
+            ms[i] = step ? mi : m0[i];
+            vs[i] = step ? vi : v0[i];
         }
-        const bool sh = SEG < 3 ? (M.bits & 2u) != 0 : ((M.bits >> (8 + i)) & 1u) != 0;
-        const float g = sh ? penalty_add(0.f, rho, x0[i], as[i]) : 0.f;
-        float xi = x0[i], mi = m0[i], vi = v0[i];
-        adam_scalar(xi, g, mi, vi, lr, a.b1, a.b2, a.eps, ic1, ic2);
-        xs[i] = step ? xi : x0[i];
-        ms[i] = step ? mi : m0[i];
-        vs[i] = step ? vi : v0[i];
-    }
-    st_row<SEG>(x)[u] = make_float4(xs[0], xs[1], xs[2], xs[3]);
-    st_row<SEG>(m)[u] = make_float4(ms[0], ms[1], ms[2], ms[3]);
-    st_row<SEG>(v)[u] = make_float4(vs[0], vs[1], vs[2], vs[3]);
-    if (SEG < 3) {
-        if (M.zf >= 0) st_row<SEG>(zo.z)[M.zf] = make_float4(xs[0], xs[1], xs[2], xs[3]);
-    } else {
-        const int j = 4 * (SEG - 3) + (tid >> 5);
+        if (u >= 0) {
+            st_row<SEG>(x)[u] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+            st_row<SEG>(m)[u] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+            st_row<SEG>(v)[u] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+            if (SEG < 3) {
+                if (M.zf >= 0) st_row<SEG>(zo.z)[M.zf] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+            } else {
+                const int j = 4 * (SEG - 3) + (tid >> 5);
 #pragma unroll
-        for (int i = 0; i < 4; i++)
-            if (M.zq[i] >= 0) zo.z.sh[(int64_t)j * zo.z.ld + M.zq[i]] = xs[i];
+                for (int i = 0; i < 4; i++)
+                    if (M.zq[i] >= 0) zo.z.sh[(int64_t)j * zo.z.ld + M.zq[i]] = xs[i];
+            }
+        }
     }
 }
 
@@ -1056,51 +1096,64 @@ template <int N>
 __device__ __forceinline__ void st_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void st_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
-// unit k of a CTA's sequence (group k / NSEG, segment k % NSEG) lives in
-// ring stage k mod NS; a group starts at stage `base`
+// The pipeline's unit is two segments (one commit group, a ring slot of
+// 2 x 4 x kStThreads float4): unit k of a CTA's sequence lives in slot
+// k mod NS, and a group's first unit in slot `base`.
 template <int NS>
-__device__ __forceinline__ float4* st_stage(float4* ring, int base, int k)
+__device__ __forceinline__ float4* st_slot(float4* ring, int base, int k)
 {
-    return ring + ((base + k) % NS) * 4 * kStThreads;
+    return ring + ((base + k) % NS) * 8 * kStThreads;
 }
 
-// segment SEG of a group: the producer's unit SEG + NS - 1 (of this group,
-// or past its last segment the next group's, with nm), then the consumer's
-template <int SEG, int NSEG, int NS, int NP>
-__device__ __forceinline__ void st_segment(float4* ring, int base, const StMeta& cm, const StMeta& nm, GView& x,
-                                           GView& m, GView& v, const GView& an, const AdamArgs& a, const Rho5& rh,
-                                           float ic1, float ic2, const ZOut& zo)
+template <int U, int NSEG, int NP>
+__device__ __forceinline__ void st_issue_unit(float4* s, const StMeta& M, const GView& x, const GView& m,
+                                              const GView& v, const GView& an)
 {
-    constexpr int P = SEG + NS - 1;
-    if constexpr (P < NSEG)
-        st_issue<P, NP>(st_stage<NS>(ring, base, P), cm, x, m, v, an);
-    else
-        st_issue<P - NSEG, NP>(st_stage<NS>(ring, base, P), nm, x, m, v, an);
+    st_issue<2 * U, NSEG, NP>(s, M, x, m, v, an);
+    st_issue<2 * U + 1, NSEG, NP>(s + 4 * kStThreads, M, x, m, v, an);
     st_commit();
-    st_wait<NS - 1>();
-    st_step<SEG, NP>(st_stage<NS>(ring, base, SEG), cm, x, m, v, a, rh, ic1, ic2, zo);
-    if constexpr (SEG + 1 < NSEG)
-        st_segment<SEG + 1, NSEG, NS, NP>(ring, base, cm, nm, x, m, v, an, a, rh, ic1, ic2, zo);
 }
 
-template <int SEG, int NS, int NP>
+// unit U of a group: the producer's unit U + NS - 1 (of this group, or past
+// its last unit the next group's, with nm -- decoded from its raw loads
+// just before its first use), then the consumer's unit U
+template <int U, int NU, int NSEG, int NS, int NP>
+__device__ __forceinline__ void st_unit(float4* ring, int base, const StMeta& cm, StMeta& nm, const StRaw& nr,
+                                        GView& x, GView& m, GView& v, const GView& an, const AdamArgs& a,
+                                        const Rho5& rh, float ic1, float ic2, const ZOut& zo)
+{
+    constexpr int P = U + NS - 1;
+    if constexpr (P < NU) {
+        st_issue_unit<P, NSEG, NP>(st_slot<NS>(ring, base, P), cm, x, m, v, an);
+    } else {
+        if constexpr (P == NU) st_decode(nm, nr, x, zo);
+        st_issue_unit<P - NU, NSEG, NP>(st_slot<NS>(ring, base, P), nm, x, m, v, an);
+    }
+    st_wait<NS - 1>();
+    float4* s = st_slot<NS>(ring, base, U);
+    st_step<2 * U, NSEG, NP>(s, cm, x, m, v, a, rh, ic1, ic2, zo);
+    st_step<2 * U + 1, NSEG, NP>(s + 4 * kStThreads, cm, x, m, v, a, rh, ic1, ic2, zo);
+    if constexpr (U + 1 < NU)
+        st_unit<U + 1, NU, NSEG, NS, NP>(ring, base, cm, nm, nr, x, m, v, an, a, rh, ic1, ic2, zo);
+}
+
+template <int U, int NS, int NSEG, int NP>
 __device__ __forceinline__ void st_prologue(float4* ring, const StMeta& cm, const GView& x, const GView& m,
                                             const GView& v, const GView& an)
 {
-    if constexpr (SEG < NS - 1) {
-        st_issue<SEG, NP>(ring + SEG * 4 * kStThreads, cm, x, m, v, an);
-        st_commit();
-        st_prologue<SEG + 1, NS, NP>(ring, cm, x, m, v, an);
+    if constexpr (U < NS - 1) {
+        st_issue_unit<U, NSEG, NP>(ring + U * 8 * kStThreads, cm, x, m, v, an);
+        st_prologue<U + 1, NS, NSEG, NP>(ring, cm, x, m, v, an);
     }
 }
 
 // the persistent streamed part 1 over list[0 .. ctr[0]) (ctr[0] written by
 // k_idle_groups): CTA b takes the entries b, b + G, b + 2 G, ... (G CTAs),
-// one group per iteration with its NSEG segments unrolled.  Producer and
-// consumer are the same threads, the producer NS - 1 segments ahead (NS <=
-// NSEG), so the producer's last NS - 1 units of an iteration are the next
-// group's first.  The next group's metadata (nm) and the list entry after it
-// are loaded a group ahead, so no load waits.
+// one group per iteration with its NU units unrolled.  Producer and consumer
+// are the same threads, the producer NS - 1 units ahead (NS <= NU), so its
+// last NS - 1 units of an iteration are the next group's first.  The next
+// group's metadata is loaded raw a group ahead and the list entry after it
+// two, so no load is waited for.
 template <int DEG>
 __global__ void __launch_bounds__(kStThreads) k_xstep_stream(GView x, GView m, GView v, GView an,
                                                             const uint8_t* __restrict__ shared,
@@ -1108,9 +1161,9 @@ __global__ void __launch_bounds__(kStThreads) k_xstep_stream(GView x, GView m, G
                                                             const uint32_t* __restrict__ ctr, AdamArgs a,
                                                             const int32_t* __restrict__ dev_step, ZOut zo)
 {
-    constexpr int NK = (DEG + 1) * (DEG + 1), NP = 3 * NK, NSEG = 3 + (NP + 3) / 4;
-    constexpr int NS = kStStages < NSEG ? kStStages : NSEG;
-    extern __shared__ __align__(16) float4 s_ring[];   // [NS][x, m, v, anchor][kStThreads]
+    constexpr int NK = (DEG + 1) * (DEG + 1), NP = 3 * NK, NSEG = 3 + (NP + 3) / 4, NU = (NSEG + 1) / 2;
+    constexpr int NS = kStStages < NU ? kStStages : NU;
+    extern __shared__ __align__(16) float4 s_ring[];   // [NS][2 segments][x, m, v, anchor][kStThreads]
     float ic1, ic2;
     bias_corr(a, dev_step, ic1, ic2);
     Rho5 rh;
@@ -1119,19 +1172,21 @@ __global__ void __launch_bounds__(kStThreads) k_xstep_stream(GView x, GView m, G
     const uint32_t n_list = ctr[0], G = gridDim.x;
     uint32_t li = blockIdx.x;
     auto entry = [&](uint32_t i) { return i < n_list ? (int64_t)list[i] * kXsThreads : (int64_t)-1; };
+    StRaw nr;
     StMeta cm, nm;
-    st_meta(cm, entry(li), x, shared, zo);
-    st_meta(nm, entry(li + G), x, shared, zo);
+    st_load(nr, entry(li), x, shared, zo);
+    st_decode(cm, nr, x, zo);
+    st_load(nr, entry(li + G), x, shared, zo);
     int64_t c0_ahead = entry(li + 2 * G);
     li += 3 * G;
-    st_prologue<0, NS, NP>(s_ring, cm, x, m, v, an);
+    st_prologue<0, NS, NSEG, NP>(s_ring, cm, x, m, v, an);
     int base = 0;
 #pragma unroll 1
     while (cm.c0 >= 0) {
-        st_segment<0, NSEG, NS, NP>(s_ring, base, cm, nm, x, m, v, an, a, rh, ic1, ic2, zo);
-        base = (base + NSEG) % NS;
+        st_unit<0, NU, NSEG, NS, NP>(s_ring, base, cm, nm, nr, x, m, v, an, a, rh, ic1, ic2, zo);
+        base = (base + NU) % NS;
         cm = nm;
-        st_meta(nm, c0_ahead, x, shared, zo);
+        st_load(nr, c0_ahead, x, shared, zo);
         c0_ahead = entry(li);
         li += G;
     }
@@ -1141,8 +1196,8 @@ __global__ void __launch_bounds__(kStThreads) k_xstep_stream(GView x, GView m, G
 template <int DEG>
 constexpr size_t st_smem_bytes()
 {
-    constexpr int NK = (DEG + 1) * (DEG + 1), NSEG = 3 + (3 * NK + 3) / 4;
-    return (size_t)(kStStages < NSEG ? kStStages : NSEG) * 4 * kStThreads * sizeof(float4);
+    constexpr int NK = (DEG + 1) * (DEG + 1), NSEG = 3 + (3 * NK + 3) / 4, NU = (NSEG + 1) / 2;
+    return (size_t)(kStStages < NU ? kStStages : NU) * 8 * kStThreads * sizeof(float4);
 }
 
 // once per device (ensure_init): the ring's dynamic shared memory, and the

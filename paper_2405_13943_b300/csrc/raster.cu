@@ -548,6 +548,27 @@ static void bwd_launch(const float4* rec, const uint32_t* vals, const uint32_t* 
                                                                  dL_dimage, drec, SlotOut{});
 }
 
+// once per device: the backward's shared-memory carveout at its maximum,
+// so that every SM keeps room beside its CTAs for the persistent x-step
+// that runs with it (dg_xstep_stream)
+int raster_bwd_init()
+{
+    const int c = (int)cudaSharedmemCarveoutMaxShared;
+    const cudaFuncAttribute at = cudaFuncAttributePreferredSharedMemoryCarveout;
+    if (cudaFuncSetAttribute(k_raster_bwd<1, 1>, at, c) != cudaSuccess ||
+        cudaFuncSetAttribute(k_raster_bwd<1, 2>, at, c) != cudaSuccess ||
+        cudaFuncSetAttribute(k_raster_bwd<2, 1>, at, c) != cudaSuccess ||
+        cudaFuncSetAttribute(k_raster_bwd<2, 2>, at, c) != cudaSuccess ||
+        cudaFuncSetAttribute(k_raster_bwd<4, 1>, at, c) != cudaSuccess ||
+        cudaFuncSetAttribute(k_raster_bwd<4, 2>, at, c) != cudaSuccess ||
+        cudaFuncSetAttribute(k_raster_bwd<8, 1>, at, c) != cudaSuccess ||
+        cudaFuncSetAttribute(k_raster_bwd<8, 2>, at, c) != cudaSuccess ||
+        cudaFuncSetAttribute(k_raster_bwd<1, 1, true>, at, c) != cudaSuccess ||
+        cudaFuncSetAttribute(k_raster_bwd<1, 2, true>, at, c) != cudaSuccess)
+        return DG_ERR_CUDA;
+    return DG_OK;
+}
+
 #define DG_RASTER_DISPATCH(P, FN, ...)                                       \
     switch (P.raster_warps * 10 + P.raster_stage) {                          \
     case 11: FN<1, 1>(__VA_ARGS__); break;                                   \

@@ -70,7 +70,8 @@ class DogsTrainer:
         # how that part runs: "stream" -- dg_xstep_stream, one persistent CTA
         # per SM (idle_ctas_per_sm: 0 = one) moving the groups through shared
         # memory, launched with the compositing adjoint, beside which it fits;
-        # "grid" -- dg_xstep_part 1 right after the projection
+        # "stream_early" -- the same right after the projection; "grid" --
+        # dg_xstep_part 1 right after the projection
         self.idle_mode = "stream"
         self.n_sm = torch.cuda.get_device_properties(device).multi_processor_count if self.side is not None else 0
         self.adaptive = adaptive
@@ -232,7 +233,7 @@ class DogsTrainer:
         D.dg_step_advance(self.dev_step)
         D.dg_project(self.x, vb)
         zf = self._zfuse(consensus)
-        if self._split_xstep() and self.idle_mode == "grid":
+        if self._split_xstep() and self.idle_mode in ("grid", "stream_early"):
             self.idle_xstep(zf)
         D.dg_bin_sort(vb)
         D.dg_rasterize_fwd(vb, self.bg)
@@ -328,7 +329,7 @@ class DogsTrainer:
         cur = torch.cuda.current_stream()
         self.side.wait_stream(cur)
         with torch.cuda.stream(self.side):
-            if self.idle_mode == "stream":
+            if self.idle_mode.startswith("stream"):
                 D.dg_xstep_stream(self.vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(), self.lr,
                                   self.xs_ws, step=1, dev_step=self.dev_step, ctas=self.n_sm * self.idle_ctas_per_sm,
                                   **self._zargs(zfuse))
