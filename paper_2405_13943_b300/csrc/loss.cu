@@ -179,29 +179,57 @@ __device__ __forceinline__ SsimItem ssim_item(const dg_camera* __restrict__ cams
     return it;
 }
 
-// copy NP planes (plane m at base[m] + m * plane_stride) of item `it`'s
+// the view of work item w (the items of a view are consecutive)
+__device__ __forceinline__ int ssim_view(int w, int TX, int TY) { return w / (3 * TX * TY); }
+
+// A thread's share of a per-view sum (the SSIM map, the L1 term) over the
+// CTA's consecutive items of one view, added to sum[v] when the next item is
+// of another view or there is none: one atomic per warp and view run, and no
+// barrier or double arithmetic per item.
+__device__ __forceinline__ void ssim_flush(float& part, int w, int n_work, int v, int TX, int TY,
+                                           double* __restrict__ sum)
+{
+    const int wn = w + (int)gridDim.x;
+    if (wn < n_work && ssim_view(wn, TX, TY) == v) return;     // uniform over the CTA
+    float s = part;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s != 0.f) atomicAdd(&sum[v], (double)s);
+    part = 0.f;
+}
+
+// copy NP planes (plane m at pl[m], an item's channel plane) of item `it`'s
 // input rows, global columns x0 - 8 .. x0 + 39, into dst[m][kIH][kIWP]: by
 // 16-byte chunks when the width and the planes allow it (a chunk is then
-// wholly inside or wholly outside the image), else element by element
+// wholly inside or wholly outside the image), else element by element.  The
+// planes are taken one after another with a constant index, so their
+// pointers stay in registers.
+struct Planes {
+    const float* p[3];
+};
+
 template <int NP>
-__device__ __forceinline__ void ssim_issue(const SsimItem& it, const float* const* base, int64_t plane_stride,
-                                           float* dst)
+__device__ __forceinline__ void ssim_issue(const SsimItem& it, const Planes& pl, float* dst)
 {
     if (!it.ok) return;
     const int gx0 = it.x0 - 8, gy0 = it.y0 - kR;
     bool vec = (it.W & 3) == 0;
 #pragma unroll
-    for (int m = 0; m < NP; m++) vec = vec && (((uintptr_t)(base[m] + m * plane_stride) & 15u) == 0);
+    for (int m = 0; m < NP; m++) vec = vec && (((uintptr_t)pl.p[m] & 15u) == 0);
     if (vec) {
-        constexpr int CH = kIWv / 4;
-        for (int i = threadIdx.x; i < NP * kIH * CH; i += kSsimThreads) {
-            const int m = i / (kIH * CH), rem = i - m * (kIH * CH);
-            const int r = rem / CH, q = rem - r * CH;
-            const int gx = gx0 + 4 * q, gy = gy0 + r;
-            const bool ok = gx >= 0 && gx < it.W && gy >= 0 && gy < it.H;
-            const float* src = base[m] + m * plane_stride + (ok ? (int64_t)gy * it.W + gx : 0);
-            cp_async16(dst + (m * kIH + r) * kIWP + 4 * q, src, ok);
-        }
+        constexpr int CH = kIWv / 4;                  // 16-byte chunks per row
+        static_assert((kIH * CH) % kSsimThreads == 0, "whole chunks per thread");
+#pragma unroll
+        for (int m = 0; m < NP; m++)
+#pragma unroll
+            for (int k = 0; k < kIH * CH / kSsimThreads; k++) {
+                const int i = (int)threadIdx.x + k * kSsimThreads;
+                const int r = i / CH, q = i - r * CH;
+                const int gx = gx0 + 4 * q, gy = gy0 + r;
+                const bool ok = gx >= 0 && gx < it.W && gy >= 0 && gy < it.H;
+                const float* src = pl.p[m] + (ok ? (int64_t)gy * it.W + gx : 0);
+                cp_async16(dst + (m * kIH + r) * kIWP + 4 * q, src, ok);
+            }
     } else {
         for (int i = threadIdx.x; i < kIH * kIWv; i += kSsimThreads) {
             const int r = i / kIWv, c = i - r * kIWv;
@@ -210,7 +238,7 @@ __device__ __forceinline__ void ssim_issue(const SsimItem& it, const float* cons
             const int64_t p = ok ? (int64_t)gy * it.W + gx : 0;
 #pragma unroll
             for (int m = 0; m < NP; m++)
-                cp_async4(dst + (m * kIH + r) * kIWP + c, base[m] + m * plane_stride + p, ok);
+                cp_async4(dst + (m * kIH + r) * kIWP + c, pl.p[m] + p, ok);
         }
     }
 }
@@ -223,15 +251,15 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restri
     extern __shared__ float s_dyn[];
     float* s_in = s_dyn;                                   // [2 buffers][x, y][kIH][kIWP]
     float (*s_tmp)[kTHP][kTWP] = reinterpret_cast<float (*)[kTHP][kTWP]>(s_dyn + 4 * kIH * kIWP);
-    __shared__ float s_w[kSsimThreads / 32];
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    float part = 0.f;   // this thread's SSIM sum over the current view's items
     int buf = 0;
     {
         const int w = blockIdx.x;
         if (w < n_work) {
             const SsimItem it = ssim_item(cams, w, TX, TY);
-            const float* bp[2] = {img + 3 * it.pix + it.ch * it.HW, tgt + 3 * it.pix + it.ch * it.HW};
-            ssim_issue<2>(it, bp, 0, s_in);
+            const Planes bp = {{img + 3 * it.pix + it.ch * it.HW, tgt + 3 * it.pix + it.ch * it.HW, nullptr}};
+            ssim_issue<2>(it, bp, s_in);
         }
         cp_async_commit();
     }
@@ -239,14 +267,17 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restri
         const int wn = w + gridDim.x;
         if (wn < n_work) {
             const SsimItem nt = ssim_item(cams, wn, TX, TY);
-            const float* bp[2] = {img + 3 * nt.pix + nt.ch * nt.HW, tgt + 3 * nt.pix + nt.ch * nt.HW};
-            ssim_issue<2>(nt, bp, 0, s_in + (buf ^ 1) * 2 * kIH * kIWP);
+            const Planes bp = {{img + 3 * nt.pix + nt.ch * nt.HW, tgt + 3 * nt.pix + nt.ch * nt.HW, nullptr}};
+            ssim_issue<2>(nt, bp, s_in + (buf ^ 1) * 2 * kIH * kIWP);
         }
         cp_async_commit();
         cp_async_wait_prev();
         __syncthreads();
         const SsimItem it = ssim_item(cams, w, TX, TY);
-        if (!it.ok) continue;                         // uniform over the CTA
+        if (!it.ok) {                                 // uniform over the CTA
+            ssim_flush(part, w, n_work, it.v, TX, TY, sums);
+            continue;
+        }
         const float* maps[2] = {s_in + buf * 2 * kIH * kIWP, s_in + (buf * 2 + 1) * kIH * kIWP};
         hpass<5, 2>(g, maps, s_tmp, [&](float (*raw)[24], int c, float (*in)[kWin8], int i) {
             const float a = raw[0][c], b = raw[1][c];
@@ -254,7 +285,6 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restri
         });
         __syncthreads();
         const float sc = -w_ssim / (float)(3 * it.HW);
-        float acc = 0.f;
         float* P = partial + 9 * it.pix + 3 * it.ch * it.HW;
         if (threadIdx.x < kTW * kVBlocks) {
             const int c = threadIdx.x % kTW, r0 = (threadIdx.x / kTW) * kBlk;
@@ -271,7 +301,7 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restri
                 const float B1 = m1 * m1 + m2 * m2 + C1, B2 = s1 + s2 + C2;
                 const float iB = __fdividef(1.f, B1 * B2);
                 const float S = A1 * A2 * iB;
-                acc += S;
+                part += S;
                 // dS/dA1, dS/dA2, dS/dB1 = -S / B1 = -S B2 iB, dS/dB2 = -S B1 iB
                 const float dA1 = A2 * iB, dA2 = A1 * iB, dB1 = -S * B2 * iB, dB2 = -S * B1 * iB;
                 const float dm1 = 2.f * m2 * dA1 - 2.f * m2 * dA2 + 2.f * m1 * dB1 - 2.f * m1 * dB2;
@@ -281,15 +311,7 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restri
                 P[2 * it.HW + p] = sc * 2.f * dA2;
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int i = 0; i < kSsimThreads / 32; i++) t += s_w[i];
-            atomicAdd(&sums[it.v], t);
-        }
+        ssim_flush(part, w, n_work, it.v, TX, TY, sums);
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
@@ -308,8 +330,8 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const float* __restri
     extern __shared__ float s_dyn[];
     float* s_in = s_dyn;                                   // [2 buffers][3 maps][kIH][kIWP]
     float (*s_tmp)[kTHP][kTWP] = reinterpret_cast<float (*)[kTHP][kTWP]>(s_dyn + 6 * kIH * kIWP);
-    __shared__ float s_w[kSsimThreads / 32];
     const bool has_out = threadIdx.x < kTW * kVBlocks;
+    float part = 0.f;   // this thread's L1 sum over the current view's items
     const int c = threadIdx.x % kTW, r0 = (threadIdx.x / kTW) * kBlk;
     int buf = 0;
     {
@@ -317,8 +339,8 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const float* __restri
         if (w < n_work) {
             const SsimItem it = ssim_item(cams, w, TX, TY);
             const float* P = partial + 9 * it.pix + 3 * it.ch * it.HW;
-            const float* bp[3] = {P, P, P};
-            ssim_issue<3>(it, bp, it.HW, s_in);
+            const Planes bp = {{P, P + it.HW, P + 2 * it.HW}};
+            ssim_issue<3>(it, bp, s_in);
         }
         cp_async_commit();
     }
@@ -327,8 +349,8 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const float* __restri
         if (wn < n_work) {
             const SsimItem nt = ssim_item(cams, wn, TX, TY);
             const float* P = partial + 9 * nt.pix + 3 * nt.ch * nt.HW;
-            const float* bp[3] = {P, P, P};
-            ssim_issue<3>(nt, bp, nt.HW, s_in + (buf ^ 1) * 3 * kIH * kIWP);
+            const Planes bp = {{P, P + nt.HW, P + 2 * nt.HW}};
+            ssim_issue<3>(nt, bp, s_in + (buf ^ 1) * 3 * kIH * kIWP);
         }
         cp_async_commit();
         const SsimItem it = ssim_item(cams, w, TX, TY);
@@ -347,14 +369,16 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const float* __restri
         }
         cp_async_wait_prev();
         __syncthreads();
-        if (!it.ok) continue;                         // uniform over the CTA
+        if (!it.ok) {                                 // uniform over the CTA
+            ssim_flush(part, w, n_work, it.v, TX, TY, l1_sum);
+            continue;
+        }
         const float* sp0 = s_in + buf * 3 * kIH * kIWP;
         const float* maps[3] = {sp0, sp0 + kIH * kIWP, sp0 + 2 * kIH * kIWP};
         hpass<3, 3>(g, maps, s_tmp, [&](float (*raw)[24], int c, float (*in)[kWin8], int i) {
             in[0][i] = raw[0][c]; in[1][i] = raw[1][c]; in[2][i] = raw[2][c];
         });
         __syncthreads();
-        float acc = 0.f;
         if (has_out) {
             float fo[3][kBlk];
             vpass<3>(g, s_tmp, c, r0, fo);
@@ -366,20 +390,12 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const float* __restri
                 if (r0 + j >= kTH || gx >= it.W || gy >= it.H) continue;
                 const int64_t p = (int64_t)gy * it.W + gx;
                 const float d = xv[j] - yv[j];
-                acc += fabsf(d);
+                part += fabsf(d);
                 const float l1g = d > 0.f ? wl : (d < 0.f ? -wl : 0.f);
                 G[p] = l1g + fo[0][j] + 2.f * xv[j] * fo[1][j] + yv[j] * fo[2][j];
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int i = 0; i < kSsimThreads / 32; i++) t += s_w[i];
-            atomicAdd(&l1_sum[it.v], t);
-        }
+        ssim_flush(part, w, n_work, it.v, TX, TY, l1_sum);
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
