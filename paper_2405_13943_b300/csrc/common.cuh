@@ -121,6 +121,20 @@ __device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b)
     return d;
 }
 
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // ---- Adam with the ADMM penalty (Eq. 8a / 12a), shared by the x-step kernels ----
 struct AdamArgs {
     float rho[5];   // groups p, q, s, f, o
@@ -169,9 +183,9 @@ __device__ __forceinline__ float penalty_add(float g, float rho, float x, float 
     return __fmaf_rn(rho, __fsub_rn(x, a), g);
 }
 
-// square root by the SFU (PTX sqrt.approx.ftz: about 1 ulp, one instruction
-// and no branch, so that the updates of several parameters interleave; the
-// quotient beside it is the approximate division too)
+// square root and reciprocal by the SFU (PTX sqrt.approx.ftz and
+// rcp.approx.ftz: about 1 ulp each, one instruction and no branch, so that
+// the updates of several parameters interleave)
 __device__ __forceinline__ float sqrt_sfu(float x)
 {
     float y;
@@ -179,13 +193,55 @@ __device__ __forceinline__ float sqrt_sfu(float x)
     return y;
 }
 
-// one Adam step of one parameter; g already holds the penalty term
+__device__ __forceinline__ float rcp_sfu(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// one Adam step of one parameter; g already holds the penalty term:
+// m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+// x <- x - lr (m ic1) / (sqrt(v ic2) + eps) with ic1, ic2 the bias corrections
 __device__ __forceinline__ void adam_scalar(float& x, float g, float& m, float& v, float lr, float b1, float b2,
                                             float eps, float ic1, float ic2)
 {
     m = __fmaf_rn(b1, m, __fmul_rn(1.f - b1, g));
     v = __fmaf_rn(b2, v, __fmul_rn(__fmul_rn(1.f - b2, g), g));
-    x = __fmaf_rn(-lr, __fdividef(__fmul_rn(m, ic1), __fadd_rn(sqrt_sfu(__fmul_rn(v, ic2)), eps)), x);
+    const float d = __fadd_rn(sqrt_sfu(__fmul_rn(v, ic2)), eps);
+    x = __fmaf_rn(-lr, __fmul_rn(__fmul_rn(m, ic1), rcp_sfu(d)), x);
+}
+
+// the same step of two parameters at once, by paired FP32 instructions
+// where the operation pairs (each lane rounded exactly as adam_scalar rounds
+// it, so the two give the same bits)
+struct AdamPair {
+    f32x2 b1, c1, b2, c2, ic1, ic2, eps;   // c1 = 1 - b1, c2 = 1 - b2, as adam_scalar forms them
+};
+
+__device__ __forceinline__ AdamPair adam_pair_args(float b1, float b2, float eps, float ic1, float ic2)
+{
+    AdamPair P;
+    P.b1 = f2_pack(b1, b1);
+    P.c1 = f2_pack(1.f - b1, 1.f - b1);
+    P.b2 = f2_pack(b2, b2);
+    P.c2 = f2_pack(1.f - b2, 1.f - b2);
+    P.ic1 = f2_pack(ic1, ic1);
+    P.ic2 = f2_pack(ic2, ic2);
+    P.eps = f2_pack(eps, eps);
+    return P;
+}
+
+// nlr = (-lr, -lr) of the two parameters
+__device__ __forceinline__ void adam_pair(f32x2& x, f32x2 g, f32x2& m, f32x2& v, f32x2 nlr, const AdamPair& P)
+{
+    m = f2_fma(P.b1, m, f2_mul(P.c1, g));
+    v = f2_fma(P.b2, v, f2_mul(f2_mul(P.c2, g), g));
+    float s0, s1;
+    f2_unpack(f2_mul(v, P.ic2), s0, s1);
+    float d0, d1;
+    f2_unpack(f2_add(f2_pack(sqrt_sfu(s0), sqrt_sfu(s1)), P.eps), d0, d1);
+    x = f2_fma(nlr, f2_mul(f2_mul(m, P.ic1), f2_pack(rcp_sfu(d0), rcp_sfu(d1))), x);
 }
 
 }  // namespace dg

@@ -923,10 +923,15 @@ struct StRaw {
 
 struct StMeta {
     int64_t c0;       // as in StRaw
-    uint32_t bits;    // 1: copy active (c < n), 2: copy shared; 1 << (4 + i): quad copy i active, 1 << (8 + i): shared
+    int64_t fo;       // float4 index of the copy in a field row: c0 + tid
+    int64_t po;       // float4 index of the quad in plane tid / 32 (segment 3; + ld per later segment)
+    uint32_t bits;    // 1: copy active (c < n), 2: copy shared; 1 << (4 + i): quad copy i active,
+                      // 1 << (8 + i): shared; 1 << 12: quad inside the planes (cq < ld); 1 << 13: every copy
+                      // of the group active (then the rest of the bits hold for the copy and the quad alike)
     int32_t zf;       // global id of an unshared copy for the z store, else -1
     int32_t zq[4];    // the same for the quad's copies
 };
+constexpr uint32_t kStQuadIn = 1u << 12, kStFull = 1u << 13;
 
 __device__ __forceinline__ void st_load(StRaw& R, int64_t c0, const GView& x, const uint8_t* __restrict__ shared,
                                         const ZOut& zo)
@@ -959,8 +964,13 @@ __device__ __forceinline__ void st_decode(StMeta& M, const StRaw& R, const GView
     M.zf = -1;
 #pragma unroll
     for (int i = 0; i < 4; i++) M.zq[i] = -1;
+    M.fo = M.po = 0;
     if (R.c0 < 0) return;
     const int64_t c = R.c0 + tid, cq = R.c0 + 4 * (tid & 31);
+    M.fo = c;
+    M.po = ((int64_t)(tid >> 5) * x.ld + cq) >> 2;
+    if (cq < x.ld) M.bits |= kStQuadIn;
+    if (R.c0 + kXsThreads <= x.n) M.bits |= kStFull;
     if (c < x.n) {
         const bool s = R.fs != 0;
         M.bits |= 1u | (s ? 2u : 0u);
@@ -989,13 +999,11 @@ __device__ __forceinline__ void st_copy16(float4* dst, const float4* src)
 template <int SEG, int NP>
 __device__ __forceinline__ int64_t st_chunk(const StMeta& M, const GView& x)
 {
-    const int tid = threadIdx.x;
     if (M.c0 < 0) return -1;
-    if (SEG < 3) return (M.bits & 1u) ? M.c0 + tid : -1;
-    const int j = 4 * (SEG - 3) + (tid >> 5);
-    const int64_t cq = M.c0 + 4 * (tid & 31);
-    if (4 * (SEG - 3) + 3 >= NP && j >= NP) return -1;    // the last segment may hold fewer planes
-    return cq < x.ld ? (((int64_t)j * x.ld + cq) >> 2) : -1;
+    if (SEG < 3) return (M.bits & 1u) ? M.fo : -1;
+    if (4 * (SEG - 3) + 3 >= NP && 4 * (SEG - 3) + (int)(threadIdx.x >> 5) >= NP)
+        return -1;                                       // the last segment may hold fewer planes
+    return (M.bits & kStQuadIn) ? M.po + (int64_t)(SEG - 3) * x.ld : -1;
 }
 
 template <int SEG>
@@ -1027,67 +1035,136 @@ struct Rho5 {
     float r[5];   // the penalties of the five groups, read once per CTA
 };
 
+// the per-CTA constants of the paired step: Adam's, and (-lr, -lr) and
+// (rho, rho) of each parameter class of a segment's float4
+struct StPair {
+    AdamPair P;
+    f32x2 nlr_p, nlr_po, nlr_q, nlr_s, nlr_dc, nlr_rest;   // p, (p, o), q, s, SH DC, SH rest
+    f32x2 rho_p, rho_po, rho_q, rho_s, rho_f;
+};
+
+__device__ __forceinline__ StPair st_pair_args(const AdamArgs& a, const Rho5& rh, float ic1, float ic2)
+{
+    StPair S;
+    S.P = adam_pair_args(a.b1, a.b2, a.eps, ic1, ic2);
+    S.nlr_p = f2_pack(-a.lr[0], -a.lr[0]);
+    S.nlr_po = f2_pack(-a.lr[0], -a.lr[5]);
+    S.nlr_q = f2_pack(-a.lr[1], -a.lr[1]);
+    S.nlr_s = f2_pack(-a.lr[2], -a.lr[2]);
+    S.nlr_dc = f2_pack(-a.lr[3], -a.lr[3]);
+    S.nlr_rest = f2_pack(-a.lr[4], -a.lr[4]);
+    S.rho_p = f2_pack(rh.r[0], rh.r[0]);
+    S.rho_po = f2_pack(rh.r[0], rh.r[4]);
+    S.rho_q = f2_pack(rh.r[1], rh.r[1]);
+    S.rho_s = f2_pack(rh.r[2], rh.r[2]);
+    S.rho_f = f2_pack(rh.r[3], rh.r[3]);
+    return S;
+}
+
+// two parameters (lanes of x2) of a chunk by the paired step: the penalty
+// rho (x - a) + 0 where the copy is shared (s0, s1), else a zero gradient
+__device__ __forceinline__ void st_pair_step(f32x2& x2, f32x2& m2, f32x2& v2, f32x2 a2, bool s0, bool s1,
+                                             f32x2 rho2, f32x2 nlr2, const AdamPair& P)
+{
+    float p0, p1;
+    f2_unpack(f2_fma(rho2, f2_sub(x2, a2), f2_pack(0.f, 0.f)), p0, p1);
+    adam_pair(x2, f2_pack(s0 ? p0 : 0.f, s1 ? p1 : 0.f), m2, v2, nlr2, P);
+}
+
 // consumer: the Adam + penalty step of this thread's chunk of segment SEG
 // from ring slot s, written back to x, m, v (and z for unshared copies).
-// Without branches: each of the chunk's four elements is stepped as
-// k_xstep_idle steps it, then kept or discarded by a select (an element that
-// is not stepped -- a copy past n, the scale's padding lane -- keeps its
-// value), and only the stores depend on whether the chunk exists, so the
-// updates of a unit's two chunks interleave.
+// A group whose copies are all active takes the paired step with no
+// per-element select; the group holding the last copies steps each
+// element as k_xstep_idle does and keeps or discards it by a select (a copy
+// past n keeps its value).  The scale's padding lane is never stepped.
 template <int SEG, int NSEG, int NP>
 __device__ __forceinline__ void st_step(const float4* s, const StMeta& M, GView& x, GView& m, GView& v,
-                                        const AdamArgs& a, const Rho5& rh, float ic1, float ic2, const ZOut& zo)
+                                        const AdamArgs& a, const Rho5& rh, const StPair& SP, float ic1,
+                                        float ic2, const ZOut& zo)
 {
     if constexpr (SEG < NSEG) {
         const int64_t u = st_chunk<SEG, NP>(M, x);
+        if (u < 0) return;
         const int tid = threadIdx.x;
         const float4 X = s[tid], Mo = s[kStThreads + tid], V = s[2 * kStThreads + tid];
-        const float4 A = s[3 * kStThreads + tid];
-        const float x0[4] = {X.x, X.y, X.z, X.w}, m0[4] = {Mo.x, Mo.y, Mo.z, Mo.w}, v0[4] = {V.x, V.y, V.z, V.w};
-        const float as[4] = {A.x, A.y, A.z, A.w};    // read only for shared copies (loaded then)
+        const float4 A = s[3 * kStThreads + tid];   // read only for shared copies (loaded then)
         float xs[4], ms[4], vs[4];
+        // plane of this thread's chunk, and whether it is an SH DC plane
+        const int j = 4 * (SEG - 3) + (tid >> 5);
+        const bool dc = SEG == 3 && j < 3;
+        if (M.bits & kStFull) {
+            bool sh[4];
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            // step, penalty and learning rate of element i (constants of SEG and i)
-            bool step;
-            float rho, lr;
+            for (int i = 0; i < 4; i++) sh[i] = SEG < 3 ? (M.bits & 2u) != 0 : ((M.bits >> (8 + i)) & 1u) != 0;
+            f32x2 x01 = f2_pack(X.x, X.y), m01 = f2_pack(Mo.x, Mo.y), v01 = f2_pack(V.x, V.y);
+            f32x2 x23 = f2_pack(X.z, X.w), m23 = f2_pack(Mo.z, Mo.w), v23 = f2_pack(V.z, V.w);
+            const f32x2 a01 = f2_pack(A.x, A.y), a23 = f2_pack(A.z, A.w);
+            f32x2 rho01, rho23, nlr01, nlr23;
             if (SEG == 0) {
-                step = (M.bits & 1u) != 0;
-                rho = rh.r[i < 3 ? 0 : 4];
-                lr = i < 3 ? a.lr[0] : a.lr[5];
+                rho01 = SP.rho_p; rho23 = SP.rho_po; nlr01 = SP.nlr_p; nlr23 = SP.nlr_po;
             } else if (SEG == 1) {
-                step = (M.bits & 1u) != 0;
-                rho = rh.r[1];
-                lr = a.lr[1];
+                rho01 = rho23 = SP.rho_q; nlr01 = nlr23 = SP.nlr_q;
             } else if (SEG == 2) {
-                step = i < 3 && (M.bits & 1u) != 0;
-                rho = rh.r[2];
-                lr = a.lr[2];
+                rho01 = rho23 = SP.rho_s; nlr01 = nlr23 = SP.nlr_s;
             } else {
-                step = ((M.bits >> (4 + i)) & 1u) != 0;
-                rho = rh.r[3];
-                lr = 4 * (SEG - 3) + (tid >> 5) < 3 ? a.lr[3] : a.lr[4];
+                rho01 = rho23 = SP.rho_f;
+                nlr01 = nlr23 = dc ? SP.nlr_dc : SP.nlr_rest;
             }
-            const bool sh = SEG < 3 ? (M.bits & 2u) != 0 : ((M.bits >> (8 + i)) & 1u) != 0;
-            const float g = sh ? penalty_add(0.f, rho, x0[i], as[i]) : 0.f;
-            float xi = x0[i], mi = m0[i], vi = v0[i];
-            adam_scalar(xi, g, mi, vi, lr, a.b1, a.b2, a.eps, ic1, ic2);
-            xs[i] = step ? xi : x0[i];
-            ms[i] = step ? mi : m0[i];
-            vs[i] = step ? vi : v0[i];
-        }
-        if (u >= 0) {
-            st_row<SEG>(x)[u] = make_float4(xs[0], xs[1], xs[2], xs[3]);
-            st_row<SEG>(m)[u] = make_float4(ms[0], ms[1], ms[2], ms[3]);
-            st_row<SEG>(v)[u] = make_float4(vs[0], vs[1], vs[2], vs[3]);
-            if (SEG < 3) {
-                if (M.zf >= 0) st_row<SEG>(zo.z)[M.zf] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+            st_pair_step(x01, m01, v01, a01, sh[0], sh[1], rho01, nlr01, SP.P);
+            f2_unpack(x01, xs[0], xs[1]); f2_unpack(m01, ms[0], ms[1]); f2_unpack(v01, vs[0], vs[1]);
+            if (SEG == 2) {                              // the scale: z stepped alone, w (padding) kept
+                xs[2] = X.z; ms[2] = Mo.z; vs[2] = V.z;
+                const float g = sh[2] ? penalty_add(0.f, rh.r[2], X.z, A.z) : 0.f;
+                adam_scalar(xs[2], g, ms[2], vs[2], a.lr[2], a.b1, a.b2, a.eps, ic1, ic2);
+                xs[3] = X.w; ms[3] = Mo.w; vs[3] = V.w;
             } else {
-                const int j = 4 * (SEG - 3) + (tid >> 5);
+                st_pair_step(x23, m23, v23, a23, sh[2], sh[3], rho23, nlr23, SP.P);
+                f2_unpack(x23, xs[2], xs[3]); f2_unpack(m23, ms[2], ms[3]); f2_unpack(v23, vs[2], vs[3]);
+            }
+        } else {
+            const float x0[4] = {X.x, X.y, X.z, X.w}, m0[4] = {Mo.x, Mo.y, Mo.z, Mo.w};
+            const float v0[4] = {V.x, V.y, V.z, V.w}, as[4] = {A.x, A.y, A.z, A.w};
 #pragma unroll
-                for (int i = 0; i < 4; i++)
-                    if (M.zq[i] >= 0) zo.z.sh[(int64_t)j * zo.z.ld + M.zq[i]] = xs[i];
+            for (int i = 0; i < 4; i++) {
+                // step, penalty and learning rate of element i (constants of SEG and i)
+                bool step;
+                float rho, lr;
+                if (SEG == 0) {
+                    step = (M.bits & 1u) != 0;
+                    rho = rh.r[i < 3 ? 0 : 4];
+                    lr = i < 3 ? a.lr[0] : a.lr[5];
+                } else if (SEG == 1) {
+                    step = (M.bits & 1u) != 0;
+                    rho = rh.r[1];
+                    lr = a.lr[1];
+                } else if (SEG == 2) {
+                    step = i < 3 && (M.bits & 1u) != 0;
+                    rho = rh.r[2];
+                    lr = a.lr[2];
+                } else {
+                    step = ((M.bits >> (4 + i)) & 1u) != 0;
+                    rho = rh.r[3];
+                    lr = dc ? a.lr[3] : a.lr[4];
+                }
+                const bool sh = SEG < 3 ? (M.bits & 2u) != 0 : ((M.bits >> (8 + i)) & 1u) != 0;
+                const float g = sh ? penalty_add(0.f, rho, x0[i], as[i]) : 0.f;
+                float xi = x0[i], mi = m0[i], vi = v0[i];
+                adam_scalar(xi, g, mi, vi, lr, a.b1, a.b2, a.eps, ic1, ic2);
+                xs[i] = step ? xi : x0[i];
+                ms[i] = step ? mi : m0[i];
+                vs[i] = step ? vi : v0[i];
             }
+        }
+        st_row<SEG>(x)[u] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+        st_row<SEG>(m)[u] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+        st_row<SEG>(v)[u] = make_float4(vs[0], vs[1], vs[2], vs[3]);
+        if (SEG < 3) {
+            if (M.zf >= 0) st_row<SEG>(zo.z)[M.zf] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+        } else {
+            float* zj = zo.z.sh + (int64_t)j * zo.z.ld;
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                if (M.zq[i] >= 0) zj[M.zq[i]] = xs[i];
         }
     }
 }
@@ -1120,7 +1197,7 @@ __device__ __forceinline__ void st_issue_unit(float4* s, const StMeta& M, const 
 template <int U, int NU, int NSEG, int NS, int NP>
 __device__ __forceinline__ void st_unit(float4* ring, int base, const StMeta& cm, StMeta& nm, const StRaw& nr,
                                         GView& x, GView& m, GView& v, const GView& an, const AdamArgs& a,
-                                        const Rho5& rh, float ic1, float ic2, const ZOut& zo)
+                                        const Rho5& rh, const StPair& sp, float ic1, float ic2, const ZOut& zo)
 {
     constexpr int P = U + NS - 1;
     if constexpr (P < NU) {
@@ -1131,10 +1208,10 @@ __device__ __forceinline__ void st_unit(float4* ring, int base, const StMeta& cm
     }
     st_wait<NS - 1>();
     float4* s = st_slot<NS>(ring, base, U);
-    st_step<2 * U, NSEG, NP>(s, cm, x, m, v, a, rh, ic1, ic2, zo);
-    st_step<2 * U + 1, NSEG, NP>(s + 4 * kStThreads, cm, x, m, v, a, rh, ic1, ic2, zo);
+    st_step<2 * U, NSEG, NP>(s, cm, x, m, v, a, rh, sp, ic1, ic2, zo);
+    st_step<2 * U + 1, NSEG, NP>(s + 4 * kStThreads, cm, x, m, v, a, rh, sp, ic1, ic2, zo);
     if constexpr (U + 1 < NU)
-        st_unit<U + 1, NU, NSEG, NS, NP>(ring, base, cm, nm, nr, x, m, v, an, a, rh, ic1, ic2, zo);
+        st_unit<U + 1, NU, NSEG, NS, NP>(ring, base, cm, nm, nr, x, m, v, an, a, rh, sp, ic1, ic2, zo);
 }
 
 template <int U, int NS, int NSEG, int NP>
@@ -1169,6 +1246,7 @@ __global__ void __launch_bounds__(kStThreads) k_xstep_stream(GView x, GView m, G
     Rho5 rh;
 #pragma unroll
     for (int k = 0; k < 5; k++) rh.r[k] = rho_of(a, k);
+    const StPair sp = st_pair_args(a, rh, ic1, ic2);
     const uint32_t n_list = ctr[0], G = gridDim.x;
     uint32_t li = blockIdx.x;
     auto entry = [&](uint32_t i) { return i < n_list ? (int64_t)list[i] * kXsThreads : (int64_t)-1; };
@@ -1183,7 +1261,7 @@ __global__ void __launch_bounds__(kStThreads) k_xstep_stream(GView x, GView m, G
     int base = 0;
 #pragma unroll 1
     while (cm.c0 >= 0) {
-        st_unit<0, NU, NSEG, NS, NP>(s_ring, base, cm, nm, nr, x, m, v, an, a, rh, ic1, ic2, zo);
+        st_unit<0, NU, NSEG, NS, NP>(s_ring, base, cm, nm, nr, x, m, v, an, a, rh, sp, ic1, ic2, zo);
         base = (base + NU) % NS;
         cm = nm;
         st_load(nr, c0_ahead, x, shared, zo);
