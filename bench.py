@@ -57,9 +57,9 @@ def parse():
     ap.add_argument("--idle-ctas", type=int, default=0,
                     help="CTAs per SM of the x-step part that runs beside compositing (0: one per SM streamed, "
                          "one per group of copies as a grid)")
-    ap.add_argument("--idle-mode", default="stream", choices=["stream", "stream_early", "grid"],
+    ap.add_argument("--idle-mode", default=None, choices=["stream", "stream_early", "grid"],
                     help="that x-step part: streamed by persistent CTAs beside the compositing adjoint, or a grid "
-                         "launched after the projection")
+                         "launched after the projection (default: the autotuner's choice, else stream)")
     ap.add_argument("--no-overlap", action="store_true", help="run that x-step part inline on the main stream")
     ap.add_argument("--variant", default=None,
                     help="compositing variant W,S[,Wb,Sb] (warps per tile, staged per thread; backward)")
@@ -385,12 +385,13 @@ def run_ours(args, dist, rank, world):
     tr = T.DogsTrainer(wl.split, z0, wl.views, targets, rho=(W["rho"],) * 5, tile=tile, loss=args.loss,
                        overlap=not args.no_overlap, intv=W["intv"] or 100)
     tr.idle_ctas_per_sm = args.idle_ctas
-    tr.idle_mode = args.idle_mode
+    if args.idle_mode:
+        tr.idle_mode = args.idle_mode
     m_max = tr.calibrate_capacity()
     tuned = None
     if not args.no_autotune and not args.profile and not args.variant:
         from paper_2405_13943_b300 import autotune
-        tuned = autotune.tune(tr, use_cache=False)
+        tuned = autotune.tune(tr, use_cache=False, idle_modes=(args.idle_mode,) if args.idle_mode else ("stream", "grid"))
         tile = tr.tile
         m_max = tr.calibrate_capacity()
     torch.cuda.synchronize()
@@ -601,7 +602,8 @@ def run_ours(args, dist, rank, world):
                                                   "staged_per_thread": tr.vb.plan.raster_stage_bwd or tr.vb.plan.raster_stage}},
                        "autotune": (None if tuned is None else
                                     {"best_ms": tuned["ms"], "tiles": len(tuned["candidates"]),
-                                     "variants_per_tile": len(tuned["candidates"][0]["variants"])}),
+                                     "variants_per_tile": len(tuned["candidates"][0]["variants"]),
+                                     "idle_mode_ms": tuned.get("idle_modes")}),
                        "loss": "0.8 L1 + 0.2 D-SSIM" if args.loss == "dssim" else "L1",
                        "consensus_every_timed_step": W["intv"] == 1,
                        "consensus_steps_timed": (args.steps if W["intv"] == 1 else 0 if W["intv"] is None else

@@ -7,7 +7,11 @@ For every tile shape the forward and the backward variants are chosen
 separately from their own kernel times (CUDA events around the two calls,
 on the workload itself); the tile shapes are then compared by full eager
 iterations (projection, binning, compositing, loss, backward, x-step) with
-their chosen variants.  The fastest is applied and cached per workload
+their chosen variants.  Last, where the x-step runs in two parts, the way
+its part for the groups without a kept record runs (streamed beside the
+compositing adjoint, or a grid after the projection) is chosen by replays
+of captured iterations: the streamed form pays where the adjoint is long
+enough to hide it.  The fastest is applied and cached per workload
 signature."""
 from __future__ import annotations
 
@@ -73,15 +77,36 @@ def _kernel_times(tr, steps: int) -> Tuple[float, float]:
     return fw, bw
 
 
+def _time_graph_steps(tr, steps: int) -> float:
+    """Mean time (ms) of replayed iterations without a consensus, captured
+    afresh (and dropped afterwards)."""
+    tr.graphs.clear()
+    tr.step(consensus=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        tr.step(consensus=False)
+    e1.record()
+    torch.cuda.synchronize()
+    tr.graphs.clear()
+    if tr.overflowed():
+        return float("inf")
+    return e0.elapsed_time(e1) / steps
+
+
 def _apply(tr, best: Dict) -> None:
     tr.set_tile(tuple(best["tile"]))
     v = list(best["fwd"]) + list(best["bwd"])
     tr.set_variant(*v)
     D.set_raster_variant(*v)
+    if best.get("idle_mode") is not None:
+        tr.idle_mode = best["idle_mode"]
+        tr.graphs.clear()
 
 
 def tune(tr, tiles: Sequence = TILES, warps: Sequence[int] = WARPS, stages: Sequence[int] = STAGES,
-         steps: int = 3, use_cache: bool = True) -> Dict:
+         steps: int = 3, use_cache: bool = True, idle_modes: Sequence[str] = ("stream", "grid")) -> Dict:
     key = signature(tr)
     cache = {}
     if use_cache and os.path.exists(CACHE):
@@ -111,9 +136,17 @@ def tune(tr, tiles: Sequence = TILES, warps: Sequence[int] = WARPS, stages: Sequ
                                      for (w, s) in per}})
     best = min(results, key=lambda r: r["ms"])
     _apply(tr, best)
-    out = dict(best, candidates=results, cached=False)
+    idle = None
+    if tr._split_xstep() and len(idle_modes) > 1:
+        idle = {}
+        for mode in idle_modes:
+            tr.idle_mode = mode
+            idle[mode] = round(_time_graph_steps(tr, 4 * steps), 4)
+        best = dict(best, idle_mode=min(idle, key=idle.get))
+        _apply(tr, best)
+    out = dict(best, candidates=results, idle_modes=idle, cached=False)
     if use_cache:
-        cache[key] = {k: best[k] for k in ("tile", "fwd", "bwd", "ms")}
+        cache[key] = {k: best[k] for k in ("tile", "fwd", "bwd", "ms", "idle_mode") if k in best}
         with open(CACHE, "w") as f:
             json.dump(cache, f, indent=1)
     return out

@@ -46,14 +46,14 @@ __device__ __forceinline__ int order_bucket(uint32_t n)
 }
 
 struct BinWs {
-    uint32_t* counts;     // n_tiles + 3 (three list counters at the end), zeroed
+    uint32_t* counts;     // n_tiles + 3 (three list counters at the end) + order_ctr, zeroed together
     uint32_t* cursor;     // n_tiles
     uint32_t* partials;   // n_chunks + 1
     uint32_t* big_list;   // n_tiles
     uint32_t* huge_list;  // n_tiles
     uint32_t* mid_list;   // n_tiles
     uint64_t* pairs;      // capacity
-    uint32_t* order_ctr;  // 2 kOrderBuckets: tiles per bucket, then the buckets' fill cursors
+    uint32_t* order_ctr;  // counts + n_tiles + 3: 2 kOrderBuckets -- tiles per bucket, then the buckets' fill cursors
 };
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -64,14 +64,14 @@ static size_t bin_ws_layout(int64_t n_tiles, int64_t capacity, BinWs* w, char* b
     size_t off = 0;
     auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align256(bytes); return p; };
     BinWs t;
-    t.counts = (uint32_t*)take(4 * (size_t)(n_tiles + 3));
+    t.counts = (uint32_t*)take(4 * (size_t)(n_tiles + 3 + 2 * kOrderBuckets));
+    t.order_ctr = t.counts ? t.counts + n_tiles + 3 : nullptr;
     t.cursor = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.partials = (uint32_t*)take(4 * (size_t)(n_chunks + 1));
     t.big_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.huge_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.mid_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.pairs = (uint64_t*)take(8 * (size_t)(capacity > 0 ? capacity : 1));
-    t.order_ctr = (uint32_t*)take(4 * (size_t)(2 * kOrderBuckets));
     if (w) *w = t;
     return off;
 }
@@ -282,12 +282,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t* __restrict_
     }
 }
 
+// ... and the histogram of the ranges' sizes over the work order's buckets
+// (from the values written, so that the order's scatter sees the same)
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ counts, int64_t n_tiles,
                                                             const uint32_t* __restrict__ partials, int64_t n_chunks,
                                                             const uint32_t* __restrict__ dev_count, int64_t capacity,
-                                                            uint32_t* __restrict__ ranges, uint32_t* __restrict__ cursor)
+                                                            uint32_t* __restrict__ ranges, uint32_t* __restrict__ cursor,
+                                                            uint32_t* __restrict__ order_hist)
 {
     __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_h[kOrderBuckets];
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_h[b] = 0;
+    __syncthreads();
     bool overflow = (int64_t)(*dev_count) > capacity;
     int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
     uint32_t v[kScanPer], s = 0;
@@ -303,9 +309,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
             ranges[2 * t] = b;
             ranges[2 * t + 1] = e;
             cursor[t] = b;
+            atomicAdd(&s_h[order_bucket(e - b)], 1u);
         }
         run += v[i];
     }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
+        if (s_h[b]) atomicAdd(&order_hist[b], s_h[b]);
 }
 
 // ---- pass 2: scatter (depth bits, record) into tile segments ------------------------
@@ -497,19 +507,6 @@ __global__ void __launch_bounds__(1024) k_sort_huge(const uint32_t* __restrict__
     }
 }
 
-__global__ void __launch_bounds__(256) k_order_hist(const uint32_t* __restrict__ ranges, int64_t n_tiles,
-                                                    uint32_t* __restrict__ ctr)
-{
-    __shared__ uint32_t s_h[kOrderBuckets];
-    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_h[b] = 0;
-    __syncthreads();
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&s_h[order_bucket(ranges[2 * t + 1] - ranges[2 * t])], 1u);
-    __syncthreads();
-    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
-        if (s_h[b]) atomicAdd(&ctr[b], s_h[b]);
-}
-
 __global__ void __launch_bounds__(256) k_order_scatter(uint32_t* __restrict__ ranges, int64_t n_tiles,
                                                        uint32_t* __restrict__ ctr)
 {
@@ -554,7 +551,8 @@ int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams,
     BinWs w;
     bin_ws_layout(plan.n_tiles, capacity, &w, (char*)ws);
     int64_t n_chunks = (plan.n_tiles + kScanChunk - 1) / kScanChunk;
-    if (cudaMemsetAsync(w.counts, 0, 4 * (size_t)(plan.n_tiles + 3), st) != cudaSuccess) return DG_ERR_CUDA;
+    if (cudaMemsetAsync(w.counts, 0, 4 * (size_t)(plan.n_tiles + 3 + 2 * kOrderBuckets), st) != cudaSuccess)
+        return DG_ERR_CUDA;
     if (plan.n_rec > 0) {
         k_expand<false><<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(
             rect, rec, cams, plan.n_views, plan.n_rec, plan.tile_w, plan.tile_h, w.counts, nullptr, 0, nullptr,
@@ -564,7 +562,7 @@ int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams,
     k_scan_reduce<<<(unsigned)n_chunks, kScanThreads, 0, st>>>(w.counts, plan.n_tiles, w.partials);
     k_scan_top<<<1, kScanThreads, 0, st>>>(w.partials, n_chunks, capacity, dev_count, dev_status);
     k_scan_down<<<(unsigned)n_chunks, kScanThreads, 0, st>>>(w.counts, plan.n_tiles, w.partials, n_chunks, dev_count,
-                                                             capacity, ranges, w.cursor);
+                                                             capacity, ranges, w.cursor, w.order_ctr);
     note_launch(3);
     if (plan.n_rec > 0) {
         k_expand<true><<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(
@@ -579,12 +577,10 @@ int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams,
     k_sort_big<<<148, 1024, kBigCap * sizeof(uint64_t), st>>>(ranges, w.pairs, vals, keys, counters, w.big_list);
     k_sort_huge<<<148, 1024, 0, st>>>(ranges, w.pairs, vals, keys, counters, w.huge_list);
     note_launch(4);
-    // the compositing's work order, after the ranges
-    if (cudaMemsetAsync(w.order_ctr, 0, 4 * (size_t)(2 * kOrderBuckets), st) != cudaSuccess) return DG_ERR_CUDA;
+    // the compositing's work order, after the ranges (bucket sizes from k_scan_down)
     const unsigned og = (unsigned)std::min<int64_t>((plan.n_tiles + 255) / 256, 148 * 2);
-    k_order_hist<<<og, 256, 0, st>>>(ranges, plan.n_tiles, w.order_ctr);
     k_order_scatter<<<og, 256, 0, st>>>(ranges, plan.n_tiles, w.order_ctr);
-    note_launch(2);
+    note_launch();
     DG_CHECK_LAUNCH();
     return DG_OK;
 }
