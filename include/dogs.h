@@ -241,8 +241,12 @@ int dg_rasterize_bwd(const float* rec, const uint32_t* rect, const uint32_t* val
 
 /* The compositing adjoint alone (the first half of dg_rasterize_bwd): drec
  * (12 floats per record) zeroed, then dL/d(mean2d, conic, opacity, colour)
- * accumulated.  Feeds dg_xstep_from_records. */
-int dg_rasterize_bwd_records(const float* rec, const uint32_t* vals, const uint32_t* ranges,
+ * accumulated.  Feeds dg_xstep_from_records.  rect: the projection's
+ * rectangles, or NULL.  Given, only the records with a non-empty rectangle
+ * (the records the adjoint adds to and the projection adjoint reads) are
+ * zeroed and the other entries of drec are left as they are; NULL zeroes
+ * every record. */
+int dg_rasterize_bwd_records(const float* rec, const uint32_t* rect, const uint32_t* vals, const uint32_t* ranges,
                              const dg_camera* dev_cams, const dg_plan* plan, const float* bg,
                              const float* T_final, const uint32_t* last, const float* dL_dimage,
                              float* drec, void* stream);

@@ -100,7 +100,7 @@ _SIGS = {
     "dg_admm_scale_duals": (C.c_int, [C.POINTER(DgGaussians), _vp, C.POINTER(C.c_float), _vp]),
     "dg_rasterize_count": (C.c_int, [_vp, _vp, _vp, _vp, C.POINTER(DgPlan), C.POINTER(C.c_float), _vp, _vp, _vp,
                                      _vp, _vp]),
-    "dg_rasterize_bwd_records": (C.c_int, [_vp, _vp, _vp, _vp, C.POINTER(DgPlan), C.POINTER(C.c_float), _vp, _vp,
+    "dg_rasterize_bwd_records": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(DgPlan), C.POINTER(C.c_float), _vp, _vp,
                                             _vp, _vp, _vp]),
     "dg_xstep_from_records": (C.c_int, [_vp, _vp, C.POINTER(DgPlan), _vp, C.POINTER(DgGaussians),
                                          C.POINTER(DgGaussians), C.POINTER(DgGaussians), C.POINTER(DgGaussians), _vp,

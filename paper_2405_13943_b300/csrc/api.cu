@@ -39,6 +39,7 @@ int launch_raster_count(const float4*, const uint32_t*, const uint32_t*, const d
                         const float*, float*, float*, uint32_t*, unsigned long long*, cudaStream_t);
 int launch_raster_bwd(const float4*, const uint32_t*, const uint32_t*, const dg_camera*, const dg_plan&,
                       const float*, const float*, const uint32_t*, const float*, float*, cudaStream_t);
+int launch_zero_kept(const uint2* rect, int64_t n_rec, float* drec, cudaStream_t st);
 size_t loss_ws_bytes(const dg_plan&);
 int launch_loss(const float*, const float*, const dg_camera*, const dg_plan&, float, float, double*, float*, void*,
                 cudaStream_t);
@@ -325,16 +326,21 @@ int dg_adam_admm_step(dg_gaussians* x, const dg_gaussians* g, dg_gaussians* m, d
                             dev_step, (cudaStream_t)stream);
 }
 
-int dg_rasterize_bwd_records(const float* rec, const uint32_t* vals, const uint32_t* ranges,
+int dg_rasterize_bwd_records(const float* rec, const uint32_t* rect, const uint32_t* vals, const uint32_t* ranges,
                              const dg_camera* dev_cams, const dg_plan* plan, const float* bg, const float* T_final,
                              const uint32_t* last, const float* dL_dimage, float* drec, void* stream)
 {
     if (!valid_plan(plan) || !bg) return DG_ERR_INVALID;
     if (plan->n_rec == 0) return DG_OK;
     if (!rec || !vals || !ranges || !dev_cams || !T_final || !last || !dL_dimage || !drec) return DG_ERR_INVALID;
-    if (!aligned16(rec) || !aligned8(dev_cams) || !aligned16(drec)) return DG_ERR_INVALID;
+    if (!aligned16(rec) || !aligned8(dev_cams) || !aligned16(drec) || !aligned8(rect)) return DG_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemsetAsync(drec, 0, (size_t)plan->n_rec * 12 * sizeof(float), st) != cudaSuccess) return DG_ERR_CUDA;
+    if (rect) {
+        int rc = launch_zero_kept((const uint2*)rect, plan->n_rec, drec, st);
+        if (rc != DG_OK) return rc;
+    } else if (cudaMemsetAsync(drec, 0, (size_t)plan->n_rec * 12 * sizeof(float), st) != cudaSuccess) {
+        return DG_ERR_CUDA;
+    }
     return launch_raster_bwd((const float4*)rec, vals, ranges, dev_cams, *plan, bg, T_final, last, dL_dimage, drec,
                              st);
 }

@@ -366,36 +366,61 @@ __device__ __forceinline__ void write_segment(const uint64_t* s, uint32_t n, uin
 // Segments of up to 256 instances: one warp per tile, a bitonic network on
 // 64-bit (depth bits, record) keys held in registers -- element e = i * 32 +
 // lane in register i of the lane -- with lane shuffles for distances below 32
-// and register exchanges above; positions >= n hold +infinity.  No barriers.
+// and register exchanges above.  The network is the "all ascending" form
+// (each merge compares an element with its mirror in its k-block first, then
+// e with e ^ j for j = k/4 .. 1, the smaller always to the lower position),
+// so positions >= n hold +infinity at every stage: a compare-exchange whose
+// upper partner is all padding changes nothing, and registers with i * 32 >=
+// n are skipped.  A compare-exchange keeps one value by a single 64-bit
+// comparison (equal values, only padding, may go either way).  No barriers.
 template <int NR>
-__device__ __forceinline__ void warp_bitonic(uint64_t* v, int lane)
+__device__ __forceinline__ void warp_bitonic(uint64_t* v, int lane, uint32_t n)
 {
     constexpr int N = 32 * NR;
 #pragma unroll
     for (int k = 2; k <= N; k <<= 1) {
+        if (k <= 32) {                      // mirror within the lanes of one register
+            const bool lo = (lane & (k >> 1)) == 0;
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = 0; i < NR; i++) {
+                if ((uint32_t)(i * 32) >= n) continue;
+                const uint64_t w = __shfl_xor_sync(0xffffffffu, v[i], k - 1);
+                v[i] = ((w < v[i]) == lo) ? w : v[i];
+            }
+        } else {                            // mirror across registers: lane L of i meets lane 31 - L of ip
+            const int K = k >> 5;
+#pragma unroll
+            for (int i = 0; i < NR; i++) {
+                if ((i % K) >= K / 2) continue;
+                const int ip = (i / K) * K + (K - 1 - (i % K));
+                if ((uint32_t)(ip * 32) >= n) continue;
+                const uint64_t a = v[i], b = v[ip];
+                const uint64_t wa = __shfl_xor_sync(0xffffffffu, b, 31);
+                const uint64_t wb = __shfl_xor_sync(0xffffffffu, a, 31);
+                v[i] = wa < a ? wa : a;
+                v[ip] = wb < b ? b : wb;
+            }
+        }
+#pragma unroll
+        for (int j = k >> 2; j > 0; j >>= 1) {
             if (j >= 32) {
                 const int ri = j >> 5;
 #pragma unroll
                 for (int i = 0; i < NR; i++) {
                     if (i & ri) continue;
-                    const int e = i * 32 + lane;
-                    const bool asc = (e & k) == 0;
+                    if ((uint32_t)((i | ri) * 32) >= n) continue;
                     const uint64_t a = v[i], b = v[i | ri];
-                    const bool sw = asc ? (a > b) : (a < b);
+                    const bool sw = b < a;
                     v[i] = sw ? b : a;
                     v[i | ri] = sw ? a : b;
                 }
             } else {
+                const bool lo = (lane & j) == 0;
 #pragma unroll
                 for (int i = 0; i < NR; i++) {
-                    const int e = i * 32 + lane;
-                    const bool asc = (e & k) == 0;
-                    const bool lower = (lane & j) == 0;
+                    if ((uint32_t)(i * 32) >= n) continue;
                     const uint64_t w = __shfl_xor_sync(0xffffffffu, v[i], j);
-                    const uint64_t mn = v[i] < w ? v[i] : w, mx = v[i] < w ? w : v[i];
-                    v[i] = (lower == asc) ? mn : mx;
+                    v[i] = ((w < v[i]) == lo) ? w : v[i];
                 }
             }
         }
@@ -413,7 +438,7 @@ __device__ __forceinline__ void warp_sort_segment(const uint64_t* __restrict__ p
         const uint32_t e = (uint32_t)(i * 32 + lane);
         v[i] = e < n ? pairs[start + e] : ~0ull;
     }
-    warp_bitonic<NR>(v, lane);
+    warp_bitonic<NR>(v, lane, n);
 #pragma unroll
     for (int i = 0; i < NR; i++) {
         const uint32_t e = (uint32_t)(i * 32 + lane);

@@ -621,6 +621,42 @@ int launch_raster_bwd(const float4* rec, const uint32_t* vals, const uint32_t* r
     return DG_OK;
 }
 
+// drec's 12 floats zeroed for the records with a non-empty rectangle (the
+// only ones the compositing adjoint adds to and the projection adjoint
+// reads); four records per thread, so four rectangle loads are in flight
+constexpr int kZeroPer = 4;
+
+__global__ void __launch_bounds__(256) k_zero_kept(const uint2* __restrict__ rect, int64_t n_rec,
+                                                   float4* __restrict__ drec)
+{
+    const int64_t base = (int64_t)blockIdx.x * (256 * kZeroPer) + threadIdx.x;
+    uint2 rr[kZeroPer];
+#pragma unroll
+    for (int j = 0; j < kZeroPer; j++) {
+        const int64_t r = base + 256 * j;
+        rr[j] = r < n_rec ? rect[r] : make_uint2(0, 0);
+    }
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kZeroPer; j++) {
+        if ((rr[j].x & 0xFFFFu) == (rr[j].y & 0xFFFFu)) continue;
+        const int64_t r = base + 256 * j;
+        drec[3 * r] = z;
+        drec[3 * r + 1] = z;
+        drec[3 * r + 2] = z;
+    }
+}
+
+int launch_zero_kept(const uint2* rect, int64_t n_rec, float* drec, cudaStream_t st)
+{
+    if (n_rec == 0) return DG_OK;
+    const int64_t per = 256 * kZeroPer;
+    k_zero_kept<<<(unsigned)((n_rec + per - 1) / per), 256, 0, st>>>(rect, n_rec, (float4*)drec);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
 // ---- deterministic mode: (record, tile) slots ---------------------------------------
 // slot_off[r] = the sum of the rectangle areas (in tiles) of the records
 // before r, by a three-pass scan (chunks of kSlotChunk records per CTA).

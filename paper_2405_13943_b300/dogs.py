@@ -271,7 +271,8 @@ def dg_rasterize_bwd(vb: ViewBatch, x: GaussianBuffer, grads: GaussianBuffer, dL
 
 def dg_rasterize_bwd_records(vb: ViewBatch, bg=(0.0, 0.0, 0.0), dL_dimage=None, stream=None) -> None:
     g = vb.dL_dimage if dL_dimage is None else dL_dimage
-    L.check(L.lib().dg_rasterize_bwd_records(L.ptr(vb.rec), L.ptr(vb.vals), L.ptr(vb.ranges), L.ptr(vb.dev_cams),
+    L.check(L.lib().dg_rasterize_bwd_records(L.ptr(vb.rec), L.ptr(vb.rect), L.ptr(vb.vals), L.ptr(vb.ranges),
+                                             L.ptr(vb.dev_cams),
                                              C.byref(vb.plan), L.floats(bg), L.ptr(vb.T_final), L.ptr(vb.last),
                                              L.ptr(g), L.ptr(vb.drec), L.stream_handle(stream)),
             "dg_rasterize_bwd_records")
