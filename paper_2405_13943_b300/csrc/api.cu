@@ -13,9 +13,9 @@ void note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_re
 int launch_project(const dg_gaussians*, const dg_camera*, const dg_plan&, float4*, uint2*, cudaStream_t);
 int launch_project_bwd(const dg_gaussians*, const dg_camera*, const dg_plan&, const uint2*, const float4*,
                        dg_gaussians*, cudaStream_t);
-size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity);
+size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity, int64_t list_records);
 int launch_bin_sort(const float4*, const uint2*, const dg_camera*, const dg_plan&, int64_t, uint64_t*, uint32_t*,
-                    uint32_t*, uint32_t*, void*, uint32_t*, cudaStream_t);
+                    uint32_t*, uint32_t*, void*, bool, uint32_t*, cudaStream_t);
 int bin_sort_init();
 size_t raster_slots_ws_bytes(int64_t n_rec);
 size_t densify_layout_ws_bytes(int64_t n_g, int64_t n_c);
@@ -221,7 +221,7 @@ int dg_project(const dg_gaussians* x, const dg_camera* dev_cams, const dg_plan* 
 size_t dg_bin_sort_workspace_size(const dg_plan* plan, int64_t capacity)
 {
     if (!valid_plan(plan) || capacity < 0) return 0;
-    return bin_sort_ws_bytes(plan->n_tiles, capacity);
+    return bin_sort_ws_bytes(plan->n_tiles, capacity, plan->n_rec);
 }
 
 int dg_bin_sort(const float* rec, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
@@ -231,11 +231,11 @@ int dg_bin_sort(const float* rec, const uint32_t* rect, const dg_camera* dev_cam
     int rc = bin_sort_args(rec, rect, dev_cams, plan, capacity, keys, vals, ranges, dev_count, dev_status);
     if (rc != DG_OK || plan->n_tiles == 0) return rc;
     if (!ws || ((uintptr_t)ws & 255u)) return DG_ERR_INVALID;
-    if (ws_bytes < bin_sort_ws_bytes(plan->n_tiles, capacity)) return DG_ERR_WORKSPACE;
+    if (ws_bytes < bin_sort_ws_bytes(plan->n_tiles, capacity, plan->n_rec)) return DG_ERR_WORKSPACE;
     rc = ensure_init();
     if (rc != DG_OK) return rc;
     return launch_bin_sort((const float4*)rec, (const uint2*)rect, dev_cams, *plan, capacity, keys, vals, ranges,
-                           dev_count, ws, dev_status, (cudaStream_t)stream);
+                           dev_count, ws, true, dev_status, (cudaStream_t)stream);
 }
 
 int dg_rasterize_fwd(const float* rec, const uint32_t* vals, const uint32_t* ranges, const dg_camera* dev_cams,
@@ -635,7 +635,7 @@ static size_t render_ws_layout(const dg_plan& p, int64_t capacity, char* base, R
     r.ranges = (uint32_t*)take((size_t)p.n_tiles * 12 + 8);   // ranges, then the work order
     r.T_final = (float*)take((size_t)p.n_pixels * 4 + 4);
     r.last = (uint32_t*)take((size_t)p.n_pixels * 4 + 4);
-    r.bin_bytes = bin_sort_ws_bytes(p.n_tiles, capacity);
+    r.bin_bytes = bin_sort_ws_bytes(p.n_tiles, capacity, p.n_rec);
     r.bin = take(r.bin_bytes);
     if (w) *w = r;
     return off;
@@ -666,7 +666,7 @@ int dg_render(const dg_gaussians* z, const dg_camera* dev_cams, const dg_plan* p
     rc = ensure_init();
     if (rc != DG_OK) return rc;
     rc = launch_bin_sort(w.rec, w.rect, dev_cams, *plan, capacity, nullptr, w.vals, w.ranges, dev_count, w.bin,
-                         dev_status, st);
+                         true, dev_status, st);
     if (rc != DG_OK) return rc;
     return launch_raster_fwd(w.rec, w.vals, w.ranges, dev_cams, *plan, bg, image, w.T_final, w.last, st);
 }

@@ -35,6 +35,8 @@ constexpr int kBigCap = 16384;                        // segment sorted by a 102
 // then start first instead of in image order, so no long tile is left to run
 // alone at the end of a compositing launch.
 constexpr int kOrderBuckets = 129;
+// counters after the per-tile counts: [0] big, [1] huge, [2] mid tile lists, [3] visible records
+constexpr int kCtrs = 4;
 
 // bucket 4 clz(n) + (3 - the two bits after n's leading one): a quarter
 // octave wide, ascending as n descends; 128 for an empty tile
@@ -46,37 +48,42 @@ __device__ __forceinline__ int order_bucket(uint32_t n)
 }
 
 struct BinWs {
-    uint32_t* counts;     // n_tiles + 3 (three list counters at the end) + order_ctr, zeroed together
+    uint32_t* counts;     // n_tiles + 4 (four counters at the end: three tile lists, the visible records) + order_ctr, zeroed together
     uint32_t* cursor;     // n_tiles
     uint32_t* partials;   // n_chunks + 1
     uint32_t* big_list;   // n_tiles
     uint32_t* huge_list;  // n_tiles
     uint32_t* mid_list;   // n_tiles
     uint64_t* pairs;      // capacity
-    uint32_t* order_ctr;  // counts + n_tiles + 3: 2 kOrderBuckets -- tiles per bucket, then the buckets' fill cursors
+    uint32_t* order_ctr;  // counts + n_tiles + 4: 2 kOrderBuckets -- tiles per bucket, then the buckets' fill cursors
+    uint32_t* vis_list;   // list_records (0: no list; the expansion then scans every record)
 };
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-static size_t bin_ws_layout(int64_t n_tiles, int64_t capacity, BinWs* w, char* base)
+static size_t bin_ws_layout(int64_t n_tiles, int64_t capacity, int64_t list_records, BinWs* w, char* base)
 {
     int64_t n_chunks = (n_tiles + kScanChunk - 1) / kScanChunk;
     size_t off = 0;
     auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align256(bytes); return p; };
     BinWs t;
-    t.counts = (uint32_t*)take(4 * (size_t)(n_tiles + 3 + 2 * kOrderBuckets));
-    t.order_ctr = t.counts ? t.counts + n_tiles + 3 : nullptr;
+    t.counts = (uint32_t*)take(4 * (size_t)(n_tiles + kCtrs + 2 * kOrderBuckets));
+    t.order_ctr = t.counts ? t.counts + n_tiles + kCtrs : nullptr;
     t.cursor = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.partials = (uint32_t*)take(4 * (size_t)(n_chunks + 1));
     t.big_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.huge_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.mid_list = (uint32_t*)take(4 * (size_t)(n_tiles + 1));
     t.pairs = (uint64_t*)take(8 * (size_t)(capacity > 0 ? capacity : 1));
+    t.vis_list = list_records > 0 ? (uint32_t*)take(4 * (size_t)list_records) : nullptr;
     if (w) *w = t;
     return off;
 }
 
-size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity) { return bin_ws_layout(n_tiles, capacity, nullptr, nullptr); }
+size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity, int64_t list_records)
+{
+    return bin_ws_layout(n_tiles, capacity, list_records, nullptr, nullptr);
+}
 
 // ---- tile culling --------------------------------------------------------------
 // A pixel at offset d from the mean is composited only if o exp(-q(d)/2) >=
@@ -133,20 +140,19 @@ __device__ __forceinline__ bool tile_reached(const CullRec& k, uint32_t tx, uint
 // Pass 1 (SCATTER = false) counts the kept pairs per tile; pass 2 writes them
 // into the tiles' ranges.  Both take the same decisions: the same inputs go
 // through the same instructions.
+// The expansion of one warp's 32 records (lane: record r when `own`); every
+// lane of the warp calls it together.
 template <bool SCATTER>
-__global__ void __launch_bounds__(256) k_expand(const uint2* __restrict__ rect, const float4* __restrict__ rec,
-                                                const dg_camera* __restrict__ cams, int n_views, int64_t n_rec,
-                                                int tw, int th, uint32_t* __restrict__ counts,
-                                                const uint32_t* __restrict__ dev_count, int64_t capacity,
-                                                const uint32_t* __restrict__ ranges, uint32_t* __restrict__ cursor,
-                                                uint64_t* __restrict__ pairs)
+__device__ __forceinline__ void expand_warp(bool own, int64_t r, const uint2* __restrict__ rect,
+                                            const float4* __restrict__ rec, const dg_camera* __restrict__ cams,
+                                            int n_views, int tw, int th, uint32_t* __restrict__ counts,
+                                            const uint32_t* __restrict__ ranges, uint32_t* __restrict__ cursor,
+                                            uint64_t* __restrict__ pairs)
 {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    if (SCATTER && (int64_t)(*dev_count) > capacity) return;   // uniform over the grid
     uint32_t x0 = 0, y0 = 0, w = 0, n = 0, toff = 0, TX = 0, dbits = 0;
     CullRec k = {0.f, 0.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f};
-    if (r < n_rec) {
+    if (own) {
         const uint2 rr = rect[r];
         x0 = rr.x & 0xFFFFu; y0 = rr.x >> 16;
         const uint32_t x1 = rr.y & 0xFFFFu, y1 = rr.y >> 16;
@@ -206,6 +212,73 @@ __global__ void __launch_bounds__(256) k_expand(const uint2* __restrict__ rect, 
             const uint32_t pos = atomicAdd(&cursor[t], 1u);
             if (pos < ranges[2 * t + 1]) pairs[pos] = ((uint64_t)od << 32) | (uint64_t)orec;   // never false
         }
+    }
+}
+
+// LIST = false: one thread per record of the batch (most of them empty in a
+// large scene).  LIST = true: a persistent grid over the list of records
+// with a non-empty rectangle that k_visible built, so every warp holds 32
+// records to expand instead of the few a run of 32 consecutive records has,
+// and the rectangle -> record load chain before the expansion is paid once
+// per 32 visible records.  The list's order is unspecified; the counts do
+// not depend on it, nor do the sorted segments (the pairs are sorted by
+// their full (depth, record) key).
+template <bool SCATTER, bool LIST>
+__global__ void __launch_bounds__(256) k_expand(const uint2* __restrict__ rect, const float4* __restrict__ rec,
+                                                const dg_camera* __restrict__ cams, int n_views, int64_t n_rec,
+                                                int tw, int th, uint32_t* __restrict__ counts,
+                                                const uint32_t* __restrict__ dev_count, int64_t capacity,
+                                                const uint32_t* __restrict__ ranges, uint32_t* __restrict__ cursor,
+                                                uint64_t* __restrict__ pairs, const uint32_t* __restrict__ list,
+                                                const uint32_t* __restrict__ n_list)
+{
+    if (SCATTER && (int64_t)(*dev_count) > capacity) return;   // uniform over the grid
+    if (LIST) {
+        const uint32_t cnt = *n_list;
+        for (uint32_t b = blockIdx.x * blockDim.x; b < cnt; b += gridDim.x * blockDim.x) {
+            const uint32_t i = b + threadIdx.x;
+            const bool own = i < cnt;
+            expand_warp<SCATTER>(own, own ? (int64_t)list[i] : 0, rect, rec, cams, n_views, tw, th, counts, ranges,
+                                 cursor, pairs);
+        }
+    } else {
+        const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        expand_warp<SCATTER>(r < n_rec, r, rect, rec, cams, n_views, tw, th, counts, ranges, cursor, pairs);
+    }
+}
+
+// The records with a non-empty rectangle, appended to list in no particular
+// order (one atomic per warp); four records per thread keep four rectangle
+// loads in flight.
+constexpr int kVisPer = 4;
+
+__global__ void __launch_bounds__(256) k_visible(const uint2* __restrict__ rect, int64_t n_rec,
+                                                 uint32_t* __restrict__ list, uint32_t* __restrict__ n_list)
+{
+    const int64_t base = (int64_t)blockIdx.x * (256 * kVisPer) + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    uint2 rr[kVisPer];
+#pragma unroll
+    for (int j = 0; j < kVisPer; j++) {
+        const int64_t r = base + 256 * j;
+        rr[j] = r < n_rec ? rect[r] : make_uint2(0, 0);
+    }
+    unsigned bal[kVisPer];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int j = 0; j < kVisPer; j++) {
+        const bool vis = (rr[j].y & 0xFFFFu) > (rr[j].x & 0xFFFFu) && (rr[j].y >> 16) > (rr[j].x >> 16);
+        bal[j] = __ballot_sync(0xffffffffu, vis);
+        tot += __popc(bal[j]);
+    }
+    uint32_t at = 0;
+    if (lane == 0 && tot) at = atomicAdd(n_list, tot);
+    at = __shfl_sync(0xffffffffu, at, 0);
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kVisPer; j++) {
+        if ((bal[j] >> lane) & 1u) list[at + __popc(bal[j] & below)] = (uint32_t)(base + 256 * j);
+        at += __popc(bal[j]);
     }
 }
 
@@ -569,19 +642,38 @@ __global__ void __launch_bounds__(256) k_order_scatter(uint32_t* __restrict__ ra
     }
 }
 
+// with_list: ws was laid out with room for a list of plan.n_rec records
 int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams, const dg_plan& plan,
                     int64_t capacity, uint64_t* keys, uint32_t* vals, uint32_t* ranges, uint32_t* dev_count,
-                    void* ws, uint32_t* dev_status, cudaStream_t st)
+                    void* ws, bool with_list, uint32_t* dev_status, cudaStream_t st)
 {
     BinWs w;
-    bin_ws_layout(plan.n_tiles, capacity, &w, (char*)ws);
+    bin_ws_layout(plan.n_tiles, capacity, with_list ? plan.n_rec : 0, &w, (char*)ws);
     int64_t n_chunks = (plan.n_tiles + kScanChunk - 1) / kScanChunk;
-    if (cudaMemsetAsync(w.counts, 0, 4 * (size_t)(plan.n_tiles + 3 + 2 * kOrderBuckets), st) != cudaSuccess)
+    if (cudaMemsetAsync(w.counts, 0, 4 * (size_t)(plan.n_tiles + kCtrs + 2 * kOrderBuckets), st) != cudaSuccess)
         return DG_ERR_CUDA;
+    uint32_t* counters = w.counts + plan.n_tiles;
+    const bool listed = with_list && plan.n_rec > 0;
+    unsigned exp_grid = (unsigned)((plan.n_rec + 255) / 256);
+    if (listed) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return DG_ERR_CUDA;
+        k_visible<<<(unsigned)((plan.n_rec + 256 * kVisPer - 1) / (256 * kVisPer)), 256, 0, st>>>(
+            rect, plan.n_rec, w.vis_list, counters + 3);
+        note_launch();
+        exp_grid = (unsigned)std::min<int64_t>(exp_grid, (int64_t)sms * 5);   // 5 CTAs of 256 fit an SM
+    }
     if (plan.n_rec > 0) {
-        k_expand<false><<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(
-            rect, rec, cams, plan.n_views, plan.n_rec, plan.tile_w, plan.tile_h, w.counts, nullptr, 0, nullptr,
-            nullptr, nullptr);
+        if (listed)
+            k_expand<false, true><<<exp_grid, 256, 0, st>>>(rect, rec, cams, plan.n_views, plan.n_rec, plan.tile_w,
+                                                           plan.tile_h, w.counts, nullptr, 0, nullptr, nullptr,
+                                                           nullptr, w.vis_list, counters + 3);
+        else
+            k_expand<false, false><<<exp_grid, 256, 0, st>>>(rect, rec, cams, plan.n_views, plan.n_rec, plan.tile_w,
+                                                            plan.tile_h, w.counts, nullptr, 0, nullptr, nullptr,
+                                                            nullptr, nullptr, nullptr);
         note_launch();
     }
     k_scan_reduce<<<(unsigned)n_chunks, kScanThreads, 0, st>>>(w.counts, plan.n_tiles, w.partials);
@@ -590,12 +682,16 @@ int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams,
                                                              capacity, ranges, w.cursor, w.order_ctr);
     note_launch(3);
     if (plan.n_rec > 0) {
-        k_expand<true><<<(unsigned)((plan.n_rec + 255) / 256), 256, 0, st>>>(
-            rect, rec, cams, plan.n_views, plan.n_rec, plan.tile_w, plan.tile_h, nullptr, dev_count, capacity,
-            ranges, w.cursor, w.pairs);
+        if (listed)
+            k_expand<true, true><<<exp_grid, 256, 0, st>>>(rect, rec, cams, plan.n_views, plan.n_rec, plan.tile_w,
+                                                          plan.tile_h, nullptr, dev_count, capacity, ranges,
+                                                          w.cursor, w.pairs, w.vis_list, counters + 3);
+        else
+            k_expand<true, false><<<exp_grid, 256, 0, st>>>(rect, rec, cams, plan.n_views, plan.n_rec, plan.tile_w,
+                                                           plan.tile_h, nullptr, dev_count, capacity, ranges,
+                                                           w.cursor, w.pairs, nullptr, nullptr);
         note_launch();
     }
-    uint32_t* counters = w.counts + plan.n_tiles;
     k_sort_warp<<<(unsigned)((plan.n_tiles + 3) / 4), 128, 0, st>>>(ranges, plan.n_tiles, w.pairs, vals, keys,
                                                                     counters, w.mid_list, w.big_list, w.huge_list);
     k_sort_small<<<148 * 4, 256, 0, st>>>(ranges, w.pairs, vals, keys, counters, w.mid_list);

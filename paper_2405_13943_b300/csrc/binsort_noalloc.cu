@@ -20,9 +20,9 @@
 
 namespace dg {
 
-size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity);
+size_t bin_sort_ws_bytes(int64_t n_tiles, int64_t capacity, int64_t list_records);
 int launch_bin_sort(const float4*, const uint2*, const dg_camera*, const dg_plan&, int64_t, uint64_t*, uint32_t*,
-                    uint32_t*, uint32_t*, void*, uint32_t*, cudaStream_t);
+                    uint32_t*, uint32_t*, void*, bool, uint32_t*, cudaStream_t);
 int ensure_init();
 int bin_sort_args(const float* rec, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
                   int64_t capacity, const uint64_t* keys, const uint32_t* vals, const uint32_t* ranges,
@@ -65,12 +65,15 @@ extern "C" int dg_bin_sort_noalloc(const float* rec, const uint32_t* rect, const
     int rc = bin_sort_args(rec, rect, dev_cams, plan, capacity, keys, vals, ranges, dev_count, dev_status);
     if (rc != DG_OK || plan->n_tiles == 0) return rc;
     if (plan->n_tiles > DG_NOALLOC_MAX_TILES || capacity > DG_NOALLOC_MAX_INSTANCES) return DG_ERR_TOO_LARGE;
-    if (bin_sort_ws_bytes(plan->n_tiles, capacity) > kNoallocScratchBytes) return DG_ERR_TOO_LARGE;
+    if (bin_sort_ws_bytes(plan->n_tiles, capacity, 0) > kNoallocScratchBytes) return DG_ERR_TOO_LARGE;
+    // the list of visible records when the array has room for it (it only
+    // speeds the expansion up; the output is the same without it)
+    const bool with_list = bin_sort_ws_bytes(plan->n_tiles, capacity, plan->n_rec) <= kNoallocScratchBytes;
     void* ws = nullptr;
     rc = scratch_address(&ws);
     if (rc != DG_OK) return rc;
     rc = ensure_init();
     if (rc != DG_OK) return rc;
     return launch_bin_sort((const float4*)rec, (const uint2*)rect, dev_cams, *plan, capacity, keys, vals, ranges,
-                           dev_count, ws, dev_status, (cudaStream_t)stream);
+                           dev_count, ws, with_list, dev_status, (cudaStream_t)stream);
 }
