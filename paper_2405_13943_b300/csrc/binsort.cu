@@ -134,12 +134,22 @@ __device__ __forceinline__ bool tile_reached(const CullRec& k, uint32_t tx, uint
 // ---- passes 1 and 2: expansion of (record, tile) candidates ---------------------
 // Each lane owns one record; the candidate pairs of the warp's 32 records
 // (every tile of each rectangle) are numbered by a warp scan and dealt out 32
-// at a time, so the lanes stay busy however the rectangle sizes vary (most
-// records of a view are empty).  A lane finds the owner of its candidate by
-// a five-step search over the scan and takes the owner's data by shuffles.
-// Pass 1 (SCATTER = false) counts the kept pairs per tile; pass 2 writes them
-// into the tiles' ranges.  Both take the same decisions: the same inputs go
+// at a time, so the lanes stay busy however the rectangle sizes vary.  A
+// lane finds the owner of its candidate by a five-step search over the scan
+// and reads the owner's fields from the warp's slice of shared memory (four
+// 16-byte loads, where shuffles took one instruction a field).  Pass 1
+// (SCATTER = false) counts the kept pairs per tile; pass 2 writes them into
+// the tiles' ranges.  Both take the same decisions: the same inputs go
 // through the same instructions.
+//
+// A candidate's row in its record's rectangle is li / w, formed as
+// (li + 1/2) * rn(1/w) truncated: the exact quotient (li + 1/2) / w lies at
+// least 1/(2w) from an integer, and the two roundings move it by at most
+// 2^-23 (li + 1/2) / w, less than that for li < 2^21 (integer division
+// above, never reached by a rectangle of this library's tile counts).
+constexpr int kExpandThreads = 256;
+struct ExpandSlice { float4 q[4][32]; };   // field group g of lane L's record at q[g][L]
+
 // The expansion of one warp's 32 records (lane: record r when `own`); every
 // lane of the warp calls it together.
 template <bool SCATTER>
@@ -147,15 +157,15 @@ __device__ __forceinline__ void expand_warp(bool own, int64_t r, const uint2* __
                                             const float4* __restrict__ rec, const dg_camera* __restrict__ cams,
                                             int n_views, int tw, int th, uint32_t* __restrict__ counts,
                                             const uint32_t* __restrict__ ranges, uint32_t* __restrict__ cursor,
-                                            uint64_t* __restrict__ pairs)
+                                            uint64_t* __restrict__ pairs, ExpandSlice& sl)
 {
     const int lane = threadIdx.x & 31;
-    uint32_t x0 = 0, y0 = 0, w = 0, n = 0, toff = 0, TX = 0, dbits = 0;
+    uint32_t xy0 = 0, w = 0, n = 0, toff = 0, TX = 0, dbits = 0;
     CullRec k = {0.f, 0.f, 0.f, 0.f, 0.f, -1.f, 0.f, 0.f};
     if (own) {
         const uint2 rr = rect[r];
-        x0 = rr.x & 0xFFFFu; y0 = rr.x >> 16;
-        const uint32_t x1 = rr.y & 0xFFFFu, y1 = rr.y >> 16;
+        xy0 = rr.x;
+        const uint32_t x0 = rr.x & 0xFFFFu, y0 = rr.x >> 16, x1 = rr.y & 0xFFFFu, y1 = rr.y >> 16;
         if (x1 > x0 && y1 > y0) {
             w = x1 - x0;
             n = w * (y1 - y0);
@@ -173,44 +183,42 @@ __device__ __forceinline__ void expand_warp(bool own, int64_t r, const uint2* __
         if (lane >= o) incl += y;
     }
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;                     // uniform over the warp
     const uint32_t excl = incl - n;
-    const uint32_t rlo = (uint32_t)r;   // record index of this lane (low 32 bits suffice: n_rec < 2^32)
+    __syncwarp();                               // the previous call's reads of the slice are done
+    sl.q[0][lane] = make_float4(k.mx, k.my, k.a, k.b);
+    sl.q[1][lane] = make_float4(k.c, k.tau, k.b_c, k.b_a);
+    sl.q[2][lane] = make_float4(__uint_as_float(xy0), __uint_as_float(w), __uint_as_float(excl),
+                                w ? __frcp_rn((float)w) : 0.f);
+    sl.q[3][lane] = make_float4(__uint_as_float(toff), __uint_as_float(TX), __uint_as_float(dbits),
+                                __uint_as_float((uint32_t)r));   // low 32 bits suffice: n_rec < 2^32
+    __syncwarp();
     for (uint32_t base = 0; base < total; base += 32) {
         const uint32_t item = base + (uint32_t)lane;
         int o = 0;
 #pragma unroll
         for (int st = 16; st > 0; st >>= 1)
             if (__shfl_sync(0xffffffffu, incl, o + st - 1) <= item) o += st;
-        const int src = o < 31 ? o : 31;
-        const uint32_t oex = __shfl_sync(0xffffffffu, excl, src);
-        const uint32_t ox0 = __shfl_sync(0xffffffffu, x0, src), oy0 = __shfl_sync(0xffffffffu, y0, src);
-        const uint32_t ow = __shfl_sync(0xffffffffu, w, src);
-        const uint32_t otoff = __shfl_sync(0xffffffffu, toff, src), oTX = __shfl_sync(0xffffffffu, TX, src);
-        CullRec ok;
-        ok.mx = __shfl_sync(0xffffffffu, k.mx, src);
-        ok.my = __shfl_sync(0xffffffffu, k.my, src);
-        ok.a = __shfl_sync(0xffffffffu, k.a, src);
-        ok.b = __shfl_sync(0xffffffffu, k.b, src);
-        ok.c = __shfl_sync(0xffffffffu, k.c, src);
-        ok.tau = __shfl_sync(0xffffffffu, k.tau, src);
-        ok.b_c = __shfl_sync(0xffffffffu, k.b_c, src);
-        ok.b_a = __shfl_sync(0xffffffffu, k.b_a, src);
-        uint32_t od = 0, orec = 0;
-        if (SCATTER) {
-            od = __shfl_sync(0xffffffffu, dbits, src);
-            orec = __shfl_sync(0xffffffffu, rlo, src);
-        }
         if (item >= total) continue;
-        const uint32_t li = item - oex;
-        const uint32_t dy = li / ow, dx = li - dy * ow;
-        const uint32_t tx = ox0 + dx, ty = oy0 + dy;
+        const int src = o < 31 ? o : 31;
+        const float4 g0 = sl.q[0][src], g1 = sl.q[1][src], g2 = sl.q[2][src], g3 = sl.q[3][src];
+        CullRec ok;
+        ok.mx = g0.x; ok.my = g0.y; ok.a = g0.z; ok.b = g0.w;
+        ok.c = g1.x; ok.tau = g1.y; ok.b_c = g1.z; ok.b_a = g1.w;
+        const uint32_t oxy = __float_as_uint(g2.x), ow = __float_as_uint(g2.y);
+        const uint32_t li = item - __float_as_uint(g2.z);
+        const uint32_t dy = li < (1u << 21) ? __float2uint_rz(__fmul_rn(__fadd_rn(__uint2float_rn(li), 0.5f), g2.w))
+                                            : li / ow;
+        const uint32_t dx = li - dy * ow;
+        const uint32_t tx = (oxy & 0xFFFFu) + dx, ty = (oxy >> 16) + dy;
         if (!tile_reached(ok, tx, ty, tw, th)) continue;
-        const uint32_t t = otoff + ty * oTX + tx;
+        const uint32_t t = __float_as_uint(g3.x) + ty * __float_as_uint(g3.y) + tx;
         if (!SCATTER) {
             atomicAdd(&counts[t], 1u);
         } else {
             const uint32_t pos = atomicAdd(&cursor[t], 1u);
-            if (pos < ranges[2 * t + 1]) pairs[pos] = ((uint64_t)od << 32) | (uint64_t)orec;   // never false
+            if (pos < ranges[2 * t + 1])   // never false
+                pairs[pos] = ((uint64_t)__float_as_uint(g3.z) << 32) | (uint64_t)__float_as_uint(g3.w);
         }
     }
 }
@@ -224,7 +232,7 @@ __device__ __forceinline__ void expand_warp(bool own, int64_t r, const uint2* __
 // not depend on it, nor do the sorted segments (the pairs are sorted by
 // their full (depth, record) key).
 template <bool SCATTER, bool LIST>
-__global__ void __launch_bounds__(256) k_expand(const uint2* __restrict__ rect, const float4* __restrict__ rec,
+__global__ void __launch_bounds__(kExpandThreads) k_expand(const uint2* __restrict__ rect, const float4* __restrict__ rec,
                                                 const dg_camera* __restrict__ cams, int n_views, int64_t n_rec,
                                                 int tw, int th, uint32_t* __restrict__ counts,
                                                 const uint32_t* __restrict__ dev_count, int64_t capacity,
@@ -233,17 +241,19 @@ __global__ void __launch_bounds__(256) k_expand(const uint2* __restrict__ rect, 
                                                 const uint32_t* __restrict__ n_list)
 {
     if (SCATTER && (int64_t)(*dev_count) > capacity) return;   // uniform over the grid
+    __shared__ ExpandSlice s_sl[kExpandThreads / 32];
+    ExpandSlice& sl = s_sl[threadIdx.x >> 5];
     if (LIST) {
         const uint32_t cnt = *n_list;
         for (uint32_t b = blockIdx.x * blockDim.x; b < cnt; b += gridDim.x * blockDim.x) {
             const uint32_t i = b + threadIdx.x;
             const bool own = i < cnt;
             expand_warp<SCATTER>(own, own ? (int64_t)list[i] : 0, rect, rec, cams, n_views, tw, th, counts, ranges,
-                                 cursor, pairs);
+                                 cursor, pairs, sl);
         }
     } else {
         const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        expand_warp<SCATTER>(r < n_rec, r, rect, rec, cams, n_views, tw, th, counts, ranges, cursor, pairs);
+        expand_warp<SCATTER>(r < n_rec, r, rect, rec, cams, n_views, tw, th, counts, ranges, cursor, pairs, sl);
     }
 }
 
@@ -663,7 +673,7 @@ int launch_bin_sort(const float4* rec, const uint2* rect, const dg_camera* cams,
         k_visible<<<(unsigned)((plan.n_rec + 256 * kVisPer - 1) / (256 * kVisPer)), 256, 0, st>>>(
             rect, plan.n_rec, w.vis_list, counters + 3);
         note_launch();
-        exp_grid = (unsigned)std::min<int64_t>(exp_grid, (int64_t)sms * 5);   // 5 CTAs of 256 fit an SM
+        exp_grid = (unsigned)std::min<int64_t>(exp_grid, (int64_t)sms * 8);   // 8 CTAs of 256 fit an SM
     }
     if (plan.n_rec > 0) {
         if (listed)
