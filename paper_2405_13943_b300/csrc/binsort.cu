@@ -407,25 +407,27 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
 // first step compares i with its mirror in the k-block, later steps compare
 // i with i + j.  The smaller element always goes to the lower index, so
 // positions >= n behave as +infinity and need no storage (virtual padding).
+// (k, half and j are powers of two: block and offset by shifts and masks)
 template <int NT>
 __device__ __forceinline__ void bitonic_sort(uint64_t* s, uint32_t n)
 {
     uint32_t N = 1;
     while (N < n) N <<= 1;
-    for (uint32_t k = 2; k <= N; k <<= 1) {
-        uint32_t half = k >> 1;
+    for (uint32_t lk = 1; (1u << lk) <= N; lk++) {
+        const uint32_t k = 1u << lk, lh = lk - 1;
         for (uint32_t p = threadIdx.x; p < N / 2; p += NT) {
-            uint32_t blk = p / half, off = p % half;
-            uint32_t i = blk * k + off, l = blk * k + k - 1 - off;
+            const uint32_t blk = p >> lh, off = p & ((1u << lh) - 1u);
+            const uint32_t i = (blk << lk) + off, l = (blk << lk) + k - 1 - off;
             if (l < n) {
                 uint64_t a = s[i], b = s[l];
                 if (a > b) { s[i] = b; s[l] = a; }
             }
         }
         __syncthreads();
-        for (uint32_t j = half >> 1; j > 0; j >>= 1) {
+        for (int lj = (int)lh - 1; lj >= 0; lj--) {
+            const uint32_t j = 1u << lj;
             for (uint32_t p = threadIdx.x; p < N / 2; p += NT) {
-                uint32_t i = (p / j) * 2 * j + (p % j), l = i + j;
+                const uint32_t i = ((p >> lj) << (lj + 1)) + (p & (j - 1u)), l = i + j;
                 if (l < n) {
                     uint64_t a = s[i], b = s[l];
                     if (a > b) { s[i] = b; s[l] = a; }
@@ -615,12 +617,17 @@ __global__ void __launch_bounds__(1024) k_sort_huge(const uint32_t* __restrict__
     }
 }
 
+// Each CTA takes 256 tiles at a time: their ranks within their buckets from
+// shared-memory counters, then one global atomic per bucket the 256 touch
+// (the work order's few buckets would otherwise take every tile's atomic on
+// a handful of addresses).
 __global__ void __launch_bounds__(256) k_order_scatter(uint32_t* __restrict__ ranges, int64_t n_tiles,
                                                        uint32_t* __restrict__ ctr)
 {
     // exclusive scan of the bucket counts by warp 0, five buckets a lane
     constexpr int kPer = (kOrderBuckets + 31) / 32;
     __shared__ uint32_t s_off[kOrderBuckets];
+    __shared__ uint32_t s_cnt[kOrderBuckets], s_base[kOrderBuckets];
     if (threadIdx.x < 32) {
         uint32_t c[kPer], sum = 0;
 #pragma unroll
@@ -643,12 +650,23 @@ __global__ void __launch_bounds__(256) k_order_scatter(uint32_t* __restrict__ ra
             run += c[j];
         }
     }
-    __syncthreads();
     uint32_t* order = ranges + 2 * n_tiles;
     uint32_t* cursor = ctr + kOrderBuckets;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += (int64_t)gridDim.x * blockDim.x) {
-        const int b = order_bucket(ranges[2 * t + 1] - ranges[2 * t]);
-        order[s_off[b] + atomicAdd(&cursor[b], 1u)] = (uint32_t)t;
+    for (int64_t c0 = (int64_t)blockIdx.x * 256; c0 < n_tiles; c0 += (int64_t)gridDim.x * 256) {
+        for (int b = threadIdx.x; b < kOrderBuckets; b += 256) s_cnt[b] = 0;
+        __syncthreads();
+        const int64_t t = c0 + threadIdx.x;
+        int b = 0;
+        uint32_t rank = 0;
+        if (t < n_tiles) {
+            b = order_bucket(ranges[2 * t + 1] - ranges[2 * t]);
+            rank = atomicAdd(&s_cnt[b], 1u);
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < kOrderBuckets; q += 256)
+            if (s_cnt[q]) s_base[q] = s_off[q] + atomicAdd(&cursor[q], s_cnt[q]);
+        __syncthreads();
+        if (t < n_tiles) order[s_base[b] + rank] = (uint32_t)t;
     }
 }
 
