@@ -162,8 +162,15 @@ int dg_project(const dg_gaussians* x, const dg_camera* dev_cams, const dg_plan* 
  * after it, empty tiles last; the order within a bucket is unspecified),
  * dev_count[0] = number of instances M.  If M > capacity the DG_STATUS_CAPACITY bit is set and
  * every range is emptied (nothing is rendered); retry with capacity >= M.
- * Workspace: dg_bin_sort_workspace_size bytes of device memory. */
+ * Workspace: dg_bin_sort_workspace_size bytes of device memory (it holds,
+ * among the per-tile counters and the unsorted pairs, a list of the records
+ * with a non-empty rectangle, 4 bytes per record, over which the expansion
+ * runs).  A workspace of at least dg_bin_sort_workspace_min_size bytes but
+ * less than that runs without the list (every record scanned; the same
+ * output, slower in scenes where few records are visible); below the
+ * minimum, DG_ERR_WORKSPACE. */
 size_t dg_bin_sort_workspace_size(const dg_plan* plan, int64_t capacity);
+size_t dg_bin_sort_workspace_min_size(const dg_plan* plan, int64_t capacity);
 int dg_bin_sort(const float* rec, const uint32_t* rect, const dg_camera* dev_cams,
                 const dg_plan* plan, int64_t capacity, uint64_t* keys, uint32_t* vals,
                 uint32_t* ranges, uint32_t* dev_count, void* ws, size_t ws_bytes,

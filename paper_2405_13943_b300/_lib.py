@@ -80,6 +80,7 @@ _SIGS = {
                                 C.POINTER(DgPlan)]),
     "dg_project": (C.c_int, [C.POINTER(DgGaussians), _vp, C.POINTER(DgPlan), _vp, _vp, _vp]),
     "dg_bin_sort_workspace_size": (C.c_size_t, [C.POINTER(DgPlan), C.c_int64]),
+    "dg_bin_sort_workspace_min_size": (C.c_size_t, [C.POINTER(DgPlan), C.c_int64]),
     "dg_bin_sort": (C.c_int, [_vp, _vp, _vp, C.POINTER(DgPlan), C.c_int64, _vp, _vp, _vp, _vp, _vp, C.c_size_t,
                               _vp, _vp]),
     "dg_bin_sort_noalloc": (C.c_int, [_vp, _vp, _vp, C.POINTER(DgPlan), C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]),

@@ -224,6 +224,12 @@ size_t dg_bin_sort_workspace_size(const dg_plan* plan, int64_t capacity)
     return bin_sort_ws_bytes(plan->n_tiles, capacity, plan->n_rec);
 }
 
+size_t dg_bin_sort_workspace_min_size(const dg_plan* plan, int64_t capacity)
+{
+    if (!valid_plan(plan) || capacity < 0) return 0;
+    return bin_sort_ws_bytes(plan->n_tiles, capacity, 0);
+}
+
 int dg_bin_sort(const float* rec, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
                 int64_t capacity, uint64_t* keys, uint32_t* vals, uint32_t* ranges, uint32_t* dev_count, void* ws,
                 size_t ws_bytes, uint32_t* dev_status, void* stream)
@@ -231,11 +237,12 @@ int dg_bin_sort(const float* rec, const uint32_t* rect, const dg_camera* dev_cam
     int rc = bin_sort_args(rec, rect, dev_cams, plan, capacity, keys, vals, ranges, dev_count, dev_status);
     if (rc != DG_OK || plan->n_tiles == 0) return rc;
     if (!ws || ((uintptr_t)ws & 255u)) return DG_ERR_INVALID;
-    if (ws_bytes < bin_sort_ws_bytes(plan->n_tiles, capacity, plan->n_rec)) return DG_ERR_WORKSPACE;
+    if (ws_bytes < bin_sort_ws_bytes(plan->n_tiles, capacity, 0)) return DG_ERR_WORKSPACE;
+    const bool with_list = ws_bytes >= bin_sort_ws_bytes(plan->n_tiles, capacity, plan->n_rec);
     rc = ensure_init();
     if (rc != DG_OK) return rc;
     return launch_bin_sort((const float4*)rec, (const uint2*)rect, dev_cams, *plan, capacity, keys, vals, ranges,
-                           dev_count, ws, true, dev_status, (cudaStream_t)stream);
+                           dev_count, ws, with_list, dev_status, (cudaStream_t)stream);
 }
 
 int dg_rasterize_fwd(const float* rec, const uint32_t* vals, const uint32_t* ranges, const dg_camera* dev_cams,

@@ -216,3 +216,23 @@ def test_slot_backward_rejects_bad_arguments_before_launch(lib):
     assert call(slots=0xB0004) == L.DG_ERR_INVALID        # the slot total is 64-bit
     assert call(wsb=need - 8) == L.DG_ERR_WORKSPACE
     assert lib.dg_launch_count() == launches
+
+
+def test_bin_sort_workspace_sizes(lib):
+    """The binning workspace: the full size holds 4 bytes a record more than
+    the minimum (the visible-record list), and a workspace below the minimum
+    is refused on the host before any launch."""
+    from paper_2405_13943_b300 import dogs as D
+    cams = [S.cube_camera(64, 48), S.cube_camera(40, 40)]
+    cams[1].block = 1
+    arr, plan = D.plan_views(cams, [0, 1000, 1600], 16, 16)
+    cap = 5000
+    full = lib.dg_bin_sort_workspace_size(C.byref(plan), cap)
+    small = lib.dg_bin_sort_workspace_min_size(C.byref(plan), cap)
+    assert full >= small + 4 * plan.n_rec and full - small <= 4 * plan.n_rec + 255
+    assert small > 8 * cap
+    call = lambda ws, nb: lib.dg_bin_sort(0x10000, 0x20000, 0x30000, C.byref(plan), cap, None, 0x40000, 0x50000,
+                                          0x60000, ws, nb, 0x70000, None)
+    assert call(0x100000, small - 1) == L.DG_ERR_WORKSPACE
+    assert call(0x100008, full) == L.DG_ERR_INVALID           # the workspace must be 256-byte aligned
+    assert call(None, full) == L.DG_ERR_INVALID

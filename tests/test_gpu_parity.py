@@ -182,6 +182,36 @@ def test_multi_block_multi_view_sh3(D, oracle, tw, th):
     gs = grads.to_synth()
     assert np.all(gs.means[off[1]:off[2]] == 0) and np.all(gs.sh[off[1]:off[2]] == 0)
     check_counts(D, O, vb, f, masks, plan, bg)
+    check_binning_without_list(D, vb, f)
+
+
+def check_binning_without_list(D, vb, f):
+    """A workspace below dg_bin_sort_workspace_size (but at least the
+    minimum) bins without the visible-record list, scanning every record:
+    the same keys, values and ranges, bit for bit, as the oracle's."""
+    import ctypes as C
+    from paper_2405_13943_b300 import _lib as L
+    lib = L.lib()
+    full = lib.dg_bin_sort_workspace_size(C.byref(vb.plan), vb.capacity)
+    small = lib.dg_bin_sort_workspace_min_size(C.byref(vb.plan), vb.capacity)
+    assert 0 < small < full
+    ws = torch.zeros(full - 1, dtype=torch.uint8, device=vb.ws.device)     # one byte short of the list
+    vb.keys.zero_(); vb.vals.zero_(); vb.ranges.zero_()
+    L.check(lib.dg_bin_sort(L.ptr(vb.rec), L.ptr(vb.rect), L.ptr(vb.dev_cams), C.byref(vb.plan), vb.capacity,
+                            L.ptr(vb.keys), L.ptr(vb.vals), L.ptr(vb.ranges), L.ptr(vb.count), L.ptr(ws),
+                            ws.numel(), L.ptr(vb.status), None), "dg_bin_sort")
+    torch.cuda.synchronize()
+    M = int(vb.count.item())
+    assert M == f["bins"]["M"]
+    np.testing.assert_array_equal(vb.keys.cpu().numpy()[:M].view(np.uint64), f["bins"]["keys"])
+    np.testing.assert_array_equal(vb.vals.cpu().numpy()[:M].view(np.uint32), f["bins"]["vals"])
+    np.testing.assert_array_equal(vb.ranges.cpu().numpy()[:2 * vb.plan.n_tiles].view(np.uint32),
+                                  f["bins"]["ranges"].reshape(-1))
+    check_work_order(vb.ranges.cpu().numpy().view(np.uint32), vb.plan.n_tiles)
+    tiny = torch.zeros(small - 1, dtype=torch.uint8, device=vb.ws.device)
+    assert lib.dg_bin_sort(L.ptr(vb.rec), L.ptr(vb.rect), L.ptr(vb.dev_cams), C.byref(vb.plan), vb.capacity,
+                           L.ptr(vb.keys), L.ptr(vb.vals), L.ptr(vb.ranges), L.ptr(vb.count), L.ptr(tiny),
+                           tiny.numel(), L.ptr(vb.status), None) == L.DG_ERR_WORKSPACE
 
 
 def check_counts(D, O, vb, f, masks, plan, bg):
