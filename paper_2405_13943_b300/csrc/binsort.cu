@@ -458,57 +458,71 @@ __device__ __forceinline__ void write_segment(const uint64_t* s, uint32_t n, uin
 // upper partner is all padding changes nothing, and registers with i * 32 >=
 // n are skipped.  A compare-exchange keeps one value by a single 64-bit
 // comparison (equal values, only padding, may go either way).  No barriers.
-template <int NR>
-__device__ __forceinline__ void warp_bitonic(uint64_t* v, int lane, uint32_t n)
+// the half-cleaners of a merge in one warp's registers: e against e ^ j for
+// j = JTOP, JTOP / 2, .. 1, the smaller to the lower position (registers
+// with i * 32 >= n hold only padding and are skipped)
+template <int NR, int JTOP>
+__device__ __forceinline__ void warp_cleaners(uint64_t* v, int lane, uint32_t n)
 {
-    constexpr int N = 32 * NR;
 #pragma unroll
-    for (int k = 2; k <= N; k <<= 1) {
-        if (k <= 32) {                      // mirror within the lanes of one register
-            const bool lo = (lane & (k >> 1)) == 0;
+    for (int j = JTOP; j > 0; j >>= 1) {
+        if (j >= 32) {
+            const int ri = j >> 5;
+#pragma unroll
+            for (int i = 0; i < NR; i++) {
+                if (i & ri) continue;
+                if ((uint32_t)((i | ri) * 32) >= n) continue;
+                const uint64_t a = v[i], b = v[i | ri];
+                const bool sw = b < a;
+                v[i] = sw ? b : a;
+                v[i | ri] = sw ? a : b;
+            }
+        } else {
+            const bool lo = (lane & j) == 0;
 #pragma unroll
             for (int i = 0; i < NR; i++) {
                 if ((uint32_t)(i * 32) >= n) continue;
-                const uint64_t w = __shfl_xor_sync(0xffffffffu, v[i], k - 1);
+                const uint64_t w = __shfl_xor_sync(0xffffffffu, v[i], j);
                 v[i] = ((w < v[i]) == lo) ? w : v[i];
             }
-        } else {                            // mirror across registers: lane L of i meets lane 31 - L of ip
-            const int K = k >> 5;
-#pragma unroll
-            for (int i = 0; i < NR; i++) {
-                if ((i % K) >= K / 2) continue;
-                const int ip = (i / K) * K + (K - 1 - (i % K));
-                if ((uint32_t)(ip * 32) >= n) continue;
-                const uint64_t a = v[i], b = v[ip];
-                const uint64_t wa = __shfl_xor_sync(0xffffffffu, b, 31);
-                const uint64_t wb = __shfl_xor_sync(0xffffffffu, a, 31);
-                v[i] = wa < a ? wa : a;
-                v[ip] = wb < b ? b : wb;
-            }
         }
+    }
+}
+
+template <int NR, int K>
+__device__ __forceinline__ void warp_merge(uint64_t* v, int lane, uint32_t n)
+{
+    if constexpr (K <= 32) {                // mirror within the lanes of one register
+        const bool lo = (lane & (K >> 1)) == 0;
 #pragma unroll
-        for (int j = k >> 2; j > 0; j >>= 1) {
-            if (j >= 32) {
-                const int ri = j >> 5;
-#pragma unroll
-                for (int i = 0; i < NR; i++) {
-                    if (i & ri) continue;
-                    if ((uint32_t)((i | ri) * 32) >= n) continue;
-                    const uint64_t a = v[i], b = v[i | ri];
-                    const bool sw = b < a;
-                    v[i] = sw ? b : a;
-                    v[i | ri] = sw ? a : b;
-                }
-            } else {
-                const bool lo = (lane & j) == 0;
-#pragma unroll
-                for (int i = 0; i < NR; i++) {
-                    if ((uint32_t)(i * 32) >= n) continue;
-                    const uint64_t w = __shfl_xor_sync(0xffffffffu, v[i], j);
-                    v[i] = ((w < v[i]) == lo) ? w : v[i];
-                }
-            }
+        for (int i = 0; i < NR; i++) {
+            if ((uint32_t)(i * 32) >= n) continue;
+            const uint64_t w = __shfl_xor_sync(0xffffffffu, v[i], K - 1);
+            v[i] = ((w < v[i]) == lo) ? w : v[i];
         }
+    } else {                                // mirror across registers: lane L of i meets lane 31 - L of ip
+        constexpr int KR = K >> 5;
+#pragma unroll
+        for (int i = 0; i < NR; i++) {
+            if ((i % KR) >= KR / 2) continue;
+            const int ip = (i / KR) * KR + (KR - 1 - (i % KR));
+            if ((uint32_t)(ip * 32) >= n) continue;
+            const uint64_t a = v[i], b = v[ip];
+            const uint64_t wa = __shfl_xor_sync(0xffffffffu, b, 31);
+            const uint64_t wb = __shfl_xor_sync(0xffffffffu, a, 31);
+            v[i] = wa < a ? wa : a;
+            v[ip] = wb < b ? b : wb;
+        }
+    }
+    warp_cleaners<NR, (K >> 2)>(v, lane, n);
+}
+
+template <int NR, int K = 2>
+__device__ __forceinline__ void warp_bitonic(uint64_t* v, int lane, uint32_t n)
+{
+    if constexpr (K <= 32 * NR) {
+        warp_merge<NR, K>(v, lane, n);
+        warp_bitonic<NR, 2 * K>(v, lane, n);
     }
 }
 
@@ -561,8 +575,69 @@ __global__ void __launch_bounds__(128) k_sort_warp(const uint32_t* __restrict__ 
     else warp_sort_segment<8>(pairs, start, n, (uint64_t)t, vals, keys, lane);
 }
 
-// Segments of 257 .. kSmallCap instances: one 256-thread CTA each, bitonic in
-// shared memory (persistent over the list filled by k_sort_warp).
+// Segments of 257 .. kSmallCap instances: one 256-thread CTA each, 8 warps
+// of E = N / 256 keys a lane (N the network's power-of-two size, 512 ..
+// 2048; element e = warp * 32 E + i * 32 + lane in register i).  Each warp
+// first sorts its 32 E keys in registers (the warp network above); every
+// later merge then takes its mirror step, and its half-cleaners of distance
+// 32 E or more, through shared memory (a barrier each), and the rest in the
+// warps' registers -- 6 barriered steps at N = 2048 instead of the 66 of a
+// network wholly in shared memory.  The form is the all-ascending one
+// throughout, so padding (+infinity) stays at the end.
+template <int E>
+__device__ __forceinline__ void cta_sort_segment(const uint64_t* __restrict__ pairs, uint32_t start, uint32_t n,
+                                                 uint64_t tile, uint32_t* __restrict__ vals,
+                                                 uint64_t* __restrict__ keys, uint64_t* s)
+{
+    constexpr int PW = 32 * E, N = 256 * E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t e0 = (uint32_t)(warp * PW + lane);
+    uint64_t v[E];
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        const uint32_t e = e0 + 32 * i;
+        v[i] = e < n ? pairs[start + e] : ~0ull;
+    }
+    const uint32_t nl = n > (uint32_t)(warp * PW) ? min(n - (uint32_t)(warp * PW), (uint32_t)PW) : 0u;
+    warp_bitonic<E>(v, lane, nl);
+#pragma unroll 1
+    for (uint32_t k = 2 * PW; k <= (uint32_t)N; k <<= 1) {
+        __syncthreads();                           // the previous step's reads of s are done
+#pragma unroll
+        for (int i = 0; i < E; i++) s[e0 + 32 * i] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < E; i++) {              // e against its mirror in its k-block
+            const uint32_t e = e0 + 32 * i, off = e & (k - 1);
+            const uint64_t w = s[(e - off) + (k - 1 - off)];
+            v[i] = off < (k >> 1) ? (w < v[i] ? w : v[i]) : (w < v[i] ? v[i] : w);
+        }
+#pragma unroll 1
+        for (uint32_t j = k >> 2; j >= (uint32_t)PW; j >>= 1) {
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < E; i++) s[e0 + 32 * i] = v[i];
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < E; i++) {          // e against e ^ j, the smaller to the lower position
+                const uint32_t e = e0 + 32 * i;
+                const uint64_t w = s[e ^ j];
+                v[i] = (e & j) == 0 ? (w < v[i] ? w : v[i]) : (w < v[i] ? v[i] : w);
+            }
+        }
+        warp_cleaners<E, PW / 2>(v, lane, nl);
+    }
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        const uint32_t e = e0 + 32 * i;
+        if (e < n) {
+            vals[start + e] = (uint32_t)v[i];
+            if (keys) keys[start + e] = (tile << 32) | (v[i] >> 32);
+        }
+    }
+}
+
+// persistent over the list k_sort_warp fills
 __global__ void __launch_bounds__(256) k_sort_small(const uint32_t* __restrict__ ranges,
                                                     const uint64_t* __restrict__ pairs, uint32_t* __restrict__ vals,
                                                     uint64_t* __restrict__ keys, const uint32_t* __restrict__ counters,
@@ -573,11 +648,10 @@ __global__ void __launch_bounds__(256) k_sort_small(const uint32_t* __restrict__
     for (uint32_t i = blockIdx.x; i < nm; i += gridDim.x) {
         const uint32_t t = mid_list[i];
         const uint32_t start = ranges[2 * (int64_t)t], n = ranges[2 * (int64_t)t + 1] - start;
-        for (uint32_t j = threadIdx.x; j < n; j += 256) s[j] = pairs[start + j];
-        __syncthreads();
-        bitonic_sort<256>(s, n);
-        write_segment(s, n, start, (uint64_t)t, vals, keys, 256);
-        __syncthreads();
+        __syncthreads();                           // the previous segment's reads of s are done
+        if (n <= 512) cta_sort_segment<2>(pairs, start, n, (uint64_t)t, vals, keys, s);
+        else if (n <= 1024) cta_sort_segment<4>(pairs, start, n, (uint64_t)t, vals, keys, s);
+        else cta_sort_segment<8>(pairs, start, n, (uint64_t)t, vals, keys, s);
     }
 }
 
