@@ -2,9 +2,12 @@
 // per view, with dL/d(image).
 //
 // SSIM: 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2, zero
-// padding, "same" size.  The forward computes the five local moments with a
-// separable filter in shared memory (tile 32x32 plus a 5-pixel halo), the SSIM
-// map, and the three per-pixel partials dS/d(mean_x), dS/d(E[x^2]),
+// padding, "same" size.  The forward computes the local moments with a
+// separable filter in shared memory (output tile 32x54 plus a 5-pixel halo):
+// the means of x and y, of xy, and of x^2 + y^2 -- the two variances enter
+// SSIM only as their sum s1 + s2 = E[x^2 + y^2] - mx^2 - my^2, so four
+// filtered maps where the five moments would take five -- then the SSIM
+// map and the three per-pixel partials dS/d(mean_x), dS/d(E[x^2]),
 // dS/d(E[xy]); the backward applies the same (symmetric) filter to those
 // partials: dL/dx = F(a) + 2 x F(b) + y F(c).
 #include <algorithm>
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restri
 {
     extern __shared__ float s_dyn[];
     float* s_in = s_dyn;                                   // [2 buffers][x, y][kIH][kIWP]
-    float (*s_tmp)[kTHP][kTWP] = reinterpret_cast<float (*)[kTHP][kTWP]>(s_dyn + 4 * kIH * kIWP);
+    float (*s_tmp)[kTHP][kTWP] = reinterpret_cast<float (*)[kTHP][kTWP]>(s_dyn + 4 * kIH * kIWP);   // 4 maps
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
     float part = 0.f;   // this thread's SSIM sum over the current view's items
     int buf = 0;
@@ -279,26 +282,27 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restri
             continue;
         }
         const float* maps[2] = {s_in + buf * 2 * kIH * kIWP, s_in + (buf * 2 + 1) * kIH * kIWP};
-        hpass<5, 2>(g, maps, s_tmp, [&](float (*raw)[24], int c, float (*in)[kWin8], int i) {
+        hpass<4, 2>(g, maps, s_tmp, [&](float (*raw)[24], int c, float (*in)[kWin8], int i) {
             const float a = raw[0][c], b = raw[1][c];
-            in[0][i] = a; in[1][i] = b; in[2][i] = a * a; in[3][i] = b * b; in[4][i] = a * b;
+            in[0][i] = a; in[1][i] = b; in[2][i] = fmaf(a, a, b * b); in[3][i] = a * b;
         });
         __syncthreads();
         const float sc = -w_ssim / (float)(3 * it.HW);
         float* P = partial + 9 * it.pix + 3 * it.ch * it.HW;
         if (threadIdx.x < kTW * kVBlocks) {
             const int c = threadIdx.x % kTW, r0 = (threadIdx.x / kTW) * kBlk;
-            float mo[5][kBlk];
-            vpass<5>(g, s_tmp, c, r0, mo);
+            float mo[4][kBlk];
+            vpass<4>(g, s_tmp, c, r0, mo);
             const int gx = it.x0 + c;
 #pragma unroll
             for (int j = 0; j < kBlk; j++) {
                 const int gy = it.y0 + r0 + j;
                 if (r0 + j >= kTH || gx >= it.W || gy >= it.H) continue;
                 const float m1 = mo[0][j], m2 = mo[1][j];
-                const float s1 = mo[2][j] - m1 * m1, s2 = mo[3][j] - m2 * m2, s12 = mo[4][j] - m1 * m2;
+                const float mm = m1 * m1 + m2 * m2;
+                const float s12 = mo[3][j] - m1 * m2;      // s1 + s2 = mo[2] - mm
                 const float A1 = 2.f * m1 * m2 + C1, A2 = 2.f * s12 + C2;
-                const float B1 = m1 * m1 + m2 * m2 + C1, B2 = s1 + s2 + C2;
+                const float B1 = mm + C1, B2 = (mo[2][j] - mm) + C2;
                 const float iB = __fdividef(1.f, B1 * B2);
                 const float S = A1 * A2 * iB;
                 part += S;
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restri
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-constexpr size_t kSsimFwdSmem = sizeof(float) * (4 * kIH * kIWP + 5 * kTHP * kTWP);
+constexpr size_t kSsimFwdSmem = sizeof(float) * (4 * kIH * kIWP + 4 * kTHP * kTWP);
 constexpr size_t kSsimBwdSmem = sizeof(float) * (6 * kIH * kIWP + 3 * kTHP * kTWP);
 
 // dL/dx = w_l1 sign(x - y) / N + F(a) + 2 x F(b) + y F(c); the L1 sum of the
