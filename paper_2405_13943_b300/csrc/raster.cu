@@ -248,9 +248,9 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
                 const float raw = strip_raw(q, h.y);
                 if (!(raw >= kAlphaMin)) continue;
                 const float a = fminf(raw, kAlphaMax);
-                const float Tn = T[k] * (1.f - a);
-                if (Tn < kTMin) { live &= ~(1u << k); off[k] = -kDeadRow; continue; }
                 const float wt = a * T[k];
+                const float Tn = T[k] - wt;                // T (1 - alpha), by the weight already formed
+                if (Tn < kTMin) { live &= ~(1u << k); off[k] = -kDeadRow; continue; }
                 C0[k] = fmaf(c.x, wt, C0[k]);
                 C1[k] = fmaf(c.y, wt, C1[k]);
                 C2[k] = fmaf(c.z, wt, C2[k]);
