@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
                 c1 = fmaf(Gk.y, wT, c1);
                 c2 = fmaf(Gk.z, wT, c2);
                 // dL/dalpha = T_j (G . c - G . B); d alpha / d power = alpha below the clamp
-                const float gd = fmaf(Gk.x, c.x, fmaf(Gk.y, c.y, Gk.z * c.z)) - Bg[k];
+                const float gd = fmaf(Gk.x, c.x, fmaf(Gk.y, c.y, fmaf(Gk.z, c.z, -Bg[k])));
                 Bg[k] = fmaf(a, gd, Bg[k]);      // G . B <- a G . c + (1 - a) G . B
                 T[k] = Tj;
                 const float dLdp = raw < kAlphaMax ? wT * gd : 0.f;
@@ -473,11 +473,12 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
                 S1 = fmaf(dLdp, (float)k, S1);
                 S2 = fmaf(dLdp, (float)(k * k), S2);
             }
-            float gr[8] = {0, 0, 0, 0, 0, 0, c0, c1};
-            float g8 = c2;
-            if (todo) {                         // lanes with no composited pixel give zeros
-                // power = -(a dx^2 + 2 b dx dy + c dy^2) / 2 with dx = mx - px,
-                // dy = my - py; its gradients summed over the strip's pixels
+            // power = -(a dx^2 + 2 b dx dy + c dy^2) / 2 with dx = mx - px,
+            // dy = my - py; its gradients summed over the strip's pixels.  Every
+            // lane forms them (the warp runs this for any lane with work); a lane
+            // with no composited pixel has zero sums and gives (signed) zeros.
+            float gr[8];
+            {
                 const float4 kc = s_k[j];
                 const float dx = g.x - Lg.fx, dy0 = g.y - Lg.fy0;
                 const float Sy = fmaf(-Lg.dy, S1, dy0 * S0);                                  // sum dLdp dy
@@ -488,7 +489,10 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
                 gr[3] = -dx * Sy;
                 gr[4] = -0.5f * Syy;
                 gr[5] = S0 * h.z;                       // d alpha / d opacity = alpha / opacity
+                gr[6] = c0;
+                gr[7] = c1;
             }
+            float g8 = c2;
             const float sred = warp_reduce_scatter8(gr, g8, lane);
             const uint32_t rid = __float_as_uint(h.w);
             if (SLOT) {
