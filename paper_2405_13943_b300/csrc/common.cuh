@@ -12,6 +12,10 @@ void note_launch(int n = 1);
 
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
+// log2(1/255) rounded to float: a pair is composited when its alpha exponent
+// e = log2(o G) is at least this (alpha >= 1/255 in the log domain, decided
+// before 2^e is formed)
+constexpr float kQMin = -7.99435329f;
 constexpr float kTMin = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;
 
@@ -74,7 +78,10 @@ __device__ __forceinline__ int find_view_of_rec(const dg_camera* cams, int n_vie
 
 // ---- compositing decision shared by the forward and the backward -------------
 // A staged instance: exponent coefficients in log2 units and log2(opacity):
-// power2 = A dx^2 + B dx dy + C dy^2, alpha = 2^(power2 + lo).
+// power2 = A dx^2 + B dx dy + C dy^2, alpha = 2^(power2 + lo).  An instance
+// whose opacity alone is below 1/255 (lo < kQMin; binning keeps a few, its
+// cull being widened) can reach no pixel: its lo is staged as -1e30, so that
+// every exponent of it fails the first test.
 struct Staged {
     float mx, my, A, B, C, lo;
 };
@@ -88,6 +95,7 @@ __device__ __forceinline__ Staged stage_geometry(float4 r0, float4 r1)
     s.B = __fmul_rn(-kLog2e, r0.w);
     s.C = __fmul_rn(-0.5f * kLog2e, r1.x);
     s.lo = __log2f(r1.y);
+    if (!(s.lo >= kQMin)) s.lo = -1e30f;
     return s;
 }
 

@@ -75,11 +75,12 @@ __device__ __forceinline__ LaneGeom lane_geom(const TileInfo& ti, int tw, int ti
 // once per instance (no expansion from the strip's first pixel, whose large
 // terms would cancel near the Gaussian's centre).  The conic is positive
 // definite, so p is never positive in exact arithmetic; a positive value is
-// rounding and is taken as 0, i.e. e = min(q, log2 o).  q >= -8 is the
-// first test of a pair (below it alpha <= 2^-8 < 1/255): it only filters,
-// since e <= q and a pixel with alpha >= 1/255 has e > -8.  The forward
-// and the backward evaluate q, e and alpha by the same instructions, so both
-// take the same decisions.
+// rounding and is taken as 0, i.e. e = min(q, log2 o).  A pair is
+// composited when e >= kQMin = log2(1/255), the skip rule of Eq. 2 in the
+// log domain; since every staged instance has log2 o >= kQMin, that is
+// q >= kQMin, one test taken before 2^e is formed.  The forward and the
+// backward evaluate q, e and alpha by the same instructions, so both take
+// the same decisions.
 struct Strip {
     float E0, Bdx, C, dy0, ddy;
 };
@@ -92,7 +93,7 @@ __device__ __forceinline__ float strip_q(const Strip& s, int k)
 
 // the same with the row offset k dy given (k dy is exact, so dy0 - off rounds
 // exactly as the fused multiply-add above); an offset of -kDeadRow moves a
-// pixel so far from every instance that it fails q >= -8
+// pixel so far from every instance that it fails q >= kQMin
 constexpr float kDeadRow = 1e15f;
 __device__ __forceinline__ float strip_q_off(const Strip& s, float off)
 {
@@ -139,7 +140,7 @@ __device__ __forceinline__ Strip strip_setup(float mx, float my, float A, float 
     return st;
 }
 
-// 2^x by the SFU (PTX ex2.approx.ftz; x >= -8 here, so no denormal result)
+// 2^x by the SFU (PTX ex2.approx.ftz; x >= kQMin > -8 here, so no denormal result)
 __device__ __forceinline__ float ex2(float x)
 {
     float y;
@@ -147,9 +148,7 @@ __device__ __forceinline__ float ex2(float x)
     return y;
 }
 
-// o G of a pixel that passed q >= -8: the pair is composited iff
-// raw >= 1/255 (alpha = min(raw, 0.99) is below 1/255 exactly when raw is,
-// 0.99 being above it), with alpha = min(raw, 0.99)
+// o G of a composited pair (q >= kQMin), with alpha = min(raw, 0.99)
 __device__ __forceinline__ float strip_raw(float q, float lo) { return ex2(fminf(q, lo)); }
 
 struct Fetch {
@@ -244,9 +243,8 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
                 const float q = qs[k];
-                if (!(q >= -8.0f)) continue;
+                if (!(q >= kQMin)) continue;
                 const float raw = strip_raw(q, h.y);
-                if (!(raw >= kAlphaMin)) continue;
                 const float a = fminf(raw, kAlphaMax);
                 const float wt = a * T[k];
                 const float Tn = T[k] - wt;                // T (1 - alpha), by the weight already formed
@@ -445,7 +443,7 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             strip_q_all<PPL>(sp, nullptr, qk);
             uint32_t reach = 0;
 #pragma unroll
-            for (int k = 0; k < PPL; k++) reach |= (uint32_t)(qk[k] >= -8.0f) << k;
+            for (int k = 0; k < PPL; k++) reach |= (uint32_t)(qk[k] >= kQMin) << k;
             const uint32_t todo = joined & reach;
             if (!__any_sync(0xffffffffu, todo != 0u)) continue;
             const float4 c = s_c[j];
@@ -456,7 +454,6 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             for (int k = 0; k < PPL; k++) {
                 if (!(todo >> k & 1u)) continue;
                 const float raw = strip_raw(qk[k], h.y);
-                if (!(raw >= kAlphaMin)) continue;
                 const float a = fminf(raw, kAlphaMax);
                 const float4 Gk = s_Gl[tid + NT * k];
                 const float Tj = T[k] * __fdividef(1.f, 1.f - a);
