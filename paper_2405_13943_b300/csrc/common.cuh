@@ -16,6 +16,9 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 // e = log2(o G) is at least this (alpha >= 1/255 in the log domain, decided
 // before 2^e is formed)
 constexpr float kQMin = -7.99435329f;
+// log2(0.99) rounded to float: alpha = min(o G, 0.99) is formed as
+// 2^min(e, kLogAlphaMax), the clamp taken in the exponent
+constexpr float kLogAlphaMax = -0.0144995693f;
 constexpr float kTMin = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;
 

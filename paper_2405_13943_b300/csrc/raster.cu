@@ -148,8 +148,10 @@ __device__ __forceinline__ float ex2(float x)
     return y;
 }
 
-// o G of a composited pair (q >= kQMin), with alpha = min(raw, 0.99)
-__device__ __forceinline__ float strip_raw(float q, float lo) { return ex2(fminf(q, lo)); }
+// alpha of a composited pair (q >= kQMin): 2^min(q, loc) with loc =
+// min(log2 o, log2 0.99) staged per instance, i.e. min(o G, 0.99) with the
+// clamp taken in the exponent (and a positive rounding of p taken as 0)
+__device__ __forceinline__ float strip_alpha(float q, float loc) { return ex2(fminf(q, loc)); }
 
 struct Fetch {
     float4 r0, r1, r2;
@@ -225,14 +227,16 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
                 Staged st = stage_geometry(nx[s].r0, nx[s].r1);
                 s_g[j] = make_float4(st.mx, st.my, st.A, st.B);
                 s_h[j] = make_float2(st.C, st.lo);
-                s_c[j] = make_float4(nx[s].r1.z, nx[s].r1.w, nx[s].r2.x, 0.f);
+                s_c[j] = make_float4(nx[s].r1.z, nx[s].r1.w, nx[s].r2.x, fminf(st.lo, kLogAlphaMax));
             }
         }
         cta_sync<NW>();
 #pragma unroll
         for (int s = 0; s < S; s++) fetch(rec, vals, ti.start, base + R + tid + s * NT, n, nx[s]);
         const uint32_t cnt = min((uint32_t)R, n - base);
-        for (uint32_t j = 0; j < cnt && live; j++) {
+        // stopped pixels fail the first test by their dead-row offset, so the
+        // walk needs no per-instance live test (the round's vote ends the tile)
+        for (uint32_t j = 0; j < cnt; j++) {
             const float4 g = s_g[j];
             const float2 h = s_h[j];
             if (CNT) n_seen += __popc(live);
@@ -244,8 +248,7 @@ __global__ void __launch_bounds__(32 * NW) k_raster_fwd(const float4* __restrict
             for (int k = 0; k < PPL; k++) {
                 const float q = qs[k];
                 if (!(q >= kQMin)) continue;
-                const float raw = strip_raw(q, h.y);
-                const float a = fminf(raw, kAlphaMax);
+                const float a = strip_alpha(q, c.w);
                 const float wt = a * T[k];
                 const float Tn = T[k] - wt;                // T (1 - alpha), by the weight already formed
                 if (Tn < kTMin) { live &= ~(1u << k); off[k] = -kDeadRow; continue; }
@@ -414,8 +417,12 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
                 Staged st = stage_geometry(nx[s].r0, nx[s].r1);
                 s_g[j] = make_float4(st.mx, st.my, st.A, st.B);
                 s_h[j] = make_float4(st.C, st.lo, __frcp_rn(nx[s].r1.y), __uint_as_float(nx[s].r));
-                s_k[j] = make_float4(nx[s].r0.z, nx[s].r0.w, nx[s].r1.x, 0.f);
-                s_c[j] = make_float4(nx[s].r1.z, nx[s].r1.w, nx[s].r2.x, 0.f);
+                // s_k.w: the exponent at and above which alpha is clamped
+                // (kLogAlphaMax, or +inf for an instance whose opacity is below
+                // 0.99: min(q, log2 o) >= kLogAlphaMax exactly when q >= it)
+                s_k[j] = make_float4(nx[s].r0.z, nx[s].r0.w, nx[s].r1.x,
+                                     st.lo >= kLogAlphaMax ? kLogAlphaMax : __int_as_float(0x7f800000));
+                s_c[j] = make_float4(nx[s].r1.z, nx[s].r1.w, nx[s].r2.x, fminf(st.lo, kLogAlphaMax));
             }
         }
         cta_sync<NW>();
@@ -447,14 +454,14 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             const uint32_t todo = joined & reach;
             if (!__any_sync(0xffffffffu, todo != 0u)) continue;
             const float4 c = s_c[j];
+            const float4 kc = s_k[j];
             // colour sums and the moments of dL/dpower along the strip:
             // S0 = sum dLdp, S1 = sum k dLdp, S2 = sum k^2 dLdp (dy_k = dy0 - k dy)
             float c0 = 0.f, c1 = 0.f, c2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
                 if (!(todo >> k & 1u)) continue;
-                const float raw = strip_raw(qk[k], h.y);
-                const float a = fminf(raw, kAlphaMax);
+                const float a = strip_alpha(qk[k], c.w);
                 const float4 Gk = s_Gl[tid + NT * k];
                 const float Tj = T[k] * __fdividef(1.f, 1.f - a);
                 const float wT = a * Tj;
@@ -465,7 +472,7 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
                 const float gd = fmaf(Gk.x, c.x, fmaf(Gk.y, c.y, fmaf(Gk.z, c.z, -Bg[k])));
                 Bg[k] = fmaf(a, gd, Bg[k]);      // G . B <- a G . c + (1 - a) G . B
                 T[k] = Tj;
-                const float dLdp = raw < kAlphaMax ? wT * gd : 0.f;
+                const float dLdp = qk[k] < kc.w ? wT * gd : 0.f;   // zero where alpha is clamped
                 S0 += dLdp;
                 S1 = fmaf(dLdp, (float)k, S1);
                 S2 = fmaf(dLdp, (float)(k * k), S2);
@@ -476,7 +483,6 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             // with no composited pixel has zero sums and gives (signed) zeros.
             float gr[8];
             {
-                const float4 kc = s_k[j];
                 const float dx = g.x - Lg.fx, dy0 = g.y - Lg.fy0;
                 const float Sy = fmaf(-Lg.dy, S1, dy0 * S0);                                  // sum dLdp dy
                 const float Syy = fmaf(Lg.dy * Lg.dy, S2, fmaf(-2.f * dy0 * Lg.dy, S1, dy0 * dy0 * S0));  // sum dLdp dy^2
