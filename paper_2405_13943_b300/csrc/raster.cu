@@ -343,6 +343,38 @@ struct SlotOut {
     uint64_t cap;
 };
 
+// The adjoint of one instance at the pixels of a thread's strip that
+// composited it (bits of todo), back to front: T and G . B of each pixel
+// stepped over the instance, the colour sums and the moments S0, S1, S2 of
+// dL/dpower along the strip (dy_k = dy0 - k dy).  CLAMP: the instance may
+// reach the 0.99 alpha clamp (exponent q at or above qc), where d alpha /
+// d power is zero.
+template <int PPL, int NT, bool CLAMP>
+__device__ __forceinline__ void bwd_rows(uint32_t todo, const float* qk, const float4& c, float qc,
+                                         const float4* s_Gl, int tid, float* T, float* Bg, float& c0, float& c1,
+                                         float& c2, float& S0, float& S1, float& S2)
+{
+#pragma unroll
+    for (int k = 0; k < PPL; k++) {
+        if (!(todo >> k & 1u)) continue;
+        const float a = strip_alpha(qk[k], c.w);
+        const float4 Gk = s_Gl[tid + NT * k];
+        const float Tj = T[k] * __fdividef(1.f, 1.f - a);
+        const float wT = a * Tj;
+        c0 = fmaf(Gk.x, wT, c0);
+        c1 = fmaf(Gk.y, wT, c1);
+        c2 = fmaf(Gk.z, wT, c2);
+        // dL/dalpha = T_j (G . c - G . B); d alpha / d power = alpha below the clamp
+        const float gd = fmaf(Gk.x, c.x, fmaf(Gk.y, c.y, fmaf(Gk.z, c.z, -Bg[k])));
+        Bg[k] = fmaf(a, gd, Bg[k]);      // G . B <- a G . c + (1 - a) G . B
+        T[k] = Tj;
+        const float dLdp = (!CLAMP || qk[k] < qc) ? wT * gd : 0.f;
+        S0 += dLdp;
+        S1 = fmaf(dLdp, (float)k, S1);
+        S2 = fmaf(dLdp, (float)(k * k), S2);
+    }
+}
+
 template <int NW, int S, bool SLOT = false>
 __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd(const float4* __restrict__ rec,
                                                         const uint32_t* __restrict__ vals,
@@ -458,25 +490,12 @@ __global__ void __launch_bounds__(32 * NW, bwd_min_blocks<NW, S>()) k_raster_bwd
             // colour sums and the moments of dL/dpower along the strip:
             // S0 = sum dLdp, S1 = sum k dLdp, S2 = sum k^2 dLdp (dy_k = dy0 - k dy)
             float c0 = 0.f, c1 = 0.f, c2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
-#pragma unroll
-            for (int k = 0; k < PPL; k++) {
-                if (!(todo >> k & 1u)) continue;
-                const float a = strip_alpha(qk[k], c.w);
-                const float4 Gk = s_Gl[tid + NT * k];
-                const float Tj = T[k] * __fdividef(1.f, 1.f - a);
-                const float wT = a * Tj;
-                c0 = fmaf(Gk.x, wT, c0);
-                c1 = fmaf(Gk.y, wT, c1);
-                c2 = fmaf(Gk.z, wT, c2);
-                // dL/dalpha = T_j (G . c - G . B); d alpha / d power = alpha below the clamp
-                const float gd = fmaf(Gk.x, c.x, fmaf(Gk.y, c.y, fmaf(Gk.z, c.z, -Bg[k])));
-                Bg[k] = fmaf(a, gd, Bg[k]);      // G . B <- a G . c + (1 - a) G . B
-                T[k] = Tj;
-                const float dLdp = qk[k] < kc.w ? wT * gd : 0.f;   // zero where alpha is clamped
-                S0 += dLdp;
-                S1 = fmaf(dLdp, (float)k, S1);
-                S2 = fmaf(dLdp, (float)(k * k), S2);
-            }
+            // an instance below 0.99 opacity (kc.w = +inf, nearly all) is never
+            // clamped: its pixels take the adjoint without the clamp test
+            if (kc.w == __int_as_float(0x7f800000))     // uniform over the warp
+                bwd_rows<PPL, NT, false>(todo, qk, c, kc.w, s_Gl, tid, T, Bg, c0, c1, c2, S0, S1, S2);
+            else
+                bwd_rows<PPL, NT, true>(todo, qk, c, kc.w, s_Gl, tid, T, Bg, c0, c1, c2, S0, S1, S2);
             // power = -(a dx^2 + 2 b dx dy + c dy^2) / 2 with dx = mx - px,
             // dy = my - py; its gradients summed over the strip's pixels.  Every
             // lane forms them (the warp runs this for any lane with work); a lane
