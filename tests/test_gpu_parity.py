@@ -155,6 +155,35 @@ def test_small_single_view_forward_backward(D, oracle):
     check_counts(D, O, vb, f, masks, plan, (0, 0, 0))
 
 
+def test_clamped_alpha_forward_backward(D, oracle):
+    """A third of the Gaussians at opacity 0.9975 (logit 6): near their centres
+    o G reaches the 0.99 clamp, which the kernels take in the exponent, and
+    the backward's adjoint gives zero d alpha / d power there (those instances
+    take its clamp-aware row loop).  Images, T_final, last and gradients
+    against the oracle, which clamps alpha = min(0.99, o G) in FP64."""
+    O = oracle
+    cam = S.cube_camera()
+    g = S.cube_scene(3000, 1007)
+    g.opacity_logits[::3] = 6.0
+    g = curate_gaussians(O, g, [cam], 16, 16)
+    xbuf, vb, grads, f, ob, masks, plan = run_pair(D, O, g, [cam], [(0, g.n)], [0, g.n], 16, 16, (0.1, 0.2, 0.3))
+    r = f["proj"]["rec"]
+    hi = np.nonzero((r[:, O.REC_VIS] == 1) & (r[:, O.REC_OP] > 0.99))[0]
+    assert hi.size > 100                                    # clamp-capable instances in view
+    # (pixel, instance) pairs with o G >= 0.99 among the pixel centres near those means
+    clamped = 0
+    for i in hi:
+        px = np.floor(r[i, O.REC_MX]) + np.arange(-2, 3) + 0.5
+        py = np.floor(r[i, O.REC_MY]) + np.arange(-2, 3) + 0.5
+        X, Y = np.meshgrid(px - r[i, O.REC_MX], py - r[i, O.REC_MY])
+        G = np.exp(-0.5 * (r[i, O.REC_A] * X * X + 2 * r[i, O.REC_B] * X * Y + r[i, O.REC_C] * Y * Y))
+        inside = np.logical_and.outer((py > 0) & (py < cam.height), (px > 0) & (px < cam.width))
+        clamped += int(((r[i, O.REC_OP] * G >= 0.99) & inside).sum())
+    assert clamped > 50
+    check_forward(D, O, vb, f, masks, plan)
+    check_backward(D, O, g, grads, ob, 0)
+
+
 @pytest.mark.parametrize("tw,th", [(16, 16), (32, 8), (8, 32)])
 def test_multi_block_multi_view_sh3(D, oracle, tw, th):
     """Three blocks (two views, none, one view), ragged image sizes, SH
