@@ -455,7 +455,12 @@ def run_ours(args, dist, rank, world):
     calls += [("bin_sort", lambda: D.dg_bin_sort(vb)),
               ("rasterize_fwd", lambda: D.dg_rasterize_fwd(vb, tr.bg)),
               ("loss", lambda: tr._loss(tr.targets[tr.t % len(tr.view_sets)]))]
-    if fused:       # compositing adjoint, then projection adjoint + x-step fused
+    listed = split and tr.idle_mode.startswith("stream") and tr.listed_part2
+    if fused and listed:    # part 2 over the groups dg_xstep_stream listed in tr.xs_ws
+        calls += [("rasterize_bwd", bwd_fused),
+                  ("xstep", lambda: D.dg_xstep_listed(2, vb, *xs_args, tr.xs_ws, step=1, dev_step=tr.dev_step,
+                                                      **zargs))]
+    elif fused:     # compositing adjoint, then projection adjoint + x-step fused
         calls += [("rasterize_bwd", bwd_fused),
                   ("xstep", lambda: D.dg_xstep_part(2 if split else 0, vb, *xs_args, step=1,
                                                     dev_step=tr.dev_step, **zargs))]

@@ -342,6 +342,33 @@ int dg_xstep_stream(int ctas, const uint32_t* rect, const dg_camera* dev_cams, c
                     float eps, int step, const int32_t* dev_step, dg_gaussians* z_unshared,
                     const int32_t* copy_gid, void* ws, size_t ws_bytes, void* stream);
 
+/* dg_xstep_stream's two launches as separate calls, and part 2 over a list:
+ * dg_xstep_groups lists, in ws (as for dg_xstep_stream), every group of 128
+ * copies once: the groups without a kept record from the front, the others
+ * from the back.  dg_xstep_listed then takes a part of dg_xstep_part's step
+ * (Eq. 8a / 12a) over those lists: part 1 streamed as dg_xstep_stream does
+ * (`ctas` as there), part 2 (the fused adjoint + step, after the compositing
+ * adjoint; `ctas` unused) with the n-th CTA on the n-th listed group with a
+ * kept record, so that the CTAs past the list, which find nothing to step,
+ * all come after those that step.  The two parts together take
+ * dg_xstep_part's step, bit for bit.  The caller
+ * orders dg_xstep_groups before both parts (on another stream: by an event
+ * recorded after it) and leaves ws alone until both have run.
+ * dg_xstep_groups: arguments as dg_xstep_stream's (x gives the copy count);
+ * DG_ERR_INVALID for a bad plan, a block with two views, a missing or
+ * misaligned rect / dev_cams / ws, DG_ERR_WORKSPACE for a small ws_bytes.
+ * dg_xstep_listed: arguments and errors as dg_xstep_part's, plus ws and
+ * ws_bytes as dg_xstep_stream's; DG_ERR_INVALID for a part other than 1 or 2
+ * or ctas outside 0..65535. */
+int dg_xstep_groups(const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                    const dg_gaussians* x, void* ws, size_t ws_bytes, void* stream);
+int dg_xstep_listed(int part, int ctas, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                    const float* drec, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v,
+                    const dg_gaussians* anchor, const uint8_t* copy_shared, const float* rho,
+                    const float* lr, float beta1, float beta2, float eps, int step,
+                    const int32_t* dev_step, dg_gaussians* z_unshared, const int32_t* copy_gid,
+                    void* ws, size_t ws_bytes, void* stream);
+
 /* ---- ADMM (K9, K10) -------------------------------------------------------- */
 /* x-step (Eq. 8a / 12a): one Adam step on every local copy with gradient
  * g + rho_grp (x - anchor) on shared copies (copy_shared[c] != 0), where the

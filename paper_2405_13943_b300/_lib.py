@@ -116,6 +116,11 @@ _SIGS = {
                                    C.POINTER(DgGaussians), C.POINTER(DgGaussians), C.POINTER(DgGaussians), _vp,
                                    C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float,
                                    C.c_int, _vp, C.POINTER(DgGaussians), _vp, _vp, C.c_size_t, _vp]),
+    "dg_xstep_groups": (C.c_int, [_vp, _vp, C.POINTER(DgPlan), C.POINTER(DgGaussians), _vp, C.c_size_t, _vp]),
+    "dg_xstep_listed": (C.c_int, [C.c_int, C.c_int, _vp, _vp, C.POINTER(DgPlan), _vp, C.POINTER(DgGaussians),
+                                   C.POINTER(DgGaussians), C.POINTER(DgGaussians), C.POINTER(DgGaussians), _vp,
+                                   C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_float, C.c_float, C.c_float,
+                                   C.c_int, _vp, C.POINTER(DgGaussians), _vp, _vp, C.c_size_t, _vp]),
     "dg_step_advance": (C.c_int, [_vp, _vp]),
     "dg_densify_stats": (C.c_int, [_vp, _vp, C.POINTER(DgPlan), _vp, _vp, _vp]),
     "dg_densify_workspace_size": (C.c_size_t, [C.c_int64]),

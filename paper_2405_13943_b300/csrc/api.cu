@@ -64,13 +64,14 @@ int launch_u8_to_f32(const uint8_t*, float*, int64_t, cudaStream_t);
 int launch_f32_to_u8(const float*, uint8_t*, int64_t, cudaStream_t);
 int launch_xstep(int, int, dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*, const uint8_t*,
                  const dg_camera*, const dg_plan&, const uint2*, const float4*, const AdamArgs&, const int32_t*,
-                 dg_gaussians*, const int32_t*, cudaStream_t);
+                 dg_gaussians*, const int32_t*, const void*, cudaStream_t);
 int xstep_stream_init();
 int raster_bwd_init();
 size_t xstep_stream_ws_bytes(int64_t n);
+int launch_xstep_groups(const dg_gaussians*, const dg_camera*, const dg_plan&, const uint2*, void*, cudaStream_t);
 int launch_xstep_stream(int, dg_gaussians*, dg_gaussians*, dg_gaussians*, const dg_gaussians*, const uint8_t*,
                         const dg_camera*, const dg_plan&, const uint2*, const AdamArgs&, const int32_t*,
-                        dg_gaussians*, const int32_t*, void*, cudaStream_t);
+                        dg_gaussians*, const int32_t*, void*, bool, cudaStream_t);
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -397,7 +398,7 @@ int dg_xstep_part(int part, int ctas, const uint32_t* rect, const dg_camera* dev
                               eps, step, dev_step, z_unshared, copy_gid, a);
     if (rc != DG_OK) return rc;
     return launch_xstep(part, ctas, x, m, v, anchor, (anchor || z_unshared) ? copy_shared : nullptr, dev_cams, *plan,
-                        (const uint2*)rect, (const float4*)drec, a, dev_step, z_unshared, copy_gid,
+                        (const uint2*)rect, (const float4*)drec, a, dev_step, z_unshared, copy_gid, nullptr,
                         (cudaStream_t)stream);
 }
 
@@ -449,8 +450,45 @@ int dg_xstep_stream(int ctas, const uint32_t* rect, const dg_camera* dev_cams, c
     rc = ensure_init();
     if (rc != DG_OK) return rc;
     return launch_xstep_stream(ctas, x, m, v, anchor, (anchor || z_unshared) ? copy_shared : nullptr, dev_cams,
-                               *plan, (const uint2*)rect, a, dev_step, z_unshared, copy_gid, ws,
+                               *plan, (const uint2*)rect, a, dev_step, z_unshared, copy_gid, ws, true,
                                (cudaStream_t)stream);
+}
+
+int dg_xstep_groups(const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan, const dg_gaussians* x,
+                    void* ws, size_t ws_bytes, void* stream)
+{
+    if (!valid_plan(plan) || !valid_gauss(x) || plan->blk_off[plan->n_blocks] > x->n) return DG_ERR_INVALID;
+    for (int k = 0; k < plan->n_blocks; k++)
+        if (plan->blk_view_off[k + 1] - plan->blk_view_off[k] > 1) return DG_ERR_INVALID;   // one view per block
+    if (plan->n_rec > 0 && (!rect || !dev_cams)) return DG_ERR_INVALID;
+    if (!aligned8(rect) || !aligned8(dev_cams)) return DG_ERR_INVALID;
+    if (x->n > 0 && (!ws || !aligned16(ws))) return DG_ERR_INVALID;
+    if (ws_bytes < xstep_stream_ws_bytes(x->n)) return DG_ERR_WORKSPACE;
+    return launch_xstep_groups(x, dev_cams, *plan, (const uint2*)rect, ws, (cudaStream_t)stream);
+}
+
+int dg_xstep_listed(int part, int ctas, const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan,
+                    const float* drec, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
+                    const uint8_t* copy_shared, const float* rho, const float* lr, float beta1, float beta2,
+                    float eps, int step, const int32_t* dev_step, dg_gaussians* z_unshared,
+                    const int32_t* copy_gid, void* ws, size_t ws_bytes, void* stream)
+{
+    if ((part != 1 && part != 2) || ctas < 0 || ctas > 65535) return DG_ERR_INVALID;
+    AdamArgs a;
+    int rc = xstep_args(part, rect, dev_cams, plan, drec, x, m, v, anchor, copy_shared, rho, lr, beta1, beta2, eps,
+                        step, dev_step, z_unshared, copy_gid, a);
+    if (rc != DG_OK) return rc;
+    if (x->n > 0 && (!ws || !aligned16(ws))) return DG_ERR_INVALID;
+    if (ws_bytes < xstep_stream_ws_bytes(x->n)) return DG_ERR_WORKSPACE;
+    const uint8_t* sh = (anchor || z_unshared) ? copy_shared : nullptr;
+    if (part == 1) {
+        rc = ensure_init();
+        if (rc != DG_OK) return rc;
+        return launch_xstep_stream(ctas, x, m, v, anchor, sh, dev_cams, *plan, (const uint2*)rect, a, dev_step,
+                                   z_unshared, copy_gid, ws, false, (cudaStream_t)stream);
+    }
+    return launch_xstep(3, ctas, x, m, v, anchor, sh, dev_cams, *plan, (const uint2*)rect, (const float4*)drec, a,
+                        dev_step, z_unshared, copy_gid, ws, (cudaStream_t)stream);
 }
 
 int dg_xstep_from_records(const uint32_t* rect, const dg_camera* dev_cams, const dg_plan* plan, const float* drec,

@@ -775,25 +775,23 @@ __device__ __forceinline__ void step_planes(GView& x, GView& m, GView& v, const 
     }
 }
 
-// PART 0: every CTA; PART 2: only the CTAs with at least one kept record
-template <int DEG, int PART>
-__global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView v, GView an,
-                                                        const uint8_t* __restrict__ shared,
-                                                        const dg_camera* __restrict__ cams, dg_plan plan,
-                                                        const uint2* __restrict__ rect,
-                                                        const float4* __restrict__ drec, AdamArgs a,
-                                                        const int32_t* __restrict__ dev_step, ZOut zo)
+// The fused adjoint + step of the group of kXsThreads copies from c0.  CHECK:
+// first find out whether a copy of the group has a kept record and leave the
+// group (uniformly) if none has: k_xstep_idle or k_xstep_stream steps it.
+template <int DEG, bool CHECK>
+__device__ __forceinline__ void xstep_group(int64_t c0, GView& x, GView& m, GView& v, const GView& an,
+                                            const uint8_t* __restrict__ shared,
+                                            const dg_camera* __restrict__ cams, const dg_plan& plan,
+                                            const uint2* __restrict__ rect, const float4* __restrict__ drec,
+                                            const AdamArgs& a, float ic1, float ic2, const ZOut& zo,
+                                            float* s_gc, float* s_Y)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
-    __shared__ __align__(16) float s_gc[3][kXsThreads];
-    __shared__ __align__(16) float s_Y[NK][kXsThreads];
     const int tid = threadIdx.x;
-    const int64_t c0 = (int64_t)blockIdx.x * kXsThreads, c = c0 + tid;
+    const int64_t c = c0 + tid;
     CamL cam;
     const int64_t r = copy_record(c, x.n, plan, cams, rect, cam);
-    if (PART == 2 && !__syncthreads_or(r >= 0)) return;    // uniform: the CTA is stepped by k_xstep_idle
-    float ic1, ic2;
-    bias_corr(a, dev_step, ic1, ic2);
+    if (CHECK && !__syncthreads_or(r >= 0)) return;    // uniform
     float gc[3] = {0.f, 0.f, 0.f}, Y[NK];
 #pragma unroll
     for (int kk = 0; kk < NK; kk++) Y[kk] = 0.f;
@@ -817,11 +815,40 @@ __global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView
         step_fields(x, m, v, an, c, s, mo, q, sc, gmu, go, gq, gs, a, ic1, ic2, zo);
     }
 #pragma unroll
-    for (int ch = 0; ch < 3; ch++) s_gc[ch][tid] = gc[ch];
+    for (int ch = 0; ch < 3; ch++) s_gc[ch * kXsThreads + tid] = gc[ch];
 #pragma unroll
-    for (int kk = 0; kk < NK; kk++) s_Y[kk][tid] = Y[kk];
+    for (int kk = 0; kk < NK; kk++) s_Y[kk * kXsThreads + tid] = Y[kk];
     __syncthreads();
-    step_planes<NK, 6, false>(x, m, v, an, shared, c0, &s_gc[0][0], &s_Y[0][0], a, ic1, ic2, zo);
+    step_planes<NK, 6, false>(x, m, v, an, shared, c0, s_gc, s_Y, a, ic1, ic2, zo);
+}
+
+// PART 0: every CTA; PART 2: only the CTAs with at least one kept record;
+// PART 3: CTA b steps the group alist[-b] of those k_idle_groups listed as
+// holding a kept record (the list grows down from alist[0]), and the CTAs
+// past the list's length actr[0] leave at once: they all come after the
+// stepping CTAs, instead of each taking its slot among them to find out.
+template <int DEG, int PART>
+__global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView v, GView an,
+                                                        const uint8_t* __restrict__ shared,
+                                                        const dg_camera* __restrict__ cams, dg_plan plan,
+                                                        const uint2* __restrict__ rect,
+                                                        const float4* __restrict__ drec, AdamArgs a,
+                                                        const int32_t* __restrict__ dev_step, ZOut zo,
+                                                        const int32_t* __restrict__ alist,
+                                                        const uint32_t* __restrict__ actr)
+{
+    constexpr int NK = (DEG + 1) * (DEG + 1);
+    __shared__ __align__(16) float s_gc[3 * kXsThreads];
+    __shared__ __align__(16) float s_Y[NK * kXsThreads];
+    int64_t grp = blockIdx.x;
+    if (PART == 3) {
+        if (blockIdx.x >= *actr) return;               // uniform
+        grp = alist[-(int64_t)blockIdx.x];
+    }
+    float ic1, ic2;
+    bias_corr(a, dev_step, ic1, ic2);
+    xstep_group<DEG, PART == 2>(grp * kXsThreads, x, m, v, an, shared, cams, plan, rect, drec, a, ic1, ic2, zo,
+                                s_gc, s_Y);
 }
 
 // the groups of k_xstep<PART 2>'s complement: no copy with a kept record, so
@@ -884,11 +911,13 @@ constexpr int kStStages = DG_XSTEP_STAGES;
 static_assert(kStStages >= 2, "the ring needs a unit in flight beside the one stepped");
 
 // one warp per group of kXsThreads copies: appends the group to list if none
-// of its copies has a kept record (the order of the list is unspecified);
-// ctr[0] counts the listed groups
-__global__ void __launch_bounds__(256) k_idle_groups(int64_t n, const dg_camera* __restrict__ cams, dg_plan plan,
-                                                     const uint2* __restrict__ rect, int32_t* __restrict__ list,
-                                                     uint32_t* __restrict__ ctr)
+// of its copies has a kept record, ctr[0] counting them, and else to the
+// list's other end (list[n_groups - 1], list[n_groups - 2], ...), ctr[1]
+// counting those; each group is listed once, so the two never meet (the
+// order within each is unspecified)
+__global__ void __launch_bounds__(256) k_idle_groups(int64_t n, int64_t n_groups, const dg_camera* __restrict__ cams,
+                                                     dg_plan plan, const uint2* __restrict__ rect,
+                                                     int32_t* __restrict__ list, uint32_t* __restrict__ ctr)
 {
     const int64_t grp = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -906,8 +935,11 @@ __global__ void __launch_bounds__(256) k_idle_groups(int64_t n, const dg_camera*
             }
         }
     }
-    if (__any_sync(0xffffffffu, kept)) return;
-    if (lane == 0) list[atomicAdd(ctr, 1u)] = (int32_t)grp;
+    const bool any = __any_sync(0xffffffffu, kept);
+    if (lane == 0) {
+        if (any) list[n_groups - 1 - (int64_t)atomicAdd(ctr + 1, 1u)] = (int32_t)grp;
+        else list[atomicAdd(ctr, 1u)] = (int32_t)grp;
+    }
 }
 
 // what a thread needs of its group: the copy c0 + tid of the field rows and
@@ -1294,16 +1326,35 @@ int xstep_stream_init()
     return DG_OK;
 }
 
-// workspace of the streamed part 1: two counters (16 bytes), then the list
+// workspace of the listed steps: two counters (16 bytes), then the list of
+// one entry per group (the groups without a kept record from the front, the
+// others from the back)
 size_t xstep_stream_ws_bytes(int64_t n)
 {
     return 16 + 4 * (size_t)((n + kXsThreads - 1) / kXsThreads);
 }
 
+// both lists of k_idle_groups into ws
+int launch_xstep_groups(const dg_gaussians* x, const dg_camera* cams, const dg_plan& plan, const uint2* rect,
+                        void* ws, cudaStream_t st)
+{
+    if (x->n == 0) return DG_OK;
+    uint32_t* ctr = static_cast<uint32_t*>(ws);
+    int32_t* list = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + 16);
+    const int64_t n_groups = (x->n + kXsThreads - 1) / kXsThreads;
+    if (cudaMemsetAsync(ctr, 0, 8, st) != cudaSuccess) return DG_ERR_CUDA;
+    k_idle_groups<<<(unsigned)((n_groups + 7) / 8), 256, 0, st>>>(x->n, n_groups, cams, plan, rect, list, ctr);
+    note_launch();
+    DG_CHECK_LAUNCH();
+    return DG_OK;
+}
+
+// build_lists: list the groups first (launch_xstep_groups); else step the
+// list an earlier launch_xstep_groups left in ws
 int launch_xstep_stream(int ctas, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
                         const uint8_t* shared, const dg_camera* cams, const dg_plan& plan, const uint2* rect,
                         const AdamArgs& a, const int32_t* dev_step, dg_gaussians* z, const int32_t* gid, void* ws,
-                        cudaStream_t st)
+                        bool build_lists, cudaStream_t st)
 {
     if (x->n == 0) return DG_OK;
     GView xv = gview(x), mv = gview(m), vv = gview(v);
@@ -1313,9 +1364,10 @@ int launch_xstep_stream(int ctas, dg_gaussians* x, dg_gaussians* m, dg_gaussians
     zo.gid = z ? gid : nullptr;
     uint32_t* ctr = static_cast<uint32_t*>(ws);
     int32_t* list = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + 16);
-    const int64_t n_groups = (x->n + kXsThreads - 1) / kXsThreads;
-    if (cudaMemsetAsync(ctr, 0, 8, st) != cudaSuccess) return DG_ERR_CUDA;
-    k_idle_groups<<<(unsigned)((n_groups + 7) / 8), 256, 0, st>>>(x->n, cams, plan, rect, list, ctr);
+    if (build_lists) {
+        const int rc = launch_xstep_groups(x, cams, plan, rect, ws, st);
+        if (rc != DG_OK) return rc;
+    }
     int dev = 0, sms = 0, least = 0, greatest = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -1345,19 +1397,20 @@ int launch_xstep_stream(int ctas, dg_gaussians* x, dg_gaussians* m, dg_gaussians
     DG_ST_CASE(3)
     }
 #undef DG_ST_CASE
-    note_launch(2);
+    note_launch();
     if (e != cudaSuccess) return DG_ERR_CUDA;
     DG_CHECK_LAUNCH();
     return DG_OK;
 }
 
 // part 0: the whole step; 1: the groups without a kept record (drec unused;
-// `ctas` CTAs, 0 = one per group); 2: the groups with one.  z / gid not NULL:
+// `ctas` CTAs, 0 = one per group); 2: the groups with one; 3: the groups
+// with one as listed in ws by launch_xstep_groups.  z / gid not NULL:
 // unshared copies also stored to z at their global ids.
 int launch_xstep(int part, int ctas, dg_gaussians* x, dg_gaussians* m, dg_gaussians* v, const dg_gaussians* anchor,
                  const uint8_t* shared, const dg_camera* cams, const dg_plan& plan, const uint2* rect,
                  const float4* drec, const AdamArgs& a, const int32_t* dev_step, dg_gaussians* z,
-                 const int32_t* gid, cudaStream_t st)
+                 const int32_t* gid, const void* ws, cudaStream_t st)
 {
     if (x->n == 0) return DG_OK;
     GView xv = gview(x), mv = gview(m), vv = gview(v);
@@ -1368,14 +1421,21 @@ int launch_xstep(int part, int ctas, dg_gaussians* x, dg_gaussians* m, dg_gaussi
     const int64_t n_groups = (x->n + kXsThreads - 1) / kXsThreads;
     dim3 grid((unsigned)n_groups);
     dim3 grid_idle((unsigned)(ctas > 0 && ctas < n_groups ? ctas : n_groups));
+    const uint32_t* actr = part == 3 ? static_cast<const uint32_t*>(ws) + 1 : nullptr;
+    const int32_t* alist = part == 3 ? reinterpret_cast<const int32_t*>(static_cast<const char*>(ws) + 16) +
+                                           (n_groups - 1)
+                                     : nullptr;
 #define DG_XSTEP_CASE(DEG)                                                                                      \
     case DEG:                                                                                                   \
         if (part == 0)                                                                                          \
             k_xstep<DEG, 0><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a,     \
-                                                         dev_step, zo);                                         \
+                                                         dev_step, zo, nullptr, nullptr);                       \
         else if (part == 2)                                                                                     \
             k_xstep<DEG, 2><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a,     \
-                                                         dev_step, zo);                                         \
+                                                         dev_step, zo, nullptr, nullptr);                       \
+        else if (part == 3)                                                                                     \
+            k_xstep<DEG, 3><<<grid, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, drec, a,     \
+                                                         dev_step, zo, alist, actr);                            \
         else                                                                                                    \
             k_xstep_idle<DEG><<<grid_idle, kXsThreads, 0, st>>>(xv, mv, vv, av, shared, cams, plan, rect, a,      \
                                                                 dev_step, zo);                                  \

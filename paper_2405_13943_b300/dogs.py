@@ -336,6 +336,29 @@ def dg_xstep_stream(vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer, v: Gaus
                                     ws.numel() * ws.element_size(), L.stream_handle(stream)), "dg_xstep_stream")
 
 
+def dg_xstep_groups(vb: ViewBatch, x: GaussianBuffer, ws: torch.Tensor, stream=None) -> None:
+    """Lists in ws (from xstep_stream_workspace(x)) the groups of copies
+    without a kept record and those with one, for dg_xstep_listed."""
+    L.check(L.lib().dg_xstep_groups(L.ptr(vb.rect), L.ptr(vb.dev_cams), C.byref(vb.plan), x.ref, L.ptr(ws),
+                                    ws.numel() * ws.element_size(), L.stream_handle(stream)), "dg_xstep_groups")
+
+
+def dg_xstep_listed(part: int, vb: ViewBatch, x: GaussianBuffer, m: GaussianBuffer, v: GaussianBuffer,
+                    anchor: Optional[GaussianBuffer], shared: Optional[torch.Tensor], rho, lr, ws: torch.Tensor,
+                    beta1=0.9, beta2=0.999, eps=1e-15, step=1, dev_step: Optional[torch.Tensor] = None,
+                    stream=None, ctas: int = 0, z_unshared: Optional[GaussianBuffer] = None,
+                    gid: Optional[torch.Tensor] = None) -> None:
+    """dg_xstep_part's part 1 (streamed by `ctas` CTAs, 0: one per SM) or
+    part 2 (one CTA per listed group) over the lists dg_xstep_groups left in
+    ws."""
+    L.check(L.lib().dg_xstep_listed(int(part), int(ctas), L.ptr(vb.rect), L.ptr(vb.dev_cams), C.byref(vb.plan),
+                                    L.ptr(vb.drec), x.ref, m.ref, v.ref, None if anchor is None else anchor.ref,
+                                    L.ptr(shared), L.rho_arg(rho), L.floats(lr), beta1, beta2, eps, int(step),
+                                    L.ptr(dev_step), None if z_unshared is None else z_unshared.ref, L.ptr(gid),
+                                    L.ptr(ws), ws.numel() * ws.element_size(), L.stream_handle(stream)),
+            "dg_xstep_listed")
+
+
 def dg_densify_stats(vb: ViewBatch, stats: torch.Tensor, stream=None) -> None:
     """Adds one iteration's densification statistic of every kept record into
     stats (float32, 2 per copy): the norm of its projected mean's gradient in

@@ -73,6 +73,12 @@ class DogsTrainer:
         # "stream_early" -- the same right after the projection; "grid" --
         # dg_xstep_part 1 right after the projection
         self.idle_mode = "stream"
+        # with a streamed part 1: the fused part 2 by persistent CTAs over the
+        # list of groups with a kept record (dg_xstep_listed), so that no CTA
+        # starts for the groups the side stream steps; False: one CTA per
+        # group, each finding out for itself (dg_xstep_part 2)
+        self.listed_part2 = True
+        self._lists_ready = None
         self.n_sm = torch.cuda.get_device_properties(device).multi_processor_count if self.side is not None else 0
         self.adaptive = adaptive
         if adaptive is not None:
@@ -164,7 +170,7 @@ class DogsTrainer:
         self.cam_pool = [D.cams_to_device(D.plan_views(vs, split.blk_off, *self.tile)[0], dev)
                          for vs in self.view_sets]
         self.graphs = {}
-        self._idle_queued = False
+        self._idle_queued, self._lists_ready = False, None
         if not first and calibrate:
             self.calibrate_capacity()
 
@@ -329,7 +335,14 @@ class DogsTrainer:
         cur = torch.cuda.current_stream()
         self.side.wait_stream(cur)
         with torch.cuda.stream(self.side):
-            if self.idle_mode.startswith("stream"):
+            if self.idle_mode.startswith("stream") and self.listed_part2:
+                D.dg_xstep_groups(self.vb, self.x, self.xs_ws)
+                self._lists_ready = torch.cuda.Event()
+                self._lists_ready.record(self.side)
+                D.dg_xstep_listed(1, self.vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(),
+                                  self.lr, self.xs_ws, step=1, dev_step=self.dev_step,
+                                  ctas=self.n_sm * self.idle_ctas_per_sm, **self._zargs(zfuse))
+            elif self.idle_mode.startswith("stream"):
                 D.dg_xstep_stream(self.vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(), self.lr,
                                   self.xs_ws, step=1, dev_step=self.dev_step, ctas=self.n_sm * self.idle_ctas_per_sm,
                                   **self._zargs(zfuse))
@@ -357,8 +370,14 @@ class DogsTrainer:
             self.idle_xstep(zfuse)                 # beside the compositing adjoint
         if self._split_xstep() and self._idle_queued:
             bwd_records(vb, bg=self.bg)
-            D.dg_xstep_part(2, vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(), self.lr,
-                            step=1, dev_step=self.dev_step, **self._zargs(zfuse))
+            if self._lists_ready is not None:      # the lists built on the side stream
+                torch.cuda.current_stream().wait_event(self._lists_ready)
+                D.dg_xstep_listed(2, vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(), self.lr,
+                                  self.xs_ws, step=1, dev_step=self.dev_step, **self._zargs(zfuse))
+                self._lists_ready = None
+            else:
+                D.dg_xstep_part(2, vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(), self.lr,
+                                step=1, dev_step=self.dev_step, **self._zargs(zfuse))
             torch.cuda.current_stream().wait_stream(self.side)
             self._idle_queued = False
         elif self.fused and D.one_view_per_block(vb.plan):

@@ -170,6 +170,40 @@ def test_xstep_stream_rejects_bad_arguments_before_launch(lib):
     assert call(nb=need - 1) == L.DG_ERR_WORKSPACE
 
 
+def test_xstep_listed_rejects_bad_arguments_before_launch(lib):
+    """dg_xstep_groups checks the plan, pointers and workspace; dg_xstep_listed
+    makes dg_xstep_part's checks, takes parts 1 and 2 only and checks its grid
+    bound and workspace, all on the host."""
+    from paper_2405_13943_b300 import dogs as D
+    arr, plan = D.plan_views([S.cube_camera(32, 32)], [0, 300], 16, 16)
+    x = L.DgGaussians(0x10000, 300, 300, 0, 0)
+    rho, lr = L.floats([1] * 5), L.floats([1] * 6)
+    rect, cams, drec, shared, ws = 0x30000, 0x40000, 0x50000, 0x60000, 0x80000
+    need = lib.dg_xstep_stream_workspace_size(C.byref(x))
+
+    def groups(r=rect, w=ws, nb=need, xx=x):
+        return lib.dg_xstep_groups(r, cams, C.byref(plan), C.byref(xx), w, nb, None)
+    assert groups(r=None) == L.DG_ERR_INVALID
+    assert groups(r=rect + 4) == L.DG_ERR_INVALID               # misaligned rectangles
+    assert groups(w=None) == L.DG_ERR_INVALID
+    assert groups(w=ws + 8) == L.DG_ERR_INVALID
+    assert groups(nb=need - 1) == L.DG_ERR_WORKSPACE
+    assert groups(xx=L.DgGaussians(0x10000, 200, 200, 0, 0)) == L.DG_ERR_INVALID   # the plan spans 300 copies
+
+    def listed(part=2, ctas=0, d=drec, w=ws, nb=need):
+        return lib.dg_xstep_listed(part, ctas, rect, cams, C.byref(plan), d, C.byref(x), C.byref(x), C.byref(x),
+                                   None, shared, rho, lr, 0.9, 0.999, 1e-15, 1, None, None, None, w, nb, None)
+    for part in (0, 3, -1):
+        assert listed(part=part) == L.DG_ERR_INVALID
+    assert listed(ctas=-1) == L.DG_ERR_INVALID
+    assert listed(ctas=65536) == L.DG_ERR_INVALID
+    assert listed(d=None) == L.DG_ERR_INVALID                   # part 2 reads the records' gradients
+    assert listed(d=drec + 8) == L.DG_ERR_INVALID
+    assert listed(w=ws + 4) == L.DG_ERR_INVALID
+    assert listed(nb=need - 4) == L.DG_ERR_WORKSPACE
+    assert listed(part=1, nb=need - 4) == L.DG_ERR_WORKSPACE
+
+
 def test_render_slot_workspace_bounds_every_admissible_batch(lib):
     """The render server sizes a slot's workspace once, on the host, for any
     batch of at most max_batch views and max_batch_pixels pixels: random mixes

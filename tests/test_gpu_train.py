@@ -403,6 +403,86 @@ def test_streamed_idle_xstep_equals_part1(mods, ctas):
         assert torch.equal(ref[n].data, out[n].data), n
 
 
+@pytest.mark.parametrize("ctas", [0, 5])
+def test_listed_xstep_equals_one_part(mods, ctas):
+    """dg_xstep_groups lists every group of 128 copies once, those without a
+    kept record from the front of the workspace's list and the others from
+    its back; dg_xstep_listed part 1 then part 2 over those lists takes the
+    one-part step bit for bit, with the unshared copies' store into z."""
+    D, srv, T = mods
+    wl, z0, targets = small_setup(D, srv, seed=41)
+    tr = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, rho=(1e-2,) * 5, loss="dssim", intv=1)
+    tr.calibrate_capacity()
+    assert tr._zfuse(True)
+    tr.step(graph=False)                       # non-zero moments and anchors
+    vb = tr.vb
+    vb.dev_cams.copy_(tr.cam_pool[tr.t % len(tr.view_sets)])
+    D.dg_project(tr.x, vb)
+    D.dg_bin_sort(vb)
+    D.dg_rasterize_fwd(vb, tr.bg)
+    tr._loss(tr.targets[tr.t % len(tr.view_sets)])
+    D.dg_rasterize_bwd_records(vb, bg=tr.bg)
+    torch.cuda.synchronize()
+    args = (tr.anchor, tr.shared, tr.rho, tr.lr)
+    ref = {n: getattr(tr, n).clone() for n in ("x", "m", "v", "z")}
+    out = {n: getattr(tr, n).clone() for n in ("x", "m", "v", "z")}
+    D.dg_xstep_part(0, vb, ref["x"], ref["m"], ref["v"], *args, step=2, z_unshared=ref["z"], gid=tr.gid)
+    ws = D.xstep_stream_workspace(tr.x)
+    ws.fill_(-1)                               # the call zeroes its own counters
+    D.dg_xstep_groups(vb, tr.x, ws)
+    torch.cuda.synchronize()
+    n_groups = -(-tr.x.n // 128)
+    n_idle, n_act = int(ws[0].item()), int(ws[1].item())
+    assert n_idle + n_act == n_groups and 0 < n_idle < n_groups
+    entries = ws[4:4 + n_groups].cpu().numpy()
+    idle, act = entries[:n_idle], entries[n_groups - n_act:]
+    assert sorted(np.concatenate([idle, act]).tolist()) == list(range(n_groups))
+    rect = vb.rect.view(-1, 2)[:vb.n_rec].cpu().numpy().view(np.uint32)
+    kept = np.zeros(tr.x.n, bool)
+    vis = (rect[:, 0] & 0xFFFF) != (rect[:, 1] & 0xFFFF)
+    for c in vb.host_cams:
+        b, e = int(c.gauss_begin), int(c.gauss_end)
+        kept[b:e] |= vis[int(c.rec_off):int(c.rec_off) + e - b]
+    g_act = np.pad(kept, (0, n_groups * 128 - len(kept))).reshape(n_groups, 128).any(1)
+    assert sorted(act.tolist()) == np.flatnonzero(g_act).tolist()
+    D.dg_xstep_listed(1, vb, out["x"], out["m"], out["v"], *args, ws, step=2, ctas=ctas, z_unshared=out["z"],
+                      gid=tr.gid)
+    D.dg_xstep_listed(2, vb, out["x"], out["m"], out["v"], *args, ws, step=2, z_unshared=out["z"], gid=tr.gid)
+    torch.cuda.synchronize()
+    for n in ref:
+        assert torch.equal(ref[n].data, out[n].data), n
+    # the same lists serve the next step too, the parts in either order
+    D.dg_xstep_part(0, vb, ref["x"], ref["m"], ref["v"], *args, step=3)
+    D.dg_xstep_listed(2, vb, out["x"], out["m"], out["v"], *args, ws, step=3)
+    D.dg_xstep_listed(1, vb, out["x"], out["m"], out["v"], *args, ws, step=3, ctas=ctas)
+    torch.cuda.synchronize()
+    for n in ("x", "m", "v"):
+        assert torch.equal(ref[n].data, out[n].data), n
+
+
+@pytest.mark.parametrize("listed", [True, False])
+def test_stream_trainer_listed_part2_matches_one_part(mods, listed):
+    """Graph replays of the streamed trainer, with part 2 over the side
+    stream's list or one CTA per group, equal the one-part step (up to the
+    float atomics of the compositing adjoint)."""
+    D, srv, T = mods
+    wl, z0, targets = small_setup(D, srv, seed=43)
+    kw = dict(rho=(1e-2,) * 5, loss="dssim", intv=2)
+    a = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, overlap=True, **kw)
+    a.idle_mode, a.listed_part2 = "stream", listed
+    a.calibrate_capacity()
+    b = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, overlap=False, **kw)
+    b.calibrate_capacity()
+    for _ in range(5):
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    for n in ("x", "z", "m"):
+        ga, gb = groups(getattr(a, n)), groups(getattr(b, n))
+        for k in ga:
+            assert rel_l2(ga[k], gb[k]) < REL_L2, (n, k)
+
+
 @pytest.mark.parametrize("mode", ["stream", "grid"])
 def test_overlapped_xstep_trainer_matches(mods, mode):
     """Graph replays with the idle part of the x-step on a side stream equal
