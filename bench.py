@@ -450,13 +450,17 @@ def run_ours(args, dist, rank, world):
             calls.append(("xstep_idle", lambda: D.dg_xstep_stream(vb, *xs_args, tr.xs_ws, step=1, dev_step=tr.dev_step,
                                                                   ctas=tr.n_sm * tr.idle_ctas_per_sm, **zargs)))
         else:
-            calls.append(("xstep_idle", lambda: D.dg_xstep_part(1, vb, *xs_args, step=1, dev_step=tr.dev_step,
-                                                                ctas=tr.n_sm * tr.idle_ctas_per_sm, **zargs)))
+            def idle_grid():
+                if tr.listed_part2:
+                    D.dg_xstep_groups(vb, tr.x, tr.xs_ws)
+                D.dg_xstep_part(1, vb, *xs_args, step=1, dev_step=tr.dev_step, ctas=tr.n_sm * tr.idle_ctas_per_sm,
+                                **zargs)
+            calls.append(("xstep_idle", idle_grid))
     calls += [("bin_sort", lambda: D.dg_bin_sort(vb)),
               ("rasterize_fwd", lambda: D.dg_rasterize_fwd(vb, tr.bg)),
               ("loss", lambda: tr._loss(tr.targets[tr.t % len(tr.view_sets)]))]
-    listed = split and tr.idle_mode.startswith("stream") and tr.listed_part2
-    if fused and listed:    # part 2 over the groups dg_xstep_stream listed in tr.xs_ws
+    listed = split and tr.listed_part2
+    if fused and listed:    # part 2 over the groups listed in tr.xs_ws by the part-1 call
         calls += [("rasterize_bwd", bwd_fused),
                   ("xstep", lambda: D.dg_xstep_listed(2, vb, *xs_args, tr.xs_ws, step=1, dev_step=tr.dev_step,
                                                       **zargs))]

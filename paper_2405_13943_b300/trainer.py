@@ -73,10 +73,11 @@ class DogsTrainer:
         # "stream_early" -- the same right after the projection; "grid" --
         # dg_xstep_part 1 right after the projection
         self.idle_mode = "stream"
-        # with a streamed part 1: the fused part 2 by persistent CTAs over the
-        # list of groups with a kept record (dg_xstep_listed), so that no CTA
-        # starts for the groups the side stream steps; False: one CTA per
-        # group, each finding out for itself (dg_xstep_part 2)
+        # the fused part 2 over the list of groups with a kept record that
+        # the side stream builds first (dg_xstep_groups, dg_xstep_listed), so
+        # that the CTAs past it, which find nothing to step, come after those
+        # that step; False: one CTA per group, each finding out for itself
+        # (dg_xstep_part 2)
         self.listed_part2 = True
         self._lists_ready = None
         self.n_sm = torch.cuda.get_device_properties(device).multi_processor_count if self.side is not None else 0
@@ -347,6 +348,10 @@ class DogsTrainer:
                                   self.xs_ws, step=1, dev_step=self.dev_step, ctas=self.n_sm * self.idle_ctas_per_sm,
                                   **self._zargs(zfuse))
             else:
+                if self.listed_part2:
+                    D.dg_xstep_groups(self.vb, self.x, self.xs_ws)
+                    self._lists_ready = torch.cuda.Event()
+                    self._lists_ready.record(self.side)
                 D.dg_xstep_part(1, self.vb, self.x, self.m, self.v, self.anchor, self.shared, self.rho_arg(),
                                 self.lr, step=1, dev_step=self.dev_step, ctas=self.n_sm * self.idle_ctas_per_sm,
                                 **self._zargs(zfuse))

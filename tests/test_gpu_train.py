@@ -460,16 +460,17 @@ def test_listed_xstep_equals_one_part(mods, ctas):
         assert torch.equal(ref[n].data, out[n].data), n
 
 
-@pytest.mark.parametrize("listed", [True, False])
-def test_stream_trainer_listed_part2_matches_one_part(mods, listed):
-    """Graph replays of the streamed trainer, with part 2 over the side
-    stream's list or one CTA per group, equal the one-part step (up to the
-    float atomics of the compositing adjoint)."""
+@pytest.mark.parametrize("mode,listed", [("stream", True), ("stream", False), ("grid", True), ("grid", False)])
+def test_trainer_listed_part2_matches_one_part(mods, mode, listed):
+    """Graph replays of the trainer with the idle part on the side stream,
+    streamed or as a grid, and part 2 over the side stream's list or one CTA
+    per group, equal the one-part step (up to the float atomics of the
+    compositing adjoint)."""
     D, srv, T = mods
     wl, z0, targets = small_setup(D, srv, seed=43)
     kw = dict(rho=(1e-2,) * 5, loss="dssim", intv=2)
     a = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, overlap=True, **kw)
-    a.idle_mode, a.listed_part2 = "stream", listed
+    a.idle_mode, a.listed_part2 = mode, listed
     a.calibrate_capacity()
     b = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, overlap=False, **kw)
     b.calibrate_capacity()
