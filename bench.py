@@ -315,7 +315,7 @@ def copy_groups(tr, rect):
 
 
 def algorithmic_bytes(tr, vb_rect_visible: int, n_visible_copies: int, active_groups=None, zfuse=False,
-                      instances: int = 0):
+                      instances: int = 0, listed: bool = False, idle_tests: bool = True):
     sp = tr.split
     P = 59
     n_c = sp.n_copies
@@ -343,12 +343,16 @@ def algorithmic_bytes(tr, vb_rect_visible: int, n_visible_copies: int, active_gr
     }
     if active_groups is not None:
         # split x-step: part 2 over the groups of 128 copies with a kept record, part 1 over the
-        # others (plus the 8-byte rectangle of each of its copies, read to find them)
+        # others.  listed: the two lists are built first from every copy's 8-byte rectangle (and one
+        # 4-byte entry per group); idle_tests: part 1 reads the rectangle of each of its copies to
+        # find its groups (the grid form, or the streamed form building its own list)
         act = np.repeat(active_groups, 128)[:n_c]
         sh = sp.copy_shared().astype(bool)
         na, nsa = int(act.sum()), int((act & sh).sum())
         out["xstep"] = na * P * 24 + nsa * P * 4 + n_visible_copies * 56
-        out["xstep_idle"] = (n_c - na) * (P * 24 + 8) + (n_sc - nsa) * P * 4
+        out["xstep_idle"] = (n_c - na) * (P * 24 + (8 if idle_tests else 0)) + (n_sc - nsa) * P * 4
+        if listed:
+            out["xstep_groups"] = n_c * 8 + 4 * len(active_groups)
         if zfuse:
             # the unshared copies' values stored into z (4 B per float) with their global ids (4 B)
             # here, so the consensus moves the shared globals' bytes only
@@ -391,7 +395,8 @@ def run_ours(args, dist, rank, world):
     tuned = None
     if not args.no_autotune and not args.profile and not args.variant:
         from paper_2405_13943_b300 import autotune
-        tuned = autotune.tune(tr, use_cache=False, idle_modes=(args.idle_mode,) if args.idle_mode else ("stream", "grid"))
+        tuned = autotune.tune(tr, use_cache=False, idle_modes=(args.idle_mode,) if args.idle_mode else ("stream", "grid"),
+                              consensus=bool(cons))
         tile = tr.tile
         m_max = tr.calibrate_capacity()
     torch.cuda.synchronize()
@@ -445,22 +450,24 @@ def run_ours(args, dist, rank, world):
         D.dg_rasterize_bwd_records(vb, bg=tr.bg)
 
     calls = [("project", lambda: D.dg_project(tr.x, vb))]
+    listed = split and tr.listed_part2
     if split:       # the part that the graph runs on a side stream, timed here in sequence
-        if tr.idle_mode.startswith("stream"):
+        if listed:  # the two group lists, then part 1 over the first (streamed) or testing each group (grid)
+            calls.append(("xstep_groups", lambda: D.dg_xstep_groups(vb, tr.x, tr.xs_ws)))
+        if tr.idle_mode.startswith("stream") and listed:
+            calls.append(("xstep_idle", lambda: D.dg_xstep_listed(1, vb, *xs_args, tr.xs_ws, step=1,
+                                                                  dev_step=tr.dev_step,
+                                                                  ctas=tr.n_sm * tr.idle_ctas_per_sm, **zargs)))
+        elif tr.idle_mode.startswith("stream"):
             calls.append(("xstep_idle", lambda: D.dg_xstep_stream(vb, *xs_args, tr.xs_ws, step=1, dev_step=tr.dev_step,
                                                                   ctas=tr.n_sm * tr.idle_ctas_per_sm, **zargs)))
         else:
-            def idle_grid():
-                if tr.listed_part2:
-                    D.dg_xstep_groups(vb, tr.x, tr.xs_ws)
-                D.dg_xstep_part(1, vb, *xs_args, step=1, dev_step=tr.dev_step, ctas=tr.n_sm * tr.idle_ctas_per_sm,
-                                **zargs)
-            calls.append(("xstep_idle", idle_grid))
+            calls.append(("xstep_idle", lambda: D.dg_xstep_part(1, vb, *xs_args, step=1, dev_step=tr.dev_step,
+                                                                ctas=tr.n_sm * tr.idle_ctas_per_sm, **zargs)))
     calls += [("bin_sort", lambda: D.dg_bin_sort(vb)),
               ("rasterize_fwd", lambda: D.dg_rasterize_fwd(vb, tr.bg)),
               ("loss", lambda: tr._loss(tr.targets[tr.t % len(tr.view_sets)]))]
-    listed = split and tr.listed_part2
-    if fused and listed:    # part 2 over the groups listed in tr.xs_ws by the part-1 call
+    if fused and listed:    # part 2 over the groups listed in tr.xs_ws by the xstep_groups call
         calls += [("rasterize_bwd", bwd_fused),
                   ("xstep", lambda: D.dg_xstep_listed(2, vb, *xs_args, tr.xs_ws, step=1, dev_step=tr.dev_step,
                                                       **zargs))]
@@ -506,7 +513,8 @@ def run_ours(args, dist, rank, world):
     vis_rec = int(((rect[:, 0] & 0xFFFF) != (rect[:, 1] & 0xFFFF)).sum())
     instances = int(vb.count.item())
     _, active_groups = copy_groups(tr, rect)
-    alg = algorithmic_bytes(tr, vis_rec, vis_rec, active_groups if split else None, zf, instances)
+    alg = algorithmic_bytes(tr, vis_rec, vis_rec, active_groups if split else None, zf, instances,
+                            listed=listed, idle_tests=not (listed and tr.idle_mode.startswith("stream")))
     peaks, peak_src = measured_peaks()
     hbm_peak = float(peaks["hbm_gbs"])
     kern = {}

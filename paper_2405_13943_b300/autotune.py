@@ -77,16 +77,18 @@ def _kernel_times(tr, steps: int) -> Tuple[float, float]:
     return fw, bw
 
 
-def _time_graph_steps(tr, steps: int) -> float:
-    """Mean time (ms) of replayed iterations without a consensus, captured
-    afresh (and dropped afterwards)."""
+def _time_graph_steps(tr, steps: int, consensus: bool = False) -> float:
+    """Mean time (ms) of replayed iterations with or without a consensus,
+    the graphs of every pool entry captured afresh before the timing (and
+    dropped afterwards)."""
     tr.graphs.clear()
-    tr.step(consensus=False)
+    tr.prepare_graphs((consensus,))
+    tr.step(consensus=consensus)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(steps):
-        tr.step(consensus=False)
+        tr.step(consensus=consensus)
     e1.record()
     torch.cuda.synchronize()
     tr.graphs.clear()
@@ -106,7 +108,12 @@ def _apply(tr, best: Dict) -> None:
 
 
 def tune(tr, tiles: Sequence = TILES, warps: Sequence[int] = WARPS, stages: Sequence[int] = STAGES,
-         steps: int = 3, use_cache: bool = True, idle_modes: Sequence[str] = ("stream", "grid")) -> Dict:
+         steps: int = 3, use_cache: bool = True, idle_modes: Sequence[str] = ("stream", "grid"),
+         consensus: bool = False) -> Dict:
+    """Tile shape, then forward and backward variants, then (with the x-step
+    split) the side stream's form, timed by graph replays of iterations with
+    `consensus` as the run takes them, each form twice in alternation and
+    its best kept."""
     key = signature(tr)
     cache = {}
     if use_cache and os.path.exists(CACHE):
@@ -139,9 +146,11 @@ def tune(tr, tiles: Sequence = TILES, warps: Sequence[int] = WARPS, stages: Sequ
     idle = None
     if tr._split_xstep() and len(idle_modes) > 1:
         idle = {}
-        for mode in idle_modes:
-            tr.idle_mode = mode
-            idle[mode] = round(_time_graph_steps(tr, 4 * steps), 4)
+        for _ in range(2):
+            for mode in idle_modes:
+                tr.idle_mode = mode
+                t = round(_time_graph_steps(tr, 4 * steps, consensus), 4)
+                idle[mode] = min(idle.get(mode, t), t)
         best = dict(best, idle_mode=min(idle, key=idle.get))
         _apply(tr, best)
     out = dict(best, candidates=results, idle_modes=idle, cached=False)

@@ -484,6 +484,30 @@ def test_trainer_listed_part2_matches_one_part(mods, mode, listed):
             assert rel_l2(ga[k], gb[k]) < REL_L2, (n, k)
 
 
+@pytest.mark.parametrize("consensus", [False, True])
+def test_autotune_times_both_idle_forms_and_applies_the_faster(mods, consensus):
+    """A reduced search (one tile shape, two variants): both side-stream
+    forms are timed by replays, with or without the consensus, the faster
+    one and the chosen variants are applied, and the tuned trainer keeps
+    stepping without overflow."""
+    D, srv, T = mods
+    from paper_2405_13943_b300 import autotune
+    wl, z0, targets = small_setup(D, srv, seed=47)
+    tr = T.DogsTrainer(wl.split, z0.clone(), wl.views, targets, rho=(1e-2,) * 5, loss="dssim", intv=1)
+    tr.calibrate_capacity()
+    out = autotune.tune(tr, tiles=((16, 16),), warps=(1, 2), stages=(1,), steps=1, use_cache=False,
+                        consensus=consensus)
+    assert set(out["idle_modes"]) == {"stream", "grid"}
+    assert all(0 < t < float("inf") for t in out["idle_modes"].values())
+    assert out["idle_mode"] == min(out["idle_modes"], key=out["idle_modes"].get) == tr.idle_mode
+    assert tuple(out["tile"]) == (16, 16) and tr.tile == (16, 16)
+    assert not tr.graphs                       # the timing's graphs are dropped
+    for _ in range(3):
+        tr.step(consensus=consensus)
+    torch.cuda.synchronize()
+    assert not tr.overflowed()
+
+
 @pytest.mark.parametrize("mode", ["stream", "grid"])
 def test_overlapped_xstep_trainer_matches(mods, mode):
     """Graph replays with the idle part of the x-step on a side stream equal
