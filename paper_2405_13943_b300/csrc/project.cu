@@ -616,10 +616,11 @@ __global__ void __launch_bounds__(128, 4) k_project_bwd(GView x, const dg_camera
 // The step can be taken in two parts, by CTA of kXsThreads consecutive
 // copies: a CTA none of whose copies has a kept record has a zero rendering
 // gradient, so its step depends only on x, m, v and the anchors and can run
-// as soon as the projection has written the rectangles (k_xstep_idle,
-// alongside the compositing kernels); the CTAs with a kept record run after
-// the compositing adjoint (k_xstep with PART = 2).  Both take the step by the
-// same device functions, so the result is the same as the one-part step.
+// as soon as the projection has written the rectangles (k_xstep_idle or
+// k_xstep_stream, alongside the compositing kernels); the CTAs with a kept
+// record run after the compositing adjoint (k_xstep with PART = 2, or 3 over
+// the list k_idle_groups made of them).  All take the step by the same device
+// functions, so the result is the same as the one-part step.
 constexpr int kXsThreads = 128;
 
 // the record of copy c in its block's view, or -1 if the forward kept none
