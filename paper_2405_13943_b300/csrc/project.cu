@@ -845,6 +845,7 @@ __global__ void __launch_bounds__(kXsThreads, 4) k_xstep(GView x, GView m, GView
     if (PART == 3) {
         if (blockIdx.x >= *actr) return;               // uniform
         grp = alist[-(int64_t)blockIdx.x];
+        if (grp < 0 || grp * kXsThreads >= x.n) return;   // a list not made for these copies
     }
     float ic1, ic2;
     bias_corr(a, dev_step, ic1, ic2);
@@ -1280,9 +1281,14 @@ __global__ void __launch_bounds__(kStThreads) k_xstep_stream(GView x, GView m, G
 #pragma unroll
     for (int k = 0; k < 5; k++) rh.r[k] = rho_of(a, k);
     const StPair sp = st_pair_args(a, rh, ic1, ic2);
-    const uint32_t n_list = ctr[0], G = gridDim.x;
+    const int64_t n_groups = (x.n + kXsThreads - 1) / kXsThreads;
+    const uint32_t n_list = (uint32_t)min((int64_t)ctr[0], n_groups), G = gridDim.x;
     uint32_t li = blockIdx.x;
-    auto entry = [&](uint32_t i) { return i < n_list ? (int64_t)list[i] * kXsThreads : (int64_t)-1; };
+    // an entry outside the copies (a list not made for them) ends the CTA's walk
+    auto entry = [&](uint32_t i) {
+        const int64_t g = i < n_list ? (int64_t)list[i] : (int64_t)-1;
+        return g >= 0 && g < n_groups ? g * kXsThreads : (int64_t)-1;
+    };
     StRaw nr;
     StMeta cm, nm;
     st_load(nr, entry(li), x, shared, zo);
