@@ -447,6 +447,7 @@ int dg_xstep_stream(int ctas, const uint32_t* rect, const dg_camera* dev_cams, c
     if (rc != DG_OK) return rc;
     if (x->n > 0 && (!ws || !aligned16(ws))) return DG_ERR_INVALID;
     if (ws_bytes < xstep_stream_ws_bytes(x->n)) return DG_ERR_WORKSPACE;
+    if (x->n == 0) return DG_OK;                  // nothing to step: no device call
     rc = ensure_init();
     if (rc != DG_OK) return rc;
     return launch_xstep_stream(ctas, x, m, v, anchor, (anchor || z_unshared) ? copy_shared : nullptr, dev_cams,
@@ -481,6 +482,7 @@ int dg_xstep_listed(int part, int ctas, const uint32_t* rect, const dg_camera* d
     if (x->n > 0 && (!ws || !aligned16(ws))) return DG_ERR_INVALID;
     if (ws_bytes < xstep_stream_ws_bytes(x->n)) return DG_ERR_WORKSPACE;
     const uint8_t* sh = (anchor || z_unshared) ? copy_shared : nullptr;
+    if (x->n == 0) return DG_OK;                  // nothing to step: no device call
     if (part == 1) {
         rc = ensure_init();
         if (rc != DG_OK) return rc;

@@ -204,6 +204,26 @@ def test_xstep_listed_rejects_bad_arguments_before_launch(lib):
     assert listed(part=1, nb=need - 4) == L.DG_ERR_WORKSPACE
 
 
+def test_xstep_calls_on_no_copies_return_ok_without_the_device(lib):
+    """With no copies, the x-step entry points check their arguments and
+    return DG_OK without any device call (this runs without a GPU)."""
+    from paper_2405_13943_b300 import dogs as D
+    arr, plan = D.plan_views([S.cube_camera(32, 32)], [0, 0], 16, 16)
+    x = L.DgGaussians(0x10000, 0, 0, 0, 0)
+    rho, lr = L.floats([1] * 5), L.floats([1] * 6)
+    cams, nb = 0x40000, lib.dg_xstep_stream_workspace_size(C.byref(x))
+    assert nb == 16
+    assert lib.dg_xstep_groups(None, cams, C.byref(plan), C.byref(x), None, nb, None) == L.DG_OK
+    for part in (1, 2):
+        assert lib.dg_xstep_listed(part, 0, None, cams, C.byref(plan), None, C.byref(x), C.byref(x), C.byref(x),
+                                   None, None, rho, lr, 0.9, 0.999, 1e-15, 1, None, None, None, None, nb,
+                                   None) == L.DG_OK
+        assert lib.dg_xstep_part(part, 0, None, cams, C.byref(plan), None, C.byref(x), C.byref(x), C.byref(x),
+                                 None, None, rho, lr, 0.9, 0.999, 1e-15, 1, None, None, None, None) == L.DG_OK
+    assert lib.dg_xstep_stream(0, None, cams, C.byref(plan), C.byref(x), C.byref(x), C.byref(x), None, None,
+                               rho, lr, 0.9, 0.999, 1e-15, 1, None, None, None, None, nb, None) == L.DG_OK
+
+
 def test_render_slot_workspace_bounds_every_admissible_batch(lib):
     """The render server sizes a slot's workspace once, on the host, for any
     batch of at most max_batch views and max_batch_pixels pixels: random mixes
